@@ -1,0 +1,196 @@
+/*
+ * rtbvh -- closest-hit and any-hit ray queries against triangulated scenes
+ * through a BVH whose splits use the hybrid surface-area + distance cost of
+ * Wang et al., "An Improved Ray Tracing Acceleration Algorithm Based on
+ * Bounding Volume Hierarchies" (arXiv 2208.10008).  GB300 (sm_103a) only.
+ *
+ * Conventions for every entry point
+ *  - Return 0 (RT_OK) on success, a negative RT_E* code on failure;
+ *    rt_last_error() then gives a message (thread-local, valid until the
+ *    next call from the same thread).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is enqueued on it and the call returns without waiting,
+ *    unless the comment says "synchronous".  Inputs must not change and
+ *    outputs must not be read until the stream has reached the call.
+ *  - Buffers named *_dev are device pointers owned by the caller.  Handles
+ *    (rt_scene, rt_session) are owned by the library and freed by their
+ *    *_destroy call.
+ *  - Triangle ids are input order: triangle i is tris[9i .. 9i+8].  The
+ *    library's internal reordering is never visible.
+ *  - A scene's calls must be issued from one host thread at a time; calls on
+ *    different scenes may run concurrently.
+ */
+#ifndef RTBVH_H
+#define RTBVH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RT_OK 0
+#define RT_EINVAL (-1)     /* bad argument (null handle, negative size, bad params) */
+#define RT_ENOMEM (-2)     /* device or host allocation failed */
+#define RT_ENOTBUILT (-3)  /* trace on a scene whose BVH has not been built */
+#define RT_ETIMEOUT (-4)   /* a bounded device wait ran out (status word set) */
+#define RT_ECUDA (-5)      /* a CUDA runtime call failed */
+#define RT_EBUSY (-6)      /* resource in use (session admission) */
+#define RT_EINTERNAL (-7)  /* a device-side consistency check failed */
+
+typedef struct rt_scene_s* rt_scene;
+typedef struct rt_session_s* rt_session;
+
+/* One ray, 32 bytes, 16-byte aligned arrays.  Points o + t d with
+ * tmin < t < tmax are on the ray.  d need not be unit length; t is in units
+ * of |d|.  A ray with a non-finite component, or tmax <= tmin, misses. */
+typedef struct {
+  float ox, oy, oz, tmin;
+  float dx, dy, dz, tmax;
+} rt_ray;
+
+/* Closest-hit result, 16 bytes.  Miss: t = +inf, tri = -1, u = v = 0.
+ * (u, v) are the barycentric weights of vertices 1 and 2 of the hit
+ * triangle (the point is (1-u-v) v0 + u v1 + v v2). */
+typedef struct {
+  float t;
+  int32_t tri;
+  float u, v;
+} rt_hit;
+
+/* Build parameters (Sec. II.B-C).  Split cost of children A, B of node C:
+ *   alpha (S(A)/S(C) k_A t_i + S(B)/S(C) k_B t_i) + (1 - alpha) d^2 + t_trav
+ * (Eq. 2; Eq. 1 when alpha = 1) with S the AABB surface area (Eq. 3 boxes),
+ * k the triangle counts and d^2 = (d_A^2 + d_B^2)/2, d_X the distance from
+ * the centre of X's AABB to `source`.  dist_norm = 1 replaces d^2 by
+ * d^2 / diag(C)^2 * k_C t_i (scale-free); 0 keeps the paper's raw m^2.
+ * A node becomes a leaf when it holds at most max_leaf triangles. */
+typedef struct {
+  float alpha;      /* [0, 1] */
+  float t_i;        /* > 0 */
+  float t_trav;     /* >= 0 (never changes a split; kept for the cost report) */
+  float source[3];  /* ray source point of Eq. 2 */
+  int32_t max_leaf; /* 1 .. 15 */
+  int32_t bins;     /* candidate planes per axis + 1: 4 .. 32 */
+  int32_t width;    /* children per traversal node: 4 */
+  int32_t dist_norm;/* 0 or 1 */
+} rt_build_params;
+
+/* Trace flags */
+#define RT_NO_FP64_RETEST 1u /* skip the float64 re-test of flagged rays (diagnostics) */
+#define RT_COUNT_STATS 2u    /* count nodes visited / triangles tested per ray */
+
+typedef struct {
+  uint32_t flags;
+  const int32_t* skip_tri_dev; /* nullable; per-ray triangle id to ignore (-1 = none),
+                                  e.g. the triangle a reflected ray leaves from */
+  uint32_t* stats_dev;         /* nullable; with RT_COUNT_STATS, per ray [nodes, tris] */
+  int32_t* n_flagged_dev;      /* nullable; receives the number of rays the float32 pass
+                                  flagged for the float64 re-test */
+} rt_trace_params;
+
+/* Build report (rt_bvh_info). */
+typedef struct {
+  int64_t n_tri;          /* triangles in the scene */
+  int64_t n_bvh2_internal;/* binary internal nodes (Sec. II.C tree) */
+  int64_t n_leaves;       /* leaves */
+  int64_t n_wide;         /* traversal nodes */
+  int32_t depth2;         /* depth of the binary tree (root = 1) */
+  int32_t depth_wide;     /* depth of the traversal tree (root = 1) */
+  int32_t max_leaf_size;  /* largest leaf */
+  int32_t status;         /* device status word, 0 = ok */
+  double build_ms;        /* device time of the last build (events) */
+} rt_bvh_info_t;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int rt_version(void);
+
+/* Number of CUDA kernels this library has launched since it was loaded
+ * (all scenes, all threads).  Reading it twice around a region gives the
+ * launches made inside it.  Never fails. */
+uint64_t rt_launch_count(void);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* rt_last_error(void);
+
+/* Copy a triangle soup into a new scene (Sec. II.A: buildings as triangular
+ * facets).  tris: n_tri * 9 floats, vertex k of triangle i at
+ * tris[9i + 3k .. 9i + 3k + 2]; a host pointer (is_device_ptr = 0; pageable
+ * or pinned) or a device pointer (1).  The caller may free `tris` once the
+ * stream has reached the call.  n_tri may be 0 (every ray then misses).
+ * Errors: RT_EINVAL (out == NULL, n_tri < 0 or > 2^27), RT_ENOMEM,
+ * RT_ECUDA. */
+int rt_scene_upload(const float* tris, int64_t n_tri, int is_device_ptr, void* stream,
+                    rt_scene* out);
+
+/* Free a scene and every device buffer it owns (synchronous). */
+int rt_scene_destroy(rt_scene scene);
+
+/* Replace the vertex data of an existing scene with n_tri triangles (same
+ * layout as rt_scene_upload).  The BVH must be rebuilt before tracing.
+ * Errors: RT_EINVAL, RT_ENOMEM, RT_ECUDA. */
+int rt_scene_update(rt_scene scene, const float* tris, int64_t n_tri, int is_device_ptr,
+                    void* stream);
+
+/* Build (or rebuild) the scene's BVH on the device (Sec. II.B-C, Fig. 2):
+ * per-triangle AABBs, scene bounds, a Morton-order presort of the
+ * centroids, a top-down split of every node by the minimum of the Eq. 2
+ * cost over `bins`-1 candidate planes on each axis, leaves of at most
+ * max_leaf triangles, then a collapse of the binary tree into `width`-ary
+ * traversal nodes.  Asynchronous: no host synchronisation, so it can be
+ * captured in a CUDA graph once the scene's buffers exist (the first build
+ * of a scene allocates them).  Errors: RT_EINVAL (bad params), RT_ENOMEM,
+ * RT_ECUDA. */
+int rt_bvh_build(rt_scene scene, const rt_build_params* params, void* stream);
+
+/* Synchronous: wait for the stream, then report the built tree.  Errors:
+ * RT_EINVAL, RT_ENOTBUILT, RT_ECUDA; RT_EINTERNAL when the device status
+ * word reports a failed check (info->status says which). */
+int rt_bvh_info(rt_scene scene, void* stream, rt_bvh_info_t* info);
+
+/* Synchronous: copy the binary tree (Sec. II.C, Fig. 1) to host arrays in
+ * the neutral form used by the tests: node i has children child[2i],
+ * child[2i+1] (>= 0: node index; < 0: leaf -1-l), leaf l covers
+ * prims[leaf_first[l] .. + leaf_count[l]), prims holds triangle ids, node
+ * 0 is the root (or leaf 0 when there is no internal node).  Array sizes
+ * come from rt_bvh_info: child 2*n_bvh2_internal, leaf arrays n_leaves,
+ * prims n_tri.  boxes (nullable) receives 12 floats per internal node: the
+ * AABBs (lo xyz, hi xyz) of its two children. */
+int rt_bvh_export(rt_scene scene, void* stream, int32_t* child, int64_t* leaf_first,
+                  int64_t* leaf_count, int32_t* prims, float* boxes);
+
+/* Closest hit for n rays (Sec. III.B, Fig. 4): descend through the boxes
+ * the ray meets within [tmin, min(tmax, best t)], test the leaf triangles
+ * and keep the nearest hit with tmin < t < tmax (ties: lowest triangle id).
+ * The float32 pass flags rays whose answer its error bounds cannot settle
+ * (a triangle edge or a second hit within the bound, a hit near tmin or
+ * tmax); those are traced again in float64 with the same hit rule as the
+ * reference definition (Moller-Trumbore, inclusive edges).
+ * rays_dev: n rt_ray (16-byte aligned); hits_dev: n rt_hit.  n may be 0.
+ * Errors: RT_EINVAL, RT_ENOTBUILT, RT_ENOMEM (first use of a larger n
+ * grows the scene's re-test queue), RT_ECUDA. */
+int rt_trace_closest(rt_scene scene, const rt_ray* rays_dev, int64_t n, rt_hit* hits_dev,
+                     const rt_trace_params* params, void* stream);
+
+/* Any hit for n rays: occluded_dev[i] = 1 when some triangle is hit with
+ * tmin < t < tmax, else 0 (visibility between two points: o = p0,
+ * d = p1 - p0, tmin = 0, tmax = 1).  Same flagging and float64 re-test as
+ * rt_trace_closest.  Errors as rt_trace_closest. */
+int rt_trace_any(rt_scene scene, const rt_ray* rays_dev, int64_t n, uint8_t* occluded_dev,
+                 const rt_trace_params* params, void* stream);
+
+/* Closest hit with HOST buffers: rays_host and hits_host are host memory
+ * (pinned for overlap; pageable works but serialises).  The library copies
+ * rays in chunks to device staging buffers, traces them and copies hits
+ * back, overlapping the copies of one chunk with the tracing of another.
+ * Synchronous with respect to the host buffers: on return, hits_host is
+ * filled.  Errors as rt_trace_closest. */
+int rt_trace_closest_host(rt_scene scene, const rt_ray* rays_host, int64_t n, rt_hit* hits_host,
+                          const rt_trace_params* params, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RTBVH_H */

@@ -1,0 +1,158 @@
+// Internal definitions shared by the CUDA translation units of librtbvh.
+//
+// Device data layout (all 16-byte aligned, in HBM):
+//   tri_in    float4[3T]  input-order triangles: (v0.xyz, id) (v1.xyz, 0) (v2.xyz, 0)
+//   prim_lo   float4[T]   per-triangle AABB min (w unused)      -- Eq. 3 boxes
+//   prim_hi   float4[T]   per-triangle AABB max
+//   keys/idx  u32/i32[T]  Morton keys and the triangle permutation (ping-pong pairs)
+//   node2     Node2[T]    binary tree of Sec. II.C / Fig. 1; internal node id =
+//                         (split position - 1), a unique slot for every split
+//   wide      WNode[T]    4-wide traversal nodes (one 128-byte line each)
+//   tri_leaf  float4[3T]  triangles in leaf order, same packing as tri_in
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "rtbvh.h"
+
+namespace rt {
+
+constexpr int kMaxLeaf = 15;   // leaf refs pack the count in 4 bits
+constexpr int kMaxBins = 32;
+constexpr int kWidth = 4;
+constexpr int kTierASmall = 2048;   // tasks above this size are split by a whole CTA
+constexpr int kSpinLimit = 1 << 24; // bounded device waits (iterations of ~200 ns)
+
+// Status codes written to the device status word (BuildCtl::status).
+enum DevStatus : int {
+  kStOk = 0,
+  kStQueueTimeout = 1,   // a work-queue wait hit kSpinLimit
+  kStQueueOverflow = 2,  // more tasks than queue slots (cannot happen for a valid tree)
+  kStBadSplit = 3,       // a partition disagreed with its bin counts
+  kStWideOverflow = 4,   // more traversal nodes than allocated
+};
+
+// Leaf reference: -1 - (first * 16 + count); internal: >= 0.
+__host__ __device__ inline int32_t leaf_ref(int32_t first, int32_t count) {
+  return -1 - (first * 16 + count);
+}
+__host__ __device__ inline int32_t leaf_first(int32_t ref) { return (-1 - ref) >> 4; }
+__host__ __device__ inline int32_t leaf_count(int32_t ref) { return (-1 - ref) & 15; }
+
+// Binary node: the AABBs of its two children; a_lo.w / b_lo.w hold the
+// child refs (int bits), a_hi.w / b_hi.w hold the children's triangle counts.
+struct __align__(16) Node2 {
+  float4 a_lo, a_hi, b_lo, b_hi;
+};
+
+// 4-wide traversal node, 128 bytes: child i's box in component i of the six
+// float4 planes; child[i] = wide node index (>= 0), leaf ref (< 0, != INT_MIN)
+// or INT_MIN for an empty slot (whose box is lo = +inf, hi = -inf).
+// meta.x = parent wide node (-1 at the root), meta.y = slot in the parent.
+struct __align__(16) WNode {
+  float4 lox, hix, loy, hiy, loz, hiz;
+  int4 child;
+  int4 meta;
+};
+static_assert(sizeof(WNode) == 128, "wide node must be one 128-byte line");
+
+struct __align__(16) Task {
+  int32_t begin, count, parent, side;  // parent: node2 id (-1 root); side 0/1
+  float clo[3];                        // centroid bounds of the task's triangles
+  int32_t depth;
+  float chi[3];
+  int32_t pad;
+};
+
+// Device control block of one scene (zeroed at the start of every build).
+struct BuildCtl {
+  int status, status_where, pad0, pad1;
+  // tier-A queue (CTA per task)
+  int qa_head, qa_tail, qa_pending, qa_cap;
+  // tier-B list (warp per task)
+  int qb_count, qb_cap, pad2, pad3;
+  // collapse queue
+  int qc_head, qc_tail, qc_pending, qc_cap;
+  // tree facts
+  int n_internal, n_leaves, depth2, max_leaf_size;
+  int n_wide, depth_wide, root_ref, pad4;
+  // scene bounds as ordered ints (see ford()): triangle AABB and centroid bounds
+  int scene_lo[3], scene_hi[3];
+  int cen_lo[3], cen_hi[3];
+};
+
+// Per-call trace scratch: counter + queue of flagged ray indices.
+struct TraceScratch {
+  int* counter = nullptr;   // [0] flagged count, [1] status
+  int* queue = nullptr;
+  int64_t cap = 0;
+};
+
+// Order-preserving float <-> int map for atomicMin/atomicMax on floats.
+__host__ __device__ inline int ford(float f) {
+#ifdef __CUDA_ARCH__
+  int i = __float_as_int(f);
+#else
+  int i;
+  memcpy(&i, &f, 4);
+#endif
+  return i >= 0 ? i : i ^ 0x7FFFFFFF;
+}
+__host__ __device__ inline float iford(int i) {
+  int j = i >= 0 ? i : i ^ 0x7FFFFFFF;
+#ifdef __CUDA_ARCH__
+  return __int_as_float(j);
+#else
+  float f;
+  memcpy(&f, &j, 4);
+  return f;
+#endif
+}
+
+// Host-side count of kernel launches (rt_launch_count); every launch site
+// adds the number of kernels it enqueues.
+void count_launches(int k);
+
+// Launch helpers implemented in build.cu / trace.cu -----------------------
+struct SceneDev;  // forward
+
+cudaError_t launch_build(struct ::rt_scene_s* s, const rt_build_params& p, cudaStream_t st);
+cudaError_t launch_trace(struct ::rt_scene_s* s, const rt_ray* rays, int64_t n, rt_hit* hits,
+                         uint8_t* occl, const rt_trace_params* tp, TraceScratch& scr,
+                         cudaStream_t st);
+
+}  // namespace rt
+
+// Host-side scene object.
+struct rt_scene_s {
+  int device = 0;
+  int64_t n_tri = 0;
+  int64_t cap_tri = 0;          // capacity of the per-triangle buffers
+  float4* tri_in = nullptr;
+  float4* prim_lo = nullptr;
+  float4* prim_hi = nullptr;
+  uint32_t* keys[2] = {nullptr, nullptr};
+  int32_t* idx[2] = {nullptr, nullptr};
+  uint32_t* sort_hist = nullptr;  // radix-sort histograms
+  int64_t sort_hist_cap = 0;
+  rt::Node2* node2 = nullptr;
+  rt::WNode* wide = nullptr;
+  float4* tri_leaf = nullptr;
+  rt::Task* qa = nullptr;       // tier-A queue
+  int* qa_ready = nullptr;
+  rt::Task* qb = nullptr;       // tier-B list
+  int4* qc = nullptr;           // collapse queue (bvh2 ref, wide id, parent, slot|depth)
+  int* qc_ready = nullptr;
+  rt::BuildCtl* ctl = nullptr;
+  rt::TraceScratch scratch;     // default trace scratch
+  rt::TraceScratch host_scr[2]; // scratch of the host-buffer pipeline
+  rt_ray* stage_rays[2] = {nullptr, nullptr};
+  rt_hit* stage_hits[2] = {nullptr, nullptr};
+  int64_t stage_cap = 0;
+  cudaStream_t host_streams[2] = {nullptr, nullptr};
+  cudaEvent_t ev_build0 = nullptr, ev_build1 = nullptr;
+  bool built = false;
+  rt_build_params params{};
+};

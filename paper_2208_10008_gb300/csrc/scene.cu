@@ -1,0 +1,392 @@
+// C-ABI entry points of librtbvh (declared in include/rtbvh.h): scene
+// lifetime, triangle upload, build / trace dispatch and the host-buffer
+// pipeline.  Device work lives in build.cu and trace.cu.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <climits>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "rt_internal.cuh"
+
+namespace rt {
+static std::atomic<uint64_t> g_launches{0};
+void count_launches(int k) { g_launches.fetch_add((uint64_t)k, std::memory_order_relaxed); }
+}  // namespace rt
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  int code = e == cudaErrorMemoryAllocation ? RT_ENOMEM : RT_ECUDA;
+  return fail(code, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define RT_CUDA(call, what)                  \
+  do {                                       \
+    cudaError_t e_ = (call);                 \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+template <class T>
+cudaError_t dev_alloc(T** p, size_t count) {
+  if (*p) {
+    cudaFree(*p);
+    *p = nullptr;
+  }
+  if (count == 0) count = 1;
+  return cudaMalloc((void**)p, count * sizeof(T));
+}
+
+// float[9] per triangle -> 3 float4 (v0.xyz, id) (v1.xyz, 0) (v2.xyz, 0)
+__global__ void k_pack(const float* __restrict__ raw, int n, float4* __restrict__ out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float* p = raw + 9 * (size_t)i;
+    out[3 * (size_t)i] = make_float4(p[0], p[1], p[2], __int_as_float(i));
+    out[3 * (size_t)i + 1] = make_float4(p[3], p[4], p[5], 0.f);
+    out[3 * (size_t)i + 2] = make_float4(p[6], p[7], p[8], 0.f);
+  }
+}
+
+void free_scene_buffers(rt_scene_s* s) {
+  void* ptrs[] = {s->tri_in, s->prim_lo, s->prim_hi, s->keys[0], s->keys[1], s->idx[0], s->idx[1],
+                  s->sort_hist, s->node2, s->wide, s->tri_leaf, s->qa, s->qa_ready, s->qb, s->qc,
+                  s->qc_ready, s->ctl, s->scratch.counter, s->scratch.queue,
+                  s->host_scr[0].counter, s->host_scr[0].queue, s->host_scr[1].counter,
+                  s->host_scr[1].queue, s->stage_rays[0], s->stage_rays[1], s->stage_hits[0],
+                  s->stage_hits[1]};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+
+// Size every per-triangle buffer for n triangles (grow only).
+int ensure_capacity(rt_scene_s* s, int64_t n) {
+  if (n <= s->cap_tri && s->ctl) return RT_OK;
+  const int64_t m = n < 1 ? 1 : n;
+  RT_CUDA(dev_alloc(&s->tri_in, 3 * m), "alloc triangles");
+  RT_CUDA(dev_alloc(&s->prim_lo, m), "alloc bounds");
+  RT_CUDA(dev_alloc(&s->prim_hi, m), "alloc bounds");
+  for (int k = 0; k < 2; ++k) {
+    RT_CUDA(dev_alloc(&s->keys[k], m), "alloc keys");
+    RT_CUDA(dev_alloc(&s->idx[k], m), "alloc index");
+  }
+  const int64_t nb = (m + 256 * 32 - 1) / (256 * 32);
+  RT_CUDA(dev_alloc(&s->sort_hist, 256 * nb), "alloc sort histogram");
+  RT_CUDA(dev_alloc(&s->node2, m), "alloc binary nodes");
+  RT_CUDA(dev_alloc(&s->wide, m + 1), "alloc wide nodes");
+  RT_CUDA(dev_alloc(&s->tri_leaf, 3 * m), "alloc leaf triangles");
+  const int64_t qa_cap = m + 4;
+  RT_CUDA(dev_alloc(&s->qa, qa_cap), "alloc task queue");
+  RT_CUDA(dev_alloc(&s->qa_ready, qa_cap), "alloc task queue");
+  RT_CUDA(dev_alloc(&s->qb, m + 1), "alloc task list");
+  RT_CUDA(dev_alloc(&s->qc, m + 1), "alloc collapse queue");
+  RT_CUDA(dev_alloc(&s->qc_ready, m + 1), "alloc collapse queue");
+  if (!s->ctl) RT_CUDA(cudaMalloc((void**)&s->ctl, sizeof(rt::BuildCtl)), "alloc control block");
+  s->cap_tri = m;
+  return RT_OK;
+}
+
+int ensure_scratch(rt::TraceScratch& scr, int64_t n) {
+  if (scr.counter && scr.cap >= n) return RT_OK;
+  if (!scr.counter) RT_CUDA(cudaMalloc((void**)&scr.counter, 4 * sizeof(int)), "alloc trace counter");
+  if (scr.queue) cudaFree(scr.queue);
+  scr.queue = nullptr;
+  int64_t cap = n < 1024 ? 1024 : n;
+  RT_CUDA(cudaMalloc((void**)&scr.queue, cap * sizeof(int)), "alloc re-test queue");
+  scr.cap = cap;
+  return RT_OK;
+}
+
+int load_triangles(rt_scene_s* s, const float* tris, int64_t n, int is_dev, cudaStream_t st) {
+  if (n > 0) {
+    int r = ensure_capacity(s, n);
+    if (r) return r;
+    const float* raw = tris;
+    if (!is_dev) {
+      // stage the raw floats in the leaf buffer (48 B per triangle >= 36 B)
+      RT_CUDA(cudaMemcpyAsync(s->tri_leaf, tris, (size_t)n * 9 * sizeof(float), cudaMemcpyHostToDevice, st),
+              "copy triangles");
+      raw = reinterpret_cast<const float*>(s->tri_leaf);
+    }
+    int g = (int)((n + 255) / 256);
+    if (g > 4096) g = 4096;
+    k_pack<<<g, 256, 0, st>>>(raw, (int)n, s->tri_in);
+    rt::count_launches(1);
+    RT_CUDA(cudaGetLastError(), "pack triangles");
+  } else {
+    int r = ensure_capacity(s, 1);
+    if (r) return r;
+  }
+  s->n_tri = n;
+  s->built = false;
+  return RT_OK;
+}
+
+int check_params(const rt_build_params* p) {
+  if (!p) return fail(RT_EINVAL, "params is NULL");
+  if (!(p->alpha >= 0.f && p->alpha <= 1.f)) return fail(RT_EINVAL, "alpha must be in [0, 1]");
+  if (!(p->t_i > 0.f)) return fail(RT_EINVAL, "t_i must be > 0");
+  if (!(p->t_trav >= 0.f)) return fail(RT_EINVAL, "t_trav must be >= 0");
+  for (int a = 0; a < 3; ++a)
+    if (!(p->source[a] == p->source[a]) || p->source[a] > 3.0e38f || p->source[a] < -3.0e38f)
+      return fail(RT_EINVAL, "source must be finite");
+  if (p->max_leaf < 1 || p->max_leaf > rt::kMaxLeaf) return fail(RT_EINVAL, "max_leaf must be 1..15");
+  if (p->bins < 4 || p->bins > rt::kMaxBins) return fail(RT_EINVAL, "bins must be 4..32");
+  if (p->width != rt::kWidth) return fail(RT_EINVAL, "width must be 4");
+  if (p->dist_norm != 0 && p->dist_norm != 1) return fail(RT_EINVAL, "dist_norm must be 0 or 1");
+  return RT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rt_version(void) { return 100; }
+
+uint64_t rt_launch_count(void) { return rt::g_launches.load(std::memory_order_relaxed); }
+
+const char* rt_last_error(void) { return g_err; }
+
+int rt_scene_upload(const float* tris, int64_t n_tri, int is_device_ptr, void* stream, rt_scene* out) {
+  g_err[0] = 0;
+  if (!out) return fail(RT_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n_tri < 0 || n_tri > (int64_t(1) << 27)) return fail(RT_EINVAL, "n_tri out of range: %lld", (long long)n_tri);
+  if (n_tri > 0 && !tris) return fail(RT_EINVAL, "tris is NULL");
+  rt_scene_s* s = new (std::nothrow) rt_scene_s();
+  if (!s) return fail(RT_ENOMEM, "host allocation failed");
+  cudaGetDevice(&s->device);
+  int r = load_triangles(s, tris, n_tri, is_device_ptr, (cudaStream_t)stream);
+  if (r) {
+    free_scene_buffers(s);
+    delete s;
+    return r;
+  }
+  cudaError_t e = cudaEventCreate(&s->ev_build0);
+  if (e == cudaSuccess) e = cudaEventCreate(&s->ev_build1);
+  if (e != cudaSuccess) {
+    free_scene_buffers(s);
+    delete s;
+    return cuda_fail(e, "create events");
+  }
+  *out = s;
+  return RT_OK;
+}
+
+int rt_scene_update(rt_scene s, const float* tris, int64_t n_tri, int is_device_ptr, void* stream) {
+  g_err[0] = 0;
+  if (!s) return fail(RT_EINVAL, "scene is NULL");
+  if (n_tri < 0 || n_tri > (int64_t(1) << 27)) return fail(RT_EINVAL, "n_tri out of range");
+  if (n_tri > 0 && !tris) return fail(RT_EINVAL, "tris is NULL");
+  return load_triangles(s, tris, n_tri, is_device_ptr, (cudaStream_t)stream);
+}
+
+int rt_scene_destroy(rt_scene s) {
+  g_err[0] = 0;
+  if (!s) return fail(RT_EINVAL, "scene is NULL");
+  cudaDeviceSynchronize();
+  free_scene_buffers(s);
+  for (int k = 0; k < 2; ++k)
+    if (s->host_streams[k]) cudaStreamDestroy(s->host_streams[k]);
+  if (s->ev_build0) cudaEventDestroy(s->ev_build0);
+  if (s->ev_build1) cudaEventDestroy(s->ev_build1);
+  delete s;
+  return RT_OK;
+}
+
+int rt_bvh_build(rt_scene s, const rt_build_params* p, void* stream) {
+  g_err[0] = 0;
+  if (!s) return fail(RT_EINVAL, "scene is NULL");
+  int r = check_params(p);
+  if (r) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(st, &cs);
+  const bool capturing = cs != cudaStreamCaptureStatusNone;
+  if (!capturing) RT_CUDA(cudaEventRecord(s->ev_build0, st), "record event");
+  RT_CUDA(rt::launch_build(s, *p, st), "launch build");
+  if (!capturing) RT_CUDA(cudaEventRecord(s->ev_build1, st), "record event");
+  s->params = *p;
+  s->built = true;
+  return RT_OK;
+}
+
+int rt_bvh_info(rt_scene s, void* stream, rt_bvh_info_t* info) {
+  g_err[0] = 0;
+  if (!s || !info) return fail(RT_EINVAL, "NULL argument");
+  if (!s->built) return fail(RT_ENOTBUILT, "BVH not built");
+  RT_CUDA(cudaStreamSynchronize((cudaStream_t)stream), "synchronize");
+  rt::BuildCtl c;
+  RT_CUDA(cudaMemcpy(&c, s->ctl, sizeof(c), cudaMemcpyDeviceToHost), "read control block");
+  info->n_tri = s->n_tri;
+  info->n_bvh2_internal = c.n_internal;
+  info->n_leaves = c.n_leaves;
+  info->n_wide = c.n_wide;
+  info->depth2 = c.depth2;
+  info->depth_wide = c.depth_wide;
+  info->max_leaf_size = c.max_leaf_size;
+  info->status = c.status;
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, s->ev_build0, s->ev_build1) != cudaSuccess) {
+    cudaGetLastError();
+    ms = -1.f;
+  }
+  info->build_ms = ms;
+  if (c.status != 0) return fail(RT_EINTERNAL, "device status %d at %d", c.status, c.status_where);
+  return RT_OK;
+}
+
+int rt_bvh_export(rt_scene s, void* stream, int32_t* child, int64_t* leaf_first, int64_t* leaf_count,
+                  int32_t* prims, float* boxes) {
+  g_err[0] = 0;
+  if (!s || !child || !leaf_first || !leaf_count || !prims) return fail(RT_EINVAL, "NULL argument");
+  if (!s->built) return fail(RT_ENOTBUILT, "BVH not built");
+  RT_CUDA(cudaStreamSynchronize((cudaStream_t)stream), "synchronize");
+  rt::BuildCtl c;
+  RT_CUDA(cudaMemcpy(&c, s->ctl, sizeof(c), cudaMemcpyDeviceToHost), "read control block");
+  const int64_t n = s->n_tri;
+  std::vector<rt::Node2> nodes((size_t)(n > 0 ? n : 1));
+  std::vector<int32_t> idx((size_t)(n > 0 ? n : 1));
+  if (n > 0) {
+    RT_CUDA(cudaMemcpy(nodes.data(), s->node2, sizeof(rt::Node2) * n, cudaMemcpyDeviceToHost), "read nodes");
+    RT_CUDA(cudaMemcpy(idx.data(), s->idx[0], sizeof(int32_t) * n, cudaMemcpyDeviceToHost), "read index");
+  }
+  for (int64_t k = 0; k < n; ++k) prims[k] = idx[k];
+  // renumber: internal nodes in depth-first order, leaves in order of discovery
+  int64_t ni = 0, nl = 0;
+  auto add_leaf = [&](int32_t ref) {
+    leaf_first[nl] = rt::leaf_first(ref);
+    leaf_count[nl] = rt::leaf_count(ref);
+    return -1 - (int32_t)(nl++);
+  };
+  if (c.root_ref < 0) {
+    if (c.root_ref != INT_MIN) add_leaf(c.root_ref);
+    return RT_OK;
+  }
+  struct Item {
+    int32_t id;
+    int64_t slot;  // where to write our neutral id (-1: root)
+  };
+  std::vector<Item> st{{c.root_ref, -1}};
+  while (!st.empty()) {
+    Item it = st.back();
+    st.pop_back();
+    if (it.id < 0 || it.id >= n) return fail(RT_EINTERNAL, "bad node id %d", it.id);
+    int64_t me = ni++;
+    if (ni > c.n_internal) return fail(RT_EINTERNAL, "more internal nodes than counted");
+    if (it.slot >= 0) child[it.slot] = (int32_t)me;
+    const rt::Node2& nd = nodes[it.id];
+    int32_t refs[2];
+    memcpy(&refs[0], &nd.a_lo.w, 4);
+    memcpy(&refs[1], &nd.b_lo.w, 4);
+    if (boxes) {
+      float b[12] = {nd.a_lo.x, nd.a_lo.y, nd.a_lo.z, nd.a_hi.x, nd.a_hi.y, nd.a_hi.z,
+                     nd.b_lo.x, nd.b_lo.y, nd.b_lo.z, nd.b_hi.x, nd.b_hi.y, nd.b_hi.z};
+      memcpy(boxes + 12 * me, b, sizeof(b));
+    }
+    for (int k = 1; k >= 0; --k) {
+      if (refs[k] >= 0 && refs[k] != INT_MAX)
+        st.push_back({refs[k], 2 * me + k});
+      else if (refs[k] == INT_MAX)
+        return fail(RT_EINTERNAL, "child never written");
+      else
+        child[2 * me + k] = add_leaf(refs[k]);
+    }
+  }
+  return RT_OK;
+}
+
+static int trace_common(rt_scene s, const rt_ray* rays, int64_t n, rt_hit* hits, uint8_t* occl,
+                        const rt_trace_params* params, void* stream) {
+  if (!s) return fail(RT_EINVAL, "scene is NULL");
+  if (n < 0 || n > INT_MAX) return fail(RT_EINVAL, "n out of range");
+  if (n > 0 && (!rays || (!hits && !occl))) return fail(RT_EINVAL, "NULL buffer");
+  if (((uintptr_t)rays & 15) || ((uintptr_t)hits & 15)) return fail(RT_EINVAL, "rays/hits must be 16-byte aligned");
+  if (!s->built) return fail(RT_ENOTBUILT, "BVH not built");
+  int r = ensure_scratch(s->scratch, n);
+  if (r) return r;
+  RT_CUDA(rt::launch_trace(s, rays, n, hits, occl, params, s->scratch, (cudaStream_t)stream), "launch trace");
+  return RT_OK;
+}
+
+int rt_trace_closest(rt_scene s, const rt_ray* rays_dev, int64_t n, rt_hit* hits_dev,
+                     const rt_trace_params* params, void* stream) {
+  g_err[0] = 0;
+  if (n > 0 && !hits_dev) return fail(RT_EINVAL, "hits is NULL");
+  return trace_common(s, rays_dev, n, hits_dev, nullptr, params, stream);
+}
+
+int rt_trace_any(rt_scene s, const rt_ray* rays_dev, int64_t n, uint8_t* occluded_dev,
+                 const rt_trace_params* params, void* stream) {
+  g_err[0] = 0;
+  if (n > 0 && !occluded_dev) return fail(RT_EINVAL, "occluded is NULL");
+  return trace_common(s, rays_dev, n, nullptr, occluded_dev, params, stream);
+}
+
+int rt_trace_closest_host(rt_scene s, const rt_ray* rays_host, int64_t n, rt_hit* hits_host,
+                          const rt_trace_params* params, void* stream) {
+  g_err[0] = 0;
+  if (!s) return fail(RT_EINVAL, "scene is NULL");
+  if (n < 0) return fail(RT_EINVAL, "n out of range");
+  if (n > 0 && (!rays_host || !hits_host)) return fail(RT_EINVAL, "NULL buffer");
+  if (!s->built) return fail(RT_ENOTBUILT, "BVH not built");
+  if (params && (params->skip_tri_dev || params->stats_dev))
+    return fail(RT_EINVAL, "per-ray device arrays are not supported with host buffers");
+  if (n == 0) return RT_OK;
+  const int64_t chunk = n < (int64_t(1) << 18) ? n : (int64_t(1) << 18);
+  if (s->stage_cap < chunk) {
+    for (int k = 0; k < 2; ++k) {
+      RT_CUDA(dev_alloc(&s->stage_rays[k], chunk), "alloc staging");
+      RT_CUDA(dev_alloc(&s->stage_hits[k], chunk), "alloc staging");
+    }
+    s->stage_cap = chunk;
+  }
+  for (int k = 0; k < 2; ++k) {
+    if (!s->host_streams[k]) RT_CUDA(cudaStreamCreateWithFlags(&s->host_streams[k], cudaStreamNonBlocking), "create stream");
+    int r = ensure_scratch(s->host_scr[k], chunk);
+    if (r) return r;
+  }
+  // the pipeline starts after everything already queued on the caller's stream
+  cudaEvent_t ev;
+  RT_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "create event");
+  cudaEventRecord(ev, (cudaStream_t)stream);
+  for (int k = 0; k < 2; ++k) cudaStreamWaitEvent(s->host_streams[k], ev, 0);
+  cudaEventDestroy(ev);
+  rt_trace_params tp{};
+  if (params) tp.flags = params->flags;
+  int rc = RT_OK;
+  for (int64_t off = 0, c = 0; off < n; off += chunk, ++c) {
+    const int k = (int)(c & 1);
+    const int64_t cnt = (n - off) < chunk ? (n - off) : chunk;
+    cudaStream_t st = s->host_streams[k];
+    cudaError_t e = cudaMemcpyAsync(s->stage_rays[k], rays_host + off, cnt * sizeof(rt_ray),
+                                    cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = rt::launch_trace(s, s->stage_rays[k], cnt, s->stage_hits[k], nullptr, &tp, s->host_scr[k], st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(hits_host + off, s->stage_hits[k], cnt * sizeof(rt_hit), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e, "host pipeline");
+      break;
+    }
+  }
+  for (int k = 0; k < 2; ++k) {
+    cudaError_t e = cudaStreamSynchronize(s->host_streams[k]);
+    if (e != cudaSuccess && rc == RT_OK) rc = cuda_fail(e, "synchronize pipeline");
+  }
+  return rc;
+}
+
+}  // extern "C"

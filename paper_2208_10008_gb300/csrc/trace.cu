@@ -1,0 +1,587 @@
+// Ray traversal (Sec. III.B, Fig. 4 of arXiv 2208.10008): collision detection
+// of a ray with the BVH -- test the bounding boxes, descend into the ones the
+// ray meets, test the triangles of the leaves reached and keep the nearest hit.
+//
+// k_trace (float32, one ray per thread)
+//   * 4-wide nodes, one 128-byte line each, read with 16-byte read-only loads;
+//     children ordered near-first on a per-thread stack.
+//   * box test: slab test with the near/far plane picked by the sign of 1/d
+//     (NaN-safe for axis-parallel rays); the interval is widened by a relative
+//     1e-6 so rounding never drops a box the exact ray meets.
+//   * ray action range: boxes are culled beyond min(tmax, best t + window),
+//     so the ray's maximal range bounds the walk (abstract, Sec. II.B).
+//   * triangle test: the watertight test of Woop, Benthin and Wald (JCGT
+//     2013), two-sided, plus a forward error bound E on its three edge
+//     functions.  Signs settled beyond E give a certain hit or miss; anything
+//     else, a second hit within the error window of the best one, a hit near
+//     tmin / tmax, or a stack overflow marks the ray for k_retest64.
+// k_retest64 (float64, one flagged ray per thread)
+//   * a stackless walk of the same tree (parent links), float64 box tests and
+//     the reference hit rule: Moller-Trumbore with inclusive edges, |det| <=
+//     1e-14 |e1||e2||d| is parallel, tmin < t < tmax, lowest id on equal t,
+//     with the operation order fixed and no contraction, so its answer is the
+//     float64 definition's answer bit for bit.
+#include <cuda_runtime.h>
+
+#include <cfloat>
+#include <climits>
+
+#include "rt_internal.cuh"
+
+namespace rt {
+namespace {
+
+constexpr int kTraceBlock = 128;
+constexpr int kStack = 64;
+constexpr int kRetestBlock = 128;
+constexpr float kU = 5.9604645e-08f;   // unit roundoff of float32, 2^-24
+constexpr float kWiden = 1e-6f;        // relative widening of box intervals
+constexpr float kTieRel = 1e-5f;       // relative window of the best-hit checks
+
+struct RayPre {
+  float ox, oy, oz, tmin, tmax;
+  float ix, iy, iz;  // 1/d
+  float Sx, Sy, Sz;  // shear constants of the watertight test
+  int kx, ky, kz;
+  bool valid;
+};
+
+__device__ __forceinline__ float sel3(float x, float y, float z, int k) {
+  return k == 0 ? x : (k == 1 ? y : z);
+}
+
+__device__ __forceinline__ RayPre setup_ray(float4 a, float4 b) {
+  RayPre r;
+  r.ox = a.x;
+  r.oy = a.y;
+  r.oz = a.z;
+  r.tmin = a.w;
+  r.tmax = b.w;
+  float dx = b.x, dy = b.y, dz = b.z;
+  bool fin = isfinite(a.x) && isfinite(a.y) && isfinite(a.z) && isfinite(dx) && isfinite(dy) &&
+             isfinite(dz) && !isnan(a.w) && !isnan(b.w);
+  r.valid = fin && (b.w > a.w) && (dx != 0.f || dy != 0.f || dz != 0.f);
+  r.ix = __frcp_rn(dx);
+  r.iy = __frcp_rn(dy);
+  r.iz = __frcp_rn(dz);
+  float ax = fabsf(dx), ay = fabsf(dy), az = fabsf(dz);
+  int kz = (ax >= ay && ax >= az) ? 0 : (ay >= az ? 1 : 2);
+  int kx = kz == 2 ? 0 : kz + 1;
+  int ky = kx == 2 ? 0 : kx + 1;
+  float dkz = sel3(dx, dy, dz, kz);
+  if (dkz < 0.f) {
+    int t = kx;
+    kx = ky;
+    ky = t;
+  }
+  r.kx = kx;
+  r.ky = ky;
+  r.kz = kz;
+  r.Sx = __fdiv_rn(sel3(dx, dy, dz, kx), dkz);
+  r.Sy = __fdiv_rn(sel3(dx, dy, dz, ky), dkz);
+  r.Sz = __frcp_rn(dkz);
+  return r;
+}
+
+// Watertight test with a forward error bound.  cls: 0 certain miss,
+// 1 certain hit (t, errT, u, v valid), 2 uncertain (tlo..thi brackets any t).
+struct TriRes {
+  int cls;
+  float t, err, u, v, tlo, thi;
+};
+
+__device__ __forceinline__ TriRes tri_test(const RayPre& r, float4 a, float4 b, float4 c) {
+  TriRes res;
+  float Ax0 = __fsub_rn(a.x, r.ox), Ay0 = __fsub_rn(a.y, r.oy), Az0 = __fsub_rn(a.z, r.oz);
+  float Bx0 = __fsub_rn(b.x, r.ox), By0 = __fsub_rn(b.y, r.oy), Bz0 = __fsub_rn(b.z, r.oz);
+  float Cx0 = __fsub_rn(c.x, r.ox), Cy0 = __fsub_rn(c.y, r.oy), Cz0 = __fsub_rn(c.z, r.oz);
+  float Akz = sel3(Ax0, Ay0, Az0, r.kz), Bkz = sel3(Bx0, By0, Bz0, r.kz), Ckz = sel3(Cx0, Cy0, Cz0, r.kz);
+  float Ax = __fmaf_rn(-r.Sx, Akz, sel3(Ax0, Ay0, Az0, r.kx));
+  float Ay = __fmaf_rn(-r.Sy, Akz, sel3(Ax0, Ay0, Az0, r.ky));
+  float Bx = __fmaf_rn(-r.Sx, Bkz, sel3(Bx0, By0, Bz0, r.kx));
+  float By = __fmaf_rn(-r.Sy, Bkz, sel3(Bx0, By0, Bz0, r.ky));
+  float Cx = __fmaf_rn(-r.Sx, Ckz, sel3(Cx0, Cy0, Cz0, r.kx));
+  float Cy = __fmaf_rn(-r.Sy, Ckz, sel3(Cx0, Cy0, Cz0, r.ky));
+  float U = __fmaf_rn(Cx, By, -__fmul_rn(Cy, Bx));
+  float V = __fmaf_rn(Ax, Cy, -__fmul_rn(Ay, Cx));
+  float W = __fmaf_rn(Bx, Ay, -__fmul_rn(By, Ax));
+  // Forward error bound of U, V, W against exact arithmetic on the same
+  // float32 inputs: |dU| <= u P (12 R + 7 P) with R the largest translated
+  // coordinate and P the largest projected one (13 R + 8 P keeps a margin).
+  float R = fmaxf(fmaxf(fmaxf(fabsf(Ax0), fabsf(Ay0)), fmaxf(fabsf(Az0), fabsf(Bx0))),
+                  fmaxf(fmaxf(fabsf(By0), fabsf(Bz0)), fmaxf(fmaxf(fabsf(Cx0), fabsf(Cy0)), fabsf(Cz0))));
+  float P = fmaxf(fmaxf(fmaxf(fabsf(Ax), fabsf(Ay)), fmaxf(fabsf(Bx), fabsf(By))),
+                  fmaxf(fabsf(Cx), fabsf(Cy)));
+  float E = kU * P * (13.f * R + 8.f * P);
+  float mn = fminf(U, fminf(V, W)), mx = fmaxf(U, fmaxf(V, W));
+  float Zs = fabsf(r.Sz);
+  float Az = __fmul_rn(r.Sz, Akz), Bz = __fmul_rn(r.Sz, Bkz), Cz = __fmul_rn(r.Sz, Ckz);
+  if (mn < -E && mx > E) {
+    res.cls = 0;
+    return res;
+  }
+  if (mn > E || mx < -E) {
+    float det = __fadd_rn(__fadd_rn(U, V), W);
+    float T = __fmaf_rn(U, Az, __fmaf_rn(V, Bz, __fmul_rn(W, Cz)));
+    float t = __fdiv_rn(T, det);
+    float zs = fmaxf(fmaxf(fabsf(Az - t), fabsf(Bz - t)), fabsf(Cz - t));
+    res.cls = 1;
+    res.t = t;
+    res.err = 3.01f * E * zs / fabsf(det) + 8.f * kU * Zs * R;
+    float id = __frcp_rn(det);
+    res.u = V * id;
+    res.v = W * id;
+    return res;
+  }
+  // uncertain: any hit lies between the smallest and largest vertex depth
+  float slack = 4.f * kU * Zs * R;
+  res.cls = 2;
+  res.tlo = fminf(Az, fminf(Bz, Cz)) - slack;
+  res.thi = fmaxf(Az, fmaxf(Bz, Cz)) + slack;
+  return res;
+}
+
+// ---------------------------------------------------------------- float-float
+// Double-float arithmetic from error-free transformations: TwoSum (Knuth),
+// TwoProduct with a fused multiply-add, and the usual renormalisation
+// (Dekker 1971).  Used once per ray to recompute the distance of the chosen
+// hit when its float32 error bound is not already inside the tolerance.
+struct ff {
+  float hi, lo;
+};
+__device__ __forceinline__ ff two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ ff quick_two_sum(float a, float b) {  // |a| >= |b|
+  float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  ff s = two_sum(a.hi, b.hi), t = two_sum(a.lo, b.lo);
+  float e = __fadd_rn(s.lo, t.hi);
+  s = quick_two_sum(s.hi, e);
+  e = __fadd_rn(s.lo, t.lo);
+  return quick_two_sum(s.hi, e);
+}
+__device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return quick_two_sum(p, e);
+}
+__device__ __forceinline__ ff ff_mulf(ff a, float b) {
+  float p = __fmul_rn(a.hi, b);
+  float e = __fmaf_rn(a.hi, b, -p);
+  e = __fmaf_rn(a.lo, b, e);
+  return quick_two_sum(p, e);
+}
+
+// Distance along the ray to the plane of (v0, v1, v2):
+// t = n.(v0 - o) / n.d with n = (v1 - v0) x (v2 - v0), all in float-float
+// (the differences are exact), rounded once to float at the end.
+__device__ float refine_t(const RayPre& r, float dx, float dy, float dz, float4 a, float4 b, float4 c) {
+  ff Ax = two_sum(a.x, -r.ox), Ay = two_sum(a.y, -r.oy), Az = two_sum(a.z, -r.oz);
+  ff e1x = two_sum(b.x, -a.x), e1y = two_sum(b.y, -a.y), e1z = two_sum(b.z, -a.z);
+  ff e2x = two_sum(c.x, -a.x), e2y = two_sum(c.y, -a.y), e2z = two_sum(c.z, -a.z);
+  ff nx = ff_add(ff_mul(e1y, e2z), ff_neg(ff_mul(e1z, e2y)));
+  ff ny = ff_add(ff_mul(e1z, e2x), ff_neg(ff_mul(e1x, e2z)));
+  ff nz = ff_add(ff_mul(e1x, e2y), ff_neg(ff_mul(e1y, e2x)));
+  ff num = ff_add(ff_add(ff_mul(nx, Ax), ff_mul(ny, Ay)), ff_mul(nz, Az));
+  ff den = ff_add(ff_add(ff_mulf(nx, dx), ff_mulf(ny, dy)), ff_mulf(nz, dz));
+  float q = __fdiv_rn(num.hi, den.hi);
+  ff rem = ff_add(num, ff_neg(ff_mulf(den, q)));
+  return __fadd_rn(q, __fdiv_rn(rem.hi, den.hi));
+}
+
+// Slab test of the 4 children of a node; returns a bit mask of children
+// whose widened interval meets [tmin, bound], near distances in tn[].
+__device__ __forceinline__ unsigned slab4(const WNode* __restrict__ node, const RayPre& r, float bound,
+                                          float tn[4], int4* child) {
+  const float4* p = reinterpret_cast<const float4*>(node);
+  float4 lox = __ldg(p + 0), hix = __ldg(p + 1), loy = __ldg(p + 2), hiy = __ldg(p + 3);
+  float4 loz = __ldg(p + 4), hiz = __ldg(p + 5);
+  int4 ch = __ldg(reinterpret_cast<const int4*>(p + 6));
+  *child = ch;
+  float4 nx = r.ix >= 0.f ? lox : hix, fx = r.ix >= 0.f ? hix : lox;
+  float4 ny = r.iy >= 0.f ? loy : hiy, fy = r.iy >= 0.f ? hiy : loy;
+  float4 nz = r.iz >= 0.f ? loz : hiz, fz = r.iz >= 0.f ? hiz : loz;
+  float nxa[4] = {nx.x, nx.y, nx.z, nx.w}, fxa[4] = {fx.x, fx.y, fx.z, fx.w};
+  float nya[4] = {ny.x, ny.y, ny.z, ny.w}, fya[4] = {fy.x, fy.y, fy.z, fy.w};
+  float nza[4] = {nz.x, nz.y, nz.z, nz.w}, fza[4] = {fz.x, fz.y, fz.z, fz.w};
+  unsigned mask = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    float t0 = fmaxf(fmaxf(__fmul_rn(__fsub_rn(nxa[i], r.ox), r.ix), __fmul_rn(__fsub_rn(nya[i], r.oy), r.iy)),
+                     __fmul_rn(__fsub_rn(nza[i], r.oz), r.iz));
+    float t1 = fminf(fminf(__fmul_rn(__fsub_rn(fxa[i], r.ox), r.ix), __fmul_rn(__fsub_rn(fya[i], r.oy), r.iy)),
+                     __fmul_rn(__fsub_rn(fza[i], r.oz), r.iz));
+    t0 = t0 - fabsf(t0) * kWiden;
+    t1 = t1 + fabsf(t1) * kWiden;
+    tn[i] = t0;
+    if (t0 <= t1 && t0 <= bound && t1 >= r.tmin) mask |= 1u << i;
+  }
+  return mask;
+}
+
+__device__ __forceinline__ void cswap(float& ta, int& ra, float& tb, int& rb) {
+  if (tb < ta) {
+    float t = ta;
+    ta = tb;
+    tb = t;
+    int x = ra;
+    ra = rb;
+    rb = x;
+  }
+}
+
+__device__ __forceinline__ void enqueue_flag(int* counter, int* queue, int qcap, int i) {
+  unsigned m = __activemask();
+  int lane = threadIdx.x & 31;
+  int leader = __ffs(m) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(counter, __popc(m));
+  base = __shfl_sync(m, base, leader);
+  int s = base + __popc(m & ((1u << lane) - 1u));
+  if (s < qcap) queue[s] = i;
+}
+
+struct TraceArgs {
+  const WNode* wide;
+  const float4* tris;
+  const rt_ray* rays;
+  int n;
+  rt_hit* hits;
+  uint8_t* occl;
+  const int32_t* skip;
+  uint32_t* stats;
+  int* counter;
+  int* queue;
+  int qcap;
+};
+
+template <bool kAny, bool kStats>
+__global__ void __launch_bounds__(kTraceBlock) k_trace(TraceArgs A) {
+  const int i = blockIdx.x * kTraceBlock + threadIdx.x;
+  if (i >= A.n) return;
+  const float4* r4 = reinterpret_cast<const float4*>(A.rays) + 2 * (size_t)i;
+  const RayPre r = setup_ray(__ldg(r4), __ldg(r4 + 1));
+  const int skip = A.skip ? __ldg(A.skip + i) : -1;
+  float t1 = INFINITY, t2 = INFINITY, e1 = 0.f, e2 = 0.f, bu = 0.f, bv = 0.f;
+  int id1 = -1, pos1 = -1;
+  bool flag = false, done = false;
+  uint32_t n_nodes = 0, n_tris = 0;
+  float bound = r.tmax;
+  int st_ref[kStack];
+  float st_t[kStack];
+  int sp = 0;
+  if (r.valid) {
+    st_ref[0] = 0;
+    st_t[0] = -INFINITY;
+    sp = 1;
+  }
+  while (sp > 0 && !done) {
+    --sp;
+    const int ref = st_ref[sp];
+    if (st_t[sp] > bound) continue;
+    if (ref >= 0) {
+      if (kStats) ++n_nodes;
+      float tn[4];
+      int4 ch;
+      unsigned m = slab4(A.wide + ref, r, bound, tn, &ch);
+      float ta = (m & 1u) ? tn[0] : INFINITY, tb = (m & 2u) ? tn[1] : INFINITY;
+      float tc = (m & 4u) ? tn[2] : INFINITY, td = (m & 8u) ? tn[3] : INFINITY;
+      int ra = ch.x, rb = ch.y, rc = ch.z, rd = ch.w;
+      // sort 4 (t, ref) pairs ascending
+      cswap(ta, ra, tb, rb);
+      cswap(tc, rc, td, rd);
+      cswap(ta, ra, tc, rc);
+      cswap(tb, rb, td, rd);
+      cswap(tb, rb, tc, rc);
+      int cnt = __popc(m);
+      if (sp + cnt > kStack) {  // cannot hold the children: leave it to the float64 pass
+        flag = true;
+        break;
+      }
+      // push farthest first so the nearest is popped next
+      if (cnt > 3) { st_ref[sp] = rd; st_t[sp] = td; ++sp; }
+      if (cnt > 2) { st_ref[sp] = rc; st_t[sp] = tc; ++sp; }
+      if (cnt > 1) { st_ref[sp] = rb; st_t[sp] = tb; ++sp; }
+      if (cnt > 0) { st_ref[sp] = ra; st_t[sp] = ta; ++sp; }
+      continue;
+    }
+    // leaf
+    const int first = leaf_first(ref), count = leaf_count(ref);
+    for (int k = 0; k < count; ++k) {
+      const float4* tp = A.tris + 3 * (size_t)(first + k);
+      float4 va = __ldg(tp), vb = __ldg(tp + 1), vc = __ldg(tp + 2);
+      const int id = __float_as_int(va.w);
+      if (id == skip) continue;
+      if (kStats) ++n_tris;
+      TriRes h = tri_test(r, va, vb, vc);
+      if (h.cls == 0) continue;
+      if (h.cls == 2) {
+        if (h.thi >= r.tmin && h.tlo <= bound) flag = true;
+        continue;
+      }
+      // certain hit: near an end of the interval the float64 rule decides
+      if (fabsf(h.t - r.tmax) <= h.err + kTieRel * fabsf(r.tmax) ||
+          fabsf(h.t - r.tmin) <= h.err + kTieRel * fabsf(h.t))
+        flag = true;
+      if (!(h.t > r.tmin && h.t < r.tmax)) continue;
+      if (kAny) {
+        if (!(fabsf(h.t - r.tmax) <= h.err + kTieRel * fabsf(r.tmax) ||
+              fabsf(h.t - r.tmin) <= h.err + kTieRel * fabsf(h.t))) {
+          done = true;
+          id1 = id;
+          break;
+        }
+        continue;
+      }
+      if (h.t < t1 || (h.t == t1 && id < id1)) {
+        t2 = t1;
+        e2 = e1;
+        t1 = h.t;
+        e1 = h.err;
+        id1 = id;
+        pos1 = first + k;
+        bu = h.u;
+        bv = h.v;
+      } else if (h.t < t2) {
+        t2 = h.t;
+        e2 = h.err;
+      }
+      bound = fminf(r.tmax, t1 + kTieRel * t1 + e1);
+    }
+  }
+  if (kAny) {
+    A.occl[i] = done ? 1 : 0;
+    if (done) flag = false;
+  } else {
+    if (t2 < INFINITY && t2 <= t1 + kTieRel * t1 + e1 + e2) flag = true;
+    if (id1 >= 0 && e1 > 0.25f * (kTieRel * t1 + 1e-6f)) {
+      // the float32 distance is not certified inside the tolerance: recompute it
+      const float4* tp = A.tris + 3 * (size_t)pos1;
+      const float4 rb4 = __ldg(r4 + 1);
+      t1 = refine_t(r, rb4.x, rb4.y, rb4.z, __ldg(tp), __ldg(tp + 1), __ldg(tp + 2));
+    }
+    float4 out = id1 >= 0 ? make_float4(t1, __int_as_float(id1), bu, bv)
+                          : make_float4(INFINITY, __int_as_float(-1), 0.f, 0.f);
+    reinterpret_cast<float4*>(A.hits)[i] = out;
+  }
+  if (kStats && A.stats) {
+    A.stats[2 * (size_t)i] = n_nodes;
+    A.stats[2 * (size_t)i + 1] = n_tris;
+  }
+  if (flag) enqueue_flag(A.counter, A.queue, A.qcap, i);
+}
+
+// ---------------------------------------------------------------- float64
+struct D3 {
+  double x, y, z;
+};
+__device__ __forceinline__ D3 dsub3(D3 a, D3 b) {
+  return {__dsub_rn(a.x, b.x), __dsub_rn(a.y, b.y), __dsub_rn(a.z, b.z)};
+}
+// (a.x*b.x + a.y*b.y) + a.z*b.z, rounded at every step
+__device__ __forceinline__ double ddot(D3 a, D3 b) {
+  double s = __dmul_rn(a.x, b.x);
+  s = __dadd_rn(s, __dmul_rn(a.y, b.y));
+  s = __dadd_rn(s, __dmul_rn(a.z, b.z));
+  return s;
+}
+__device__ __forceinline__ D3 dcross(D3 a, D3 b) {
+  return {__dsub_rn(__dmul_rn(a.y, b.z), __dmul_rn(a.z, b.y)),
+          __dsub_rn(__dmul_rn(a.z, b.x), __dmul_rn(a.x, b.z)),
+          __dsub_rn(__dmul_rn(a.x, b.y), __dmul_rn(a.y, b.x))};
+}
+
+// Moller-Trumbore, the reference hit rule (see file header).
+__device__ bool mt64(D3 o, D3 d, D3 v0, D3 v1, D3 v2, double* t, double* u, double* v) {
+  D3 e1 = dsub3(v1, v0), e2 = dsub3(v2, v0);
+  D3 p = dcross(d, e2);
+  double det = ddot(e1, p);
+  double n1 = __dsqrt_rn(ddot(e1, e1)), n2 = __dsqrt_rn(ddot(e2, e2)), nd = __dsqrt_rn(ddot(d, d));
+  double lim = __dmul_rn(1e-14, __dmul_rn(__dmul_rn(n1, n2), nd));
+  if (fabs(det) <= lim) return false;
+  double inv = __ddiv_rn(1.0, det);
+  D3 s = dsub3(o, v0);
+  double uu = __dmul_rn(ddot(s, p), inv);
+  if (uu < 0.0 || uu > 1.0) return false;
+  D3 q = dcross(s, e1);
+  double vv = __dmul_rn(ddot(d, q), inv);
+  if (vv < 0.0 || __dadd_rn(uu, vv) > 1.0) return false;
+  *t = __dmul_rn(ddot(e2, q), inv);
+  *u = uu;
+  *v = vv;
+  return true;
+}
+
+// float64 slab test of one child box, widened so that no box the exact ray
+// meets is missed (the result only decides which boxes are opened).
+__device__ bool slab64(D3 o, D3 d, const float lo[3], const float hi[3], double tlo, double thi) {
+  const double oo[3] = {o.x, o.y, o.z}, dd[3] = {d.x, d.y, d.z};
+  double t0 = -INFINITY, t1 = INFINITY;
+  for (int a = 0; a < 3; ++a) {
+    double pad = 1e-9 * (fabs((double)lo[a]) + fabs((double)hi[a]) + fabs(oo[a])) + 1e-12;
+    double l = (double)lo[a] - pad, h = (double)hi[a] + pad;
+    if (!(l <= h)) return false;  // empty slot
+    if (dd[a] == 0.0) {
+      if (oo[a] < l || oo[a] > h) return false;
+      continue;
+    }
+    double ta = (l - oo[a]) / dd[a], tb = (h - oo[a]) / dd[a];
+    if (ta > tb) {
+      double x = ta;
+      ta = tb;
+      tb = x;
+    }
+    t0 = fmax(t0, ta);
+    t1 = fmin(t1, tb);
+  }
+  double s0 = 1e-9 * fabs(t0), s1 = 1e-9 * fabs(t1);
+  return !(t0 - s0 > t1 + s1) && !(t1 + s1 < tlo) && !(t0 - s0 > thi);
+}
+
+template <bool kAny>
+__global__ void __launch_bounds__(kRetestBlock) k_retest64(TraceArgs A) {
+  const int nflag = min(*(volatile int*)A.counter, A.qcap);
+  for (int j = blockIdx.x * kRetestBlock + threadIdx.x; j < nflag; j += gridDim.x * kRetestBlock) {
+    const int i = A.queue[j];
+    const rt_ray ry = A.rays[i];
+    const D3 o{ry.ox, ry.oy, ry.oz}, d{ry.dx, ry.dy, ry.dz};
+    const double tmin = ry.tmin, tmax = ry.tmax;
+    const int skip = A.skip ? A.skip[i] : -1;
+    double bt = INFINITY, bu = 0.0, bv = 0.0;
+    int bid = -1;
+    bool any = false;
+    int node = 0, slot = 0;
+    for (;;) {
+      const WNode& w = A.wide[node];
+      const float lxa[4] = {w.lox.x, w.lox.y, w.lox.z, w.lox.w}, hxa[4] = {w.hix.x, w.hix.y, w.hix.z, w.hix.w};
+      const float lya[4] = {w.loy.x, w.loy.y, w.loy.z, w.loy.w}, hya[4] = {w.hiy.x, w.hiy.y, w.hiy.z, w.hiy.w};
+      const float lza[4] = {w.loz.x, w.loz.y, w.loz.z, w.loz.w}, hza[4] = {w.hiz.x, w.hiz.y, w.hiz.z, w.hiz.w};
+      const int cha[4] = {w.child.x, w.child.y, w.child.z, w.child.w};
+      double thi = fmin(bt, tmax);
+      thi = thi + 1e-9 * fabs(thi);
+      int found = -1;
+      for (; slot < 4; ++slot) {
+        if (cha[slot] == INT_MIN) continue;
+        const float lo[3] = {lxa[slot], lya[slot], lza[slot]}, hi[3] = {hxa[slot], hya[slot], hza[slot]};
+        if (slab64(o, d, lo, hi, tmin, thi)) {
+          found = slot;
+          break;
+        }
+      }
+      if (found >= 0) {
+        const int ref = cha[found];
+        if (ref >= 0) {
+          node = ref;
+          slot = 0;
+          continue;
+        }
+        const int first = leaf_first(ref), count = leaf_count(ref);
+        for (int k = 0; k < count && !(kAny && any); ++k) {
+          const float4* tp = A.tris + 3 * (size_t)(first + k);
+          float4 va = tp[0], vb = tp[1], vc = tp[2];
+          int id = __float_as_int(va.w);
+          if (id == skip) continue;
+          double t, u, v;
+          if (mt64(o, d, D3{va.x, va.y, va.z}, D3{vb.x, vb.y, vb.z}, D3{vc.x, vc.y, vc.z}, &t, &u, &v) &&
+              t > tmin && t < tmax) {
+            any = true;
+            if (t < bt || (t == bt && id < bid)) {
+              bt = t;
+              bid = id;
+              bu = u;
+              bv = v;
+            }
+          }
+        }
+        if (kAny && any) break;
+        slot = found + 1;
+        continue;
+      }
+      if (node == 0) break;
+      slot = w.meta.y + 1;
+      node = w.meta.x;
+    }
+    if (kAny) {
+      A.occl[i] = any ? 1 : 0;
+    } else {
+      float4 out = bid >= 0 ? make_float4((float)bt, __int_as_float(bid), (float)bu, (float)bv)
+                            : make_float4(INFINITY, __int_as_float(-1), 0.f, 0.f);
+      reinterpret_cast<float4*>(A.hits)[i] = out;
+    }
+  }
+}
+
+int sm_count_t() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+}  // namespace
+
+cudaError_t launch_trace(rt_scene_s* s, const rt_ray* rays, int64_t n, rt_hit* hits, uint8_t* occl,
+                         const rt_trace_params* tp, TraceScratch& scr, cudaStream_t st) {
+  cudaError_t e;
+  int n_launched = 0;
+  if ((e = cudaMemsetAsync(scr.counter, 0, 2 * sizeof(int), st))) return e;
+  if (n > 0) {
+    TraceArgs A;
+    A.wide = s->wide;
+    A.tris = s->tri_leaf;
+    A.rays = rays;
+    A.n = (int)n;
+    A.hits = hits;
+    A.occl = occl;
+    A.skip = tp ? tp->skip_tri_dev : nullptr;
+    const bool stats = tp && (tp->flags & RT_COUNT_STATS) && tp->stats_dev;
+    A.stats = stats ? tp->stats_dev : nullptr;
+    A.counter = scr.counter;
+    A.queue = scr.queue;
+    A.qcap = (int)scr.cap;
+    const int grid = (int)((n + kTraceBlock - 1) / kTraceBlock);
+    if (occl) {
+      if (stats)
+        k_trace<true, true><<<grid, kTraceBlock, 0, st>>>(A);
+      else
+        k_trace<true, false><<<grid, kTraceBlock, 0, st>>>(A);
+    } else {
+      if (stats)
+        k_trace<false, true><<<grid, kTraceBlock, 0, st>>>(A);
+      else
+        k_trace<false, false><<<grid, kTraceBlock, 0, st>>>(A);
+    }
+    ++n_launched;
+    if (!(tp && (tp->flags & RT_NO_FP64_RETEST))) {
+      int g = (int)((n + kRetestBlock - 1) / kRetestBlock);
+      int gmax = sm_count_t() * 4;
+      g = g < gmax ? g : gmax;
+      if (occl)
+        k_retest64<true><<<g, kRetestBlock, 0, st>>>(A);
+      else
+        k_retest64<false><<<g, kRetestBlock, 0, st>>>(A);
+      ++n_launched;
+    }
+  }
+  if (tp && tp->n_flagged_dev) {
+    if ((e = cudaMemcpyAsync(tp->n_flagged_dev, scr.counter, sizeof(int), cudaMemcpyDeviceToDevice, st)))
+      return e;
+  }
+  count_launches(n_launched);
+  return cudaGetLastError();
+}
+
+}  // namespace rt

@@ -1,0 +1,293 @@
+"""Python binding of librtbvh (include/rtbvh.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts torch
+tensors / numpy arrays to pointers and sizes, passes the current CUDA stream
+and turns error codes into exceptions.  There is no CPU fallback: if the
+library cannot be built or loaded, every call raises.
+
+Tensor conventions
+  tris  float32 [T, 3, 3]  (numpy on the host or a CUDA tensor)
+  rays  float32 [R, 8]     CUDA tensor, 16-byte aligned: (o, tmin, d, tmax)
+  hits  float32 [R, 4]     CUDA tensor: (t, tri id as int32 bits, u, v);
+                           hits.view(torch.int32)[:, 1] gives the ids
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build_ext
+
+RT_NO_FP64_RETEST = 1
+RT_COUNT_STATS = 2
+
+_lock = threading.Lock()
+_lib = None
+
+ERRORS = {-1: "RT_EINVAL", -2: "RT_ENOMEM", -3: "RT_ENOTBUILT", -4: "RT_ETIMEOUT", -5: "RT_ECUDA",
+          -6: "RT_EBUSY", -7: "RT_EINTERNAL"}
+
+# Every symbol the header declares (checked by the ABI test).
+EXPORTS = ["rt_version", "rt_launch_count", "rt_last_error", "rt_scene_upload", "rt_scene_destroy", "rt_scene_update",
+           "rt_bvh_build", "rt_bvh_info", "rt_bvh_export", "rt_trace_closest", "rt_trace_any",
+           "rt_trace_closest_host"]
+
+
+class RtError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "?"), code, msg))
+        self.code = code
+
+
+class BuildParams(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_float), ("t_i", ctypes.c_float), ("t_trav", ctypes.c_float),
+                ("source", ctypes.c_float * 3), ("max_leaf", ctypes.c_int32),
+                ("bins", ctypes.c_int32), ("width", ctypes.c_int32), ("dist_norm", ctypes.c_int32)]
+
+
+class TraceParams(ctypes.Structure):
+    _fields_ = [("flags", ctypes.c_uint32), ("skip_tri_dev", ctypes.c_void_p),
+                ("stats_dev", ctypes.c_void_p), ("n_flagged_dev", ctypes.c_void_p)]
+
+
+class BvhInfo(ctypes.Structure):
+    _fields_ = [("n_tri", ctypes.c_int64), ("n_bvh2_internal", ctypes.c_int64),
+                ("n_leaves", ctypes.c_int64), ("n_wide", ctypes.c_int64), ("depth2", ctypes.c_int32),
+                ("depth_wide", ctypes.c_int32), ("max_leaf_size", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("build_ms", ctypes.c_double)]
+
+
+def lib_path() -> str:
+    return build_ext.LIB
+
+
+def lib(build: bool = True):
+    """Load librtbvh.so (building it first if sources are newer)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build_ext.build() if build else build_ext.LIB
+            if not os.path.exists(path):
+                raise RuntimeError("librtbvh.so is missing at %s; run __graft_entry__.build()" % path)
+            L = ctypes.CDLL(path)
+            vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+            L.rt_version.restype = i32
+            L.rt_launch_count.restype = ctypes.c_uint64
+            L.rt_last_error.restype = ctypes.c_char_p
+            L.rt_scene_upload.argtypes = [vp, i64, i32, vp, ctypes.POINTER(vp)]
+            L.rt_scene_update.argtypes = [vp, vp, i64, i32, vp]
+            L.rt_scene_destroy.argtypes = [vp]
+            L.rt_bvh_build.argtypes = [vp, ctypes.POINTER(BuildParams), vp]
+            L.rt_bvh_info.argtypes = [vp, vp, ctypes.POINTER(BvhInfo)]
+            L.rt_bvh_export.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+            L.rt_trace_closest.argtypes = [vp, vp, i64, vp, ctypes.POINTER(TraceParams), vp]
+            L.rt_trace_any.argtypes = [vp, vp, i64, vp, ctypes.POINTER(TraceParams), vp]
+            L.rt_trace_closest_host.argtypes = [vp, vp, i64, vp, ctypes.POINTER(TraceParams), vp]
+            _lib = L
+    return _lib
+
+
+def _check(code):
+    if code != 0:
+        raise RtError(code, lib().rt_last_error().decode(errors="replace"))
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev_ptr(t, dtype, cols=None, name="tensor"):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda):
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype or not t.is_contiguous():
+        raise TypeError("%s must be contiguous %s" % (name, dtype))
+    if cols is not None and (t.dim() != 2 or t.shape[1] != cols):
+        raise TypeError("%s must have shape [n, %d]" % (name, cols))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Scene:
+    """Owns one rt_scene handle."""
+
+    def __init__(self, handle, n_tri):
+        self._h = handle
+        self.n_tri = n_tri
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise RuntimeError("scene destroyed")
+        return self._h
+
+    def destroy(self):
+        if self._h:
+            _check(lib().rt_scene_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def rt_version() -> int:
+    return lib().rt_version()
+
+
+def rt_launch_count() -> int:
+    return int(lib().rt_launch_count())
+
+
+def rt_scene_upload(tris, stream=None) -> Scene:
+    import torch
+    h = ctypes.c_void_p()
+    if isinstance(tris, torch.Tensor) and tris.is_cuda:
+        t = tris.reshape(-1, 9)
+        _dev_ptr(t, torch.float32, 9, "tris")
+        n = t.shape[0]
+        _check(lib().rt_scene_upload(ctypes.c_void_p(t.data_ptr()), n, 1, _stream(stream), ctypes.byref(h)))
+    else:
+        a = np.ascontiguousarray(np.asarray(tris, dtype=np.float32).reshape(-1, 9))
+        n = a.shape[0]
+        _check(lib().rt_scene_upload(a.ctypes.data_as(ctypes.c_void_p), n, 0, _stream(stream), ctypes.byref(h)))
+        torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+    return Scene(h.value, n)
+
+
+def rt_scene_update(scene: Scene, tris, stream=None):
+    import torch
+    if isinstance(tris, torch.Tensor) and tris.is_cuda:
+        t = tris.reshape(-1, 9)
+        _dev_ptr(t, torch.float32, 9, "tris")
+        _check(lib().rt_scene_update(scene.handle, ctypes.c_void_p(t.data_ptr()), t.shape[0], 1, _stream(stream)))
+        scene.n_tri = t.shape[0]
+    else:
+        a = np.ascontiguousarray(np.asarray(tris, dtype=np.float32).reshape(-1, 9))
+        _check(lib().rt_scene_update(scene.handle, a.ctypes.data_as(ctypes.c_void_p), a.shape[0], 0, _stream(stream)))
+        scene.n_tri = a.shape[0]
+        (torch.cuda.current_stream() if stream is None else stream).synchronize()
+
+
+def build_params(alpha=1.0, source=(0.0, 0.0, 0.0), max_leaf=4, bins=16, width=4, dist_norm=0,
+                 t_i=1.0, t_trav=1.0) -> BuildParams:
+    p = BuildParams()
+    p.alpha, p.t_i, p.t_trav = alpha, t_i, t_trav
+    for k in range(3):
+        p.source[k] = float(source[k])
+    p.max_leaf, p.bins, p.width, p.dist_norm = int(max_leaf), int(bins), int(width), int(dist_norm)
+    return p
+
+
+def rt_bvh_build(scene: Scene, stream=None, **kw):
+    p = build_params(**kw)
+    _check(lib().rt_bvh_build(scene.handle, ctypes.byref(p), _stream(stream)))
+
+
+def rt_bvh_info(scene: Scene, stream=None) -> dict:
+    info = BvhInfo()
+    code = lib().rt_bvh_info(scene.handle, _stream(stream), ctypes.byref(info))
+    d = {f: getattr(info, f) for f, _ in BvhInfo._fields_}
+    if code != 0:
+        raise RtError(code, lib().rt_last_error().decode() + " info=%r" % d)
+    return d
+
+
+def rt_bvh_export(scene: Scene, stream=None) -> dict:
+    info = rt_bvh_info(scene, stream)
+    ni, nl, n = info["n_bvh2_internal"], info["n_leaves"], info["n_tri"]
+    child = np.zeros(2 * max(ni, 1), np.int32)
+    lf = np.zeros(max(nl, 1), np.int64)
+    lc = np.zeros(max(nl, 1), np.int64)
+    prims = np.zeros(max(n, 1), np.int32)
+    boxes = np.zeros(12 * max(ni, 1), np.float32)
+    _check(lib().rt_bvh_export(scene.handle, _stream(stream), child.ctypes.data_as(ctypes.c_void_p),
+                               lf.ctypes.data_as(ctypes.c_void_p), lc.ctypes.data_as(ctypes.c_void_p),
+                               prims.ctypes.data_as(ctypes.c_void_p), boxes.ctypes.data_as(ctypes.c_void_p)))
+    return dict(child=child[: 2 * ni].reshape(-1, 2), leaf_first=lf[:nl], leaf_count=lc[:nl],
+                prims=prims[:n], boxes=boxes[: 12 * ni].reshape(-1, 12), info=info)
+
+
+def _trace_params(flags, skip, stats, n_flagged, n):
+    import torch
+    tp = TraceParams()
+    tp.flags = int(flags)
+    if skip is not None:
+        if skip.shape != (n,):
+            raise TypeError("skip must have shape [n]")
+        tp.skip_tri_dev = _dev_ptr(skip, torch.int32, None, "skip").value
+    if stats is not None:
+        if stats.shape != (n, 2):
+            raise TypeError("stats must have shape [n, 2]")
+        tp.stats_dev = _dev_ptr(stats, torch.int32, 2, "stats").value
+        tp.flags |= RT_COUNT_STATS
+    if n_flagged is not None:
+        tp.n_flagged_dev = _dev_ptr(n_flagged, torch.int32, None, "n_flagged").value
+    return tp
+
+
+def rt_trace_closest(scene: Scene, rays, hits=None, skip=None, flags=0, stats=None, n_flagged=None,
+                     stream=None):
+    """Closest hit of every ray; returns hits float32 [n, 4] (see module doc)."""
+    import torch
+    rp = _dev_ptr(rays, torch.float32, 8, "rays")
+    n = rays.shape[0]
+    if hits is None:
+        hits = torch.empty((n, 4), dtype=torch.float32, device=rays.device)
+    hp = _dev_ptr(hits, torch.float32, 4, "hits")
+    tp = _trace_params(flags, skip, stats, n_flagged, n)
+    _check(lib().rt_trace_closest(scene.handle, rp, n, hp, ctypes.byref(tp), _stream(stream)))
+    return hits
+
+
+def rt_trace_any(scene: Scene, rays, occluded=None, skip=None, flags=0, stats=None, n_flagged=None,
+                 stream=None):
+    """Any hit of every ray; returns uint8 [n] (1 = some triangle within (tmin, tmax))."""
+    import torch
+    rp = _dev_ptr(rays, torch.float32, 8, "rays")
+    n = rays.shape[0]
+    if occluded is None:
+        occluded = torch.empty((n,), dtype=torch.uint8, device=rays.device)
+    op = _dev_ptr(occluded, torch.uint8, None, "occluded")
+    tp = _trace_params(flags, skip, stats, n_flagged, n)
+    _check(lib().rt_trace_any(scene.handle, rp, n, op, ctypes.byref(tp), _stream(stream)))
+    return occluded
+
+
+def rt_trace_closest_host(scene: Scene, rays_host, hits_host=None, flags=0, stream=None):
+    """Closest hit with host buffers (pinned torch tensors or numpy arrays)."""
+    import torch
+    if isinstance(rays_host, torch.Tensor):
+        if rays_host.is_cuda or rays_host.dtype != torch.float32 or not rays_host.is_contiguous():
+            raise TypeError("rays_host must be a contiguous host float32 tensor")
+        n = rays_host.shape[0]
+        rp = ctypes.c_void_p(rays_host.data_ptr())
+        if hits_host is None:
+            hits_host = torch.empty((n, 4), dtype=torch.float32, pin_memory=True)
+        hp = ctypes.c_void_p(hits_host.data_ptr())
+    else:
+        a = np.ascontiguousarray(rays_host, dtype=np.float32)
+        n = a.shape[0]
+        rp = a.ctypes.data_as(ctypes.c_void_p)
+        if hits_host is None:
+            hits_host = np.empty((n, 4), np.float32)
+        hp = hits_host.ctypes.data_as(ctypes.c_void_p)
+    tp = TraceParams()
+    tp.flags = int(flags)
+    _check(lib().rt_trace_closest_host(scene.handle, rp, n, hp, ctypes.byref(tp), _stream(stream)))
+    return hits_host
+
+
+def hit_ids(hits):
+    """int32 triangle ids of a hits tensor/array [n, 4]."""
+    import torch
+    if isinstance(hits, torch.Tensor):
+        return hits.view(torch.int32)[:, 1]
+    return np.ascontiguousarray(hits).view(np.int32)[:, 1]

@@ -1,0 +1,44 @@
+"""The C-ABI library builds, loads and exports every symbol its header
+declares (no GPU calls)."""
+import ctypes
+import os
+import re
+
+from paper_2208_10008_gb300 import build_ext, rtbvh
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            names |= set(re.findall(r"^\s*(?:const\s+)?\w+\**\s+\**(rt_\w+)\s*\(", src, re.M))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    path = build_ext.build()
+    lib = ctypes.CDLL(path)
+    names = declared()
+    assert len(names) >= 10
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(rtbvh.EXPORTS) == names
+
+
+def test_version_and_error_string_without_gpu():
+    lib = rtbvh.lib()
+    assert lib.rt_version() >= 100
+    assert isinstance(lib.rt_last_error(), bytes)
+
+
+def test_null_arguments_rejected_without_gpu():
+    lib = rtbvh.lib()
+    assert lib.rt_scene_destroy(None) == -1
+    assert lib.rt_bvh_build(None, None, None) == -1
+    assert lib.rt_trace_closest(None, None, 0, None, None, None) == -1
+    out = ctypes.c_void_p()
+    assert lib.rt_scene_upload(None, -5, 0, None, ctypes.byref(out)) == -1
+    assert b"n_tri" in lib.rt_last_error()
