@@ -35,7 +35,6 @@ constexpr int kTierABlock = 256;
 constexpr int kTierAWarps = kTierABlock / 32;
 constexpr int kTierBBlock = 256;
 constexpr int kTierBWarps = kTierBBlock / 32;
-constexpr int kTierBStack = 32;
 constexpr int kCollapseBlock = 128;
 
 __device__ __forceinline__ void set_status(BuildCtl* ctl, int code, int where) {
@@ -115,7 +114,7 @@ __global__ void __launch_bounds__(kPrepBlock) k_prep(const float4* __restrict__ 
                            fminf(a.z, fminf(b.z, c.z)));
     float3 h = make_float3(fmaxf(a.x, fmaxf(b.x, c.x)), fmaxf(a.y, fmaxf(b.y, c.y)),
                            fmaxf(a.z, fmaxf(b.z, c.z)));
-    plo[i] = make_float4(l.x, l.y, l.z, 0.f);
+    plo[i] = make_float4(l.x, l.y, l.z, __int_as_float(i));
     phi[i] = make_float4(h.x, h.y, h.z, 0.f);
     float cc[3] = {centre(l.x, h.x), centre(l.y, h.y), centre(l.z, h.z)};
     float ll[3] = {l.x, l.y, l.z}, hh[3] = {h.x, h.y, h.z};
@@ -452,10 +451,8 @@ __device__ __forceinline__ bool goes_left(float4 lo, float4 hi, const SplitResul
 }
 
 struct BuildArgs {
-  const float4* plo;
-  const float4* phi;
-  int32_t* idx;
-  int32_t* tmp;
+  float4* rec;       // [2T] primitive records in build order: (lo.xyz, id) (hi.xyz, 0)
+  float4* rec_tmp;   // [2T] partition scratch
   Node2* node2;
   BuildCtl* ctl;
   Task* qa;
@@ -475,13 +472,13 @@ __device__ void emit_node(const BuildArgs& A, const Task& t, int nl, const float
   int cnt[2] = {nl, t.count - nl};
   int ref[2];
   *nout = 0;
+  int leaves = 0, big = 0;
   for (int s = 0; s < 2; ++s) {
     int b = s == 0 ? t.begin : t.begin + nl;
     if (cnt[s] <= A.max_leaf) {
       ref[s] = leaf_ref(b, cnt[s]);
-      atomicAdd(&A.ctl->n_leaves, 1);
-      atomicMax(&A.ctl->max_leaf_size, cnt[s]);
-      atomicMax(&A.ctl->depth2, t.depth + 1);
+      ++leaves;
+      big = max(big, cnt[s]);
     } else {
       ref[s] = INT_MAX;  // patched by the child when it splits
       Task c;
@@ -512,7 +509,13 @@ __device__ void emit_node(const BuildArgs& A, const Task& t, int nl, const float
     *slot = __int_as_float(id);
   }
   atomicAdd(&A.ctl->n_internal, 1);
-  atomicMax(&A.ctl->depth2, t.depth);
+  if (leaves) {
+    atomicAdd(&A.ctl->n_leaves, leaves);
+    atomicMax(&A.ctl->max_leaf_size, big);
+    atomicMax(&A.ctl->depth2, t.depth + 1);
+  } else {
+    atomicMax(&A.ctl->depth2, t.depth);
+  }
 }
 
 __device__ void push_a(const BuildArgs& A, const Task& c) {
@@ -536,14 +539,57 @@ __device__ void push_b(const BuildArgs& A, const Task& c) {
   A.qb[s] = c;
 }
 
+// Best candidate of a bin set: (cost, candidate) minimum over the calling
+// threads' share, reduced within the warp (ties: lowest candidate index, i.e.
+// lowest axis, then lowest plane).
+__device__ __forceinline__ void warp_best(const int* bins, int K, int n, const float scl[3],
+                                          const CostP& cp, float3 nlo, float3 nhi, int first,
+                                          int stride, float* best, int* bestc) {
+  *best = INFINITY;
+  *bestc = INT_MAX;
+  for (int c = first; c < 3 * (K - 1); c += stride) {
+    float v = eval_candidate(bins, K, c, n, scl, cp, nlo, nhi);
+    if (v < *best) {
+      *best = v;
+      *bestc = c;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    float ov = __shfl_xor_sync(0xffffffffu, *best, o);
+    int oc = __shfl_xor_sync(0xffffffffu, *bestc, o);
+    if (ov < *best || (ov == *best && oc < *bestc)) {
+      *best = ov;
+      *bestc = oc;
+    }
+  }
+}
+
+__device__ __forceinline__ SplitResult make_split(const int* bins, int K, int n, float best, int bestc) {
+  SplitResult sr;
+  if (bestc == INT_MAX || !(best < INFINITY)) {
+    sr.axis = -1;  // no usable plane: split the range in the middle
+    sr.plane = 0;
+    sr.nl = n / 2;
+  } else {
+    sr.axis = bestc / (K - 1);
+    sr.plane = 1 + bestc % (K - 1);
+    sr.nl = left_count(bins, K, sr.axis, sr.plane);
+  }
+  return sr;
+}
+
 // ------------------------------------------------------------------ tier A
+// One CTA per node of more than kTierASmall triangles.  Records are read
+// coalesced, kUnrollA per thread in flight.
+constexpr int kUnrollA = 4;
+
 __global__ void __launch_bounds__(kTierABlock) k_tier_a(BuildArgs A) {
   __shared__ int wbins[kTierAWarps][kBinStride];
-  __shared__ int bins[3 * kMaxBins * 8];
+  __shared__ int bins[kBinStride];
   __shared__ Task task;
   __shared__ int s_slot;
-  __shared__ float s_cost[kTierABlock];
-  __shared__ int s_cand[kTierABlock];
+  __shared__ float s_cost[kTierAWarps];
+  __shared__ int s_cand[kTierAWarps];
   __shared__ SplitResult s_sr;
   __shared__ int s_wcount[kTierAWarps];
   __shared__ float s_acc[kTierAWarps][24];
@@ -582,6 +628,10 @@ __global__ void __launch_bounds__(kTierABlock) k_tier_a(BuildArgs A) {
     __syncthreads();
     if (s_slot < 0) return;
     const Task t = task;
+    // records of this range were written by other CTAs of this kernel: every
+    // read below goes through L2 (ld.global.cg), never a stale L1 line
+    const float4* rec = A.rec + 2 * (size_t)t.begin;
+    float4* tmp = A.rec_tmp + 2 * (size_t)t.begin;
     float cmin[3], scl[3];
     for (int a = 0; a < 3; ++a) {
       cmin[a] = t.clo[a];
@@ -590,9 +640,19 @@ __global__ void __launch_bounds__(kTierABlock) k_tier_a(BuildArgs A) {
     // 1. bin (warp-private bins, then merge)
     bins_zero(&wbins[0][0], K, kTierAWarps, tid, kTierABlock);
     __syncthreads();
-    for (int k = tid; k < t.count; k += kTierABlock) {
-      int p = A.idx[t.begin + k];
-      bins_add(wbins[warp], K, cmin, scl, A.plo[p], A.phi[p]);
+    for (int k0 = 0; k0 < t.count; k0 += kUnrollA * kTierABlock) {
+      float4 lo[kUnrollA], hi[kUnrollA];
+#pragma unroll
+      for (int j = 0; j < kUnrollA; ++j) {
+        int k = k0 + j * kTierABlock + tid;
+        if (k < t.count) {
+          lo[j] = __ldcg(rec + 2 * k);
+          hi[j] = __ldcg(rec + 2 * k + 1);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < kUnrollA; ++j)
+        if (k0 + j * kTierABlock + tid < t.count) bins_add(wbins[warp], K, cmin, scl, lo[j], hi[j]);
     }
     __syncthreads();
     for (int e = tid; e < 3 * K * 8; e += kTierABlock) {
@@ -605,27 +665,12 @@ __global__ void __launch_bounds__(kTierABlock) k_tier_a(BuildArgs A) {
       bins[e] = v;
     }
     __syncthreads();
-    // 2. Eq. 2 at every plane; argmin with (cost, candidate index) order
+    // 2. Eq. 2 at every plane
     float3 nlo, nhi;
     node_box(bins, K, scl, &nlo, &nhi);
-    const int ncand = 3 * (K - 1);
-    float best = INFINITY;
-    int bestc = INT_MAX;
-    for (int c = tid; c < ncand; c += kTierABlock) {
-      float v = eval_candidate(bins, K, c, t.count, scl, A.cp, nlo, nhi);
-      if (v < best) {
-        best = v;
-        bestc = c;
-      }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      float ov = __shfl_xor_sync(0xffffffffu, best, o);
-      int oc = __shfl_xor_sync(0xffffffffu, bestc, o);
-      if (ov < best || (ov == best && oc < bestc)) {
-        best = ov;
-        bestc = oc;
-      }
-    }
+    float best;
+    int bestc;
+    warp_best(bins, K, t.count, scl, A.cp, nlo, nhi, tid, kTierABlock, &best, &bestc);
     if (lane == 0) {
       s_cost[warp] = best;
       s_cand[warp] = bestc;
@@ -637,17 +682,7 @@ __global__ void __launch_bounds__(kTierABlock) k_tier_a(BuildArgs A) {
           best = s_cost[w];
           bestc = s_cand[w];
         }
-      SplitResult sr;
-      if (bestc == INT_MAX || !(best < INFINITY)) {
-        sr.axis = -1;
-        sr.plane = 0;
-        sr.nl = t.count / 2;
-      } else {
-        sr.axis = bestc / (K - 1);
-        sr.plane = 1 + bestc % (K - 1);
-        sr.nl = left_count(bins, K, sr.axis, sr.plane);
-      }
-      s_sr = sr;
+      s_sr = make_split(bins, K, t.count, best, bestc);
     }
     __syncthreads();
     const SplitResult sr = s_sr;
@@ -658,9 +693,8 @@ __global__ void __launch_bounds__(kTierABlock) k_tier_a(BuildArgs A) {
     for (int t0 = 0; t0 < t.count; t0 += kTierABlock) {
       int k = t0 + tid;
       bool valid = k < t.count;
-      int p = valid ? A.idx[t.begin + k] : 0;
-      float4 lo = valid ? A.plo[p] : make_float4(0, 0, 0, 0);
-      float4 hi = valid ? A.phi[p] : make_float4(0, 0, 0, 0);
+      float4 lo = valid ? __ldcg(rec + 2 * k) : make_float4(0, 0, 0, 0);
+      float4 hi = valid ? __ldcg(rec + 2 * k + 1) : make_float4(0, 0, 0, 0);
       bool left = valid && goes_left(lo, hi, sr, k, cmin, scl, K);
       unsigned m = __ballot_sync(0xffffffffu, left);
       int rank = __popc(m & ((1u << lane) - 1u));
@@ -674,13 +708,10 @@ __global__ void __launch_bounds__(kTierABlock) k_tier_a(BuildArgs A) {
       }
       if (valid) {
         int lpos = woff + rank;  // lefts before k in this tile
-        if (left) {
-          A.tmp[t.begin + lbase + lpos] = p;
-          acc.add(0, lo, hi);
-        } else {
-          A.tmp[t.begin + sr.nl + rbase + (k - t0 - lpos)] = p;
-          acc.add(1, lo, hi);
-        }
+        int dst = left ? lbase + lpos : sr.nl + rbase + (k - t0 - lpos);
+        tmp[2 * dst] = lo;
+        tmp[2 * dst + 1] = hi;
+        acc.add(left ? 0 : 1, lo, hi);
       }
       lbase += tot;
       rbase += min(kTierABlock, t.count - t0) - tot;
@@ -697,7 +728,10 @@ __global__ void __launch_bounds__(kTierABlock) k_tier_a(BuildArgs A) {
       s_fin[tid] = v;
     }
     if (tid == 0 && lbase != sr.nl) set_status(A.ctl, kStBadSplit, 1);
-    for (int k = tid; k < t.count; k += kTierABlock) A.idx[t.begin + k] = A.tmp[t.begin + k];
+    {
+      float4* __restrict__ dst = A.rec + 2 * (size_t)t.begin;
+      for (int k = tid; k < 2 * t.count; k += kTierABlock) dst[k] = __ldcg(tmp + k);
+    }
     __syncthreads();
     // 4. node + children
     if (tid == 0) {
@@ -718,20 +752,96 @@ __global__ void __launch_bounds__(kTierABlock) k_tier_a(BuildArgs A) {
 }
 
 // ------------------------------------------------------------------ tier B
+// One CTA per subtree of at most kTierASmall triangles.  The subtree's
+// records are copied to shared memory once; its nodes are then split by the
+// CTA's warps in parallel, each warp taking whole nodes from a shared stack
+// (and a short private stack when the shared one is full).
+constexpr int kTierBShared = 128;  // shared task stack entries
+constexpr int kTierBPriv = 16;     // private entries per warp (>= log2 kTierASmall + 2)
+
+struct TierBSmem {
+  float4 rec[2 * kTierASmall];
+  uint16_t idx[2][kTierASmall];
+  int bins[kTierBWarps][kBinStride];
+  Task shared_stack[kTierBShared];
+  Task priv[kTierBWarps][kTierBPriv];
+  Task cur[kTierBWarps];
+  int sp, pending, lock, pad;
+};
+
+// Critical sections are a few instructions long; the bound only guards
+// against a logic error turning into a hang.
+__device__ __forceinline__ bool smem_lock(int* l) {
+  for (int it = 0; atomicCAS(l, 0, 1) != 0; ++it) {
+    if (it > kSpinLimit) return false;
+    __nanosleep(32);
+  }
+  __threadfence_block();
+  return true;
+}
+__device__ __forceinline__ void smem_unlock(int* l) {
+  __threadfence_block();
+  atomicExch(l, 0);
+}
+
 __global__ void __launch_bounds__(kTierBBlock) k_tier_b(BuildArgs A) {
-  __shared__ int sbins[kTierBWarps][kBinStride];
-  __shared__ Task sstack[kTierBWarps][kTierBStack];
-  __shared__ Task scur[kTierBWarps];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int* bins = sbins[warp];
-  Task* stack = sstack[warp];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TierBSmem& S = *reinterpret_cast<TierBSmem*>(smem_raw);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int K = A.K;
-  const int nwarps = gridDim.x * kTierBWarps;
+  int* bins = S.bins[warp];
   const int total = min(*(volatile int*)&A.ctl->qb_count, A.ctl->qb_cap);
-  for (int ti = blockIdx.x * kTierBWarps + warp; ti < total; ti += nwarps) {
-    int sp = 0;
-    Task t = A.qb[ti];
-    for (;;) {
+  for (int ti = blockIdx.x; ti < total; ti += gridDim.x) {
+    const Task root = A.qb[ti];
+    const int gb = root.begin, n = root.count;
+    for (int k = tid; k < 2 * n; k += kTierBBlock) S.rec[k] = __ldcg(A.rec + 2 * (size_t)gb + k);
+    for (int k = tid; k < n; k += kTierBBlock) S.idx[0][k] = (uint16_t)k;
+    if (tid == 0) {
+      Task r = root;
+      r.begin = 0;
+      S.shared_stack[0] = r;
+      S.sp = 1;
+      S.pending = 1;
+      S.lock = 0;
+    }
+    __syncthreads();
+    int psp = 0;  // private stack depth (uniform in the warp)
+    for (int spin = 0;;) {
+      // lane 0 alone looks at the shared state; the warp follows its decision
+      int got = 0, done = 0;
+      if (lane == 0) {
+        if (psp > 0) {
+          S.cur[warp] = S.priv[warp][psp - 1];
+          got = 1;
+        } else {
+          if (smem_lock(&S.lock)) {
+            if (S.sp > 0) {
+              S.cur[warp] = S.shared_stack[--S.sp];
+              got = 1;
+            }
+            smem_unlock(&S.lock);
+          } else {
+            set_status(A.ctl, kStQueueTimeout, 4);
+            done = 1;
+          }
+        }
+        if (!got && *(volatile int*)&S.pending == 0) done = 1;
+      }
+      got = __shfl_sync(0xffffffffu, got, 0);
+      done = __shfl_sync(0xffffffffu, done, 0);
+      if (got && psp > 0) --psp;
+      if (!got) {
+        if (done) break;
+        if (++spin > kSpinLimit) {
+          set_status(A.ctl, kStQueueTimeout, 3);
+          break;
+        }
+        __nanosleep(64);
+        continue;
+      }
+      spin = 0;
+      __syncwarp();
+      const Task t = S.cur[warp];
       float cmin[3], scl[3];
       for (int a = 0; a < 3; ++a) {
         cmin[a] = t.clo[a];
@@ -740,104 +850,90 @@ __global__ void __launch_bounds__(kTierBBlock) k_tier_b(BuildArgs A) {
       bins_zero(bins, K, 1, lane, 32);
       __syncwarp();
       for (int k = lane; k < t.count; k += 32) {
-        int p = A.idx[t.begin + k];
-        bins_add(bins, K, cmin, scl, A.plo[p], A.phi[p]);
+        const int li = S.idx[0][t.begin + k];
+        bins_add(bins, K, cmin, scl, S.rec[2 * li], S.rec[2 * li + 1]);
       }
       __syncwarp();
       float3 nlo, nhi;
       node_box(bins, K, scl, &nlo, &nhi);
-      float best = INFINITY;
-      int bestc = INT_MAX;
-      for (int c = lane; c < 3 * (K - 1); c += 32) {
-        float v = eval_candidate(bins, K, c, t.count, scl, A.cp, nlo, nhi);
-        if (v < best) {
-          best = v;
-          bestc = c;
-        }
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        float ov = __shfl_xor_sync(0xffffffffu, best, o);
-        int oc = __shfl_xor_sync(0xffffffffu, bestc, o);
-        if (ov < best || (ov == best && oc < bestc)) {
-          best = ov;
-          bestc = oc;
-        }
-      }
-      SplitResult sr;
-      if (bestc == INT_MAX || !(best < INFINITY)) {
-        sr.axis = -1;
-        sr.plane = 0;
-        sr.nl = t.count / 2;
-      } else {
-        sr.axis = bestc / (K - 1);
-        sr.plane = 1 + bestc % (K - 1);
-        sr.nl = left_count(bins, K, sr.axis, sr.plane);
-      }
+      float best;
+      int bestc;
+      warp_best(bins, K, t.count, scl, A.cp, nlo, nhi, lane, 32, &best, &bestc);
+      const SplitResult sr = make_split(bins, K, t.count, best, bestc);
       Acc acc;
       acc.init();
       int lbase = 0, rbase = 0;
       for (int t0 = 0; t0 < t.count; t0 += 32) {
-        int k = t0 + lane;
-        bool valid = k < t.count;
-        int p = valid ? A.idx[t.begin + k] : 0;
-        float4 lo = valid ? A.plo[p] : make_float4(0, 0, 0, 0);
-        float4 hi = valid ? A.phi[p] : make_float4(0, 0, 0, 0);
-        bool left = valid && goes_left(lo, hi, sr, k, cmin, scl, K);
-        unsigned m = __ballot_sync(0xffffffffu, left);
-        int rank = __popc(m & ((1u << lane) - 1u));
+        const int k = t0 + lane;
+        const bool valid = k < t.count;
+        const int li = valid ? S.idx[0][t.begin + k] : 0;
+        const float4 lo = S.rec[2 * li], hi = S.rec[2 * li + 1];
+        const bool left = valid && goes_left(lo, hi, sr, k, cmin, scl, K);
+        const unsigned m = __ballot_sync(0xffffffffu, left);
+        const int rank = __popc(m & ((1u << lane) - 1u));
         if (valid) {
-          if (left) {
-            A.tmp[t.begin + lbase + rank] = p;
-            acc.add(0, lo, hi);
-          } else {
-            A.tmp[t.begin + sr.nl + rbase + (lane - rank)] = p;
-            acc.add(1, lo, hi);
-          }
+          const int dst = left ? lbase + rank : sr.nl + rbase + (lane - rank);
+          S.idx[1][t.begin + dst] = (uint16_t)li;
+          acc.add(left ? 0 : 1, lo, hi);
         }
-        int tot = __popc(m);
+        const int tot = __popc(m);
         lbase += tot;
         rbase += min(32, t.count - t0) - tot;
       }
       acc.warp_reduce();
       if (lane == 0 && lbase != sr.nl) set_status(A.ctl, kStBadSplit, 2);
       __syncwarp();
-      for (int k = lane; k < t.count; k += 32) A.idx[t.begin + k] = A.tmp[t.begin + k];
+      for (int k = lane; k < t.count; k += 32) S.idx[0][t.begin + k] = S.idx[1][t.begin + k];
       __syncwarp();
-      Task out[2];
-      int nout = 0;
-      if (lane == 0) emit_node(A, t, sr.nl, acc.v, out, &nout);
-      // continue with the smaller child and stack the larger one: every stacked
-      // entry halves the current size, so the stack never exceeds log2(n)
-      int have = 0;
       if (lane == 0) {
-        if (nout == 2) {
-          int small = out[0].count <= out[1].count ? 0 : 1;
-          if (sp < kTierBStack) {
-            stack[sp] = out[1 - small];
-            ++sp;
-          } else {
-            set_status(A.ctl, kStQueueOverflow, 3);
-          }
-          scur[warp] = out[small];
-          have = 1;
-        } else if (nout == 1) {
-          scur[warp] = out[0];
-          have = 1;
+        Task g = t;
+        g.begin = gb + t.begin;
+        Task out[2];
+        int nout = 0;
+        emit_node(A, g, sr.nl, acc.v, out, &nout);
+        if (nout) atomicAdd(&S.pending, nout);
+        // larger child to the shared stack (work for idle warps), smaller
+        // child kept by this warp; a full shared stack keeps both here
+        int order[2] = {0, 1};
+        if (nout == 2 && out[0].count < out[1].count) {
+          order[0] = 1;
+          order[1] = 0;
         }
+        for (int q = 0; q < nout; ++q) {
+          Task c = out[order[q]];
+          c.begin -= gb;
+          bool shared = false;
+          if (q == 0 && nout == 2) {
+            if (smem_lock(&S.lock)) {
+              if (S.sp < kTierBShared) {
+                S.shared_stack[S.sp++] = c;
+                shared = true;
+              }
+              smem_unlock(&S.lock);
+            }
+          }
+          if (!shared) {
+            if (psp < kTierBPriv) {
+              S.priv[warp][psp++] = c;
+            } else {
+              set_status(A.ctl, kStQueueOverflow, 4);
+              atomicSub(&S.pending, 1);
+            }
+          }
+        }
+        __threadfence_block();
+        atomicSub(&S.pending, 1);
       }
-      have = __shfl_sync(0xffffffffu, have, 0);
-      sp = __shfl_sync(0xffffffffu, sp, 0);
-      __syncwarp();
-      if (have) {
-        t = scur[warp];
-        __syncwarp();
-        continue;
-      }
-      if (sp == 0) break;
-      --sp;
-      t = stack[sp];
+      psp = __shfl_sync(0xffffffffu, psp, 0);
       __syncwarp();
     }
+    __syncthreads();
+    for (int k = tid; k < n; k += kTierBBlock) {
+      const int li = S.idx[0][k];
+      A.rec[2 * ((size_t)gb + k)] = S.rec[2 * li];
+      A.rec[2 * ((size_t)gb + k) + 1] = S.rec[2 * li + 1];
+    }
+    __syncthreads();
   }
 }
 
@@ -1018,13 +1114,25 @@ __global__ void __launch_bounds__(kCollapseBlock) k_collapse(CollapseArgs C) {
   }
 }
 
-__global__ void k_gather(const float4* __restrict__ tri_in, const int32_t* __restrict__ idx, int n,
-                         float4* __restrict__ tri_leaf) {
+// Records in Morton order (the build's starting order).
+__global__ void k_make_recs(const float4* __restrict__ plo, const float4* __restrict__ phi,
+                            const int32_t* __restrict__ idx, int n, float4* __restrict__ rec) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     int p = idx[k];
-    tri_leaf[3 * k] = tri_in[3 * p];
-    tri_leaf[3 * k + 1] = tri_in[3 * p + 1];
-    tri_leaf[3 * k + 2] = tri_in[3 * p + 2];
+    rec[2 * (size_t)k] = plo[p];
+    rec[2 * (size_t)k + 1] = phi[p];
+  }
+}
+
+// Triangles in leaf order (the final record order carries the ids).
+__global__ void k_gather(const float4* __restrict__ tri_in, const float4* __restrict__ rec, int n,
+                         float4* __restrict__ tri_leaf, int32_t* __restrict__ order) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    int p = __float_as_int(rec[2 * (size_t)k].w);
+    order[k] = p;
+    tri_leaf[3 * (size_t)k] = tri_in[3 * (size_t)p];
+    tri_leaf[3 * (size_t)k + 1] = tri_in[3 * (size_t)p + 1];
+    tri_leaf[3 * (size_t)k + 2] = tri_in[3 * (size_t)p + 2];
   }
 }
 
@@ -1073,13 +1181,17 @@ cudaError_t launch_build(rt_scene_s* s, const rt_build_params& p, cudaStream_t s
     ++n_launched;
     }
   }
-  k_root<<<1, 32, 0, st>>>(s->ctl, s->qa, s->qa_ready, s->qb, n, p.max_leaf, s->node2);
+  if (n > 0) {
+    int g = (n + 255) / 256;
+    g = g < nsm * 8 ? g : nsm * 8;
+    k_make_recs<<<g, 256, 0, st>>>(s->prim_lo, s->prim_hi, s->idx[0], n, s->rec[0]);
     ++n_launched;
+  }
+  k_root<<<1, 32, 0, st>>>(s->ctl, s->qa, s->qa_ready, s->qb, n, p.max_leaf, s->node2);
+  ++n_launched;
   BuildArgs A;
-  A.plo = s->prim_lo;
-  A.phi = s->prim_hi;
-  A.idx = s->idx[0];
-  A.tmp = s->idx[1];
+  A.rec = s->rec[0];
+  A.rec_tmp = s->rec[1];
   A.node2 = s->node2;
   A.ctl = s->ctl;
   A.qa = s->qa;
@@ -1092,13 +1204,18 @@ cudaError_t launch_build(rt_scene_s* s, const rt_build_params& p, cudaStream_t s
     k_tier_a<<<nsm, kTierABlock, 0, st>>>(A);
     ++n_launched;
   }
-  if (n > 0) {
-    k_tier_b<<<nsm * 2, kTierBBlock, 0, st>>>(A);
+  if (n > p.max_leaf) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_tier_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TierBSmem));
+      attr = true;
+    }
+    k_tier_b<<<nsm * 2, kTierBBlock, sizeof(TierBSmem), st>>>(A);
     ++n_launched;
   }
   CollapseArgs C{s->node2, s->wide, s->ctl, s->qc, s->qc_ready, qc_cap, n};
   k_collapse_init<<<1, 32, 0, st>>>(C);
-    ++n_launched;
+  ++n_launched;
   if (n > p.max_leaf) {
     k_collapse<<<nsm * 2, kCollapseBlock, 0, st>>>(C);
     ++n_launched;
@@ -1106,7 +1223,7 @@ cudaError_t launch_build(rt_scene_s* s, const rt_build_params& p, cudaStream_t s
   if (n > 0) {
     int g = (n + 255) / 256;
     g = g < nsm * 8 ? g : nsm * 8;
-    k_gather<<<g, 256, 0, st>>>(s->tri_in, s->idx[0], n, s->tri_leaf);
+    k_gather<<<g, 256, 0, st>>>(s->tri_in, s->rec[0], n, s->tri_leaf, s->idx[0]);
     ++n_launched;
   }
   count_launches(n_launched);

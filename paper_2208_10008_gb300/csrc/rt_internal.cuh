@@ -5,6 +5,8 @@
 //   prim_lo   float4[T]   per-triangle AABB min (w unused)      -- Eq. 3 boxes
 //   prim_hi   float4[T]   per-triangle AABB max
 //   keys/idx  u32/i32[T]  Morton keys and the triangle permutation (ping-pong pairs)
+//   rec       float4[2T]  build records (lo.xyz, id) (hi.xyz, 0), moved by every
+//                         partition so each pass reads them contiguously
 //   node2     Node2[T]    binary tree of Sec. II.C / Fig. 1; internal node id =
 //                         (split position - 1), a unique slot for every split
 //   wide      WNode[T]    4-wide traversal nodes (one 128-byte line each)
@@ -134,7 +136,8 @@ struct rt_scene_s {
   float4* prim_lo = nullptr;
   float4* prim_hi = nullptr;
   uint32_t* keys[2] = {nullptr, nullptr};
-  int32_t* idx[2] = {nullptr, nullptr};
+  int32_t* idx[2] = {nullptr, nullptr};  // idx[0] holds the leaf order after a build
+  float4* rec[2] = {nullptr, nullptr};   // primitive records (2 float4 each) + scratch
   uint32_t* sort_hist = nullptr;  // radix-sort histograms
   int64_t sort_hist_cap = 0;
   rt::Node2* node2 = nullptr;

@@ -63,6 +63,7 @@ __global__ void k_pack(const float* __restrict__ raw, int n, float4* __restrict_
 
 void free_scene_buffers(rt_scene_s* s) {
   void* ptrs[] = {s->tri_in, s->prim_lo, s->prim_hi, s->keys[0], s->keys[1], s->idx[0], s->idx[1],
+                  s->rec[0], s->rec[1],
                   s->sort_hist, s->node2, s->wide, s->tri_leaf, s->qa, s->qa_ready, s->qb, s->qc,
                   s->qc_ready, s->ctl, s->scratch.counter, s->scratch.queue,
                   s->host_scr[0].counter, s->host_scr[0].queue, s->host_scr[1].counter,
@@ -82,6 +83,7 @@ int ensure_capacity(rt_scene_s* s, int64_t n) {
   for (int k = 0; k < 2; ++k) {
     RT_CUDA(dev_alloc(&s->keys[k], m), "alloc keys");
     RT_CUDA(dev_alloc(&s->idx[k], m), "alloc index");
+    RT_CUDA(dev_alloc(&s->rec[k], 2 * m), "alloc build records");
   }
   const int64_t nb = (m + 256 * 32 - 1) / (256 * 32);
   RT_CUDA(dev_alloc(&s->sort_hist, 256 * nb), "alloc sort histogram");

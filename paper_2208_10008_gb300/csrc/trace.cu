@@ -16,11 +16,13 @@
 //     else, a second hit within the error window of the best one, a hit near
 //     tmin / tmax, or a stack overflow marks the ray for k_retest64.
 // k_retest64 (float64, one flagged ray per thread)
-//   * a stackless walk of the same tree (parent links), float64 box tests and
-//     the reference hit rule: Moller-Trumbore with inclusive edges, |det| <=
-//     1e-14 |e1||e2||d| is parallel, tmin < t < tmax, lowest id on equal t,
-//     with the operation order fixed and no contraction, so its answer is the
-//     float64 definition's answer bit for bit.
+//   * a stackless walk of the same tree (parent links), the same conservative
+//     float32 box test culled at the float64 best distance, and for every
+//     triangle the float32 bound does not prove missed, the reference hit
+//     rule: Moller-Trumbore with inclusive edges, |det| <= 1e-14 |e1||e2||d|
+//     is parallel, tmin < t < tmax, lowest id on equal t, with the operation
+//     order fixed and no contraction, so its answer is the float64
+//     definition's answer bit for bit.
 #include <cuda_runtime.h>
 
 #include <cfloat>
@@ -421,64 +423,34 @@ __device__ bool mt64(D3 o, D3 d, D3 v0, D3 v1, D3 v2, double* t, double* u, doub
   return true;
 }
 
-// float64 slab test of one child box, widened so that no box the exact ray
-// meets is missed (the result only decides which boxes are opened).
-__device__ bool slab64(D3 o, D3 d, const float lo[3], const float hi[3], double tlo, double thi) {
-  const double oo[3] = {o.x, o.y, o.z}, dd[3] = {d.x, d.y, d.z};
-  double t0 = -INFINITY, t1 = INFINITY;
-  for (int a = 0; a < 3; ++a) {
-    double pad = 1e-9 * (fabs((double)lo[a]) + fabs((double)hi[a]) + fabs(oo[a])) + 1e-12;
-    double l = (double)lo[a] - pad, h = (double)hi[a] + pad;
-    if (!(l <= h)) return false;  // empty slot
-    if (dd[a] == 0.0) {
-      if (oo[a] < l || oo[a] > h) return false;
-      continue;
-    }
-    double ta = (l - oo[a]) / dd[a], tb = (h - oo[a]) / dd[a];
-    if (ta > tb) {
-      double x = ta;
-      ta = tb;
-      tb = x;
-    }
-    t0 = fmax(t0, ta);
-    t1 = fmin(t1, tb);
-  }
-  double s0 = 1e-9 * fabs(t0), s1 = 1e-9 * fabs(t1);
-  return !(t0 - s0 > t1 + s1) && !(t1 + s1 < tlo) && !(t0 - s0 > thi);
-}
-
 template <bool kAny>
 __global__ void __launch_bounds__(kRetestBlock) k_retest64(TraceArgs A) {
   const int nflag = min(*(volatile int*)A.counter, A.qcap);
   for (int j = blockIdx.x * kRetestBlock + threadIdx.x; j < nflag; j += gridDim.x * kRetestBlock) {
     const int i = A.queue[j];
-    const rt_ray ry = A.rays[i];
-    const D3 o{ry.ox, ry.oy, ry.oz}, d{ry.dx, ry.dy, ry.dz};
-    const double tmin = ry.tmin, tmax = ry.tmax;
+    const float4* r4 = reinterpret_cast<const float4*>(A.rays) + 2 * (size_t)i;
+    const float4 ra = r4[0], rb = r4[1];
+    const RayPre r = setup_ray(ra, rb);
+    const D3 o{ra.x, ra.y, ra.z}, d{rb.x, rb.y, rb.z};
+    const double tmin = ra.w, tmax = rb.w;
     const int skip = A.skip ? A.skip[i] : -1;
     double bt = INFINITY, bu = 0.0, bv = 0.0;
     int bid = -1;
     bool any = false;
     int node = 0, slot = 0;
-    for (;;) {
-      const WNode& w = A.wide[node];
-      const float lxa[4] = {w.lox.x, w.lox.y, w.lox.z, w.lox.w}, hxa[4] = {w.hix.x, w.hix.y, w.hix.z, w.hix.w};
-      const float lya[4] = {w.loy.x, w.loy.y, w.loy.z, w.loy.w}, hya[4] = {w.hiy.x, w.hiy.y, w.hiy.z, w.hiy.w};
-      const float lza[4] = {w.loz.x, w.loz.y, w.loz.z, w.loz.w}, hza[4] = {w.hiz.x, w.hiz.y, w.hiz.z, w.hiz.w};
-      const int cha[4] = {w.child.x, w.child.y, w.child.z, w.child.w};
-      double thi = fmin(bt, tmax);
-      thi = thi + 1e-9 * fabs(thi);
-      int found = -1;
-      for (; slot < 4; ++slot) {
-        if (cha[slot] == INT_MIN) continue;
-        const float lo[3] = {lxa[slot], lya[slot], lza[slot]}, hi[3] = {hxa[slot], hya[slot], hza[slot]};
-        if (slab64(o, d, lo, hi, tmin, thi)) {
-          found = slot;
-          break;
-        }
-      }
-      if (found >= 0) {
-        const int ref = cha[found];
+    // Stackless walk (parent links) so that any depth works.  Boxes use the
+    // same widened float32 slab test as k_trace, culled at the float64 best
+    // distance rounded up; triangles the float32 bound proves missed are
+    // skipped, every other one goes through the float64 rule.
+    while (r.valid) {
+      float bf = (float)fmin(bt, tmax);
+      bf = bf + fabsf(bf) * 2e-6f;
+      float tn[4];
+      int4 ch;
+      unsigned m = slab4(A.wide + node, r, bf, tn, &ch) & (0xfu << slot) & 0xfu;
+      if (m) {
+        const int s = __ffs(m) - 1;
+        const int ref = s == 0 ? ch.x : (s == 1 ? ch.y : (s == 2 ? ch.z : ch.w));
         if (ref >= 0) {
           node = ref;
           slot = 0;
@@ -487,9 +459,10 @@ __global__ void __launch_bounds__(kRetestBlock) k_retest64(TraceArgs A) {
         const int first = leaf_first(ref), count = leaf_count(ref);
         for (int k = 0; k < count && !(kAny && any); ++k) {
           const float4* tp = A.tris + 3 * (size_t)(first + k);
-          float4 va = tp[0], vb = tp[1], vc = tp[2];
-          int id = __float_as_int(va.w);
+          const float4 va = tp[0], vb = tp[1], vc = tp[2];
+          const int id = __float_as_int(va.w);
           if (id == skip) continue;
+          if (tri_test(r, va, vb, vc).cls == 0) continue;  // certain miss
           double t, u, v;
           if (mt64(o, d, D3{va.x, va.y, va.z}, D3{vb.x, vb.y, vb.z}, D3{vc.x, vc.y, vc.z}, &t, &u, &v) &&
               t > tmin && t < tmax) {
@@ -503,12 +476,13 @@ __global__ void __launch_bounds__(kRetestBlock) k_retest64(TraceArgs A) {
           }
         }
         if (kAny && any) break;
-        slot = found + 1;
+        slot = s + 1;
         continue;
       }
       if (node == 0) break;
-      slot = w.meta.y + 1;
-      node = w.meta.x;
+      const int4 meta = A.wide[node].meta;
+      node = meta.x;
+      slot = meta.y + 1;
     }
     if (kAny) {
       A.occl[i] = any ? 1 : 0;
