@@ -4,14 +4,16 @@
 //   k_prep        per-triangle AABB (Eq. 3 boxes) + scene / centroid bounds
 //   k_morton      30-bit Morton key of each AABB centre (locality presort)
 //   radix sort    4 stable LSD passes (8-bit digits): hist, scan, scatter
+//   k_make_recs   32-byte records (box + id) in Morton order
 //   k_root        the root task (Fig. 2: "calculate the bounding volume that
 //                 contains all triangular facets")
-//   k_tier_a      one CTA per node of more than kTierASmall triangles, fed by
-//                 a device work queue: bin AABB centres into `bins` slabs per
-//                 axis, evaluate Eq. 2 at every bin plane, take the minimum
-//                 (ties: lowest axis, lowest plane), stable-partition the
-//                 node's index range, emit children (Fig. 2 recursion)
-//   k_tier_b      one warp per remaining subtree, depth first
+//   k_nodes       one CTA per node of more than kMicro triangles, fed by a
+//                 device work queue: bin the AABB centres into `bins` slabs
+//                 per axis, evaluate Eq. 2 at every bin plane, take the
+//                 minimum (ties: lowest axis, lowest plane), stable-partition
+//                 the node's range, emit the children (Fig. 2 recursion)
+//   k_micro       one warp per node of at most kMicro triangles: its whole
+//                 subtree, Eq. 2 over the splits of the range's order
 //   k_collapse    binary tree -> 4-wide traversal nodes (greedy by area)
 //   k_gather      triangles copied into leaf order
 //
@@ -30,12 +32,6 @@ namespace {
 
 constexpr int kPrepBlock = 256;
 constexpr int kSortBlock = 256;          // one element per thread per tile
-constexpr int kSortChunk = 256 * 32;     // elements per block per pass
-constexpr int kTierABlock = 256;
-constexpr int kTierAWarps = kTierABlock / 32;
-constexpr int kTierBBlock = 256;
-constexpr int kTierBWarps = kTierBBlock / 32;
-constexpr int kCollapseBlock = 128;
 
 __device__ __forceinline__ void set_status(BuildCtl* ctl, int code, int where) {
   if (atomicCAS(&ctl->status, 0, code) == 0) ctl->status_where = where;
@@ -178,58 +174,55 @@ __global__ void k_morton(const float4* __restrict__ plo, const float4* __restric
 // ------------------------------------------------------------------ radix sort
 __global__ void __launch_bounds__(kSortBlock) k_sort_hist(const uint32_t* __restrict__ keys, int n,
                                                           int shift, uint32_t* __restrict__ hist,
-                                                          int nblocks) {
+                                                          int nblocks, int chunk) {
   __shared__ uint32_t h[256];
   h[threadIdx.x] = 0;
   __syncthreads();
-  int b = blockIdx.x * kSortChunk, e = min(n, b + kSortChunk);
+  int b = blockIdx.x * chunk, e = min(n, b + chunk);
   for (int i = b + threadIdx.x; i < e; i += kSortBlock) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
   __syncthreads();
-  hist[threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+  hist[blockIdx.x * 256 + threadIdx.x] = h[threadIdx.x];
 }
 
-// Exclusive scan of m counters in one CTA of 1024 threads.
-__global__ void __launch_bounds__(1024) k_sort_scan(uint32_t* hist, int m) {
-  __shared__ uint32_t warp_sums[32];
-  __shared__ uint32_t carry;
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
-  for (int base = 0; base < m; base += 1024) {
-    int i = base + threadIdx.x;
-    uint32_t v = i < m ? hist[i] : 0u;
-    uint32_t x = v;
-    for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if ((threadIdx.x & 31) >= o) x += y;
-    }
-    if ((threadIdx.x & 31) == 31) warp_sums[threadIdx.x >> 5] = x;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      uint32_t w = warp_sums[threadIdx.x];
-      for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
-        if (threadIdx.x >= o) w += y;
-      }
-      warp_sums[threadIdx.x] = w;
-    }
-    __syncthreads();
-    uint32_t wofs = (threadIdx.x >> 5) ? warp_sums[(threadIdx.x >> 5) - 1] : 0u;
-    if (i < m) hist[i] = carry + wofs + x - v;
-    __syncthreads();
-    if (threadIdx.x == 1023) carry += wofs + x;
-    __syncthreads();
+// Exclusive offsets of every (block, digit) counter: hist[b * 256 + d] <-
+// (elements with digit < d) + (elements with digit d in blocks < b).  One
+// CTA, thread d walks digit d over the blocks (coalesced across threads).
+__global__ void __launch_bounds__(256) k_sort_scan(uint32_t* hist, int nblocks) {
+  __shared__ uint32_t tot[256];
+  __shared__ uint32_t wsum[8];
+  const int d = threadIdx.x;
+  uint32_t run = 0;
+  for (int b = 0; b < nblocks; ++b) {
+    uint32_t c = hist[b * 256 + d];
+    hist[b * 256 + d] = run;
+    run += c;
   }
+  // exclusive scan of the digit totals
+  uint32_t x = run;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if ((d & 31) >= o) x += y;
+  }
+  if ((d & 31) == 31) wsum[d >> 5] = x;
+  __syncthreads();
+  uint32_t wofs = 0;
+  for (int w = 0; w < (d >> 5); ++w) wofs += wsum[w];
+  tot[d] = wofs + x - run;
+  __syncthreads();
+  const uint32_t base = tot[d];
+  for (int b = 0; b < nblocks; ++b) hist[b * 256 + d] += base;
 }
 
 // Stable scatter: tiles of 256 elements, warp-major; ranks from match_any.
 __global__ void __launch_bounds__(kSortBlock) k_sort_scatter(
     const uint32_t* __restrict__ kin, const int32_t* __restrict__ vin, uint32_t* __restrict__ kout,
-    int32_t* __restrict__ vout, int n, int shift, const uint32_t* __restrict__ hist, int nblocks) {
+    int32_t* __restrict__ vout, int n, int shift, const uint32_t* __restrict__ hist, int nblocks,
+    int chunk) {
   __shared__ uint32_t base[256];
   __shared__ uint32_t wh[kSortBlock / 32][256];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  base[threadIdx.x] = hist[threadIdx.x * nblocks + blockIdx.x];
-  int b = blockIdx.x * kSortChunk, e = min(n, b + kSortChunk);
+  base[threadIdx.x] = hist[blockIdx.x * 256 + threadIdx.x];
+  int b = blockIdx.x * chunk, e = min(n, b + chunk);
   for (int t0 = b; t0 < e; t0 += kSortBlock) {
     for (int k = threadIdx.x; k < (kSortBlock / 32) * 256; k += kSortBlock) (&wh[0][0])[k] = 0u;
     __syncthreads();
@@ -285,7 +278,7 @@ __global__ void k_root(BuildCtl* ctl, Task* qa, int* qa_ready, Task* qb, int n, 
     t.clo[a] = iford(ctl->cen_lo[a]);
     t.chi[a] = iford(ctl->cen_hi[a]);
   }
-  if (n > kTierASmall) {
+  if (n > kMicro) {
     qa[0] = t;
     ctl->qa_tail = 1;
     ctl->qa_pending = 1;
@@ -303,15 +296,25 @@ struct SplitResult {
   int axis, plane, nl;  // axis < 0: median fallback
 };
 
-constexpr int kBinStride = 3 * kMaxBins * 8;  // ints per bin set
+// A bin entry is 9 ints: count, lo xyz, hi xyz (ordered floats), 2 pad.  The
+// odd stride puts consecutive bins in different shared-memory banks.
+constexpr int kBinEnt = 9;
+constexpr int kBinStride = 3 * kMaxBins * kBinEnt;  // ints per bin set
 
-// Reset `nsets` bin sets laid out kBinStride ints apart (first 3*K*8 used).
+// Reset `nsets` bin sets laid out kBinStride ints apart (first 3*K entries used).
 __device__ __forceinline__ void bins_zero(int* bins, int K, int nsets, int tid, int nthreads) {
-  const int per = 3 * K * 8;
-  for (int k = tid; k < per * nsets; k += nthreads) {
-    int w = k / per, e = k - w * per;
-    int f = e & 7;
-    bins[w * kBinStride + e] = f == 0 ? 0 : (f <= 3 ? ford(FLT_MAX) : (f <= 6 ? ford(-FLT_MAX) : 0));
+  const int ent = 3 * K;
+  const int lo = ford(FLT_MAX), hi = ford(-FLT_MAX);
+  for (int k = tid; k < ent * nsets; k += nthreads) {
+    const int w = k >= ent ? k / ent : 0;
+    int* e = bins + w * kBinStride + (k - w * ent) * kBinEnt;
+    e[0] = 0;
+    e[1] = lo;
+    e[2] = lo;
+    e[3] = lo;
+    e[4] = hi;
+    e[5] = hi;
+    e[6] = hi;
   }
 }
 
@@ -340,7 +343,7 @@ __device__ __forceinline__ void bins_add(int* bins, int K, const float cmin[3], 
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     if (scl[a] <= 0.f) continue;
-    int* bb = bins + (a * K + bin_of(c[a], cmin[a], scl[a], K)) * 8;
+    int* bb = bins + (a * K + bin_of(c[a], cmin[a], scl[a], K)) * kBinEnt;
     atomicAdd(bb, 1);
     atomicMin(bb + 1, ford(lo.x));
     atomicMin(bb + 2, ford(lo.y));
@@ -348,54 +351,6 @@ __device__ __forceinline__ void bins_add(int* bins, int K, const float cmin[3], 
     atomicMax(bb + 4, ford(hi.x));
     atomicMax(bb + 5, ford(hi.y));
     atomicMax(bb + 6, ford(hi.z));
-  }
-}
-
-// Cost of candidate c (axis c / (K-1), plane 1 + c % (K-1)); +inf when invalid.
-__device__ float eval_candidate(const int* bins, int K, int c, int n, const float scl[3],
-                                const CostP& cp, float3 nlo, float3 nhi) {
-  int a = c / (K - 1), p = 1 + c % (K - 1);
-  if (scl[a] <= 0.f) return INFINITY;
-  const int* ba = bins + a * K * 8;
-  int nl = 0;
-  float3 llo = make_float3(FLT_MAX, FLT_MAX, FLT_MAX), lhi = make_float3(-FLT_MAX, -FLT_MAX, -FLT_MAX);
-  float3 rlo = llo, rhi = lhi;
-  for (int b = 0; b < K; ++b) {
-    const int* e = ba + b * 8;
-    int cnt = e[0];
-    if (cnt == 0) continue;
-    float3 lo = make_float3(iford(e[1]), iford(e[2]), iford(e[3]));
-    float3 hi = make_float3(iford(e[4]), iford(e[5]), iford(e[6]));
-    if (b < p) {
-      nl += cnt;
-      llo = make_float3(fminf(llo.x, lo.x), fminf(llo.y, lo.y), fminf(llo.z, lo.z));
-      lhi = make_float3(fmaxf(lhi.x, hi.x), fmaxf(lhi.y, hi.y), fmaxf(lhi.z, hi.z));
-    } else {
-      rlo = make_float3(fminf(rlo.x, lo.x), fminf(rlo.y, lo.y), fminf(rlo.z, lo.z));
-      rhi = make_float3(fmaxf(rhi.x, hi.x), fmaxf(rhi.y, hi.y), fmaxf(rhi.z, hi.z));
-    }
-  }
-  if (nl == 0 || nl == n) return INFINITY;
-  return eq2_cost(llo, lhi, nl, rlo, rhi, n - nl, nlo, nhi, cp);
-}
-
-__device__ __forceinline__ int left_count(const int* bins, int K, int axis, int plane) {
-  int nl = 0;
-  for (int b = 0; b < plane; ++b) nl += bins[(axis * K + b) * 8];
-  return nl;
-}
-
-// Node box = union of all bins of any active axis (every triangle is in
-// exactly one bin per active axis).
-__device__ void node_box(const int* bins, int K, const float scl[3], float3* lo, float3* hi) {
-  *lo = make_float3(FLT_MAX, FLT_MAX, FLT_MAX);
-  *hi = make_float3(-FLT_MAX, -FLT_MAX, -FLT_MAX);
-  int a = scl[0] > 0.f ? 0 : (scl[1] > 0.f ? 1 : 2);
-  for (int b = 0; b < K; ++b) {
-    const int* e = bins + (a * K + b) * 8;
-    if (e[0] == 0) continue;
-    *lo = make_float3(fminf(lo->x, iford(e[1])), fminf(lo->y, iford(e[2])), fminf(lo->z, iford(e[3])));
-    *hi = make_float3(fmaxf(hi->x, iford(e[4])), fmaxf(hi->y, iford(e[5])), fmaxf(hi->z, iford(e[6])));
   }
 }
 
@@ -431,13 +386,17 @@ struct Acc {
       }
     }
   }
+  // 24 independent butterflies, interleaved so their shuffles pipeline
   __device__ void warp_reduce() {
 #pragma unroll
-    for (int k = 0; k < 24; ++k) {
-      bool is_min = (k % 12) < 3 || ((k % 12) >= 6 && (k % 12) < 9);
-      for (int o = 16; o > 0; o >>= 1) {
-        float y = __shfl_xor_sync(0xffffffffu, v[k], o);
-        v[k] = is_min ? fminf(v[k], y) : fmaxf(v[k], y);
+    for (int o = 16; o > 0; o >>= 1) {
+      float y[24];
+#pragma unroll
+      for (int k = 0; k < 24; ++k) y[k] = __shfl_xor_sync(0xffffffffu, v[k], o);
+#pragma unroll
+      for (int k = 0; k < 24; ++k) {
+        const bool is_min = (k % 12) < 3 || ((k % 12) >= 6 && (k % 12) < 9);
+        v[k] = is_min ? fminf(v[k], y[k]) : fmaxf(v[k], y[k]);
       }
     }
   }
@@ -451,8 +410,8 @@ __device__ __forceinline__ bool goes_left(float4 lo, float4 hi, const SplitResul
 }
 
 struct BuildArgs {
-  float4* rec;       // [2T] primitive records in build order: (lo.xyz, id) (hi.xyz, 0)
-  float4* rec_tmp;   // [2T] partition scratch
+  float4* rec[2];    // [2T] each: primitive records (lo.xyz, id) (hi.xyz, 0); a task's
+                     // range lives in rec[task.pad], its children go to the other one
   Node2* node2;
   BuildCtl* ctl;
   Task* qa;
@@ -539,32 +498,71 @@ __device__ void push_b(const BuildArgs& A, const Task& c) {
   A.qb[s] = c;
 }
 
-// Best candidate of a bin set: (cost, candidate) minimum over the calling
-// threads' share, reduced within the warp (ties: lowest candidate index, i.e.
-// lowest axis, then lowest plane).
-__device__ __forceinline__ void warp_best(const int* bins, int K, int n, const float scl[3],
-                                          const CostP& cp, float3 nlo, float3 nhi, int first,
-                                          int stride, float* best, int* bestc) {
+// The K-1 planes of axis `a` evaluated by one warp.  Lane 0 accumulates the
+// prefix unions of the bins and lane 1 the suffix unions into `scan` (shared,
+// 2 x K entries of 7 floats); then lane p evaluates plane p from prefix p-1
+// and suffix p.  Every lane gets the best (cost, candidate, left count);
+// candidate = a * (K - 1) + plane - 1.  The full prefix is the node box
+// (every triangle sits in exactly one bin of an active axis).
+__device__ __forceinline__ void warp_axis_best(const int* bins, int K, int n, int a, const CostP& cp,
+                                               float* scan, float* best, int* bestc, int* bestnl) {
+  const int lane = threadIdx.x & 31;
+  if (lane < 2) {
+    const bool fwd = lane == 0;
+    float c = 0.f, l0 = FLT_MAX, l1 = FLT_MAX, l2 = FLT_MAX, h0 = -FLT_MAX, h1 = -FLT_MAX, h2 = -FLT_MAX;
+    for (int i = 0; i < K; ++i) {
+      const int b = fwd ? i : K - 1 - i;
+      const int* e = bins + (a * K + b) * kBinEnt;
+      const int cnt = e[0];
+      if (cnt) {
+        c += (float)cnt;
+        l0 = fminf(l0, iford(e[1]));
+        l1 = fminf(l1, iford(e[2]));
+        l2 = fminf(l2, iford(e[3]));
+        h0 = fmaxf(h0, iford(e[4]));
+        h1 = fmaxf(h1, iford(e[5]));
+        h2 = fmaxf(h2, iford(e[6]));
+      }
+      float* o = scan + ((fwd ? 0 : K) + b) * 7;
+      o[0] = c;
+      o[1] = l0;
+      o[2] = l1;
+      o[3] = l2;
+      o[4] = h0;
+      o[5] = h1;
+      o[6] = h2;
+    }
+  }
+  __syncwarp();
   *best = INFINITY;
   *bestc = INT_MAX;
-  for (int c = first; c < 3 * (K - 1); c += stride) {
-    float v = eval_candidate(bins, K, c, n, scl, cp, nlo, nhi);
-    if (v < *best) {
-      *best = v;
-      *bestc = c;
+  *bestnl = 0;
+  if (lane >= 1 && lane < K) {
+    const float* L = scan + (lane - 1) * 7;  // bins 0..lane-1
+    const float* R = scan + (K + lane) * 7;  // bins lane..K-1
+    const float* N = scan + (K - 1) * 7;     // all bins: the node box
+    const int lc = (int)L[0];
+    if (lc > 0 && lc < n) {
+      *best = eq2_cost(make_float3(L[1], L[2], L[3]), make_float3(L[4], L[5], L[6]), lc,
+                       make_float3(R[1], R[2], R[3]), make_float3(R[4], R[5], R[6]), n - lc,
+                       make_float3(N[1], N[2], N[3]), make_float3(N[4], N[5], N[6]), cp);
+      *bestc = a * (K - 1) + lane - 1;
+      *bestnl = lc;
     }
   }
   for (int o = 16; o > 0; o >>= 1) {
-    float ov = __shfl_xor_sync(0xffffffffu, *best, o);
-    int oc = __shfl_xor_sync(0xffffffffu, *bestc, o);
+    const float ov = __shfl_xor_sync(0xffffffffu, *best, o);
+    const int oc = __shfl_xor_sync(0xffffffffu, *bestc, o);
+    const int on = __shfl_xor_sync(0xffffffffu, *bestnl, o);
     if (ov < *best || (ov == *best && oc < *bestc)) {
       *best = ov;
       *bestc = oc;
+      *bestnl = on;
     }
   }
 }
 
-__device__ __forceinline__ SplitResult make_split(const int* bins, int K, int n, float best, int bestc) {
+__device__ __forceinline__ SplitResult make_split(int K, int n, float best, int bestc, int bestnl) {
   SplitResult sr;
   if (bestc == INT_MAX || !(best < INFINITY)) {
     sr.axis = -1;  // no usable plane: split the range in the middle
@@ -573,43 +571,263 @@ __device__ __forceinline__ SplitResult make_split(const int* bins, int K, int n,
   } else {
     sr.axis = bestc / (K - 1);
     sr.plane = 1 + bestc % (K - 1);
-    sr.nl = left_count(bins, K, sr.axis, sr.plane);
+    sr.nl = bestnl;
   }
   return sr;
 }
 
-// ------------------------------------------------------------------ tier A
-// One CTA per node of more than kTierASmall triangles.  Records are read
-// coalesced, kUnrollA per thread in flight.
+// ------------------------------------------------------------------ micro subtrees
+// A node of at most 32 * E triangles (E = 1, 2 or 4) is finished by one warp
+// in registers: lane j holds records E*j .. E*j + E-1 of the node's range (in
+// the order the stable partitions kept, i.e. Morton order within the node).
+// Every split of the subtree is the minimum of Eq. 2 over all splits of that
+// order, evaluated from lane-local prefix/suffix unions of the records' boxes
+// and one warp scan of the lane totals; ranges never move, so there is no
+// partition step.
+struct Box6 {
+  float l0, l1, l2, h0, h1, h2;
+};
+__device__ __forceinline__ Box6 box_empty() { return {FLT_MAX, FLT_MAX, FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX}; }
+__device__ __forceinline__ Box6 box_join(const Box6& a, const Box6& b) {
+  return {fminf(a.l0, b.l0), fminf(a.l1, b.l1), fminf(a.l2, b.l2),
+          fmaxf(a.h0, b.h0), fmaxf(a.h1, b.h1), fmaxf(a.h2, b.h2)};
+}
+__device__ __forceinline__ Box6 box_shfl_up(const Box6& a, int o) {
+  return {__shfl_up_sync(0xffffffffu, a.l0, o), __shfl_up_sync(0xffffffffu, a.l1, o),
+          __shfl_up_sync(0xffffffffu, a.l2, o), __shfl_up_sync(0xffffffffu, a.h0, o),
+          __shfl_up_sync(0xffffffffu, a.h1, o), __shfl_up_sync(0xffffffffu, a.h2, o)};
+}
+__device__ __forceinline__ Box6 box_shfl_down(const Box6& a, int o) {
+  return {__shfl_down_sync(0xffffffffu, a.l0, o), __shfl_down_sync(0xffffffffu, a.l1, o),
+          __shfl_down_sync(0xffffffffu, a.l2, o), __shfl_down_sync(0xffffffffu, a.h0, o),
+          __shfl_down_sync(0xffffffffu, a.h1, o), __shfl_down_sync(0xffffffffu, a.h2, o)};
+}
+__device__ __forceinline__ Box6 box_shfl(const Box6& a, int src) {
+  return {__shfl_sync(0xffffffffu, a.l0, src), __shfl_sync(0xffffffffu, a.l1, src),
+          __shfl_sync(0xffffffffu, a.l2, src), __shfl_sync(0xffffffffu, a.h0, src),
+          __shfl_sync(0xffffffffu, a.h1, src), __shfl_sync(0xffffffffu, a.h2, src)};
+}
+
+template <int E>
+__device__ void micro_build(const BuildArgs& A, const float4 (&rlo)[E], const float4 (&rhi)[E], int n,
+                            int gbase, int parent, int side, int depth) {
+  const int lane = threadIdx.x & 31;
+  // uniform stack of pending ranges: (b, e, parent, side | depth << 1); the
+  // larger child is stacked, so at most log2(32 E) + 1 entries
+  int4 st[10];
+  int sp = 0;
+  st[sp++] = make_int4(0, n, parent, side | (depth << 1));
+  int n_int = 0, n_leaf = 0, big = 0, deep = 0;
+  while (sp > 0) {
+    const int4 tk = st[--sp];
+    const int b = tk.x, e = tk.y, par = tk.z, sd = tk.w & 1, dep = tk.w >> 1;
+    // lane-local inclusive prefix / suffix of the in-range records
+    Box6 pre[E], suf[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      const int q = E * lane + i;
+      const bool in = q >= b && q < e;
+      Box6 x = in ? Box6{rlo[i].x, rlo[i].y, rlo[i].z, rhi[i].x, rhi[i].y, rhi[i].z} : box_empty();
+      pre[i] = i ? box_join(pre[i - 1], x) : x;
+    }
+#pragma unroll
+    for (int i = E - 1; i >= 0; --i) {
+      const int q = E * lane + i;
+      const bool in = q >= b && q < e;
+      Box6 x = in ? Box6{rlo[i].x, rlo[i].y, rlo[i].z, rhi[i].x, rhi[i].y, rhi[i].z} : box_empty();
+      suf[i] = i < E - 1 ? box_join(suf[i + 1], x) : x;
+    }
+    // warp scans of the lane totals: inclusive prefix / suffix, then exclusive
+    Box6 ip = pre[E - 1], is = suf[0];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const Box6 u = box_shfl_up(ip, o), d = box_shfl_down(is, o);
+      if (lane >= o) ip = box_join(ip, u);
+      if (lane + o < 32) is = box_join(is, d);
+    }
+    Box6 xp = box_shfl_up(ip, 1), xs = box_shfl_down(is, 1);
+    if (lane == 0) xp = box_empty();
+    if (lane == 31) xs = box_empty();
+    const Box6 node = box_shfl(ip, 31);
+    const float3 clo = make_float3(node.l0, node.l1, node.l2), chi = make_float3(node.h0, node.h1, node.h2);
+    // candidate: last left record q (b <= q < e - 1)
+    float best = INFINITY;
+    int bq = 1 << 20;
+    Box6 bl = box_empty(), br = box_empty();
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      const int q = E * lane + i;
+      if (q >= b && q + 1 < e) {
+        const Box6 L = box_join(xp, pre[i]);
+        const Box6 R = box_join(xs, i + 1 < E ? suf[i + 1 < E ? i + 1 : i] : box_empty());
+        const float c = eq2_cost(make_float3(L.l0, L.l1, L.l2), make_float3(L.h0, L.h1, L.h2), q - b + 1,
+                                 make_float3(R.l0, R.l1, R.l2), make_float3(R.h0, R.h1, R.h2), e - q - 1,
+                                 clo, chi, A.cp);
+        if (c < best) {  // increasing q within the lane: strict < keeps the lowest
+          best = c;
+          bq = q;
+          bl = L;
+          br = R;
+        }
+      }
+    }
+    float wb = best;
+    int wq = bq;
+    for (int o = 16; o > 0; o >>= 1) {
+      const float oc = __shfl_xor_sync(0xffffffffu, wb, o);
+      const int oq = __shfl_xor_sync(0xffffffffu, wq, o);
+      if (oc < wb || (oc == wb && oq < wq)) {
+        wb = oc;
+        wq = oq;
+      }
+    }
+    const int q = wq < (1 << 20) ? wq : (b + e) / 2 - 1;  // all costs non-finite: middle
+    const int j = q + 1;                                  // first record of the right child
+    const int id = gbase + q;
+    const int nl = j - b, nr = e - j;
+    const int rl = nl <= A.max_leaf ? leaf_ref(gbase + b, nl) : INT_MAX;
+    const int rr = nr <= A.max_leaf ? leaf_ref(gbase + j, nr) : INT_MAX;
+    const bool writer = wq < (1 << 20) ? (bq == wq) : (lane == 0);
+    if (writer) {
+      Box6 L = bl, R = br;
+      if (!(wq < (1 << 20))) {  // middle split: boxes recomputed by lane 0 below
+        L = box_empty();
+        R = box_empty();
+      }
+      Node2 nd;
+      nd.a_lo = make_float4(L.l0, L.l1, L.l2, __int_as_float(rl));
+      nd.a_hi = make_float4(L.h0, L.h1, L.h2, __int_as_float(nl));
+      nd.b_lo = make_float4(R.l0, R.l1, R.l2, __int_as_float(rr));
+      nd.b_hi = make_float4(R.h0, R.h1, R.h2, __int_as_float(nr));
+      A.node2[id] = nd;
+      if (par < 0)
+        A.ctl->root_ref = id;
+      else
+        *(sd == 0 ? &A.node2[par].a_lo.w : &A.node2[par].b_lo.w) = __int_as_float(id);
+    }
+    if (!(wq < (1 << 20))) {
+      // degenerate (non-finite costs): compute the two child boxes by reduction
+      Box6 L = box_empty(), R = box_empty();
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        const int qq = E * lane + i;
+        Box6 x = Box6{rlo[i].x, rlo[i].y, rlo[i].z, rhi[i].x, rhi[i].y, rhi[i].z};
+        if (qq >= b && qq < j) L = box_join(L, x);
+        if (qq >= j && qq < e) R = box_join(R, x);
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        L = box_join(L, Box6{__shfl_xor_sync(0xffffffffu, L.l0, o), __shfl_xor_sync(0xffffffffu, L.l1, o),
+                             __shfl_xor_sync(0xffffffffu, L.l2, o), __shfl_xor_sync(0xffffffffu, L.h0, o),
+                             __shfl_xor_sync(0xffffffffu, L.h1, o), __shfl_xor_sync(0xffffffffu, L.h2, o)});
+        R = box_join(R, Box6{__shfl_xor_sync(0xffffffffu, R.l0, o), __shfl_xor_sync(0xffffffffu, R.l1, o),
+                             __shfl_xor_sync(0xffffffffu, R.l2, o), __shfl_xor_sync(0xffffffffu, R.h0, o),
+                             __shfl_xor_sync(0xffffffffu, R.h1, o), __shfl_xor_sync(0xffffffffu, R.h2, o)});
+      }
+      if (lane == 0) {
+        A.node2[id].a_lo = make_float4(L.l0, L.l1, L.l2, __int_as_float(rl));
+        A.node2[id].a_hi = make_float4(L.h0, L.h1, L.h2, __int_as_float(nl));
+        A.node2[id].b_lo = make_float4(R.l0, R.l1, R.l2, __int_as_float(rr));
+        A.node2[id].b_hi = make_float4(R.h0, R.h1, R.h2, __int_as_float(nr));
+      }
+    }
+    ++n_int;
+    deep = max(deep, dep);
+    if (rl != INT_MAX) {
+      ++n_leaf;
+      big = max(big, nl);
+      deep = max(deep, dep + 1);
+    }
+    if (rr != INT_MAX) {
+      ++n_leaf;
+      big = max(big, nr);
+      deep = max(deep, dep + 1);
+    }
+    // stack the larger internal child first so the smaller is taken next
+    const int4 cl = make_int4(b, j, id, 0 | ((dep + 1) << 1));
+    const int4 cr = make_int4(j, e, id, 1 | ((dep + 1) << 1));
+    const bool il = rl == INT_MAX, ir = rr == INT_MAX;
+    if (il && ir) {
+      if (nl >= nr) {
+        st[sp++] = cl;
+        st[sp++] = cr;
+      } else {
+        st[sp++] = cr;
+        st[sp++] = cl;
+      }
+    } else if (il) {
+      st[sp++] = cl;
+    } else if (ir) {
+      st[sp++] = cr;
+    }
+  }
+  if (lane == 0) {
+    atomicAdd(&A.ctl->n_internal, n_int);
+    atomicAdd(&A.ctl->n_leaves, n_leaf);
+    atomicMax(&A.ctl->max_leaf_size, big);
+    atomicMax(&A.ctl->depth2, deep);
+  }
+}
+
+// ------------------------------------------------------------------ node kernel
+// Every node of more than kMicro triangles is split by one CTA (Fig. 2, one
+// recursion step): bin the AABB centres of its triangles into `bins` slabs
+// per axis (warp-private bins, each lane on its own sub-chunk of its warp's
+// segment, so neighbouring triangles -- which share bins -- do not contend),
+// evaluate Eq. 2 at every bin plane with one warp per axis, then partition
+// the range stably into the other record buffer (count pass, scan over the
+// warps, scatter pass).  Nodes of at most kStage triangles are first staged
+// in shared memory.  A CTA keeps the larger child as its next task and hands
+// the other to the device queue; children of at most kMicro triangles go to
+// the micro list.
+constexpr int kNodeBlock = 256;
+constexpr int kNodeWarps = kNodeBlock / 32;
+constexpr int kStage = 2048;
 constexpr int kUnrollA = 4;
 
-__global__ void __launch_bounds__(kTierABlock) k_tier_a(BuildArgs A) {
-  __shared__ int wbins[kTierAWarps][kBinStride];
-  __shared__ int bins[kBinStride];
-  __shared__ Task task;
-  __shared__ int s_slot;
-  __shared__ float s_cost[kTierAWarps];
-  __shared__ int s_cand[kTierAWarps];
-  __shared__ SplitResult s_sr;
-  __shared__ int s_wcount[kTierAWarps];
-  __shared__ float s_acc[kTierAWarps][24];
-  __shared__ float s_fin[24];
+struct NodeSmem {
+  float4 rec[2 * kStage];
+  int wbins[kNodeWarps][kBinStride];
+  int bins[kBinStride];
+  float scan[3][2 * kMaxBins * 7];
+  Task task, cont;
+  SplitResult sr;
+  float ax_cost[3];
+  int ax_c[3], ax_nl[3];
+  int wleft[kNodeWarps];
+  float acc[kNodeWarps][24];
+  float fin[24];
+  int have, have_cont;
+};
+
+__device__ __forceinline__ float4 ld_rec(bool staged, const float4* srec, const float4* grec, int k) {
+  return staged ? srec[k] : __ldcg(grec + k);
+}
+
+__global__ void __launch_bounds__(kNodeBlock) k_nodes(BuildArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  NodeSmem& S = *reinterpret_cast<NodeSmem*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int K = A.K;
+  if (tid == 0) S.have_cont = 0;
+  __syncthreads();
   for (;;) {
     if (tid == 0) {
-      int slot = -1;
-      if (A.ctl->status == 0) {
-        int s = atomicAdd(&A.ctl->qa_head, 1);
+      S.have = 0;
+      if (S.have_cont) {
+        S.task = S.cont;
+        S.have_cont = 0;
+        S.have = 1;
+      } else if (A.ctl->status == 0) {
+        const int s = atomicAdd(&A.ctl->qa_head, 1);
         int seen = -1;
         for (int it = 0;; ++it) {
           if (s < A.ctl->qa_cap && *(volatile int*)&A.qa_ready[s]) {
             __threadfence();
-            slot = s;
+            S.task = load_task_cg(&A.qa[s]);
+            S.have = 1;
             break;
           }
-          const int pend = *(volatile int*)&A.ctl->qa_pending;
-          if (pend == 0 || *(volatile int*)&A.ctl->status != 0) break;
+          if (*(volatile int*)&A.ctl->qa_pending == 0 || *(volatile int*)&A.ctl->status != 0) break;
           const int tail = *(volatile int*)&A.ctl->qa_tail;
           if (tail != seen) {  // the queue moved: restart the no-progress budget
             seen = tail;
@@ -622,127 +840,187 @@ __global__ void __launch_bounds__(kTierABlock) k_tier_a(BuildArgs A) {
           __nanosleep(128);
         }
       }
-      s_slot = slot;
-      if (slot >= 0) task = load_task_cg(&A.qa[slot]);
     }
     __syncthreads();
-    if (s_slot < 0) return;
-    const Task t = task;
-    // records of this range were written by other CTAs of this kernel: every
-    // read below goes through L2 (ld.global.cg), never a stale L1 line
-    const float4* rec = A.rec + 2 * (size_t)t.begin;
-    float4* tmp = A.rec_tmp + 2 * (size_t)t.begin;
+    if (!S.have) return;
+    const Task t = S.task;
+    const int par = t.pad & 1;
+    // records of this range were written by other CTAs of this kernel: global
+    // reads go through L2 (ld.global.cg), never a stale L1 line
+    const float4* grec = A.rec[par] + 2 * (size_t)t.begin;
+    float4* dst = A.rec[par ^ 1] + 2 * (size_t)t.begin;
+    const bool staged = t.count <= kStage;
+    if (staged)
+      for (int k0 = tid; k0 < 2 * t.count; k0 += 4 * kNodeBlock) {
+        float4 v[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (k0 + j * kNodeBlock < 2 * t.count) v[j] = __ldcg(grec + k0 + j * kNodeBlock);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (k0 + j * kNodeBlock < 2 * t.count) S.rec[k0 + j * kNodeBlock] = v[j];
+      }
+    const int seg = (t.count + kNodeWarps - 1) / kNodeWarps;
+    const int sb = min(warp * seg, t.count), se = min(sb + seg, t.count);
     float cmin[3], scl[3];
     for (int a = 0; a < 3; ++a) {
       cmin[a] = t.clo[a];
       scl[a] = bin_scale(t.clo[a], t.chi[a], K);
     }
-    // 1. bin (warp-private bins, then merge)
-    bins_zero(&wbins[0][0], K, kTierAWarps, tid, kTierABlock);
+    // 1. bin
+    bins_zero(&S.wbins[0][0], K, kNodeWarps, tid, kNodeBlock);
     __syncthreads();
-    for (int k0 = 0; k0 < t.count; k0 += kUnrollA * kTierABlock) {
+    {
+      const int c = (se - sb + 31) >> 5;
+      const int lb = sb + lane * c, le = min(lb + c, se);
+      for (int k0 = lb; k0 < le; k0 += kUnrollA) {
+        float4 lo[kUnrollA], hi[kUnrollA];
+#pragma unroll
+        for (int j = 0; j < kUnrollA; ++j)
+          if (k0 + j < le) {
+            lo[j] = ld_rec(staged, S.rec, grec, 2 * (k0 + j));
+            hi[j] = ld_rec(staged, S.rec, grec, 2 * (k0 + j) + 1);
+          }
+#pragma unroll
+        for (int j = 0; j < kUnrollA; ++j)
+          if (k0 + j < le) bins_add(S.wbins[warp], K, cmin, scl, lo[j], hi[j]);
+      }
+    }
+    __syncthreads();
+    for (int q = tid; q < 3 * K * 7; q += kNodeBlock) {
+      const int ent = q / 7, f = q - ent * 7;
+      const int e = ent * kBinEnt + f;
+      int v = S.wbins[0][e];
+      for (int w = 1; w < kNodeWarps; ++w) {
+        const int x = S.wbins[w][e];
+        v = f == 0 ? v + x : (f <= 3 ? min(v, x) : max(v, x));
+      }
+      S.bins[e] = v;
+    }
+    __syncthreads();
+    // 2. Eq. 2 at every plane, one warp per axis
+    if (warp < 3) {
+      float best = INFINITY;
+      int bestc = INT_MAX, bestnl = 0;
+      if (scl[warp] > 0.f) warp_axis_best(S.bins, K, t.count, warp, A.cp, S.scan[warp], &best, &bestc, &bestnl);
+      if (lane == 0) {
+        S.ax_cost[warp] = best;
+        S.ax_c[warp] = bestc;
+        S.ax_nl[warp] = bestnl;
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      float best = INFINITY;
+      int bestc = INT_MAX, bestnl = 0;
+      for (int a = 0; a < 3; ++a)
+        if (S.ax_cost[a] < best || (S.ax_cost[a] == best && S.ax_c[a] < bestc)) {
+          best = S.ax_cost[a];
+          bestc = S.ax_c[a];
+          bestnl = S.ax_nl[a];
+        }
+      S.sr = make_split(K, t.count, best, bestc, bestnl);
+    }
+    __syncthreads();
+    const SplitResult sr = S.sr;
+    // 3. lefts per warp segment (kUnrollA chunks of 32 in flight)
+    int nleft = 0;
+    for (int k0 = sb; k0 < se; k0 += 32 * kUnrollA) {
       float4 lo[kUnrollA], hi[kUnrollA];
 #pragma unroll
       for (int j = 0; j < kUnrollA; ++j) {
-        int k = k0 + j * kTierABlock + tid;
-        if (k < t.count) {
-          lo[j] = __ldcg(rec + 2 * k);
-          hi[j] = __ldcg(rec + 2 * k + 1);
+        const int k = k0 + 32 * j + lane;
+        if (k < se) {
+          lo[j] = ld_rec(staged, S.rec, grec, 2 * k);
+          hi[j] = ld_rec(staged, S.rec, grec, 2 * k + 1);
         }
       }
 #pragma unroll
-      for (int j = 0; j < kUnrollA; ++j)
-        if (k0 + j * kTierABlock + tid < t.count) bins_add(wbins[warp], K, cmin, scl, lo[j], hi[j]);
-    }
-    __syncthreads();
-    for (int e = tid; e < 3 * K * 8; e += kTierABlock) {
-      int f = e & 7;
-      int v = wbins[0][e];
-      for (int w = 1; w < kTierAWarps; ++w) {
-        int x = wbins[w][e];
-        v = f == 0 ? v + x : (f <= 3 ? min(v, x) : (f <= 6 ? max(v, x) : 0));
+      for (int j = 0; j < kUnrollA; ++j) {
+        const int k = k0 + 32 * j + lane;
+        nleft += __popc(__ballot_sync(0xffffffffu, k < se && goes_left(lo[j], hi[j], sr, k, cmin, scl, K)));
       }
-      bins[e] = v;
     }
+    if (lane == 0) S.wleft[warp] = nleft;
     __syncthreads();
-    // 2. Eq. 2 at every plane
-    float3 nlo, nhi;
-    node_box(bins, K, scl, &nlo, &nhi);
-    float best;
-    int bestc;
-    warp_best(bins, K, t.count, scl, A.cp, nlo, nhi, tid, kTierABlock, &best, &bestc);
-    if (lane == 0) {
-      s_cost[warp] = best;
-      s_cand[warp] = bestc;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      for (int w = 1; w < kTierAWarps; ++w)
-        if (s_cost[w] < best || (s_cost[w] == best && s_cand[w] < bestc)) {
-          best = s_cost[w];
-          bestc = s_cand[w];
-        }
-      s_sr = make_split(bins, K, t.count, best, bestc);
-    }
-    __syncthreads();
-    const SplitResult sr = s_sr;
-    // 3. stable partition into tmp, accumulating child bounds
+    int lbase = 0;
+    for (int w = 0; w < warp; ++w) lbase += S.wleft[w];
+    int rbase = sb - lbase;  // rights before this segment
+    // 4. stable scatter into the other buffer, accumulating child bounds
     Acc acc;
     acc.init();
-    int lbase = 0, rbase = 0;
-    for (int t0 = 0; t0 < t.count; t0 += kTierABlock) {
-      int k = t0 + tid;
-      bool valid = k < t.count;
-      float4 lo = valid ? __ldcg(rec + 2 * k) : make_float4(0, 0, 0, 0);
-      float4 hi = valid ? __ldcg(rec + 2 * k + 1) : make_float4(0, 0, 0, 0);
-      bool left = valid && goes_left(lo, hi, sr, k, cmin, scl, K);
-      unsigned m = __ballot_sync(0xffffffffu, left);
-      int rank = __popc(m & ((1u << lane) - 1u));
-      if (lane == 0) s_wcount[warp] = __popc(m);
-      __syncthreads();
-      int woff = 0, tot = 0;
-      for (int w = 0; w < kTierAWarps; ++w) {
-        int c = s_wcount[w];
-        if (w < warp) woff += c;
-        tot += c;
+    for (int k0 = sb; k0 < se; k0 += 32 * kUnrollA) {
+      float4 lo[kUnrollA], hi[kUnrollA];
+#pragma unroll
+      for (int j = 0; j < kUnrollA; ++j) {
+        const int k = k0 + 32 * j + lane;
+        if (k < se) {
+          lo[j] = ld_rec(staged, S.rec, grec, 2 * k);
+          hi[j] = ld_rec(staged, S.rec, grec, 2 * k + 1);
+        }
       }
-      if (valid) {
-        int lpos = woff + rank;  // lefts before k in this tile
-        int dst = left ? lbase + lpos : sr.nl + rbase + (k - t0 - lpos);
-        tmp[2 * dst] = lo;
-        tmp[2 * dst + 1] = hi;
-        acc.add(left ? 0 : 1, lo, hi);
+#pragma unroll
+      for (int j = 0; j < kUnrollA; ++j) {
+        const int c0 = k0 + 32 * j;
+        if (c0 >= se) break;
+        const int k = c0 + lane;
+        const bool valid = k < se;
+        const bool left = valid && goes_left(lo[j], hi[j], sr, k, cmin, scl, K);
+        const unsigned m = __ballot_sync(0xffffffffu, left);
+        const int rank = __popc(m & ((1u << lane) - 1u));
+        if (valid) {
+          const int d = left ? lbase + rank : sr.nl + rbase + (lane - rank);
+          dst[2 * d] = lo[j];
+          dst[2 * d + 1] = hi[j];
+          acc.add(left ? 0 : 1, lo[j], hi[j]);
+        }
+        const int tot = __popc(m);
+        lbase += tot;
+        rbase += min(32, se - c0) - tot;
       }
-      lbase += tot;
-      rbase += min(kTierABlock, t.count - t0) - tot;
-      __syncthreads();
     }
     acc.warp_reduce();
     if (lane == 0)
-      for (int k = 0; k < 24; ++k) s_acc[warp][k] = acc.v[k];
+      for (int k = 0; k < 24; ++k) S.acc[warp][k] = acc.v[k];
     __syncthreads();
     if (tid < 24) {
-      bool is_min = (tid % 12) < 3 || ((tid % 12) >= 6 && (tid % 12) < 9);
-      float v = s_acc[0][tid];
-      for (int w = 1; w < kTierAWarps; ++w) v = is_min ? fminf(v, s_acc[w][tid]) : fmaxf(v, s_acc[w][tid]);
-      s_fin[tid] = v;
+      const bool is_min = (tid % 12) < 3 || ((tid % 12) >= 6 && (tid % 12) < 9);
+      float v = S.acc[0][tid];
+      for (int w = 1; w < kNodeWarps; ++w) v = is_min ? fminf(v, S.acc[w][tid]) : fmaxf(v, S.acc[w][tid]);
+      S.fin[tid] = v;
     }
-    if (tid == 0 && lbase != sr.nl) set_status(A.ctl, kStBadSplit, 1);
-    {
-      float4* __restrict__ dst = A.rec + 2 * (size_t)t.begin;
-      for (int k = tid; k < 2 * t.count; k += kTierABlock) dst[k] = __ldcg(tmp + k);
+    if (warp == kNodeWarps - 1 && lane == 0 && lbase != sr.nl) set_status(A.ctl, kStBadSplit, 1);
+    // leaves keep their records in buffer 0
+    if (par == 0) {
+      const int ln = sr.nl, rn = t.count - sr.nl;
+      if (ln <= A.max_leaf)
+        for (int k = tid; k < 2 * ln; k += kNodeBlock) A.rec[0][2 * (size_t)t.begin + k] = __ldcg(dst + k);
+      if (rn <= A.max_leaf)
+        for (int k = tid; k < 2 * rn; k += kNodeBlock)
+          A.rec[0][2 * ((size_t)t.begin + ln) + k] = __ldcg(dst + 2 * ln + k);
     }
     __syncthreads();
-    // 4. node + children
+    // 5. node + children: the larger big child stays here, the rest is handed out
     if (tid == 0) {
       Task out[2];
       int nout;
-      emit_node(A, t, sr.nl, s_fin, out, &nout);
+      emit_node(A, t, sr.nl, S.fin, out, &nout);
+      int keep = -1;
       for (int i = 0; i < nout; ++i) {
-        if (out[i].count > kTierASmall)
+        out[i].pad = par ^ 1;
+        if (out[i].count > kMicro && (keep < 0 || out[i].count > out[keep].count)) keep = i;
+      }
+      for (int i = 0; i < nout; ++i) {
+        if (i == keep) continue;
+        if (out[i].count > kMicro)
           push_a(A, out[i]);
         else
           push_b(A, out[i]);
+      }
+      if (keep >= 0) {
+        S.cont = out[keep];
+        S.have_cont = 1;
+        atomicAdd(&A.ctl->qa_pending, 1);
       }
       __threadfence();
       atomicSub(&A.ctl->qa_pending, 1);
@@ -751,189 +1029,40 @@ __global__ void __launch_bounds__(kTierABlock) k_tier_a(BuildArgs A) {
   }
 }
 
-// ------------------------------------------------------------------ tier B
-// One CTA per subtree of at most kTierASmall triangles.  The subtree's
-// records are copied to shared memory once; its nodes are then split by the
-// CTA's warps in parallel, each warp taking whole nodes from a shared stack
-// (and a short private stack when the shared one is full).
-constexpr int kTierBShared = 128;  // shared task stack entries
-constexpr int kTierBPriv = 16;     // private entries per warp (>= log2 kTierASmall + 2)
-
-struct TierBSmem {
-  float4 rec[2 * kTierASmall];
-  uint16_t idx[2][kTierASmall];
-  int bins[kTierBWarps][kBinStride];
-  Task shared_stack[kTierBShared];
-  Task priv[kTierBWarps][kTierBPriv];
-  Task cur[kTierBWarps];
-  int sp, pending, lock, pad;
-};
-
-// Critical sections are a few instructions long; the bound only guards
-// against a logic error turning into a hang.
-__device__ __forceinline__ bool smem_lock(int* l) {
-  for (int it = 0; atomicCAS(l, 0, 1) != 0; ++it) {
-    if (it > kSpinLimit) return false;
-    __nanosleep(32);
+// One warp per micro task: the subtree of a node of at most kMicro triangles.
+template <int E>
+__device__ __forceinline__ void micro_task(const BuildArgs& A, const Task& t) {
+  const int lane = threadIdx.x & 31;
+  const int par = t.pad & 1;
+  float4 lo[E], hi[E];
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    const int q = E * lane + i;
+    lo[i] = hi[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (q < t.count) {
+      const float4* g = A.rec[par] + 2 * ((size_t)t.begin + q);
+      lo[i] = g[0];
+      hi[i] = g[1];
+      if (par) {  // the final record order lives in buffer 0
+        A.rec[0][2 * ((size_t)t.begin + q)] = lo[i];
+        A.rec[0][2 * ((size_t)t.begin + q) + 1] = hi[i];
+      }
+    }
   }
-  __threadfence_block();
-  return true;
-}
-__device__ __forceinline__ void smem_unlock(int* l) {
-  __threadfence_block();
-  atomicExch(l, 0);
+  micro_build<E>(A, lo, hi, t.count, t.begin, t.parent, t.side, t.depth);
 }
 
-__global__ void __launch_bounds__(kTierBBlock) k_tier_b(BuildArgs A) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  TierBSmem& S = *reinterpret_cast<TierBSmem*>(smem_raw);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int K = A.K;
-  int* bins = S.bins[warp];
+__global__ void __launch_bounds__(256) k_micro(BuildArgs A) {
+  const int nwarps = gridDim.x * (blockDim.x >> 5);
   const int total = min(*(volatile int*)&A.ctl->qb_count, A.ctl->qb_cap);
-  for (int ti = blockIdx.x; ti < total; ti += gridDim.x) {
-    const Task root = A.qb[ti];
-    const int gb = root.begin, n = root.count;
-    for (int k = tid; k < 2 * n; k += kTierBBlock) S.rec[k] = __ldcg(A.rec + 2 * (size_t)gb + k);
-    for (int k = tid; k < n; k += kTierBBlock) S.idx[0][k] = (uint16_t)k;
-    if (tid == 0) {
-      Task r = root;
-      r.begin = 0;
-      S.shared_stack[0] = r;
-      S.sp = 1;
-      S.pending = 1;
-      S.lock = 0;
-    }
-    __syncthreads();
-    int psp = 0;  // private stack depth (uniform in the warp)
-    for (int spin = 0;;) {
-      // lane 0 alone looks at the shared state; the warp follows its decision
-      int got = 0, done = 0;
-      if (lane == 0) {
-        if (psp > 0) {
-          S.cur[warp] = S.priv[warp][psp - 1];
-          got = 1;
-        } else {
-          if (smem_lock(&S.lock)) {
-            if (S.sp > 0) {
-              S.cur[warp] = S.shared_stack[--S.sp];
-              got = 1;
-            }
-            smem_unlock(&S.lock);
-          } else {
-            set_status(A.ctl, kStQueueTimeout, 4);
-            done = 1;
-          }
-        }
-        if (!got && *(volatile int*)&S.pending == 0) done = 1;
-      }
-      got = __shfl_sync(0xffffffffu, got, 0);
-      done = __shfl_sync(0xffffffffu, done, 0);
-      if (got && psp > 0) --psp;
-      if (!got) {
-        if (done) break;
-        if (++spin > kSpinLimit) {
-          set_status(A.ctl, kStQueueTimeout, 3);
-          break;
-        }
-        __nanosleep(64);
-        continue;
-      }
-      spin = 0;
-      __syncwarp();
-      const Task t = S.cur[warp];
-      float cmin[3], scl[3];
-      for (int a = 0; a < 3; ++a) {
-        cmin[a] = t.clo[a];
-        scl[a] = bin_scale(t.clo[a], t.chi[a], K);
-      }
-      bins_zero(bins, K, 1, lane, 32);
-      __syncwarp();
-      for (int k = lane; k < t.count; k += 32) {
-        const int li = S.idx[0][t.begin + k];
-        bins_add(bins, K, cmin, scl, S.rec[2 * li], S.rec[2 * li + 1]);
-      }
-      __syncwarp();
-      float3 nlo, nhi;
-      node_box(bins, K, scl, &nlo, &nhi);
-      float best;
-      int bestc;
-      warp_best(bins, K, t.count, scl, A.cp, nlo, nhi, lane, 32, &best, &bestc);
-      const SplitResult sr = make_split(bins, K, t.count, best, bestc);
-      Acc acc;
-      acc.init();
-      int lbase = 0, rbase = 0;
-      for (int t0 = 0; t0 < t.count; t0 += 32) {
-        const int k = t0 + lane;
-        const bool valid = k < t.count;
-        const int li = valid ? S.idx[0][t.begin + k] : 0;
-        const float4 lo = S.rec[2 * li], hi = S.rec[2 * li + 1];
-        const bool left = valid && goes_left(lo, hi, sr, k, cmin, scl, K);
-        const unsigned m = __ballot_sync(0xffffffffu, left);
-        const int rank = __popc(m & ((1u << lane) - 1u));
-        if (valid) {
-          const int dst = left ? lbase + rank : sr.nl + rbase + (lane - rank);
-          S.idx[1][t.begin + dst] = (uint16_t)li;
-          acc.add(left ? 0 : 1, lo, hi);
-        }
-        const int tot = __popc(m);
-        lbase += tot;
-        rbase += min(32, t.count - t0) - tot;
-      }
-      acc.warp_reduce();
-      if (lane == 0 && lbase != sr.nl) set_status(A.ctl, kStBadSplit, 2);
-      __syncwarp();
-      for (int k = lane; k < t.count; k += 32) S.idx[0][t.begin + k] = S.idx[1][t.begin + k];
-      __syncwarp();
-      if (lane == 0) {
-        Task g = t;
-        g.begin = gb + t.begin;
-        Task out[2];
-        int nout = 0;
-        emit_node(A, g, sr.nl, acc.v, out, &nout);
-        if (nout) atomicAdd(&S.pending, nout);
-        // larger child to the shared stack (work for idle warps), smaller
-        // child kept by this warp; a full shared stack keeps both here
-        int order[2] = {0, 1};
-        if (nout == 2 && out[0].count < out[1].count) {
-          order[0] = 1;
-          order[1] = 0;
-        }
-        for (int q = 0; q < nout; ++q) {
-          Task c = out[order[q]];
-          c.begin -= gb;
-          bool shared = false;
-          if (q == 0 && nout == 2) {
-            if (smem_lock(&S.lock)) {
-              if (S.sp < kTierBShared) {
-                S.shared_stack[S.sp++] = c;
-                shared = true;
-              }
-              smem_unlock(&S.lock);
-            }
-          }
-          if (!shared) {
-            if (psp < kTierBPriv) {
-              S.priv[warp][psp++] = c;
-            } else {
-              set_status(A.ctl, kStQueueOverflow, 4);
-              atomicSub(&S.pending, 1);
-            }
-          }
-        }
-        __threadfence_block();
-        atomicSub(&S.pending, 1);
-      }
-      psp = __shfl_sync(0xffffffffu, psp, 0);
-      __syncwarp();
-    }
-    __syncthreads();
-    for (int k = tid; k < n; k += kTierBBlock) {
-      const int li = S.idx[0][k];
-      A.rec[2 * ((size_t)gb + k)] = S.rec[2 * li];
-      A.rec[2 * ((size_t)gb + k) + 1] = S.rec[2 * li + 1];
-    }
-    __syncthreads();
+  for (int ti = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); ti < total; ti += nwarps) {
+    const Task t = A.qb[ti];
+    if (t.count <= 32)
+      micro_task<1>(A, t);
+    else if (t.count <= 64)
+      micro_task<2>(A, t);
+    else
+      micro_task<4>(A, t);
   }
 }
 
@@ -956,6 +1085,7 @@ __global__ void k_collapse_init(CollapseArgs C) {
   int r = C.ctl->root_ref;
   C.ctl->n_wide = 1;
   C.ctl->depth_wide = 1;
+  C.ctl->qc_tail = 0;
   if (r < 0) {  // the whole scene is one leaf (or empty)
     WNode w;
     float inf = INFINITY;
@@ -980,11 +1110,12 @@ __global__ void k_collapse_init(CollapseArgs C) {
     C.wide[0] = w;
     return;
   }
-  C.q[0] = make_int4(r, 0, -1, 0 | (1 << 4));
+  if (!link_ok(r, C.n_tri)) {
+    set_status(C.ctl, kStBadSplit, 13);
+    return;
+  }
+  C.q[0] = make_int4(r, 0, -1, 0);  // (binary node, -, parent wide node, slot)
   C.ctl->qc_tail = 1;
-  C.ctl->qc_pending = 1;
-  __threadfence();
-  C.ready[0] = 1;
 }
 
 __device__ __forceinline__ void child_of(const Node2& n, int s, int* ref, float3* lo, float3* hi) {
@@ -994,123 +1125,132 @@ __device__ __forceinline__ void child_of(const Node2& n, int s, int* ref, float3
   *hi = make_float3(h.x, h.y, h.z);
 }
 
-__global__ void __launch_bounds__(kCollapseBlock) k_collapse(CollapseArgs C) {
-  for (;;) {
-    int slot = -1;
-    if (*(volatile int*)&C.ctl->status != 0) return;
-    int s = atomicAdd(&C.ctl->qc_head, 1);
-    int seen = -1;
-    for (int it = 0;; ++it) {
-      if (s < C.cap && *(volatile int*)&C.ready[s]) {
-        __threadfence();
-        slot = s;
-        break;
+// Binary tree -> 4-wide nodes, top-down, one level of the wide tree at a
+// time in a single CTA.  Queue item i becomes wide node i: a wide node opens
+// the internal child of largest surface area until it has 4 children; its
+// internal children are appended to the queue at positions from a block
+// scan, so the layout is breadth-first and the same on every run.
+constexpr int kCollapseThreads = 1024;
+
+__global__ void __launch_bounds__(kCollapseThreads) k_collapse(CollapseArgs C) {
+  __shared__ int s_warp[kCollapseThreads / 32];
+  __shared__ int s_tail;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (C.ctl->qc_tail == 0) return;  // leaf root: done by k_collapse_init
+  int lb = 0, le = 1, depth = 1;
+  if (tid == 0) s_tail = 1;
+  __syncthreads();
+  while (lb < le) {
+    for (int c0 = lb; c0 < le; c0 += kCollapseThreads) {
+      const int i = c0 + tid;
+      const bool valid = i < le;
+      int ref[kWidth];
+      float3 lo[kWidth], hi[kWidth];
+      int m = 0;
+      int4 item = make_int4(0, 0, 0, 0);
+      if (valid) {
+        item = __ldcg(&C.q[i]);
+        Node2 n = C.node2[item.x];
+        child_of(n, 0, &ref[0], &lo[0], &hi[0]);
+        child_of(n, 1, &ref[1], &lo[1], &hi[1]);
+        m = 2;
+        for (int q = 0; q < 2; ++q)
+          if (!link_ok(ref[q], C.n_tri)) {
+            set_status(C.ctl, kStBadSplit, 11);
+            ref[q] = INT_MIN;
+          }
+        while (m < kWidth) {
+          int pick = -1;
+          float best = -1.f;
+          for (int q = 0; q < m; ++q)
+            if (ref[q] >= 0) {
+              const float ar = area(lo[q], hi[q]);
+              if (ar > best) {
+                best = ar;
+                pick = q;
+              }
+            }
+          if (pick < 0) break;
+          Node2 g = C.node2[ref[pick]];
+          child_of(g, 1, &ref[m], &lo[m], &hi[m]);
+          child_of(g, 0, &ref[pick], &lo[pick], &hi[pick]);
+          for (int q : {pick, m})
+            if (!link_ok(ref[q], C.n_tri)) {
+              set_status(C.ctl, kStBadSplit, 12);
+              ref[q] = INT_MIN;
+            }
+          ++m;
+        }
       }
-      if (*(volatile int*)&C.ctl->qc_pending == 0 || *(volatile int*)&C.ctl->status != 0) break;
-      const int tail = *(volatile int*)&C.ctl->qc_tail;
-      if (tail != seen) {
-        seen = tail;
-        it = 0;
+      // positions of this chunk's internal children: block exclusive scan
+      int cnt = 0;
+      for (int q = 0; q < m; ++q) cnt += ref[q] >= 0 ? 1 : 0;
+      int x = cnt;
+      for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
       }
-      if (it > kSpinLimit) {
-        set_status(C.ctl, kStQueueTimeout, 2);
-        break;
+      if (lane == 31) s_warp[warp] = x;
+      __syncthreads();
+      int base = 0, total = 0;
+      for (int w = 0; w < kCollapseThreads / 32; ++w) {
+        const int v = s_warp[w];
+        if (w < warp) base += v;
+        total += v;
       }
-      __nanosleep(256);
-    }
-    if (slot < 0) return;
-    int4 item = __ldcg(&C.q[slot]);
-    const int wid = item.y, depth = item.w >> 4;
-    // greedy expansion: open the internal child with the largest surface area
-    int ref[kWidth];
-    float3 lo[kWidth], hi[kWidth];
-    int m = 2;
-    if (!link_ok(item.x, C.n_tri) || item.x < 0) {
-      set_status(C.ctl, kStBadSplit, 10);
-      ref[0] = ref[1] = INT_MIN;
-      lo[0] = lo[1] = make_float3(INFINITY, INFINITY, INFINITY);
-      hi[0] = hi[1] = make_float3(-INFINITY, -INFINITY, -INFINITY);
-    } else {
-      Node2 n = C.node2[item.x];
-      child_of(n, 0, &ref[0], &lo[0], &hi[0]);
-      child_of(n, 1, &ref[1], &lo[1], &hi[1]);
-    }
-    for (int i = 0; i < 2; ++i)
-      if (!link_ok(ref[i], C.n_tri)) {
-        set_status(C.ctl, kStBadSplit, 11);
-        ref[i] = INT_MIN;
-      }
-    while (m < kWidth) {
-      int pick = -1;
-      float best = -1.f;
-      for (int i = 0; i < m; ++i)
-        if (ref[i] >= 0) {
-          float a = area(lo[i], hi[i]);
-          if (a > best) {
-            best = a;
-            pick = i;
+      const int tail0 = s_tail;
+      int pos = tail0 + base + x - cnt;
+      if (valid) {
+        float lx[4], ly[4], lz[4], hx[4], hy[4], hz[4];
+        int ch[4];
+        for (int q = 0; q < kWidth; ++q) {
+          if (q < m && ref[q] != INT_MIN) {
+            lx[q] = lo[q].x;
+            ly[q] = lo[q].y;
+            lz[q] = lo[q].z;
+            hx[q] = hi[q].x;
+            hy[q] = hi[q].y;
+            hz[q] = hi[q].z;
+            if (ref[q] >= 0) {
+              if (pos >= C.cap) {
+                set_status(C.ctl, kStWideOverflow, 1);
+                ch[q] = INT_MIN;
+                continue;
+              }
+              C.q[pos] = make_int4(ref[q], 0, i, q);
+              ch[q] = pos++;
+            } else {
+              ch[q] = ref[q];
+            }
+          } else {
+            lx[q] = ly[q] = lz[q] = INFINITY;
+            hx[q] = hy[q] = hz[q] = -INFINITY;
+            ch[q] = INT_MIN;
           }
         }
-      if (pick < 0) break;
-      Node2 n = C.node2[ref[pick]];
-      child_of(n, 1, &ref[m], &lo[m], &hi[m]);
-      child_of(n, 0, &ref[pick], &lo[pick], &hi[pick]);
-      for (int i : {pick, m})
-        if (!link_ok(ref[i], C.n_tri)) {
-          set_status(C.ctl, kStBadSplit, 12);
-          ref[i] = INT_MIN;
-        }
-      ++m;
-    }
-    WNode w;
-    float lx[4], ly[4], lz[4], hx[4], hy[4], hz[4];
-    int ch[4];
-    for (int i = 0; i < kWidth; ++i) {
-      if (i < m) {
-        lx[i] = lo[i].x;
-        ly[i] = lo[i].y;
-        lz[i] = lo[i].z;
-        hx[i] = hi[i].x;
-        hy[i] = hi[i].y;
-        hz[i] = hi[i].z;
-        if (ref[i] == INT_MIN) {
-          lx[i] = ly[i] = lz[i] = INFINITY;
-          hx[i] = hy[i] = hz[i] = -INFINITY;
-          ch[i] = INT_MIN;
-        } else if (ref[i] >= 0) {
-          int c = atomicAdd(&C.ctl->n_wide, 1);
-          if (c >= C.cap) {
-            set_status(C.ctl, kStWideOverflow, 1);
-            ch[i] = INT_MIN;
-            continue;
-          }
-          ch[i] = c;
-          int qs = atomicAdd(&C.ctl->qc_tail, 1);
-          atomicAdd(&C.ctl->qc_pending, 1);
-          C.q[qs] = make_int4(ref[i], c, wid, i | ((depth + 1) << 4));
-          __threadfence();
-          atomicExch(&C.ready[qs], 1);
-        } else {
-          ch[i] = ref[i];
-        }
-      } else {
-        lx[i] = ly[i] = lz[i] = INFINITY;
-        hx[i] = hy[i] = hz[i] = -INFINITY;
-        ch[i] = INT_MIN;
+        WNode w;
+        w.lox = make_float4(lx[0], lx[1], lx[2], lx[3]);
+        w.hix = make_float4(hx[0], hx[1], hx[2], hx[3]);
+        w.loy = make_float4(ly[0], ly[1], ly[2], ly[3]);
+        w.hiy = make_float4(hy[0], hy[1], hy[2], hy[3]);
+        w.loz = make_float4(lz[0], lz[1], lz[2], lz[3]);
+        w.hiz = make_float4(hz[0], hz[1], hz[2], hz[3]);
+        w.child = make_int4(ch[0], ch[1], ch[2], ch[3]);
+        w.meta = make_int4(item.z, item.w, 0, 0);
+        C.wide[i] = w;
       }
+      __syncthreads();
+      if (tid == 0) s_tail = tail0 + total;
+      __syncthreads();
     }
-    w.lox = make_float4(lx[0], lx[1], lx[2], lx[3]);
-    w.hix = make_float4(hx[0], hx[1], hx[2], hx[3]);
-    w.loy = make_float4(ly[0], ly[1], ly[2], ly[3]);
-    w.hiy = make_float4(hy[0], hy[1], hy[2], hy[3]);
-    w.loz = make_float4(lz[0], lz[1], lz[2], lz[3]);
-    w.hiz = make_float4(hz[0], hz[1], hz[2], hz[3]);
-    w.child = make_int4(ch[0], ch[1], ch[2], ch[3]);
-    w.meta = make_int4(item.z, item.w & 15, 0, 0);
-    C.wide[wid] = w;
-    atomicMax(&C.ctl->depth_wide, depth);
-    __threadfence();
-    atomicSub(&C.ctl->qc_pending, 1);
+    lb = le;
+    le = min(s_tail, C.cap);
+    if (lb < le) ++depth;
+  }
+  if (tid == 0) {
+    C.ctl->n_wide = le;
+    C.ctl->depth_wide = depth;
+    C.ctl->qc_tail = le;
   }
 }
 
@@ -1136,6 +1276,13 @@ __global__ void k_gather(const float4* __restrict__ tri_in, const float4* __rest
   }
 }
 
+// Elements per radix-sort block: at least one tile, about two blocks per SM.
+int sort_chunk(int n, int nsm) {
+  int c = (n + 2 * nsm - 1) / (2 * nsm);
+  c = (c + kSortBlock - 1) / kSortBlock * kSortBlock;
+  return c < 4 * kSortBlock ? 4 * kSortBlock : c;
+}
+
 int sm_count() {
   static int n = 0;
   if (!n) {
@@ -1159,7 +1306,6 @@ cudaError_t launch_build(rt_scene_s* s, const rt_build_params& p, cudaStream_t s
   int n_launched = 0;
   if ((e = cudaMemsetAsync(s->ctl, 0, sizeof(BuildCtl), st))) return e;
   if ((e = cudaMemsetAsync(s->qa_ready, 0, sizeof(int) * qa_cap, st))) return e;
-  if ((e = cudaMemsetAsync(s->qc_ready, 0, sizeof(int) * qc_cap, st))) return e;
   k_init_ctl<<<1, 32, 0, st>>>(s->ctl, qa_cap, qb_cap, qc_cap);
     ++n_launched;
   if (n > 0) {
@@ -1169,15 +1315,16 @@ cudaError_t launch_build(rt_scene_s* s, const rt_build_params& p, cudaStream_t s
     ++n_launched;
     k_morton<<<g, kPrepBlock, 0, st>>>(s->prim_lo, s->prim_hi, n, s->ctl, s->keys[0], s->idx[0]);
     ++n_launched;
-    const int nb = (n + kSortChunk - 1) / kSortChunk;
+    const int chunk = sort_chunk(n, nsm);
+    const int nb = (n + chunk - 1) / chunk;
     for (int pass = 0; pass < 4; ++pass) {
       int src = pass & 1, dst = src ^ 1;
-      k_sort_hist<<<nb, kSortBlock, 0, st>>>(s->keys[src], n, 8 * pass, s->sort_hist, nb);
+      k_sort_hist<<<nb, kSortBlock, 0, st>>>(s->keys[src], n, 8 * pass, s->sort_hist, nb, chunk);
     ++n_launched;
-      k_sort_scan<<<1, 1024, 0, st>>>(s->sort_hist, 256 * nb);
+      k_sort_scan<<<1, 256, 0, st>>>(s->sort_hist, nb);
     ++n_launched;
       k_sort_scatter<<<nb, kSortBlock, 0, st>>>(s->keys[src], s->idx[src], s->keys[dst], s->idx[dst],
-                                                n, 8 * pass, s->sort_hist, nb);
+                                                n, 8 * pass, s->sort_hist, nb, chunk);
     ++n_launched;
     }
   }
@@ -1190,8 +1337,8 @@ cudaError_t launch_build(rt_scene_s* s, const rt_build_params& p, cudaStream_t s
   k_root<<<1, 32, 0, st>>>(s->ctl, s->qa, s->qa_ready, s->qb, n, p.max_leaf, s->node2);
   ++n_launched;
   BuildArgs A;
-  A.rec = s->rec[0];
-  A.rec_tmp = s->rec[1];
+  A.rec[0] = s->rec[0];
+  A.rec[1] = s->rec[1];
   A.node2 = s->node2;
   A.ctl = s->ctl;
   A.qa = s->qa;
@@ -1200,24 +1347,24 @@ cudaError_t launch_build(rt_scene_s* s, const rt_build_params& p, cudaStream_t s
   A.K = p.bins;
   A.max_leaf = p.max_leaf;
   A.cp = CostP{p.alpha, p.t_i, p.t_trav, p.source[0], p.source[1], p.source[2], p.dist_norm};
-  if (n > kTierASmall) {
-    k_tier_a<<<nsm, kTierABlock, 0, st>>>(A);
+  if (n > kMicro) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_nodes, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(NodeSmem));
+      attr = true;
+    }
+    k_nodes<<<nsm, kNodeBlock, sizeof(NodeSmem), st>>>(A);
     ++n_launched;
   }
   if (n > p.max_leaf) {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_tier_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TierBSmem));
-      attr = true;
-    }
-    k_tier_b<<<nsm * 2, kTierBBlock, sizeof(TierBSmem), st>>>(A);
+    k_micro<<<2 * nsm, 256, 0, st>>>(A);
     ++n_launched;
   }
   CollapseArgs C{s->node2, s->wide, s->ctl, s->qc, s->qc_ready, qc_cap, n};
   k_collapse_init<<<1, 32, 0, st>>>(C);
   ++n_launched;
   if (n > p.max_leaf) {
-    k_collapse<<<nsm * 2, kCollapseBlock, 0, st>>>(C);
+    k_collapse<<<1, kCollapseThreads, 0, st>>>(C);
     ++n_launched;
   }
   if (n > 0) {

@@ -24,7 +24,7 @@ namespace rt {
 constexpr int kMaxLeaf = 15;   // leaf refs pack the count in 4 bits
 constexpr int kMaxBins = 32;
 constexpr int kWidth = 4;
-constexpr int kTierASmall = 2048;   // tasks above this size are split by a whole CTA
+constexpr int kMicro = 32;          // nodes up to this size are finished by one warp
 constexpr int kSpinLimit = 1 << 24; // bounded device waits (iterations of ~200 ns)
 
 // Status codes written to the device status word (BuildCtl::status).
@@ -88,9 +88,11 @@ struct BuildCtl {
 // Per-call trace scratch: counter + queue of flagged ray indices.
 struct TraceScratch {
   int* counter = nullptr;   // [0] flagged count, [1] status
-  int* queue = nullptr;
+  int* queue = nullptr;     // flagged ray indices
+  int* cand = nullptr;      // per queue slot: 1 + kTraceCand ints
   int64_t cap = 0;
 };
+constexpr int kTraceCand = 8;
 
 // Order-preserving float <-> int map for atomicMin/atomicMax on floats.
 __host__ __device__ inline int ford(float f) {

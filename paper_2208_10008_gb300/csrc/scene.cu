@@ -65,9 +65,9 @@ void free_scene_buffers(rt_scene_s* s) {
   void* ptrs[] = {s->tri_in, s->prim_lo, s->prim_hi, s->keys[0], s->keys[1], s->idx[0], s->idx[1],
                   s->rec[0], s->rec[1],
                   s->sort_hist, s->node2, s->wide, s->tri_leaf, s->qa, s->qa_ready, s->qb, s->qc,
-                  s->qc_ready, s->ctl, s->scratch.counter, s->scratch.queue,
-                  s->host_scr[0].counter, s->host_scr[0].queue, s->host_scr[1].counter,
-                  s->host_scr[1].queue, s->stage_rays[0], s->stage_rays[1], s->stage_hits[0],
+                  s->qc_ready, s->ctl, s->scratch.counter, s->scratch.queue, s->scratch.cand,
+                  s->host_scr[0].counter, s->host_scr[0].queue, s->host_scr[0].cand,
+                  s->host_scr[1].counter, s->host_scr[1].queue, s->host_scr[1].cand, s->stage_rays[0], s->stage_rays[1], s->stage_hits[0],
                   s->stage_hits[1]};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -85,7 +85,9 @@ int ensure_capacity(rt_scene_s* s, int64_t n) {
     RT_CUDA(dev_alloc(&s->idx[k], m), "alloc index");
     RT_CUDA(dev_alloc(&s->rec[k], 2 * m), "alloc build records");
   }
-  const int64_t nb = (m + 256 * 32 - 1) / (256 * 32);
+  // radix-sort histograms: 256 counters per block, blocks = ceil(n / chunk) with
+  // chunk >= 256 (the build never uses more than n / 256 + 1 blocks)
+  const int64_t nb = m / 256 + 2;
   RT_CUDA(dev_alloc(&s->sort_hist, 256 * nb), "alloc sort histogram");
   RT_CUDA(dev_alloc(&s->node2, m), "alloc binary nodes");
   RT_CUDA(dev_alloc(&s->wide, m + 1), "alloc wide nodes");
@@ -105,9 +107,12 @@ int ensure_scratch(rt::TraceScratch& scr, int64_t n) {
   if (scr.counter && scr.cap >= n) return RT_OK;
   if (!scr.counter) RT_CUDA(cudaMalloc((void**)&scr.counter, 4 * sizeof(int)), "alloc trace counter");
   if (scr.queue) cudaFree(scr.queue);
+  if (scr.cand) cudaFree(scr.cand);
   scr.queue = nullptr;
+  scr.cand = nullptr;
   int64_t cap = n < 1024 ? 1024 : n;
   RT_CUDA(cudaMalloc((void**)&scr.queue, cap * sizeof(int)), "alloc re-test queue");
+  RT_CUDA(cudaMalloc((void**)&scr.cand, cap * (rt::kTraceCand + 1) * sizeof(int)), "alloc re-test candidates");
   scr.cap = cap;
   return RT_OK;
 }

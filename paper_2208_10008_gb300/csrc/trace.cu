@@ -39,6 +39,7 @@ constexpr int kRetestBlock = 128;
 constexpr float kU = 5.9604645e-08f;   // unit roundoff of float32, 2^-24
 constexpr float kWiden = 1e-6f;        // relative widening of box intervals
 constexpr float kTieRel = 1e-5f;       // relative window of the best-hit checks
+constexpr int kCand = kTraceCand;      // float64 candidates remembered per ray
 
 struct RayPre {
   float ox, oy, oz, tmin, tmax;
@@ -241,7 +242,7 @@ __device__ __forceinline__ void cswap(float& ta, int& ra, float& tb, int& rb) {
   }
 }
 
-__device__ __forceinline__ void enqueue_flag(int* counter, int* queue, int qcap, int i) {
+__device__ __forceinline__ int enqueue_flag(int* counter, int* queue, int qcap, int i) {
   unsigned m = __activemask();
   int lane = threadIdx.x & 31;
   int leader = __ffs(m) - 1;
@@ -249,7 +250,11 @@ __device__ __forceinline__ void enqueue_flag(int* counter, int* queue, int qcap,
   if (lane == leader) base = atomicAdd(counter, __popc(m));
   base = __shfl_sync(m, base, leader);
   int s = base + __popc(m & ((1u << lane) - 1u));
-  if (s < qcap) queue[s] = i;
+  if (s < qcap) {
+    queue[s] = i;
+    return s;
+  }
+  return -1;
 }
 
 struct TraceArgs {
@@ -263,6 +268,7 @@ struct TraceArgs {
   uint32_t* stats;
   int* counter;
   int* queue;
+  int* cand;  // per queue slot: count (-1 = walk the whole tree) + kCand leaf positions
   int qcap;
 };
 
@@ -281,6 +287,32 @@ __global__ void __launch_bounds__(kTraceBlock) k_trace(TraceArgs A) {
   int st_ref[kStack];
   float st_t[kStack];
   int sp = 0;
+  // Triangles whose float64 answer could beat the float32 one: uncertain
+  // ones and every certain hit near the interval, with a lower bound on t.
+  // If the ray is flagged, the float64 pass evaluates exactly these.
+  int cpos[kCand];
+  float clo[kCand];
+  int nc = 0;
+  bool walk_all = false;
+  auto remember = [&](int pos, float lo) {
+    if (nc == kCand) {  // make room: drop entries already beyond the cull bound
+      int w = 0;
+      for (int q = 0; q < kCand; ++q)
+        if (clo[q] <= bound) {
+          cpos[w] = cpos[q];
+          clo[w] = clo[q];
+          ++w;
+        }
+      nc = w;
+    }
+    if (nc < kCand) {
+      cpos[nc] = pos;
+      clo[nc] = lo;
+      ++nc;
+    } else {
+      walk_all = true;
+    }
+  };
   if (r.valid) {
     st_ref[0] = 0;
     st_t[0] = -INFINITY;
@@ -307,6 +339,7 @@ __global__ void __launch_bounds__(kTraceBlock) k_trace(TraceArgs A) {
       int cnt = __popc(m);
       if (sp + cnt > kStack) {  // cannot hold the children: leave it to the float64 pass
         flag = true;
+        walk_all = true;
         break;
       }
       // push farthest first so the nearest is popped next
@@ -327,13 +360,17 @@ __global__ void __launch_bounds__(kTraceBlock) k_trace(TraceArgs A) {
       TriRes h = tri_test(r, va, vb, vc);
       if (h.cls == 0) continue;
       if (h.cls == 2) {
-        if (h.thi >= r.tmin && h.tlo <= bound) flag = true;
+        if (h.thi >= r.tmin && h.tlo <= bound) {
+          flag = true;
+          remember(first + k, h.tlo);
+        }
         continue;
       }
       // certain hit: near an end of the interval the float64 rule decides
-      if (fabsf(h.t - r.tmax) <= h.err + kTieRel * fabsf(r.tmax) ||
-          fabsf(h.t - r.tmin) <= h.err + kTieRel * fabsf(h.t))
-        flag = true;
+      const bool near_end = fabsf(h.t - r.tmax) <= h.err + kTieRel * fabsf(r.tmax) ||
+                            fabsf(h.t - r.tmin) <= h.err + kTieRel * fabsf(h.t);
+      if (near_end) flag = true;
+      if (near_end || (h.t > r.tmin && h.t < r.tmax)) remember(first + k, h.t - h.err);
       if (!(h.t > r.tmin && h.t < r.tmax)) continue;
       if (kAny) {
         if (!(fabsf(h.t - r.tmax) <= h.err + kTieRel * fabsf(r.tmax) ||
@@ -379,7 +416,17 @@ __global__ void __launch_bounds__(kTraceBlock) k_trace(TraceArgs A) {
     A.stats[2 * (size_t)i] = n_nodes;
     A.stats[2 * (size_t)i + 1] = n_tris;
   }
-  if (flag) enqueue_flag(A.counter, A.queue, A.qcap, i);
+  if (flag) {
+    const int slot = enqueue_flag(A.counter, A.queue, A.qcap, i);
+    if (slot >= 0) {
+      int* c = A.cand + (size_t)slot * (kCand + 1);
+      int w = 0;
+      if (!walk_all)
+        for (int q = 0; q < nc; ++q)
+          if (clo[q] <= bound) c[1 + w++] = cpos[q];
+      c[0] = walk_all ? -1 : w;
+    }
+  }
 }
 
 // ---------------------------------------------------------------- float64
@@ -437,12 +484,31 @@ __global__ void __launch_bounds__(kRetestBlock) k_retest64(TraceArgs A) {
     double bt = INFINITY, bu = 0.0, bv = 0.0;
     int bid = -1;
     bool any = false;
+    const int* cl = A.cand + (size_t)j * (kCand + 1);
+    const int ncand = cl[0];
+    for (int q = 0; q < ncand; ++q) {
+      const float4* tp = A.tris + 3 * (size_t)cl[1 + q];
+      const float4 va = tp[0], vb = tp[1], vc = tp[2];
+      const int id = __float_as_int(va.w);
+      if (id == skip) continue;
+      double t, u, v;
+      if (mt64(o, d, D3{va.x, va.y, va.z}, D3{vb.x, vb.y, vb.z}, D3{vc.x, vc.y, vc.z}, &t, &u, &v) &&
+          t > tmin && t < tmax) {
+        any = true;
+        if (t < bt || (t == bt && id < bid)) {
+          bt = t;
+          bid = id;
+          bu = u;
+          bv = v;
+        }
+      }
+    }
     int node = 0, slot = 0;
-    // Stackless walk (parent links) so that any depth works.  Boxes use the
+    // Without a complete candidate list: stackless walk (parent links) so that any depth works.  Boxes use the
     // same widened float32 slab test as k_trace, culled at the float64 best
     // distance rounded up; triangles the float32 bound proves missed are
     // skipped, every other one goes through the float64 rule.
-    while (r.valid) {
+    while (r.valid && ncand < 0) {
       float bf = (float)fmin(bt, tmax);
       bf = bf + fabsf(bf) * 2e-6f;
       float tn[4];
@@ -525,6 +591,7 @@ cudaError_t launch_trace(rt_scene_s* s, const rt_ray* rays, int64_t n, rt_hit* h
     A.stats = stats ? tp->stats_dev : nullptr;
     A.counter = scr.counter;
     A.queue = scr.queue;
+    A.cand = scr.cand;
     A.qcap = (int)scr.cap;
     const int grid = (int)((n + kTraceBlock - 1) / kTraceBlock);
     if (occl) {
