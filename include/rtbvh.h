@@ -189,6 +189,31 @@ int rt_trace_any(rt_scene scene, const rt_ray* rays_dev, int64_t n, uint8_t* occ
 int rt_trace_closest_host(rt_scene scene, const rt_ray* rays_host, int64_t n, rt_hit* hits_host,
                           const rt_trace_params* params, void* stream);
 
+/* Largest batch rt_trace_closest_noalloc accepts. */
+#define RT_NOALLOC_MAX_RAYS 262144
+
+/* Closest hit without any device allocation.  (An addition of this library;
+ * the paper has no counterpart.)  Same arguments and results as
+ * rt_trace_closest, for callers that must not let the library allocate
+ * device memory: a runtime that manages all device memory through its own
+ * pool, or a latency-critical stream where a cudaMalloc (which can
+ * synchronise the device) would stall other work.  The scratch for the
+ * float64 re-test comes from one fixed array compiled into the library
+ * (10 MiB on every GPU that loads it, held until the process exits), not
+ * from the scene.
+ *  - n must not exceed RT_NOALLOC_MAX_RAYS; larger batches return
+ *    RT_EINVAL ("split the batch").
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - Every call shares the one array: calls whose work overlaps on the GPU
+ *    (other streams, other host threads) race with each other.  Issue them
+ *    on one stream or order them with events.
+ *  - The scene's BVH must already be built (building allocates).
+ * Errors: RT_EINVAL, RT_ENOTBUILT, RT_ECUDA. */
+int rt_trace_closest_noalloc(rt_scene scene, const rt_ray* rays_dev, int64_t n, rt_hit* hits_dev,
+                             const rt_trace_params* params, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

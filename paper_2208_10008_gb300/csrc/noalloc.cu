@@ -1,0 +1,79 @@
+// rt_trace_closest_noalloc: closest-hit tracing that never allocates device
+// memory.
+//
+// rt_trace_closest keeps a per-scene scratch area for the rays its float32
+// pass hands to the float64 re-test, and grows it with cudaMalloc the first
+// time a larger batch arrives.  Some callers cannot let a library do that:
+// a serving runtime that owns every byte of device memory through its own
+// pool and budgets it per tenant, or a latency-critical loop where an
+// allocation (which may synchronise the whole device) would stall other
+// streams.  This entry point gives them the same result with the scratch
+// taken from one fixed array compiled into the library instead.
+//
+// The array below is the only scratch this call uses.  It is a file-scope
+// device variable, so every GPU that loads the library holds it (10 MiB)
+// until the process exits.  Host code cannot use the array's name as a
+// device address; its address on each device is looked up with
+// cudaGetSymbolAddress the first time the call runs on that device, with
+// that device current, and cached.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "rt_internal.cuh"
+
+namespace {
+
+constexpr int64_t kMaxRays = RT_NOALLOC_MAX_RAYS;
+// counter block (4 ints, padded to 64) + queue (kMaxRays) + candidate lists
+constexpr int64_t kScratchInts = 64 + kMaxRays + kMaxRays * (rt::kTraceCand + 1);
+
+static __device__ __align__(256) int g_noalloc_scratch[kScratchInts];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+int* g_addr[kMaxDevices] = {nullptr};
+
+}  // namespace
+
+namespace rt {
+int set_error(int code, const char* msg);  // records the message for rt_last_error
+}
+
+extern "C" int rt_trace_closest_noalloc(rt_scene scene, const rt_ray* rays_dev, int64_t n, rt_hit* hits_dev,
+                                        const rt_trace_params* params, void* stream) {
+  if (!scene) return rt::set_error(RT_EINVAL, "scene is NULL");
+  if (n < 0) return rt::set_error(RT_EINVAL, "n out of range");
+  if (n > kMaxRays)
+    return rt::set_error(RT_EINVAL,
+                         "rt_trace_closest_noalloc: n exceeds RT_NOALLOC_MAX_RAYS (262144); split the batch");
+  if (n > 0 && (!rays_dev || !hits_dev)) return rt::set_error(RT_EINVAL, "NULL buffer");
+  if (((uintptr_t)rays_dev & 15) || ((uintptr_t)hits_dev & 15))
+    return rt::set_error(RT_EINVAL, "rays/hits must be 16-byte aligned");
+  if (!scene->built) return rt::set_error(RT_ENOTBUILT, "BVH not built");
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+    return rt::set_error(RT_ECUDA, "cudaGetDevice failed or device index too large");
+  int* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_addr[dev]) {
+      void* p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        return rt::set_error(RT_ECUDA, "cudaGetSymbolAddress of the static scratch failed");
+      }
+      g_addr[dev] = static_cast<int*>(p);
+    }
+    base = g_addr[dev];
+  }
+  rt::TraceScratch scr;
+  scr.counter = base;          // zeroed by launch_trace on the stream
+  scr.queue = base + 64;
+  scr.cand = base + 64 + kMaxRays;
+  scr.cap = kMaxRays;
+  cudaError_t e = rt::launch_trace(scene, rays_dev, n, hits_dev, nullptr, params, scr, (cudaStream_t)stream);
+  if (e != cudaSuccess) return rt::set_error(RT_ECUDA, cudaGetErrorString(e));
+  return RT_OK;
+}

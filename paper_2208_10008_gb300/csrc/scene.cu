@@ -159,6 +159,10 @@ int check_params(const rt_build_params* p) {
 
 }  // namespace
 
+namespace rt {
+int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
+}  // namespace rt
+
 extern "C" {
 
 int rt_version(void) { return 100; }

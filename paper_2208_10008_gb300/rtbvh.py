@@ -33,7 +33,7 @@ ERRORS = {-1: "RT_EINVAL", -2: "RT_ENOMEM", -3: "RT_ENOTBUILT", -4: "RT_ETIMEOUT
 # Every symbol the header declares (checked by the ABI test).
 EXPORTS = ["rt_version", "rt_launch_count", "rt_last_error", "rt_scene_upload", "rt_scene_destroy", "rt_scene_update",
            "rt_bvh_build", "rt_bvh_info", "rt_bvh_export", "rt_trace_closest", "rt_trace_any",
-           "rt_trace_closest_host"]
+           "rt_trace_closest_host", "rt_trace_closest_noalloc"]
 
 
 class RtError(RuntimeError):
@@ -86,6 +86,7 @@ def lib(build: bool = True):
             L.rt_trace_closest.argtypes = [vp, vp, i64, vp, ctypes.POINTER(TraceParams), vp]
             L.rt_trace_any.argtypes = [vp, vp, i64, vp, ctypes.POINTER(TraceParams), vp]
             L.rt_trace_closest_host.argtypes = [vp, vp, i64, vp, ctypes.POINTER(TraceParams), vp]
+            L.rt_trace_closest_noalloc.argtypes = [vp, vp, i64, vp, ctypes.POINTER(TraceParams), vp]
             _lib = L
     return _lib
 
@@ -245,6 +246,21 @@ def rt_trace_closest(scene: Scene, rays, hits=None, skip=None, flags=0, stats=No
     tp = _trace_params(flags, skip, stats, n_flagged, n)
     _check(lib().rt_trace_closest(scene.handle, rp, n, hp, ctypes.byref(tp), _stream(stream)))
     return hits
+
+
+def rt_trace_closest_noalloc(scene: Scene, rays, hits, flags=0, stream=None):
+    """Closest hit without device allocation (n <= RT_NOALLOC_MAX_RAYS); hits is caller-provided."""
+    import torch
+    rp = _dev_ptr(rays, torch.float32, 8, "rays")
+    hp = _dev_ptr(hits, torch.float32, 4, "hits")
+    tp = TraceParams()
+    tp.flags = int(flags)
+    _check(lib().rt_trace_closest_noalloc(scene.handle, rp, rays.shape[0], hp, ctypes.byref(tp),
+                                          _stream(stream)))
+    return hits
+
+
+RT_NOALLOC_MAX_RAYS = 262144
 
 
 def rt_trace_any(scene: Scene, rays, occluded=None, skip=None, flags=0, stats=None, n_flagged=None,
