@@ -189,6 +189,99 @@ int rt_trace_any(rt_scene scene, const rt_ray* rays_dev, int64_t n, uint8_t* occ
 int rt_trace_closest_host(rt_scene scene, const rt_ray* rays_host, int64_t n, rt_hit* hits_host,
                           const rt_trace_params* params, void* stream);
 
+/* Launch direction sets (Sec. III.A). */
+#define RT_RAYS_FIBONACCI 0 /* param = number of rays N: z_i = 1 - (2i+1)/N, azimuth i pi (3 - sqrt 5) */
+#define RT_RAYS_ICOSPHERE 1 /* param = level L: vertices of the icosahedron with every edge cut into
+                               f = 2^L, 10 f^2 + 2 rays; order: 12 corners, edge points, face points */
+
+/* Number of rays of a launch (RT_RAYS_FIBONACCI: param; RT_RAYS_ICOSPHERE:
+ * 10 * 4^param + 2); -1 for an invalid kind or param.  Never touches the GPU. */
+int64_t rt_ray_count(int kind, int64_t param);
+
+/* Fill rays_dev with the launch of Sec. III.A from `origin`: unit
+ * directions (float32, formed with the azimuth reduced exactly in integer
+ * arithmetic for RT_RAYS_FIBONACCI; the planar subdivision point normalised
+ * for RT_RAYS_ICOSPHERE), tmin / tmax as given.  capacity must be at least
+ * rt_ray_count(kind, param).  Icosphere levels 0..12.
+ * Errors: RT_EINVAL, RT_ECUDA. */
+int rt_gen_rays(int kind, const float* origin, int64_t param, float tmin, float tmax, rt_ray* rays_dev,
+                int64_t capacity, void* stream);
+
+/* Specular bounce (Sec. III.B: a ray that meets a facet generates a
+ * reflected ray) with compaction.  For every ray i whose hit has tri >= 0
+ * and remaining range tmax - t > 0, in input order, writes the next ray
+ * (o + t d, 0, d - 2 (d.n) n, tmax - t), n the unit geometric normal
+ * (v1 - v0) x (v2 - v0) of the hit triangle, to out_rays_dev; the hit
+ * triangle to out_skip_dev (pass it as skip_tri_dev when tracing the new
+ * rays: a reflected ray never meets the facet it leaves); i to out_src_dev
+ * (nullable); the number written to *out_count_dev (device int).  Output
+ * arrays hold n entries.  Allocates per-scene scratch on first use of a
+ * larger n.  Errors: RT_EINVAL, RT_ENOMEM, RT_ECUDA. */
+int rt_reflect(rt_scene scene, const rt_ray* rays_dev, const rt_hit* hits_dev, int64_t n,
+               rt_ray* out_rays_dev, int32_t* out_skip_dev, int32_t* out_src_dev,
+               int32_t* out_count_dev, void* stream);
+
+/* ---- batched multi-bounce tracing ------------------------------------ */
+typedef struct rt_batch_s* rt_batch;
+
+#define RT_BATCH_MAX_ORDER 8
+
+/* Many transmitters with uneven ray counts, traced with up to max_order
+ * specular reflections each (Sec. III.B: paths stop at the order limit or
+ * when the ray action range tmax is used up) plus the visibility of every
+ * transmitter-receiver pair (any hit on the segment). */
+typedef struct {
+  int32_t n_tx;
+  const float* tx_pos;     /* host, n_tx * 3 */
+  const int64_t* tx_param; /* host, n_tx: rays per transmitter (RT_RAYS_FIBONACCI) or level */
+  int32_t dir_kind;        /* RT_RAYS_FIBONACCI or RT_RAYS_ICOSPHERE */
+  int32_t max_order;       /* reflections after the direct rays: 0 .. RT_BATCH_MAX_ORDER */
+  float tmax;              /* ray action range: total length of every path */
+  int32_t n_rx;            /* receivers (0: no visibility pass) */
+  const float* rx_pos;     /* host, n_rx * 3 */
+  int32_t use_graph;       /* 1: capture the pipeline in a CUDA graph on the second run, replay after */
+} rt_batch_desc;
+
+typedef struct {
+  int32_t n_orders;                     /* max_order + 1 */
+  int64_t rays[RT_BATCH_MAX_ORDER + 1]; /* rays traced in each order */
+  int64_t segments;                     /* visibility segments (n_tx * n_rx) */
+  int64_t total_rays;                   /* all orders + segments */
+  int64_t visible;                      /* segments with no hit */
+  int32_t flagged;                      /* float64 re-tests of the last trace (diagnostic) */
+} rt_batch_stats;
+
+/* Allocate everything the pipeline needs for these transmitters on `scene`
+ * (whose BVH must be built before rt_batch_run): per order k a ray queue, a
+ * hit array, the skip and parent-index arrays, and the visibility segments
+ * d = rx - tx, t in (0, 1).  Synchronous.  Errors: RT_EINVAL, RT_ENOMEM,
+ * RT_ECUDA. */
+int rt_batch_create(rt_scene scene, const rt_batch_desc* desc, rt_batch* out);
+
+/* Run the whole pipeline ordered after the work already on `stream`:
+ * launch the rays of every transmitter (Sec. III.A) into one queue, trace
+ * closest hits, then max_order times reflect + compact on the device
+ * (rt_reflect) and trace the survivors (counts never leave the device),
+ * then the visibility segments (rt_trace_any).  Work runs on the batch's
+ * own stream; `stream` waits for it.  Results stay valid until the next run
+ * starts.  Errors: RT_EINVAL, RT_ENOTBUILT, RT_ECUDA. */
+int rt_batch_run(rt_batch batch, void* stream);
+
+/* Synchronous: wait for `stream` and the batch, report counts. */
+int rt_batch_stats_get(rt_batch batch, void* stream, rt_batch_stats* stats);
+
+/* Device pointers of order k's rays, hits, parent indices (into order k-1;
+ * NULL for k = 0) and device ray count (NULL for k = 0: every launched ray).
+ * Valid until rt_batch_destroy. */
+int rt_batch_order(rt_batch batch, int order, const rt_ray** rays_dev, const rt_hit** hits_dev,
+                   const int32_t** src_dev, const int32_t** count_dev);
+
+/* Device array [n_tx * n_rx] (transmitter-major): 1 = segment blocked. */
+int rt_batch_visibility(rt_batch batch, const uint8_t** occluded_dev);
+
+/* Free the batch (synchronous). */
+int rt_batch_destroy(rt_batch batch);
+
 /* Largest batch rt_trace_closest_noalloc accepts. */
 #define RT_NOALLOC_MAX_RAYS 262144
 

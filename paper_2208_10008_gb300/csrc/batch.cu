@@ -1,0 +1,276 @@
+// Batched multi-bounce tracing: many transmitters, uneven ray counts,
+// reflection orders, and transmitter-receiver visibility in one device
+// pipeline (Sec. III: launch -> trace -> bounce until the order limit).
+//
+// One rt_batch owns every buffer the pipeline needs (sized at creation from
+// the transmitters' ray counts), so a run allocates nothing and never waits
+// on the host: the count of each reflection order stays on the device and
+// the next trace reads it there.  The first run executes directly; the
+// second captures the whole pipeline into a CUDA graph, which every later
+// run replays with a single launch.
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "rt_internal.cuh"
+
+struct rt_batch_s {
+  rt_scene scene = nullptr;
+  int n_tx = 0, kind = 0, max_order = 0, n_rx = 0;
+  float tmax = 0.f;
+  bool use_graph = true;
+  std::vector<float> tx;
+  std::vector<long long> param, count, offset;
+  long long n0 = 0, n_seg = 0;
+  rt_ray* rays[RT_BATCH_MAX_ORDER + 1] = {};
+  rt_hit* hits[RT_BATCH_MAX_ORDER + 1] = {};
+  int* skip[RT_BATCH_MAX_ORDER + 1] = {};
+  int* src[RT_BATCH_MAX_ORDER + 1] = {};
+  int* counts = nullptr;  // device: rays of order k at counts[k] (k >= 1)
+  int* blocks = nullptr;  // reflect block counts
+  rt_ray* seg = nullptr;  // visibility segments, transmitter-major
+  uint8_t* occl = nullptr;
+  rt::TraceScratch scr;
+  cudaStream_t st = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int runs = 0;
+  long long graph_kernels = 0;  // kernels in the captured graph
+};
+
+namespace rt {
+int set_error(int code, const char* msg);
+}
+
+namespace {
+
+void free_batch(rt_batch_s* b) {
+  for (int k = 0; k <= RT_BATCH_MAX_ORDER; ++k) {
+    if (b->rays[k]) cudaFree(b->rays[k]);
+    if (b->hits[k]) cudaFree(b->hits[k]);
+    if (b->skip[k]) cudaFree(b->skip[k]);
+    if (b->src[k]) cudaFree(b->src[k]);
+  }
+  void* p[] = {b->counts, b->blocks, b->seg, b->occl, b->scr.counter, b->scr.queue, b->scr.cand};
+  for (void* q : p)
+    if (q) cudaFree(q);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->ev_in) cudaEventDestroy(b->ev_in);
+  if (b->ev_out) cudaEventDestroy(b->ev_out);
+  if (b->st) cudaStreamDestroy(b->st);
+}
+
+cudaError_t enqueue(rt_batch_s* b) {
+  cudaError_t e;
+  cudaStream_t st = b->st;
+  for (int t = 0; t < b->n_tx; ++t) {
+    if ((e = rt::launch_gen_rays(b->kind, &b->tx[3 * t], b->param[t], 0.f, b->tmax, b->rays[0] + b->offset[t],
+                                 b->count[t], st)))
+      return e;
+  }
+  rt_trace_params tp{};
+  if ((e = rt::launch_trace_dev(b->scene, b->rays[0], b->n0, nullptr, b->hits[0], nullptr, &tp, b->scr, st)))
+    return e;
+  for (int k = 1; k <= b->max_order; ++k) {
+    const int* prev = k == 1 ? nullptr : b->counts + (k - 1);
+    if ((e = rt::launch_reflect(b->scene, b->rays[k - 1], b->hits[k - 1], b->n0, prev, b->rays[k], b->skip[k],
+                                b->src[k], b->counts + k, b->blocks, b->n0, st)))
+      return e;
+    rt_trace_params tk{};
+    tk.skip_tri_dev = b->skip[k];
+    if ((e = rt::launch_trace_dev(b->scene, b->rays[k], b->n0, b->counts + k, b->hits[k], nullptr, &tk, b->scr,
+                                  st)))
+      return e;
+  }
+  if (b->n_seg > 0) {
+    rt_trace_params tv{};
+    if ((e = rt::launch_trace_dev(b->scene, b->seg, b->n_seg, nullptr, nullptr, b->occl, &tv, b->scr, st)))
+      return e;
+  }
+  return cudaSuccess;
+}
+
+template <class T>
+cudaError_t alloc(T** p, long long n) {
+  return cudaMalloc((void**)p, (size_t)(n < 1 ? 1 : n) * sizeof(T));
+}
+
+}  // namespace
+
+extern "C" {
+
+int rt_batch_create(rt_scene scene, const rt_batch_desc* d, rt_batch* out) {
+  if (!out || !scene || !d) return rt::set_error(RT_EINVAL, "NULL argument");
+  *out = nullptr;
+  if (d->n_tx < 1 || !d->tx_pos || !d->tx_param) return rt::set_error(RT_EINVAL, "need at least one transmitter");
+  if (d->dir_kind != RT_RAYS_FIBONACCI && d->dir_kind != RT_RAYS_ICOSPHERE)
+    return rt::set_error(RT_EINVAL, "bad dir_kind");
+  if (d->max_order < 0 || d->max_order > RT_BATCH_MAX_ORDER) return rt::set_error(RT_EINVAL, "max_order out of range");
+  if (!(d->tmax > 0.f)) return rt::set_error(RT_EINVAL, "tmax must be > 0");
+  if (d->n_rx < 0 || (d->n_rx > 0 && !d->rx_pos)) return rt::set_error(RT_EINVAL, "bad receivers");
+  rt_batch_s* b = new (std::nothrow) rt_batch_s();
+  if (!b) return rt::set_error(RT_ENOMEM, "host allocation failed");
+  b->scene = scene;
+  b->n_tx = d->n_tx;
+  b->kind = d->dir_kind;
+  b->max_order = d->max_order;
+  b->n_rx = d->n_rx;
+  b->tmax = d->tmax;
+  b->use_graph = d->use_graph != 0;
+  b->tx.assign(d->tx_pos, d->tx_pos + 3 * d->n_tx);
+  long long total = 0;
+  for (int t = 0; t < d->n_tx; ++t) {
+    const long long c = rt_ray_count(d->dir_kind, d->tx_param[t]);
+    if (c < 0) {
+      delete b;
+      return rt::set_error(RT_EINVAL, "bad ray count for a transmitter");
+    }
+    b->param.push_back(d->tx_param[t]);
+    b->count.push_back(c);
+    b->offset.push_back(total);
+    total += c;
+  }
+  if (total < 1 || total > INT_MAX) {
+    delete b;
+    return rt::set_error(RT_EINVAL, "total ray count out of range");
+  }
+  b->n0 = total;
+  b->n_seg = (long long)d->n_tx * d->n_rx;
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k <= b->max_order && e == cudaSuccess; ++k) {
+    e = alloc(&b->rays[k], total);
+    if (e == cudaSuccess) e = alloc(&b->hits[k], total);
+    if (e == cudaSuccess && k > 0) e = alloc(&b->skip[k], total);
+    if (e == cudaSuccess && k > 0) e = alloc(&b->src[k], total);
+  }
+  if (e == cudaSuccess) e = alloc(&b->counts, RT_BATCH_MAX_ORDER + 1);
+  if (e == cudaSuccess) e = alloc(&b->blocks, total / 256 + 2);
+  const long long qcap = total > b->n_seg ? total : b->n_seg;
+  if (e == cudaSuccess) e = alloc(&b->scr.counter, 4);
+  if (e == cudaSuccess) e = alloc(&b->scr.queue, qcap);
+  if (e == cudaSuccess) e = alloc(&b->scr.cand, qcap * (rt::kTraceCand + 1));
+  b->scr.cap = qcap;
+  if (e == cudaSuccess && b->n_seg > 0) {
+    e = alloc(&b->seg, b->n_seg);
+    if (e == cudaSuccess) e = alloc(&b->occl, b->n_seg);
+    if (e == cudaSuccess) {
+      std::vector<rt_ray> h((size_t)b->n_seg);
+      for (int t = 0; t < b->n_tx; ++t)
+        for (int r = 0; r < b->n_rx; ++r) {
+          rt_ray& s = h[(size_t)t * b->n_rx + r];
+          const float* a = &b->tx[3 * t];
+          const float* c = d->rx_pos + 3 * r;
+          s = rt_ray{a[0], a[1], a[2], 0.f, c[0] - a[0], c[1] - a[1], c[2] - a[2], 1.f};
+        }
+      e = cudaMemcpy(b->seg, h.data(), h.size() * sizeof(rt_ray), cudaMemcpyHostToDevice);
+    }
+  }
+  if (e == cudaSuccess) e = cudaMemset(b->counts, 0, (RT_BATCH_MAX_ORDER + 1) * sizeof(int));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    free_batch(b);
+    delete b;
+    cudaGetLastError();
+    return rt::set_error(e == cudaErrorMemoryAllocation ? RT_ENOMEM : RT_ECUDA, cudaGetErrorString(e));
+  }
+  *out = b;
+  return RT_OK;
+}
+
+int rt_batch_run(rt_batch b, void* stream) {
+  if (!b) return rt::set_error(RT_EINVAL, "batch is NULL");
+  if (!b->scene->built) return rt::set_error(RT_ENOTBUILT, "BVH not built");
+  cudaError_t e = cudaEventRecord(b->ev_in, (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(b->st, b->ev_in, 0);
+  if (e == cudaSuccess) {
+    if (!b->use_graph || b->runs == 0) {
+      e = enqueue(b);  // the first run also initialises lazily loaded tables
+    } else {
+      if (!b->exec) {
+        e = cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+          const unsigned long long c0 = rt_launch_count();
+          cudaError_t e2 = enqueue(b);
+          b->graph_kernels = (long long)(rt_launch_count() - c0);
+          rt::count_launches(-(int)b->graph_kernels);  // captured, not launched
+          e = cudaStreamEndCapture(b->st, &b->graph);
+          if (e2 != cudaSuccess) e = e2;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+      }
+      if (e == cudaSuccess) {
+        e = cudaGraphLaunch(b->exec, b->st);
+        rt::count_launches((int)b->graph_kernels);
+      }
+    }
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(b->ev_out, b->st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent((cudaStream_t)stream, b->ev_out, 0);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return rt::set_error(RT_ECUDA, cudaGetErrorString(e));
+  }
+  ++b->runs;
+  return RT_OK;
+}
+
+int rt_batch_stats_get(rt_batch b, void* stream, rt_batch_stats* s) {
+  if (!b || !s) return rt::set_error(RT_EINVAL, "NULL argument");
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess || cudaStreamSynchronize(b->st) != cudaSuccess)
+    return rt::set_error(RT_ECUDA, "synchronize");
+  int c[RT_BATCH_MAX_ORDER + 1];
+  if (cudaMemcpy(c, b->counts, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return rt::set_error(RT_ECUDA, "read counts");
+  memset(s, 0, sizeof(*s));
+  s->n_orders = b->max_order + 1;
+  s->rays[0] = b->n0;
+  s->total_rays = b->n0 + b->n_seg;
+  for (int k = 1; k <= b->max_order; ++k) {
+    s->rays[k] = c[k];
+    s->total_rays += c[k];
+  }
+  if (b->n_seg > 0) {
+    std::vector<uint8_t> o((size_t)b->n_seg);
+    if (cudaMemcpy(o.data(), b->occl, o.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return rt::set_error(RT_ECUDA, "read visibility");
+    for (uint8_t v : o) s->visible += v == 0;
+  }
+  int fl = 0;
+  cudaMemcpy(&fl, b->scr.counter, sizeof(int), cudaMemcpyDeviceToHost);
+  s->flagged = fl;
+  s->segments = b->n_seg;
+  return RT_OK;
+}
+
+int rt_batch_order(rt_batch b, int order, const rt_ray** rays, const rt_hit** hits, const int32_t** src,
+                   const int32_t** count) {
+  if (!b || order < 0 || order > b->max_order) return rt::set_error(RT_EINVAL, "bad batch or order");
+  if (rays) *rays = b->rays[order];
+  if (hits) *hits = b->hits[order];
+  if (src) *src = order ? b->src[order] : nullptr;
+  if (count) *count = order ? b->counts + order : nullptr;
+  return RT_OK;
+}
+
+int rt_batch_visibility(rt_batch b, const uint8_t** occluded) {
+  if (!b || !occluded) return rt::set_error(RT_EINVAL, "NULL argument");
+  *occluded = b->occl;
+  return RT_OK;
+}
+
+int rt_batch_destroy(rt_batch b) {
+  if (!b) return rt::set_error(RT_EINVAL, "batch is NULL");
+  cudaStreamSynchronize(b->st);
+  free_batch(b);
+  delete b;
+  return RT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,323 @@
+// Ray launch (Sec. III.A) and specular bounce with compaction (Sec. III.B).
+//
+// k_gen_fibonacci / k_gen_icosphere write rays from a source point towards
+//   Fibonacci-sphere points or the vertices of a subdivided regular
+//   icosahedron (f = 2^level segments per edge, 10 f^2 + 2 directions), in
+//   float32, in the same order as the host generators: the 12 corners, the
+//   points inside each edge, the points inside each face.
+// k_reflect_* turn every hit ray into its specular reflection r = d -
+//   2 (d.n) n about the unit geometric normal of the hit triangle, starting at
+//   the hit point with the remaining range tmax - t and the hit triangle to
+//   be skipped, and compact the survivors into the next order's ray queue in
+//   input order (count per block, scan, scatter: deterministic).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <mutex>
+#include <vector>
+
+#include "rt_internal.cuh"
+
+namespace rt {
+namespace {
+
+constexpr int kRayBlock = 256;
+
+// 0.38196601125010515... = (3 - sqrt 5) / 2 as a 64-bit binary fraction, so
+// that the fractional part of i * g (the azimuth in turns) is exact integer
+// arithmetic for every i.
+constexpr unsigned long long kGoldenFrac = 0x61C8864680B583EAull;
+
+__global__ void k_gen_fibonacci(float ox, float oy, float oz, long long n, float tmin, float tmax,
+                                float4* __restrict__ rays) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    // z = 1 - (2i + 1)/n = (n - 2i - 1)/n and rho = sqrt(1 - z^2) =
+    // sqrt((2i + 1)(2n - 2i - 1)) / n, each from exact integers (no
+    // cancellation near the poles)
+    const double dn = (double)n;
+    const float z = (float)((double)(n - 2 * i - 1) / dn);
+    const float rho = (float)(sqrt((double)(2 * i + 1) * (double)(2 * n - 2 * i - 1)) / dn);
+    // azimuth in turns, i (3 - sqrt 5)/2 mod 1, reduced to [-1/2, 1/2) in
+    // exact integer arithmetic before the one rounding to float
+    const unsigned long long turns = (unsigned long long)i * kGoldenFrac;  // mod 2^64
+    const float a = (float)(int)(unsigned)(turns >> 32) * 2.3283064365386963e-10f;  // 2^-32
+    float s, c;
+    sincospif(2.f * a, &s, &c);
+    rays[2 * i] = make_float4(ox, oy, oz, tmin);
+    rays[2 * i + 1] = make_float4(rho * c, rho * s, z, tmax);
+  }
+}
+
+// Icosahedron tables (vertices, edges, faces) for the device generator.
+struct Ico {
+  float v[12][3];
+  int e[30][2];
+  int f[20][3];
+};
+__constant__ Ico c_ico;
+
+__global__ void k_gen_icosphere(float ox, float oy, float oz, int fseg, long long n, float tmin, float tmax,
+                                float4* __restrict__ rays) {
+  const long long f = fseg;
+  const long long n_edge_pts = 30 * (f - 1);
+  const long long per_face = (f - 1) * (f - 2) / 2;
+  const float inv_f = 1.f / (float)f;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    float p0, p1, p2;
+    if (k < 12) {
+      p0 = c_ico.v[k][0];
+      p1 = c_ico.v[k][1];
+      p2 = c_ico.v[k][2];
+    } else if (k < 12 + n_edge_pts) {
+      const long long r = k - 12;
+      const int e = (int)(r / (f - 1));
+      const long long s = r - (long long)e * (f - 1) + 1;  // 1 .. f-1
+      const float t = (float)s * inv_f;
+      const float* a = c_ico.v[c_ico.e[e][0]];
+      const float* b = c_ico.v[c_ico.e[e][1]];
+      p0 = a[0] * (1.f - t) + b[0] * t;
+      p1 = a[1] * (1.f - t) + b[1] * t;
+      p2 = a[2] * (1.f - t) + b[2] * t;
+    } else {
+      const long long r = k - 12 - n_edge_pts;
+      const int fc = (int)(r / per_face);
+      long long q = r - (long long)fc * per_face;
+      // row i (1 .. f-2) holds f-1-i points; rows start at (i-1)(f-1) - (i-1)i/2
+      const double ff = (double)(f - 1);
+      long long i = 1 + (long long)floor(ff - 0.5 - sqrt(fmax(0.0, (ff - 0.5) * (ff - 0.5) - 2.0 * (double)q)));
+      if (i < 1) i = 1;
+      auto row_start = [&](long long ii) { return (ii - 1) * (f - 1) - (ii - 1) * ii / 2; };
+      while (i > 1 && row_start(i) > q) --i;
+      while (row_start(i + 1) <= q) ++i;
+      const long long j = q - row_start(i) + 1;
+      const float wi = (float)i * inv_f, wj = (float)j * inv_f, w0 = 1.f - wi - wj;
+      const float* a = c_ico.v[c_ico.f[fc][0]];
+      const float* b = c_ico.v[c_ico.f[fc][1]];
+      const float* c = c_ico.v[c_ico.f[fc][2]];
+      p0 = a[0] * w0 + b[0] * wi + c[0] * wj;
+      p1 = a[1] * w0 + b[1] * wi + c[1] * wj;
+      p2 = a[2] * w0 + b[2] * wi + c[2] * wj;
+    }
+    const float il = rsqrtf(p0 * p0 + p1 * p1 + p2 * p2);
+    rays[2 * k] = make_float4(ox, oy, oz, tmin);
+    rays[2 * k + 1] = make_float4(p0 * il, p1 * il, p2 * il, tmax);
+  }
+}
+
+// ------------------------------------------------------------------ bounce
+struct ReflectArgs {
+  const float4* rays;
+  const float4* hits;
+  const int* n_dev;      // nullable: count on the device (else n)
+  long long n;
+  const float4* tri_in;  // input-order triangles
+  float4* out_rays;
+  int* out_skip;
+  int* out_src;          // nullable
+  int* out_count;
+  int* block_counts;
+  long long cap;
+};
+
+__device__ __forceinline__ bool survives(const ReflectArgs& A, long long i, float4* hit) {
+  *hit = A.hits[i];
+  const int id = __float_as_int(hit->y);
+  const float4 rb = A.rays[2 * i + 1];
+  return id >= 0 && rb.w - hit->x > 0.f;
+}
+
+__device__ __forceinline__ long long count_of(const ReflectArgs& A) {
+  return A.n_dev ? (long long)*A.n_dev : A.n;
+}
+
+__global__ void __launch_bounds__(kRayBlock) k_reflect_count(ReflectArgs A) {
+  __shared__ int wsum[kRayBlock / 32];
+  const long long n = count_of(A);
+  const long long i = blockIdx.x * (long long)kRayBlock + threadIdx.x;
+  float4 h;
+  const bool keep = i < n && survives(A, i, &h);
+  const unsigned m = __ballot_sync(0xffffffffu, keep);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = __popc(m);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < kRayBlock / 32; ++w) t += wsum[w];
+    A.block_counts[blockIdx.x] = t;
+  }
+}
+
+// Exclusive scan of the block counts (one CTA) and the total.
+__global__ void __launch_bounds__(1024) k_reflect_scan(ReflectArgs A, int nblocks) {
+  __shared__ int carry;
+  __shared__ int ws[32];
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int b0 = 0; b0 < nblocks; b0 += 1024) {
+    const int b = b0 + threadIdx.x;
+    const int v = b < nblocks ? A.block_counts[b] : 0;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if ((threadIdx.x & 31) >= o) x += y;
+    }
+    if ((threadIdx.x & 31) == 31) ws[threadIdx.x >> 5] = x;
+    __syncthreads();
+    int off = 0, tot = 0;
+    for (int w = 0; w < 32; ++w) {
+      if (w < (int)(threadIdx.x >> 5)) off += ws[w];
+      tot += ws[w];
+    }
+    if (b < nblocks) A.block_counts[b] = carry + off + x - v;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *A.out_count = (int)min((long long)carry, A.cap);
+}
+
+__global__ void __launch_bounds__(kRayBlock) k_reflect_scatter(ReflectArgs A) {
+  __shared__ int wsum[kRayBlock / 32];
+  const long long n = count_of(A);
+  const long long i = blockIdx.x * (long long)kRayBlock + threadIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float4 h = make_float4(0.f, 0.f, 0.f, 0.f);
+  const bool keep = i < n && survives(A, i, &h);
+  const unsigned m = __ballot_sync(0xffffffffu, keep);
+  if (lane == 0) wsum[warp] = __popc(m);
+  __syncthreads();
+  if (!keep) return;
+  int pos = A.block_counts[blockIdx.x];
+  for (int w = 0; w < warp; ++w) pos += wsum[w];
+  pos += __popc(m & ((1u << lane) - 1u));
+  if (pos >= A.cap) return;
+  const float4 ra = A.rays[2 * i], rb = A.rays[2 * i + 1];
+  const int id = __float_as_int(h.y);
+  const float t = h.x;
+  const float4 a = A.tri_in[3 * (size_t)id], b = A.tri_in[3 * (size_t)id + 1], c = A.tri_in[3 * (size_t)id + 2];
+  const float e1x = b.x - a.x, e1y = b.y - a.y, e1z = b.z - a.z;
+  const float e2x = c.x - a.x, e2y = c.y - a.y, e2z = c.z - a.z;
+  float nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
+  const float inv = rsqrtf(nx * nx + ny * ny + nz * nz);
+  nx *= inv;
+  ny *= inv;
+  nz *= inv;
+  const float dn = rb.x * nx + rb.y * ny + rb.z * nz;
+  A.out_rays[2 * (size_t)pos] = make_float4(fmaf(t, rb.x, ra.x), fmaf(t, rb.y, ra.y), fmaf(t, rb.z, ra.z), 0.f);
+  A.out_rays[2 * (size_t)pos + 1] =
+      make_float4(rb.x - 2.f * dn * nx, rb.y - 2.f * dn * ny, rb.z - 2.f * dn * nz, rb.w - t);
+  A.out_skip[pos] = id;
+  if (A.out_src) A.out_src[pos] = (int)i;
+}
+
+std::once_flag g_ico_once;
+bool g_ico_ok = false;
+
+// The regular icosahedron with vertices (0, +-1, +-phi) and cyclic shifts;
+// edges and faces found as vertex pairs / triples at the edge length 2,
+// listed in lexicographic order of their sorted indices.
+void init_ico() {
+  Ico h;
+  const double g = (1.0 + std::sqrt(5.0)) / 2.0;
+  double v[12][3];
+  int k = 0;
+  for (double a : {-1.0, 1.0})
+    for (double b : {-g, g}) {
+      const double tri[3][3] = {{0.0, a, b}, {a, b, 0.0}, {b, 0.0, a}};
+      for (auto& p : tri) {
+        v[k][0] = p[0];
+        v[k][1] = p[1];
+        v[k][2] = p[2];
+        ++k;
+      }
+    }
+  auto adj = [&](int i, int j) {
+    const double dx = v[i][0] - v[j][0], dy = v[i][1] - v[j][1], dz = v[i][2] - v[j][2];
+    return std::fabs(std::sqrt(dx * dx + dy * dy + dz * dz) - 2.0) < 1e-9;
+  };
+  int ne = 0, nf = 0;
+  for (int i = 0; i < 12; ++i)
+    for (int j = i + 1; j < 12; ++j) {
+      if (!adj(i, j)) continue;
+      if (ne < 30) {
+        h.e[ne][0] = i;
+        h.e[ne][1] = j;
+      }
+      ++ne;
+      for (int l = j + 1; l < 12; ++l)
+        if (adj(j, l) && adj(i, l)) {
+          if (nf < 20) {
+            h.f[nf][0] = i;
+            h.f[nf][1] = j;
+            h.f[nf][2] = l;
+          }
+          ++nf;
+        }
+    }
+  for (int i = 0; i < 12; ++i)
+    for (int a = 0; a < 3; ++a) h.v[i][a] = (float)v[i][a];
+  g_ico_ok = ne == 30 && nf == 20 && cudaMemcpyToSymbol(c_ico, &h, sizeof(h)) == cudaSuccess;
+}
+
+int grid_for(long long n, int nsm) {
+  long long g = (n + kRayBlock - 1) / kRayBlock;
+  const long long gmax = (long long)nsm * 16;
+  if (g > gmax) g = gmax;
+  return g < 1 ? 1 : (int)g;
+}
+
+int sms() {
+  static int n = 0;
+  if (!n) {
+    int d = 0;
+    cudaGetDevice(&d);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+}  // namespace
+
+cudaError_t launch_gen_rays(int kind, const float* o, long long param, float tmin, float tmax, rt_ray* rays,
+                            long long count, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  if (kind == RT_RAYS_FIBONACCI) {
+    k_gen_fibonacci<<<grid_for(count, sms()), kRayBlock, 0, st>>>(o[0], o[1], o[2], count, tmin, tmax,
+                                                                   reinterpret_cast<float4*>(rays));
+  } else {
+    std::call_once(g_ico_once, init_ico);
+    if (!g_ico_ok) return cudaErrorInitializationError;
+    k_gen_icosphere<<<grid_for(count, sms()), kRayBlock, 0, st>>>(o[0], o[1], o[2], 1 << param, count, tmin,
+                                                                   tmax, reinterpret_cast<float4*>(rays));
+  }
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reflect(const rt_scene_s* s, const rt_ray* rays, const rt_hit* hits, long long n,
+                           const int* n_dev, rt_ray* out_rays, int* out_skip, int* out_src, int* out_count,
+                           int* block_counts, long long cap, cudaStream_t st) {
+  ReflectArgs A;
+  A.rays = reinterpret_cast<const float4*>(rays);
+  A.hits = reinterpret_cast<const float4*>(hits);
+  A.n_dev = n_dev;
+  A.n = n;
+  A.tri_in = s->tri_in;
+  A.out_rays = reinterpret_cast<float4*>(out_rays);
+  A.out_skip = out_skip;
+  A.out_src = out_src;
+  A.out_count = out_count;
+  A.block_counts = block_counts;
+  A.cap = cap;
+  const int nb = (int)((n + kRayBlock - 1) / kRayBlock);
+  if (nb == 0) return cudaMemsetAsync(out_count, 0, sizeof(int), st);
+  k_reflect_count<<<nb, kRayBlock, 0, st>>>(A);
+  k_reflect_scan<<<1, 1024, 0, st>>>(A, nb);
+  k_reflect_scatter<<<nb, kRayBlock, 0, st>>>(A);
+  count_launches(3);
+  return cudaGetLastError();
+}
+
+}  // namespace rt

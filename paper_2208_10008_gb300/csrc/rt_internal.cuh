@@ -126,6 +126,16 @@ cudaError_t launch_build(struct ::rt_scene_s* s, const rt_build_params& p, cudaS
 cudaError_t launch_trace(struct ::rt_scene_s* s, const rt_ray* rays, int64_t n, rt_hit* hits,
                          uint8_t* occl, const rt_trace_params* tp, TraceScratch& scr,
                          cudaStream_t st);
+// As launch_trace, with the ray count read on the device from n_dev (<= n, the capacity).
+cudaError_t launch_trace_dev(struct ::rt_scene_s* s, const rt_ray* rays, int64_t n, const int* n_dev,
+                             rt_hit* hits, uint8_t* occl, const rt_trace_params* tp, TraceScratch& scr,
+                             cudaStream_t st);
+cudaError_t launch_gen_rays(int kind, const float* origin, long long param, float tmin, float tmax,
+                            rt_ray* rays, long long count, cudaStream_t st);
+cudaError_t launch_reflect(const struct ::rt_scene_s* s, const rt_ray* rays, const rt_hit* hits,
+                           long long n, const int* n_dev, rt_ray* out_rays, int* out_skip,
+                           int* out_src, int* out_count, int* block_counts, long long cap,
+                           cudaStream_t st);
 
 }  // namespace rt
 
@@ -153,6 +163,8 @@ struct rt_scene_s {
   rt::BuildCtl* ctl = nullptr;
   rt::TraceScratch scratch;     // default trace scratch
   rt::TraceScratch host_scr[2]; // scratch of the host-buffer pipeline
+  int* reflect_blocks = nullptr; // per-block counts of rt_reflect
+  int64_t reflect_blocks_cap = 0;
   rt_ray* stage_rays[2] = {nullptr, nullptr};
   rt_hit* stage_hits[2] = {nullptr, nullptr};
   int64_t stage_cap = 0;

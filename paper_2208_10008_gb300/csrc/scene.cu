@@ -15,7 +15,7 @@
 
 namespace rt {
 static std::atomic<uint64_t> g_launches{0};
-void count_launches(int k) { g_launches.fetch_add((uint64_t)k, std::memory_order_relaxed); }
+void count_launches(int k) { g_launches.fetch_add((uint64_t)(int64_t)k, std::memory_order_relaxed); }
 }  // namespace rt
 
 namespace {
@@ -67,7 +67,7 @@ void free_scene_buffers(rt_scene_s* s) {
                   s->sort_hist, s->node2, s->wide, s->tri_leaf, s->qa, s->qa_ready, s->qb, s->qc,
                   s->qc_ready, s->ctl, s->scratch.counter, s->scratch.queue, s->scratch.cand,
                   s->host_scr[0].counter, s->host_scr[0].queue, s->host_scr[0].cand,
-                  s->host_scr[1].counter, s->host_scr[1].queue, s->host_scr[1].cand, s->stage_rays[0], s->stage_rays[1], s->stage_hits[0],
+                  s->host_scr[1].counter, s->host_scr[1].queue, s->host_scr[1].cand, s->reflect_blocks, s->stage_rays[0], s->stage_rays[1], s->stage_hits[0],
                   s->stage_hits[1]};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -345,6 +345,51 @@ int rt_trace_any(rt_scene s, const rt_ray* rays_dev, int64_t n, uint8_t* occlude
   g_err[0] = 0;
   if (n > 0 && !occluded_dev) return fail(RT_EINVAL, "occluded is NULL");
   return trace_common(s, rays_dev, n, nullptr, occluded_dev, params, stream);
+}
+
+int64_t rt_ray_count(int kind, int64_t param) {
+  if (kind == RT_RAYS_FIBONACCI) return param >= 0 ? param : -1;
+  if (kind == RT_RAYS_ICOSPHERE) {
+    if (param < 0 || param > 12) return -1;
+    const int64_t f = int64_t(1) << param;
+    return 10 * f * f + 2;
+  }
+  return -1;
+}
+
+int rt_gen_rays(int kind, const float* origin, int64_t param, float tmin, float tmax, rt_ray* rays_dev,
+                int64_t capacity, void* stream) {
+  g_err[0] = 0;
+  const int64_t n = rt_ray_count(kind, param);
+  if (n < 0) return fail(RT_EINVAL, "bad launch kind or param");
+  if (n > INT_MAX) return fail(RT_EINVAL, "too many rays");
+  if (!origin || (n > 0 && !rays_dev)) return fail(RT_EINVAL, "NULL argument");
+  if (capacity < n) return fail(RT_EINVAL, "capacity %lld < %lld rays", (long long)capacity, (long long)n);
+  if ((uintptr_t)rays_dev & 15) return fail(RT_EINVAL, "rays must be 16-byte aligned");
+  RT_CUDA(rt::launch_gen_rays(kind, origin, kind == RT_RAYS_FIBONACCI ? n : param, tmin, tmax, rays_dev, n,
+                              (cudaStream_t)stream),
+          "generate rays");
+  return RT_OK;
+}
+
+int rt_reflect(rt_scene s, const rt_ray* rays_dev, const rt_hit* hits_dev, int64_t n, rt_ray* out_rays_dev,
+               int32_t* out_skip_dev, int32_t* out_src_dev, int32_t* out_count_dev, void* stream) {
+  g_err[0] = 0;
+  if (!s) return fail(RT_EINVAL, "scene is NULL");
+  if (n < 0 || n > INT_MAX) return fail(RT_EINVAL, "n out of range");
+  if (!out_count_dev || (n > 0 && (!rays_dev || !hits_dev || !out_rays_dev || !out_skip_dev)))
+    return fail(RT_EINVAL, "NULL buffer");
+  if (((uintptr_t)rays_dev & 15) || ((uintptr_t)hits_dev & 15) || ((uintptr_t)out_rays_dev & 15))
+    return fail(RT_EINVAL, "rays/hits must be 16-byte aligned");
+  const int64_t nb = (n + 255) / 256 + 1;
+  if (s->reflect_blocks_cap < nb) {
+    RT_CUDA(dev_alloc(&s->reflect_blocks, nb), "alloc reflect scratch");
+    s->reflect_blocks_cap = nb;
+  }
+  RT_CUDA(rt::launch_reflect(s, rays_dev, hits_dev, n, nullptr, out_rays_dev, out_skip_dev, out_src_dev,
+                             out_count_dev, s->reflect_blocks, n, (cudaStream_t)stream),
+          "reflect");
+  return RT_OK;
 }
 
 int rt_trace_closest_host(rt_scene s, const rt_ray* rays_host, int64_t n, rt_hit* hits_host,

@@ -262,6 +262,7 @@ struct TraceArgs {
   const float4* tris;
   const rt_ray* rays;
   int n;
+  const int* n_dev;  // nullable: the number of rays lives on the device (<= n)
   rt_hit* hits;
   uint8_t* occl;
   const int32_t* skip;
@@ -275,7 +276,7 @@ struct TraceArgs {
 template <bool kAny, bool kStats>
 __global__ void __launch_bounds__(kTraceBlock) k_trace(TraceArgs A) {
   const int i = blockIdx.x * kTraceBlock + threadIdx.x;
-  if (i >= A.n) return;
+  if (i >= A.n || (A.n_dev && i >= *A.n_dev)) return;
   const float4* r4 = reinterpret_cast<const float4*>(A.rays) + 2 * (size_t)i;
   const RayPre r = setup_ray(__ldg(r4), __ldg(r4 + 1));
   const int skip = A.skip ? __ldg(A.skip + i) : -1;
@@ -575,6 +576,11 @@ int sm_count_t() {
 
 cudaError_t launch_trace(rt_scene_s* s, const rt_ray* rays, int64_t n, rt_hit* hits, uint8_t* occl,
                          const rt_trace_params* tp, TraceScratch& scr, cudaStream_t st) {
+  return launch_trace_dev(s, rays, n, nullptr, hits, occl, tp, scr, st);
+}
+
+cudaError_t launch_trace_dev(rt_scene_s* s, const rt_ray* rays, int64_t n, const int* n_dev, rt_hit* hits,
+                             uint8_t* occl, const rt_trace_params* tp, TraceScratch& scr, cudaStream_t st) {
   cudaError_t e;
   int n_launched = 0;
   if ((e = cudaMemsetAsync(scr.counter, 0, 2 * sizeof(int), st))) return e;
@@ -584,6 +590,7 @@ cudaError_t launch_trace(rt_scene_s* s, const rt_ray* rays, int64_t n, rt_hit* h
     A.tris = s->tri_leaf;
     A.rays = rays;
     A.n = (int)n;
+    A.n_dev = n_dev;
     A.hits = hits;
     A.occl = occl;
     A.skip = tp ? tp->skip_tri_dev : nullptr;

@@ -23,6 +23,8 @@ from . import build_ext
 
 RT_NO_FP64_RETEST = 1
 RT_COUNT_STATS = 2
+RT_RAYS_FIBONACCI = 0
+RT_RAYS_ICOSPHERE = 1
 
 _lock = threading.Lock()
 _lib = None
@@ -33,7 +35,9 @@ ERRORS = {-1: "RT_EINVAL", -2: "RT_ENOMEM", -3: "RT_ENOTBUILT", -4: "RT_ETIMEOUT
 # Every symbol the header declares (checked by the ABI test).
 EXPORTS = ["rt_version", "rt_launch_count", "rt_last_error", "rt_scene_upload", "rt_scene_destroy", "rt_scene_update",
            "rt_bvh_build", "rt_bvh_info", "rt_bvh_export", "rt_trace_closest", "rt_trace_any",
-           "rt_trace_closest_host", "rt_trace_closest_noalloc"]
+           "rt_trace_closest_host", "rt_trace_closest_noalloc", "rt_ray_count", "rt_gen_rays",
+           "rt_reflect", "rt_batch_create", "rt_batch_run", "rt_batch_stats_get", "rt_batch_order",
+           "rt_batch_visibility", "rt_batch_destroy"]
 
 
 class RtError(RuntimeError):
@@ -58,6 +62,21 @@ class BvhInfo(ctypes.Structure):
                 ("n_leaves", ctypes.c_int64), ("n_wide", ctypes.c_int64), ("depth2", ctypes.c_int32),
                 ("depth_wide", ctypes.c_int32), ("max_leaf_size", ctypes.c_int32),
                 ("status", ctypes.c_int32), ("build_ms", ctypes.c_double)]
+
+
+RT_BATCH_MAX_ORDER = 8
+
+
+class BatchDesc(ctypes.Structure):
+    _fields_ = [("n_tx", ctypes.c_int32), ("tx_pos", ctypes.c_void_p), ("tx_param", ctypes.c_void_p),
+                ("dir_kind", ctypes.c_int32), ("max_order", ctypes.c_int32), ("tmax", ctypes.c_float),
+                ("n_rx", ctypes.c_int32), ("rx_pos", ctypes.c_void_p), ("use_graph", ctypes.c_int32)]
+
+
+class BatchStats(ctypes.Structure):
+    _fields_ = [("n_orders", ctypes.c_int32), ("rays", ctypes.c_int64 * (RT_BATCH_MAX_ORDER + 1)),
+                ("segments", ctypes.c_int64), ("total_rays", ctypes.c_int64), ("visible", ctypes.c_int64),
+                ("flagged", ctypes.c_int32)]
 
 
 def lib_path() -> str:
@@ -87,6 +106,18 @@ def lib(build: bool = True):
             L.rt_trace_any.argtypes = [vp, vp, i64, vp, ctypes.POINTER(TraceParams), vp]
             L.rt_trace_closest_host.argtypes = [vp, vp, i64, vp, ctypes.POINTER(TraceParams), vp]
             L.rt_trace_closest_noalloc.argtypes = [vp, vp, i64, vp, ctypes.POINTER(TraceParams), vp]
+            L.rt_ray_count.restype = i64
+            L.rt_ray_count.argtypes = [i32, i64]
+            L.rt_gen_rays.argtypes = [i32, ctypes.POINTER(ctypes.c_float), i64, ctypes.c_float, ctypes.c_float,
+                                      vp, i64, vp]
+            L.rt_reflect.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp, vp]
+            L.rt_batch_create.argtypes = [vp, ctypes.POINTER(BatchDesc), ctypes.POINTER(vp)]
+            L.rt_batch_run.argtypes = [vp, vp]
+            L.rt_batch_stats_get.argtypes = [vp, vp, ctypes.POINTER(BatchStats)]
+            L.rt_batch_order.argtypes = [vp, i32, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                         ctypes.POINTER(vp)]
+            L.rt_batch_visibility.argtypes = [vp, ctypes.POINTER(vp)]
+            L.rt_batch_destroy.argtypes = [vp]
             _lib = L
     return _lib
 
@@ -307,3 +338,122 @@ def hit_ids(hits):
     if isinstance(hits, torch.Tensor):
         return hits.view(torch.int32)[:, 1]
     return np.ascontiguousarray(hits).view(np.int32)[:, 1]
+
+
+def rt_ray_count(kind: int, param: int) -> int:
+    return int(lib().rt_ray_count(int(kind), int(param)))
+
+
+def rt_gen_rays(kind: int, origin, param: int, tmin: float = 0.0, tmax: float = float("inf"), rays=None,
+                stream=None):
+    """Launch rays of Sec. III.A on the device; returns float32 [n, 8] CUDA tensor."""
+    import torch
+    n = rt_ray_count(kind, param)
+    if n < 0:
+        raise RtError(-1, "bad launch kind or param")
+    if rays is None:
+        rays = torch.empty((n, 8), dtype=torch.float32, device="cuda")
+    rp = _dev_ptr(rays, torch.float32, 8, "rays")
+    o = (ctypes.c_float * 3)(*[float(x) for x in origin])
+    _check(lib().rt_gen_rays(int(kind), o, int(param), float(tmin), float(tmax), rp, rays.shape[0],
+                             _stream(stream)))
+    return rays
+
+
+def rt_reflect(scene: Scene, rays, hits, out_rays=None, out_skip=None, out_src=None, out_count=None,
+               stream=None):
+    """Specular bounce + compaction; returns (out_rays, out_skip, out_src, out_count) device tensors."""
+    import torch
+    n = rays.shape[0]
+    dev = rays.device
+    if out_rays is None:
+        out_rays = torch.empty((n, 8), dtype=torch.float32, device=dev)
+    if out_skip is None:
+        out_skip = torch.empty((n,), dtype=torch.int32, device=dev)
+    if out_src is None:
+        out_src = torch.empty((n,), dtype=torch.int32, device=dev)
+    if out_count is None:
+        out_count = torch.zeros((1,), dtype=torch.int32, device=dev)
+    _check(lib().rt_reflect(scene.handle, _dev_ptr(rays, torch.float32, 8, "rays"),
+                            _dev_ptr(hits, torch.float32, 4, "hits"), n,
+                            _dev_ptr(out_rays, torch.float32, 8, "out_rays"),
+                            _dev_ptr(out_skip, torch.int32, None, "out_skip"),
+                            _dev_ptr(out_src, torch.int32, None, "out_src"),
+                            _dev_ptr(out_count, torch.int32, None, "out_count"), _stream(stream)))
+    return out_rays, out_skip, out_src, out_count
+
+
+class _DevArray:
+    """Zero-copy view of library-owned device memory (__cuda_array_interface__)."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (int(ptr or 0), False), "version": 3, "strides": None}
+
+
+def _view(ptr, shape, typestr):
+    import torch
+    return torch.as_tensor(_DevArray(ptr, shape, typestr), device="cuda")
+
+
+class Batch:
+    """Owns one rt_batch handle (multi-transmitter, multi-bounce pipeline)."""
+
+    def __init__(self, scene, tx_pos, tx_param, kind=RT_RAYS_FIBONACCI, max_order=3, tmax=1000.0, rx_pos=None,
+                 use_graph=True):
+        self.scene = scene          # keeps the scene alive
+        self.tx = np.ascontiguousarray(tx_pos, dtype=np.float32).reshape(-1, 3)
+        self.param = np.ascontiguousarray(tx_param, dtype=np.int64).reshape(-1)
+        self.rx = None if rx_pos is None else np.ascontiguousarray(rx_pos, dtype=np.float32).reshape(-1, 3)
+        d = BatchDesc()
+        d.n_tx = len(self.tx)
+        d.tx_pos = self.tx.ctypes.data
+        d.tx_param = self.param.ctypes.data
+        d.dir_kind, d.max_order, d.tmax = int(kind), int(max_order), float(tmax)
+        d.n_rx = 0 if self.rx is None else len(self.rx)
+        d.rx_pos = None if self.rx is None else self.rx.ctypes.data
+        d.use_graph = 1 if use_graph else 0
+        h = ctypes.c_void_p()
+        _check(lib().rt_batch_create(scene.handle, ctypes.byref(d), ctypes.byref(h)))
+        self._h = h.value
+        self.max_order = int(max_order)
+        self.n0 = int(sum(rt_ray_count(kind, p) for p in self.param))
+        self.n_seg = d.n_tx * d.n_rx
+
+    def run(self, stream=None):
+        _check(lib().rt_batch_run(self._h, _stream(stream)))
+
+    def stats(self, stream=None) -> dict:
+        st = BatchStats()
+        _check(lib().rt_batch_stats_get(self._h, _stream(stream), ctypes.byref(st)))
+        return dict(rays=list(st.rays)[: st.n_orders], segments=st.segments, total_rays=st.total_rays,
+                    visible=st.visible, flagged=st.flagged)
+
+    def order(self, k):
+        """(rays [n,8], hits [n,4], src [n] or None, count) for order k (views; count is a python int)."""
+        r, h, s, c = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        _check(lib().rt_batch_order(self._h, int(k), ctypes.byref(r), ctypes.byref(h), ctypes.byref(s),
+                                    ctypes.byref(c)))
+        n = self.n0
+        if k > 0:
+            n = int(_view(c.value, (1,), "<i4").item())
+        rays = _view(r.value, (n, 8), "<f4")
+        hits = _view(h.value, (n, 4), "<f4")
+        src = _view(s.value, (n,), "<i4") if k > 0 else None
+        return rays, hits, src, n
+
+    def visibility(self):
+        p = ctypes.c_void_p()
+        _check(lib().rt_batch_visibility(self._h, ctypes.byref(p)))
+        return _view(p.value, (self.n_seg,), "|u1")
+
+    def destroy(self):
+        if getattr(self, "_h", None):
+            _check(lib().rt_batch_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass

@@ -42,3 +42,10 @@ def test_null_arguments_rejected_without_gpu():
     out = ctypes.c_void_p()
     assert lib.rt_scene_upload(None, -5, 0, None, ctypes.byref(out)) == -1
     assert b"n_tri" in lib.rt_last_error()
+
+
+def test_ray_count_without_gpu():
+    lib = rtbvh.lib()
+    assert lib.rt_ray_count(0, 4096) == 4096
+    assert [lib.rt_ray_count(1, L) for L in (0, 1, 8)] == [12, 42, 655362]
+    assert lib.rt_ray_count(1, 13) == -1 and lib.rt_ray_count(7, 1) == -1 and lib.rt_ray_count(0, -1) == -1
