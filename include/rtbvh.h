@@ -282,6 +282,62 @@ int rt_batch_visibility(rt_batch batch, const uint8_t** occluded_dev);
 /* Free the batch (synchronous). */
 int rt_batch_destroy(rt_batch batch);
 
+/* ---- serving --------------------------------------------------------- */
+/* A trace request: one transmitter's launch on a resident scene, traced
+ * with up to max_order reflections (Sec. III). */
+typedef struct {
+  int32_t scene_id;          /* from rt_session_add_scene */
+  float tx[3];               /* transmitter (ray source point) */
+  int32_t dir_kind;          /* RT_RAYS_FIBONACCI or RT_RAYS_ICOSPHERE */
+  int64_t param;             /* ray count or icosphere level */
+  int32_t max_order;         /* 0 .. RT_BATCH_MAX_ORDER */
+  float tmax;                /* ray action range */
+  rt_hit* hits_host;         /* nullable: receives the closest hits of the launched rays */
+  int64_t* order_counts_host;/* nullable: receives rays traced per order [max_order + 1] */
+} rt_request;
+
+typedef struct {
+  int64_t submitted, completed, failed, queued, running, peak_running;
+  int64_t rays;              /* rays traced by completed requests (all orders) */
+  int64_t pool_bytes, peak_pool_bytes;
+  double p50_ms, p99_ms, mean_ms; /* submit-to-completion latency of completed requests */
+  double span_s;             /* first submit to last completion */
+} rt_session_stats;
+
+/* Create a serving session: one device pool of pool_bytes (allocated now)
+ * and max_slots concurrent requests (1..64), each on its own stream.  A
+ * worker thread admits queued requests in arrival order whenever a slot is
+ * free and the pool holds all of the request's buffers (rays, hits and skip
+ * arrays per order, re-test scratch: about n * (52 (max_order + 1) + 44)
+ * bytes for n rays), so requests of uneven sizes run side by side on the
+ * device.  The calling thread's current device is used.
+ * Errors: RT_EINVAL, RT_ENOMEM, RT_ECUDA. */
+int rt_session_create(size_t pool_bytes, int max_slots, rt_session* out);
+
+/* Make a scene (BVH already built) available to requests; *scene_id is its
+ * index.  The scene must outlive the session and must not be rebuilt while
+ * requests run.  Errors: RT_EINVAL, RT_ENOTBUILT. */
+int rt_session_add_scene(rt_session session, rt_scene scene, int32_t* scene_id);
+
+/* Queue a request (the struct is copied; hits_host / order_counts_host must
+ * stay valid until the request completes).  Never blocks on the device.
+ * Errors: RT_EINVAL, RT_ENOMEM (the request can never fit the pool). */
+int rt_session_submit(rt_session session, const rt_request* req, uint64_t* ticket);
+
+/* *done = 1 once the request's results are in its host buffers.
+ * Errors: RT_EINVAL (unknown ticket), RT_ECUDA (the request failed). */
+int rt_session_poll(rt_session session, uint64_t ticket, int* done);
+
+/* Block until the request completes, or timeout_ns (< 0: no limit).
+ * Errors: RT_EINVAL, RT_ETIMEOUT, RT_ECUDA. */
+int rt_session_wait(rt_session session, uint64_t ticket, int64_t timeout_ns);
+
+/* Counters and latency percentiles so far. */
+int rt_session_stats_get(rt_session session, rt_session_stats* stats);
+
+/* Finish queued and running requests, stop the worker, free the pool. */
+int rt_session_destroy(rt_session session);
+
 /* Largest batch rt_trace_closest_noalloc accepts. */
 #define RT_NOALLOC_MAX_RAYS 262144
 

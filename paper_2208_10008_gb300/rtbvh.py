@@ -37,7 +37,9 @@ EXPORTS = ["rt_version", "rt_launch_count", "rt_last_error", "rt_scene_upload", 
            "rt_bvh_build", "rt_bvh_info", "rt_bvh_export", "rt_trace_closest", "rt_trace_any",
            "rt_trace_closest_host", "rt_trace_closest_noalloc", "rt_ray_count", "rt_gen_rays",
            "rt_reflect", "rt_batch_create", "rt_batch_run", "rt_batch_stats_get", "rt_batch_order",
-           "rt_batch_visibility", "rt_batch_destroy"]
+           "rt_batch_visibility", "rt_batch_destroy", "rt_session_create", "rt_session_add_scene",
+           "rt_session_submit", "rt_session_poll", "rt_session_wait", "rt_session_stats_get",
+           "rt_session_destroy"]
 
 
 class RtError(RuntimeError):
@@ -79,6 +81,20 @@ class BatchStats(ctypes.Structure):
                 ("flagged", ctypes.c_int32)]
 
 
+class Request(ctypes.Structure):
+    _fields_ = [("scene_id", ctypes.c_int32), ("tx", ctypes.c_float * 3), ("dir_kind", ctypes.c_int32),
+                ("param", ctypes.c_int64), ("max_order", ctypes.c_int32), ("tmax", ctypes.c_float),
+                ("hits_host", ctypes.c_void_p), ("order_counts_host", ctypes.c_void_p)]
+
+
+class SessionStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("queued", ctypes.c_int64), ("running", ctypes.c_int64), ("peak_running", ctypes.c_int64),
+                ("rays", ctypes.c_int64), ("pool_bytes", ctypes.c_int64), ("peak_pool_bytes", ctypes.c_int64),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("span_s", ctypes.c_double)]
+
+
 def lib_path() -> str:
     return build_ext.LIB
 
@@ -118,6 +134,13 @@ def lib(build: bool = True):
                                          ctypes.POINTER(vp)]
             L.rt_batch_visibility.argtypes = [vp, ctypes.POINTER(vp)]
             L.rt_batch_destroy.argtypes = [vp]
+            L.rt_session_create.argtypes = [ctypes.c_size_t, i32, ctypes.POINTER(vp)]
+            L.rt_session_add_scene.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int32)]
+            L.rt_session_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
+            L.rt_session_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)]
+            L.rt_session_wait.argtypes = [vp, ctypes.c_uint64, i64]
+            L.rt_session_stats_get.argtypes = [vp, ctypes.POINTER(SessionStats)]
+            L.rt_session_destroy.argtypes = [vp]
             _lib = L
     return _lib
 
@@ -450,6 +473,69 @@ class Batch:
     def destroy(self):
         if getattr(self, "_h", None):
             _check(lib().rt_batch_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+class Session:
+    """Owns one rt_session (resident scenes, memory-admitted requests)."""
+
+    def __init__(self, pool_bytes, max_slots=4):
+        h = ctypes.c_void_p()
+        _check(lib().rt_session_create(int(pool_bytes), int(max_slots), ctypes.byref(h)))
+        self._h = h.value
+        self._keep = {}        # ticket -> host buffers kept alive until completion
+        self._scenes = []
+
+    def add_scene(self, scene) -> int:
+        sid = ctypes.c_int32()
+        _check(lib().rt_session_add_scene(self._h, scene.handle, ctypes.byref(sid)))
+        self._scenes.append(scene)
+        return sid.value
+
+    def submit(self, scene_id, tx, kind, param, max_order=0, tmax=1000.0, want_hits=True):
+        """Returns a ticket; results via result(ticket) after wait()."""
+        n = rt_ray_count(kind, param)
+        hits = np.empty((n, 4), np.float32) if want_hits else None
+        counts = np.zeros(RT_BATCH_MAX_ORDER + 1, np.int64)
+        r = Request()
+        r.scene_id, r.dir_kind, r.param, r.max_order, r.tmax = int(scene_id), int(kind), int(param), \
+            int(max_order), float(tmax)
+        for k in range(3):
+            r.tx[k] = float(tx[k])
+        r.hits_host = hits.ctypes.data if hits is not None else None
+        r.order_counts_host = counts.ctypes.data
+        t = ctypes.c_uint64()
+        _check(lib().rt_session_submit(self._h, ctypes.byref(r), ctypes.byref(t)))
+        self._keep[t.value] = (hits, counts, int(max_order))
+        return t.value
+
+    def poll(self, ticket) -> bool:
+        d = ctypes.c_int()
+        _check(lib().rt_session_poll(self._h, ticket, ctypes.byref(d)))
+        return bool(d.value)
+
+    def wait(self, ticket, timeout_s=None):
+        ns = -1 if timeout_s is None else int(timeout_s * 1e9)
+        _check(lib().rt_session_wait(self._h, ticket, ns))
+
+    def result(self, ticket):
+        hits, counts, mo = self._keep[ticket]
+        return hits, counts[: mo + 1]
+
+    def stats(self) -> dict:
+        st = SessionStats()
+        _check(lib().rt_session_stats_get(self._h, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in SessionStats._fields_}
+
+    def destroy(self):
+        if getattr(self, "_h", None):
+            _check(lib().rt_session_destroy(self._h))
             self._h = None
 
     def __del__(self):
