@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--batched-runs", type=int, default=5)
+    ap.add_argument("--serve-seconds", type=float, default=6.0)
+    ap.add_argument("--no-extra", action="store_true", help="skip the batched and served comparisons")
     return ap.parse_args()
 
 
@@ -171,6 +174,107 @@ def run_reference(args):
                              "sample": "full workload per step: exact-sweep Eq. 2 build + float64 walk of all %d rays" % len(rays)},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- batched / served
+def run_batched(rtbvh, torch, runs):
+    """16 transmitters, orders 0-3, visibility: graph-replayed batch vs per-call host-driven path."""
+    from paper_2208_10008_gb300 import scenes
+    sc, tx, counts, rx = scenes.workload_batched()
+    scene = rtbvh.rt_scene_upload(sc.tris)
+    rtbvh.rt_bvh_build(scene, alpha=0.7, source=tuple(tx.mean(0)), max_leaf=4, bins=16, dist_norm=1)
+    tmax, orders = 1000.0, 3
+    b = rtbvh.Batch(scene, tx, counts, rtbvh.RT_RAYS_FIBONACCI, max_order=orders, tmax=tmax, rx_pos=rx)
+    for _ in range(3):
+        b.run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(runs):
+        b.run()
+    e1.record()
+    torch.cuda.synchronize()
+    ms_b = e0.elapsed_time(e1) / runs
+    st = b.stats()
+    # plain: the same work, one library call at a time, counts read back by the host
+    seg = torch.from_numpy(scenes.segment_rays(np.repeat(tx, len(rx), 0), np.tile(rx, (len(tx), 1)))).cuda()
+
+    def plain():
+        total = 0
+        for t in range(len(tx)):
+            cur = rtbvh.rt_gen_rays(rtbvh.RT_RAYS_FIBONACCI, tx[t], int(counts[t]), 0.0, tmax)
+            skip = None
+            for k in range(orders + 1):
+                h = rtbvh.rt_trace_closest(scene, cur, skip=skip)
+                total += cur.shape[0]
+                if k == orders:
+                    break
+                nr, ns, _, c = rtbvh.rt_reflect(scene, cur, h)
+                m = int(c.item())
+                cur, skip = nr[:m], ns[:m]
+        rtbvh.rt_trace_any(scene, seg)
+        return total + seg.shape[0]
+
+    plain()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tot = 0
+    for _ in range(max(1, runs // 2)):
+        tot = plain()
+    torch.cuda.synchronize()
+    ms_p = 1e3 * (time.perf_counter() - t0) / max(1, runs // 2)
+    b.destroy()
+    scene.destroy()
+    return {"workload": "batched_city_10000_buildings_16tx_orders0-3_4096rx", "n_tri": sc.n_tri,
+            "rays_per_run": st["total_rays"], "rays_per_order": st["rays"], "visible_pairs": st["visible"],
+            "batched_mrays_s": st["total_rays"] / (ms_b * 1e-3) / 1e6, "batched_ms": ms_b,
+            "plain_mrays_s": tot / (ms_p * 1e-3) / 1e6, "plain_ms": ms_p,
+            "speedup": ms_p / ms_b, "batched": "one CUDA graph replay per run (device-side counts)",
+            "plain": "per-transmitter rt_gen_rays / rt_trace_closest / rt_reflect calls, counts read by the host"}
+
+
+def run_served(rtbvh, torch, seconds):
+    """8 resident scenes, Poisson 200 req/s, 64k-4M rays, <= 2 reflections; admission by a pool budget."""
+    from paper_2208_10008_gb300 import scenes
+    scs = scenes.serving_scenes()
+    built = []
+    for sc in scs:
+        s = rtbvh.rt_scene_upload(sc.tris)
+        x0, y0, x1, y1 = sc.area
+        rtbvh.rt_bvh_build(s, alpha=0.7, source=((x0 + x1) / 2, (y0 + y1) / 2, 25.0), max_leaf=4, bins=16,
+                           dist_norm=1)
+        built.append(s)
+    torch.cuda.synchronize()
+    arrivals = scenes.serving_arrivals(scs, seconds)
+
+    def serve(slots, items):
+        sess = rtbvh.Session(pool_bytes=8 << 30, max_slots=slots)
+        ids = [sess.add_scene(s) for s in built]
+        t0 = time.perf_counter()
+        tickets = []
+        for (ta, k, tx, n, mo) in items:
+            now = time.perf_counter() - t0
+            if ta > now:
+                time.sleep(ta - now)
+            tickets.append(sess.submit(ids[k], tx, rtbvh.RT_RAYS_FIBONACCI, n, mo, 1000.0, want_hits=False))
+        for t in tickets:
+            sess.wait(t, timeout_s=600)
+        st = sess.stats()
+        sess.destroy()
+        return st
+
+    st = serve(8, arrivals)
+    n_seq = min(len(arrivals), 200)
+    sq = serve(1, arrivals[:n_seq])
+    for s in built:
+        s.destroy()
+    return {"workload": "8_resident_scenes_poisson_200hz_64k-4M_rays_orders0-2", "n_tri": [sc.n_tri for sc in scs],
+            "requests": st["completed"], "seconds_of_arrivals": seconds,
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
+            "mrays_s": st["rays"] / max(st["span_s"], 1e-9) / 1e6, "peak_running": st["peak_running"],
+            "peak_pool_gb": st["peak_pool_bytes"] / 2 ** 30, "pool_gb": st["pool_bytes"] / 2 ** 30,
+            "one_at_a_time": {"requests": sq["completed"], "p50_ms": sq["p50_ms"], "p99_ms": sq["p99_ms"],
+                              "mrays_s": sq["rays"] / max(sq["span_s"], 1e-9) / 1e6}}
 
 
 # ---------------------------------------------------------------- GPU
@@ -310,6 +414,10 @@ def run_ours(args):
     torch.cuda.synchronize()
     l2_gbs = 50 * 2 * a.numel() / (e0.elapsed_time(e1) * 1e-3) / 1e9
 
+    extra = {}
+    if not args.no_extra:
+        extra["batched"] = run_batched(rtbvh, torch, args.batched_runs)
+        extra["served"] = run_served(rtbvh, torch, args.serve_seconds)
     mean_trace_ms = statistics.mean(trace_ms)
     achieved = bytes_per_ray * R / (mean_trace_ms * 1e-3) / 1e9
     value = ws * R * args.steps / (total_ms * 1e-3) / 1e6
@@ -345,6 +453,7 @@ def run_ours(args):
         "gpu_launches": int(gpu_launches),
         "clocks": clk,
     }
+    line.update(extra)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

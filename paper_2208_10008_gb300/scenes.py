@@ -312,3 +312,45 @@ def workload_medium(level: int = 8):
     sc = medium_city(seed=2)
     rays = make_rays(sc.tx[0], icosphere_directions(level), 0.0, 500.0)
     return sc, rays, dict(alpha=0.4, source=tuple(sc.tx[0]))
+
+
+def workload_batched(seed: int = 3):
+    """10,000 convex 4-8-gon prisms on 3 x 3 km; 16 transmitters at 10-40 m with
+    Fibonacci launches of log-uniform 64k-2M rays; a 64 x 64 receiver grid at 10 m."""
+    rng = _rng(seed + 1000)
+    size = 3000.0
+    tx = np.stack([rng.uniform(0, size, 16), rng.uniform(0, size, 16), rng.uniform(10, 40, 16)], 1)
+    counts = np.exp(rng.uniform(np.log(65536), np.log(2 * 1024 * 1024), 16)).astype(np.int64)
+    sc = prism_city(10000, size, seed, tx_keepout=[tuple(t) for t in tx], name="batched_city")
+    g = (np.arange(64) + 0.5) * (size / 64)
+    gx, gy = np.meshgrid(g, g)
+    rx = np.stack([gx.ravel(), gy.ravel(), np.full(gx.size, 10.0)], 1)
+    return sc, tx, counts, rx
+
+
+def serving_scenes(n: int = 8, seed0: int = 101):
+    """Resident scenes of 1000 .. 50000 buildings (log-spaced), generated as the
+    1000-building city with other seeds; area grows with the building count."""
+    counts = np.unique(np.round(np.exp(np.linspace(np.log(1000), np.log(50000), n))).astype(int))
+    out = []
+    for i, nb in enumerate(counts):
+        size = 1000.0 * math.sqrt(nb / 1000.0)
+        out.append(prism_city(int(nb), size, seed0 + i, name="serving_%d" % nb))
+    return out
+
+
+def serving_arrivals(scenes_, duration_s: float, rate_hz: float = 200.0, seed: int = 4):
+    """Poisson arrivals: (time, scene index, tx, rays, max_order) with rays
+    log-uniform 64k-4M and up to 2 reflections."""
+    rng = _rng(seed)
+    t, out = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / rate_hz)
+        if t > duration_s:
+            break
+        k = int(rng.integers(0, len(scenes_)))
+        x0, y0, x1, y1 = scenes_[k].area
+        tx = (rng.uniform(x0, x1), rng.uniform(y0, y1), rng.uniform(10, 40))
+        rays = int(np.exp(rng.uniform(np.log(65536), np.log(4 * 1024 * 1024))))
+        out.append((t, k, tx, rays, int(rng.integers(0, 3))))
+    return out
