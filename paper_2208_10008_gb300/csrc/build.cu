@@ -1,27 +1,43 @@
 // BVH construction on the device (Sec. II.B-C of arXiv 2208.10008).
 //
-// Pipeline, all asynchronous on one stream:
-//   k_prep        per-triangle AABB (Eq. 3 boxes) + scene / centroid bounds
-//   k_morton      30-bit Morton key of each AABB centre (locality presort)
-//   radix sort    4 stable LSD passes (8-bit digits): hist, scan, scatter
-//   k_make_recs   32-byte records (box + id) in Morton order
-//   k_root        the root task (Fig. 2: "calculate the bounding volume that
-//                 contains all triangular facets")
-//   k_nodes       one CTA per node of more than kMicro triangles, fed by a
-//                 device work queue: bin the AABB centres into `bins` slabs
-//                 per axis, evaluate Eq. 2 at every bin plane, take the
-//                 minimum (ties: lowest axis, lowest plane), stable-partition
-//                 the node's range, emit the children (Fig. 2 recursion)
-//   k_micro       one warp per node of at most kMicro triangles: its whole
-//                 subtree, Eq. 2 over the splits of the range's order
-//   k_collapse    binary tree -> 4-wide traversal nodes (greedy by area)
-//   k_gather      triangles copied into leaf order
+// Pipeline, all asynchronous on one stream.  Every kernel after the first is
+// launched with programmatic dependent launch and waits for its predecessor
+// (griddepcontrol.wait) before it reads anything that kernel wrote, so the
+// launches overlap their set-up with the previous kernel's tail.
+//   memset        control block
+//   k_prep        Eq. 3 box of every triangle -> build record; scene and
+//                 centroid bounds
+//   k_bin_root    30-bit Morton key of every box centre (kept in the record
+//                 for the small subtrees); the root task; the root's bins
+//   k_split       one persistent launch for the whole recursion of Fig. 2.
+//                 Its first CTAs take the chunk items of big nodes (more than
+//                 `big` triangles, cut into chunks of 256..1024 records, CTA
+//                 per chunk): Eq. 2 at every bin plane from the node's merged
+//                 bins, stable partition of the chunk into the other record
+//                 buffer, and on the way the children's bins and per-chunk
+//                 counts; the CTA finishing a node's last chunk writes the node
+//                 and publishes its children's items.  The other warps take
+//                 the remaining nodes of more than 32 triangles from a device
+//                 queue (warp per node, the larger child stays with the warp)
+//                 and finish nodes of at most 32 triangles in registers over
+//                 the Morton order of their records.  No CTA waits for another
+//                 except for work to appear (bounded waits).
+//   k_post        4-wide traversal nodes (greedy by surface area), stored at the
+//                 id of their binary root; triangles in leaf order
+//
+// Bins.  A bin holds 13 words: the record count, the union of the records'
+// boxes and the bounds of their box centres, the floats as order-preserving
+// unsigned codes (min slots store the complement) so that every merge is an
+// atomicAdd or atomicMax and all-zero is the empty bin.  A node's bins give the
+// exact boxes and centroid bounds of both children of any plane, so a child is
+// binned while its parent is partitioned.
 //
 // Node identity: the binary node that splits its range at position s gets id
 // s - 1.  Split positions of distinct internal nodes differ, so ids need no
-// allocator and the tree is the same whatever order the tasks ran in.
+// allocator and the tree is the same whatever order the work ran in.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cfloat>
 #include <climits>
 
@@ -30,18 +46,27 @@
 namespace rt {
 namespace {
 
-constexpr int kPrepBlock = 256;
-constexpr int kSortBlock = 256;          // one element per thread per tile
+constexpr int kBlock = 256;  // threads of every build CTA
+constexpr int kWarps = kBlock / 32;
+constexpr int kBinVals = 13;  // count, box lo xyz, box hi xyz, centre lo xyz, centre hi xyz
+constexpr int kBinWords = 3 * kMaxBins * kBinVals;
+constexpr int kCntStride = 3 * kMaxBins;
+constexpr int kMaxRpt = 4;     // records per thread of a big node's chunk
+constexpr int kBigMin = 1024;  // big nodes have more triangles than this
+constexpr int kStageW = 256;   // records a mid-level warp keeps in shared memory
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 __device__ __forceinline__ void set_status(BuildCtl* ctl, int code, int where) {
   if (atomicCAS(&ctl->status, 0, code) == 0) ctl->status_where = where;
 }
 
+__device__ __forceinline__ int ld_volatile(const int* p) { return *(const volatile int*)p; }
 
 // AABB centre, evaluated identically wherever a bin is needed.
-__device__ __forceinline__ float centre(float lo, float hi) {
-  return __fmul_rn(__fadd_rn(lo, hi), 0.5f);
-}
+__device__ __forceinline__ float centre(float lo, float hi) { return __fmul_rn(__fadd_rn(lo, hi), 0.5f); }
 
 // Bin index of centroid coordinate c for slab [cmin, cmin + K/scale).
 __device__ __forceinline__ int bin_of(float c, float cmin, float scale, int K) {
@@ -59,83 +84,430 @@ __device__ __forceinline__ float area(float3 lo, float3 hi) {
   return 2.f * (dx * dy + dy * dz + dz * dx);
 }
 
+__device__ __forceinline__ float sel3(float x, float y, float z, int k) { return k == 0 ? x : (k == 1 ? y : z); }
+
 struct CostP {
   float alpha, t_i, t_trav, sx, sy, sz;
   int dist_norm;
 };
 
 // Eq. 2 (Eq. 1 at alpha = 1): children L (nl triangles), R (nr) of node C.
-__device__ float eq2_cost(float3 llo, float3 lhi, int nl, float3 rlo, float3 rhi, int nr,
-                          float3 clo, float3 chi, const CostP& p) {
-  float sc = area(clo, chi);
-  float sah = sc > 0.f ? (area(llo, lhi) / sc * (float)nl + area(rlo, rhi) / sc * (float)nr) * p.t_i
-                       : (float)(nl + nr) * p.t_i;
-  float ax = 0.5f * (llo.x + lhi.x) - p.sx, ay = 0.5f * (llo.y + lhi.y) - p.sy,
-        az = 0.5f * (llo.z + lhi.z) - p.sz;
-  float bx = 0.5f * (rlo.x + rhi.x) - p.sx, by = 0.5f * (rlo.y + rhi.y) - p.sy,
-        bz = 0.5f * (rlo.z + rhi.z) - p.sz;
+// The two divisions by the node's area and squared diagonal are reciprocals
+// times products (the build's cost needs no correctly rounded quotient, only
+// the same value for the same inputs).
+__device__ __forceinline__ float eq2_cost(float3 llo, float3 lhi, int nl, float3 rlo, float3 rhi, int nr, float3 clo,
+                                          float3 chi, const CostP& p) {
+  const float sc = area(clo, chi);
+  const float sah = sc > 0.f ? (area(llo, lhi) * (float)nl + area(rlo, rhi) * (float)nr) * __frcp_rn(sc) * p.t_i
+                             : (float)(nl + nr) * p.t_i;
+  const float ax = 0.5f * (llo.x + lhi.x) - p.sx, ay = 0.5f * (llo.y + lhi.y) - p.sy, az = 0.5f * (llo.z + lhi.z) - p.sz;
+  const float bx = 0.5f * (rlo.x + rhi.x) - p.sx, by = 0.5f * (rlo.y + rhi.y) - p.sy, bz = 0.5f * (rlo.z + rhi.z) - p.sz;
   float d2 = 0.5f * ((ax * ax + ay * ay + az * az) + (bx * bx + by * by + bz * bz));
   if (p.dist_norm) {
-    float dx = chi.x - clo.x, dy = chi.y - clo.y, dz = chi.z - clo.z;
-    float diag2 = dx * dx + dy * dy + dz * dz;
-    d2 = (diag2 > 0.f ? d2 / diag2 : 0.f) * (float)(nl + nr) * p.t_i;
+    const float dx = chi.x - clo.x, dy = chi.y - clo.y, dz = chi.z - clo.z;
+    const float diag2 = dx * dx + dy * dy + dz * dz;
+    d2 = (diag2 > 0.f ? d2 * __frcp_rn(diag2) : 0.f) * (float)(nl + nr) * p.t_i;
   }
   return p.alpha * sah + (1.f - p.alpha) * d2 + p.t_trav;
 }
 
-// ------------------------------------------------------------------ prep
-__global__ void k_init_ctl(BuildCtl* ctl, int qa_cap, int qb_cap, int qc_cap) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    for (int a = 0; a < 3; ++a) {
-      ctl->scene_lo[a] = ford(FLT_MAX);
-      ctl->scene_hi[a] = ford(-FLT_MAX);
-      ctl->cen_lo[a] = ford(FLT_MAX);
-      ctl->cen_hi[a] = ford(-FLT_MAX);
+// Order-preserving unsigned code of a float: a < b <=> ucode(a) < ucode(b).
+__device__ __forceinline__ unsigned ucode(float x) { return (unsigned)ford(x) ^ 0x80000000u; }
+__device__ __forceinline__ float uval(unsigned u) { return iford((int)(u ^ 0x80000000u)); }
+
+// ------------------------------------------------------------------ bins
+// Union of a run of bins (or of records): count, box, centre bounds.
+struct BinU {
+  int n;
+  float l0, l1, l2, h0, h1, h2;  // box
+  float a0, a1, a2, b0, b1, b2;  // centre bounds
+};
+
+__device__ __forceinline__ BinU binu_empty() {
+  return {0, FLT_MAX, FLT_MAX, FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX,
+          FLT_MAX, FLT_MAX, FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX};
+}
+__device__ __forceinline__ BinU binu_join(const BinU& x, const BinU& y) {
+  return {x.n + y.n,
+          fminf(x.l0, y.l0), fminf(x.l1, y.l1), fminf(x.l2, y.l2),
+          fmaxf(x.h0, y.h0), fmaxf(x.h1, y.h1), fmaxf(x.h2, y.h2),
+          fminf(x.a0, y.a0), fminf(x.a1, y.a1), fminf(x.a2, y.a2),
+          fmaxf(x.b0, y.b0), fmaxf(x.b1, y.b1), fmaxf(x.b2, y.b2)};
+}
+__device__ __forceinline__ BinU binu_record(float4 lo, float4 hi) {
+  const float cx = centre(lo.x, hi.x), cy = centre(lo.y, hi.y), cz = centre(lo.z, hi.z);
+  return {1, lo.x, lo.y, lo.z, hi.x, hi.y, hi.z, cx, cy, cz, cx, cy, cz};
+}
+#define RT_BINU_SHFL(F, x, arg)                                                                               \
+  BinU {                                                                                                      \
+    F(kFull, (x).n, arg), F(kFull, (x).l0, arg), F(kFull, (x).l1, arg), F(kFull, (x).l2, arg),                \
+        F(kFull, (x).h0, arg), F(kFull, (x).h1, arg), F(kFull, (x).h2, arg), F(kFull, (x).a0, arg),           \
+        F(kFull, (x).a1, arg), F(kFull, (x).a2, arg), F(kFull, (x).b0, arg), F(kFull, (x).b1, arg),           \
+        F(kFull, (x).b2, arg)                                                                                 \
+  }
+__device__ __forceinline__ BinU binu_up(const BinU& x, int o) { return RT_BINU_SHFL(__shfl_up_sync, x, o); }
+__device__ __forceinline__ BinU binu_down(const BinU& x, int o) { return RT_BINU_SHFL(__shfl_down_sync, x, o); }
+__device__ __forceinline__ BinU binu_idx(const BinU& x, int l) { return RT_BINU_SHFL(__shfl_sync, x, l); }
+__device__ __forceinline__ BinU binu_xor(const BinU& x, int o) { return RT_BINU_SHFL(__shfl_xor_sync, x, o); }
+#undef RT_BINU_SHFL
+
+// Decode a 13-word bin entry.
+__device__ __forceinline__ BinU binu_load(const unsigned* e) {
+  const unsigned c = e[0];
+  if (c == 0) return binu_empty();
+  return {(int)c,          uval(~e[1]), uval(~e[2]), uval(~e[3]), uval(e[4]),  uval(e[5]), uval(e[6]),
+          uval(~e[7]),     uval(~e[8]), uval(~e[9]), uval(e[10]), uval(e[11]), uval(e[12])};
+}
+
+// A record's 12 bin codes: box lo / hi and centre (twice: min and max slot).
+struct RecCodes {
+  unsigned v[12];
+};
+__device__ __forceinline__ RecCodes rec_codes(float4 lo, float4 hi, float cx, float cy, float cz) {
+  RecCodes r;
+  r.v[0] = ~ucode(lo.x);
+  r.v[1] = ~ucode(lo.y);
+  r.v[2] = ~ucode(lo.z);
+  r.v[3] = ucode(hi.x);
+  r.v[4] = ucode(hi.y);
+  r.v[5] = ucode(hi.z);
+  r.v[6] = ~ucode(cx);
+  r.v[7] = ~ucode(cy);
+  r.v[8] = ~ucode(cz);
+  r.v[9] = ucode(cx);
+  r.v[10] = ucode(cy);
+  r.v[11] = ucode(cz);
+  return r;
+}
+
+// Add the record of every lane whose key is >= 0 to its bin entry `e`
+// (lanes with equal keys name the same entry; `cnt`, may be null, also gets
+// the number of records).  One pass per distinct key in the warp: the lanes
+// holding it are combined with full-warp reductions and the first of them
+// issues the shared-memory atomics.  All 32 lanes of the warp must call.
+__device__ __forceinline__ void bin_add_warp(int key, unsigned* e, unsigned* cnt, const RecCodes& c) {
+  const int lane = threadIdx.x & 31;
+  __syncwarp();  // lanes that left a divergent loop must run together from here
+  unsigned act = __ballot_sync(kFull, key >= 0);
+  while (act) {
+    const int leader = __ffs(act) - 1;
+    const int k = __shfl_sync(kFull, key, leader);
+    const unsigned peers = __ballot_sync(kFull, key == k);
+    const bool mine = (peers >> lane) & 1u;
+    unsigned r[12];
+#pragma unroll
+    for (int q = 0; q < 12; ++q) r[q] = __reduce_max_sync(kFull, mine ? c.v[q] : 0u);
+    if (lane == leader) {
+      const unsigned m = (unsigned)__popc(peers);
+      atomicAdd(e, m);
+#pragma unroll
+      for (int q = 0; q < 12; ++q) atomicMax(e + 1 + q, r[q]);
+      if (cnt) atomicAdd(cnt, m);
     }
-    ctl->qa_cap = qa_cap;
-    ctl->qb_cap = qb_cap;
-    ctl->qc_cap = qc_cap;
-    ctl->root_ref = INT_MIN;
+    act &= ~peers;
   }
 }
 
-__global__ void __launch_bounds__(kPrepBlock) k_prep(const float4* __restrict__ tri, int n,
-                                                     float4* __restrict__ plo,
-                                                     float4* __restrict__ phi, BuildCtl* ctl) {
-  float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
-  float clo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, chi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    float4 a = tri[3 * i], b = tri[3 * i + 1], c = tri[3 * i + 2];
-    float3 l = make_float3(fminf(a.x, fminf(b.x, c.x)), fminf(a.y, fminf(b.y, c.y)),
-                           fminf(a.z, fminf(b.z, c.z)));
-    float3 h = make_float3(fmaxf(a.x, fmaxf(b.x, c.x)), fmaxf(a.y, fmaxf(b.y, c.y)),
-                           fmaxf(a.z, fmaxf(b.z, c.z)));
-    plo[i] = make_float4(l.x, l.y, l.z, __int_as_float(i));
-    phi[i] = make_float4(h.x, h.y, h.z, 0.f);
-    float cc[3] = {centre(l.x, h.x), centre(l.y, h.y), centre(l.z, h.z)};
-    float ll[3] = {l.x, l.y, l.z}, hh[3] = {h.x, h.y, h.z};
-    for (int k = 0; k < 3; ++k) {
-      lo[k] = fminf(lo[k], ll[k]);
-      hi[k] = fmaxf(hi[k], hh[k]);
-      clo[k] = fminf(clo[k], cc[k]);
-      chi[k] = fmaxf(chi[k], cc[k]);
+// Add one record to bin entry `e` with plain shared-memory atomics (callers
+// spread the lanes over distant records, so lanes rarely share an entry).
+__device__ __forceinline__ void bin_add_plain(unsigned* e, const RecCodes& c) {
+  atomicAdd(e, 1u);
+#pragma unroll
+  for (int q = 0; q < 12; ++q) atomicMax(e + 1 + q, c.v[q]);
+}
+
+// ------------------------------------------------------------------ Eq. 2 evaluation
+struct Split {
+  float cost;
+  int cand;  // axis * (K - 1) + plane - 1 (INT_MAX: none)
+  BinU L, R;
+};
+
+__device__ __forceinline__ void split_none(Split& s) {
+  s.cost = INFINITY;
+  s.cand = INT_MAX;
+  s.L = binu_empty();
+  s.R = binu_empty();
+}
+
+// The K - 1 planes of axis `a` by one warp: lane k holds bin k; warp scans
+// give every lane the union of the bins left of plane k and right of it;
+// lane k evaluates Eq. 2 at plane k.  `best` (identical in every lane) is
+// replaced if this axis has a lower cost, ties going to the lower candidate
+// (lowest axis, then lowest plane).  The union of all bins is the node box.
+__device__ __forceinline__ void eval_axis(const unsigned* bins, int K, int n, int a, const CostP& cp, Split& best) {
+  const int lane = threadIdx.x & 31;
+  __syncwarp();
+  const BinU x = lane < K ? binu_load(bins + (a * K + lane) * kBinVals) : binu_empty();
+  BinU pre = x, suf = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const BinU u = binu_up(pre, o), d = binu_down(suf, o);
+    if (lane >= o) pre = binu_join(pre, u);
+    if (lane + o < 32) suf = binu_join(suf, d);
+  }
+  const BinU L = binu_up(pre, 1);  // lane k: bins 0 .. k-1
+  const BinU C = binu_idx(pre, 31);
+  float cost = INFINITY;
+  int cand = INT_MAX;
+  if (lane >= 1 && lane < K && L.n > 0 && L.n < n) {
+    const float c = eq2_cost(make_float3(L.l0, L.l1, L.l2), make_float3(L.h0, L.h1, L.h2), L.n,
+                             make_float3(suf.l0, suf.l1, suf.l2), make_float3(suf.h0, suf.h1, suf.h2), n - L.n,
+                             make_float3(C.l0, C.l1, C.l2), make_float3(C.h0, C.h1, C.h2), cp);
+    if (c < INFINITY) {
+      cost = c;
+      cand = a * (K - 1) + lane - 1;
     }
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oc = __shfl_xor_sync(kFull, cost, o);
+    const int ok = __shfl_xor_sync(kFull, cand, o);
+    if (oc < cost || (oc == cost && ok < cand)) {
+      cost = oc;
+      cand = ok;
+    }
+  }
+  if (cand != INT_MAX && (cost < best.cost || (cost == best.cost && cand < best.cand))) {
+    const int w = cand - a * (K - 1) + 1;
+    best.cost = cost;
+    best.cand = cand;
+    best.L = binu_idx(L, w);
+    best.R = binu_idx(suf, w);
+  }
+}
+
+// eval_axis for two axes at once (K <= 16): lanes 0..15 take the bins of
+// axis a0, lanes 16..31 those of axis a1, and the scans stop at the half-warp
+// boundary.  Same candidates, costs and tie rule as two eval_axis calls.
+__device__ __forceinline__ void eval_pair(const unsigned* bins, int K, int n, int a0, int a1, const CostP& cp,
+                                          Split& best) {
+  const int lane = threadIdx.x & 31;
+  const int hi16 = lane >> 4, sl = lane & 15;
+  const int a = hi16 ? a1 : a0;
+  __syncwarp();
+  const BinU x = sl < K ? binu_load(bins + (a * K + sl) * kBinVals) : binu_empty();
+  BinU pre = x, suf = x;
+#pragma unroll
+  for (int o = 1; o < 16; o <<= 1) {
+    const BinU u = binu_up(pre, o), d = binu_down(suf, o);
+    if (sl >= o) pre = binu_join(pre, u);
+    if (sl + o < 16) suf = binu_join(suf, d);
+  }
+  const BinU L = binu_up(pre, 1);  // lane k of a half: bins 0 .. k-1 of its axis
+  const BinU C = binu_idx(pre, hi16 * 16 + 15);
+  float cost = INFINITY;
+  int cand = INT_MAX;
+  if (sl >= 1 && sl < K && L.n > 0 && L.n < n) {
+    const float c = eq2_cost(make_float3(L.l0, L.l1, L.l2), make_float3(L.h0, L.h1, L.h2), L.n,
+                             make_float3(suf.l0, suf.l1, suf.l2), make_float3(suf.h0, suf.h1, suf.h2), n - L.n,
+                             make_float3(C.l0, C.l1, C.l2), make_float3(C.h0, C.h1, C.h2), cp);
+    if (c < INFINITY) {
+      cost = c;
+      cand = a * (K - 1) + sl - 1;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oc = __shfl_xor_sync(kFull, cost, o);
+    const int ok = __shfl_xor_sync(kFull, cand, o);
+    if (oc < cost || (oc == cost && ok < cand)) {
+      cost = oc;
+      cand = ok;
+    }
+  }
+  if (cand != INT_MAX && (cost < best.cost || (cost == best.cost && cand < best.cand))) {
+    const int ax = cand / (K - 1);
+    const int w = (ax == a0 ? 0 : 16) + cand - ax * (K - 1) + 1;
+    best.cost = cost;
+    best.cand = cand;
+    best.L = binu_idx(L, w);
+    best.R = binu_idx(suf, w);
+  }
+}
+
+// ------------------------------------------------------------------ arguments
+struct BuildArgs {
+  const float4* tri;  // input-order triangles
+  float4* rec[2];     // [2T] records (lo.xyz, id) (hi.xyz, morton); a node's range lives
+                      // in one buffer, its children go to the other
+  Node2* node2;
+  int2* link2;
+  BuildCtl* ctl;
+  Task* qa;  // mid-level queue
+  int* qa_ready;
+  TopTask* ttask;  // big nodes
+  int* tdone;
+  unsigned* tbins;
+  unsigned* tccnt;
+  unsigned* tscnt;
+  int2* titem;  // chunk items of big nodes
+  int* tready;
+  WNode* wide;
+  float4* tri_leaf;
+  int32_t* order;
+  int* epoch_dev;
+  int n, K, max_leaf;
+  int big, chunk, rpt, cap_t, cap_c, qa_cap, top_ctas;
+  CostP cp;
+};
+
+__device__ __forceinline__ unsigned* tbins_at(const BuildArgs& A, int slot) {
+  return A.tbins + (size_t)slot * kBinWords;
+}
+__device__ __forceinline__ unsigned* tccnt_at(const BuildArgs& A, int c) { return A.tccnt + (size_t)c * kCntStride; }
+__device__ __forceinline__ unsigned* tscnt_at(const BuildArgs& A, int c) { return A.tscnt + (size_t)c * kCntStride; }
+
+__device__ __forceinline__ TopTask load_top_cg(const TopTask* p) {
+  const int4* q = reinterpret_cast<const int4*>(p);
+  const int4 a = __ldcg(q), b = __ldcg(q + 1), c = __ldcg(q + 2), d = __ldcg(q + 3);
+  TopTask t;
+  t.begin = a.x;
+  t.count = a.y;
+  t.parent = a.z;
+  t.side = a.w;
+  t.clo[0] = __int_as_float(b.x);
+  t.clo[1] = __int_as_float(b.y);
+  t.clo[2] = __int_as_float(b.z);
+  t.depth = b.w;
+  t.chi[0] = __int_as_float(c.x);
+  t.chi[1] = __int_as_float(c.y);
+  t.chi[2] = __int_as_float(c.z);
+  t.nchunk = c.w;
+  t.chunk_first = d.x;
+  t.child_slot = d.y;
+  t.chunk_res = d.z;
+  t.parity = d.w;
+  return t;
+}
+
+// Hand a task to the mid-level queue (one thread).  The slot's ready word
+// takes this build's epoch, so stale slots from older builds never match.
+__device__ void push_task(const BuildArgs& A, const Task& t, int epoch) {
+  const int s = atomicAdd(&A.ctl->qa_tail, 1);
+  if (s >= A.qa_cap) {
+    set_status(A.ctl, kStQueueOverflow, 1);
+    return;
+  }
+  atomicAdd(&A.ctl->qa_pending, 1);
+  A.qa[s] = t;
+  __threadfence();
+  atomicExch(&A.qa_ready[s], epoch);
+}
+
+__device__ __forceinline__ Task make_task(int begin, int count, int parent, int side, int depth, const BinU& u,
+                                          int parity) {
+  Task t;
+  t.begin = begin;
+  t.count = count;
+  t.parent = parent;
+  t.side = side;
+  t.clo[0] = u.a0;
+  t.clo[1] = u.a1;
+  t.clo[2] = u.a2;
+  t.chi[0] = u.b0;
+  t.chi[1] = u.b1;
+  t.chi[2] = u.b2;
+  t.depth = depth;
+  t.pad = parity;
+  return t;
+}
+
+// Reserve `amt` consecutive items of a counter bounded by `cap` (-1 if they
+// do not fit; the counter is then left unchanged).
+__device__ int reserve(int* ctr, int amt, int cap) {
+  int old = ld_volatile(ctr);
+  for (int it = 0; it < (1 << 20); ++it) {
+    if (old + amt > cap) return -1;
+    const int prev = atomicCAS(ctr, old, old + amt);
+    if (prev == old) return old;
+    old = prev;
+  }
+  return -1;
+}
+
+// Write binary node `id` (both children's boxes, refs, counts) and link it
+// to its parent.  One thread.
+__device__ __forceinline__ void write_node(const BuildArgs& A, int id, int parent, int side, const BinU& L, int refl,
+                                           int nl, const BinU& R, int refr, int nr, int epoch) {
+  Node2 nd;
+  nd.a_lo = make_float4(L.l0, L.l1, L.l2, __int_as_float(refl));
+  nd.a_hi = make_float4(L.h0, L.h1, L.h2, __int_as_float(nl));
+  nd.b_lo = make_float4(R.l0, R.l1, R.l2, __int_as_float(refr));
+  nd.b_hi = make_float4(R.h0, R.h1, R.h2, __int_as_float(nr));
+  A.node2[id] = nd;
+  if (parent < 0)
+    A.ctl->root_ref = id;
+  else if (parent < A.n - 1)
+    *(side == 0 ? &A.node2[parent].a_lo.w : &A.node2[parent].b_lo.w) = __int_as_float(id);
+  else
+    set_status(A.ctl, kStBadLink, 3);
+  A.link2[id] = make_int2(parent, epoch);
+}
+
+// ------------------------------------------------------------------ prep
+__global__ void __launch_bounds__(kBlock) k_prep(BuildArgs A) {
+  pdl_wait();
+  pdl_launch();
+  __shared__ float red[kWarps][12];
+  const int n = A.n;
+  const int gt = blockIdx.x * kBlock + threadIdx.x, gs = gridDim.x * kBlock;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (gt == 0) {
+    const int e = *A.epoch_dev + 1;
+    *A.epoch_dev = e;
+    A.ctl->epoch = e;
+  }
+  // the root's bins and 32-chunk group counts start empty
+  const int nch = (n + A.chunk - 1) / A.chunk;
+  for (int k = gt; k < kBinWords; k += gs) A.tbins[k] = 0u;
+  for (int k = gt; k < (nch / 32 + 1) * kCntStride; k += gs) A.tscnt[k] = 0u;
+  float v[12];
+#pragma unroll
   for (int k = 0; k < 3; ++k) {
-    for (int o = 16; o > 0; o >>= 1) {
-      lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
-      hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
-      clo[k] = fminf(clo[k], __shfl_xor_sync(0xffffffffu, clo[k], o));
-      chi[k] = fmaxf(chi[k], __shfl_xor_sync(0xffffffffu, chi[k], o));
-    }
+    v[k] = FLT_MAX;       // box lo
+    v[3 + k] = -FLT_MAX;  // box hi
+    v[6 + k] = FLT_MAX;   // centre lo
+    v[9 + k] = -FLT_MAX;  // centre hi
   }
-  if ((threadIdx.x & 31) == 0) {
-    for (int k = 0; k < 3; ++k) {
-      atomicMin(&ctl->scene_lo[k], ford(lo[k]));
-      atomicMax(&ctl->scene_hi[k], ford(hi[k]));
-      atomicMin(&ctl->cen_lo[k], ford(clo[k]));
-      atomicMax(&ctl->cen_hi[k], ford(chi[k]));
+  for (int i = gt; i < n; i += gs) {
+    const float4 a = A.tri[3 * (size_t)i], b = A.tri[3 * (size_t)i + 1], c = A.tri[3 * (size_t)i + 2];
+    const float lx = fminf(a.x, fminf(b.x, c.x)), ly = fminf(a.y, fminf(b.y, c.y)), lz = fminf(a.z, fminf(b.z, c.z));
+    const float hx = fmaxf(a.x, fmaxf(b.x, c.x)), hy = fmaxf(a.y, fmaxf(b.y, c.y)), hz = fmaxf(a.z, fmaxf(b.z, c.z));
+    A.rec[0][2 * (size_t)i] = make_float4(lx, ly, lz, __int_as_float(i));
+    A.rec[0][2 * (size_t)i + 1] = make_float4(hx, hy, hz, 0.f);
+    const float cx = centre(lx, hx), cy = centre(ly, hy), cz = centre(lz, hz);
+    v[0] = fminf(v[0], lx);
+    v[1] = fminf(v[1], ly);
+    v[2] = fminf(v[2], lz);
+    v[3] = fmaxf(v[3], hx);
+    v[4] = fmaxf(v[4], hy);
+    v[5] = fmaxf(v[5], hz);
+    v[6] = fminf(v[6], cx);
+    v[7] = fminf(v[7], cy);
+    v[8] = fminf(v[8], cz);
+    v[9] = fmaxf(v[9], cx);
+    v[10] = fmaxf(v[10], cy);
+    v[11] = fmaxf(v[11], cz);
+  }
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    const bool mn = k < 3 || (k >= 6 && k < 9);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float y = __shfl_xor_sync(kFull, v[k], o);
+      v[k] = mn ? fminf(v[k], y) : fmaxf(v[k], y);
     }
+    if (lane == 0) red[warp][k] = v[k];
+  }
+  __syncthreads();
+  if (threadIdx.x < 12) {
+    const int k = threadIdx.x;
+    const bool mn = k < 3 || (k >= 6 && k < 9);
+    float x = red[0][k];
+    for (int w = 1; w < kWarps; ++w) x = mn ? fminf(x, red[w][k]) : fmaxf(x, red[w][k]);
+    if (n > 0) atomicMax(&A.ctl->sb[k], mn ? ~ucode(x) : ucode(x));
   }
 }
 
@@ -149,440 +521,544 @@ __device__ __forceinline__ uint32_t spread10(uint32_t v) {
   return v;
 }
 
-__global__ void k_morton(const float4* __restrict__ plo, const float4* __restrict__ phi, int n,
-                         const BuildCtl* ctl, uint32_t* __restrict__ keys,
-                         int32_t* __restrict__ idx) {
-  float cl[3], sc[3];
-  for (int a = 0; a < 3; ++a) {
-    cl[a] = iford(ctl->cen_lo[a]);
-    float ext = iford(ctl->cen_hi[a]) - cl[a];
-    sc[a] = ext > 0.f ? 1023.99f / ext : 0.f;
-  }
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    float4 l = plo[i], h = phi[i];
-    float c[3] = {centre(l.x, h.x), centre(l.y, h.y), centre(l.z, h.z)};
-    uint32_t q[3];
-    for (int a = 0; a < 3; ++a) {
-      float f = (c[a] - cl[a]) * sc[a];
-      q[a] = (uint32_t)min(max((int)f, 0), 1023);
-    }
-    keys[i] = (spread10(q[0]) << 2) | (spread10(q[1]) << 1) | spread10(q[2]);
-    idx[i] = i;
-  }
-}
-
-// ------------------------------------------------------------------ radix sort
-__global__ void __launch_bounds__(kSortBlock) k_sort_hist(const uint32_t* __restrict__ keys, int n,
-                                                          int shift, uint32_t* __restrict__ hist,
-                                                          int nblocks, int chunk) {
-  __shared__ uint32_t h[256];
-  h[threadIdx.x] = 0;
-  __syncthreads();
-  int b = blockIdx.x * chunk, e = min(n, b + chunk);
-  for (int i = b + threadIdx.x; i < e; i += kSortBlock) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
-  __syncthreads();
-  hist[blockIdx.x * 256 + threadIdx.x] = h[threadIdx.x];
-}
-
-// Exclusive offsets of every (block, digit) counter: hist[b * 256 + d] <-
-// (elements with digit < d) + (elements with digit d in blocks < b).  One
-// CTA, thread d walks digit d over the blocks (coalesced across threads).
-__global__ void __launch_bounds__(256) k_sort_scan(uint32_t* hist, int nblocks) {
-  __shared__ uint32_t tot[256];
-  __shared__ uint32_t wsum[8];
-  const int d = threadIdx.x;
-  uint32_t run = 0;
-  for (int b = 0; b < nblocks; ++b) {
-    uint32_t c = hist[b * 256 + d];
-    hist[b * 256 + d] = run;
-    run += c;
-  }
-  // exclusive scan of the digit totals
-  uint32_t x = run;
-  for (int o = 1; o < 32; o <<= 1) {
-    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-    if ((d & 31) >= o) x += y;
-  }
-  if ((d & 31) == 31) wsum[d >> 5] = x;
-  __syncthreads();
-  uint32_t wofs = 0;
-  for (int w = 0; w < (d >> 5); ++w) wofs += wsum[w];
-  tot[d] = wofs + x - run;
-  __syncthreads();
-  const uint32_t base = tot[d];
-  for (int b = 0; b < nblocks; ++b) hist[b * 256 + d] += base;
-}
-
-// Stable scatter: tiles of 256 elements, warp-major; ranks from match_any.
-__global__ void __launch_bounds__(kSortBlock) k_sort_scatter(
-    const uint32_t* __restrict__ kin, const int32_t* __restrict__ vin, uint32_t* __restrict__ kout,
-    int32_t* __restrict__ vout, int n, int shift, const uint32_t* __restrict__ hist, int nblocks,
-    int chunk) {
-  __shared__ uint32_t base[256];
-  __shared__ uint32_t wh[kSortBlock / 32][256];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  base[threadIdx.x] = hist[blockIdx.x * 256 + threadIdx.x];
-  int b = blockIdx.x * chunk, e = min(n, b + chunk);
-  for (int t0 = b; t0 < e; t0 += kSortBlock) {
-    for (int k = threadIdx.x; k < (kSortBlock / 32) * 256; k += kSortBlock) (&wh[0][0])[k] = 0u;
-    __syncthreads();
-    int i = t0 + threadIdx.x;
-    bool valid = i < e;
-    uint32_t key = valid ? kin[i] : 0u;
-    int32_t val = valid ? vin[i] : 0;
-    uint32_t d = valid ? ((key >> shift) & 255u) : 256u;
-    uint32_t peers = __match_any_sync(0xffffffffu, d);
-    uint32_t rank = __popc(peers & ((1u << lane) - 1u));
-    if (valid && rank == 0) wh[w][d] = __popc(peers);
-    __syncthreads();
-    {
-      uint32_t run = 0;
-      int dd = threadIdx.x;
-      for (int ww = 0; ww < kSortBlock / 32; ++ww) {
-        uint32_t c = wh[ww][dd];
-        wh[ww][dd] = run;
-        run += c;
-      }
-      __syncthreads();
-      if (valid) {
-        uint32_t pos = base[d] + wh[w][d] + rank;
-        kout[pos] = key;
-        vout[pos] = val;
-      }
-      __syncthreads();
-      base[dd] += run;
-    }
-    __syncthreads();
-  }
-}
-
 // ------------------------------------------------------------------ root
-__global__ void k_root(BuildCtl* ctl, Task* qa, int* qa_ready, Task* qb, int n, int max_leaf,
-                       Node2* node2) {
-  if (threadIdx.x || blockIdx.x) return;
-  if (n <= max_leaf) {
-    ctl->root_ref = leaf_ref(0, n);
-    ctl->n_leaves = 1;
-    ctl->depth2 = 1;
-    ctl->max_leaf_size = n;
-    return;
-  }
-  Task t;
-  t.begin = 0;
-  t.count = n;
-  t.parent = -1;
-  t.side = 0;
-  t.depth = 1;
-  t.pad = 0;
+// Morton keys of all records; the root task (a top task, a mid-level task, a
+// leaf or nothing); the root's bins and per-chunk counts when it is a top task.
+__global__ void __launch_bounds__(kBlock) k_bin_root(BuildArgs A) {
+  pdl_wait();
+  pdl_launch();
+  __shared__ unsigned sbins[kBinWords];
+  __shared__ unsigned scnt[kCntStride];
+  const int n = A.n, K = A.K, K3 = 3 * K, CH = A.chunk;
+  const int nch = (n + CH - 1) / CH;
+  const bool top = n > A.big;
+  const int gt = blockIdx.x * kBlock + threadIdx.x, gs = gridDim.x * kBlock;
+  float cl[3], chh[3], msc[3], scl[3];
+#pragma unroll
   for (int a = 0; a < 3; ++a) {
-    t.clo[a] = iford(ctl->cen_lo[a]);
-    t.chi[a] = iford(ctl->cen_hi[a]);
+    cl[a] = uval(~__ldcg(&A.ctl->sb[6 + a]));
+    chh[a] = uval(__ldcg(&A.ctl->sb[9 + a]));
+    const float ext = chh[a] - cl[a];
+    msc[a] = ext > 0.f ? 1023.99f / ext : 0.f;
+    scl[a] = bin_scale(cl[a], chh[a], K);
   }
-  if (n > kMicro) {
-    qa[0] = t;
-    ctl->qa_tail = 1;
-    ctl->qa_pending = 1;
-    __threadfence();
-    qa_ready[0] = 1;
-  } else {
-    qb[0] = t;
-    ctl->qb_count = 1;
+  if (gt == 0) {
+    const int epoch = __ldcg(&A.ctl->epoch);
+    BinU cu = binu_empty();
+    cu.a0 = cl[0];
+    cu.a1 = cl[1];
+    cu.a2 = cl[2];
+    cu.b0 = chh[0];
+    cu.b1 = chh[1];
+    cu.b2 = chh[2];
+    if (n == 0) {
+      A.ctl->root_ref = INT_MIN;
+    } else if (n <= A.max_leaf) {
+      A.ctl->root_ref = leaf_ref(0, n);
+      A.ctl->n_leaves = 1;
+      A.ctl->depth2 = 1;
+      A.ctl->max_leaf_size = n;
+    } else if (!top) {
+      push_task(A, make_task(0, n, -1, 0, 1, cu, 0), epoch);
+    } else {
+      TopTask R;
+      R.begin = 0;
+      R.count = n;
+      R.parent = -1;
+      R.side = 0;
+      for (int a = 0; a < 3; ++a) {
+        R.clo[a] = cl[a];
+        R.chi[a] = chh[a];
+      }
+      R.depth = 1;
+      R.nchunk = nch;
+      R.chunk_first = 0;   // count slots 0 .. nch-1: the root's chunks (written below)
+      R.child_slot = 1;    // task slots 1, 2
+      R.chunk_res = nch;   // count slots nch .. 2 nch + 1
+      R.parity = 0;
+      A.ttask[0] = R;
+      A.ctl->t_slot_next = 3;
+      A.ctl->t_cnt_next = 2 * nch + 2;
+      A.ctl->ti_tail = nch;
+      A.ctl->ti_pending = nch;
+    }
+  }
+  if (top) {
+    // the root's children start empty; the root's chunks become items
+    const int epoch = __ldcg(&A.ctl->epoch);
+    for (int k = gt; k < 2 * kBinWords; k += gs) tbins_at(A, 1)[k] = 0u;
+    for (int k = gt; k < (nch + 2) * kCntStride; k += gs) {
+      tccnt_at(A, nch)[k] = 0u;
+      tscnt_at(A, nch)[k] = 0u;
+    }
+    if (gt < 3) A.tdone[gt] = 0;
+    for (int c = gt; c < nch; c += gs) {
+      A.titem[c] = make_int2(0, c);
+      A.tready[c] = epoch;
+    }
+  }
+  float4* rec = A.rec[0];
+  for (int c = blockIdx.x; c < nch; c += gridDim.x) {
+    if (top) {
+      for (int w = threadIdx.x; w < K3 * kBinVals; w += kBlock) sbins[w] = 0u;
+      for (int w = threadIdx.x; w < K3; w += kBlock) scnt[w] = 0u;
+      __syncthreads();
+    }
+    for (int r = 0; r < A.rpt; ++r) {
+      const int k = c * CH + r * kBlock + threadIdx.x;
+      const bool valid = k < n;
+      float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
+      float cx = 0.f, cy = 0.f, cz = 0.f;
+      if (valid) {
+        lo = __ldcg(rec + 2 * (size_t)k);
+        hi = __ldcg(rec + 2 * (size_t)k + 1);
+        cx = centre(lo.x, hi.x);
+        cy = centre(lo.y, hi.y);
+        cz = centre(lo.z, hi.z);
+        uint32_t q[3];
+        const float cc[3] = {cx, cy, cz};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) q[a] = (uint32_t)min(max((int)((cc[a] - cl[a]) * msc[a]), 0), 1023);
+        const uint32_t key = (spread10(q[0]) << 2) | (spread10(q[1]) << 1) | spread10(q[2]);
+        hi.w = __uint_as_float(key);
+        rec[2 * (size_t)k + 1] = hi;
+      }
+      if (top) {
+        const float cc[3] = {cx, cy, cz};
+        const RecCodes rc = rec_codes(lo, hi, cx, cy, cz);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const int e = a * K + bin_of(cc[a], cl[a], scl[a], K);
+          bin_add_warp(valid ? e : -1, sbins + e * kBinVals, scnt + e, rc);
+        }
+      }
+    }
+    if (top) {
+      __syncthreads();
+      unsigned* gc = tccnt_at(A, c);
+      unsigned* gg = tscnt_at(A, c >> 5);
+      for (int w = threadIdx.x; w < K3; w += kBlock) {
+        const unsigned v = scnt[w];
+        gc[w] = v;
+        if (v) atomicAdd(gg + w, v);
+      }
+      unsigned* gb = tbins_at(A, 0);
+      for (int w = threadIdx.x; w < K3 * kBinVals; w += kBlock) {
+        const unsigned v = sbins[w];
+        if (v) {
+          if (w % kBinVals == 0)
+            atomicAdd(gb + w, v);
+          else
+            atomicMax(gb + w, v);
+        }
+      }
+      __syncthreads();
+    }
   }
 }
 
-// ------------------------------------------------------------------ split core
-// Bins: [axis][bin][8] ints: count, lo xyz, hi xyz (ordered floats), pad.
-struct SplitResult {
-  int axis, plane, nl;  // axis < 0: median fallback
+// ------------------------------------------------------------------ big nodes
+struct TopSmem {
+  unsigned pbins[kBinWords];
+  unsigned cbins[2][kBinWords];
+  unsigned ccnt[2][2][kCntStride];
+  Split ax[3];
+  int wl[kWarps];
+  int red[kWarps];
+  int2 item;
+  int last;
+  int created[2], zslot[2], zchunk[2], zn[2], ibase[2];
 };
 
-// A bin entry is 9 ints: count, lo xyz, hi xyz (ordered floats), 2 pad.  The
-// odd stride puts consecutive bins in different shared-memory banks.
-constexpr int kBinEnt = 9;
-constexpr int kBinStride = 3 * kMaxBins * kBinEnt;  // ints per bin set
-
-// Reset `nsets` bin sets laid out kBinStride ints apart (first 3*K entries used).
-__device__ __forceinline__ void bins_zero(int* bins, int K, int nsets, int tid, int nthreads) {
-  const int ent = 3 * K;
-  const int lo = ford(FLT_MAX), hi = ford(-FLT_MAX);
-  for (int k = tid; k < ent * nsets; k += nthreads) {
-    const int w = k >= ent ? k / ent : 0;
-    int* e = bins + w * kBinStride + (k - w * ent) * kBinEnt;
-    e[0] = 0;
-    e[1] = lo;
-    e[2] = lo;
-    e[3] = lo;
-    e[4] = hi;
-    e[5] = hi;
-    e[6] = hi;
-  }
-}
-
-__device__ __forceinline__ Task load_task_cg(const Task* p) {
-  const int4* q = reinterpret_cast<const int4*>(p);
-  int4 a = __ldcg(q), b = __ldcg(q + 1), c = __ldcg(q + 2);
-  Task t;
-  t.begin = a.x;
-  t.count = a.y;
-  t.parent = a.z;
-  t.side = a.w;
-  t.clo[0] = __int_as_float(b.x);
-  t.clo[1] = __int_as_float(b.y);
-  t.clo[2] = __int_as_float(b.z);
-  t.depth = b.w;
-  t.chi[0] = __int_as_float(c.x);
-  t.chi[1] = __int_as_float(c.y);
-  t.chi[2] = __int_as_float(c.z);
-  t.pad = c.w;
+__device__ __forceinline__ int block_sum(int v, int* red) {
+  __syncwarp();
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  int t = 0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) t += red[w];
+  __syncthreads();
   return t;
 }
 
-__device__ __forceinline__ void bins_add(int* bins, int K, const float cmin[3], const float scl[3],
-                                         float4 lo, float4 hi) {
-  float c[3] = {centre(lo.x, hi.x), centre(lo.y, hi.y), centre(lo.z, hi.z)};
+// One thread takes the next chunk item and waits for it to be published
+// (no warp-synchronous operation in this loop; the other threads wait at a
+// barrier).  Returns (-1, 0) when no big node is left (or the build failed).
+// The wait is bounded: kSpinLimit polls without new items set a timeout
+// status.
+__device__ int2 claim_item(const BuildArgs& A, int epoch) {
+  const int s = atomicAdd(&A.ctl->ti_head, 1);
+  int seen = -1;
+  for (int it = 0;; ++it) {
+    if (s < A.cap_c && ld_volatile(&A.tready[s]) == epoch) {
+      __threadfence();
+      return __ldcg(A.titem + s);
+    }
+    if ((it & 3) == 0) {
+      if (ld_volatile(&A.ctl->ti_pending) == 0 || ld_volatile(&A.ctl->status) != 0) break;
+      const int tail = ld_volatile(&A.ctl->ti_tail);
+      if (tail != seen) {  // new items appeared: restart the no-progress budget
+        seen = tail;
+        it = 0;
+      }
+    }
+    if (it > kSpinLimit) {
+      set_status(A.ctl, kStQueueTimeout, 2);
+      break;
+    }
+    __nanosleep(128);
+  }
+  return make_int2(-1, 0);
+}
+
+__device__ void top_emit(const BuildArgs& A, TopSmem& S, const TopTask& T, int epoch, int nl, int nr,
+                         const BinU& cu0, const BinU& cu1, bool top0, bool top1, int nch0, int nch1, int cfirst0,
+                         int cfirst1);
+
+// Chunk j of big node T (one CTA): Eq. 2 at every bin plane from the node's
+// merged bins (every chunk of the node picks the same plane), stable
+// partition of the chunk into the other record buffer, and on the way the
+// bins and per-chunk counts of the children that are big nodes too.  The CTA
+// that finishes the node's last chunk writes the node and creates its
+// children: big ones get their chunk items, the others go to the mid-level
+// queue.  No CTA ever waits for another.
+__device__ void top_chunk(const BuildArgs& A, TopSmem& S, const TopTask& T, int slot, int j, int epoch) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int K = A.K, K3 = 3 * K, CH = A.chunk;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  const int n = T.count;
+  const int par = T.parity & 1;
+  const float4* src = A.rec[par];
+  float4* dst = A.rec[par ^ 1];
+  const int r0 = j * CH;
+  const int rn = min(CH, n - r0);
+  // the chunk's records, in flight while the split is chosen
+  float4 lo[kMaxRpt], hi[kMaxRpt];
+#pragma unroll
+  for (int r = 0; r < kMaxRpt; ++r) {
+    const int k = r * kBlock + tid;
+    lo[r] = hi[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (r < A.rpt && k < rn) {
+      const float4* p = src + 2 * ((size_t)T.begin + r0 + k);
+      lo[r] = __ldcg(p);
+      hi[r] = __ldcg(p + 1);
+    }
+  }
+  {
+    const unsigned* gb = tbins_at(A, slot);
+    for (int w = tid; w < K3 * kBinVals; w += kBlock) S.pbins[w] = __ldcg(gb + w);
+    for (int w = tid; w < 2 * kBinWords; w += kBlock) (&S.cbins[0][0])[w] = 0u;
+    for (int w = tid; w < 4 * kCntStride; w += kBlock) (&S.ccnt[0][0][0])[w] = 0u;
+  }
+  float cmin[3], scl[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    if (scl[a] <= 0.f) continue;
-    int* bb = bins + (a * K + bin_of(c[a], cmin[a], scl[a], K)) * kBinEnt;
-    atomicAdd(bb, 1);
-    atomicMin(bb + 1, ford(lo.x));
-    atomicMin(bb + 2, ford(lo.y));
-    atomicMin(bb + 3, ford(lo.z));
-    atomicMax(bb + 4, ford(hi.x));
-    atomicMax(bb + 5, ford(hi.y));
-    atomicMax(bb + 6, ford(hi.z));
+    cmin[a] = T.clo[a];
+    scl[a] = bin_scale(T.clo[a], T.chi[a], K);
   }
-}
-
-// Per-side accumulator of child bounds during the partition pass.
-struct Acc {
-  float v[24];  // side s: [s*12 + 0..2] lo, [3..5] hi, [6..8] centroid lo, [9..11] centroid hi
-  __device__ void init() {
-#pragma unroll
-    for (int s = 0; s < 2; ++s)
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        v[s * 12 + k] = FLT_MAX;
-        v[s * 12 + 3 + k] = -FLT_MAX;
-        v[s * 12 + 6 + k] = FLT_MAX;
-        v[s * 12 + 9 + k] = -FLT_MAX;
-      }
+  __syncthreads();
+  // Eq. 2 at every plane: every warp evaluates axis warp mod 3 (no branch on
+  // the warp index around the shuffles: inside one, they run an order of
+  // magnitude slower); warps 0..2 publish.  An axis without extent has all
+  // records in bin 0 and yields no candidate.
+  {
+    Split sp;
+    split_none(sp);
+    eval_axis(S.pbins, K, n, warp % 3, A.cp, sp);
+    if (lane == 0 && warp < 3) S.ax[warp] = sp;
   }
-  __device__ void add(int s, float4 lo, float4 hi) {
-    float l[3] = {lo.x, lo.y, lo.z}, h[3] = {hi.x, hi.y, hi.z};
+  __syncthreads();
+  Split best = S.ax[0];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      float c = centre(l[k], h[k]);
-      if (s == 0) {
-        v[k] = fminf(v[k], l[k]);
-        v[3 + k] = fmaxf(v[3 + k], h[k]);
-        v[6 + k] = fminf(v[6 + k], c);
-        v[9 + k] = fmaxf(v[9 + k], c);
+  for (int a = 1; a < 3; ++a) {
+    const float ca = S.ax[a].cost;
+    const int ka = S.ax[a].cand;
+    if (ka != INT_MAX && (ca < best.cost || (ca == best.cost && ka < best.cand))) best = S.ax[a];
+  }
+  int axis, plane, nl;
+  BinU cu0, cu1;
+  if (best.cand != INT_MAX) {
+    axis = best.cand / (K - 1);
+    plane = 1 + best.cand % (K - 1);
+    nl = best.L.n;
+    cu0 = best.L;
+    cu1 = best.R;
+  } else {  // no usable plane: split the range in the middle, children take the node's bounds
+    axis = -1;
+    plane = 0;
+    nl = n / 2;
+    BinU node = binu_empty();
+    for (int b = 0; b < K; ++b) node = binu_join(node, binu_load(S.pbins + b * kBinVals));
+    node.a0 = T.clo[0];
+    node.a1 = T.clo[1];
+    node.a2 = T.clo[2];
+    node.b0 = T.chi[0];
+    node.b1 = T.chi[1];
+    node.b2 = T.chi[2];
+    cu0 = node;
+    cu1 = node;
+  }
+  const int nr = n - nl;
+  cu0.n = nl;
+  cu1.n = nr;
+  const bool top0 = nl > A.big, top1 = nr > A.big;
+  const int nch0 = (nl + CH - 1) / CH, nch1 = (nr + CH - 1) / CH;
+  const int cfirst0 = T.chunk_res, cfirst1 = T.chunk_res + nch0;
+  const float cmin0[3] = {cu0.a0, cu0.a1, cu0.a2}, cmin1[3] = {cu1.a0, cu1.a1, cu1.a2};
+  const float scl0[3] = {bin_scale(cu0.a0, cu0.b0, K), bin_scale(cu0.a1, cu0.b1, K), bin_scale(cu0.a2, cu0.b2, K)};
+  const float scl1[3] = {bin_scale(cu1.a0, cu1.b0, K), bin_scale(cu1.a1, cu1.b1, K), bin_scale(cu1.a2, cu1.b2, K)};
+  // records of the node's earlier chunks that go left: 32-chunk group
+  // totals, then the chunks of this chunk's own group
+  int lbase;
+  if (axis >= 0) {
+    const int g = j >> 5;
+    const int ng = g * plane, nc = (j - 32 * g) * plane;
+    int part = 0;
+    for (int it = tid; it < ng + nc; it += kBlock) {
+      if (it < ng) {
+        const int q = it / plane, b = it - q * plane;
+        part += (int)__ldcg(tscnt_at(A, T.chunk_first + q) + axis * K + b);
       } else {
-        v[12 + k] = fminf(v[12 + k], l[k]);
-        v[15 + k] = fmaxf(v[15 + k], h[k]);
-        v[18 + k] = fminf(v[18 + k], c);
-        v[21 + k] = fmaxf(v[21 + k], c);
+        const int i2 = it - ng, q = i2 / plane, b = i2 - q * plane;
+        part += (int)__ldcg(tccnt_at(A, T.chunk_first + 32 * g + q) + axis * K + b);
       }
     }
+    lbase = block_sum(part, S.red);
+  } else {
+    lbase = min(r0, nl);
   }
-  // 24 independent butterflies, interleaved so their shuffles pipeline
-  __device__ void warp_reduce() {
+  const int rbase = r0 - lbase;
+  const int dfirst0 = lbase / CH, dfirst1 = rbase / CH;
+  // stable partition of the chunk; the records of children that are big
+  // nodes too are binned for them on the way
+  int lrun = 0, rrun = 0;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      float y[24];
-#pragma unroll
-      for (int k = 0; k < 24; ++k) y[k] = __shfl_xor_sync(0xffffffffu, v[k], o);
-#pragma unroll
-      for (int k = 0; k < 24; ++k) {
-        const bool is_min = (k % 12) < 3 || ((k % 12) >= 6 && (k % 12) < 9);
-        v[k] = is_min ? fminf(v[k], y[k]) : fmaxf(v[k], y[k]);
+  for (int r = 0; r < kMaxRpt; ++r) {
+    if (r >= A.rpt || r * kBlock >= rn) break;
+    const int k = r * kBlock + tid;
+    const bool valid = k < rn;
+    bool left = false;
+    if (valid) {
+      if (axis >= 0) {
+        const float cc = axis == 0 ? centre(lo[r].x, hi[r].x)
+                                   : (axis == 1 ? centre(lo[r].y, hi[r].y) : centre(lo[r].z, hi[r].z));
+        left = bin_of(cc, sel3(cmin[0], cmin[1], cmin[2], axis), sel3(scl[0], scl[1], scl[2], axis), K) < plane;
+      } else {
+        left = r0 + k < nl;
       }
     }
+    __syncwarp();
+    const unsigned bal = __ballot_sync(kFull, left);
+    if (lane == 0) S.wl[warp] = __popc(bal);
+    __syncthreads();
+    int woff = 0, rtot = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+      const int v = S.wl[w];
+      woff += w < warp ? v : 0;
+      rtot += v;
+    }
+    const int lbefore = woff + __popc(bal & lt_mask);
+    const int dest = left ? lbase + lrun + lbefore : rbase + rrun + tid - lbefore;
+    const int s = left ? 0 : 1;
+    if (valid) {
+      if (dest < (s ? nr : nl)) {
+        const size_t gp = (size_t)T.begin + (s ? nl : 0) + dest;
+        dst[2 * gp] = lo[r];
+        dst[2 * gp + 1] = hi[r];
+      } else {
+        set_status(A.ctl, kStBadSplit, 3);
+      }
+    }
+    if (top0 || top1) {
+      const bool act = valid && (s ? top1 : top0);
+      const int jj = dest / CH - (s ? dfirst1 : dfirst0);
+      const float cx = centre(lo[r].x, hi[r].x), cy = centre(lo[r].y, hi[r].y), cz = centre(lo[r].z, hi[r].z);
+      const float cc[3] = {cx, cy, cz};
+      const RecCodes rc = rec_codes(lo[r], hi[r], cx, cy, cz);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const int b = s ? bin_of(cc[a], cmin1[a], scl1[a], K) : bin_of(cc[a], cmin0[a], scl0[a], K);
+        const int e = a * K + b;
+        const int key = act ? ((s * 2 + (jj & 1)) * 3 + a) * kMaxBins + b : -1;
+        bin_add_warp(key, &S.cbins[s][e * kBinVals], &S.ccnt[s][jj & 1][e], rc);
+      }
+    }
+    lrun += rtot;
+    rrun += min(kBlock, rn - r * kBlock) - rtot;
+    __syncthreads();
   }
-};
-
-__device__ __forceinline__ bool goes_left(float4 lo, float4 hi, const SplitResult& sr, int pos,
-                                          const float cmin[3], const float scl[3], int K) {
-  if (sr.axis < 0) return pos < sr.nl;
-  float c = sr.axis == 0 ? centre(lo.x, hi.x) : (sr.axis == 1 ? centre(lo.y, hi.y) : centre(lo.z, hi.z));
-  return bin_of(c, cmin[sr.axis], scl[sr.axis], K) < sr.plane;
-}
-
-struct BuildArgs {
-  float4* rec[2];    // [2T] each: primitive records (lo.xyz, id) (hi.xyz, 0); a task's
-                     // range lives in rec[task.pad], its children go to the other one
-  Node2* node2;
-  BuildCtl* ctl;
-  Task* qa;
-  int* qa_ready;
-  Task* qb;
-  int K;
-  int max_leaf;
-  CostP cp;
-};
-
-// Emit the node for task t split into (left, right), both ranges already in
-// place.  Called by one thread.  Returns child tasks needing more work in
-// out[0..1] (count in *nout) -- the caller routes them to a tier.
-__device__ void emit_node(const BuildArgs& A, const Task& t, int nl, const float* acc,
-                          Task* out, int* nout) {
-  const int id = t.begin + nl - 1;
-  int cnt[2] = {nl, t.count - nl};
-  int ref[2];
-  *nout = 0;
-  int leaves = 0, big = 0;
+  // the children's bins and chunk counts
+#pragma unroll
   for (int s = 0; s < 2; ++s) {
-    int b = s == 0 ? t.begin : t.begin + nl;
-    if (cnt[s] <= A.max_leaf) {
-      ref[s] = leaf_ref(b, cnt[s]);
-      ++leaves;
-      big = max(big, cnt[s]);
-    } else {
-      ref[s] = INT_MAX;  // patched by the child when it splits
-      Task c;
-      c.begin = b;
-      c.count = cnt[s];
-      c.parent = id;
-      c.side = s;
-      c.depth = t.depth + 1;
-      c.pad = 0;
-      for (int k = 0; k < 3; ++k) {
-        c.clo[k] = acc[s * 12 + 6 + k];
-        c.chi[k] = acc[s * 12 + 9 + k];
+    if (!(s ? top1 : top0)) continue;
+    unsigned* gb = tbins_at(A, T.child_slot + s);
+    for (int w = tid; w < K3 * kBinVals; w += kBlock) {
+      const unsigned v = S.cbins[s][w];
+      if (v) {
+        if (w % kBinVals == 0)
+          atomicAdd(gb + w, v);
+        else
+          atomicMax(gb + w, v);
       }
-      out[(*nout)++] = c;
+    }
+    const int cf = s ? cfirst1 : cfirst0, df = s ? dfirst1 : dfirst0, ncs = s ? nch1 : nch0;
+    for (int q = tid; q < 2 * K3; q += kBlock) {
+      const int jj = q / K3, e = q - jj * K3;
+      const unsigned v = S.ccnt[s][jj][e];
+      const int chunk = df + jj;
+      if (v && chunk < ncs) {
+        atomicAdd(tccnt_at(A, cf + chunk) + e, v);
+        atomicAdd(tscnt_at(A, cf + (chunk >> 5)) + e, v);
+      }
     }
   }
-  Node2 nd;
-  nd.a_lo = make_float4(acc[0], acc[1], acc[2], __int_as_float(ref[0]));
-  nd.a_hi = make_float4(acc[3], acc[4], acc[5], __int_as_float(cnt[0]));
-  nd.b_lo = make_float4(acc[12], acc[13], acc[14], __int_as_float(ref[1]));
-  nd.b_hi = make_float4(acc[15], acc[16], acc[17], __int_as_float(cnt[1]));
-  // children patch a_lo.w / b_lo.w later; write the whole node first
-  A.node2[id] = nd;
-  if (t.parent < 0) {
-    A.ctl->root_ref = id;
-  } else {
-    float* slot = t.side == 0 ? &A.node2[t.parent].a_lo.w : &A.node2[t.parent].b_lo.w;
-    *slot = __int_as_float(id);
+  // the last chunk of the node to finish writes it and creates its children
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    S.last = atomicAdd(&A.tdone[slot], 1) == T.nchunk - 1;
   }
-  atomicAdd(&A.ctl->n_internal, 1);
-  if (leaves) {
-    atomicAdd(&A.ctl->n_leaves, leaves);
-    atomicMax(&A.ctl->max_leaf_size, big);
-    atomicMax(&A.ctl->depth2, t.depth + 1);
-  } else {
-    atomicMax(&A.ctl->depth2, t.depth);
-  }
+  __syncthreads();
+  if (S.last) top_emit(A, S, T, epoch, nl, nr, cu0, cu1, top0, top1, nch0, nch1, cfirst0, cfirst1);
 }
 
-__device__ void push_a(const BuildArgs& A, const Task& c) {
-  int s = atomicAdd(&A.ctl->qa_tail, 1);
-  if (s >= A.ctl->qa_cap) {
-    set_status(A.ctl, kStQueueOverflow, 1);
-    return;
-  }
-  atomicAdd(&A.ctl->qa_pending, 1);
-  A.qa[s] = c;
+// Write the node split by the chunks just finished and create its children
+// (the CTA that finished the node's last chunk).
+__device__ void top_emit(const BuildArgs& A, TopSmem& S, const TopTask& T, int epoch, int nl, int nr,
+                         const BinU& cu0, const BinU& cu1, bool top0, bool top1, int nch0, int nch1, int cfirst0,
+                         int cfirst1) {
+  const int tid = threadIdx.x;
+  const int par = T.parity & 1;
   __threadfence();
-  atomicExch(&A.qa_ready[s], 1);
-}
-
-__device__ void push_b(const BuildArgs& A, const Task& c) {
-  int s = atomicAdd(&A.ctl->qb_count, 1);
-  if (s >= A.ctl->qb_cap) {
-    set_status(A.ctl, kStQueueOverflow, 2);
-    return;
-  }
-  A.qb[s] = c;
-}
-
-// The K-1 planes of axis `a` evaluated by one warp.  Lane 0 accumulates the
-// prefix unions of the bins and lane 1 the suffix unions into `scan` (shared,
-// 2 x K entries of 7 floats); then lane p evaluates plane p from prefix p-1
-// and suffix p.  Every lane gets the best (cost, candidate, left count);
-// candidate = a * (K - 1) + plane - 1.  The full prefix is the node box
-// (every triangle sits in exactly one bin of an active axis).
-__device__ __forceinline__ void warp_axis_best(const int* bins, int K, int n, int a, const CostP& cp,
-                                               float* scan, float* best, int* bestc, int* bestnl) {
-  const int lane = threadIdx.x & 31;
-  if (lane < 2) {
-    const bool fwd = lane == 0;
-    float c = 0.f, l0 = FLT_MAX, l1 = FLT_MAX, l2 = FLT_MAX, h0 = -FLT_MAX, h1 = -FLT_MAX, h2 = -FLT_MAX;
-    for (int i = 0; i < K; ++i) {
-      const int b = fwd ? i : K - 1 - i;
-      const int* e = bins + (a * K + b) * kBinEnt;
-      const int cnt = e[0];
-      if (cnt) {
-        c += (float)cnt;
-        l0 = fminf(l0, iford(e[1]));
-        l1 = fminf(l1, iford(e[2]));
-        l2 = fminf(l2, iford(e[3]));
-        h0 = fmaxf(h0, iford(e[4]));
-        h1 = fmaxf(h1, iford(e[5]));
-        h2 = fmaxf(h2, iford(e[6]));
+  if (tid == 0) {
+    const int id = T.begin + nl - 1;
+    const int refl = nl <= A.max_leaf ? leaf_ref(T.begin, nl) : INT_MAX;
+    const int refr = nr <= A.max_leaf ? leaf_ref(T.begin + nl, nr) : INT_MAX;
+    write_node(A, id, T.parent, T.side, cu0, refl, nl, cu1, refr, nr, epoch);
+    const int leaves = (refl != INT_MAX) + (refr != INT_MAX);
+    atomicAdd(&A.ctl->n_internal, 1);
+    if (leaves) {
+      atomicAdd(&A.ctl->n_leaves, leaves);
+      atomicMax(&A.ctl->max_leaf_size, max(refl != INT_MAX ? nl : 0, refr != INT_MAX ? nr : 0));
+    }
+    atomicMax(&A.ctl->depth2, leaves ? T.depth + 1 : T.depth);
+    for (int s = 0; s < 2; ++s) {
+      const int cn = s ? nr : nl, cb = T.begin + (s ? nl : 0);
+      const BinU& cu = s ? cu1 : cu0;
+      S.created[s] = 0;
+      if (cn <= A.max_leaf) {
+        if (par == 0) push_task(A, make_task(cb, cn, id, s, T.depth + 1, cu, 1), epoch);  // copy to buffer 0
+        continue;
       }
-      float* o = scan + ((fwd ? 0 : K) + b) * 7;
-      o[0] = c;
-      o[1] = l0;
-      o[2] = l1;
-      o[3] = l2;
-      o[4] = h0;
-      o[5] = h1;
-      o[6] = h2;
+      if (s ? top1 : top0) {
+        const int ncs = s ? nch1 : nch0;
+        const int cs = reserve(&A.ctl->t_slot_next, 2, A.cap_t);
+        const int cr = cs >= 0 ? reserve(&A.ctl->t_cnt_next, ncs + 2, A.cap_c) : -1;
+        const int ib = cr >= 0 ? reserve(&A.ctl->ti_tail, ncs, A.cap_c) : -1;
+        if (ib >= 0) {
+          TopTask X;
+          X.begin = cb;
+          X.count = cn;
+          X.parent = id;
+          X.side = s;
+          X.clo[0] = cu.a0;
+          X.clo[1] = cu.a1;
+          X.clo[2] = cu.a2;
+          X.chi[0] = cu.b0;
+          X.chi[1] = cu.b1;
+          X.chi[2] = cu.b2;
+          X.depth = T.depth + 1;
+          X.nchunk = ncs;
+          X.chunk_first = s ? cfirst1 : cfirst0;
+          X.child_slot = cs;
+          X.chunk_res = cr;
+          X.parity = par ^ 1;
+          A.ttask[T.child_slot + s] = X;
+          S.created[s] = 1;
+          S.zslot[s] = cs;
+          S.zchunk[s] = cr;
+          S.zn[s] = ncs + 2;
+          S.ibase[s] = ib;
+          continue;
+        }
+      }
+      push_task(A, make_task(cb, cn, id, s, T.depth + 1, cu, par ^ 1), epoch);  // pools full: a warp takes it
     }
   }
-  __syncwarp();
-  *best = INFINITY;
-  *bestc = INT_MAX;
-  *bestnl = 0;
-  if (lane >= 1 && lane < K) {
-    const float* L = scan + (lane - 1) * 7;  // bins 0..lane-1
-    const float* R = scan + (K + lane) * 7;  // bins lane..K-1
-    const float* N = scan + (K - 1) * 7;     // all bins: the node box
-    const int lc = (int)L[0];
-    if (lc > 0 && lc < n) {
-      *best = eq2_cost(make_float3(L[1], L[2], L[3]), make_float3(L[4], L[5], L[6]), lc,
-                       make_float3(R[1], R[2], R[3]), make_float3(R[4], R[5], R[6]), n - lc,
-                       make_float3(N[1], N[2], N[3]), make_float3(N[4], N[5], N[6]), cp);
-      *bestc = a * (K - 1) + lane - 1;
-      *bestnl = lc;
+  __syncthreads();
+  // what a created child's chunks will fill: its children's bins, done
+  // counters and chunk counts start empty
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    if (!S.created[s]) continue;
+    unsigned* zb = tbins_at(A, S.zslot[s]);
+    for (int w = tid; w < 2 * kBinWords; w += kBlock) zb[w] = 0u;
+    if (tid < 2) A.tdone[S.zslot[s] + tid] = 0;
+    unsigned* zc = tccnt_at(A, S.zchunk[s]);
+    unsigned* zs = tscnt_at(A, S.zchunk[s]);
+    for (int w = tid; w < S.zn[s] * kCntStride; w += kBlock) {
+      zc[w] = 0u;
+      zs[w] = 0u;
     }
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    const float ov = __shfl_xor_sync(0xffffffffu, *best, o);
-    const int oc = __shfl_xor_sync(0xffffffffu, *bestc, o);
-    const int on = __shfl_xor_sync(0xffffffffu, *bestnl, o);
-    if (ov < *best || (ov == *best && oc < *bestc)) {
-      *best = ov;
-      *bestc = oc;
-      *bestnl = on;
+  if (tid == 0 && (S.created[0] || S.created[1]))
+    atomicAdd(&A.ctl->ti_pending, (S.created[0] ? nch0 : 0) + (S.created[1] ? nch1 : 0));
+  __threadfence();
+  __syncthreads();
+  // publish the children's chunk items
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    if (!S.created[s]) continue;
+    const int ncs = s ? nch1 : nch0;
+    for (int q = tid; q < ncs; q += kBlock) {
+      A.titem[S.ibase[s] + q] = make_int2(T.child_slot + s, q);
+      __threadfence();
+      atomicExch(&A.tready[S.ibase[s] + q], epoch);
     }
   }
 }
 
-__device__ __forceinline__ SplitResult make_split(int K, int n, float best, int bestc, int bestnl) {
-  SplitResult sr;
-  if (bestc == INT_MAX || !(best < INFINITY)) {
-    sr.axis = -1;  // no usable plane: split the range in the middle
-    sr.plane = 0;
-    sr.nl = n / 2;
+// Chunk j of big node `slot`, after checking the node's fields.
+__device__ void top_item(const BuildArgs& A, TopSmem& S, int slot, int j, int epoch) {
+  const int tid = threadIdx.x;
+  TopTask T;
+  bool ok = slot >= 0 && slot < A.cap_t;
+  if (ok) T = load_top_cg(A.ttask + slot);
+  const int n = ok ? T.count : 0;
+  ok = ok && T.begin >= 0 && n > A.big && T.begin <= A.n - n && j >= 0 && j < T.nchunk && T.chunk_first >= 0 &&
+       T.chunk_first + T.nchunk <= A.cap_c && T.child_slot >= 0 && T.child_slot + 2 <= A.cap_t &&
+       T.chunk_res >= 0 && T.chunk_res + T.nchunk + 2 <= A.cap_c;
+  if (!ok) {
+    if (tid == 0) set_status(A.ctl, kStBadSplit, 4);
   } else {
-    sr.axis = bestc / (K - 1);
-    sr.plane = 1 + bestc % (K - 1);
-    sr.nl = bestnl;
+    top_chunk(A, S, T, slot, j, epoch);
   }
-  return sr;
 }
 
-// ------------------------------------------------------------------ micro subtrees
-// A node of at most 32 * E triangles (E = 1, 2 or 4) is finished by one warp
-// in registers: lane j holds records E*j .. E*j + E-1 of the node's range (in
-// the order the stable partitions kept, i.e. Morton order within the node).
-// Every split of the subtree is the minimum of Eq. 2 over all splits of that
-// order, evaluated from lane-local prefix/suffix unions of the records' boxes
-// and one warp scan of the lane totals; ranges never move, so there is no
+__device__ void top_loop(const BuildArgs& A, TopSmem& S, int epoch) {
+  for (;;) {
+    if (threadIdx.x == 0) S.item = claim_item(A, epoch);
+    __syncthreads();
+    const int2 it = S.item;
+    __syncthreads();
+    if (it.x < 0) return;
+    top_item(A, S, it.x, it.y, epoch);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicSub(&A.ctl->ti_pending, 1);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ small subtrees
+// A node of at most 32 triangles is finished by one warp in registers: lane
+// j holds record j of the node's range in Morton order.  Every split of the
+// subtree is the minimum of Eq. 2 over all splits of that order, evaluated
+// from warp scans of the records' boxes; ranges never move, so there is no
 // partition step.
 struct Box6 {
   float l0, l1, l2, h0, h1, h2;
@@ -593,107 +1069,92 @@ __device__ __forceinline__ Box6 box_join(const Box6& a, const Box6& b) {
           fmaxf(a.h0, b.h0), fmaxf(a.h1, b.h1), fmaxf(a.h2, b.h2)};
 }
 __device__ __forceinline__ Box6 box_shfl_up(const Box6& a, int o) {
-  return {__shfl_up_sync(0xffffffffu, a.l0, o), __shfl_up_sync(0xffffffffu, a.l1, o),
-          __shfl_up_sync(0xffffffffu, a.l2, o), __shfl_up_sync(0xffffffffu, a.h0, o),
-          __shfl_up_sync(0xffffffffu, a.h1, o), __shfl_up_sync(0xffffffffu, a.h2, o)};
+  return {__shfl_up_sync(kFull, a.l0, o), __shfl_up_sync(kFull, a.l1, o), __shfl_up_sync(kFull, a.l2, o),
+          __shfl_up_sync(kFull, a.h0, o), __shfl_up_sync(kFull, a.h1, o), __shfl_up_sync(kFull, a.h2, o)};
 }
 __device__ __forceinline__ Box6 box_shfl_down(const Box6& a, int o) {
-  return {__shfl_down_sync(0xffffffffu, a.l0, o), __shfl_down_sync(0xffffffffu, a.l1, o),
-          __shfl_down_sync(0xffffffffu, a.l2, o), __shfl_down_sync(0xffffffffu, a.h0, o),
-          __shfl_down_sync(0xffffffffu, a.h1, o), __shfl_down_sync(0xffffffffu, a.h2, o)};
+  return {__shfl_down_sync(kFull, a.l0, o), __shfl_down_sync(kFull, a.l1, o), __shfl_down_sync(kFull, a.l2, o),
+          __shfl_down_sync(kFull, a.h0, o), __shfl_down_sync(kFull, a.h1, o), __shfl_down_sync(kFull, a.h2, o)};
 }
 __device__ __forceinline__ Box6 box_shfl(const Box6& a, int src) {
-  return {__shfl_sync(0xffffffffu, a.l0, src), __shfl_sync(0xffffffffu, a.l1, src),
-          __shfl_sync(0xffffffffu, a.l2, src), __shfl_sync(0xffffffffu, a.h0, src),
-          __shfl_sync(0xffffffffu, a.h1, src), __shfl_sync(0xffffffffu, a.h2, src)};
+  return {__shfl_sync(kFull, a.l0, src), __shfl_sync(kFull, a.l1, src), __shfl_sync(kFull, a.l2, src),
+          __shfl_sync(kFull, a.h0, src), __shfl_sync(kFull, a.h1, src), __shfl_sync(kFull, a.h2, src)};
+}
+__device__ __forceinline__ Box6 box_xor(const Box6& a, int o) {
+  return {__shfl_xor_sync(kFull, a.l0, o), __shfl_xor_sync(kFull, a.l1, o), __shfl_xor_sync(kFull, a.l2, o),
+          __shfl_xor_sync(kFull, a.h0, o), __shfl_xor_sync(kFull, a.h1, o), __shfl_xor_sync(kFull, a.h2, o)};
 }
 
-template <int E>
-__device__ void micro_build(const BuildArgs& A, const float4 (&rlo)[E], const float4 (&rhi)[E], int n,
-                            int gbase, int parent, int side, int depth) {
+// Tree facts gathered by a warp, added to the control block when it exits.
+struct WarpStats {
+  int n_int, n_leaf, big, deep;
+};
+
+__device__ void micro_build(const BuildArgs& A, float4 rlo, float4 rhi, int n, int gbase, int parent, int side,
+                            int depth, int epoch, WarpStats& ws) {
   const int lane = threadIdx.x & 31;
   // uniform stack of pending ranges: (b, e, parent, side | depth << 1); the
-  // larger child is stacked, so at most log2(32 E) + 1 entries
-  int4 st[10];
+  // larger child is stacked first, so at most log2(32) + 1 entries
+  int4 st[8];
   int sp = 0;
   st[sp++] = make_int4(0, n, parent, side | (depth << 1));
-  int n_int = 0, n_leaf = 0, big = 0, deep = 0;
   while (sp > 0) {
+    __syncwarp();
     const int4 tk = st[--sp];
     const int b = tk.x, e = tk.y, par = tk.z, sd = tk.w & 1, dep = tk.w >> 1;
-    // lane-local inclusive prefix / suffix of the in-range records
-    Box6 pre[E], suf[E];
-#pragma unroll
-    for (int i = 0; i < E; ++i) {
-      const int q = E * lane + i;
-      const bool in = q >= b && q < e;
-      Box6 x = in ? Box6{rlo[i].x, rlo[i].y, rlo[i].z, rhi[i].x, rhi[i].y, rhi[i].z} : box_empty();
-      pre[i] = i ? box_join(pre[i - 1], x) : x;
-    }
-#pragma unroll
-    for (int i = E - 1; i >= 0; --i) {
-      const int q = E * lane + i;
-      const bool in = q >= b && q < e;
-      Box6 x = in ? Box6{rlo[i].x, rlo[i].y, rlo[i].z, rhi[i].x, rhi[i].y, rhi[i].z} : box_empty();
-      suf[i] = i < E - 1 ? box_join(suf[i + 1], x) : x;
-    }
-    // warp scans of the lane totals: inclusive prefix / suffix, then exclusive
-    Box6 ip = pre[E - 1], is = suf[0];
+    const bool in = lane >= b && lane < e;
+    const Box6 x = in ? Box6{rlo.x, rlo.y, rlo.z, rhi.x, rhi.y, rhi.z} : box_empty();
+    // inclusive prefix / suffix unions over the lanes
+    Box6 ip = x, is = x;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const Box6 u = box_shfl_up(ip, o), d = box_shfl_down(is, o);
       if (lane >= o) ip = box_join(ip, u);
       if (lane + o < 32) is = box_join(is, d);
     }
-    Box6 xp = box_shfl_up(ip, 1), xs = box_shfl_down(is, 1);
-    if (lane == 0) xp = box_empty();
-    if (lane == 31) xs = box_empty();
+    const Box6 xs = box_shfl_down(is, 1);
+    const Box6 sufn = lane == 31 ? box_empty() : xs;  // records after this lane
     const Box6 node = box_shfl(ip, 31);
     const float3 clo = make_float3(node.l0, node.l1, node.l2), chi = make_float3(node.h0, node.h1, node.h2);
-    // candidate: last left record q (b <= q < e - 1)
+    // candidate: lane q is the last left record (b <= q < e - 1)
     float best = INFINITY;
     int bq = 1 << 20;
-    Box6 bl = box_empty(), br = box_empty();
-#pragma unroll
-    for (int i = 0; i < E; ++i) {
-      const int q = E * lane + i;
-      if (q >= b && q + 1 < e) {
-        const Box6 L = box_join(xp, pre[i]);
-        const Box6 R = box_join(xs, i + 1 < E ? suf[i + 1 < E ? i + 1 : i] : box_empty());
-        const float c = eq2_cost(make_float3(L.l0, L.l1, L.l2), make_float3(L.h0, L.h1, L.h2), q - b + 1,
-                                 make_float3(R.l0, R.l1, R.l2), make_float3(R.h0, R.h1, R.h2), e - q - 1,
-                                 clo, chi, A.cp);
-        if (c < best) {  // increasing q within the lane: strict < keeps the lowest
-          best = c;
-          bq = q;
-          bl = L;
-          br = R;
-        }
+    if (lane >= b && lane + 1 < e) {
+      const float c = eq2_cost(make_float3(ip.l0, ip.l1, ip.l2), make_float3(ip.h0, ip.h1, ip.h2), lane - b + 1,
+                               make_float3(sufn.l0, sufn.l1, sufn.l2), make_float3(sufn.h0, sufn.h1, sufn.h2),
+                               e - lane - 1, clo, chi, A.cp);
+      if (c < INFINITY) {
+        best = c;
+        bq = lane;
       }
     }
     float wb = best;
     int wq = bq;
+#pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      const float oc = __shfl_xor_sync(0xffffffffu, wb, o);
-      const int oq = __shfl_xor_sync(0xffffffffu, wq, o);
+      const float oc = __shfl_xor_sync(kFull, wb, o);
+      const int oq = __shfl_xor_sync(kFull, wq, o);
       if (oc < wb || (oc == wb && oq < wq)) {
         wb = oc;
         wq = oq;
       }
     }
-    const int q = wq < (1 << 20) ? wq : (b + e) / 2 - 1;  // all costs non-finite: middle
-    const int j = q + 1;                                  // first record of the right child
+    const bool found = wq < (1 << 20);
+    const int q = found ? wq : (b + e) / 2 - 1;  // no finite cost: middle
+    const int j = q + 1;                         // first record of the right child
     const int id = gbase + q;
     const int nl = j - b, nr = e - j;
     const int rl = nl <= A.max_leaf ? leaf_ref(gbase + b, nl) : INT_MAX;
     const int rr = nr <= A.max_leaf ? leaf_ref(gbase + j, nr) : INT_MAX;
-    const bool writer = wq < (1 << 20) ? (bq == wq) : (lane == 0);
-    if (writer) {
-      Box6 L = bl, R = br;
-      if (!(wq < (1 << 20))) {  // middle split: boxes recomputed by lane 0 below
-        L = box_empty();
-        R = box_empty();
-      }
+    // child boxes: the unions left / right of the split, by reduction
+    Box6 L = (lane >= b && lane < j) ? x : box_empty();
+    Box6 R = (lane >= j && lane < e) ? x : box_empty();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      L = box_join(L, box_xor(L, o));
+      R = box_join(R, box_xor(R, o));
+    }
+    if (lane == 0) {
       Node2 nd;
       nd.a_lo = make_float4(L.l0, L.l1, L.l2, __int_as_float(rl));
       nd.a_hi = make_float4(L.h0, L.h1, L.h2, __int_as_float(nl));
@@ -702,47 +1163,24 @@ __device__ void micro_build(const BuildArgs& A, const float4 (&rlo)[E], const fl
       A.node2[id] = nd;
       if (par < 0)
         A.ctl->root_ref = id;
-      else
+      else if (par < A.n - 1)
         *(sd == 0 ? &A.node2[par].a_lo.w : &A.node2[par].b_lo.w) = __int_as_float(id);
+      else
+        set_status(A.ctl, kStBadLink, 4);
+      A.link2[id] = make_int2(par, epoch);
     }
-    if (!(wq < (1 << 20))) {
-      // degenerate (non-finite costs): compute the two child boxes by reduction
-      Box6 L = box_empty(), R = box_empty();
-#pragma unroll
-      for (int i = 0; i < E; ++i) {
-        const int qq = E * lane + i;
-        Box6 x = Box6{rlo[i].x, rlo[i].y, rlo[i].z, rhi[i].x, rhi[i].y, rhi[i].z};
-        if (qq >= b && qq < j) L = box_join(L, x);
-        if (qq >= j && qq < e) R = box_join(R, x);
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        L = box_join(L, Box6{__shfl_xor_sync(0xffffffffu, L.l0, o), __shfl_xor_sync(0xffffffffu, L.l1, o),
-                             __shfl_xor_sync(0xffffffffu, L.l2, o), __shfl_xor_sync(0xffffffffu, L.h0, o),
-                             __shfl_xor_sync(0xffffffffu, L.h1, o), __shfl_xor_sync(0xffffffffu, L.h2, o)});
-        R = box_join(R, Box6{__shfl_xor_sync(0xffffffffu, R.l0, o), __shfl_xor_sync(0xffffffffu, R.l1, o),
-                             __shfl_xor_sync(0xffffffffu, R.l2, o), __shfl_xor_sync(0xffffffffu, R.h0, o),
-                             __shfl_xor_sync(0xffffffffu, R.h1, o), __shfl_xor_sync(0xffffffffu, R.h2, o)});
-      }
-      if (lane == 0) {
-        A.node2[id].a_lo = make_float4(L.l0, L.l1, L.l2, __int_as_float(rl));
-        A.node2[id].a_hi = make_float4(L.h0, L.h1, L.h2, __int_as_float(nl));
-        A.node2[id].b_lo = make_float4(R.l0, R.l1, R.l2, __int_as_float(rr));
-        A.node2[id].b_hi = make_float4(R.h0, R.h1, R.h2, __int_as_float(nr));
-      }
-    }
-    ++n_int;
-    deep = max(deep, dep);
+    ++ws.n_int;
+    ws.deep = max(ws.deep, dep);
     if (rl != INT_MAX) {
-      ++n_leaf;
-      big = max(big, nl);
-      deep = max(deep, dep + 1);
+      ++ws.n_leaf;
+      ws.big = max(ws.big, nl);
+      ws.deep = max(ws.deep, dep + 1);
     }
     if (rr != INT_MAX) {
-      ++n_leaf;
-      big = max(big, nr);
-      deep = max(deep, dep + 1);
+      ++ws.n_leaf;
+      ws.big = max(ws.big, nr);
+      ws.deep = max(ws.deep, dep + 1);
     }
-    // stack the larger internal child first so the smaller is taken next
     const int4 cl = make_int4(b, j, id, 0 | ((dep + 1) << 1));
     const int4 cr = make_int4(j, e, id, 1 | ((dep + 1) << 1));
     const bool il = rl == INT_MAX, ir = rr == INT_MAX;
@@ -760,527 +1198,486 @@ __device__ void micro_build(const BuildArgs& A, const float4 (&rlo)[E], const fl
       st[sp++] = cr;
     }
   }
+}
+
+// Load a node of at most 32 records, order them by (Morton key, id) with a
+// warp bitonic sort, write them to buffer 0 in that order (the final order of
+// their leaves) and build the subtree.
+__device__ void micro_task(const BuildArgs& A, int begin, int n, int parity, int parent, int side, int depth,
+                           int epoch, WarpStats& ws) {
+  const int lane = threadIdx.x & 31;
+  float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
+  unsigned long long key = ~0ull;
+  if (lane < n) {
+    const float4* p = A.rec[parity] + 2 * ((size_t)begin + lane);
+    lo = __ldcg(p);
+    hi = __ldcg(p + 1);
+    key = ((unsigned long long)__float_as_uint(hi.w) << 32) | (unsigned)__float_as_int(lo.w);
+  }
+  int src = lane;
+  __syncwarp();
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (int jj = k >> 1; jj > 0; jj >>= 1) {
+      const unsigned long long ok = __shfl_xor_sync(kFull, key, jj);
+      const int os = __shfl_xor_sync(kFull, src, jj);
+      const bool up = (lane & k) == 0;
+      const bool lower = (lane & jj) == 0;
+      const bool take = (lower == up) ? (ok < key) : (ok > key);
+      if (take) {
+        key = ok;
+        src = os;
+      }
+    }
+  }
+  const float4 slo = make_float4(__shfl_sync(kFull, lo.x, src), __shfl_sync(kFull, lo.y, src),
+                                 __shfl_sync(kFull, lo.z, src), __shfl_sync(kFull, lo.w, src));
+  const float4 shi = make_float4(__shfl_sync(kFull, hi.x, src), __shfl_sync(kFull, hi.y, src),
+                                 __shfl_sync(kFull, hi.z, src), __shfl_sync(kFull, hi.w, src));
+  if (lane < n) {
+    float4* p = A.rec[0] + 2 * ((size_t)begin + lane);
+    p[0] = slo;
+    p[1] = shi;
+  }
+  if (n > A.max_leaf) micro_build(A, slo, shi, n, begin, parent, side, depth, epoch, ws);
+}
+
+// ------------------------------------------------------------------ mid levels
+struct MidWarp {
+  unsigned bins[kBinWords];
+  float4 stage[2 * kStageW];
+};
+struct MidSmem {
+  MidWarp w[kWarps];
+};
+
+// Lane 0 takes the next queue slot; the whole warp then waits for it to be
+// filled, every lane polling the same words (broadcast loads), so the warp
+// stays converged: no lane ever parks at a warp-synchronous instruction
+// while another spins, which would tie up the SM's shuffle path.  Returns
+// false when the queue is drained (no big node and no task pending) or the
+// build failed.  The wait is bounded: kSpinLimit polls without progress set
+// a timeout status.
+__device__ bool claim_task(const BuildArgs& A, int epoch, Task& t) {
+  const int lane = threadIdx.x & 31;
+  int s = 0;
+  if (lane == 0) s = atomicAdd(&A.ctl->qa_head, 1);
+  s = __shfl_sync(kFull, s, 0);
+  int seen = -1, it = 0;
+  bool got = false;
+  // every exit is a warp vote, so the warp leaves the loop converged
+  for (;;) {
+    const bool rdy = s < A.qa_cap && ld_volatile(&A.qa_ready[s]) == epoch;
+    if (__any_sync(kFull, rdy)) {
+      got = true;
+      break;
+    }
+    bool stop = false;
+    if ((it & 3) == 0) {
+      // done when no big node is left and then no mid-level task either
+      if (ld_volatile(&A.ctl->ti_pending) == 0) {
+        __threadfence();
+        stop = ld_volatile(&A.ctl->qa_pending) == 0;
+      }
+      stop = stop || ld_volatile(&A.ctl->status) != 0;
+      const int prog = __shfl_sync(kFull, ld_volatile(&A.ctl->qa_tail) + ld_volatile(&A.ctl->ti_head), 0);
+      if (prog != seen) {  // work moved: restart the no-progress budget
+        seen = prog;
+        it = 0;
+      }
+    }
+    if (__any_sync(kFull, stop)) break;
+    if (++it > kSpinLimit) {
+      if (lane == 0) set_status(A.ctl, kStQueueTimeout, 1);
+      break;
+    }
+    __nanosleep(200);
+  }
+  if (got) {
+    __threadfence();
+    const int4* q = reinterpret_cast<const int4*>(A.qa + s);
+    const int4 a = __ldcg(q), b = __ldcg(q + 1), c = __ldcg(q + 2);
+    t.begin = a.x;
+    t.count = a.y;
+    t.parent = a.z;
+    t.side = a.w;
+    t.clo[0] = __int_as_float(b.x);
+    t.clo[1] = __int_as_float(b.y);
+    t.clo[2] = __int_as_float(b.z);
+    t.depth = b.w;
+    t.chi[0] = __int_as_float(c.x);
+    t.chi[1] = __int_as_float(c.y);
+    t.chi[2] = __int_as_float(c.z);
+    t.pad = c.w;
+  }
+  return got;
+}
+
+// Split one node of more than 32 triangles with one warp (bin, Eq. 2, stable
+// partition), write it, and route its children: the larger internal child
+// becomes *cont, the other is queued, small ones are finished here.
+__device__ void mid_split(const BuildArgs& A, MidWarp& W, const Task& t, int epoch, WarpStats& ws, Task& cont,
+                          bool& have_cont) {
+  const int lane = threadIdx.x & 31;
+  const int K = A.K, K3 = 3 * K, n = t.count, par = t.pad & 1;
+  const float4* src = A.rec[par] + 2 * (size_t)t.begin;
+  float4* dst = A.rec[par ^ 1] + 2 * (size_t)t.begin;
+  const bool staged = n <= kStageW;
+  float cmin[3], scl[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    cmin[a] = t.clo[a];
+    scl[a] = bin_scale(t.clo[a], t.chi[a], K);
+  }
+  for (int w = lane; w < K3 * kBinVals; w += 32) W.bins[w] = 0u;
+  if (staged) {
+    for (int k = lane; k < n; k += 32) {
+      W.stage[2 * k] = __ldcg(src + 2 * k);
+      W.stage[2 * k + 1] = __ldcg(src + 2 * k + 1);
+    }
+  }
+  __syncwarp();
+  // lane l bins records l*c .. l*c + c - 1: lanes work on distant records,
+  // which seldom share a bin, so plain atomics rarely collide
+  {
+    const int c = (n + 31) / 32;
+    for (int i = 0; i < c; ++i) {
+      const int k = lane * c + i;
+      if (k < n) {
+        const float4 lo = staged ? W.stage[2 * k] : __ldcg(src + 2 * k);
+        const float4 hi = staged ? W.stage[2 * k + 1] : __ldcg(src + 2 * k + 1);
+        const float cx = centre(lo.x, hi.x), cy = centre(lo.y, hi.y), cz = centre(lo.z, hi.z);
+        const RecCodes rc = rec_codes(lo, hi, cx, cy, cz);
+        bin_add_plain(W.bins + (0 * K + bin_of(cx, cmin[0], scl[0], K)) * kBinVals, rc);
+        bin_add_plain(W.bins + (1 * K + bin_of(cy, cmin[1], scl[1], K)) * kBinVals, rc);
+        bin_add_plain(W.bins + (2 * K + bin_of(cz, cmin[2], scl[2], K)) * kBinVals, rc);
+      }
+    }
+  }
+  __syncwarp();
+  Split best;
+  split_none(best);
+  if (K <= 16) {  // axes x and y in one pass, then z
+    eval_pair(W.bins, K, n, 0, 1, A.cp, best);
+    if (scl[2] > 0.f) eval_axis(W.bins, K, n, 2, A.cp, best);
+  } else {
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if (scl[a] > 0.f) eval_axis(W.bins, K, n, a, A.cp, best);
+  }
+  int axis, plane, nl;
+  if (best.cand != INT_MAX) {
+    axis = best.cand / (K - 1);
+    plane = 1 + best.cand % (K - 1);
+    nl = best.L.n;
+  } else {
+    axis = -1;
+    plane = 0;
+    nl = n / 2;
+  }
+  const float acmin = sel3(cmin[0], cmin[1], cmin[2], axis < 0 ? 0 : axis);
+  const float ascl = sel3(scl[0], scl[1], scl[2], axis < 0 ? 0 : axis);
+  // stable partition into the other buffer (child bounds by reduction when
+  // no plane was usable)
+  int lrun = 0, rrun = 0;
+  BinU accL = binu_empty(), accR = binu_empty();
+  for (int g = 0; g < n; g += 32) {
+    const int k = g + lane;
+    const bool valid = k < n;
+    float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
+    if (valid) {
+      if (staged) {
+        lo = W.stage[2 * k];
+        hi = W.stage[2 * k + 1];
+      } else {
+        lo = __ldcg(src + 2 * k);
+        hi = __ldcg(src + 2 * k + 1);
+      }
+    }
+    bool left = false;
+    if (valid) {
+      if (axis >= 0) {
+        const float cc = axis == 0 ? centre(lo.x, hi.x) : (axis == 1 ? centre(lo.y, hi.y) : centre(lo.z, hi.z));
+        left = bin_of(cc, acmin, ascl, K) < plane;
+      } else {
+        left = k < nl;
+      }
+    }
+    __syncwarp();
+    const unsigned bal = __ballot_sync(kFull, left);
+    const int rank = __popc(bal & ((1u << lane) - 1u));
+    const int dest = left ? lrun + rank : nl + rrun + (lane - rank);
+    if (valid && dest < n) {
+      dst[2 * dest] = lo;
+      dst[2 * dest + 1] = hi;
+      if (axis < 0) {
+        if (left)
+          accL = binu_join(accL, binu_record(lo, hi));
+        else
+          accR = binu_join(accR, binu_record(lo, hi));
+      }
+    }
+    const int tot = __popc(bal);
+    lrun += tot;
+    rrun += min(32, n - g) - tot;
+  }
+  BinU L = best.L, R = best.R;
+  if (axis < 0) {
+    __syncwarp();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      accL = binu_join(accL, binu_xor(accL, o));
+      accR = binu_join(accR, binu_xor(accR, o));
+    }
+    L = accL;
+    R = accR;
+  }
+  if (lane == 0 && lrun != nl) set_status(A.ctl, kStBadSplit, 2);
+  __syncwarp();
+  const int nr = n - nl;
+  // leaves keep their records in buffer 0
+  if (par == 0) {
+    if (nl <= A.max_leaf)
+      for (int k = lane; k < 2 * nl; k += 32) A.rec[0][2 * (size_t)t.begin + k] = __ldcg(dst + k);
+    if (nr <= A.max_leaf)
+      for (int k = lane; k < 2 * nr; k += 32) A.rec[0][2 * ((size_t)t.begin + nl) + k] = __ldcg(dst + 2 * nl + k);
+  }
+  const int id = t.begin + nl - 1;
+  const int refl = nl <= A.max_leaf ? leaf_ref(t.begin, nl) : INT_MAX;
+  const int refr = nr <= A.max_leaf ? leaf_ref(t.begin + nl, nr) : INT_MAX;
+  if (lane == 0) write_node(A, id, t.parent, t.side, L, refl, nl, R, refr, nr, epoch);
+  ++ws.n_int;
+  const int leaves = (refl != INT_MAX) + (refr != INT_MAX);
+  ws.n_leaf += leaves;
+  if (refl != INT_MAX) ws.big = max(ws.big, nl);
+  if (refr != INT_MAX) ws.big = max(ws.big, nr);
+  ws.deep = max(ws.deep, leaves ? t.depth + 1 : t.depth);
+  // children: the larger one of more than 32 stays with this warp
+  L.n = nl;
+  R.n = nr;
+  const bool bigl = nl > kMicro, bigr = nr > kMicro;
+  const int keep = (bigl && bigr) ? (nl >= nr ? 0 : 1) : (bigl ? 0 : (bigr ? 1 : -1));
+  if (keep >= 0) {
+    cont = keep == 0 ? make_task(t.begin, nl, id, 0, t.depth + 1, L, par ^ 1)
+                     : make_task(t.begin + nl, nr, id, 1, t.depth + 1, R, par ^ 1);
+    have_cont = true;
+  }
   if (lane == 0) {
-    atomicAdd(&A.ctl->n_internal, n_int);
-    atomicAdd(&A.ctl->n_leaves, n_leaf);
-    atomicMax(&A.ctl->max_leaf_size, big);
-    atomicMax(&A.ctl->depth2, deep);
+    if (bigl && bigr) {
+      if (keep == 0)
+        push_task(A, make_task(t.begin + nl, nr, id, 1, t.depth + 1, R, par ^ 1), epoch);
+      else
+        push_task(A, make_task(t.begin, nl, id, 0, t.depth + 1, L, par ^ 1), epoch);
+    }
+    // small subtrees go to idle warps while this one goes on down the tree
+    if (keep >= 0) {
+      if (nl > A.max_leaf && !bigl) push_task(A, make_task(t.begin, nl, id, 0, t.depth + 1, L, par ^ 1), epoch);
+      if (nr > A.max_leaf && !bigr) push_task(A, make_task(t.begin + nl, nr, id, 1, t.depth + 1, R, par ^ 1), epoch);
+    }
+  }
+  __syncwarp();
+  if (keep < 0) {
+    if (nl > A.max_leaf) micro_task(A, t.begin, nl, par ^ 1, id, 0, t.depth + 1, epoch, ws);
+    if (nr > A.max_leaf) micro_task(A, t.begin + nl, nr, par ^ 1, id, 1, t.depth + 1, epoch, ws);
   }
 }
 
-// ------------------------------------------------------------------ node kernel
-// Every node of more than kMicro triangles is split by one CTA (Fig. 2, one
-// recursion step): bin the AABB centres of its triangles into `bins` slabs
-// per axis (warp-private bins, each lane on its own sub-chunk of its warp's
-// segment, so neighbouring triangles -- which share bins -- do not contend),
-// evaluate Eq. 2 at every bin plane with one warp per axis, then partition
-// the range stably into the other record buffer (count pass, scan over the
-// warps, scatter pass).  Nodes of at most kStage triangles are first staged
-// in shared memory.  A CTA keeps the larger child as its next task and hands
-// the other to the device queue; children of at most kMicro triangles go to
-// the micro list.
-constexpr int kNodeBlock = 256;
-constexpr int kNodeWarps = kNodeBlock / 32;
-constexpr int kStage = 2048;
-constexpr int kUnrollA = 4;
-
-struct NodeSmem {
-  float4 rec[2 * kStage];
-  int wbins[kNodeWarps][kBinStride];
-  int bins[kBinStride];
-  float scan[3][2 * kMaxBins * 7];
-  Task task, cont;
-  SplitResult sr;
-  float ax_cost[3];
-  int ax_c[3], ax_nl[3];
-  int wleft[kNodeWarps];
-  float acc[kNodeWarps][24];
-  float fin[24];
-  int have, have_cont;
-};
-
-__device__ __forceinline__ float4 ld_rec(bool staged, const float4* srec, const float4* grec, int k) {
-  return staged ? srec[k] : __ldcg(grec + k);
-}
-
-__global__ void __launch_bounds__(kNodeBlock) k_nodes(BuildArgs A) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  NodeSmem& S = *reinterpret_cast<NodeSmem*>(smem_raw);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int K = A.K;
-  if (tid == 0) S.have_cont = 0;
-  __syncthreads();
+__device__ void mid_loop(const BuildArgs& A, MidWarp& W, int epoch) {
+  const int lane = threadIdx.x & 31;
+  WarpStats ws{0, 0, 0, 0};
+  Task cont;
+  bool have_cont = false;
   for (;;) {
-    if (tid == 0) {
-      S.have = 0;
-      if (S.have_cont) {
-        S.task = S.cont;
-        S.have_cont = 0;
-        S.have = 1;
-      } else if (A.ctl->status == 0) {
-        const int s = atomicAdd(&A.ctl->qa_head, 1);
-        int seen = -1;
-        for (int it = 0;; ++it) {
-          if (s < A.ctl->qa_cap && *(volatile int*)&A.qa_ready[s]) {
-            __threadfence();
-            S.task = load_task_cg(&A.qa[s]);
-            S.have = 1;
-            break;
-          }
-          if (*(volatile int*)&A.ctl->qa_pending == 0 || *(volatile int*)&A.ctl->status != 0) break;
-          const int tail = *(volatile int*)&A.ctl->qa_tail;
-          if (tail != seen) {  // the queue moved: restart the no-progress budget
-            seen = tail;
-            it = 0;
-          }
-          if (it > kSpinLimit) {
-            set_status(A.ctl, kStQueueTimeout, 1);
-            break;
-          }
-          __nanosleep(128);
-        }
-      }
+    Task t;
+    if (have_cont) {
+      t = cont;
+      have_cont = false;
+    } else if (!claim_task(A, epoch, t)) {
+      break;
     }
-    __syncthreads();
-    if (!S.have) return;
-    const Task t = S.task;
     const int par = t.pad & 1;
-    // records of this range were written by other CTAs of this kernel: global
-    // reads go through L2 (ld.global.cg), never a stale L1 line
-    const float4* grec = A.rec[par] + 2 * (size_t)t.begin;
-    float4* dst = A.rec[par ^ 1] + 2 * (size_t)t.begin;
-    const bool staged = t.count <= kStage;
-    if (staged)
-      for (int k0 = tid; k0 < 2 * t.count; k0 += 4 * kNodeBlock) {
-        float4 v[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          if (k0 + j * kNodeBlock < 2 * t.count) v[j] = __ldcg(grec + k0 + j * kNodeBlock);
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          if (k0 + j * kNodeBlock < 2 * t.count) S.rec[k0 + j * kNodeBlock] = v[j];
-      }
-    const int seg = (t.count + kNodeWarps - 1) / kNodeWarps;
-    const int sb = min(warp * seg, t.count), se = min(sb + seg, t.count);
-    float cmin[3], scl[3];
-    for (int a = 0; a < 3; ++a) {
-      cmin[a] = t.clo[a];
-      scl[a] = bin_scale(t.clo[a], t.chi[a], K);
+    if (t.begin < 0 || t.count < 1 || t.begin > A.n - t.count) {
+      if (lane == 0) set_status(A.ctl, kStBadSplit, 5);
+    } else if (t.count <= A.max_leaf) {
+      // a leaf made by a top level whose records sit in buffer 1
+      if (par)
+        for (int k = lane; k < 2 * t.count; k += 32)
+          A.rec[0][2 * (size_t)t.begin + k] = __ldcg(A.rec[1] + 2 * (size_t)t.begin + k);
+    } else if (t.count <= kMicro) {
+      micro_task(A, t.begin, t.count, par, t.parent, t.side, t.depth, epoch, ws);
+    } else {
+      mid_split(A, W, t, epoch, ws, cont, have_cont);
     }
-    // 1. bin
-    bins_zero(&S.wbins[0][0], K, kNodeWarps, tid, kNodeBlock);
-    __syncthreads();
-    {
-      const int c = (se - sb + 31) >> 5;
-      const int lb = sb + lane * c, le = min(lb + c, se);
-      for (int k0 = lb; k0 < le; k0 += kUnrollA) {
-        float4 lo[kUnrollA], hi[kUnrollA];
-#pragma unroll
-        for (int j = 0; j < kUnrollA; ++j)
-          if (k0 + j < le) {
-            lo[j] = ld_rec(staged, S.rec, grec, 2 * (k0 + j));
-            hi[j] = ld_rec(staged, S.rec, grec, 2 * (k0 + j) + 1);
-          }
-#pragma unroll
-        for (int j = 0; j < kUnrollA; ++j)
-          if (k0 + j < le) bins_add(S.wbins[warp], K, cmin, scl, lo[j], hi[j]);
-      }
-    }
-    __syncthreads();
-    for (int q = tid; q < 3 * K * 7; q += kNodeBlock) {
-      const int ent = q / 7, f = q - ent * 7;
-      const int e = ent * kBinEnt + f;
-      int v = S.wbins[0][e];
-      for (int w = 1; w < kNodeWarps; ++w) {
-        const int x = S.wbins[w][e];
-        v = f == 0 ? v + x : (f <= 3 ? min(v, x) : max(v, x));
-      }
-      S.bins[e] = v;
-    }
-    __syncthreads();
-    // 2. Eq. 2 at every plane, one warp per axis
-    if (warp < 3) {
-      float best = INFINITY;
-      int bestc = INT_MAX, bestnl = 0;
-      if (scl[warp] > 0.f) warp_axis_best(S.bins, K, t.count, warp, A.cp, S.scan[warp], &best, &bestc, &bestnl);
-      if (lane == 0) {
-        S.ax_cost[warp] = best;
-        S.ax_c[warp] = bestc;
-        S.ax_nl[warp] = bestnl;
-      }
-    }
-    __syncthreads();
-    if (tid == 0) {
-      float best = INFINITY;
-      int bestc = INT_MAX, bestnl = 0;
-      for (int a = 0; a < 3; ++a)
-        if (S.ax_cost[a] < best || (S.ax_cost[a] == best && S.ax_c[a] < bestc)) {
-          best = S.ax_cost[a];
-          bestc = S.ax_c[a];
-          bestnl = S.ax_nl[a];
-        }
-      S.sr = make_split(K, t.count, best, bestc, bestnl);
-    }
-    __syncthreads();
-    const SplitResult sr = S.sr;
-    // 3. lefts per warp segment (kUnrollA chunks of 32 in flight)
-    int nleft = 0;
-    for (int k0 = sb; k0 < se; k0 += 32 * kUnrollA) {
-      float4 lo[kUnrollA], hi[kUnrollA];
-#pragma unroll
-      for (int j = 0; j < kUnrollA; ++j) {
-        const int k = k0 + 32 * j + lane;
-        if (k < se) {
-          lo[j] = ld_rec(staged, S.rec, grec, 2 * k);
-          hi[j] = ld_rec(staged, S.rec, grec, 2 * k + 1);
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < kUnrollA; ++j) {
-        const int k = k0 + 32 * j + lane;
-        nleft += __popc(__ballot_sync(0xffffffffu, k < se && goes_left(lo[j], hi[j], sr, k, cmin, scl, K)));
-      }
-    }
-    if (lane == 0) S.wleft[warp] = nleft;
-    __syncthreads();
-    int lbase = 0;
-    for (int w = 0; w < warp; ++w) lbase += S.wleft[w];
-    int rbase = sb - lbase;  // rights before this segment
-    // 4. stable scatter into the other buffer, accumulating child bounds
-    Acc acc;
-    acc.init();
-    for (int k0 = sb; k0 < se; k0 += 32 * kUnrollA) {
-      float4 lo[kUnrollA], hi[kUnrollA];
-#pragma unroll
-      for (int j = 0; j < kUnrollA; ++j) {
-        const int k = k0 + 32 * j + lane;
-        if (k < se) {
-          lo[j] = ld_rec(staged, S.rec, grec, 2 * k);
-          hi[j] = ld_rec(staged, S.rec, grec, 2 * k + 1);
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < kUnrollA; ++j) {
-        const int c0 = k0 + 32 * j;
-        if (c0 >= se) break;
-        const int k = c0 + lane;
-        const bool valid = k < se;
-        const bool left = valid && goes_left(lo[j], hi[j], sr, k, cmin, scl, K);
-        const unsigned m = __ballot_sync(0xffffffffu, left);
-        const int rank = __popc(m & ((1u << lane) - 1u));
-        if (valid) {
-          const int d = left ? lbase + rank : sr.nl + rbase + (lane - rank);
-          dst[2 * d] = lo[j];
-          dst[2 * d + 1] = hi[j];
-          acc.add(left ? 0 : 1, lo[j], hi[j]);
-        }
-        const int tot = __popc(m);
-        lbase += tot;
-        rbase += min(32, se - c0) - tot;
-      }
-    }
-    acc.warp_reduce();
-    if (lane == 0)
-      for (int k = 0; k < 24; ++k) S.acc[warp][k] = acc.v[k];
-    __syncthreads();
-    if (tid < 24) {
-      const bool is_min = (tid % 12) < 3 || ((tid % 12) >= 6 && (tid % 12) < 9);
-      float v = S.acc[0][tid];
-      for (int w = 1; w < kNodeWarps; ++w) v = is_min ? fminf(v, S.acc[w][tid]) : fmaxf(v, S.acc[w][tid]);
-      S.fin[tid] = v;
-    }
-    if (warp == kNodeWarps - 1 && lane == 0 && lbase != sr.nl) set_status(A.ctl, kStBadSplit, 1);
-    // leaves keep their records in buffer 0
-    if (par == 0) {
-      const int ln = sr.nl, rn = t.count - sr.nl;
-      if (ln <= A.max_leaf)
-        for (int k = tid; k < 2 * ln; k += kNodeBlock) A.rec[0][2 * (size_t)t.begin + k] = __ldcg(dst + k);
-      if (rn <= A.max_leaf)
-        for (int k = tid; k < 2 * rn; k += kNodeBlock)
-          A.rec[0][2 * ((size_t)t.begin + ln) + k] = __ldcg(dst + 2 * ln + k);
-    }
-    __syncthreads();
-    // 5. node + children: the larger big child stays here, the rest is handed out
-    if (tid == 0) {
-      Task out[2];
-      int nout;
-      emit_node(A, t, sr.nl, S.fin, out, &nout);
-      int keep = -1;
-      for (int i = 0; i < nout; ++i) {
-        out[i].pad = par ^ 1;
-        if (out[i].count > kMicro && (keep < 0 || out[i].count > out[keep].count)) keep = i;
-      }
-      for (int i = 0; i < nout; ++i) {
-        if (i == keep) continue;
-        if (out[i].count > kMicro)
-          push_a(A, out[i]);
-        else
-          push_b(A, out[i]);
-      }
-      if (keep >= 0) {
-        S.cont = out[keep];
-        S.have_cont = 1;
-        atomicAdd(&A.ctl->qa_pending, 1);
-      }
+    __syncwarp();
+    if (!have_cont && lane == 0) {
       __threadfence();
       atomicSub(&A.ctl->qa_pending, 1);
     }
-    __syncthreads();
+  }
+  if (lane == 0) {
+    if (ws.n_int) atomicAdd(&A.ctl->n_internal, ws.n_int);
+    if (ws.n_leaf) atomicAdd(&A.ctl->n_leaves, ws.n_leaf);
+    if (ws.big) atomicMax(&A.ctl->max_leaf_size, ws.big);
+    if (ws.deep) atomicMax(&A.ctl->depth2, ws.deep);
   }
 }
 
-// One warp per micro task: the subtree of a node of at most kMicro triangles.
-template <int E>
-__device__ __forceinline__ void micro_task(const BuildArgs& A, const Task& t) {
-  const int lane = threadIdx.x & 31;
-  const int par = t.pad & 1;
-  float4 lo[E], hi[E];
-#pragma unroll
-  for (int i = 0; i < E; ++i) {
-    const int q = E * lane + i;
-    lo[i] = hi[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (q < t.count) {
-      const float4* g = A.rec[par] + 2 * ((size_t)t.begin + q);
-      lo[i] = g[0];
-      hi[i] = g[1];
-      if (par) {  // the final record order lives in buffer 0
-        A.rec[0][2 * ((size_t)t.begin + q)] = lo[i];
-        A.rec[0][2 * ((size_t)t.begin + q) + 1] = hi[i];
-      }
-    }
-  }
-  micro_build<E>(A, lo, hi, t.count, t.begin, t.parent, t.side, t.depth);
-}
-
-__global__ void __launch_bounds__(256) k_micro(BuildArgs A) {
-  const int nwarps = gridDim.x * (blockDim.x >> 5);
-  const int total = min(*(volatile int*)&A.ctl->qb_count, A.ctl->qb_cap);
-  for (int ti = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); ti < total; ti += nwarps) {
-    const Task t = A.qb[ti];
-    if (t.count <= 32)
-      micro_task<1>(A, t);
-    else if (t.count <= 64)
-      micro_task<2>(A, t);
-    else
-      micro_task<4>(A, t);
-  }
-}
-
-// ------------------------------------------------------------------ collapse
-struct CollapseArgs {
-  const Node2* node2;
-  WNode* wide;
-  BuildCtl* ctl;
-  int4* q;
-  int* ready;
-  int cap;
-  int n_tri;  // binary node ids are < n_tri - 1; anything else is a broken link
+// The split phase: the first top_ctas CTAs work the chunk items of big nodes
+// (CTA per item) and then join the others, whose warps take the mid-level
+// queue (warp per node).  Both run at once, so small subtrees proceed while
+// the big nodes of other branches are still being split.
+union SplitSmem {
+  TopSmem top;
+  MidSmem mid;
 };
 
-// A binary child link is usable only if it is a leaf or a valid node id.
-__device__ __forceinline__ bool link_ok(int ref, int n_tri) { return ref < 0 || ref < n_tri - 1; }
-
-__global__ void k_collapse_init(CollapseArgs C) {
-  if (threadIdx.x || blockIdx.x) return;
-  int r = C.ctl->root_ref;
-  C.ctl->n_wide = 1;
-  C.ctl->depth_wide = 1;
-  C.ctl->qc_tail = 0;
-  if (r < 0) {  // the whole scene is one leaf (or empty)
-    WNode w;
-    float inf = INFINITY;
-    w.lox = w.loy = w.loz = make_float4(inf, inf, inf, inf);
-    w.hix = w.hiy = w.hiz = make_float4(-inf, -inf, -inf, -inf);
-    w.child = make_int4(INT_MIN, INT_MIN, INT_MIN, INT_MIN);
-    if (r != INT_MIN && leaf_count(r) > 0) {
-      float lo[3], hi[3];
-      for (int a = 0; a < 3; ++a) {
-        lo[a] = iford(C.ctl->scene_lo[a]);
-        hi[a] = iford(C.ctl->scene_hi[a]);
-      }
-      w.lox.x = lo[0];
-      w.loy.x = lo[1];
-      w.loz.x = lo[2];
-      w.hix.x = hi[0];
-      w.hiy.x = hi[1];
-      w.hiz.x = hi[2];
-      w.child.x = r;
-    }
-    w.meta = make_int4(-1, 0, 0, 0);
-    C.wide[0] = w;
-    return;
+__global__ void __launch_bounds__(kBlock, 2) k_split(BuildArgs A) {
+  pdl_wait();
+  pdl_launch();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SplitSmem& S = *reinterpret_cast<SplitSmem*>(smem_raw);
+  const int epoch = __ldcg(&A.ctl->epoch);
+  if ((int)blockIdx.x < A.top_ctas) {
+    top_loop(A, S.top, epoch);
+    __syncthreads();
   }
-  if (!link_ok(r, C.n_tri)) {
-    set_status(C.ctl, kStBadSplit, 13);
-    return;
-  }
-  C.q[0] = make_int4(r, 0, -1, 0);  // (binary node, -, parent wide node, slot)
-  C.ctl->qc_tail = 1;
+  mid_loop(A, S.mid.w[threadIdx.x >> 5], epoch);
 }
 
+// ------------------------------------------------------------------ traversal nodes + leaf order
 __device__ __forceinline__ void child_of(const Node2& n, int s, int* ref, float3* lo, float3* hi) {
-  float4 l = s == 0 ? n.a_lo : n.b_lo, h = s == 0 ? n.a_hi : n.b_hi;
+  const float4 l = s == 0 ? n.a_lo : n.b_lo, h = s == 0 ? n.a_hi : n.b_hi;
   *ref = __float_as_int(l.w);
   *lo = make_float3(l.x, l.y, l.z);
   *hi = make_float3(h.x, h.y, h.z);
 }
 
-// Binary tree -> 4-wide nodes, top-down, one level of the wide tree at a
-// time in a single CTA.  Queue item i becomes wide node i: a wide node opens
-// the internal child of largest surface area until it has 4 children; its
-// internal children are appended to the queue at positions from a block
-// scan, so the layout is breadth-first and the same on every run.
-constexpr int kCollapseThreads = 1024;
+__device__ __forceinline__ Node2 load_node_cg(const Node2* p) {
+  const float4* q = reinterpret_cast<const float4*>(p);
+  Node2 n;
+  n.a_lo = __ldcg(q);
+  n.a_hi = __ldcg(q + 1);
+  n.b_lo = __ldcg(q + 2);
+  n.b_hi = __ldcg(q + 3);
+  return n;
+}
 
-__global__ void __launch_bounds__(kCollapseThreads) k_collapse(CollapseArgs C) {
-  __shared__ int s_warp[kCollapseThreads / 32];
-  __shared__ int s_tail;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (C.ctl->qc_tail == 0) return;  // leaf root: done by k_collapse_init
-  int lb = 0, le = 1, depth = 1;
-  if (tid == 0) s_tail = 1;
-  __syncthreads();
-  while (lb < le) {
-    for (int c0 = lb; c0 < le; c0 += kCollapseThreads) {
-      const int i = c0 + tid;
-      const bool valid = i < le;
-      int ref[kWidth];
-      float3 lo[kWidth], hi[kWidth];
-      int m = 0;
-      int4 item = make_int4(0, 0, 0, 0);
-      if (valid) {
-        item = __ldcg(&C.q[i]);
-        Node2 n = C.node2[item.x];
-        child_of(n, 0, &ref[0], &lo[0], &hi[0]);
-        child_of(n, 1, &ref[1], &lo[1], &hi[1]);
-        m = 2;
-        for (int q = 0; q < 2; ++q)
-          if (!link_ok(ref[q], C.n_tri)) {
-            set_status(C.ctl, kStBadSplit, 11);
-            ref[q] = INT_MIN;
-          }
-        while (m < kWidth) {
-          int pick = -1;
-          float best = -1.f;
-          for (int q = 0; q < m; ++q)
-            if (ref[q] >= 0) {
-              const float ar = area(lo[q], hi[q]);
-              if (ar > best) {
-                best = ar;
-                pick = q;
-              }
-            }
-          if (pick < 0) break;
-          Node2 g = C.node2[ref[pick]];
-          child_of(g, 1, &ref[m], &lo[m], &hi[m]);
-          child_of(g, 0, &ref[pick], &lo[pick], &hi[pick]);
-          for (int q : {pick, m})
-            if (!link_ok(ref[q], C.n_tri)) {
-              set_status(C.ctl, kStBadSplit, 12);
-              ref[q] = INT_MIN;
-            }
-          ++m;
-        }
-      }
-      // positions of this chunk's internal children: block exclusive scan
-      int cnt = 0;
-      for (int q = 0; q < m; ++q) cnt += ref[q] >= 0 ? 1 : 0;
-      int x = cnt;
-      for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-      }
-      if (lane == 31) s_warp[warp] = x;
-      __syncthreads();
-      int base = 0, total = 0;
-      for (int w = 0; w < kCollapseThreads / 32; ++w) {
-        const int v = s_warp[w];
-        if (w < warp) base += v;
-        total += v;
-      }
-      const int tail0 = s_tail;
-      int pos = tail0 + base + x - cnt;
-      if (valid) {
-        float lx[4], ly[4], lz[4], hx[4], hy[4], hz[4];
-        int ch[4];
-        for (int q = 0; q < kWidth; ++q) {
-          if (q < m && ref[q] != INT_MIN) {
-            lx[q] = lo[q].x;
-            ly[q] = lo[q].y;
-            lz[q] = lo[q].z;
-            hx[q] = hi[q].x;
-            hy[q] = hi[q].y;
-            hz[q] = hi[q].z;
-            if (ref[q] >= 0) {
-              if (pos >= C.cap) {
-                set_status(C.ctl, kStWideOverflow, 1);
-                ch[q] = INT_MIN;
-                continue;
-              }
-              C.q[pos] = make_int4(ref[q], 0, i, q);
-              ch[q] = pos++;
-            } else {
-              ch[q] = ref[q];
-            }
-          } else {
-            lx[q] = ly[q] = lz[q] = INFINITY;
-            hx[q] = hy[q] = hz[q] = -INFINITY;
-            ch[q] = INT_MIN;
-          }
-        }
-        WNode w;
-        w.lox = make_float4(lx[0], lx[1], lx[2], lx[3]);
-        w.hix = make_float4(hx[0], hx[1], hx[2], hx[3]);
-        w.loy = make_float4(ly[0], ly[1], ly[2], ly[3]);
-        w.hiy = make_float4(hy[0], hy[1], hy[2], hy[3]);
-        w.loz = make_float4(lz[0], lz[1], lz[2], lz[3]);
-        w.hiz = make_float4(hz[0], hz[1], hz[2], hz[3]);
-        w.child = make_int4(ch[0], ch[1], ch[2], ch[3]);
-        w.meta = make_int4(item.z, item.w, 0, 0);
-        C.wide[i] = w;
-      }
-      __syncthreads();
-      if (tid == 0) s_tail = tail0 + total;
-      __syncthreads();
+// A child reference is usable if it is a leaf or a node written by this build.
+__device__ __forceinline__ bool ref_ok(const BuildArgs& A, int ref, int epoch) {
+  if (ref == INT_MIN) return false;
+  if (ref < 0) return true;
+  return ref < A.n - 1 && __ldcg(&A.link2[ref]).y == epoch;
+}
+
+// The 4-wide node rooted at binary node x: open the internal child of
+// largest surface area until there are 4 children (the first of equal areas
+// wins; the opened node's children take its slot and the next free one).
+__device__ void make_wide(const BuildArgs& A, int x, int epoch) {
+  int ref[kWidth];
+  float3 lo[kWidth], hi[kWidth];
+  const Node2 nd = load_node_cg(A.node2 + x);
+  child_of(nd, 0, &ref[0], &lo[0], &hi[0]);
+  child_of(nd, 1, &ref[1], &lo[1], &hi[1]);
+  int m = 2;
+  for (int q = 0; q < 2; ++q)
+    if (!ref_ok(A, ref[q], epoch)) {
+      set_status(A.ctl, kStBadLink, 1);
+      ref[q] = INT_MIN;
     }
-    lb = le;
-    le = min(s_tail, C.cap);
-    if (lb < le) ++depth;
+  while (m < kWidth) {
+    int pick = -1;
+    float best = -1.f;
+    for (int q = 0; q < m; ++q)
+      if (ref[q] >= 0) {
+        const float ar = area(lo[q], hi[q]);
+        if (ar > best) {
+          best = ar;
+          pick = q;
+        }
+      }
+    if (pick < 0) break;
+    const Node2 g = load_node_cg(A.node2 + ref[pick]);
+    child_of(g, 1, &ref[m], &lo[m], &hi[m]);
+    child_of(g, 0, &ref[pick], &lo[pick], &hi[pick]);
+    for (int q : {pick, m})
+      if (!ref_ok(A, ref[q], epoch)) {
+        set_status(A.ctl, kStBadLink, 2);
+        ref[q] = INT_MIN;
+      }
+    ++m;
   }
-  if (tid == 0) {
-    C.ctl->n_wide = le;
-    C.ctl->depth_wide = depth;
-    C.ctl->qc_tail = le;
+  float lx[4], ly[4], lz[4], hx[4], hy[4], hz[4];
+  int ch[4];
+  for (int q = 0; q < kWidth; ++q) {
+    if (q < m && ref[q] != INT_MIN) {
+      lx[q] = lo[q].x;
+      ly[q] = lo[q].y;
+      lz[q] = lo[q].z;
+      hx[q] = hi[q].x;
+      hy[q] = hi[q].y;
+      hz[q] = hi[q].z;
+      ch[q] = ref[q];
+    } else {
+      lx[q] = ly[q] = lz[q] = INFINITY;
+      hx[q] = hy[q] = hz[q] = -INFINITY;
+      ch[q] = INT_MIN;
+    }
   }
+  WNode w;
+  w.lox = make_float4(lx[0], lx[1], lx[2], lx[3]);
+  w.hix = make_float4(hx[0], hx[1], hx[2], hx[3]);
+  w.loy = make_float4(ly[0], ly[1], ly[2], ly[3]);
+  w.hiy = make_float4(hy[0], hy[1], hy[2], hy[3]);
+  w.loz = make_float4(lz[0], lz[1], lz[2], lz[3]);
+  w.hiz = make_float4(hz[0], hz[1], hz[2], hz[3]);
+  w.child = make_int4(ch[0], ch[1], ch[2], ch[3]);
+  w.meta = make_int4(__ldcg(&A.link2[x]).x, 0, 0, 0);
+  A.wide[x] = w;
 }
 
-// Records in Morton order (the build's starting order).
-__global__ void k_make_recs(const float4* __restrict__ plo, const float4* __restrict__ phi,
-                            const int32_t* __restrict__ idx, int n, float4* __restrict__ rec) {
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-    int p = idx[k];
-    rec[2 * (size_t)k] = plo[p];
-    rec[2 * (size_t)k + 1] = phi[p];
+__global__ void __launch_bounds__(kBlock) k_post(BuildArgs A) {
+  pdl_wait();
+  pdl_launch();
+  const int n = A.n;
+  const int epoch = __ldcg(&A.ctl->epoch);
+  const int gt = blockIdx.x * kBlock + threadIdx.x, gs = gridDim.x * kBlock;
+  if (gt == 0) {
+    const int r = __ldcg(&A.ctl->root_ref);
+    if (r >= 0) {
+      A.ctl->wide_root = r;
+    } else {  // the whole scene is one leaf (or empty): a wrapper node in slot 0
+      WNode w;
+      const float inf = INFINITY;
+      w.lox = w.loy = w.loz = make_float4(inf, inf, inf, inf);
+      w.hix = w.hiy = w.hiz = make_float4(-inf, -inf, -inf, -inf);
+      w.child = make_int4(INT_MIN, INT_MIN, INT_MIN, INT_MIN);
+      if (r != INT_MIN && leaf_count(r) > 0) {
+        w.lox.x = uval(~__ldcg(&A.ctl->sb[0]));
+        w.loy.x = uval(~__ldcg(&A.ctl->sb[1]));
+        w.loz.x = uval(~__ldcg(&A.ctl->sb[2]));
+        w.hix.x = uval(__ldcg(&A.ctl->sb[3]));
+        w.hiy.x = uval(__ldcg(&A.ctl->sb[4]));
+        w.hiz.x = uval(__ldcg(&A.ctl->sb[5]));
+        w.child.x = r;
+      }
+      w.meta = make_int4(-1, 0, 0, 0);
+      A.wide[0] = w;
+      A.ctl->wide_root = 0;
+    }
   }
-}
-
-// Triangles in leaf order (the final record order carries the ids).
-__global__ void k_gather(const float4* __restrict__ tri_in, const float4* __restrict__ rec, int n,
-                         float4* __restrict__ tri_leaf, int32_t* __restrict__ order) {
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-    int p = __float_as_int(rec[2 * (size_t)k].w);
-    order[k] = p;
-    tri_leaf[3 * (size_t)k] = tri_in[3 * (size_t)p];
-    tri_leaf[3 * (size_t)k + 1] = tri_in[3 * (size_t)p + 1];
-    tri_leaf[3 * (size_t)k + 2] = tri_in[3 * (size_t)p + 2];
+  for (int i = gt; i < n; i += gs) {
+    const int p = __float_as_int(__ldcg(A.rec[0] + 2 * (size_t)i).w);
+    if (p < 0 || p >= n) {
+      set_status(A.ctl, kStBadSplit, 20);
+      continue;
+    }
+    A.order[i] = p;
+    A.tri_leaf[3 * (size_t)i] = A.tri[3 * (size_t)p];
+    A.tri_leaf[3 * (size_t)i + 1] = A.tri[3 * (size_t)p + 1];
+    A.tri_leaf[3 * (size_t)i + 2] = A.tri[3 * (size_t)p + 2];
+    if (i < n - 1 && __ldcg(&A.link2[i]).y == epoch) make_wide(A, i, epoch);
   }
-}
-
-// Elements per radix-sort block: at least one tile, about two blocks per SM.
-int sort_chunk(int n, int nsm) {
-  int c = (n + 2 * nsm - 1) / (2 * nsm);
-  c = (c + kSortBlock - 1) / kSortBlock * kSortBlock;
-  return c < 4 * kSortBlock ? 4 * kSortBlock : c;
 }
 
 int sm_count() {
@@ -1294,87 +1691,102 @@ int sm_count() {
   return n;
 }
 
+// Launch with programmatic stream serialization when `pdl` is set: the
+// kernel may start while its predecessor drains and waits for it in-kernel.
+template <typename... P, typename... Q>
+cudaError_t launch(void (*k)(P...), int grid, size_t smem, cudaStream_t st, bool pdl, Q... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kBlock);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 }  // namespace
+
+BuildGeom build_geometry(int64_t n, int nsm) {
+  BuildGeom g{};
+  const int64_t T = n < 1 ? 1 : n;
+  g.big = (int)std::max<int64_t>(kBigMin, (T + 4095) / 4096);
+  int64_t rpt = (T + (int64_t)nsm * 512 - 1) / ((int64_t)nsm * 512);
+  rpt = std::min<int64_t>(std::max<int64_t>(rpt, 1), kMaxRpt);
+  g.rpt = (int)rpt;
+  g.chunk = kBlock * g.rpt;
+  // Pools of one build (a full pool sends further big nodes to the warps,
+  // slower but correct).  Big nodes of one depth are disjoint, so there are at
+  // most T / big of them per depth; 16 depths' worth covers the uneven trees
+  // of alpha < 1.  Chunk counts: a big node reserves its chunks + 2 for its
+  // children; per depth that is at most T / chunk + 3 T / big, where
+  // T' / chunk(T') <= max(2 nsm, T / 1024) + 1 for every T' <= T.
+  const int64_t nb = (T + g.big - 1) / g.big;
+  const int64_t nc = std::max<int64_t>(2 * (int64_t)nsm, (T + 1023) / 1024) + 1;
+  g.cap_t = (int)(16 * nb + 256);
+  g.cap_c = (int)(16 * nc + 3 * (int64_t)g.cap_t + 64);
+  // pushes: at most one per binary node of more than max_leaf triangles plus
+  // one per leaf cut from a big node
+  g.qa_cap = (int)(2 * T + 16);
+  return g;
+}
 
 cudaError_t launch_build(rt_scene_s* s, const rt_build_params& p, cudaStream_t st) {
   const int n = (int)s->n_tri;
   const int nsm = sm_count();
-  const int qa_cap = n + 4;  // a peeling chain can make almost every node a tier-A task
-  const int qb_cap = n + 1;
-  const int qc_cap = n + 1;
-  cudaError_t e;
-  int n_launched = 0;
-  if ((e = cudaMemsetAsync(s->ctl, 0, sizeof(BuildCtl), st))) return e;
-  if ((e = cudaMemsetAsync(s->qa_ready, 0, sizeof(int) * qa_cap, st))) return e;
-  k_init_ctl<<<1, 32, 0, st>>>(s->ctl, qa_cap, qb_cap, qc_cap);
-    ++n_launched;
-  if (n > 0) {
-    int g = (n + kPrepBlock - 1) / kPrepBlock;
-    g = g < nsm * 8 ? g : nsm * 8;
-    k_prep<<<g, kPrepBlock, 0, st>>>(s->tri_in, n, s->prim_lo, s->prim_hi, s->ctl);
-    ++n_launched;
-    k_morton<<<g, kPrepBlock, 0, st>>>(s->prim_lo, s->prim_hi, n, s->ctl, s->keys[0], s->idx[0]);
-    ++n_launched;
-    const int chunk = sort_chunk(n, nsm);
-    const int nb = (n + chunk - 1) / chunk;
-    for (int pass = 0; pass < 4; ++pass) {
-      int src = pass & 1, dst = src ^ 1;
-      k_sort_hist<<<nb, kSortBlock, 0, st>>>(s->keys[src], n, 8 * pass, s->sort_hist, nb, chunk);
-    ++n_launched;
-      k_sort_scan<<<1, 256, 0, st>>>(s->sort_hist, nb);
-    ++n_launched;
-      k_sort_scatter<<<nb, kSortBlock, 0, st>>>(s->keys[src], s->idx[src], s->keys[dst], s->idx[dst],
-                                                n, 8 * pass, s->sort_hist, nb, chunk);
-    ++n_launched;
-    }
-  }
-  if (n > 0) {
-    int g = (n + 255) / 256;
-    g = g < nsm * 8 ? g : nsm * 8;
-    k_make_recs<<<g, 256, 0, st>>>(s->prim_lo, s->prim_hi, s->idx[0], n, s->rec[0]);
-    ++n_launched;
-  }
-  k_root<<<1, 32, 0, st>>>(s->ctl, s->qa, s->qa_ready, s->qb, n, p.max_leaf, s->node2);
-  ++n_launched;
+  const BuildGeom g = build_geometry(n, nsm);
+  if (g.cap_t > s->geom.cap_t || g.cap_c > s->geom.cap_c || g.qa_cap > s->geom.qa_cap) return cudaErrorInvalidValue;
   BuildArgs A;
+  A.tri = s->tri_in;
   A.rec[0] = s->rec[0];
   A.rec[1] = s->rec[1];
   A.node2 = s->node2;
+  A.link2 = s->link2;
   A.ctl = s->ctl;
   A.qa = s->qa;
   A.qa_ready = s->qa_ready;
-  A.qb = s->qb;
+  A.ttask = s->top_task;
+  A.tdone = s->top_done;
+  A.tbins = s->top_bins;
+  A.tccnt = s->top_ccnt;
+  A.tscnt = s->top_scnt;
+  A.titem = s->top_item;
+  A.tready = s->top_ready;
+  A.wide = s->wide;
+  A.tri_leaf = s->tri_leaf;
+  A.order = s->idx[0];
+  A.epoch_dev = s->epoch;
+  A.n = n;
   A.K = p.bins;
   A.max_leaf = p.max_leaf;
+  A.big = g.big;
+  A.chunk = g.chunk;
+  A.rpt = g.rpt;
+  A.cap_t = s->geom.cap_t;
+  A.cap_c = s->geom.cap_c;
+  A.qa_cap = s->geom.qa_cap;
+  A.top_ctas = n > g.big ? nsm : 0;
   A.cp = CostP{p.alpha, p.t_i, p.t_trav, p.source[0], p.source[1], p.source[2], p.dist_norm};
-  if (n > kMicro) {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_nodes, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(NodeSmem));
-      attr = true;
-    }
-    k_nodes<<<nsm, kNodeBlock, sizeof(NodeSmem), st>>>(A);
-    ++n_launched;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(s->ctl, 0, sizeof(BuildCtl), st))) return e;
+  const int nch = (n + g.chunk - 1) / g.chunk;
+  int gp = (n + kBlock - 1) / kBlock;
+  gp = std::max(1, std::min(gp, nsm * 8));
+  static bool attr = false;
+  if (!attr) {
+    if ((e = cudaFuncSetAttribute(k_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SplitSmem))))
+      return e;
+    attr = true;
   }
-  if (n > p.max_leaf) {
-    k_micro<<<2 * nsm, 256, 0, st>>>(A);
-    ++n_launched;
-  }
-  CollapseArgs C{s->node2, s->wide, s->ctl, s->qc, s->qc_ready, qc_cap, n};
-  k_collapse_init<<<1, 32, 0, st>>>(C);
-  ++n_launched;
-  if (n > p.max_leaf) {
-    k_collapse<<<1, kCollapseThreads, 0, st>>>(C);
-    ++n_launched;
-  }
-  if (n > 0) {
-    int g = (n + 255) / 256;
-    g = g < nsm * 8 ? g : nsm * 8;
-    k_gather<<<g, 256, 0, st>>>(s->tri_in, s->rec[0], n, s->tri_leaf, s->idx[0]);
-    ++n_launched;
-  }
-  count_launches(n_launched);
-  return cudaGetLastError();
+  if ((e = launch(k_prep, gp, 0, st, false, A))) return e;
+  if ((e = launch(k_bin_root, std::max(1, std::min(nch, nsm * 4)), 0, st, true, A))) return e;
+  if ((e = launch(k_split, 2 * nsm, sizeof(SplitSmem), st, true, A))) return e;
+  if ((e = launch(k_post, gp, 0, st, true, A))) return e;
+  count_launches(4);
+  return cudaSuccess;
 }
 
 }  // namespace rt

@@ -138,6 +138,7 @@ __global__ void __launch_bounds__(kRayBlock) k_reflect_count(ReflectArgs A) {
   const long long i = blockIdx.x * (long long)kRayBlock + threadIdx.x;
   float4 h;
   const bool keep = i < n && survives(A, i, &h);
+  __syncwarp();
   const unsigned m = __ballot_sync(0xffffffffu, keep);
   if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = __popc(m);
   __syncthreads();
@@ -184,6 +185,7 @@ __global__ void __launch_bounds__(kRayBlock) k_reflect_scatter(ReflectArgs A) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float4 h = make_float4(0.f, 0.f, 0.f, 0.f);
   const bool keep = i < n && survives(A, i, &h);
+  __syncwarp();
   const unsigned m = __ballot_sync(0xffffffffu, keep);
   if (lane == 0) wsum[warp] = __popc(m);
   __syncthreads();

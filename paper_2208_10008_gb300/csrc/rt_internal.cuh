@@ -2,14 +2,15 @@
 //
 // Device data layout (all 16-byte aligned, in HBM):
 //   tri_in    float4[3T]  input-order triangles: (v0.xyz, id) (v1.xyz, 0) (v2.xyz, 0)
-//   prim_lo   float4[T]   per-triangle AABB min (w unused)      -- Eq. 3 boxes
-//   prim_hi   float4[T]   per-triangle AABB max
-//   keys/idx  u32/i32[T]  Morton keys and the triangle permutation (ping-pong pairs)
-//   rec       float4[2T]  build records (lo.xyz, id) (hi.xyz, 0), moved by every
-//                         partition so each pass reads them contiguously
+//   rec       float4[2T]  build records (lo.xyz, id) (hi.xyz, morton key): the Eq. 3
+//                         box of a triangle; every partition moves them so each
+//                         node's records are contiguous (ping-pong pair)
 //   node2     Node2[T]    binary tree of Sec. II.C / Fig. 1; internal node id =
 //                         (split position - 1), a unique slot for every split
-//   wide      WNode[T]    4-wide traversal nodes (one 128-byte line each)
+//   link2     int2[T]     (parent id, build epoch) of every binary node: the epoch
+//                         marks the nodes written by the latest build
+//   wide      WNode[T]    4-wide traversal nodes, one 128-byte line each, stored at
+//                         the id of the binary node they are rooted at
 //   tri_leaf  float4[3T]  triangles in leaf order, same packing as tri_in
 #pragma once
 
@@ -34,6 +35,7 @@ enum DevStatus : int {
   kStQueueOverflow = 2,  // more tasks than queue slots (cannot happen for a valid tree)
   kStBadSplit = 3,       // a partition disagreed with its bin counts
   kStWideOverflow = 4,   // more traversal nodes than allocated
+  kStBadLink = 5,        // a binary node refers to a node this build never wrote
 };
 
 // Leaf reference: -1 - (first * 16 + count); internal: >= 0.
@@ -52,7 +54,7 @@ struct __align__(16) Node2 {
 // 4-wide traversal node, 128 bytes: child i's box in component i of the six
 // float4 planes; child[i] = wide node index (>= 0), leaf ref (< 0, != INT_MIN)
 // or INT_MIN for an empty slot (whose box is lo = +inf, hi = -inf).
-// meta.x = parent wide node (-1 at the root), meta.y = slot in the parent.
+// meta.x = binary parent of the node's root (-1 at the root), rest unused.
 struct __align__(16) WNode {
   float4 lox, hix, loy, hiy, loz, hiz;
   int4 child;
@@ -68,22 +70,48 @@ struct __align__(16) Task {
   int32_t pad;
 };
 
+// A node of more than `big` triangles, split by several CTAs at once (one
+// per chunk of its range): its range, centroid bounds, its chunks' count
+// slots and what it reserved for its children (task slots, count slots).
+struct __align__(16) TopTask {
+  int32_t begin, count, parent, side;
+  float clo[3];
+  int32_t depth;
+  float chi[3];
+  int32_t nchunk;       // ceil(count / chunk)
+  int32_t chunk_first;  // count slots of this task's chunks (written by its parent's chunks)
+  int32_t child_slot;   // 2 task slots reserved for the children
+  int32_t chunk_res;    // nchunk + 2 count slots reserved for the children's chunks
+  int32_t parity;       // record buffer holding this task's range
+};
+
 // Device control block of one scene (zeroed at the start of every build).
 struct BuildCtl {
-  int status, status_where, pad0, pad1;
-  // tier-A queue (CTA per task)
-  int qa_head, qa_tail, qa_pending, qa_cap;
-  // tier-B list (warp per task)
-  int qb_count, qb_cap, pad2, pad3;
-  // collapse queue
-  int qc_head, qc_tail, qc_pending, qc_cap;
+  int status, status_where, epoch, wide_root;
+  // chunk items of top tasks (CTA per item)
+  int ti_head, ti_tail, ti_pending, pad0;
+  // pools of one build: top task slots, count slots
+  int t_slot_next, t_cnt_next, pad1, pad2;
+  // mid-level task queue (warp per task)
+  int qa_head, qa_tail, qa_pending, pad3;
   // tree facts
   int n_internal, n_leaves, depth2, max_leaf_size;
-  int n_wide, depth_wide, root_ref, pad4;
-  // scene bounds as ordered ints (see ford()): triangle AABB and centroid bounds
-  int scene_lo[3], scene_hi[3];
-  int cen_lo[3], cen_hi[3];
+  int root_ref, pad4, pad5, pad6;
+  // scene bounds, order-preserving unsigned codes, max-reduced (0 = empty):
+  // [0..2] ~code(box lo), [3..5] code(box hi), [6..8] ~code(centre lo), [9..11] code(centre hi)
+  unsigned sb[12];
 };
+
+// Launch geometry of a build of T triangles (host side; also sizes the buffers).
+struct BuildGeom {
+  int big;        // nodes of more than `big` triangles are split chunk-parallel
+  int chunk;      // records per chunk (one CTA's share of a big node)
+  int rpt;        // records per thread in a chunk (chunk / 256)
+  int cap_t;      // top task slots
+  int cap_c;      // count slots and chunk items
+  int qa_cap;     // mid-level queue slots
+};
+BuildGeom build_geometry(int64_t n_tri, int nsm);
 
 // Per-call trace scratch: counter + queue of flagged ray indices.
 struct TraceScratch {
@@ -145,21 +173,23 @@ struct rt_scene_s {
   int64_t n_tri = 0;
   int64_t cap_tri = 0;          // capacity of the per-triangle buffers
   float4* tri_in = nullptr;
-  float4* prim_lo = nullptr;
-  float4* prim_hi = nullptr;
-  uint32_t* keys[2] = {nullptr, nullptr};
-  int32_t* idx[2] = {nullptr, nullptr};  // idx[0] holds the leaf order after a build
-  float4* rec[2] = {nullptr, nullptr};   // primitive records (2 float4 each) + scratch
-  uint32_t* sort_hist = nullptr;  // radix-sort histograms
-  int64_t sort_hist_cap = 0;
+  int32_t* idx[2] = {nullptr, nullptr};  // idx[0]: input id of each leaf-order triangle
+  float4* rec[2] = {nullptr, nullptr};   // primitive records (2 float4 each), ping-pong
   rt::Node2* node2 = nullptr;
   rt::WNode* wide = nullptr;
+  int2* link2 = nullptr;        // (parent, epoch) per binary node
+  int* epoch = nullptr;         // build counter on the device
   float4* tri_leaf = nullptr;
-  rt::Task* qa = nullptr;       // tier-A queue
-  int* qa_ready = nullptr;
-  rt::Task* qb = nullptr;       // tier-B list
-  int4* qc = nullptr;           // collapse queue (bvh2 ref, wide id, parent, slot|depth)
-  int* qc_ready = nullptr;
+  rt::Task* qa = nullptr;       // mid-level task queue
+  int* qa_ready = nullptr;      // epoch stamp of each filled queue slot
+  rt::TopTask* top_task = nullptr;  // [cap_t] big nodes
+  int* top_done = nullptr;          // [cap_t] finished chunks of each
+  unsigned* top_bins = nullptr;     // [cap_t][3 * kMaxBins * 13] merged bins
+  unsigned* top_ccnt = nullptr;     // [cap_c][3 * kMaxBins] per-chunk bin counts
+  unsigned* top_scnt = nullptr;     // [cap_c][3 * kMaxBins] per 32-chunk group counts
+  int2* top_item = nullptr;         // [cap_c] chunk items (task slot, chunk index)
+  int* top_ready = nullptr;         // [cap_c] epoch stamp of each published item
+  rt::BuildGeom geom{};             // geometry the buffers were sized for
   rt::BuildCtl* ctl = nullptr;
   rt::TraceScratch scratch;     // default trace scratch
   rt::TraceScratch host_scr[2]; // scratch of the host-buffer pipeline

@@ -62,43 +62,54 @@ __global__ void k_pack(const float* __restrict__ raw, int n, float4* __restrict_
 }
 
 void free_scene_buffers(rt_scene_s* s) {
-  void* ptrs[] = {s->tri_in, s->prim_lo, s->prim_hi, s->keys[0], s->keys[1], s->idx[0], s->idx[1],
-                  s->rec[0], s->rec[1],
-                  s->sort_hist, s->node2, s->wide, s->tri_leaf, s->qa, s->qa_ready, s->qb, s->qc,
-                  s->qc_ready, s->ctl, s->scratch.counter, s->scratch.queue, s->scratch.cand,
+  void* ptrs[] = {s->tri_in, s->idx[0], s->idx[1], s->rec[0], s->rec[1], s->node2, s->wide, s->link2, s->epoch,
+                  s->tri_leaf, s->qa, s->qa_ready, s->top_task, s->top_done, s->top_bins, s->top_ccnt,
+                  s->top_scnt, s->top_item, s->top_ready, s->ctl, s->scratch.counter, s->scratch.queue, s->scratch.cand,
                   s->host_scr[0].counter, s->host_scr[0].queue, s->host_scr[0].cand,
-                  s->host_scr[1].counter, s->host_scr[1].queue, s->host_scr[1].cand, s->reflect_blocks, s->stage_rays[0], s->stage_rays[1], s->stage_hits[0],
-                  s->stage_hits[1]};
+                  s->host_scr[1].counter, s->host_scr[1].queue, s->host_scr[1].cand, s->reflect_blocks,
+                  s->stage_rays[0], s->stage_rays[1], s->stage_hits[0], s->stage_hits[1]};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
 
-// Size every per-triangle buffer for n triangles (grow only).
+int sm_count_dev() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 1;
+}
+
+// Size every per-triangle buffer for n triangles (grow only).  Buffers whose
+// old contents must never match a new build's epoch start zeroed.
 int ensure_capacity(rt_scene_s* s, int64_t n) {
   if (n <= s->cap_tri && s->ctl) return RT_OK;
   const int64_t m = n < 1 ? 1 : n;
+  const rt::BuildGeom g = rt::build_geometry(m, sm_count_dev());
   RT_CUDA(dev_alloc(&s->tri_in, 3 * m), "alloc triangles");
-  RT_CUDA(dev_alloc(&s->prim_lo, m), "alloc bounds");
-  RT_CUDA(dev_alloc(&s->prim_hi, m), "alloc bounds");
-  for (int k = 0; k < 2; ++k) {
-    RT_CUDA(dev_alloc(&s->keys[k], m), "alloc keys");
-    RT_CUDA(dev_alloc(&s->idx[k], m), "alloc index");
-    RT_CUDA(dev_alloc(&s->rec[k], 2 * m), "alloc build records");
-  }
-  // radix-sort histograms: 256 counters per block, blocks = ceil(n / chunk) with
-  // chunk >= 256 (the build never uses more than n / 256 + 1 blocks)
-  const int64_t nb = m / 256 + 2;
-  RT_CUDA(dev_alloc(&s->sort_hist, 256 * nb), "alloc sort histogram");
+  RT_CUDA(dev_alloc(&s->idx[0], m), "alloc index");
+  for (int k = 0; k < 2; ++k) RT_CUDA(dev_alloc(&s->rec[k], 2 * m), "alloc build records");
   RT_CUDA(dev_alloc(&s->node2, m), "alloc binary nodes");
+  RT_CUDA(dev_alloc(&s->link2, m), "alloc binary links");
+  RT_CUDA(cudaMemset(s->link2, 0, sizeof(int2) * m), "clear binary links");
   RT_CUDA(dev_alloc(&s->wide, m + 1), "alloc wide nodes");
   RT_CUDA(dev_alloc(&s->tri_leaf, 3 * m), "alloc leaf triangles");
-  const int64_t qa_cap = m + 4;
-  RT_CUDA(dev_alloc(&s->qa, qa_cap), "alloc task queue");
-  RT_CUDA(dev_alloc(&s->qa_ready, qa_cap), "alloc task queue");
-  RT_CUDA(dev_alloc(&s->qb, m + 1), "alloc task list");
-  RT_CUDA(dev_alloc(&s->qc, m + 1), "alloc collapse queue");
-  RT_CUDA(dev_alloc(&s->qc_ready, m + 1), "alloc collapse queue");
+  RT_CUDA(dev_alloc(&s->qa, g.qa_cap), "alloc task queue");
+  RT_CUDA(dev_alloc(&s->qa_ready, g.qa_cap), "alloc task queue");
+  RT_CUDA(cudaMemset(s->qa_ready, 0, sizeof(int) * g.qa_cap), "clear task queue");
+  RT_CUDA(dev_alloc(&s->top_task, (size_t)g.cap_t), "alloc top tasks");
+  RT_CUDA(dev_alloc(&s->top_done, (size_t)g.cap_t), "alloc top tasks");
+  RT_CUDA(dev_alloc(&s->top_bins, (size_t)g.cap_t * 3 * rt::kMaxBins * 13), "alloc top bins");
+  RT_CUDA(dev_alloc(&s->top_ccnt, (size_t)g.cap_c * 3 * rt::kMaxBins), "alloc top counts");
+  RT_CUDA(dev_alloc(&s->top_scnt, (size_t)g.cap_c * 3 * rt::kMaxBins), "alloc top counts");
+  RT_CUDA(dev_alloc(&s->top_item, (size_t)g.cap_c), "alloc top items");
+  RT_CUDA(dev_alloc(&s->top_ready, (size_t)g.cap_c), "alloc top items");
+  RT_CUDA(cudaMemset(s->top_ready, 0, sizeof(int) * g.cap_c), "clear top items");
+  if (!s->epoch) {
+    RT_CUDA(cudaMalloc((void**)&s->epoch, sizeof(int)), "alloc epoch");
+    RT_CUDA(cudaMemset(s->epoch, 0, sizeof(int)), "clear epoch");
+  }
   if (!s->ctl) RT_CUDA(cudaMalloc((void**)&s->ctl, sizeof(rt::BuildCtl)), "alloc control block");
+  s->geom = g;
   s->cap_tri = m;
   return RT_OK;
 }
@@ -245,9 +256,7 @@ int rt_bvh_info(rt_scene s, void* stream, rt_bvh_info_t* info) {
   info->n_tri = s->n_tri;
   info->n_bvh2_internal = c.n_internal;
   info->n_leaves = c.n_leaves;
-  info->n_wide = c.n_wide;
   info->depth2 = c.depth2;
-  info->depth_wide = c.depth_wide;
   info->max_leaf_size = c.max_leaf_size;
   info->status = c.status;
   float ms = 0.f;
@@ -257,6 +266,25 @@ int rt_bvh_info(rt_scene s, void* stream, rt_bvh_info_t* info) {
   }
   info->build_ms = ms;
   if (c.status != 0) return fail(RT_EINTERNAL, "device status %d at %d", c.status, c.status_where);
+  // traversal nodes reachable from the root, and their depth
+  const int64_t slots = s->n_tri > 1 ? s->n_tri : 1;
+  std::vector<rt::WNode> w((size_t)slots);
+  RT_CUDA(cudaMemcpy(w.data(), s->wide, sizeof(rt::WNode) * slots, cudaMemcpyDeviceToHost), "read wide nodes");
+  std::vector<std::pair<int32_t, int32_t>> st{{c.wide_root, 1}};
+  int64_t nw = 0;
+  int32_t dw = 0;
+  while (!st.empty()) {
+    const auto it = st.back();
+    st.pop_back();
+    if (it.first < 0 || it.first >= slots || nw > slots) return fail(RT_EINTERNAL, "bad wide node %d", it.first);
+    ++nw;
+    if (it.second > dw) dw = it.second;
+    const int32_t ch[4] = {w[it.first].child.x, w[it.first].child.y, w[it.first].child.z, w[it.first].child.w};
+    for (int k = 0; k < 4; ++k)
+      if (ch[k] >= 0) st.push_back({ch[k], it.second + 1});
+  }
+  info->n_wide = nw;
+  info->depth_wide = dw;
   return RT_OK;
 }
 

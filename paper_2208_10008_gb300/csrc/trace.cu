@@ -16,8 +16,10 @@
 //     else, a second hit within the error window of the best one, a hit near
 //     tmin / tmax, or a stack overflow marks the ray for k_retest64.
 // k_retest64 (float64, one flagged ray per thread)
-//   * a stackless walk of the same tree (parent links), the same conservative
-//     float32 box test culled at the float64 best distance, and for every
+//   * the float64 rule on the ray's candidate triangles, or, when the list
+//     overflowed, a stackless walk of the binary tree (parent links) with the
+//     same conservative float32 box test culled at the float64 best
+//     distance, and for every
 //     triangle the float32 bound does not prove missed, the reference hit
 //     rule: Moller-Trumbore with inclusive edges, |det| <= 1e-14 |e1||e2||d|
 //     is parallel, tmin < t < tmax, lowest id on equal t, with the operation
@@ -231,6 +233,20 @@ __device__ __forceinline__ unsigned slab4(const WNode* __restrict__ node, const 
   return mask;
 }
 
+// The same conservative slab test for one box (lo, hi) of a binary node.
+__device__ __forceinline__ bool slab1(float4 lo, float4 hi, const RayPre& r, float bound) {
+  const float nx = r.ix >= 0.f ? lo.x : hi.x, fx = r.ix >= 0.f ? hi.x : lo.x;
+  const float ny = r.iy >= 0.f ? lo.y : hi.y, fy = r.iy >= 0.f ? hi.y : lo.y;
+  const float nz = r.iz >= 0.f ? lo.z : hi.z, fz = r.iz >= 0.f ? hi.z : lo.z;
+  float t0 = fmaxf(fmaxf(__fmul_rn(__fsub_rn(nx, r.ox), r.ix), __fmul_rn(__fsub_rn(ny, r.oy), r.iy)),
+                   __fmul_rn(__fsub_rn(nz, r.oz), r.iz));
+  float t1 = fminf(fminf(__fmul_rn(__fsub_rn(fx, r.ox), r.ix), __fmul_rn(__fsub_rn(fy, r.oy), r.iy)),
+                   __fmul_rn(__fsub_rn(fz, r.oz), r.iz));
+  t0 = t0 - fabsf(t0) * kWiden;
+  t1 = t1 + fabsf(t1) * kWiden;
+  return t0 <= t1 && t0 <= bound && t1 >= r.tmin;
+}
+
 __device__ __forceinline__ void cswap(float& ta, int& ra, float& tb, int& rb) {
   if (tb < ta) {
     float t = ta;
@@ -259,6 +275,11 @@ __device__ __forceinline__ int enqueue_flag(int* counter, int* queue, int qcap, 
 
 struct TraceArgs {
   const WNode* wide;
+  const int* wide_root;  // device word: index of the root traversal node
+  const Node2* node2;
+  const int2* link2;     // (parent, epoch) of every binary node
+  const int* root_ref;   // device word: binary root (leaf ref if the root is a leaf)
+  int n_tri;             // binary node ids are < n_tri - 1
   const float4* tris;
   const rt_ray* rays;
   int n;
@@ -315,7 +336,7 @@ __global__ void __launch_bounds__(kTraceBlock) k_trace(TraceArgs A) {
     }
   };
   if (r.valid) {
-    st_ref[0] = 0;
+    st_ref[0] = __ldg(A.wide_root);
     st_t[0] = -INFINITY;
     sp = 1;
   }
@@ -504,52 +525,67 @@ __global__ void __launch_bounds__(kRetestBlock) k_retest64(TraceArgs A) {
         }
       }
     }
-    int node = 0, slot = 0;
-    // Without a complete candidate list: stackless walk (parent links) so that any depth works.  Boxes use the
-    // same widened float32 slab test as k_trace, culled at the float64 best
-    // distance rounded up; triangles the float32 bound proves missed are
-    // skipped, every other one goes through the float64 rule.
-    while (r.valid && ncand < 0) {
-      float bf = (float)fmin(bt, tmax);
-      bf = bf + fabsf(bf) * 2e-6f;
-      float tn[4];
-      int4 ch;
-      unsigned m = slab4(A.wide + node, r, bf, tn, &ch) & (0xfu << slot) & 0xfu;
-      if (m) {
-        const int s = __ffs(m) - 1;
-        const int ref = s == 0 ? ch.x : (s == 1 ? ch.y : (s == 2 ? ch.z : ch.w));
-        if (ref >= 0) {
-          node = ref;
-          slot = 0;
-          continue;
-        }
-        const int first = leaf_first(ref), count = leaf_count(ref);
-        for (int k = 0; k < count && !(kAny && any); ++k) {
-          const float4* tp = A.tris + 3 * (size_t)(first + k);
-          const float4 va = tp[0], vb = tp[1], vc = tp[2];
-          const int id = __float_as_int(va.w);
-          if (id == skip) continue;
-          if (tri_test(r, va, vb, vc).cls == 0) continue;  // certain miss
-          double t, u, v;
-          if (mt64(o, d, D3{va.x, va.y, va.z}, D3{vb.x, vb.y, vb.z}, D3{vc.x, vc.y, vc.z}, &t, &u, &v) &&
-              t > tmin && t < tmax) {
-            any = true;
-            if (t < bt || (t == bt && id < bid)) {
-              bt = t;
-              bid = id;
-              bu = u;
-              bv = v;
-            }
+    // Without a complete candidate list: a stackless walk of the binary tree
+    // (parent links), so that any depth works.  Boxes use the same widened
+    // float32 slab test as k_trace, culled at the float64 best distance
+    // rounded up; triangles the float32 bound proves missed are skipped,
+    // every other one goes through the float64 rule.
+    auto test_leaf = [&](int ref) {
+      const int first = leaf_first(ref), count = leaf_count(ref);
+      for (int k = 0; k < count && !(kAny && any); ++k) {
+        const float4* tp = A.tris + 3 * (size_t)(first + k);
+        const float4 va = tp[0], vb = tp[1], vc = tp[2];
+        const int id = __float_as_int(va.w);
+        if (id == skip) continue;
+        if (tri_test(r, va, vb, vc).cls == 0) continue;  // certain miss
+        double t, u, v;
+        if (mt64(o, d, D3{va.x, va.y, va.z}, D3{vb.x, vb.y, vb.z}, D3{vc.x, vc.y, vc.z}, &t, &u, &v) && t > tmin &&
+            t < tmax) {
+          any = true;
+          if (t < bt || (t == bt && id < bid)) {
+            bt = t;
+            bid = id;
+            bu = u;
+            bv = v;
           }
         }
-        if (kAny && any) break;
-        slot = s + 1;
-        continue;
       }
-      if (node == 0) break;
-      const int4 meta = A.wide[node].meta;
-      node = meta.x;
-      slot = meta.y + 1;
+    };
+    if (r.valid && ncand < 0) {
+      const int root = *A.root_ref;
+      if (root >= A.n_tri - 1) {
+        // no usable tree: nothing to walk
+      } else if (root < 0) {
+        if (root != INT_MIN) test_leaf(root);
+      } else {
+        int node = root, s = 0;  // s: next child of `node` to try (2: done)
+        for (long long guard = 0; guard < (1ll << 32); ++guard) {
+          if (s < 2) {
+            const Node2* nd = A.node2 + node;
+            const float4 lo = s == 0 ? nd->a_lo : nd->b_lo, hi = s == 0 ? nd->a_hi : nd->b_hi;
+            float bf = (float)fmin(bt, tmax);
+            bf = bf + fabsf(bf) * 2e-6f;
+            ++s;
+            if (!slab1(lo, hi, r, bf)) continue;
+            const int ref = __float_as_int(lo.w);
+            if (ref >= 0) {
+              if (ref < A.n_tri - 1) {  // a link the build never wrote is skipped
+                node = ref;
+                s = 0;
+              }
+              continue;
+            }
+            test_leaf(ref);
+            if (kAny && any) break;
+            continue;
+          }
+          if (node == root) break;
+          const int p = A.link2[node].x;
+          if (p < 0 || p >= A.n_tri - 1) break;
+          s = __float_as_int(A.node2[p].a_lo.w) == node ? 1 : 2;
+          node = p;
+        }
+      }
     }
     if (kAny) {
       A.occl[i] = any ? 1 : 0;
@@ -587,6 +623,11 @@ cudaError_t launch_trace_dev(rt_scene_s* s, const rt_ray* rays, int64_t n, const
   if (n > 0) {
     TraceArgs A;
     A.wide = s->wide;
+    A.wide_root = &s->ctl->wide_root;
+    A.node2 = s->node2;
+    A.link2 = s->link2;
+    A.root_ref = &s->ctl->root_ref;
+    A.n_tri = (int)s->n_tri;
     A.tris = s->tri_leaf;
     A.rays = rays;
     A.n = (int)n;
