@@ -395,6 +395,21 @@ __device__ void push_task(const BuildArgs& A, const Task& t, int epoch) {
   atomicExch(&A.qa_ready[s], epoch);
 }
 
+// Hand up to 3 tasks to the mid-level queue at once (one thread): one slot
+// reservation, one fence.
+__device__ void push_tasks(const BuildArgs& A, const Task* t, int k, int epoch) {
+  if (k <= 0) return;
+  const int s = atomicAdd(&A.ctl->qa_tail, k);
+  if (s + k > A.qa_cap) {
+    set_status(A.ctl, kStQueueOverflow, 3);
+    return;
+  }
+  atomicAdd(&A.ctl->qa_pending, k);
+  for (int i = 0; i < k; ++i) A.qa[s + i] = t[i];
+  __threadfence();
+  for (int i = 0; i < k; ++i) atomicExch(&A.qa_ready[s + i], epoch);
+}
+
 __device__ __forceinline__ Task make_task(int begin, int count, int parent, int side, int depth, const BinU& u,
                                           int parity) {
   Task t;
@@ -1059,7 +1074,8 @@ __device__ void top_loop(const BuildArgs& A, TopSmem& S, int epoch) {
 // j holds record j of the node's range in Morton order.  Every split of the
 // subtree is the minimum of Eq. 2 over all splits of that order, evaluated
 // from warp scans of the records' boxes; ranges never move, so there is no
-// partition step.
+// partition step, and all nodes of one level of the subtree are split
+// together (scans that stop at each node's bounds).
 struct Box6 {
   float l0, l1, l2, h0, h1, h2;
 };
@@ -1080,10 +1096,6 @@ __device__ __forceinline__ Box6 box_shfl(const Box6& a, int src) {
   return {__shfl_sync(kFull, a.l0, src), __shfl_sync(kFull, a.l1, src), __shfl_sync(kFull, a.l2, src),
           __shfl_sync(kFull, a.h0, src), __shfl_sync(kFull, a.h1, src), __shfl_sync(kFull, a.h2, src)};
 }
-__device__ __forceinline__ Box6 box_xor(const Box6& a, int o) {
-  return {__shfl_xor_sync(kFull, a.l0, o), __shfl_xor_sync(kFull, a.l1, o), __shfl_xor_sync(kFull, a.l2, o),
-          __shfl_xor_sync(kFull, a.h0, o), __shfl_xor_sync(kFull, a.h1, o), __shfl_xor_sync(kFull, a.h2, o)};
-}
 
 // Tree facts gathered by a warp, added to the control block when it exits.
 struct WarpStats {
@@ -1093,111 +1105,104 @@ struct WarpStats {
 __device__ void micro_build(const BuildArgs& A, float4 rlo, float4 rhi, int n, int gbase, int parent, int side,
                             int depth, int epoch, WarpStats& ws) {
   const int lane = threadIdx.x & 31;
-  // uniform stack of pending ranges: (b, e, parent, side | depth << 1); the
-  // larger child is stacked first, so at most log2(32) + 1 entries
-  int4 st[8];
-  int sp = 0;
-  st[sp++] = make_int4(0, n, parent, side | (depth << 1));
-  while (sp > 0) {
-    __syncwarp();
-    const int4 tk = st[--sp];
-    const int b = tk.x, e = tk.y, par = tk.z, sd = tk.w & 1, dep = tk.w >> 1;
-    const bool in = lane >= b && lane < e;
-    const Box6 x = in ? Box6{rlo.x, rlo.y, rlo.z, rhi.x, rhi.y, rhi.z} : box_empty();
-    // inclusive prefix / suffix unions over the lanes
+  // every lane follows the node its record belongs to: range [b, e), its
+  // parent, side and depth; lanes past n sit in empty ranges of their own
+  const bool valid = lane < n;
+  int b = valid ? 0 : lane, e = valid ? n : lane + 1;
+  int par = parent, sd = side, dep = depth;
+  const Box6 x = valid ? Box6{rlo.x, rlo.y, rlo.z, rhi.x, rhi.y, rhi.z} : box_empty();
+  int n_int = 0, n_leaf = 0, big = 0, deep = 0;  // per node, counted by its first lane
+  for (int level = 0; level < 32; ++level) {
+    const bool active = valid && e - b > A.max_leaf;
+    if (!__any_sync(kFull, active)) break;
+    // unions of the records from the start of the lane's node up to the lane
+    // (ip) and from the lane to the node's end (is): scans that stop at the
+    // node's bounds, all nodes of the level at once
     Box6 ip = x, is = x;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const Box6 u = box_shfl_up(ip, o), d = box_shfl_down(is, o);
-      if (lane >= o) ip = box_join(ip, u);
-      if (lane + o < 32) is = box_join(is, d);
+      if (lane - o >= b) ip = box_join(ip, u);
+      if (lane + o < e) is = box_join(is, d);
     }
-    const Box6 xs = box_shfl_down(is, 1);
-    const Box6 sufn = lane == 31 ? box_empty() : xs;  // records after this lane
-    const Box6 node = box_shfl(ip, 31);
+    const Box6 sufn = box_shfl_down(is, 1);    // records after the lane, within the node
+    const Box6 node = box_shfl(ip, e - 1);     // the whole node
     const float3 clo = make_float3(node.l0, node.l1, node.l2), chi = make_float3(node.h0, node.h1, node.h2);
-    // candidate: lane q is the last left record (b <= q < e - 1)
-    float best = INFINITY;
-    int bq = 1 << 20;
-    if (lane >= b && lane + 1 < e) {
+    // candidate: the lane is the last left record
+    float cost = INFINITY;
+    int cq = 1 << 20;
+    if (active && lane + 1 < e) {
       const float c = eq2_cost(make_float3(ip.l0, ip.l1, ip.l2), make_float3(ip.h0, ip.h1, ip.h2), lane - b + 1,
                                make_float3(sufn.l0, sufn.l1, sufn.l2), make_float3(sufn.h0, sufn.h1, sufn.h2),
                                e - lane - 1, clo, chi, A.cp);
       if (c < INFINITY) {
-        best = c;
-        bq = lane;
+        cost = c;
+        cq = lane;
       }
     }
-    float wb = best;
-    int wq = bq;
+    // lowest cost of the node (ties: lowest position), found at its last lane
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const float oc = __shfl_xor_sync(kFull, wb, o);
-      const int oq = __shfl_xor_sync(kFull, wq, o);
-      if (oc < wb || (oc == wb && oq < wq)) {
-        wb = oc;
-        wq = oq;
+    for (int o = 1; o < 32; o <<= 1) {
+      const float oc = __shfl_up_sync(kFull, cost, o);
+      const int oq = __shfl_up_sync(kFull, cq, o);
+      if (lane - o >= b && (oc < cost || (oc == cost && oq < cq))) {
+        cost = oc;
+        cq = oq;
       }
     }
-    const bool found = wq < (1 << 20);
-    const int q = found ? wq : (b + e) / 2 - 1;  // no finite cost: middle
-    const int j = q + 1;                         // first record of the right child
-    const int id = gbase + q;
-    const int nl = j - b, nr = e - j;
-    const int rl = nl <= A.max_leaf ? leaf_ref(gbase + b, nl) : INT_MAX;
-    const int rr = nr <= A.max_leaf ? leaf_ref(gbase + j, nr) : INT_MAX;
-    // child boxes: the unions left / right of the split, by reduction
-    Box6 L = (lane >= b && lane < j) ? x : box_empty();
-    Box6 R = (lane >= j && lane < e) ? x : box_empty();
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      L = box_join(L, box_xor(L, o));
-      R = box_join(R, box_xor(R, o));
-    }
-    if (lane == 0) {
-      Node2 nd;
-      nd.a_lo = make_float4(L.l0, L.l1, L.l2, __int_as_float(rl));
-      nd.a_hi = make_float4(L.h0, L.h1, L.h2, __int_as_float(nl));
-      nd.b_lo = make_float4(R.l0, R.l1, R.l2, __int_as_float(rr));
-      nd.b_hi = make_float4(R.h0, R.h1, R.h2, __int_as_float(nr));
-      A.node2[id] = nd;
-      if (par < 0)
-        A.ctl->root_ref = id;
-      else if (par < A.n - 1)
-        *(sd == 0 ? &A.node2[par].a_lo.w : &A.node2[par].b_lo.w) = __int_as_float(id);
-      else
-        set_status(A.ctl, kStBadLink, 4);
-      A.link2[id] = make_int2(par, epoch);
-    }
-    ++ws.n_int;
-    ws.deep = max(ws.deep, dep);
-    if (rl != INT_MAX) {
-      ++ws.n_leaf;
-      ws.big = max(ws.big, nl);
-      ws.deep = max(ws.deep, dep + 1);
-    }
-    if (rr != INT_MAX) {
-      ++ws.n_leaf;
-      ws.big = max(ws.big, nr);
-      ws.deep = max(ws.deep, dep + 1);
-    }
-    const int4 cl = make_int4(b, j, id, 0 | ((dep + 1) << 1));
-    const int4 cr = make_int4(j, e, id, 1 | ((dep + 1) << 1));
-    const bool il = rl == INT_MAX, ir = rr == INT_MAX;
-    if (il && ir) {
-      if (nl >= nr) {
-        st[sp++] = cl;
-        st[sp++] = cr;
+    const int wq = __shfl_sync(kFull, cq, e - 1);
+    const int q = !active ? lane : (wq < (1 << 20) ? wq : (b + e) / 2 - 1);  // no finite cost: middle
+    const int j = q + 1;                                                       // first record of the right child
+    const Box6 L = box_shfl(ip, q);
+    const Box6 R = box_shfl(is, min(j, 31));
+    if (active) {
+      const int id = gbase + q;
+      const int nl = j - b, nr = e - j;
+      const int rl = nl <= A.max_leaf ? leaf_ref(gbase + b, nl) : INT_MAX;
+      const int rr = nr <= A.max_leaf ? leaf_ref(gbase + j, nr) : INT_MAX;
+      if (lane == b) {
+        Node2 nd;
+        nd.a_lo = make_float4(L.l0, L.l1, L.l2, __int_as_float(rl));
+        nd.a_hi = make_float4(L.h0, L.h1, L.h2, __int_as_float(nl));
+        nd.b_lo = make_float4(R.l0, R.l1, R.l2, __int_as_float(rr));
+        nd.b_hi = make_float4(R.h0, R.h1, R.h2, __int_as_float(nr));
+        A.node2[id] = nd;
+        if (par < 0)
+          A.ctl->root_ref = id;
+        else if (par < A.n - 1)
+          *(sd == 0 ? &A.node2[par].a_lo.w : &A.node2[par].b_lo.w) = __int_as_float(id);
+        else
+          set_status(A.ctl, kStBadLink, 4);
+        A.link2[id] = make_int2(par, epoch);
+        ++n_int;
+        deep = max(deep, dep);
+        if (rl != INT_MAX) {
+          ++n_leaf;
+          big = max(big, nl);
+          deep = max(deep, dep + 1);
+        }
+        if (rr != INT_MAX) {
+          ++n_leaf;
+          big = max(big, nr);
+          deep = max(deep, dep + 1);
+        }
+      }
+      // follow the child holding this lane's record
+      if (lane < j) {
+        e = j;
+        sd = 0;
       } else {
-        st[sp++] = cr;
-        st[sp++] = cl;
+        b = j;
+        sd = 1;
       }
-    } else if (il) {
-      st[sp++] = cl;
-    } else if (ir) {
-      st[sp++] = cr;
+      par = id;
+      ++dep;
     }
   }
+  ws.n_int += __reduce_add_sync(kFull, n_int);
+  ws.n_leaf += __reduce_add_sync(kFull, n_leaf);
+  ws.big = max(ws.big, (int)__reduce_max_sync(kFull, (unsigned)big));
+  ws.deep = max(ws.deep, (int)__reduce_max_sync(kFull, (unsigned)deep));
 }
 
 // Load a node of at most 32 records, order them by (Morton key, id) with a
@@ -1464,17 +1469,17 @@ __device__ void mid_split(const BuildArgs& A, MidWarp& W, const Task& t, int epo
     have_cont = true;
   }
   if (lane == 0) {
-    if (bigl && bigr) {
-      if (keep == 0)
-        push_task(A, make_task(t.begin + nl, nr, id, 1, t.depth + 1, R, par ^ 1), epoch);
-      else
-        push_task(A, make_task(t.begin, nl, id, 0, t.depth + 1, L, par ^ 1), epoch);
-    }
+    Task out[3];
+    int k = 0;
+    if (bigl && bigr)  // the other big child
+      out[k++] = keep == 0 ? make_task(t.begin + nl, nr, id, 1, t.depth + 1, R, par ^ 1)
+                           : make_task(t.begin, nl, id, 0, t.depth + 1, L, par ^ 1);
     // small subtrees go to idle warps while this one goes on down the tree
     if (keep >= 0) {
-      if (nl > A.max_leaf && !bigl) push_task(A, make_task(t.begin, nl, id, 0, t.depth + 1, L, par ^ 1), epoch);
-      if (nr > A.max_leaf && !bigr) push_task(A, make_task(t.begin + nl, nr, id, 1, t.depth + 1, R, par ^ 1), epoch);
+      if (nl > A.max_leaf && !bigl) out[k++] = make_task(t.begin, nl, id, 0, t.depth + 1, L, par ^ 1);
+      if (nr > A.max_leaf && !bigr) out[k++] = make_task(t.begin + nl, nr, id, 1, t.depth + 1, R, par ^ 1);
     }
+    push_tasks(A, out, k, epoch);
   }
   __syncwarp();
   if (keep < 0) {
