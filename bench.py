@@ -7,11 +7,12 @@ transmitter at the area centre 30 m up casting the 655,362 rays of a
 level-8 icosahedral subdivision (Sec. III.A), t_max = 500 m.
 
 One step = the whole path on device-resident inputs: build the BVH with the
-hybrid Eq. 2 cost around the transmitter (bounds, Morton presort, binned
-splits, 4-wide collapse) and trace every ray to its closest hit (float32
-walk + float64 re-test of flagged rays).  Each step is replayed from two
-CUDA graphs (build, trace) with CUDA events around each; L2 is flushed
-between steps by writing a 256 MB buffer.
+hybrid Eq. 2 cost around the transmitter (bounds, binned splits, Morton
+order inside small subtrees, 4-wide collapse) and trace every ray to its
+closest hit (float32 walk + float64 re-test of flagged rays).  The build is
+launched directly with CUDA events around it and around its split kernel
+(recorded by the library); the trace is replayed from a CUDA graph.  L2 is
+flushed between steps by writing a 256 MB buffer.
 
 Prints one JSON line (rank 0).  --impl reference times the float64 CPU
 checker (build + walk of the same workload) on the host cores instead.
@@ -49,6 +50,7 @@ def parse():
     ap.add_argument("--max-leaf", type=int, default=4)
     ap.add_argument("--bins", type=int, default=16)
     ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="fixed max_leaf / bins / ray tile instead of rt_autotune")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--batched-runs", type=int, default=5)
@@ -182,9 +184,15 @@ def run_batched(rtbvh, torch, runs):
     from paper_2208_10008_gb300 import scenes
     sc, tx, counts, rx = scenes.workload_batched()
     scene = rtbvh.rt_scene_upload(sc.tris)
-    rtbvh.rt_bvh_build(scene, alpha=0.7, source=tuple(tx.mean(0)), max_leaf=4, bins=16, dist_norm=1)
     tmax, orders = 1000.0, 3
-    b = rtbvh.Batch(scene, tx, counts, rtbvh.RT_RAYS_FIBONACCI, max_order=orders, tmax=tmax, rx_pos=rx)
+    # one build, many traces: tune on the largest transmitter's rays with no build weight
+    big = int(np.argmax(counts))
+    sample = rtbvh.rt_gen_rays(rtbvh.RT_RAYS_FIBONACCI, tx[big], int(counts[big]), 0.0, tmax)
+    tune = rtbvh.rt_autotune(scene, sample, build_weight=0.0, alpha=0.7, source=tuple(tx.mean(0)), dist_norm=1)
+    tile = tune["block"]
+    del sample
+    b = rtbvh.Batch(scene, tx, counts, rtbvh.RT_RAYS_FIBONACCI, max_order=orders, tmax=tmax, rx_pos=rx,
+                    ray_tile=tile)
     for _ in range(3):
         b.run()
     torch.cuda.synchronize()
@@ -205,14 +213,14 @@ def run_batched(rtbvh, torch, runs):
             cur = rtbvh.rt_gen_rays(rtbvh.RT_RAYS_FIBONACCI, tx[t], int(counts[t]), 0.0, tmax)
             skip = None
             for k in range(orders + 1):
-                h = rtbvh.rt_trace_closest(scene, cur, skip=skip)
+                h = rtbvh.rt_trace_closest(scene, cur, skip=skip, block=tile)
                 total += cur.shape[0]
                 if k == orders:
                     break
                 nr, ns, _, c = rtbvh.rt_reflect(scene, cur, h)
                 m = int(c.item())
                 cur, skip = nr[:m], ns[:m]
-        rtbvh.rt_trace_any(scene, seg)
+        rtbvh.rt_trace_any(scene, seg, block=tile)
         return total + seg.shape[0]
 
     plain()
@@ -229,7 +237,8 @@ def run_batched(rtbvh, torch, runs):
             "rays_per_run": st["total_rays"], "rays_per_order": st["rays"], "visible_pairs": st["visible"],
             "batched_mrays_s": st["total_rays"] / (ms_b * 1e-3) / 1e6, "batched_ms": ms_b,
             "plain_mrays_s": tot / (ms_p * 1e-3) / 1e6, "plain_ms": ms_p,
-            "speedup": ms_p / ms_b, "batched": "one CUDA graph replay per run (device-side counts)",
+            "speedup": ms_p / ms_b, "autotuned": tune,
+            "batched": "one CUDA graph replay per run (device-side counts)",
             "plain": "per-transmitter rt_gen_rays / rt_trace_closest / rt_reflect calls, counts read by the host"}
 
 
@@ -278,6 +287,34 @@ def run_served(rtbvh, torch, seconds):
 
 
 # ---------------------------------------------------------------- GPU
+def split_kernel_bytes(ex):
+    """Algorithmic bytes of one launch of the split kernel for this tree: every
+    32-byte record read and written once per binary level above the
+    32-triangle subtrees, once more by its subtree (sorted into leaf order),
+    plus 72 bytes per binary node written (node + parent link)."""
+    child = ex["child"].reshape(-1, 2)
+    lc = ex["leaf_count"]
+    n_int = len(child) if len(ex["leaf_count"]) > 1 else 0
+    n_tri = len(ex["prims"])
+    if n_int == 0:
+        return 64 * n_tri
+    size = np.zeros(n_int, np.int64)
+    order, st = [], [0]
+    while st:
+        v = st.pop()
+        order.append(v)
+        st.extend(int(c) for c in child[v] if c >= 0)
+    for v in reversed(order):
+        size[v] = sum(size[c] if c >= 0 else lc[-1 - c] for c in child[v])
+    moved = int(size[size > 32].sum())
+    micro = int(size[0]) if size[0] <= 32 else 0
+    for v in np.nonzero(size > 32)[0]:
+        for c in child[v]:
+            if c >= 0 and size[c] <= 32:
+                micro += int(size[c])
+    return 64 * (moved + micro) + 72 * n_int
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_env()
@@ -302,11 +339,19 @@ def run_ours(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.Stream()
 
+    # autotuner (outside the timed region): leaf size, bins and ray tile for
+    # this scene and ray set, one build per trace as in every step
+    tune, tile = None, 0
+    if not args.no_tune:
+        with torch.cuda.stream(stream):
+            tune = rtbvh.rt_autotune(scene, rays, build_weight=1.0, stream=stream, **bp)
+        bp["max_leaf"], bp["bins"], tile = tune["max_leaf"], tune["bins"], tune["block"]
+
     def build():
         rtbvh.rt_bvh_build(scene, stream=stream, **bp)
 
     def trace():
-        rtbvh.rt_trace_closest(scene, rays, hits, n_flagged=nflag, stream=stream)
+        rtbvh.rt_trace_closest(scene, rays, hits, n_flagged=nflag, stream=stream, block=tile)
 
     with torch.cuda.stream(stream):
         for _ in range(max(args.warmup, 1)):
@@ -324,28 +369,34 @@ def run_ours(args):
     bytes_per_ray = 32 + 16 + 128 * nodes_per_ray + 48 * tris_per_ray
     flagged = int(nflag.item())
 
+    split_bytes = split_kernel_bytes(rtbvh.rt_bvh_export(scene, stream=stream))
+
+    # The trace is replayed from a CUDA graph; the build is launched directly
+    # every step so that the library records fresh events around its split
+    # kernel (the dominant kernel) in each timed step.
     use_graph = not args.no_graph
-    launches_per_step = None
+    trace_launches = None
     if use_graph:
-        gb, gt = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+        gt = torch.cuda.CUDAGraph()
         c0 = rtbvh.rt_launch_count()
-        with torch.cuda.graph(gb, stream=stream):
-            build()
-        c1 = rtbvh.rt_launch_count()
         with torch.cuda.graph(gt, stream=stream):
             trace()
-        c2 = rtbvh.rt_launch_count()
-        launches_per_step = (c1 - c0) + (c2 - c1)
-        run_build, run_trace = gb.replay, gt.replay
+        trace_launches = rtbvh.rt_launch_count() - c0
+        run_trace = gt.replay
     else:
-        run_build, run_trace = build, trace
+        run_trace = trace
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
-            run_build()
+            build()
             run_trace()
     stream.synchronize()
 
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    sev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
+    with torch.cuda.stream(stream):
+        for e in sev:  # create the events before the timed region
+            e[0].record(stream)
+            e[1].record(stream)
     clocks = Clocks(gpu_smi_id(torch, dev)) if rank == 0 else None
     time.sleep(0.3 if clocks else 0)
     if dist:
@@ -355,25 +406,28 @@ def run_ours(args):
     with torch.cuda.stream(stream):
         for k in range(args.steps):
             flush.zero_()
+            rtbvh.rt_scene_set_split_events(scene, sev[k][0], sev[k][1])
             evs[k][0].record(stream)
-            run_build()
+            build()
             evs[k][1].record(stream)
             run_trace()
             evs[k][2].record(stream)
     torch.cuda.synchronize()
     lc1 = rtbvh.rt_launch_count()
+    rtbvh.rt_scene_set_split_events(scene)
     if dist:
         dist.barrier()
     clk = clocks.stop() if clocks else None
     step_ms = [e[0].elapsed_time(e[2]) for e in evs]
     build_ms = [e[0].elapsed_time(e[1]) for e in evs]
     trace_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    split_ms = [e[0].elapsed_time(e[1]) for e in sev]
     total_ms = sum(step_ms)
     if dist:
         t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    gpu_launches = (launches_per_step * args.steps) if use_graph else (lc1 - lc0)
+    gpu_launches = (lc1 - lc0) + (trace_launches * args.steps if use_graph else 0)
 
     # e2e: host buffers through the C ABI (scene + rays in, hits out, every step)
     tris_host = np.ascontiguousarray(sc.tris)
@@ -385,7 +439,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         rtbvh.rt_scene_update(scene, tris_host, stream=stream)
         rtbvh.rt_bvh_build(scene, stream=stream, **bp)
-        rtbvh.rt_trace_closest_host(scene, rays_pin, hits_pin, stream=stream)
+        rtbvh.rt_trace_closest_host(scene, rays_pin, hits_pin, stream=stream, block=tile)
         torch.cuda.synchronize()
         if k >= args.warmup:
             e2e_ms.append(1e3 * (time.perf_counter() - t0))
@@ -419,7 +473,24 @@ def run_ours(args):
         extra["batched"] = run_batched(rtbvh, torch, args.batched_runs)
         extra["served"] = run_served(rtbvh, torch, args.serve_seconds)
     mean_trace_ms = statistics.mean(trace_ms)
-    achieved = bytes_per_ray * R / (mean_trace_ms * 1e-3) / 1e9
+    mean_split_ms = statistics.mean(split_ms)
+    trace_gbs = bytes_per_ray * R / (mean_trace_ms * 1e-3) / 1e9
+    split_gbs = split_bytes / (mean_split_ms * 1e-3) / 1e9
+    roof_trace = {"bound": "hbm", "achieved": trace_gbs, "peak": hbm, "unit": "GB/s", "frac": trace_gbs / hbm,
+                  "traffic": None, "kernel": "k_trace + k_retest64 (one rt_trace_closest)", "peak_source": peak_src,
+                  "ms": mean_trace_ms, "bytes_per_ray": bytes_per_ray, "algorithmic_bytes": bytes_per_ray * R,
+                  "l2_probe_gbs": l2_gbs, "frac_of_l2_probe": trace_gbs / l2_gbs,
+                  "note": "algorithmic bytes = 32 ray + 16 hit + 128 B x nodes + 48 B x triangles per ray; "
+                          "nodes and triangles stay in L2 for this scene"}
+    roof_split = {"bound": "hbm", "achieved": split_gbs, "peak": hbm, "unit": "GB/s", "frac": split_gbs / hbm,
+                  "traffic": None, "kernel": "k_split (one launch per build)", "peak_source": peak_src,
+                  "ms": mean_split_ms, "algorithmic_bytes": split_bytes, "l2_probe_gbs": l2_gbs,
+                  "frac_of_l2_probe": split_gbs / l2_gbs,
+                  "note": "algorithmic bytes = 64 B per record per binary level above the 32-triangle subtrees "
+                          "+ 64 B per record for its subtree + 72 B per binary node; the kernel is bound by the "
+                          "latency of dependent splits, not by bandwidth (events recorded by the library around "
+                          "the kernel in every timed step)"}
+    dominant_split = mean_split_ms >= mean_trace_ms
     value = ws * R * args.steps / (total_ms * 1e-3) / 1e6
     cpu_v, cores, reps, el = cpu_checker_rate(sc, rays_np, p, args, args.cpu_seconds)
     line = {
@@ -427,23 +498,20 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_tri": T, "rays_per_step": R, "t_max_m": 500.0,
-                   "alpha": args.alpha, "dist_norm": args.dist_norm, "max_leaf": args.max_leaf,
-                   "bins": args.bins, "width": 4, "step": "bvh_build + trace_closest (fp64 re-test incl.)",
-                   "cuda_graph": use_graph, "l2": "flushed between steps (256 MB write)",
+                   "alpha": args.alpha, "dist_norm": args.dist_norm, "max_leaf": bp["max_leaf"],
+                   "bins": bp["bins"], "ray_tile": tile or 128, "width": 4,
+                   "autotuned": tune, "step": "bvh_build + trace_closest (fp64 re-test incl.)",
+                   "cuda_graph": "trace replayed from a graph; build launched directly (per-step split-kernel events)"
+                   if use_graph else False, "l2": "flushed between steps (256 MB write)",
                    "parallelism": "replicas" if ws > 1 else "single"},
-        "breakdown": {"build_ms": statistics.mean(build_ms), "trace_ms": mean_trace_ms,
+        "breakdown": {"build_ms": statistics.mean(build_ms), "split_kernel_ms": mean_split_ms,
+                      "trace_ms": mean_trace_ms,
                       "trace_mrays_s": R / (mean_trace_ms * 1e-3) / 1e6,
                       "flagged_rays": flagged, "flagged_frac": flagged / R,
                       "nodes_per_ray": nodes_per_ray, "tris_per_ray": tris_per_ray,
                       "bvh": {k: info[k] for k in ("n_wide", "n_leaves", "depth2", "depth_wide")}},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None,
-                     "kernel": "k_trace + k_retest64 (one rt_trace_closest)",
-                     "peak_source": peak_src,
-                     "bytes_per_ray": bytes_per_ray,
-                     "l2_probe_gbs": l2_gbs, "frac_of_l2_probe": achieved / l2_gbs,
-                     "note": "algorithmic bytes = 32 ray + 16 hit + 128 B x nodes + 48 B x triangles per ray; "
-                             "the 0.4 MB node array and 1 MB triangle array stay in L2"},
+        "roofline": roof_split if dominant_split else roof_trace,
+        "roofline_other": roof_trace if dominant_split else roof_split,
         "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": "%d repetitions of the full workload (exact-sweep Eq. 2 build + float64 walk of %d rays) in %.1f s" % (reps, R, el)},
         "e2e": {"value": R / (e2e_step * 1e-3) / 1e6, "unit": UNIT,

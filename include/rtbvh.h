@@ -88,6 +88,8 @@ typedef struct {
   uint32_t* stats_dev;         /* nullable; with RT_COUNT_STATS, per ray [nodes, tris] */
   int32_t* n_flagged_dev;      /* nullable; receives the number of rays the float32 pass
                                   flagged for the float64 re-test */
+  int32_t block;               /* rays per CTA of the float32 walk (ray tile): 64, 128 or
+                                  256; 0 = 128.  Results do not depend on it. */
 } rt_trace_params;
 
 /* Build report (rt_bvh_info). */
@@ -134,15 +136,53 @@ int rt_scene_update(rt_scene scene, const float* tris, int64_t n_tri, int is_dev
                     void* stream);
 
 /* Build (or rebuild) the scene's BVH on the device (Sec. II.B-C, Fig. 2):
- * per-triangle AABBs, scene bounds, a Morton-order presort of the
- * centroids, a top-down split of every node by the minimum of the Eq. 2
- * cost over `bins`-1 candidate planes on each axis, leaves of at most
- * max_leaf triangles, then a collapse of the binary tree into `width`-ary
- * traversal nodes.  Asynchronous: no host synchronisation, so it can be
- * captured in a CUDA graph once the scene's buffers exist (the first build
- * of a scene allocates them).  Errors: RT_EINVAL (bad params), RT_ENOMEM,
- * RT_ECUDA. */
+ * per-triangle AABBs (Eq. 3), scene bounds, a top-down split of every node
+ * by the minimum of the Eq. 2 cost over `bins`-1 candidate planes on each
+ * axis (nodes of at most 32 triangles: over the splits of the Morton order
+ * of their box centres), leaves of at most max_leaf triangles, then a
+ * collapse of the binary tree into `width`-ary traversal nodes.
+ * Asynchronous: no host synchronisation, so it can be captured in a CUDA
+ * graph once the scene's buffers exist (the first build of a scene
+ * allocates them).  Errors: RT_EINVAL (bad params), RT_ENOMEM, RT_ECUDA. */
 int rt_bvh_build(rt_scene scene, const rt_build_params* params, void* stream);
+
+/* Instrumentation, with no counterpart in the paper: record the CUDA events
+ * ev_begin and ev_end (cudaEvent_t passed as void*) on the build stream just
+ * before and just after the split kernel (the recursion of Fig. 2, the
+ * build's longest kernel) of every later rt_bvh_build of this scene, so
+ * that the caller can time that kernel alone (cudaEventElapsedTime).  Both
+ * NULL stops it.  Inside a stream capture the records become event-record
+ * nodes of the graph.  The events stay the caller's and must outlive the
+ * builds that record them.  Errors: RT_EINVAL (scene NULL, or only one of
+ * the two events given). */
+int rt_scene_set_split_events(rt_scene scene, void* ev_begin, void* ev_end);
+
+/* Autotuner result (rt_autotune). */
+typedef struct {
+  int32_t max_leaf;   /* chosen leaf size */
+  int32_t bins;       /* chosen bins per axis */
+  int32_t block;      /* chosen ray tile of the walk (rt_trace_params.block) */
+  int32_t n_tried;    /* configurations timed */
+  float build_ms;     /* device time of one build with the choice */
+  float trace_ms;     /* device time of one trace of the sample with the choice */
+  float score_ms;     /* build_weight * build_ms + trace_ms */
+  float default_score_ms; /* the same for max_leaf 4, bins 16, block 128 */
+} rt_tune_result;
+
+/* Autotuner of the build and walk parameters (no counterpart in the paper):
+ * for max_leaf in {2, 4, 6, 8} x bins in {8, 16, 32} x ray tile in {64,
+ * 128, 256}, build the scene's BVH from `base` (alpha, t_i, t_trav, source,
+ * dist_norm kept) and time the closest-hit walk of the n_rays sample rays
+ * (device pointer), each timing the best of 3 with CUDA events; pick the
+ * lowest build_weight * build_ms + trace_ms (build_weight = builds per
+ * traced sample: 1 when the scene is rebuilt for every batch, 0 when it is
+ * built once and traced many times).  Every configuration gives the same
+ * hits (the hit rule does not depend on the tree).  On return the scene
+ * holds the BVH built with the choice.  Synchronous.  Allocates and frees
+ * one n_rays hit buffer.  Errors: RT_EINVAL (NULL arguments, n_rays < 1,
+ * build_weight < 0, bad base params), RT_ENOMEM, RT_ECUDA. */
+int rt_autotune(rt_scene scene, const rt_build_params* base, const rt_ray* rays_dev, int64_t n_rays,
+                float build_weight, rt_tune_result* out, void* stream);
 
 /* Synchronous: wait for the stream, then report the built tree.  Errors:
  * RT_EINVAL, RT_ENOTBUILT, RT_ECUDA; RT_EINTERNAL when the device status
@@ -240,6 +280,8 @@ typedef struct {
   int32_t n_rx;            /* receivers (0: no visibility pass) */
   const float* rx_pos;     /* host, n_rx * 3 */
   int32_t use_graph;       /* 1: capture the pipeline in a CUDA graph on the second run, replay after */
+  int32_t ray_tile;        /* rt_trace_params.block of every walk of the batch (0 = default),
+                              e.g. rt_autotune's choice */
 } rt_batch_desc;
 
 typedef struct {

@@ -22,6 +22,7 @@ struct rt_batch_s {
   int n_tx = 0, kind = 0, max_order = 0, n_rx = 0;
   float tmax = 0.f;
   bool use_graph = true;
+  int ray_tile = 0;  // rays per CTA of every walk (0 = default)
   std::vector<float> tx;
   std::vector<long long> param, count, offset;
   long long n0 = 0, n_seg = 0;
@@ -74,6 +75,7 @@ cudaError_t enqueue(rt_batch_s* b) {
       return e;
   }
   rt_trace_params tp{};
+  tp.block = b->ray_tile;
   if ((e = rt::launch_trace_dev(b->scene, b->rays[0], b->n0, nullptr, b->hits[0], nullptr, &tp, b->scr, st)))
     return e;
   for (int k = 1; k <= b->max_order; ++k) {
@@ -83,12 +85,14 @@ cudaError_t enqueue(rt_batch_s* b) {
       return e;
     rt_trace_params tk{};
     tk.skip_tri_dev = b->skip[k];
+    tk.block = b->ray_tile;
     if ((e = rt::launch_trace_dev(b->scene, b->rays[k], b->n0, b->counts + k, b->hits[k], nullptr, &tk, b->scr,
                                   st)))
       return e;
   }
   if (b->n_seg > 0) {
     rt_trace_params tv{};
+    tv.block = b->ray_tile;
     if ((e = rt::launch_trace_dev(b->scene, b->seg, b->n_seg, nullptr, nullptr, b->occl, &tv, b->scr, st)))
       return e;
   }
@@ -122,6 +126,11 @@ int rt_batch_create(rt_scene scene, const rt_batch_desc* d, rt_batch* out) {
   b->n_rx = d->n_rx;
   b->tmax = d->tmax;
   b->use_graph = d->use_graph != 0;
+  if (d->ray_tile != 0 && d->ray_tile != 64 && d->ray_tile != 128 && d->ray_tile != 256) {
+    delete b;
+    return rt::set_error(RT_EINVAL, "ray_tile must be 0, 64, 128 or 256");
+  }
+  b->ray_tile = d->ray_tile;
   b->tx.assign(d->tx_pos, d->tx_pos + 3 * d->n_tx);
   long long total = 0;
   for (int t = 0; t < d->n_tx; ++t) {

@@ -1788,7 +1788,12 @@ cudaError_t launch_build(rt_scene_s* s, const rt_build_params& p, cudaStream_t s
   }
   if ((e = launch(k_prep, gp, 0, st, false, A))) return e;
   if ((e = launch(k_bin_root, std::max(1, std::min(nch, nsm * 4)), 0, st, true, A))) return e;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (s->split_ev[0] && (e = cudaStreamIsCapturing(st, &cs))) return e;
+  const unsigned evflags = cs == cudaStreamCaptureStatusNone ? cudaEventRecordDefault : cudaEventRecordExternal;
+  if (s->split_ev[0] && (e = cudaEventRecordWithFlags(s->split_ev[0], st, evflags))) return e;
   if ((e = launch(k_split, 2 * nsm, sizeof(SplitSmem), st, true, A))) return e;
+  if (s->split_ev[1] && (e = cudaEventRecordWithFlags(s->split_ev[1], st, evflags))) return e;
   if ((e = launch(k_post, gp, 0, st, true, A))) return e;
   count_launches(4);
   return cudaSuccess;

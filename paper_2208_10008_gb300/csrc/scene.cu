@@ -246,6 +246,15 @@ int rt_bvh_build(rt_scene s, const rt_build_params* p, void* stream) {
   return RT_OK;
 }
 
+int rt_scene_set_split_events(rt_scene s, void* ev_begin, void* ev_end) {
+  g_err[0] = 0;
+  if (!s) return fail(RT_EINVAL, "scene is NULL");
+  if ((ev_begin == nullptr) != (ev_end == nullptr)) return fail(RT_EINVAL, "give both events or neither");
+  s->split_ev[0] = (cudaEvent_t)ev_begin;
+  s->split_ev[1] = (cudaEvent_t)ev_end;
+  return RT_OK;
+}
+
 int rt_bvh_info(rt_scene s, void* stream, rt_bvh_info_t* info) {
   g_err[0] = 0;
   if (!s || !info) return fail(RT_EINVAL, "NULL argument");
@@ -354,6 +363,8 @@ static int trace_common(rt_scene s, const rt_ray* rays, int64_t n, rt_hit* hits,
   if (n < 0 || n > INT_MAX) return fail(RT_EINVAL, "n out of range");
   if (n > 0 && (!rays || (!hits && !occl))) return fail(RT_EINVAL, "NULL buffer");
   if (((uintptr_t)rays & 15) || ((uintptr_t)hits & 15)) return fail(RT_EINVAL, "rays/hits must be 16-byte aligned");
+  if (params && params->block != 0 && params->block != 64 && params->block != 128 && params->block != 256)
+    return fail(RT_EINVAL, "block must be 0, 64, 128 or 256");
   if (!s->built) return fail(RT_ENOTBUILT, "BVH not built");
   int r = ensure_scratch(s->scratch, n);
   if (r) return r;

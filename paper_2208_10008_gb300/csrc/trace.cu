@@ -294,9 +294,9 @@ struct TraceArgs {
   int qcap;
 };
 
-template <bool kAny, bool kStats>
-__global__ void __launch_bounds__(kTraceBlock) k_trace(TraceArgs A) {
-  const int i = blockIdx.x * kTraceBlock + threadIdx.x;
+template <bool kAny, bool kStats, int kTile>
+__global__ void __launch_bounds__(kTile) k_trace(TraceArgs A) {
+  const int i = blockIdx.x * kTile + threadIdx.x;
   if (i >= A.n || (A.n_dev && i >= *A.n_dev)) return;
   const float4* r4 = reinterpret_cast<const float4*>(A.rays) + 2 * (size_t)i;
   const RayPre r = setup_ray(__ldg(r4), __ldg(r4 + 1));
@@ -504,7 +504,7 @@ __global__ void __launch_bounds__(kRetestBlock) k_retest64(TraceArgs A) {
     const double tmin = ra.w, tmax = rb.w;
     const int skip = A.skip ? A.skip[i] : -1;
     double bt = INFINITY, bu = 0.0, bv = 0.0;
-    int bid = -1;
+    int bid = -1, bpos = -1;
     bool any = false;
     const int* cl = A.cand + (size_t)j * (kCand + 1);
     const int ncand = cl[0];
@@ -520,6 +520,7 @@ __global__ void __launch_bounds__(kRetestBlock) k_retest64(TraceArgs A) {
         if (t < bt || (t == bt && id < bid)) {
           bt = t;
           bid = id;
+          bpos = cl[1 + q];
           bu = u;
           bv = v;
         }
@@ -545,6 +546,7 @@ __global__ void __launch_bounds__(kRetestBlock) k_retest64(TraceArgs A) {
           if (t < bt || (t == bt && id < bid)) {
             bt = t;
             bid = id;
+            bpos = first + k;
             bu = u;
             bv = v;
           }
@@ -590,8 +592,22 @@ __global__ void __launch_bounds__(kRetestBlock) k_retest64(TraceArgs A) {
     if (kAny) {
       A.occl[i] = any ? 1 : 0;
     } else {
-      float4 out = bid >= 0 ? make_float4((float)bt, __int_as_float(bid), (float)bu, (float)bv)
-                            : make_float4(INFINITY, __int_as_float(-1), 0.f, 0.f);
+      float4 out = make_float4(INFINITY, __int_as_float(-1), 0.f, 0.f);
+      if (bid >= 0) {
+        out = make_float4((float)bt, __int_as_float(bid), (float)bu, (float)bv);
+        // The record is a function of the ray and the winning triangle only:
+        // where the float32 test certifies the winner, report exactly what
+        // the float32 walk reports for it (so the result never depends on
+        // whether this tree's walk flagged the ray).
+        const float4* tp = A.tris + 3 * (size_t)bpos;
+        const float4 va = tp[0], vb = tp[1], vc = tp[2];
+        const TriRes h = tri_test(r, va, vb, vc);
+        if (h.cls == 1 && h.t > r.tmin && h.t < r.tmax) {
+          float t = h.t;
+          if (h.err > 0.25f * (kTieRel * h.t + 1e-6f)) t = refine_t(r, rb.x, rb.y, rb.z, va, vb, vc);
+          out = make_float4(t, __int_as_float(bid), h.u, h.v);
+        }
+      }
       reinterpret_cast<float4*>(A.hits)[i] = out;
     }
   }
@@ -641,17 +657,30 @@ cudaError_t launch_trace_dev(rt_scene_s* s, const rt_ray* rays, int64_t n, const
     A.queue = scr.queue;
     A.cand = scr.cand;
     A.qcap = (int)scr.cap;
-    const int grid = (int)((n + kTraceBlock - 1) / kTraceBlock);
-    if (occl) {
-      if (stats)
-        k_trace<true, true><<<grid, kTraceBlock, 0, st>>>(A);
+    // ray tile (rays per CTA); the counting walk always uses the default
+    const int req = (tp && !stats) ? tp->block : 0;
+    const int tile = (req == 64 || req == 256) ? req : kTraceBlock;
+    const int grid = (int)((n + tile - 1) / tile);
+    if (stats) {
+      if (occl)
+        k_trace<true, true, kTraceBlock><<<grid, kTraceBlock, 0, st>>>(A);
       else
-        k_trace<true, false><<<grid, kTraceBlock, 0, st>>>(A);
+        k_trace<false, true, kTraceBlock><<<grid, kTraceBlock, 0, st>>>(A);
+    } else if (tile == 64) {
+      if (occl)
+        k_trace<true, false, 64><<<grid, 64, 0, st>>>(A);
+      else
+        k_trace<false, false, 64><<<grid, 64, 0, st>>>(A);
+    } else if (tile == 256) {
+      if (occl)
+        k_trace<true, false, 256><<<grid, 256, 0, st>>>(A);
+      else
+        k_trace<false, false, 256><<<grid, 256, 0, st>>>(A);
     } else {
-      if (stats)
-        k_trace<false, true><<<grid, kTraceBlock, 0, st>>>(A);
+      if (occl)
+        k_trace<true, false, kTraceBlock><<<grid, kTraceBlock, 0, st>>>(A);
       else
-        k_trace<false, false><<<grid, kTraceBlock, 0, st>>>(A);
+        k_trace<false, false, kTraceBlock><<<grid, kTraceBlock, 0, st>>>(A);
     }
     ++n_launched;
     if (!(tp && (tp->flags & RT_NO_FP64_RETEST))) {

@@ -1,0 +1,114 @@
+// Autotuner of the build and walk parameters (rt_autotune in rtbvh.h).
+//
+// The knobs are the ones that trade build time against walk time without
+// changing any hit: the leaf size, the number of bins per axis and the ray
+// tile (rays per CTA) of the float32 walk.  Every configuration is built
+// and timed with CUDA events on the caller's stream (best of 3), and the
+// scene is left built with the winner.
+#include <cuda_runtime.h>
+
+#include <cfloat>
+#include <climits>
+
+#include "rt_internal.cuh"
+
+namespace rt {
+int set_error(int code, const char* msg);  // records the message for rt_last_error
+}
+
+namespace {
+
+struct Events {
+  cudaEvent_t e[3] = {nullptr, nullptr, nullptr};
+  ~Events() {
+    for (cudaEvent_t x : e)
+      if (x) cudaEventDestroy(x);
+  }
+};
+
+// Device time of `fn` (enqueueing on st), best of `reps`; negative on failure.
+template <class F>
+float best_ms(cudaStream_t st, const Events& ev, int reps, F fn, int* err) {
+  float best = FLT_MAX;
+  for (int r = 0; r < reps; ++r) {
+    if (cudaEventRecord(ev.e[0], st) != cudaSuccess) return -1.f;
+    *err = fn();
+    if (*err) return -1.f;
+    if (cudaEventRecord(ev.e[1], st) != cudaSuccess || cudaEventSynchronize(ev.e[1]) != cudaSuccess) return -1.f;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ev.e[0], ev.e[1]) != cudaSuccess) return -1.f;
+    best = ms < best ? ms : best;
+  }
+  return best;
+}
+
+}  // namespace
+
+extern "C" int rt_autotune(rt_scene s, const rt_build_params* base, const rt_ray* rays, int64_t n,
+                           float build_weight, rt_tune_result* out, void* stream) {
+  if (!s || !base || !rays || !out) return rt::set_error(RT_EINVAL, "NULL argument");
+  if (n < 1 || n > INT_MAX) return rt::set_error(RT_EINVAL, "n_rays out of range");
+  if (!(build_weight >= 0.f) || build_weight > 1e6f) return rt::set_error(RT_EINVAL, "build_weight must be >= 0");
+  if (((uintptr_t)rays & 15)) return rt::set_error(RT_EINVAL, "rays must be 16-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream;
+  Events ev;
+  for (cudaEvent_t& x : ev.e)
+    if (cudaEventCreate(&x) != cudaSuccess) return rt::set_error(RT_ECUDA, "create events");
+  rt_hit* hits = nullptr;
+  if (cudaMalloc((void**)&hits, sizeof(rt_hit) * (size_t)n) != cudaSuccess) {
+    cudaGetLastError();
+    return rt::set_error(RT_ENOMEM, "hit buffer");
+  }
+  const int leaves[] = {2, 4, 6, 8}, binsv[] = {8, 16, 32}, tiles[] = {64, 128, 256};
+  rt_tune_result best{};
+  best.score_ms = FLT_MAX;
+  best.default_score_ms = -1.f;
+  int err = 0, tried = 0;
+  for (int ml : leaves) {
+    for (int bn : binsv) {
+      rt_build_params p = *base;
+      p.max_leaf = ml;
+      p.bins = bn;
+      err = rt_bvh_build(s, &p, stream);  // warm: the first build sizes the scene's buffers
+      if (err) goto done;
+      const float tb = best_ms(st, ev, 3, [&] { return rt_bvh_build(s, &p, stream); }, &err);
+      if (tb < 0.f) goto fail_cuda;
+      for (int tile : tiles) {
+        rt_trace_params tp{};
+        tp.block = tile;
+        err = rt_trace_closest(s, rays, n, hits, &tp, stream);
+        if (err) goto done;
+        const float tt = best_ms(st, ev, 3, [&] { return rt_trace_closest(s, rays, n, hits, &tp, stream); }, &err);
+        if (tt < 0.f) goto fail_cuda;
+        const float score = build_weight * tb + tt;
+        ++tried;
+        if (ml == 4 && bn == 16 && tile == 128) best.default_score_ms = score;
+        if (score < best.score_ms) {
+          best.max_leaf = ml;
+          best.bins = bn;
+          best.block = tile;
+          best.build_ms = tb;
+          best.trace_ms = tt;
+          best.score_ms = score;
+        }
+      }
+    }
+  }
+  {
+    rt_build_params p = *base;
+    p.max_leaf = best.max_leaf;
+    p.bins = best.bins;
+    err = rt_bvh_build(s, &p, stream);
+    if (err) goto done;
+    if (cudaStreamSynchronize(st) != cudaSuccess) goto fail_cuda;
+  }
+  best.n_tried = tried;
+  *out = best;
+done:
+  cudaFree(hits);
+  return err;
+fail_cuda:
+  cudaFree(hits);
+  if (err) return err;
+  return rt::set_error(RT_ECUDA, "timing failed");
+}

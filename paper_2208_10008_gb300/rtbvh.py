@@ -39,7 +39,7 @@ EXPORTS = ["rt_version", "rt_launch_count", "rt_last_error", "rt_scene_upload", 
            "rt_reflect", "rt_batch_create", "rt_batch_run", "rt_batch_stats_get", "rt_batch_order",
            "rt_batch_visibility", "rt_batch_destroy", "rt_session_create", "rt_session_add_scene",
            "rt_session_submit", "rt_session_poll", "rt_session_wait", "rt_session_stats_get",
-           "rt_session_destroy"]
+           "rt_session_destroy", "rt_scene_set_split_events", "rt_autotune"]
 
 
 class RtError(RuntimeError):
@@ -56,7 +56,13 @@ class BuildParams(ctypes.Structure):
 
 class TraceParams(ctypes.Structure):
     _fields_ = [("flags", ctypes.c_uint32), ("skip_tri_dev", ctypes.c_void_p),
-                ("stats_dev", ctypes.c_void_p), ("n_flagged_dev", ctypes.c_void_p)]
+                ("stats_dev", ctypes.c_void_p), ("n_flagged_dev", ctypes.c_void_p), ("block", ctypes.c_int32)]
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("max_leaf", ctypes.c_int32), ("bins", ctypes.c_int32), ("block", ctypes.c_int32),
+                ("n_tried", ctypes.c_int32), ("build_ms", ctypes.c_float), ("trace_ms", ctypes.c_float),
+                ("score_ms", ctypes.c_float), ("default_score_ms", ctypes.c_float)]
 
 
 class BvhInfo(ctypes.Structure):
@@ -72,7 +78,8 @@ RT_BATCH_MAX_ORDER = 8
 class BatchDesc(ctypes.Structure):
     _fields_ = [("n_tx", ctypes.c_int32), ("tx_pos", ctypes.c_void_p), ("tx_param", ctypes.c_void_p),
                 ("dir_kind", ctypes.c_int32), ("max_order", ctypes.c_int32), ("tmax", ctypes.c_float),
-                ("n_rx", ctypes.c_int32), ("rx_pos", ctypes.c_void_p), ("use_graph", ctypes.c_int32)]
+                ("n_rx", ctypes.c_int32), ("rx_pos", ctypes.c_void_p), ("use_graph", ctypes.c_int32),
+                ("ray_tile", ctypes.c_int32)]
 
 
 class BatchStats(ctypes.Structure):
@@ -117,6 +124,9 @@ def lib(build: bool = True):
             L.rt_scene_destroy.argtypes = [vp]
             L.rt_bvh_build.argtypes = [vp, ctypes.POINTER(BuildParams), vp]
             L.rt_bvh_info.argtypes = [vp, vp, ctypes.POINTER(BvhInfo)]
+            L.rt_scene_set_split_events.argtypes = [vp, vp, vp]
+            L.rt_autotune.argtypes = [vp, ctypes.POINTER(BuildParams), vp, i64, ctypes.c_float,
+                                      ctypes.POINTER(TuneResult), vp]
             L.rt_bvh_export.argtypes = [vp, vp, vp, vp, vp, vp, vp]
             L.rt_trace_closest.argtypes = [vp, vp, i64, vp, ctypes.POINTER(TraceParams), vp]
             L.rt_trace_any.argtypes = [vp, vp, i64, vp, ctypes.POINTER(TraceParams), vp]
@@ -246,6 +256,28 @@ def rt_bvh_build(scene: Scene, stream=None, **kw):
     _check(lib().rt_bvh_build(scene.handle, ctypes.byref(p), _stream(stream)))
 
 
+def rt_scene_set_split_events(scene: Scene, ev_begin=None, ev_end=None):
+    """Record two torch.cuda.Event (timing enabled) around the split kernel of
+    every later build of `scene`; no arguments stops it."""
+    for e in (ev_begin, ev_end):
+        if e is not None and not e.cuda_event:
+            e.record()  # torch creates its event on the first record
+    h = [ctypes.c_void_p(e.cuda_event) if e is not None else None for e in (ev_begin, ev_end)]
+    _check(lib().rt_scene_set_split_events(scene.handle, h[0], h[1]))
+
+
+def rt_autotune(scene: Scene, rays, build_weight=1.0, stream=None, **base) -> dict:
+    """Time build + walk of `rays` over max_leaf x bins x ray tile and leave the
+    scene built with the fastest; returns the choice and its timings."""
+    import torch
+    rp = _dev_ptr(rays, torch.float32, 8, "rays")
+    p = build_params(**base)
+    r = TuneResult()
+    _check(lib().rt_autotune(scene.handle, ctypes.byref(p), rp, rays.shape[0], float(build_weight),
+                             ctypes.byref(r), _stream(stream)))
+    return {f: getattr(r, f) for f, _ in TuneResult._fields_}
+
+
 def rt_bvh_info(scene: Scene, stream=None) -> dict:
     info = BvhInfo()
     code = lib().rt_bvh_info(scene.handle, _stream(stream), ctypes.byref(info))
@@ -270,10 +302,11 @@ def rt_bvh_export(scene: Scene, stream=None) -> dict:
                 prims=prims[:n], boxes=boxes[: 12 * ni].reshape(-1, 12), info=info)
 
 
-def _trace_params(flags, skip, stats, n_flagged, n):
+def _trace_params(flags, skip, stats, n_flagged, n, block=0):
     import torch
     tp = TraceParams()
     tp.flags = int(flags)
+    tp.block = int(block)
     if skip is not None:
         if skip.shape != (n,):
             raise TypeError("skip must have shape [n]")
@@ -289,7 +322,7 @@ def _trace_params(flags, skip, stats, n_flagged, n):
 
 
 def rt_trace_closest(scene: Scene, rays, hits=None, skip=None, flags=0, stats=None, n_flagged=None,
-                     stream=None):
+                     stream=None, block=0):
     """Closest hit of every ray; returns hits float32 [n, 4] (see module doc)."""
     import torch
     rp = _dev_ptr(rays, torch.float32, 8, "rays")
@@ -297,7 +330,7 @@ def rt_trace_closest(scene: Scene, rays, hits=None, skip=None, flags=0, stats=No
     if hits is None:
         hits = torch.empty((n, 4), dtype=torch.float32, device=rays.device)
     hp = _dev_ptr(hits, torch.float32, 4, "hits")
-    tp = _trace_params(flags, skip, stats, n_flagged, n)
+    tp = _trace_params(flags, skip, stats, n_flagged, n, block)
     _check(lib().rt_trace_closest(scene.handle, rp, n, hp, ctypes.byref(tp), _stream(stream)))
     return hits
 
@@ -318,7 +351,7 @@ RT_NOALLOC_MAX_RAYS = 262144
 
 
 def rt_trace_any(scene: Scene, rays, occluded=None, skip=None, flags=0, stats=None, n_flagged=None,
-                 stream=None):
+                 stream=None, block=0):
     """Any hit of every ray; returns uint8 [n] (1 = some triangle within (tmin, tmax))."""
     import torch
     rp = _dev_ptr(rays, torch.float32, 8, "rays")
@@ -326,12 +359,12 @@ def rt_trace_any(scene: Scene, rays, occluded=None, skip=None, flags=0, stats=No
     if occluded is None:
         occluded = torch.empty((n,), dtype=torch.uint8, device=rays.device)
     op = _dev_ptr(occluded, torch.uint8, None, "occluded")
-    tp = _trace_params(flags, skip, stats, n_flagged, n)
+    tp = _trace_params(flags, skip, stats, n_flagged, n, block)
     _check(lib().rt_trace_any(scene.handle, rp, n, op, ctypes.byref(tp), _stream(stream)))
     return occluded
 
 
-def rt_trace_closest_host(scene: Scene, rays_host, hits_host=None, flags=0, stream=None):
+def rt_trace_closest_host(scene: Scene, rays_host, hits_host=None, flags=0, stream=None, block=0):
     """Closest hit with host buffers (pinned torch tensors or numpy arrays)."""
     import torch
     if isinstance(rays_host, torch.Tensor):
@@ -351,6 +384,7 @@ def rt_trace_closest_host(scene: Scene, rays_host, hits_host=None, flags=0, stre
         hp = hits_host.ctypes.data_as(ctypes.c_void_p)
     tp = TraceParams()
     tp.flags = int(flags)
+    tp.block = int(block)
     _check(lib().rt_trace_closest_host(scene.handle, rp, n, hp, ctypes.byref(tp), _stream(stream)))
     return hits_host
 
@@ -423,7 +457,7 @@ class Batch:
     """Owns one rt_batch handle (multi-transmitter, multi-bounce pipeline)."""
 
     def __init__(self, scene, tx_pos, tx_param, kind=RT_RAYS_FIBONACCI, max_order=3, tmax=1000.0, rx_pos=None,
-                 use_graph=True):
+                 use_graph=True, ray_tile=0):
         self.scene = scene          # keeps the scene alive
         self.tx = np.ascontiguousarray(tx_pos, dtype=np.float32).reshape(-1, 3)
         self.param = np.ascontiguousarray(tx_param, dtype=np.int64).reshape(-1)
@@ -436,6 +470,7 @@ class Batch:
         d.n_rx = 0 if self.rx is None else len(self.rx)
         d.rx_pos = None if self.rx is None else self.rx.ctypes.data
         d.use_graph = 1 if use_graph else 0
+        d.ray_tile = int(ray_tile)
         h = ctypes.c_void_p()
         _check(lib().rt_batch_create(scene.handle, ctypes.byref(d), ctypes.byref(h)))
         self._h = h.value

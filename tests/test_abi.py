@@ -49,3 +49,10 @@ def test_ray_count_without_gpu():
     assert lib.rt_ray_count(0, 4096) == 4096
     assert [lib.rt_ray_count(1, L) for L in (0, 1, 8)] == [12, 42, 655362]
     assert lib.rt_ray_count(1, 13) == -1 and lib.rt_ray_count(7, 1) == -1 and lib.rt_ray_count(0, -1) == -1
+
+
+def test_new_entry_points_reject_null_without_gpu():
+    lib = rtbvh.lib()
+    assert lib.rt_scene_set_split_events(None, None, None) == -1
+    assert lib.rt_autotune(None, None, None, 0, 1.0, None, None) == -1
+    assert b"NULL" in lib.rt_last_error()

@@ -1,0 +1,109 @@
+"""Autotuner, ray tiles and split-kernel timing events (needs a GB300).
+
+Every configuration the autotuner may pick must return the same hits: the
+hit rule does not depend on the tree or on the walk's tile."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2208_10008_gb300 import scenes
+from helpers import compare_closest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def rb():
+    from paper_2208_10008_gb300 import rtbvh
+    assert torch.cuda.is_available(), "these tests need a CUDA GPU"
+    rtbvh.lib()
+    return rtbvh
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def test_every_tuning_gives_the_same_hits(rb):
+    sc, rays, p = scenes.workload_medium(level=5)
+    rnd = scenes.random_rays(sc, 3000, seed=21, tmax=400.0)
+    r = dev(np.concatenate([rays, rnd]))
+    s = rb.rt_scene_upload(sc.tris)
+    ref = None
+    for ml in (2, 4, 6, 8):
+        for bins in (8, 16, 32):
+            rb.rt_bvh_build(s, alpha=0.7, source=p["source"], max_leaf=ml, bins=bins, dist_norm=1)
+            for tile in (64, 128, 256):
+                h = rb.rt_trace_closest(s, r, block=tile)
+                o = rb.rt_trace_any(s, r, block=tile)
+                torch.cuda.synchronize()
+                got = (h.view(torch.int32).cpu().numpy(), o.cpu().numpy())
+                if ref is None:
+                    ref = got
+                else:
+                    assert np.array_equal(got[0], ref[0]), (ml, bins, tile)
+                    assert np.array_equal(got[1], ref[1]), (ml, bins, tile)
+
+
+def test_autotune_result_and_hits(rb, orc):
+    sc, rays, p = scenes.workload_tiny()
+    s = rb.rt_scene_upload(sc.tris)
+    r = dev(rays)
+    res = rb.rt_autotune(s, r, build_weight=1.0, alpha=0.7, source=p["source"], dist_norm=1)
+    assert res["n_tried"] == 36
+    assert res["max_leaf"] in (2, 4, 6, 8) and res["bins"] in (8, 16, 32) and res["block"] in (64, 128, 256)
+    assert 0 < res["score_ms"] <= res["default_score_ms"]
+    assert res["score_ms"] == pytest.approx(res["build_ms"] + res["trace_ms"], rel=1e-5)
+    # the scene is left built with the choice: its tree and hits are valid
+    info = rb.rt_bvh_info(s)
+    assert info["status"] == 0 and info["max_leaf_size"] <= res["max_leaf"]
+    h = rb.rt_trace_closest(s, r, block=res["block"])
+    torch.cuda.synchronize()
+    compare_closest(h.cpu().numpy(), orc.closest_brute(sc.tris, rays), sc.tris, rays, "autotuned")
+
+
+def test_batch_ray_tile_does_not_change_results(rb):
+    sc = scenes.tiny_city(seed=1)
+    rng = np.random.default_rng(5)
+    tx = np.stack([rng.uniform(20, 180, 2), rng.uniform(20, 180, 2), rng.uniform(10, 40, 2)], 1)
+    counts = np.array([900, 2100])
+    gx, gy = np.meshgrid(np.linspace(5, 195, 4), np.linspace(5, 195, 4))
+    rx = np.stack([gx.ravel(), gy.ravel(), np.full(gx.size, 10.0)], 1)
+    s = rb.rt_scene_upload(sc.tris)
+    rb.rt_bvh_build(s, alpha=0.7, source=tuple(tx.mean(0)), max_leaf=4, dist_norm=1)
+    outs = []
+    for tile in (0, 64, 256):
+        b = rb.Batch(s, tx, counts, rb.RT_RAYS_FIBONACCI, max_order=2, tmax=700.0, rx_pos=rx, ray_tile=tile)
+        b.run()
+        torch.cuda.synchronize()
+        outs.append(([b.order(k)[1].clone() for k in range(3)], b.visibility().clone()))
+        b.destroy()
+    for hits, vis in outs[1:]:
+        for k in range(3):
+            assert torch.equal(hits[k].view(torch.int32), outs[0][0][k].view(torch.int32))
+        assert torch.equal(vis, outs[0][1])
+    with pytest.raises(rb.RtError):
+        rb.Batch(s, tx, counts, rb.RT_RAYS_FIBONACCI, max_order=1, tmax=700.0, rx_pos=rx, ray_tile=100)
+
+
+def test_split_events_time_the_split_kernel(rb):
+    sc, rays, p = scenes.workload_medium(level=1)
+    s = rb.rt_scene_upload(sc.tris)
+    st = torch.cuda.Stream()
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(st):
+        rb.rt_bvh_build(s, stream=st, alpha=0.7, source=p["source"], dist_norm=1)
+        rb.rt_scene_set_split_events(s, s0, s1)
+        b0.record(st)
+        rb.rt_bvh_build(s, stream=st, alpha=0.7, source=p["source"], dist_norm=1)
+        b1.record(st)
+        rb.rt_scene_set_split_events(s)
+    st.synchronize()
+    whole, split = b0.elapsed_time(b1), s0.elapsed_time(s1)
+    assert 0 < split <= whole
+    # one event without the other is refused
+    assert rb.lib().rt_scene_set_split_events(s.handle, ctypes.c_void_p(s0.cuda_event), None) == -1
