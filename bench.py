@@ -66,6 +66,23 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(value, dist, device):
+    """The job's time is the slowest rank's: MAX all-reduce of one float
+    (identity when there is no process group)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world_size, steps, total_ms):
+    """Whole-job throughput (millions of units per second) for replicas that
+    each process units_per_rank per step, over the slowest rank's time."""
+    return world_size * units_per_rank * steps / (total_ms * 1e-3) / 1e6
+
+
 # ---------------------------------------------------------------- clocks
 class Clocks:
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -240,6 +257,42 @@ def run_batched(rtbvh, torch, runs):
             "speedup": ms_p / ms_b, "autotuned": tune,
             "batched": "one CUDA graph replay per run (device-side counts)",
             "plain": "per-transmitter rt_gen_rays / rt_trace_closest / rt_reflect calls, counts read by the host"}
+
+
+def run_alpha_sweep(rtbvh, torch, sc, rays, source, reps=10):
+    """The paper's comparison on this workload: the traditional SAH tree
+    (alpha = 1, Eq. 1) against the improved trees (alpha < 1, Eq. 2), same
+    rays, same walk: build and trace device times, nodes and triangles per ray."""
+    out = []
+    scene = rtbvh.rt_scene_upload(sc.tris)
+    hits = torch.empty((rays.shape[0], 4), dtype=torch.float32, device="cuda")
+    stats = torch.zeros((rays.shape[0], 2), dtype=torch.int32, device="cuda")
+    for alpha, dn in ((1.0, 0), (0.7, 1), (0.4, 1)):
+        kw = dict(alpha=alpha, dist_norm=dn, source=source, max_leaf=4, bins=16)
+        rtbvh.rt_bvh_build(scene, **kw)
+        rtbvh.rt_trace_closest(scene, rays, hits)
+        rtbvh.rt_trace_closest(scene, rays, torch.empty_like(hits), stats=stats)
+        torch.cuda.synchronize()
+        st = stats.double().mean(0).cpu().numpy()
+        bt, tt = [], []
+        for _ in range(reps):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record()
+            rtbvh.rt_bvh_build(scene, **kw)
+            e[1].record()
+            rtbvh.rt_trace_closest(scene, rays, hits)
+            e[2].record()
+            torch.cuda.synchronize()
+            bt.append(e[0].elapsed_time(e[1]))
+            tt.append(e[1].elapsed_time(e[2]))
+        out.append({"alpha": alpha, "dist_norm": dn, "build_ms": statistics.median(bt),
+                    "trace_ms": statistics.median(tt), "nodes_per_ray": float(st[0]),
+                    "tris_per_ray": float(st[1])})
+    scene.destroy()
+    base = out[0]["trace_ms"]
+    for o in out:
+        o["trace_speedup_vs_alpha1"] = base / o["trace_ms"]
+    return out
 
 
 def run_served(rtbvh, torch, seconds):
@@ -422,11 +475,7 @@ def run_ours(args):
     build_ms = [e[0].elapsed_time(e[1]) for e in evs]
     trace_ms = [e[1].elapsed_time(e[2]) for e in evs]
     split_ms = [e[0].elapsed_time(e[1]) for e in sev]
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), dist, "cuda")
     gpu_launches = (lc1 - lc0) + (trace_launches * args.steps if use_graph else 0)
 
     # e2e: host buffers through the C ABI (scene + rays in, hits out, every step)
@@ -470,6 +519,7 @@ def run_ours(args):
 
     extra = {}
     if not args.no_extra:
+        extra["alpha_sweep"] = run_alpha_sweep(rtbvh, torch, sc, rays, p["source"])
         extra["batched"] = run_batched(rtbvh, torch, args.batched_runs)
         extra["served"] = run_served(rtbvh, torch, args.serve_seconds)
     mean_trace_ms = statistics.mean(trace_ms)
@@ -491,7 +541,7 @@ def run_ours(args):
                           "latency of dependent splits, not by bandwidth (events recorded by the library around "
                           "the kernel in every timed step)"}
     dominant_split = mean_split_ms >= mean_trace_ms
-    value = ws * R * args.steps / (total_ms * 1e-3) / 1e6
+    value = job_rate(R, ws, args.steps, total_ms)
     cpu_v, cores, reps, el = cpu_checker_rate(sc, rays_np, p, args, args.cpu_seconds)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

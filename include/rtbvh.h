@@ -184,9 +184,29 @@ typedef struct {
 int rt_autotune(rt_scene scene, const rt_build_params* base, const rt_ray* rays_dev, int64_t n_rays,
                 float build_weight, rt_tune_result* out, void* stream);
 
+/* Test hooks (no counterpart in the paper): make failures happen on purpose,
+ * without faulting the device, so that the error paths can be tested.
+ * Process-wide; value 0 turns a hook off.
+ *   RT_DEBUG_SPIN_LIMIT    polls a build's work-queue wait may make without
+ *                          progress before it gives up (default 2^24)
+ *   RT_DEBUG_PHANTOM_TASK  every later build counts this many mid-level tasks
+ *                          that are never published: its warps wait for them
+ *                          until the spin limit, the build ends with the
+ *                          timeout status (rt_bvh_info: RT_ETIMEOUT)
+ *   RT_DEBUG_PHANTOM_ITEM  the same for big-node chunk items
+ *   RT_DEBUG_FAIL_ALLOC    the value-th device allocation from now fails
+ *                          (RT_ENOMEM) without calling the allocator
+ * Errors: RT_EINVAL (unknown hook or negative value). */
+#define RT_DEBUG_SPIN_LIMIT 1
+#define RT_DEBUG_PHANTOM_TASK 2
+#define RT_DEBUG_PHANTOM_ITEM 3
+#define RT_DEBUG_FAIL_ALLOC 4
+int rt_debug_inject(int hook, int64_t value);
+
 /* Synchronous: wait for the stream, then report the built tree.  Errors:
- * RT_EINVAL, RT_ENOTBUILT, RT_ECUDA; RT_EINTERNAL when the device status
- * word reports a failed check (info->status says which). */
+ * RT_EINVAL, RT_ENOTBUILT, RT_ECUDA; RT_ETIMEOUT when a work-queue wait of
+ * the build ran out (status 1); RT_EINTERNAL when the device status word
+ * reports a failed check (info->status says which). */
 int rt_bvh_info(rt_scene scene, void* stream, rt_bvh_info_t* info);
 
 /* Synchronous: copy the binary tree (Sec. II.C, Fig. 1) to host arrays in

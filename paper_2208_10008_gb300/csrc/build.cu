@@ -349,6 +349,8 @@ struct BuildArgs {
   int* epoch_dev;
   int n, K, max_leaf;
   int big, chunk, rpt, cap_t, cap_c, qa_cap, top_ctas;
+  int spin_limit;                    // polls without progress before a wait gives up
+  int phantom_tasks, phantom_items;  // test hooks: pending work that never comes
   CostP cp;
 };
 
@@ -597,6 +599,8 @@ __global__ void __launch_bounds__(kBlock) k_bin_root(BuildArgs A) {
       A.ctl->ti_tail = nch;
       A.ctl->ti_pending = nch;
     }
+    if (A.phantom_tasks) atomicAdd(&A.ctl->qa_pending, A.phantom_tasks);
+    if (A.phantom_items) atomicAdd(&A.ctl->ti_pending, A.phantom_items);
   }
   if (top) {
     // the root's children start empty; the root's chunks become items
@@ -701,7 +705,7 @@ __device__ __forceinline__ int block_sum(int v, int* red) {
 // One thread takes the next chunk item and waits for it to be published
 // (no warp-synchronous operation in this loop; the other threads wait at a
 // barrier).  Returns (-1, 0) when no big node is left (or the build failed).
-// The wait is bounded: kSpinLimit polls without new items set a timeout
+// The wait is bounded: spin_limit polls without new items set a timeout
 // status.
 __device__ int2 claim_item(const BuildArgs& A, int epoch) {
   const int s = atomicAdd(&A.ctl->ti_head, 1);
@@ -719,7 +723,7 @@ __device__ int2 claim_item(const BuildArgs& A, int epoch) {
         it = 0;
       }
     }
-    if (it > kSpinLimit) {
+    if (it > A.spin_limit) {
       set_status(A.ctl, kStQueueTimeout, 2);
       break;
     }
@@ -1262,7 +1266,7 @@ struct MidSmem {
 // stays converged: no lane ever parks at a warp-synchronous instruction
 // while another spins, which would tie up the SM's shuffle path.  Returns
 // false when the queue is drained (no big node and no task pending) or the
-// build failed.  The wait is bounded: kSpinLimit polls without progress set
+// build failed.  The wait is bounded: spin_limit polls without progress set
 // a timeout status.
 __device__ bool claim_task(const BuildArgs& A, int epoch, Task& t) {
   const int lane = threadIdx.x & 31;
@@ -1293,7 +1297,7 @@ __device__ bool claim_task(const BuildArgs& A, int epoch, Task& t) {
       }
     }
     if (__any_sync(kFull, stop)) break;
-    if (++it > kSpinLimit) {
+    if (++it > A.spin_limit) {
       if (lane == 0) set_status(A.ctl, kStQueueTimeout, 1);
       break;
     }
@@ -1774,6 +1778,11 @@ cudaError_t launch_build(rt_scene_s* s, const rt_build_params& p, cudaStream_t s
   A.cap_c = s->geom.cap_c;
   A.qa_cap = s->geom.qa_cap;
   A.top_ctas = n > g.big ? nsm : 0;
+  const DebugHooks dh = debug_hooks();
+  A.spin_limit = dh.spin_limit > 0 ? dh.spin_limit : kSpinLimit;
+  A.phantom_tasks = dh.phantom_tasks;
+  A.phantom_items = dh.phantom_items;
+  if (A.phantom_items && !A.top_ctas) A.top_ctas = nsm;  // someone must wait for the phantom items
   A.cp = CostP{p.alpha, p.t_i, p.t_trav, p.source[0], p.source[1], p.source[2], p.dist_norm};
   cudaError_t e;
   if ((e = cudaMemsetAsync(s->ctl, 0, sizeof(BuildCtl), st))) return e;

@@ -147,6 +147,14 @@ __host__ __device__ inline float iford(int i) {
 // adds the number of kernels it enqueues.
 void count_launches(int k);
 
+// Test hooks of rt_debug_inject (process-wide).
+struct DebugHooks {
+  int spin_limit;     // 0: kSpinLimit
+  int phantom_tasks;  // mid-level tasks counted but never published
+  int phantom_items;  // big-node chunk items counted but never published
+};
+DebugHooks debug_hooks();
+
 // Launch helpers implemented in build.cu / trace.cu -----------------------
 struct SceneDev;  // forward
 

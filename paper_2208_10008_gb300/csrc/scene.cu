@@ -16,6 +16,20 @@
 namespace rt {
 static std::atomic<uint64_t> g_launches{0};
 void count_launches(int k) { g_launches.fetch_add((uint64_t)(int64_t)k, std::memory_order_relaxed); }
+
+static std::atomic<int> g_spin_limit{0}, g_phantom_tasks{0}, g_phantom_items{0};
+static std::atomic<long long> g_fail_alloc{0};  // allocations left before the injected failure (0: off)
+DebugHooks debug_hooks() {
+  return DebugHooks{g_spin_limit.load(), g_phantom_tasks.load(), g_phantom_items.load()};
+}
+// True when the injected allocation failure is due now.
+bool alloc_should_fail() {
+  long long v = g_fail_alloc.load();
+  while (v > 0) {
+    if (g_fail_alloc.compare_exchange_weak(v, v - 1)) return v == 1;
+  }
+  return false;
+}
 }  // namespace rt
 
 namespace {
@@ -48,6 +62,7 @@ cudaError_t dev_alloc(T** p, size_t count) {
     *p = nullptr;
   }
   if (count == 0) count = 1;
+  if (rt::alloc_should_fail()) return cudaErrorMemoryAllocation;
   return cudaMalloc((void**)p, count * sizeof(T));
 }
 
@@ -79,11 +94,44 @@ int sm_count_dev() {
   return n > 0 ? n : 1;
 }
 
-// Size every per-triangle buffer for n triangles (grow only).  Buffers whose
-// old contents must never match a new build's epoch start zeroed.
+int alloc_capacity(rt_scene_s* s, int64_t m);
+
+// Size every per-triangle buffer for n triangles (grow only).  On failure
+// the scene is left empty (no triangles, no buffers, not built), never half
+// sized.
 int ensure_capacity(rt_scene_s* s, int64_t n) {
   if (n <= s->cap_tri && s->ctl) return RT_OK;
-  const int64_t m = n < 1 ? 1 : n;
+  const int r = alloc_capacity(s, n < 1 ? 1 : n);
+  if (r) {
+    void* per_tri[] = {s->tri_in, s->idx[0], s->rec[0], s->rec[1], s->node2, s->link2, s->wide, s->tri_leaf,
+                       s->qa, s->qa_ready, s->top_task, s->top_done, s->top_bins, s->top_ccnt, s->top_scnt,
+                       s->top_item, s->top_ready};
+    for (void* p : per_tri)
+      if (p) cudaFree(p);
+    s->tri_in = s->tri_leaf = nullptr;
+    s->idx[0] = nullptr;
+    s->rec[0] = s->rec[1] = nullptr;
+    s->node2 = nullptr;
+    s->link2 = nullptr;
+    s->wide = nullptr;
+    s->qa = nullptr;
+    s->qa_ready = nullptr;
+    s->top_task = nullptr;
+    s->top_done = nullptr;
+    s->top_bins = s->top_ccnt = s->top_scnt = nullptr;
+    s->top_item = nullptr;
+    s->top_ready = nullptr;
+    s->cap_tri = 0;
+    s->n_tri = 0;
+    s->built = false;
+    s->geom = rt::BuildGeom{};
+  }
+  return r;
+}
+
+// Buffers whose old contents must never match a new build's epoch start
+// zeroed.
+int alloc_capacity(rt_scene_s* s, int64_t m) {
   const rt::BuildGeom g = rt::build_geometry(m, sm_count_dev());
   RT_CUDA(dev_alloc(&s->tri_in, 3 * m), "alloc triangles");
   RT_CUDA(dev_alloc(&s->idx[0], m), "alloc index");
@@ -232,6 +280,7 @@ int rt_scene_destroy(rt_scene s) {
 int rt_bvh_build(rt_scene s, const rt_build_params* p, void* stream) {
   g_err[0] = 0;
   if (!s) return fail(RT_EINVAL, "scene is NULL");
+  if (!s->tri_in || !s->ctl) return fail(RT_EINVAL, "scene has no buffers (a failed upload or update)");
   int r = check_params(p);
   if (r) return r;
   cudaStream_t st = (cudaStream_t)stream;
@@ -244,6 +293,27 @@ int rt_bvh_build(rt_scene s, const rt_build_params* p, void* stream) {
   s->params = *p;
   s->built = true;
   return RT_OK;
+}
+
+int rt_debug_inject(int hook, int64_t value) {
+  g_err[0] = 0;
+  if (value < 0 || value > INT_MAX) return fail(RT_EINVAL, "value out of range");
+  switch (hook) {
+    case RT_DEBUG_SPIN_LIMIT:
+      rt::g_spin_limit.store((int)value);
+      return RT_OK;
+    case RT_DEBUG_PHANTOM_TASK:
+      rt::g_phantom_tasks.store((int)value);
+      return RT_OK;
+    case RT_DEBUG_PHANTOM_ITEM:
+      rt::g_phantom_items.store((int)value);
+      return RT_OK;
+    case RT_DEBUG_FAIL_ALLOC:
+      rt::g_fail_alloc.store(value);
+      return RT_OK;
+    default:
+      return fail(RT_EINVAL, "unknown hook %d", hook);
+  }
 }
 
 int rt_scene_set_split_events(rt_scene s, void* ev_begin, void* ev_end) {
@@ -274,6 +344,8 @@ int rt_bvh_info(rt_scene s, void* stream, rt_bvh_info_t* info) {
     ms = -1.f;
   }
   info->build_ms = ms;
+  if (c.status == rt::kStQueueTimeout)
+    return fail(RT_ETIMEOUT, "a work-queue wait of the build ran out (at %d)", c.status_where);
   if (c.status != 0) return fail(RT_EINTERNAL, "device status %d at %d", c.status, c.status_where);
   // traversal nodes reachable from the root, and their depth
   const int64_t slots = s->n_tri > 1 ? s->n_tri : 1;

@@ -39,7 +39,10 @@ EXPORTS = ["rt_version", "rt_launch_count", "rt_last_error", "rt_scene_upload", 
            "rt_reflect", "rt_batch_create", "rt_batch_run", "rt_batch_stats_get", "rt_batch_order",
            "rt_batch_visibility", "rt_batch_destroy", "rt_session_create", "rt_session_add_scene",
            "rt_session_submit", "rt_session_poll", "rt_session_wait", "rt_session_stats_get",
-           "rt_session_destroy", "rt_scene_set_split_events", "rt_autotune"]
+           "rt_session_destroy", "rt_scene_set_split_events", "rt_autotune", "rt_debug_inject"]
+
+# test hooks (rt_debug_inject)
+RT_DEBUG_SPIN_LIMIT, RT_DEBUG_PHANTOM_TASK, RT_DEBUG_PHANTOM_ITEM, RT_DEBUG_FAIL_ALLOC = 1, 2, 3, 4
 
 
 class RtError(RuntimeError):
@@ -125,6 +128,7 @@ def lib(build: bool = True):
             L.rt_bvh_build.argtypes = [vp, ctypes.POINTER(BuildParams), vp]
             L.rt_bvh_info.argtypes = [vp, vp, ctypes.POINTER(BvhInfo)]
             L.rt_scene_set_split_events.argtypes = [vp, vp, vp]
+            L.rt_debug_inject.argtypes = [i32, i64]
             L.rt_autotune.argtypes = [vp, ctypes.POINTER(BuildParams), vp, i64, ctypes.c_float,
                                       ctypes.POINTER(TuneResult), vp]
             L.rt_bvh_export.argtypes = [vp, vp, vp, vp, vp, vp, vp]
@@ -264,6 +268,11 @@ def rt_scene_set_split_events(scene: Scene, ev_begin=None, ev_end=None):
             e.record()  # torch creates its event on the first record
     h = [ctypes.c_void_p(e.cuda_event) if e is not None else None for e in (ev_begin, ev_end)]
     _check(lib().rt_scene_set_split_events(scene.handle, h[0], h[1]))
+
+
+def rt_debug_inject(hook: int, value: int):
+    """Test hooks (see rtbvh.h): spin limit, phantom work, failing allocations."""
+    _check(lib().rt_debug_inject(int(hook), int(value)))
 
 
 def rt_autotune(scene: Scene, rays, build_weight=1.0, stream=None, **base) -> dict:

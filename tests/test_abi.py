@@ -56,3 +56,12 @@ def test_new_entry_points_reject_null_without_gpu():
     assert lib.rt_scene_set_split_events(None, None, None) == -1
     assert lib.rt_autotune(None, None, None, 0, 1.0, None, None) == -1
     assert b"NULL" in lib.rt_last_error()
+
+
+def test_debug_hooks_validate_without_gpu():
+    lib = rtbvh.lib()
+    assert lib.rt_debug_inject(99, 1) == -1
+    assert lib.rt_debug_inject(rtbvh.RT_DEBUG_SPIN_LIMIT, -5) == -1
+    for hook in (rtbvh.RT_DEBUG_SPIN_LIMIT, rtbvh.RT_DEBUG_PHANTOM_TASK, rtbvh.RT_DEBUG_PHANTOM_ITEM,
+                 rtbvh.RT_DEBUG_FAIL_ALLOC):
+        assert lib.rt_debug_inject(hook, 0) == 0
