@@ -173,6 +173,54 @@ def prism_city(n_buildings: int, size: float, seed: int, ngon=(4, 8),
                  [np.asarray(t, dtype=np.float64) for t in tx_keepout])
 
 
+def metro_city(seed: int = 5, n_buildings: int = 300_000, size: float = 20_000.0, ngon=(8, 16),
+               rmin: float = 4.0, rmax: float = 12.5, clusters: int = 20, sigma: float = 800.0) -> Scene:
+    """The large metro: convex 8-16-gon prisms on a 20 x 20 km ground, centres
+    from an equal mixture of 20 Gaussians (uniform centres, std 800 m, clipped),
+    heights lognormal(3, 0.5) m.  Same footprint and height recipe as
+    prism_city, drawn in bulk (whole arrays per quantity) so that millions of
+    triangles take seconds; per prism the same triangles as _prism."""
+    rng = _rng(seed)
+    nb = int(n_buildings)
+    cc = rng.uniform(rmax, size - rmax, size=(clusters, 2))
+    ng = rng.integers(ngon[0], ngon[1] + 1, size=nb)
+    ang = rng.uniform(0.0, 2 * math.pi, size=(nb, ngon[1]))
+    r = rng.uniform(rmin, rmax, size=nb)
+    rot = rng.uniform(0.0, math.pi, size=nb)
+    k = rng.integers(0, clusters, size=nb)
+    c = np.clip(cc[k] + rng.normal(0.0, sigma, size=(nb, 2)), r[:, None], size - r[:, None])
+    h = rng.lognormal(3.0, 0.5, size=nb)
+    # the first ng angles of each row, sorted
+    ang = np.where(np.arange(ngon[1])[None, :] < ng[:, None], ang, np.inf)
+    ang = np.sort(ang, axis=1)
+    parts = []
+    for n in range(ngon[0], ngon[1] + 1):
+        sel = np.nonzero(ng == n)[0]
+        if len(sel) == 0:
+            continue
+        a = ang[sel, :n] + rot[sel, None]
+        x = c[sel, 0, None] + r[sel, None] * np.cos(a)
+        y = c[sel, 1, None] + r[sel, None] * np.sin(a)
+        z0 = np.zeros_like(x)
+        z1 = np.broadcast_to(h[sel, None], x.shape)
+        bot = np.stack([x, y, z0], axis=-1)          # [m, n, 3]
+        top = np.stack([x, y, z1], axis=-1)
+        i = np.arange(n)
+        j = (i + 1) % n
+        walls_a = np.stack([bot[:, i], bot[:, j], top[:, j]], axis=2)   # [m, n, 3, 3]
+        walls_b = np.stack([bot[:, i], top[:, j], top[:, i]], axis=2)
+        walls = np.stack([walls_a, walls_b], axis=2).reshape(len(sel), 2 * n, 3, 3)
+        f = np.arange(1, n - 1)
+        roof = np.stack([np.broadcast_to(top[:, :1], (len(sel), n - 2, 3)), top[:, f], top[:, f + 1]], axis=2)
+        floor = np.stack([np.broadcast_to(bot[:, :1], (len(sel), n - 2, 3)), bot[:, f + 1], bot[:, f]], axis=2)
+        parts.append((sel, np.concatenate([walls, roof, floor], axis=1).astype(np.float32)))
+    # buildings in draw order
+    order = np.argsort(np.concatenate([p[0] for p in parts]), kind="stable")
+    per = [t for p in parts for t in p[1]]
+    tris = np.concatenate([per[o] for o in order] + [np.asarray(_ground(0.0, 0.0, size, size), np.float32)])
+    return Scene(tris, (0.0, 0.0, size, size), nb, seed, "metro_city", [])
+
+
 def medium_city(seed: int = 2, n_buildings: int = 1000, size: float = 1000.0) -> Scene:
     """1000 convex 4-8-gon prisms on 1 x 1 km (~20k triangles), Tx at the centre, 30 m."""
     tx = (size / 2, size / 2, 30.0)

@@ -491,3 +491,21 @@ def test_generators_deterministic_and_counts():
     tx = m.tx[0]
     # the transmitter is not inside any building footprint's bounding circle
     assert tx[2] == 30.0
+
+
+def test_metro_generator_counts_prisms_and_determinism():
+    a = scenes.metro_city(n_buildings=300, size=1500.0)
+    b = scenes.metro_city(n_buildings=300, size=1500.0)
+    assert a.tris.tobytes() == b.tris.tobytes()
+    # every building is a closed convex 8..16-gon prism: 4n - 4 triangles, plus 2 ground
+    assert (a.n_tri - 2) % 4 == 0 and 300 * 28 <= a.n_tri - 2 <= 300 * 60
+    # the first building, rebuilt with the per-prism generator from its own footprint
+    t = a.tris.astype(np.float64)
+    h = t[:, :, 2].max(axis=1)
+    k = 0
+    while t[k, 0, 2] == 0.0:  # building 0's walls start at its floor; its roof fan starts at z = h
+        k += 1
+    n = k // 2
+    poly = t[0:2 * n:2, 0, :2]
+    ref = np.asarray(scenes._prism(poly, h[0]), np.float64).astype(np.float32)
+    assert np.array_equal(a.tris[:len(ref)], ref)
