@@ -65,6 +65,20 @@ __device__ __forceinline__ void set_status(BuildCtl* ctl, int code, int where) {
 
 __device__ __forceinline__ int ld_volatile(const int* p) { return *(const volatile int*)p; }
 
+// Acquire load / release store / release add at GPU scope: the flag and
+// counter protocol of the work queues without full memory fences.
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_release_add(int* p, int v) {
+  asm volatile("red.release.gpu.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 // AABB centre, evaluated identically wherever a bin is needed.
 __device__ __forceinline__ float centre(float lo, float hi) { return __fmul_rn(__fadd_rn(lo, hi), 0.5f); }
 
@@ -393,8 +407,7 @@ __device__ void push_task(const BuildArgs& A, const Task& t, int epoch) {
   }
   atomicAdd(&A.ctl->qa_pending, 1);
   A.qa[s] = t;
-  __threadfence();
-  atomicExch(&A.qa_ready[s], epoch);
+  st_release(&A.qa_ready[s], epoch);
 }
 
 // Hand up to 3 tasks to the mid-level queue at once (one thread): one slot
@@ -408,8 +421,7 @@ __device__ void push_tasks(const BuildArgs& A, const Task* t, int k, int epoch) 
   }
   atomicAdd(&A.ctl->qa_pending, k);
   for (int i = 0; i < k; ++i) A.qa[s + i] = t[i];
-  __threadfence();
-  for (int i = 0; i < k; ++i) atomicExch(&A.qa_ready[s + i], epoch);
+  for (int i = 0; i < k; ++i) st_release(&A.qa_ready[s + i], epoch);
 }
 
 __device__ __forceinline__ Task make_task(int begin, int count, int parent, int side, int depth, const BinU& u,
@@ -711,8 +723,7 @@ __device__ int2 claim_item(const BuildArgs& A, int epoch) {
   const int s = atomicAdd(&A.ctl->ti_head, 1);
   int seen = -1;
   for (int it = 0;; ++it) {
-    if (s < A.cap_c && ld_volatile(&A.tready[s]) == epoch) {
-      __threadfence();
+    if (s < A.cap_c && ld_acquire(&A.tready[s]) == epoch) {
       return __ldcg(A.titem + s);
     }
     if ((it & 3) == 0) {
@@ -1034,8 +1045,7 @@ __device__ void top_emit(const BuildArgs& A, TopSmem& S, const TopTask& T, int e
     const int ncs = s ? nch1 : nch0;
     for (int q = tid; q < ncs; q += kBlock) {
       A.titem[S.ibase[s] + q] = make_int2(T.child_slot + s, q);
-      __threadfence();
-      atomicExch(&A.tready[S.ibase[s] + q], epoch);
+      st_release(&A.tready[S.ibase[s] + q], epoch);
     }
   }
 }
@@ -1066,10 +1076,9 @@ __device__ void top_loop(const BuildArgs& A, TopSmem& S, int epoch) {
     if (it.x < 0) return;
     top_item(A, S, it.x, it.y, epoch);
     __syncthreads();
-    if (threadIdx.x == 0) {
-      __threadfence();
-      atomicSub(&A.ctl->ti_pending, 1);
-    }
+    // release: the mid-level tasks this item pushed are counted before the
+    // item stops counting (the warps' exit test reads ti_pending first)
+    if (threadIdx.x == 0) red_release_add(&A.ctl->ti_pending, -1);
   }
 }
 
@@ -1277,7 +1286,7 @@ __device__ bool claim_task(const BuildArgs& A, int epoch, Task& t) {
   bool got = false;
   // every exit is a warp vote, so the warp leaves the loop converged
   for (;;) {
-    const bool rdy = s < A.qa_cap && ld_volatile(&A.qa_ready[s]) == epoch;
+    const bool rdy = s < A.qa_cap && ld_acquire(&A.qa_ready[s]) == epoch;
     if (__any_sync(kFull, rdy)) {
       got = true;
       break;
@@ -1285,10 +1294,7 @@ __device__ bool claim_task(const BuildArgs& A, int epoch, Task& t) {
     bool stop = false;
     if ((it & 3) == 0) {
       // done when no big node is left and then no mid-level task either
-      if (ld_volatile(&A.ctl->ti_pending) == 0) {
-        __threadfence();
-        stop = ld_volatile(&A.ctl->qa_pending) == 0;
-      }
+      if (ld_acquire(&A.ctl->ti_pending) == 0) stop = ld_volatile(&A.ctl->qa_pending) == 0;
       stop = stop || ld_volatile(&A.ctl->status) != 0;
       const int prog = __shfl_sync(kFull, ld_volatile(&A.ctl->qa_tail) + ld_volatile(&A.ctl->ti_head), 0);
       if (prog != seen) {  // work moved: restart the no-progress budget
@@ -1304,7 +1310,6 @@ __device__ bool claim_task(const BuildArgs& A, int epoch, Task& t) {
     __nanosleep(200);
   }
   if (got) {
-    __threadfence();
     const int4* q = reinterpret_cast<const int4*>(A.qa + s);
     const int4 a = __ldcg(q), b = __ldcg(q + 1), c = __ldcg(q + 2);
     t.begin = a.x;
@@ -1340,10 +1345,21 @@ __device__ void mid_split(const BuildArgs& A, MidWarp& W, const Task& t, int epo
     scl[a] = bin_scale(t.clo[a], t.chi[a], K);
   }
   for (int w = lane; w < K3 * kBinVals; w += 32) W.bins[w] = 0u;
-  if (staged) {
-    for (int k = lane; k < n; k += 32) {
-      W.stage[2 * k] = __ldcg(src + 2 * k);
-      W.stage[2 * k + 1] = __ldcg(src + 2 * k + 1);
+  if (staged) {  // two records per lane in flight
+    for (int k0 = lane; k0 < n; k0 += 64) {
+      float4 v[4];
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+        if (k0 + 32 * u < n) {
+          v[2 * u] = __ldcg(src + 2 * (k0 + 32 * u));
+          v[2 * u + 1] = __ldcg(src + 2 * (k0 + 32 * u) + 1);
+        }
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+        if (k0 + 32 * u < n) {
+          W.stage[2 * (k0 + 32 * u)] = v[2 * u];
+          W.stage[2 * (k0 + 32 * u) + 1] = v[2 * u + 1];
+        }
     }
   }
   __syncwarp();
@@ -1519,10 +1535,9 @@ __device__ void mid_loop(const BuildArgs& A, MidWarp& W, int epoch) {
       mid_split(A, W, t, epoch, ws, cont, have_cont);
     }
     __syncwarp();
-    if (!have_cont && lane == 0) {
-      __threadfence();
-      atomicSub(&A.ctl->qa_pending, 1);
-    }
+    // a task's pushes incremented this same counter first, so the decrement
+    // can never make it read zero while they are pending
+    if (!have_cont && lane == 0) atomicSub(&A.ctl->qa_pending, 1);
   }
   if (lane == 0) {
     if (ws.n_int) atomicAdd(&A.ctl->n_internal, ws.n_int);
