@@ -291,28 +291,30 @@ __device__ __forceinline__ void eval_axis(const unsigned* bins, int K, int n, in
   }
 }
 
-// eval_axis for two axes at once (K <= 16): lanes 0..15 take the bins of
-// axis a0, lanes 16..31 those of axis a1, and the scans stop at the half-warp
-// boundary.  Same candidates, costs and tie rule as two eval_axis calls.
-__device__ __forceinline__ void eval_pair(const unsigned* bins, int K, int n, int a0, int a1, const CostP& cp,
+// eval_axis for several axes at once: lanes are cut into segments of K,
+// segment g holding the bins of axis a0 + g (up to 32 / K axes per pass),
+// and the scans stop at the segment bounds.  Same candidates, costs and tie
+// rule as one eval_axis call per axis.
+__device__ __forceinline__ void eval_axes(const unsigned* bins, int K, int n, int a0, int na, const CostP& cp,
                                           Split& best) {
   const int lane = threadIdx.x & 31;
-  const int hi16 = lane >> 4, sl = lane & 15;
-  const int a = hi16 ? a1 : a0;
+  const int g = lane / K, sl = lane - g * K;
+  const bool in = g < na;
+  const int a = a0 + (in ? g : 0);
   __syncwarp();
-  const BinU x = sl < K ? binu_load(bins + (a * K + sl) * kBinVals) : binu_empty();
+  const BinU x = in ? binu_load(bins + (a * K + sl) * kBinVals) : binu_empty();
   BinU pre = x, suf = x;
 #pragma unroll
-  for (int o = 1; o < 16; o <<= 1) {
+  for (int o = 1; o < 32; o <<= 1) {
     const BinU u = binu_up(pre, o), d = binu_down(suf, o);
     if (sl >= o) pre = binu_join(pre, u);
-    if (sl + o < 16) suf = binu_join(suf, d);
+    if (sl + o < K) suf = binu_join(suf, d);
   }
-  const BinU L = binu_up(pre, 1);  // lane k of a half: bins 0 .. k-1 of its axis
-  const BinU C = binu_idx(pre, hi16 * 16 + 15);
+  const BinU L = binu_up(pre, 1);  // lane k of a segment: bins 0 .. k-1 of its axis
+  const BinU C = binu_idx(pre, min(g * K + K - 1, 31));
   float cost = INFINITY;
   int cand = INT_MAX;
-  if (sl >= 1 && sl < K && L.n > 0 && L.n < n) {
+  if (in && sl >= 1 && L.n > 0 && L.n < n) {
     const float c = eq2_cost(make_float3(L.l0, L.l1, L.l2), make_float3(L.h0, L.h1, L.h2), L.n,
                              make_float3(suf.l0, suf.l1, suf.l2), make_float3(suf.h0, suf.h1, suf.h2), n - L.n,
                              make_float3(C.l0, C.l1, C.l2), make_float3(C.h0, C.h1, C.h2), cp);
@@ -332,7 +334,7 @@ __device__ __forceinline__ void eval_pair(const unsigned* bins, int K, int n, in
   }
   if (cand != INT_MAX && (cost < best.cost || (cost == best.cost && cand < best.cand))) {
     const int ax = cand / (K - 1);
-    const int w = (ax == a0 ? 0 : 16) + cand - ax * (K - 1) + 1;
+    const int w = (ax - a0) * K + cand - ax * (K - 1) + 1;
     best.cost = cost;
     best.cand = cand;
     best.L = binu_idx(L, w);
@@ -1383,8 +1385,10 @@ __device__ void mid_split(const BuildArgs& A, MidWarp& W, const Task& t, int epo
   __syncwarp();
   Split best;
   split_none(best);
-  if (K <= 16) {  // axes x and y in one pass, then z
-    eval_pair(W.bins, K, n, 0, 1, A.cp, best);
+  if (3 * K <= 32) {  // all three axes in one pass
+    eval_axes(W.bins, K, n, 0, 3, A.cp, best);
+  } else if (2 * K <= 32) {  // x and y in one pass, then z
+    eval_axes(W.bins, K, n, 0, 2, A.cp, best);
     if (scl[2] > 0.f) eval_axis(W.bins, K, n, 2, A.cp, best);
   } else {
 #pragma unroll
