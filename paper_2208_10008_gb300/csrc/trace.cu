@@ -306,8 +306,7 @@ __global__ void __launch_bounds__(kTile) k_trace(TraceArgs A) {
   bool flag = false, done = false;
   uint32_t n_nodes = 0, n_tris = 0;
   float bound = r.tmax;
-  int st_ref[kStack];
-  float st_t[kStack];
+  int2 st[kStack];  // (ref, entry distance bits) of the boxes still to visit
   int sp = 0;
   // Triangles whose float64 answer could beat the float32 one: uncertain
   // ones and every certain hit near the interval, with a lower bound on t.
@@ -335,15 +334,20 @@ __global__ void __launch_bounds__(kTile) k_trace(TraceArgs A) {
       walk_all = true;
     }
   };
-  if (r.valid) {
-    st_ref[0] = __ldg(A.wide_root);
-    st_t[0] = -INFINITY;
-    sp = 1;
-  }
-  while (sp > 0 && !done) {
-    --sp;
-    const int ref = st_ref[sp];
-    if (st_t[sp] > bound) continue;
+  // the node being visited stays in registers (cur); only the other
+  // children hit by the ray go to the stack, nearest popped first
+  int cur = r.valid ? __ldg(A.wide_root) : INT_MIN;
+  float cur_t = -INFINITY;
+  while (!done) {
+    if (cur == INT_MIN) {
+      if (sp == 0) break;
+      --sp;
+      cur = st[sp].x;
+      cur_t = __int_as_float(st[sp].y);
+    }
+    const int ref = cur;
+    cur = INT_MIN;
+    if (cur_t > bound) continue;
     if (ref >= 0) {
       if (kStats) ++n_nodes;
       float tn[4];
@@ -359,16 +363,18 @@ __global__ void __launch_bounds__(kTile) k_trace(TraceArgs A) {
       cswap(tb, rb, td, rd);
       cswap(tb, rb, tc, rc);
       int cnt = __popc(m);
-      if (sp + cnt > kStack) {  // cannot hold the children: leave it to the float64 pass
+      if (cnt == 0) continue;
+      if (sp + cnt - 1 > kStack) {  // cannot hold the children: leave it to the float64 pass
         flag = true;
         walk_all = true;
         break;
       }
-      // push farthest first so the nearest is popped next
-      if (cnt > 3) { st_ref[sp] = rd; st_t[sp] = td; ++sp; }
-      if (cnt > 2) { st_ref[sp] = rc; st_t[sp] = tc; ++sp; }
-      if (cnt > 1) { st_ref[sp] = rb; st_t[sp] = tb; ++sp; }
-      if (cnt > 0) { st_ref[sp] = ra; st_t[sp] = ta; ++sp; }
+      // push farthest first so the nearest stacked one is popped next
+      if (cnt > 3) st[sp++] = make_int2(rd, __float_as_int(td));
+      if (cnt > 2) st[sp++] = make_int2(rc, __float_as_int(tc));
+      if (cnt > 1) st[sp++] = make_int2(rb, __float_as_int(tb));
+      cur = ra;
+      cur_t = ta;
       continue;
     }
     // leaf
