@@ -244,74 +244,60 @@ __device__ __forceinline__ void split_none(Split& s) {
   s.R = binu_empty();
 }
 
-// The K - 1 planes of axis `a` by one warp: lane k holds bin k; warp scans
-// give every lane the union of the bins left of plane k and right of it;
-// lane k evaluates Eq. 2 at plane k.  `best` (identical in every lane) is
-// replaced if this axis has a lower cost, ties going to the lower candidate
-// (lowest axis, then lowest plane).  The union of all bins is the node box.
-__device__ __forceinline__ void eval_axis(const unsigned* bins, int K, int n, int a, const CostP& cp, Split& best) {
-  const int lane = threadIdx.x & 31;
-  __syncwarp();
-  const BinU x = lane < K ? binu_load(bins + (a * K + lane) * kBinVals) : binu_empty();
-  BinU pre = x, suf = x;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const BinU u = binu_up(pre, o), d = binu_down(suf, o);
-    if (lane >= o) pre = binu_join(pre, u);
-    if (lane + o < 32) suf = binu_join(suf, d);
-  }
-  const BinU L = binu_up(pre, 1);  // lane k: bins 0 .. k-1
-  const BinU C = binu_idx(pre, 31);
-  float cost = INFINITY;
-  int cand = INT_MAX;
-  if (lane >= 1 && lane < K && L.n > 0 && L.n < n) {
-    const float c = eq2_cost(make_float3(L.l0, L.l1, L.l2), make_float3(L.h0, L.h1, L.h2), L.n,
-                             make_float3(suf.l0, suf.l1, suf.l2), make_float3(suf.h0, suf.h1, suf.h2), n - L.n,
-                             make_float3(C.l0, C.l1, C.l2), make_float3(C.h0, C.h1, C.h2), cp);
-    if (c < INFINITY) {
-      cost = c;
-      cand = a * (K - 1) + lane - 1;
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const float oc = __shfl_xor_sync(kFull, cost, o);
-    const int ok = __shfl_xor_sync(kFull, cand, o);
-    if (oc < cost || (oc == cost && ok < cand)) {
-      cost = oc;
-      cand = ok;
-    }
-  }
-  if (cand != INT_MAX && (cost < best.cost || (cost == best.cost && cand < best.cand))) {
-    const int w = cand - a * (K - 1) + 1;
-    best.cost = cost;
-    best.cand = cand;
-    best.L = binu_idx(L, w);
-    best.R = binu_idx(suf, w);
-  }
+// Count and box of a run of bins: the part of a bin the cost needs.
+struct BinB {
+  int n;
+  float l0, l1, l2, h0, h1, h2;
+};
+__device__ __forceinline__ BinB binb_empty() { return {0, FLT_MAX, FLT_MAX, FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX}; }
+__device__ __forceinline__ BinB binb_join(const BinB& x, const BinB& y) {
+  return {x.n + y.n,          fminf(x.l0, y.l0), fminf(x.l1, y.l1), fminf(x.l2, y.l2),
+          fmaxf(x.h0, y.h0),  fmaxf(x.h1, y.h1), fmaxf(x.h2, y.h2)};
 }
+__device__ __forceinline__ BinB binb_load(const unsigned* e) {
+  const unsigned c = e[0];
+  if (c == 0) return binb_empty();
+  return {(int)c, uval(~e[1]), uval(~e[2]), uval(~e[3]), uval(e[4]), uval(e[5]), uval(e[6])};
+}
+#define RT_BINB_SHFL(F, x, arg)                                                                            \
+  BinB {                                                                                                   \
+    F(kFull, (x).n, arg), F(kFull, (x).l0, arg), F(kFull, (x).l1, arg), F(kFull, (x).l2, arg),             \
+        F(kFull, (x).h0, arg), F(kFull, (x).h1, arg), F(kFull, (x).h2, arg)                                 \
+  }
 
-// eval_axis for several axes at once: lanes are cut into segments of K,
-// segment g holding the bins of axis a0 + g (up to 32 / K axes per pass),
-// and the scans stop at the segment bounds.  Same candidates, costs and tie
-// rule as one eval_axis call per axis.
-__device__ __forceinline__ void eval_axes(const unsigned* bins, int K, int n, int a0, int na, const CostP& cp,
-                                          Split& best) {
+// Eq. 2 at the K - 1 planes of na axes (a0 .. a0 + na - 1, na * K <= 32) by
+// one warp.  Lanes are cut into segments of K, lane sl of segment g holding
+// bin sl of axis a0 + g (`bins0` points at the bins of axis a0, the others
+// follow); segmented warp scans (log2 K steps) of the bins' counts and boxes
+// give every lane the union of the bins left of plane sl and right of it,
+// and lane sl evaluates Eq. 2 there.  `best` (identical in every lane) is
+// replaced if a plane has a lower cost, ties going to the lower candidate
+// (lowest axis, then lowest plane); the winning children's centre bounds
+// are then gathered by warp reductions over the bins' codes.  The union of
+// a segment is the node box.
+// kVals: words per bin (13, or 7 for bins of count and box only); kCentres:
+// gather the children's centre bounds (13-word bins only; otherwise the
+// caller derives the children's unions itself and only best.L.n is exact).
+template <int kVals, bool kCentres>
+__device__ __forceinline__ void eval_seg(const unsigned* bins0, int K, int n, int a0, int na, const CostP& cp,
+                                         Split& best) {
   const int lane = threadIdx.x & 31;
   const int g = lane / K, sl = lane - g * K;
   const bool in = g < na;
   const int a = a0 + (in ? g : 0);
+  const unsigned* e = bins0 + ((in ? g : 0) * K + sl) * kVals;
   __syncwarp();
-  const BinU x = in ? binu_load(bins + (a * K + sl) * kBinVals) : binu_empty();
-  BinU pre = x, suf = x;
+  const BinB x = in ? binb_load(e) : binb_empty();
+  BinB pre = x, suf = x;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const BinU u = binu_up(pre, o), d = binu_down(suf, o);
-    if (sl >= o) pre = binu_join(pre, u);
-    if (sl + o < K) suf = binu_join(suf, d);
+    if (o >= K) break;
+    const BinB u = RT_BINB_SHFL(__shfl_up_sync, pre, o), d = RT_BINB_SHFL(__shfl_down_sync, suf, o);
+    if (sl >= o) pre = binb_join(pre, u);
+    if (sl + o < K) suf = binb_join(suf, d);
   }
-  const BinU L = binu_up(pre, 1);  // lane k of a segment: bins 0 .. k-1 of its axis
-  const BinU C = binu_idx(pre, min(g * K + K - 1, 31));
+  const BinB L = RT_BINB_SHFL(__shfl_up_sync, pre, 1);  // lane sl: bins 0 .. sl-1 of its axis
+  const BinB C = RT_BINB_SHFL(__shfl_sync, pre, min(g * K + K - 1, 31));
   float cost = INFINITY;
   int cand = INT_MAX;
   if (in && sl >= 1 && L.n > 0 && L.n < n) {
@@ -332,14 +318,45 @@ __device__ __forceinline__ void eval_axes(const unsigned* bins, int K, int n, in
       cand = ok;
     }
   }
-  if (cand != INT_MAX && (cost < best.cost || (cost == best.cost && cand < best.cand))) {
-    const int ax = cand / (K - 1);
-    const int w = (ax - a0) * K + cand - ax * (K - 1) + 1;
+  if (__any_sync(kFull, cand != INT_MAX && (cost < best.cost || (cost == best.cost && cand < best.cand)))) {
+    const int ax = cand / (K - 1), gw = ax - a0, pl = cand - ax * (K - 1) + 1;  // plane pl of axis ax
+    const int w = gw * K + pl;
+    const BinB Lb = RT_BINB_SHFL(__shfl_sync, L, w), Rb = RT_BINB_SHFL(__shfl_sync, suf, w);
+    const bool mine = in && g == gw;
+    unsigned lc[6] = {0u, 0u, 0u, 0u, 0u, 0u}, rc[6] = {0u, 0u, 0u, 0u, 0u, 0u};
+    if (kCentres) {
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        const unsigned v = mine ? e[7 + q] : 0u;
+        lc[q] = __reduce_max_sync(kFull, sl < pl ? v : 0u);
+        rc[q] = __reduce_max_sync(kFull, sl >= pl ? v : 0u);
+      }
+    }
     best.cost = cost;
     best.cand = cand;
-    best.L = binu_idx(L, w);
-    best.R = binu_idx(suf, w);
+    best.L = {Lb.n, Lb.l0, Lb.l1, Lb.l2, Lb.h0, Lb.h1, Lb.h2,
+              uval(~lc[0]), uval(~lc[1]), uval(~lc[2]), uval(lc[3]), uval(lc[4]), uval(lc[5])};
+    best.R = {Rb.n, Rb.l0, Rb.l1, Rb.l2, Rb.h0, Rb.h1, Rb.h2,
+              uval(~rc[0]), uval(~rc[1]), uval(~rc[2]), uval(rc[3]), uval(rc[4]), uval(rc[5])};
   }
+}
+#undef RT_BINB_SHFL
+
+// One axis (`abins`: its K bins).
+__device__ __forceinline__ void eval_axis_at(const unsigned* abins, int K, int n, int a, const CostP& cp,
+                                             Split& best) {
+  eval_seg<kBinVals, true>(abins, K, n, a, 1, cp, best);
+}
+__device__ __forceinline__ void eval_axis(const unsigned* bins, int K, int n, int a, const CostP& cp, Split& best) {
+  eval_seg<kBinVals, true>(bins + a * K * kBinVals, K, n, a, 1, cp, best);
+}
+__device__ __forceinline__ void eval_axes_at(const unsigned* bins0, int K, int n, int a0, int na, const CostP& cp,
+                                             Split& best) {
+  eval_seg<kBinVals, true>(bins0, K, n, a0, na, cp, best);
+}
+__device__ __forceinline__ void eval_axes(const unsigned* bins, int K, int n, int a0, int na, const CostP& cp,
+                                          Split& best) {
+  eval_seg<kBinVals, true>(bins + a0 * K * kBinVals, K, n, a0, na, cp, best);
 }
 
 // ------------------------------------------------------------------ arguments
@@ -1220,20 +1237,15 @@ __device__ void micro_build(const BuildArgs& A, float4 rlo, float4 rhi, int n, i
   ws.deep = max(ws.deep, (int)__reduce_max_sync(kFull, (unsigned)deep));
 }
 
-// Load a node of at most 32 records, order them by (Morton key, id) with a
-// warp bitonic sort, write them to buffer 0 in that order (the final order of
-// their leaves) and build the subtree.
-__device__ void micro_task(const BuildArgs& A, int begin, int n, int parity, int parent, int side, int depth,
-                           int epoch, WarpStats& ws) {
+// A node of at most 32 records, record `lane` in registers (lo, hi): order
+// them by (Morton key, id) with a warp bitonic sort, write them to buffer 0
+// at gbegin in that order (the final order of their leaves) and build the
+// subtree.
+__device__ void micro_sort_build(const BuildArgs& A, float4 lo, float4 hi, int gbegin, int n, int parent, int side,
+                                 int depth, int epoch, WarpStats& ws) {
   const int lane = threadIdx.x & 31;
-  float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
-  unsigned long long key = ~0ull;
-  if (lane < n) {
-    const float4* p = A.rec[parity] + 2 * ((size_t)begin + lane);
-    lo = __ldcg(p);
-    hi = __ldcg(p + 1);
-    key = ((unsigned long long)__float_as_uint(hi.w) << 32) | (unsigned)__float_as_int(lo.w);
-  }
+  unsigned long long key =
+      lane < n ? ((unsigned long long)__float_as_uint(hi.w) << 32) | (unsigned)__float_as_int(lo.w) : ~0ull;
   int src = lane;
   __syncwarp();
 #pragma unroll
@@ -1256,11 +1268,24 @@ __device__ void micro_task(const BuildArgs& A, int begin, int n, int parity, int
   const float4 shi = make_float4(__shfl_sync(kFull, hi.x, src), __shfl_sync(kFull, hi.y, src),
                                  __shfl_sync(kFull, hi.z, src), __shfl_sync(kFull, hi.w, src));
   if (lane < n) {
-    float4* p = A.rec[0] + 2 * ((size_t)begin + lane);
+    float4* p = A.rec[0] + 2 * ((size_t)gbegin + lane);
     p[0] = slo;
     p[1] = shi;
   }
-  if (n > A.max_leaf) micro_build(A, slo, shi, n, begin, parent, side, depth, epoch, ws);
+  if (__any_sync(kFull, n > A.max_leaf)) micro_build(A, slo, shi, n, gbegin, parent, side, depth, epoch, ws);
+}
+
+// micro_sort_build of a node whose records sit in global buffer `parity`.
+__device__ void micro_task(const BuildArgs& A, int begin, int n, int parity, int parent, int side, int depth,
+                           int epoch, WarpStats& ws) {
+  const int lane = threadIdx.x & 31;
+  float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
+  if (lane < n) {
+    const float4* p = A.rec[parity] + 2 * ((size_t)begin + lane);
+    lo = __ldcg(p);
+    hi = __ldcg(p + 1);
+  }
+  micro_sort_build(A, lo, hi, begin, n, parent, side, depth, epoch, ws);
 }
 
 // ------------------------------------------------------------------ mid levels
@@ -1268,66 +1293,48 @@ struct MidWarp {
   unsigned bins[kBinWords];
   float4 stage[2 * kStageW];
 };
-struct MidSmem {
-  MidWarp w[kWarps];
-};
-
-// Lane 0 takes the next queue slot; the whole warp then waits for it to be
-// filled, every lane polling the same words (broadcast loads), so the warp
-// stays converged: no lane ever parks at a warp-synchronous instruction
-// while another spins, which would tie up the SM's shuffle path.  Returns
-// false when the queue is drained (no big node and no task pending) or the
-// build failed.  The wait is bounded: spin_limit polls without progress set
-// a timeout status.
+// One thread takes the next queue slot and waits for it to be filled (the
+// other threads of the CTA wait at a barrier; nothing warp-synchronous runs
+// in this loop).  Returns false when the queue is drained (no big node and
+// no task pending) or the build failed.  The wait is bounded: spin_limit
+// polls without progress set a timeout status.
 __device__ bool claim_task(const BuildArgs& A, int epoch, Task& t) {
-  const int lane = threadIdx.x & 31;
-  int s = 0;
-  if (lane == 0) s = atomicAdd(&A.ctl->qa_head, 1);
-  s = __shfl_sync(kFull, s, 0);
-  int seen = -1, it = 0;
-  bool got = false;
-  // every exit is a warp vote, so the warp leaves the loop converged
-  for (;;) {
-    const bool rdy = s < A.qa_cap && ld_acquire(&A.qa_ready[s]) == epoch;
-    if (__any_sync(kFull, rdy)) {
-      got = true;
-      break;
+  const int s = atomicAdd(&A.ctl->qa_head, 1);
+  int seen = -1;
+  for (int it = 0;; ++it) {
+    if (s < A.qa_cap && ld_acquire(&A.qa_ready[s]) == epoch) {
+      const int4* q = reinterpret_cast<const int4*>(A.qa + s);
+      const int4 a = __ldcg(q), b = __ldcg(q + 1), c = __ldcg(q + 2);
+      t.begin = a.x;
+      t.count = a.y;
+      t.parent = a.z;
+      t.side = a.w;
+      t.clo[0] = __int_as_float(b.x);
+      t.clo[1] = __int_as_float(b.y);
+      t.clo[2] = __int_as_float(b.z);
+      t.depth = b.w;
+      t.chi[0] = __int_as_float(c.x);
+      t.chi[1] = __int_as_float(c.y);
+      t.chi[2] = __int_as_float(c.z);
+      t.pad = c.w;
+      return true;
     }
-    bool stop = false;
     if ((it & 3) == 0) {
       // done when no big node is left and then no mid-level task either
-      if (ld_acquire(&A.ctl->ti_pending) == 0) stop = ld_volatile(&A.ctl->qa_pending) == 0;
-      stop = stop || ld_volatile(&A.ctl->status) != 0;
-      const int prog = __shfl_sync(kFull, ld_volatile(&A.ctl->qa_tail) + ld_volatile(&A.ctl->ti_head), 0);
+      if (ld_acquire(&A.ctl->ti_pending) == 0 && ld_volatile(&A.ctl->qa_pending) == 0) return false;
+      if (ld_volatile(&A.ctl->status) != 0) return false;
+      const int prog = ld_volatile(&A.ctl->qa_tail) + ld_volatile(&A.ctl->ti_head);
       if (prog != seen) {  // work moved: restart the no-progress budget
         seen = prog;
         it = 0;
       }
     }
-    if (__any_sync(kFull, stop)) break;
-    if (++it > A.spin_limit) {
-      if (lane == 0) set_status(A.ctl, kStQueueTimeout, 1);
-      break;
+    if (it > A.spin_limit) {
+      set_status(A.ctl, kStQueueTimeout, 1);
+      return false;
     }
     __nanosleep(200);
   }
-  if (got) {
-    const int4* q = reinterpret_cast<const int4*>(A.qa + s);
-    const int4 a = __ldcg(q), b = __ldcg(q + 1), c = __ldcg(q + 2);
-    t.begin = a.x;
-    t.count = a.y;
-    t.parent = a.z;
-    t.side = a.w;
-    t.clo[0] = __int_as_float(b.x);
-    t.clo[1] = __int_as_float(b.y);
-    t.clo[2] = __int_as_float(b.z);
-    t.depth = b.w;
-    t.chi[0] = __int_as_float(c.x);
-    t.chi[1] = __int_as_float(c.y);
-    t.chi[2] = __int_as_float(c.z);
-    t.pad = c.w;
-  }
-  return got;
 }
 
 // Split one node of more than 32 triangles with one warp (bin, Eq. 2, stable
@@ -1389,11 +1396,11 @@ __device__ void mid_split(const BuildArgs& A, MidWarp& W, const Task& t, int epo
     eval_axes(W.bins, K, n, 0, 3, A.cp, best);
   } else if (2 * K <= 32) {  // x and y in one pass, then z
     eval_axes(W.bins, K, n, 0, 2, A.cp, best);
-    if (scl[2] > 0.f) eval_axis(W.bins, K, n, 2, A.cp, best);
+    if (__any_sync(kFull, scl[2] > 0.f)) eval_axis(W.bins, K, n, 2, A.cp, best);
   } else {
 #pragma unroll
     for (int a = 0; a < 3; ++a)
-      if (scl[a] > 0.f) eval_axis(W.bins, K, n, a, A.cp, best);
+      if (__any_sync(kFull, scl[a] > 0.f)) eval_axis(W.bins, K, n, a, A.cp, best);
   }
   int axis, plane, nl;
   if (best.cand != INT_MAX) {
@@ -1411,7 +1418,7 @@ __device__ void mid_split(const BuildArgs& A, MidWarp& W, const Task& t, int epo
   // no plane was usable)
   int lrun = 0, rrun = 0;
   BinU accL = binu_empty(), accR = binu_empty();
-  for (int g = 0; g < n; g += 32) {
+  for (int g = 0; __any_sync(kFull, g < n); g += 32) {
     const int k = g + lane;
     const bool valid = k < n;
     float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
@@ -1452,7 +1459,7 @@ __device__ void mid_split(const BuildArgs& A, MidWarp& W, const Task& t, int epo
     rrun += min(32, n - g) - tot;
   }
   BinU L = best.L, R = best.R;
-  if (axis < 0) {
+  if (__any_sync(kFull, axis < 0)) {
     __syncwarp();
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -1512,36 +1519,654 @@ __device__ void mid_split(const BuildArgs& A, MidWarp& W, const Task& t, int epo
   }
 }
 
-__device__ void mid_loop(const BuildArgs& A, MidWarp& W, int epoch) {
+// ------------------------------------------------------------------ subtrees in shared memory
+// A CTA takes a task of at most kSubMax records, loads its records into
+// shared memory once and builds the whole subtree there: nodes of more than
+// kWarpMax records are split by the whole CTA, one after the other; then the
+// warps split the remaining nodes in parallel (warp per node, larger child
+// kept) and finish nodes of at most 32 records in registers.  Records leave
+// shared memory only as leaves, in their final order, into buffer 0.
+constexpr int kSubMax = 1024;   // records of a subtree built in shared memory
+constexpr int kWarpMax = 256;   // nodes up to this size are split by one warp
+constexpr int kSubList = 32;    // pending warp nodes (> 32 records, disjoint: at most kSubMax / 33)
+constexpr int kSubStack = 4;    // pending CTA nodes (> kWarpMax records, disjoint: at most 3)
+constexpr int kMicroList = kSubMax / 2;  // pending nodes of at most 32 (>= 2 records each, disjoint)
+constexpr int kBoxVals = 7;  // a subtree bin: count, box lo (complemented codes), box hi
+constexpr int kWBinWords = 3 * kMaxBins * kBoxVals;  // a warp's bins, three axes
+static_assert(kWBinWords + 2 * kBinVals <= kWarps * kWBinWords, "CTA bins and child unions fit in the warps' bins");
+static_assert(kSubMax <= kBlock * 4, "a CTA partition keeps at most 4 records per thread");
+static_assert(kSubMax <= 1024 && kMicro < 64, "packed small-node fields");
+
+// A node of the subtree: local range [b, b + n) of shared buffer `par`,
+// parent id, side, depth, centroid bounds.
+struct SubNode {
+  int b, n, parent, side, depth, par;
+  float clo[3], chi[3];
+};
+
+struct SubSmem {
+  float4 rec[2][2 * kSubMax];
+  unsigned wbins[kWarps][kWBinWords];
+  SubNode wl[kSubList];    // warp nodes
+  SubNode cs[kSubStack];   // CTA nodes
+  int2 ml[kMicroList];     // nodes of at most 32: (parent, b | n << 10 | side << 16 | par << 17 | depth << 18)
+  SubNode cur;
+  Task task;
+  int red[kWarps];
+  int lock, nw, nm, ncs, active, got;
+};
+static_assert(sizeof(MidWarp) <= sizeof(float4) * 2 * 2 * kSubMax, "a warp's global-memory split state fits");
+
+__device__ __forceinline__ SubNode sub_node(int b, int n, int parent, int side, int depth, int par, const BinU& u) {
+  SubNode x;
+  x.b = b;
+  x.n = n;
+  x.parent = parent;
+  x.side = side;
+  x.depth = depth;
+  x.par = par;
+  x.clo[0] = u.a0;
+  x.clo[1] = u.a1;
+  x.clo[2] = u.a2;
+  x.chi[0] = u.b0;
+  x.chi[1] = u.b1;
+  x.chi[2] = u.b2;
+  return x;
+}
+
+// Packed node of at most 32 records; depth is relative to the task (a
+// subtree of kSubMax records is less than kSubMax deep).
+__device__ __forceinline__ int2 micro_pack(int b, int n, int parent, int side, int depth, int par) {
+  return make_int2(parent, b | (n << 10) | (side << 16) | (par << 17) | (depth << 18));
+}
+
+// The shared lists' lock, taken by the whole warp together (lane 0 tries,
+// every lane learns the outcome), so no lane ever spins alone.  Bounded.
+__device__ __forceinline__ bool sub_lock(const BuildArgs& A, SubSmem& S) {
   const int lane = threadIdx.x & 31;
-  WarpStats ws{0, 0, 0, 0};
-  Task cont;
-  bool have_cont = false;
-  for (;;) {
-    Task t;
-    if (have_cont) {
-      t = cont;
-      have_cont = false;
-    } else if (!claim_task(A, epoch, t)) {
-      break;
+  for (int it = 0; it <= A.spin_limit; ++it) {
+    int got = 0;
+    if (lane == 0) got = atomicCAS(&S.lock, 0, 1) == 0;
+    if (__any_sync(kFull, got)) {
+      __threadfence_block();
+      return true;
     }
+  }
+  if (lane == 0) set_status(A.ctl, kStQueueTimeout, 7);
+  return false;
+}
+__device__ __forceinline__ void sub_unlock(SubSmem& S) {
+  __threadfence_block();
+  if ((threadIdx.x & 31) == 0) atomicExch(&S.lock, 0);
+  __syncwarp();
+}
+
+// Bin the run of records [k0, k1) of src on all three axes (count and box
+// per bin).  Consecutive records of the Morton order mostly share a bin, so
+// the run is accumulated in registers and each stretch of equal bins costs
+// one flush of shared-memory atomics.
+__device__ __forceinline__ void flush_box(unsigned* e, const unsigned* acc) {
+  atomicAdd(e, acc[0]);
+#pragma unroll
+  for (int q = 1; q < kBoxVals; ++q) atomicMax(e + q, acc[q]);
+}
+__device__ __forceinline__ void bin_run(unsigned* bins, const float4* src, int k0, int k1, int K, const float* cmin,
+                                        const float* scl) {
+  int key[3] = {-1, -1, -1};
+  unsigned acc[3][kBoxVals];
+  for (int k = k0; k < k1; ++k) {
+    const float4 lo = src[2 * k], hi = src[2 * k + 1];
+    const unsigned c6[6] = {~ucode(lo.x), ~ucode(lo.y), ~ucode(lo.z), ucode(hi.x), ucode(hi.y), ucode(hi.z)};
+    const float cc[3] = {centre(lo.x, hi.x), centre(lo.y, hi.y), centre(lo.z, hi.z)};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int kk = bin_of(cc[a], cmin[a], scl[a], K);
+      if (kk != key[a]) {
+        if (key[a] >= 0) flush_box(bins + (a * K + key[a]) * kBoxVals, acc[a]);
+        key[a] = kk;
+        acc[a][0] = 1u;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) acc[a][1 + q] = c6[q];
+      } else {
+        acc[a][0] += 1u;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) acc[a][1 + q] = max(acc[a][1 + q], c6[q]);
+      }
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    if (key[a] >= 0) flush_box(bins + (a * K + key[a]) * kBoxVals, acc[a]);
+}
+
+// Eq. 2 over the 7-word bins of all three axes (as many axes per warp pass
+// as 32 lanes hold).  Only best.cand and best.L.n are used afterwards.
+__device__ __forceinline__ void eval_box(const unsigned* bins, int K, int n, const float* scl, const CostP& cp,
+                                         Split& best) {
+  for (int g = 0; g < 3;) {
+    const int m = min(3 - g, 32 / K);
+    if (m >= 2 || __any_sync(kFull, scl[g] > 0.f))
+      eval_seg<kBoxVals, false>(bins + g * K * kBoxVals, K, n, g, m, cp, best);
+    g += m;
+  }
+}
+
+// A child's union (count, box, centre bounds) accumulated over records: 13
+// words in bin order (count, then the codes of a record).
+__device__ __forceinline__ void acc13_add(unsigned* v, const RecCodes& c) {
+  v[0] += 1u;
+#pragma unroll
+  for (int q = 0; q < 12; ++q) v[1 + q] = max(v[1 + q], c.v[q]);
+}
+__device__ __forceinline__ void acc13_warp(unsigned* v) {
+  v[0] = __reduce_add_sync(kFull, v[0]);
+#pragma unroll
+  for (int q = 1; q < kBinVals; ++q) v[q] = __reduce_max_sync(kFull, v[q]);
+}
+
+// Copy a leaf's records from shared memory to buffer 0 (its final place).
+__device__ __forceinline__ void leaf_out(const BuildArgs& A, const float4* src, int gpos, int n, int t0, int nt) {
+  for (int k = t0; k < 2 * n; k += nt) A.rec[0][2 * (size_t)gpos + k] = src[k];
+}
+
+// Account a written binary node (one thread per node).
+__device__ __forceinline__ void note_node(WarpStats& ws, int nl, int nr, bool leafl, bool leafr, int depth) {
+  ++ws.n_int;
+  ws.n_leaf += (int)leafl + (int)leafr;
+  if (leafl) ws.big = max(ws.big, nl);
+  if (leafr) ws.big = max(ws.big, nr);
+  ws.deep = max(ws.deep, (leafl || leafr) ? depth + 1 : depth);
+}
+
+// Split node X of the subtree with the whole CTA: bins (count and box) in
+// one shared array, each thread binning a run of records (thread (w, l)
+// takes run l * 8 + w, so the lanes of a warp work far apart); Eq. 2
+// evaluated by every warp (all reach the same split); stable partition by a
+// block scan, which also gathers both children's unions.  Thread 0 writes
+// the node and files the children; the others wait at the next barrier.
+__device__ void cta_split(const BuildArgs& A, SubSmem& S, const SubNode& X, int gbegin, int tdepth, int epoch,
+                          WarpStats& ws) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int K = A.K, n = X.n, p = X.par;
+  const int nbw = 3 * K * kBoxVals;
+  unsigned* cb = &S.wbins[0][0];
+  unsigned* cu = cb + nbw;  // the children's unions, 2 x 13 words
+  const float4* src = S.rec[p] + 2 * X.b;
+  float4* dst = S.rec[p ^ 1] + 2 * X.b;
+  float cmin[3], scl[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    cmin[a] = X.clo[a];
+    scl[a] = bin_scale(X.clo[a], X.chi[a], K);
+  }
+  for (int w = tid; w < nbw + 2 * kBinVals; w += kBlock) cb[w] = 0u;
+  // thread t owns records [t c, t c + c), c <= 4, for the partition; runs
+  // for the bins use the spread order
+  const int c = (n + kBlock - 1) / kBlock;
+  __syncthreads();
+  {
+    const int r = lane * kWarps + warp, k0 = min(r * c, n), k1 = min(k0 + c, n);
+    bin_run(cb, src, k0, k1, K, cmin, scl);
+  }
+  __syncthreads();
+  Split best;
+  split_none(best);
+  eval_box(cb, K, n, scl, A.cp, best);
+  int axis, plane, nl;
+  if (best.cand != INT_MAX) {
+    axis = best.cand / (K - 1);
+    plane = 1 + best.cand % (K - 1);
+    nl = best.L.n;
+  } else {
+    axis = -1;
+    plane = 0;
+    nl = n / 2;
+  }
+  const float acmin = sel3(cmin[0], cmin[1], cmin[2], axis < 0 ? 0 : axis);
+  const float ascl = sel3(scl[0], scl[1], scl[2], axis < 0 ? 0 : axis);
+  const int k0 = min(tid * c, n);
+  float4 rl[4], rh[4];
+  unsigned fl = 0;
+  int cnt = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int k = k0 + i;
+    if (i < c && k < n) {
+      rl[i] = src[2 * k];
+      rh[i] = src[2 * k + 1];
+      bool left;
+      if (axis >= 0) {
+        const float cc = axis == 0 ? centre(rl[i].x, rh[i].x)
+                                   : (axis == 1 ? centre(rl[i].y, rh[i].y) : centre(rl[i].z, rh[i].z));
+        left = bin_of(cc, acmin, ascl, K) < plane;
+      } else {
+        left = k < nl;
+      }
+      fl |= (unsigned)left << i;
+      cnt += left;
+    }
+  }
+  int inc = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int u = __shfl_up_sync(kFull, inc, o);
+    if (lane >= o) inc += u;
+  }
+  if (lane == 31) S.red[warp] = inc;
+  __syncthreads();
+  int before = 0, total = 0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) {
+    const int v = S.red[w];
+    before += w < warp ? v : 0;
+    total += v;
+  }
+  int lb = before + inc - cnt, rb = k0 - lb;
+  unsigned ua[kBinVals], ub[kBinVals];
+#pragma unroll
+  for (int q = 0; q < kBinVals; ++q) ua[q] = ub[q] = 0u;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int k = k0 + i;
+    if (i < c && k < n) {
+      const bool left = (fl >> i) & 1u;
+      const int d = left ? lb++ : nl + rb++;
+      if (d < n) {
+        dst[2 * d] = rl[i];
+        dst[2 * d + 1] = rh[i];
+      }
+      const RecCodes rc =
+          rec_codes(rl[i], rh[i], centre(rl[i].x, rh[i].x), centre(rl[i].y, rh[i].y), centre(rl[i].z, rh[i].z));
+      if (left)
+        acc13_add(ua, rc);
+      else
+        acc13_add(ub, rc);
+    }
+  }
+  acc13_warp(ua);
+  acc13_warp(ub);
+  if (lane == 0) {
+    atomicAdd(cu, ua[0]);
+    atomicAdd(cu + kBinVals, ub[0]);
+#pragma unroll
+    for (int q = 1; q < kBinVals; ++q) {
+      atomicMax(cu + q, ua[q]);
+      atomicMax(cu + kBinVals + q, ub[q]);
+    }
+  }
+  __syncthreads();
+  const BinU L = binu_load(cu), R = binu_load(cu + kBinVals);
+  const int nr = n - nl;
+  const bool leafl = nl <= A.max_leaf, leafr = nr <= A.max_leaf;
+  if (leafl) leaf_out(A, dst, gbegin + X.b, nl, tid, kBlock);
+  if (leafr) leaf_out(A, dst + 2 * nl, gbegin + X.b + nl, nr, tid, kBlock);
+  // the larger child of more than 32 records stays; the other one of more
+  // than 32 goes to the device queue (records to buffer 1), where an idle
+  // CTA takes it, so the subtree spreads over the SMs as it branches
+  const int keep = nl >= nr ? 0 : 1;
+  const int ex = (keep == 0 ? nr : nl) > kMicro ? 1 - keep : -1;
+  if (ex >= 0) {
+    const int eb = ex ? nl : 0, en = ex ? nr : nl;
+    for (int k = tid; k < 2 * en; k += kBlock) __stcg(A.rec[1] + 2 * ((size_t)gbegin + X.b + eb) + k, dst[2 * eb + k]);
+    __threadfence();
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (total != nl) set_status(A.ctl, kStBadSplit, 6);
+    const int id = gbegin + X.b + nl - 1;
+    write_node(A, id, X.parent, X.side, L, leafl ? leaf_ref(gbegin + X.b, nl) : INT_MAX, nl, R,
+               leafr ? leaf_ref(gbegin + X.b + nl, nr) : INT_MAX, nr, epoch);
+    note_node(ws, nl, nr, leafl, leafr, X.depth);
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const int cn = s ? nr : nl, b = X.b + (s ? nl : 0);
+      if (cn <= A.max_leaf) continue;
+      const SubNode ch = sub_node(b, cn, id, s, X.depth + 1, p ^ 1, s ? R : L);
+      if (s == ex) {
+        push_task(A, make_task(gbegin + b, cn, id, s, X.depth + 1, s ? R : L, 1), epoch);
+      } else if (cn <= kMicro) {
+        if (S.nm < kMicroList)
+          S.ml[S.nm++] = micro_pack(b, cn, id, s, X.depth + 1 - tdepth, p ^ 1);
+        else
+          set_status(A.ctl, kStQueueOverflow, 4);
+      } else if (cn <= kWarpMax) {
+        if (S.nw < kSubList)
+          S.wl[S.nw++] = ch;
+        else
+          set_status(A.ctl, kStQueueOverflow, 5);
+      } else {
+        if (S.ncs < kSubStack)
+          S.cs[S.ncs++] = ch;
+        else
+          set_status(A.ctl, kStQueueOverflow, 6);
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Split node X (kMicro < n <= kWarpMax) of the subtree with one warp: the
+// warp's own bins (count and box; lane l bins the run of records l c .. l c
+// + c - 1), Eq. 2, stable ballot partition into the other shared buffer,
+// which also gathers both children's unions.  The larger child of more than
+// 32 records is returned in *cont; the other one, and the small children
+// when there is a continuation, go to the shared lists (under the lock);
+// without a continuation the small children are finished here.
+__device__ bool warp_split(const BuildArgs& A, SubSmem& S, const SubNode& X, int gbegin, int tdepth, int epoch,
+                           WarpStats& ws, SubNode& cont) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int K = A.K, n = X.n, p = X.par;
+  unsigned* wb = S.wbins[warp];
+  const float4* src = S.rec[p] + 2 * X.b;
+  float4* dst = S.rec[p ^ 1] + 2 * X.b;
+  float cmin[3], scl[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    cmin[a] = X.clo[a];
+    scl[a] = bin_scale(X.clo[a], X.chi[a], K);
+  }
+  __syncwarp();
+  for (int w = lane; w < 3 * K * kBoxVals; w += 32) wb[w] = 0u;
+  __syncwarp();
+  {
+    const int c = (n + 31) / 32, k0 = min(lane * c, n), k1 = min(k0 + c, n);
+    bin_run(wb, src, k0, k1, K, cmin, scl);
+  }
+  __syncwarp();
+  Split best;
+  split_none(best);
+  eval_box(wb, K, n, scl, A.cp, best);
+  int axis, plane, nl;
+  if (best.cand != INT_MAX) {
+    axis = best.cand / (K - 1);
+    plane = 1 + best.cand % (K - 1);
+    nl = best.L.n;
+  } else {
+    axis = -1;
+    plane = 0;
+    nl = n / 2;
+  }
+  const float acmin = sel3(cmin[0], cmin[1], cmin[2], axis < 0 ? 0 : axis);
+  const float ascl = sel3(scl[0], scl[1], scl[2], axis < 0 ? 0 : axis);
+  int lrun = 0, rrun = 0;
+  unsigned ua[kBinVals], ub[kBinVals];
+#pragma unroll
+  for (int q = 0; q < kBinVals; ++q) ua[q] = ub[q] = 0u;
+  for (int g = 0; __any_sync(kFull, g < n); g += 32) {
+    const int k = g + lane;
+    const bool valid = k < n;
+    float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
+    bool left = false;
+    float cx = 0.f, cy = 0.f, cz = 0.f;
+    if (valid) {
+      lo = src[2 * k];
+      hi = src[2 * k + 1];
+      cx = centre(lo.x, hi.x);
+      cy = centre(lo.y, hi.y);
+      cz = centre(lo.z, hi.z);
+      left = axis >= 0 ? bin_of(axis == 0 ? cx : (axis == 1 ? cy : cz), acmin, ascl, K) < plane : k < nl;
+    }
+    __syncwarp();
+    const unsigned bal = __ballot_sync(kFull, left);
+    const int rank = __popc(bal & ((1u << lane) - 1u));
+    const int d = left ? lrun + rank : nl + rrun + (lane - rank);
+    if (valid && d < n) {
+      dst[2 * d] = lo;
+      dst[2 * d + 1] = hi;
+      if (left)
+        acc13_add(ua, rec_codes(lo, hi, cx, cy, cz));
+      else
+        acc13_add(ub, rec_codes(lo, hi, cx, cy, cz));
+    }
+    const int tot = __popc(bal);
+    lrun += tot;
+    rrun += min(32, n - g) - tot;
+  }
+  acc13_warp(ua);
+  acc13_warp(ub);
+  const BinU L = binu_load(ua), R = binu_load(ub);
+  __syncwarp();
+  const int nr = n - nl;
+  const bool leafl = nl <= A.max_leaf, leafr = nr <= A.max_leaf;
+  if (leafl) leaf_out(A, dst, gbegin + X.b, nl, lane, 32);
+  if (leafr) leaf_out(A, dst + 2 * nl, gbegin + X.b + nl, nr, lane, 32);
+  const int id = gbegin + X.b + nl - 1;
+  if (lane == 0) {
+    if (lrun != nl) set_status(A.ctl, kStBadSplit, 7);
+    write_node(A, id, X.parent, X.side, L, leafl ? leaf_ref(gbegin + X.b, nl) : INT_MAX, nl, R,
+               leafr ? leaf_ref(gbegin + X.b + nl, nr) : INT_MAX, nr, epoch);
+  }
+  note_node(ws, nl, nr, leafl, leafr, X.depth);
+  const bool bigl = nl > kMicro, bigr = nr > kMicro;
+  const int keep = (bigl && bigr) ? (nl >= nr ? 0 : 1) : (bigl ? 0 : (bigr ? 1 : -1));
+  const SubNode cl = sub_node(X.b, nl, id, 0, X.depth + 1, p ^ 1, L);
+  const SubNode cr = sub_node(X.b + nl, nr, id, 1, X.depth + 1, p ^ 1, R);
+  if (__any_sync(kFull, keep >= 0)) {
+    cont = keep == 0 ? cl : cr;
+    // hand the rest to the shared lists: records and node first, then the lock
+    const bool pw = bigl && bigr;
+    const bool ml = nl > A.max_leaf && !bigl, mr = nr > A.max_leaf && !bigr;
+    if (__any_sync(kFull, pw || ml || mr)) {
+      __threadfence_block();
+      __syncwarp();
+      if (sub_lock(A, S)) {
+        if (lane == 0) {
+          if (pw) {
+            if (S.nw < kSubList)
+              S.wl[S.nw++] = keep == 0 ? cr : cl;
+            else
+              set_status(A.ctl, kStQueueOverflow, 7);
+          }
+          for (int s = 0; s < 2; ++s) {
+            if (!(s ? mr : ml)) continue;
+            const SubNode& ch = s ? cr : cl;
+            if (S.nm < kMicroList)
+              S.ml[S.nm++] = micro_pack(ch.b, ch.n, id, s, ch.depth - tdepth, p ^ 1);
+            else
+              set_status(A.ctl, kStQueueOverflow, 8);
+          }
+        }
+        sub_unlock(S);
+      }
+    }
+    return true;
+  }
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const SubNode& ch = s ? cr : cl;
+    if (!__any_sync(kFull, ch.n > A.max_leaf)) continue;
+    float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
+    if (lane < ch.n) {
+      lo = S.rec[p ^ 1][2 * (ch.b + lane)];
+      hi = S.rec[p ^ 1][2 * (ch.b + lane) + 1];
+    }
+    micro_sort_build(A, lo, hi, gbegin + ch.b, ch.n, id, s, ch.depth, epoch, ws);
+  }
+  return false;
+}
+
+// The warps' part of a subtree: take nodes from the shared lists (warp
+// nodes first) until the lists are empty and no warp is working.  Waits
+// are bounded.
+__device__ void warp_phase(const BuildArgs& A, SubSmem& S, int gbegin, int tdepth, int epoch, WarpStats& ws) {
+  const int lane = threadIdx.x & 31;
+  int idle = 0, nap = 32;
+  for (;;) {
+    // look before taking the lock: an idle warp only reads and sleeps
+    // (backing off), so it leaves the shared-memory pipe to working warps
+    const bool look = ld_volatile(&S.nw) + ld_volatile(&S.nm) > 0 || ld_volatile(&S.active) == 0;
+    if (!__any_sync(kFull, look)) {
+      if (++idle > A.spin_limit) {
+        if (lane == 0) set_status(A.ctl, kStQueueTimeout, 8);
+        break;
+      }
+      __nanosleep(nap);
+      nap = min(2 * nap, 1024);
+      continue;
+    }
+    int kind = -1;  // -1 stop, 0 nothing yet, 1 warp node, 2 small node
+    SubNode X;
+    int2 m = make_int2(0, 0);
+    if (sub_lock(A, S)) {
+      if (lane == 0) {
+        // `active` also drops outside the lock (a warp finishing a node), so
+        // every change to it is atomic
+        if (S.nw > 0) {
+          X = S.wl[--S.nw];
+          kind = 1;
+          atomicAdd(&S.active, 1);
+        } else if (S.nm > 0) {
+          m = S.ml[--S.nm];
+          kind = 2;
+          atomicAdd(&S.active, 1);
+        } else {
+          kind = (ld_volatile(&S.active) == 0 || ld_volatile(&A.ctl->status) != 0) ? -1 : 0;
+        }
+      }
+      sub_unlock(S);
+    }
+    // branch only on warp votes: their results are uniform by construction,
+    // so the warp-synchronous code below runs in a provably converged warp
+    if (__any_sync(kFull, lane == 0 && kind < 0)) break;
+    if (__any_sync(kFull, lane == 0 && kind == 0)) {
+      if (++idle > A.spin_limit) {
+        if (lane == 0) set_status(A.ctl, kStQueueTimeout, 8);
+        break;
+      }
+      __nanosleep(nap);
+      nap = min(2 * nap, 1024);
+      continue;
+    }
+    idle = 0;
+    nap = 32;
+    if (__any_sync(kFull, lane == 0 && kind == 1)) {
+      X.b = __shfl_sync(kFull, X.b, 0);
+      X.n = __shfl_sync(kFull, X.n, 0);
+      X.parent = __shfl_sync(kFull, X.parent, 0);
+      X.side = __shfl_sync(kFull, X.side, 0);
+      X.depth = __shfl_sync(kFull, X.depth, 0);
+      X.par = __shfl_sync(kFull, X.par, 0);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        X.clo[a] = __shfl_sync(kFull, X.clo[a], 0);
+        X.chi[a] = __shfl_sync(kFull, X.chi[a], 0);
+      }
+      SubNode cur = X;
+      for (int guard = 0; guard < kSubMax; ++guard) {
+        SubNode nx;
+        if (!__any_sync(kFull, warp_split(A, S, cur, gbegin, tdepth, epoch, ws, nx))) break;
+        cur = nx;
+      }
+    } else {
+      const int parent = __shfl_sync(kFull, m.x, 0), f = __shfl_sync(kFull, m.y, 0);
+      const int b = f & 1023, n = (f >> 10) & 63, side = (f >> 16) & 1, par = (f >> 17) & 1, dep = f >> 18;
+      float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
+      if (lane < n) {
+        lo = S.rec[par][2 * (b + lane)];
+        hi = S.rec[par][2 * (b + lane) + 1];
+      }
+      micro_sort_build(A, lo, hi, gbegin + b, n, parent, side, tdepth + dep, epoch, ws);
+    }
+    __threadfence_block();
+    __syncwarp();
+    if (lane == 0) atomicSub(&S.active, 1);
+  }
+}
+
+// Build the subtree of task t (max_leaf < t.count <= kSubMax) in shared
+// memory with the whole CTA.
+__device__ void sub_tree(const BuildArgs& A, SubSmem& S, const Task& t, int epoch, WarpStats& ws) {
+  const int tid = threadIdx.x;
+  const int n = t.count;
+  const float4* g = A.rec[t.pad & 1] + 2 * (size_t)t.begin;
+  for (int k = tid; k < 2 * n; k += kBlock) S.rec[0][k] = __ldcg(g + k);
+  if (tid == 0) {
+    S.lock = 0;
+    S.nw = S.nm = S.ncs = S.active = 0;
+    SubNode r;
+    r.b = 0;
+    r.n = n;
+    r.parent = t.parent;
+    r.side = t.side;
+    r.depth = t.depth;
+    r.par = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      r.clo[a] = t.clo[a];
+      r.chi[a] = t.chi[a];
+    }
+    if (n <= kMicro)
+      S.ml[S.nm++] = micro_pack(0, n, t.parent, t.side, 0, 0);
+    else if (n <= kWarpMax)
+      S.wl[S.nw++] = r;
+    else
+      S.cs[S.ncs++] = r;
+  }
+  __syncthreads();
+  for (;;) {  // nodes of more than kWarpMax records: the whole CTA, one at a time
+    if (tid == 0) {
+      S.got = S.ncs > 0;
+      if (S.got) S.cur = S.cs[--S.ncs];
+    }
+    __syncthreads();
+    if (!S.got) break;
+    const SubNode X = S.cur;
+    cta_split(A, S, X, t.begin, t.depth, epoch, ws);
+  }
+  warp_phase(A, S, t.begin, t.depth, epoch, ws);
+  __syncthreads();
+}
+
+// The mid-level role of every CTA: take a task from the queue, build its
+// subtree (tasks of more than kSubMax records are first split in global
+// memory by one warp, down to a part that fits), repeat until the queue is
+// drained.
+__device__ void sub_loop(const BuildArgs& A, SubSmem& S, int epoch) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  WarpStats ws{0, 0, 0, 0};
+  for (;;) {
+    if (tid == 0) S.got = claim_task(A, epoch, S.task);
+    __syncthreads();
+    const bool got = S.got;
+    Task t = S.task;
+    __syncthreads();
+    if (!got) break;
     const int par = t.pad & 1;
     if (t.begin < 0 || t.count < 1 || t.begin > A.n - t.count) {
-      if (lane == 0) set_status(A.ctl, kStBadSplit, 5);
+      if (tid == 0) set_status(A.ctl, kStBadSplit, 5);
     } else if (t.count <= A.max_leaf) {
       // a leaf made by a top level whose records sit in buffer 1
       if (par)
-        for (int k = lane; k < 2 * t.count; k += 32)
+        for (int k = tid; k < 2 * t.count; k += kBlock)
           A.rec[0][2 * (size_t)t.begin + k] = __ldcg(A.rec[1] + 2 * (size_t)t.begin + k);
-    } else if (t.count <= kMicro) {
-      micro_task(A, t.begin, t.count, par, t.parent, t.side, t.depth, epoch, ws);
     } else {
-      mid_split(A, W, t, epoch, ws, cont, have_cont);
+      if (t.count > kSubMax) {
+        if (warp == 0) {
+          MidWarp& W = *reinterpret_cast<MidWarp*>(&S.rec[0][0]);
+          Task cur = t;
+          bool more = true;
+          while (more && cur.count > kSubMax) {
+            Task nx;
+            more = false;
+            mid_split(A, W, cur, epoch, ws, nx, more);
+            if (more) cur = nx;
+          }
+          if (lane == 0) {
+            S.got = more;
+            S.task = cur;
+          }
+        }
+        __syncthreads();
+        t = S.task;
+        const bool more = S.got;
+        __syncthreads();
+        if (!more) t.count = 0;
+      }
+      if (t.count > 0) sub_tree(A, S, t, epoch, ws);
     }
-    __syncwarp();
-    // a task's pushes incremented this same counter first, so the decrement
-    // can never make it read zero while they are pending
-    if (!have_cont && lane == 0) atomicSub(&A.ctl->qa_pending, 1);
+    __syncthreads();
+    // the pushes of this task counted first, so this never reads zero early
+    if (tid == 0) atomicSub(&A.ctl->qa_pending, 1);
   }
   if (lane == 0) {
     if (ws.n_int) atomicAdd(&A.ctl->n_internal, ws.n_int);
@@ -1552,12 +2177,12 @@ __device__ void mid_loop(const BuildArgs& A, MidWarp& W, int epoch) {
 }
 
 // The split phase: the first top_ctas CTAs work the chunk items of big nodes
-// (CTA per item) and then join the others, whose warps take the mid-level
-// queue (warp per node).  Both run at once, so small subtrees proceed while
-// the big nodes of other branches are still being split.
+// (CTA per item) and then join the others, which take the mid-level queue
+// (CTA per subtree).  Both run at once, so subtrees proceed while the big
+// nodes of other branches are still being split.
 union SplitSmem {
   TopSmem top;
-  MidSmem mid;
+  SubSmem sub;
 };
 
 __global__ void __launch_bounds__(kBlock, 2) k_split(BuildArgs A) {
@@ -1570,7 +2195,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_split(BuildArgs A) {
     top_loop(A, S.top, epoch);
     __syncthreads();
   }
-  mid_loop(A, S.mid.w[threadIdx.x >> 5], epoch);
+  sub_loop(A, S.sub, epoch);
 }
 
 // ------------------------------------------------------------------ traversal nodes + leaf order
