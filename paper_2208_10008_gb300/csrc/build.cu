@@ -106,13 +106,13 @@ struct CostP {
 };
 
 // Eq. 2 (Eq. 1 at alpha = 1): children L (nl triangles), R (nr) of node C.
-// The two divisions by the node's area and squared diagonal are reciprocals
-// times products (the build's cost needs no correctly rounded quotient, only
-// the same value for the same inputs).
+// The two divisions by the node's area and squared diagonal are fast
+// approximate reciprocals times products: the build's cost needs no correctly
+// rounded quotient, only the same value for the same inputs.
 __device__ __forceinline__ float eq2_cost(float3 llo, float3 lhi, int nl, float3 rlo, float3 rhi, int nr, float3 clo,
                                           float3 chi, const CostP& p) {
   const float sc = area(clo, chi);
-  const float sah = sc > 0.f ? (area(llo, lhi) * (float)nl + area(rlo, rhi) * (float)nr) * __frcp_rn(sc) * p.t_i
+  const float sah = sc > 0.f ? (area(llo, lhi) * (float)nl + area(rlo, rhi) * (float)nr) * __fdividef(1.f, sc) * p.t_i
                              : (float)(nl + nr) * p.t_i;
   const float ax = 0.5f * (llo.x + lhi.x) - p.sx, ay = 0.5f * (llo.y + lhi.y) - p.sy, az = 0.5f * (llo.z + lhi.z) - p.sz;
   const float bx = 0.5f * (rlo.x + rhi.x) - p.sx, by = 0.5f * (rlo.y + rhi.y) - p.sy, bz = 0.5f * (rlo.z + rhi.z) - p.sz;
@@ -120,7 +120,7 @@ __device__ __forceinline__ float eq2_cost(float3 llo, float3 lhi, int nl, float3
   if (p.dist_norm) {
     const float dx = chi.x - clo.x, dy = chi.y - clo.y, dz = chi.z - clo.z;
     const float diag2 = dx * dx + dy * dy + dz * dz;
-    d2 = (diag2 > 0.f ? d2 * __frcp_rn(diag2) : 0.f) * (float)(nl + nr) * p.t_i;
+    d2 = (diag2 > 0.f ? d2 * __fdividef(1.f, diag2) : 0.f) * (float)(nl + nr) * p.t_i;
   }
   return p.alpha * sah + (1.f - p.alpha) * d2 + p.t_trav;
 }
@@ -1521,19 +1521,17 @@ __device__ void mid_split(const BuildArgs& A, MidWarp& W, const Task& t, int epo
 
 // ------------------------------------------------------------------ subtrees in shared memory
 // A CTA takes a task of at most kSubMax records, loads its records into
-// shared memory once and builds the whole subtree there: nodes of more than
-// kWarpMax records are split by the whole CTA, one after the other; then the
-// warps split the remaining nodes in parallel (warp per node, larger child
-// kept) and finish nodes of at most 32 records in registers.  Records leave
-// shared memory only as leaves, in their final order, into buffer 0.
-constexpr int kSubMax = 1024;   // records of a subtree built in shared memory
-constexpr int kWarpMax = 256;   // nodes up to this size are split by one warp
-constexpr int kSubList = 32;    // pending warp nodes (> 32 records, disjoint: at most kSubMax / 33)
-constexpr int kSubStack = 4;    // pending CTA nodes (> kWarpMax records, disjoint: at most 3)
-constexpr int kMicroList = kSubMax / 2;  // pending nodes of at most 32 (>= 2 records each, disjoint)
-constexpr int kBoxVals = 7;  // a subtree bin: count, box lo (complemented codes), box hi
-constexpr int kWBinWords = 3 * kMaxBins * kBoxVals;  // a warp's bins, three axes
-static_assert(kWBinWords + 2 * kBinVals <= kWarps * kWBinWords, "CTA bins and child unions fit in the warps' bins");
+// shared memory once and builds the subtree there.  Every node of more than
+// 32 records is split by the whole CTA; the larger child stays with the CTA
+// and the smaller one, if it has more than 32 records, goes back to the
+// device queue (records to buffer 1) for an idle CTA, so a subtree spreads
+// over the SMs as it branches.  Nodes of at most 32 records are collected
+// and finished at the end by the warps in parallel, in registers.  Records
+// leave shared memory only as leaves, in their final order, into buffer 0.
+constexpr int kSubMax = 1024;            // records of a subtree built in shared memory
+constexpr int kMicroList = kSubMax / 2;  // nodes of at most 32 records (>= 2 each, disjoint)
+constexpr int kBoxVals = 7;              // a subtree bin: count, box lo (complemented codes), box hi
+constexpr int kCtaBinWords = 3 * kMaxBins * kBoxVals + 2 * kBinVals;  // bins, then the children's unions
 static_assert(kSubMax <= kBlock * 4, "a CTA partition keeps at most 4 records per thread");
 static_assert(kSubMax <= 1024 && kMicro < 64, "packed small-node fields");
 
@@ -1546,14 +1544,12 @@ struct SubNode {
 
 struct SubSmem {
   float4 rec[2][2 * kSubMax];
-  unsigned wbins[kWarps][kWBinWords];
-  SubNode wl[kSubList];    // warp nodes
-  SubNode cs[kSubStack];   // CTA nodes
-  int2 ml[kMicroList];     // nodes of at most 32: (parent, b | n << 10 | side << 16 | par << 17 | depth << 18)
-  SubNode cur;
+  unsigned bins[kCtaBinWords];
+  int2 ml[kMicroList];  // nodes of at most 32: (parent, b | n << 10 | side << 16 | par << 17 | depth << 18)
+  SubNode cur;          // the next node the CTA splits
   Task task;
   int red[kWarps];
-  int lock, nw, nm, ncs, active, got;
+  int nm, mnext, got;
 };
 static_assert(sizeof(MidWarp) <= sizeof(float4) * 2 * 2 * kSubMax, "a warp's global-memory split state fits");
 
@@ -1578,27 +1574,6 @@ __device__ __forceinline__ SubNode sub_node(int b, int n, int parent, int side, 
 // subtree of kSubMax records is less than kSubMax deep).
 __device__ __forceinline__ int2 micro_pack(int b, int n, int parent, int side, int depth, int par) {
   return make_int2(parent, b | (n << 10) | (side << 16) | (par << 17) | (depth << 18));
-}
-
-// The shared lists' lock, taken by the whole warp together (lane 0 tries,
-// every lane learns the outcome), so no lane ever spins alone.  Bounded.
-__device__ __forceinline__ bool sub_lock(const BuildArgs& A, SubSmem& S) {
-  const int lane = threadIdx.x & 31;
-  for (int it = 0; it <= A.spin_limit; ++it) {
-    int got = 0;
-    if (lane == 0) got = atomicCAS(&S.lock, 0, 1) == 0;
-    if (__any_sync(kFull, got)) {
-      __threadfence_block();
-      return true;
-    }
-  }
-  if (lane == 0) set_status(A.ctl, kStQueueTimeout, 7);
-  return false;
-}
-__device__ __forceinline__ void sub_unlock(SubSmem& S) {
-  __threadfence_block();
-  if ((threadIdx.x & 31) == 0) atomicExch(&S.lock, 0);
-  __syncwarp();
 }
 
 // Bin the run of records [k0, k1) of src on all three axes (count and box
@@ -1683,13 +1658,15 @@ __device__ __forceinline__ void note_node(WarpStats& ws, int nl, int nr, bool le
 // takes run l * 8 + w, so the lanes of a warp work far apart); Eq. 2
 // evaluated by every warp (all reach the same split); stable partition by a
 // block scan, which also gathers both children's unions.  Thread 0 writes
-// the node and files the children; the others wait at the next barrier.
+// the node and routes the children: the larger one of more than 32 records
+// becomes S.cur (S.got), the smaller one of more than 32 goes to the device
+// queue, those of at most 32 to the small-node list.
 __device__ void cta_split(const BuildArgs& A, SubSmem& S, const SubNode& X, int gbegin, int tdepth, int epoch,
                           WarpStats& ws) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int K = A.K, n = X.n, p = X.par;
   const int nbw = 3 * K * kBoxVals;
-  unsigned* cb = &S.wbins[0][0];
+  unsigned* cb = S.bins;
   unsigned* cu = cb + nbw;  // the children's unions, 2 x 13 words
   const float4* src = S.rec[p] + 2 * X.b;
   float4* dst = S.rec[p ^ 1] + 2 * X.b;
@@ -1808,8 +1785,7 @@ __device__ void cta_split(const BuildArgs& A, SubSmem& S, const SubNode& X, int 
   if (ex >= 0) {
     const int eb = ex ? nl : 0, en = ex ? nr : nl;
     for (int k = tid; k < 2 * en; k += kBlock) __stcg(A.rec[1] + 2 * ((size_t)gbegin + X.b + eb) + k, dst[2 * eb + k]);
-    __threadfence();
-    __syncthreads();
+    __syncthreads();  // thread 0 publishes them below (fence, then a release store)
   }
   if (tid == 0) {
     if (total != nl) set_status(A.ctl, kStBadSplit, 6);
@@ -1817,259 +1793,47 @@ __device__ void cta_split(const BuildArgs& A, SubSmem& S, const SubNode& X, int 
     write_node(A, id, X.parent, X.side, L, leafl ? leaf_ref(gbegin + X.b, nl) : INT_MAX, nl, R,
                leafr ? leaf_ref(gbegin + X.b + nl, nr) : INT_MAX, nr, epoch);
     note_node(ws, nl, nr, leafl, leafr, X.depth);
+    S.got = 0;
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
       const int cn = s ? nr : nl, b = X.b + (s ? nl : 0);
       if (cn <= A.max_leaf) continue;
-      const SubNode ch = sub_node(b, cn, id, s, X.depth + 1, p ^ 1, s ? R : L);
       if (s == ex) {
+        __threadfence();
         push_task(A, make_task(gbegin + b, cn, id, s, X.depth + 1, s ? R : L, 1), epoch);
       } else if (cn <= kMicro) {
         if (S.nm < kMicroList)
           S.ml[S.nm++] = micro_pack(b, cn, id, s, X.depth + 1 - tdepth, p ^ 1);
         else
           set_status(A.ctl, kStQueueOverflow, 4);
-      } else if (cn <= kWarpMax) {
-        if (S.nw < kSubList)
-          S.wl[S.nw++] = ch;
-        else
-          set_status(A.ctl, kStQueueOverflow, 5);
       } else {
-        if (S.ncs < kSubStack)
-          S.cs[S.ncs++] = ch;
-        else
-          set_status(A.ctl, kStQueueOverflow, 6);
+        S.cur = sub_node(b, cn, id, s, X.depth + 1, p ^ 1, s ? R : L);
+        S.got = 1;
       }
     }
   }
   __syncthreads();
 }
 
-// Split node X (kMicro < n <= kWarpMax) of the subtree with one warp: the
-// warp's own bins (count and box; lane l bins the run of records l c .. l c
-// + c - 1), Eq. 2, stable ballot partition into the other shared buffer,
-// which also gathers both children's unions.  The larger child of more than
-// 32 records is returned in *cont; the other one, and the small children
-// when there is a continuation, go to the shared lists (under the lock);
-// without a continuation the small children are finished here.
-__device__ bool warp_split(const BuildArgs& A, SubSmem& S, const SubNode& X, int gbegin, int tdepth, int epoch,
-                           WarpStats& ws, SubNode& cont) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int K = A.K, n = X.n, p = X.par;
-  unsigned* wb = S.wbins[warp];
-  const float4* src = S.rec[p] + 2 * X.b;
-  float4* dst = S.rec[p ^ 1] + 2 * X.b;
-  float cmin[3], scl[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    cmin[a] = X.clo[a];
-    scl[a] = bin_scale(X.clo[a], X.chi[a], K);
-  }
-  __syncwarp();
-  for (int w = lane; w < 3 * K * kBoxVals; w += 32) wb[w] = 0u;
-  __syncwarp();
-  {
-    const int c = (n + 31) / 32, k0 = min(lane * c, n), k1 = min(k0 + c, n);
-    bin_run(wb, src, k0, k1, K, cmin, scl);
-  }
-  __syncwarp();
-  Split best;
-  split_none(best);
-  eval_box(wb, K, n, scl, A.cp, best);
-  int axis, plane, nl;
-  if (best.cand != INT_MAX) {
-    axis = best.cand / (K - 1);
-    plane = 1 + best.cand % (K - 1);
-    nl = best.L.n;
-  } else {
-    axis = -1;
-    plane = 0;
-    nl = n / 2;
-  }
-  const float acmin = sel3(cmin[0], cmin[1], cmin[2], axis < 0 ? 0 : axis);
-  const float ascl = sel3(scl[0], scl[1], scl[2], axis < 0 ? 0 : axis);
-  int lrun = 0, rrun = 0;
-  unsigned ua[kBinVals], ub[kBinVals];
-#pragma unroll
-  for (int q = 0; q < kBinVals; ++q) ua[q] = ub[q] = 0u;
-  for (int g = 0; __any_sync(kFull, g < n); g += 32) {
-    const int k = g + lane;
-    const bool valid = k < n;
-    float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
-    bool left = false;
-    float cx = 0.f, cy = 0.f, cz = 0.f;
-    if (valid) {
-      lo = src[2 * k];
-      hi = src[2 * k + 1];
-      cx = centre(lo.x, hi.x);
-      cy = centre(lo.y, hi.y);
-      cz = centre(lo.z, hi.z);
-      left = axis >= 0 ? bin_of(axis == 0 ? cx : (axis == 1 ? cy : cz), acmin, ascl, K) < plane : k < nl;
-    }
-    __syncwarp();
-    const unsigned bal = __ballot_sync(kFull, left);
-    const int rank = __popc(bal & ((1u << lane) - 1u));
-    const int d = left ? lrun + rank : nl + rrun + (lane - rank);
-    if (valid && d < n) {
-      dst[2 * d] = lo;
-      dst[2 * d + 1] = hi;
-      if (left)
-        acc13_add(ua, rec_codes(lo, hi, cx, cy, cz));
-      else
-        acc13_add(ub, rec_codes(lo, hi, cx, cy, cz));
-    }
-    const int tot = __popc(bal);
-    lrun += tot;
-    rrun += min(32, n - g) - tot;
-  }
-  acc13_warp(ua);
-  acc13_warp(ub);
-  const BinU L = binu_load(ua), R = binu_load(ub);
-  __syncwarp();
-  const int nr = n - nl;
-  const bool leafl = nl <= A.max_leaf, leafr = nr <= A.max_leaf;
-  if (leafl) leaf_out(A, dst, gbegin + X.b, nl, lane, 32);
-  if (leafr) leaf_out(A, dst + 2 * nl, gbegin + X.b + nl, nr, lane, 32);
-  const int id = gbegin + X.b + nl - 1;
-  if (lane == 0) {
-    if (lrun != nl) set_status(A.ctl, kStBadSplit, 7);
-    write_node(A, id, X.parent, X.side, L, leafl ? leaf_ref(gbegin + X.b, nl) : INT_MAX, nl, R,
-               leafr ? leaf_ref(gbegin + X.b + nl, nr) : INT_MAX, nr, epoch);
-  }
-  note_node(ws, nl, nr, leafl, leafr, X.depth);
-  const bool bigl = nl > kMicro, bigr = nr > kMicro;
-  const int keep = (bigl && bigr) ? (nl >= nr ? 0 : 1) : (bigl ? 0 : (bigr ? 1 : -1));
-  const SubNode cl = sub_node(X.b, nl, id, 0, X.depth + 1, p ^ 1, L);
-  const SubNode cr = sub_node(X.b + nl, nr, id, 1, X.depth + 1, p ^ 1, R);
-  if (__any_sync(kFull, keep >= 0)) {
-    cont = keep == 0 ? cl : cr;
-    // hand the rest to the shared lists: records and node first, then the lock
-    const bool pw = bigl && bigr;
-    const bool ml = nl > A.max_leaf && !bigl, mr = nr > A.max_leaf && !bigr;
-    if (__any_sync(kFull, pw || ml || mr)) {
-      __threadfence_block();
-      __syncwarp();
-      if (sub_lock(A, S)) {
-        if (lane == 0) {
-          if (pw) {
-            if (S.nw < kSubList)
-              S.wl[S.nw++] = keep == 0 ? cr : cl;
-            else
-              set_status(A.ctl, kStQueueOverflow, 7);
-          }
-          for (int s = 0; s < 2; ++s) {
-            if (!(s ? mr : ml)) continue;
-            const SubNode& ch = s ? cr : cl;
-            if (S.nm < kMicroList)
-              S.ml[S.nm++] = micro_pack(ch.b, ch.n, id, s, ch.depth - tdepth, p ^ 1);
-            else
-              set_status(A.ctl, kStQueueOverflow, 8);
-          }
-        }
-        sub_unlock(S);
-      }
-    }
-    return true;
-  }
-#pragma unroll
-  for (int s = 0; s < 2; ++s) {
-    const SubNode& ch = s ? cr : cl;
-    if (!__any_sync(kFull, ch.n > A.max_leaf)) continue;
-    float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
-    if (lane < ch.n) {
-      lo = S.rec[p ^ 1][2 * (ch.b + lane)];
-      hi = S.rec[p ^ 1][2 * (ch.b + lane) + 1];
-    }
-    micro_sort_build(A, lo, hi, gbegin + ch.b, ch.n, id, s, ch.depth, epoch, ws);
-  }
-  return false;
-}
-
-// The warps' part of a subtree: take nodes from the shared lists (warp
-// nodes first) until the lists are empty and no warp is working.  Waits
-// are bounded.
-__device__ void warp_phase(const BuildArgs& A, SubSmem& S, int gbegin, int tdepth, int epoch, WarpStats& ws) {
+// The warps finish the collected nodes of at most 32 records, one node per
+// warp at a time (no node is added any more).
+__device__ void micro_phase(const BuildArgs& A, SubSmem& S, int gbegin, int tdepth, int epoch, WarpStats& ws) {
   const int lane = threadIdx.x & 31;
-  int idle = 0, nap = 32;
+  const int nm = S.nm;
   for (;;) {
-    // look before taking the lock: an idle warp only reads and sleeps
-    // (backing off), so it leaves the shared-memory pipe to working warps
-    const bool look = ld_volatile(&S.nw) + ld_volatile(&S.nm) > 0 || ld_volatile(&S.active) == 0;
-    if (!__any_sync(kFull, look)) {
-      if (++idle > A.spin_limit) {
-        if (lane == 0) set_status(A.ctl, kStQueueTimeout, 8);
-        break;
-      }
-      __nanosleep(nap);
-      nap = min(2 * nap, 1024);
-      continue;
+    int i = 0;
+    if (lane == 0) i = atomicAdd(&S.mnext, 1);
+    i = __shfl_sync(kFull, i, 0);
+    if (i >= nm) break;
+    const int2 m = S.ml[i];
+    const int f = m.y;
+    const int b = f & 1023, n = (f >> 10) & 63, side = (f >> 16) & 1, par = (f >> 17) & 1, dep = f >> 18;
+    float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
+    if (lane < n) {
+      lo = S.rec[par][2 * (b + lane)];
+      hi = S.rec[par][2 * (b + lane) + 1];
     }
-    int kind = -1;  // -1 stop, 0 nothing yet, 1 warp node, 2 small node
-    SubNode X;
-    int2 m = make_int2(0, 0);
-    if (sub_lock(A, S)) {
-      if (lane == 0) {
-        // `active` also drops outside the lock (a warp finishing a node), so
-        // every change to it is atomic
-        if (S.nw > 0) {
-          X = S.wl[--S.nw];
-          kind = 1;
-          atomicAdd(&S.active, 1);
-        } else if (S.nm > 0) {
-          m = S.ml[--S.nm];
-          kind = 2;
-          atomicAdd(&S.active, 1);
-        } else {
-          kind = (ld_volatile(&S.active) == 0 || ld_volatile(&A.ctl->status) != 0) ? -1 : 0;
-        }
-      }
-      sub_unlock(S);
-    }
-    // branch only on warp votes: their results are uniform by construction,
-    // so the warp-synchronous code below runs in a provably converged warp
-    if (__any_sync(kFull, lane == 0 && kind < 0)) break;
-    if (__any_sync(kFull, lane == 0 && kind == 0)) {
-      if (++idle > A.spin_limit) {
-        if (lane == 0) set_status(A.ctl, kStQueueTimeout, 8);
-        break;
-      }
-      __nanosleep(nap);
-      nap = min(2 * nap, 1024);
-      continue;
-    }
-    idle = 0;
-    nap = 32;
-    if (__any_sync(kFull, lane == 0 && kind == 1)) {
-      X.b = __shfl_sync(kFull, X.b, 0);
-      X.n = __shfl_sync(kFull, X.n, 0);
-      X.parent = __shfl_sync(kFull, X.parent, 0);
-      X.side = __shfl_sync(kFull, X.side, 0);
-      X.depth = __shfl_sync(kFull, X.depth, 0);
-      X.par = __shfl_sync(kFull, X.par, 0);
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        X.clo[a] = __shfl_sync(kFull, X.clo[a], 0);
-        X.chi[a] = __shfl_sync(kFull, X.chi[a], 0);
-      }
-      SubNode cur = X;
-      for (int guard = 0; guard < kSubMax; ++guard) {
-        SubNode nx;
-        if (!__any_sync(kFull, warp_split(A, S, cur, gbegin, tdepth, epoch, ws, nx))) break;
-        cur = nx;
-      }
-    } else {
-      const int parent = __shfl_sync(kFull, m.x, 0), f = __shfl_sync(kFull, m.y, 0);
-      const int b = f & 1023, n = (f >> 10) & 63, side = (f >> 16) & 1, par = (f >> 17) & 1, dep = f >> 18;
-      float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
-      if (lane < n) {
-        lo = S.rec[par][2 * (b + lane)];
-        hi = S.rec[par][2 * (b + lane) + 1];
-      }
-      micro_sort_build(A, lo, hi, gbegin + b, n, parent, side, tdepth + dep, epoch, ws);
-    }
-    __threadfence_block();
-    __syncwarp();
-    if (lane == 0) atomicSub(&S.active, 1);
+    micro_sort_build(A, lo, hi, gbegin + b, n, m.x, side, tdepth + dep, epoch, ws);
   }
 }
 
@@ -2081,39 +1845,33 @@ __device__ void sub_tree(const BuildArgs& A, SubSmem& S, const Task& t, int epoc
   const float4* g = A.rec[t.pad & 1] + 2 * (size_t)t.begin;
   for (int k = tid; k < 2 * n; k += kBlock) S.rec[0][k] = __ldcg(g + k);
   if (tid == 0) {
-    S.lock = 0;
-    S.nw = S.nm = S.ncs = S.active = 0;
-    SubNode r;
-    r.b = 0;
-    r.n = n;
-    r.parent = t.parent;
-    r.side = t.side;
-    r.depth = t.depth;
-    r.par = 0;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      r.clo[a] = t.clo[a];
-      r.chi[a] = t.chi[a];
-    }
-    if (n <= kMicro)
+    S.nm = 0;
+    S.mnext = 0;
+    S.got = 0;
+    if (n <= kMicro) {
       S.ml[S.nm++] = micro_pack(0, n, t.parent, t.side, 0, 0);
-    else if (n <= kWarpMax)
-      S.wl[S.nw++] = r;
-    else
-      S.cs[S.ncs++] = r;
+    } else {
+      SubNode& r = S.cur;
+      r.b = 0;
+      r.n = n;
+      r.parent = t.parent;
+      r.side = t.side;
+      r.depth = t.depth;
+      r.par = 0;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        r.clo[a] = t.clo[a];
+        r.chi[a] = t.chi[a];
+      }
+      S.got = 1;
+    }
   }
   __syncthreads();
-  for (;;) {  // nodes of more than kWarpMax records: the whole CTA, one at a time
-    if (tid == 0) {
-      S.got = S.ncs > 0;
-      if (S.got) S.cur = S.cs[--S.ncs];
-    }
-    __syncthreads();
-    if (!S.got) break;
+  while (S.got) {  // the chain of larger children, split by the whole CTA
     const SubNode X = S.cur;
     cta_split(A, S, X, t.begin, t.depth, epoch, ws);
   }
-  warp_phase(A, S, t.begin, t.depth, epoch, ws);
+  micro_phase(A, S, t.begin, t.depth, epoch, ws);
   __syncthreads();
 }
 
