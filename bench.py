@@ -340,6 +340,17 @@ def run_served(rtbvh, torch, seconds):
 
 
 # ---------------------------------------------------------------- GPU
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# two kernels on this workload, from one ncu capture each of the current
+# kernels (max_leaf 4, 16 bins, 128-ray tile, alpha 0.7).
+NCU_TRAFFIC = {
+    "k_split": (1.703424e6 + 1.024e3, "ncu capture of k_split, medium city (profiles/k_split_medium_city.md)"),
+    "k_trace": (21.520384e6 + 0.122112e6,
+                "ncu capture of k_trace<0,0,128> (k_retest64 not included), medium city "
+                "(profiles/k_trace_medium_city.md)"),
+}
+
+
 def split_kernel_bytes(ex):
     """Algorithmic bytes of one launch of the split kernel for this tree: every
     32-byte record read and written once per binary level above the
@@ -527,13 +538,17 @@ def run_ours(args):
     trace_gbs = bytes_per_ray * R / (mean_trace_ms * 1e-3) / 1e9
     split_gbs = split_bytes / (mean_split_ms * 1e-3) / 1e9
     roof_trace = {"bound": "hbm", "achieved": trace_gbs, "peak": hbm, "unit": "GB/s", "frac": trace_gbs / hbm,
-                  "traffic": None, "kernel": "k_trace + k_retest64 (one rt_trace_closest)", "peak_source": peak_src,
+                  "traffic": NCU_TRAFFIC["k_trace"][0], "traffic_unit": "bytes per launch",
+                  "traffic_source": NCU_TRAFFIC["k_trace"][1],
+                  "kernel": "k_trace + k_retest64 (one rt_trace_closest)", "peak_source": peak_src,
                   "ms": mean_trace_ms, "bytes_per_ray": bytes_per_ray, "algorithmic_bytes": bytes_per_ray * R,
                   "l2_probe_gbs": l2_gbs, "frac_of_l2_probe": trace_gbs / l2_gbs,
                   "note": "algorithmic bytes = 32 ray + 16 hit + 128 B x nodes + 48 B x triangles per ray; "
                           "nodes and triangles stay in L2 for this scene"}
     roof_split = {"bound": "hbm", "achieved": split_gbs, "peak": hbm, "unit": "GB/s", "frac": split_gbs / hbm,
-                  "traffic": None, "kernel": "k_split (one launch per build)", "peak_source": peak_src,
+                  "traffic": NCU_TRAFFIC["k_split"][0], "traffic_unit": "bytes per launch",
+                  "traffic_source": NCU_TRAFFIC["k_split"][1],
+                  "kernel": "k_split (one launch per build)", "peak_source": peak_src,
                   "ms": mean_split_ms, "algorithmic_bytes": split_bytes, "l2_probe_gbs": l2_gbs,
                   "frac_of_l2_probe": split_gbs / l2_gbs,
                   "note": "algorithmic bytes = 64 B per record per binary level above the 32-triangle subtrees "
