@@ -86,6 +86,10 @@ def lib():
             L.orc_fibonacci.argtypes = [ctypes.c_int64, _f64p]
             L.orc_icosphere.restype = ctypes.c_int64
             L.orc_icosphere.argtypes = [ctypes.c_int, _f64p]
+            L.orc_receive.restype = ctypes.c_int64
+            L.orc_receive.argtypes = [_f32p, _f32p, ctypes.c_int64, _f32p, ctypes.c_int64,
+                                      ctypes.c_double, ctypes.c_double, ctypes.c_double, _i32p,
+                                      _f64p, ctypes.c_int64]
             _lib = L
     return _lib
 
@@ -264,3 +268,25 @@ def icosphere(level) -> np.ndarray:
     m = lib().orc_icosphere(level, _p(out, _f64p))
     assert m == n
     return out
+
+
+def receive(rays, hit_t, rx, delta, range0, tol=0.0):
+    """Receiving-sphere test of Sec. III.C (Eq. 4), every segment against every receiver.
+
+    Returns (pairs int32 [k, 3] = (ray, rx, class), vals float64 [k, 3] = (l, distance,
+    radius)); class 1 = received with more than `tol` to spare, class 2 = within `tol` of
+    the sphere or of a segment end (either answer is right at float32 precision)."""
+    ry = _rays(rays)
+    n = ry.shape[0]
+    ht = np.ascontiguousarray(hit_t, dtype=np.float32).reshape(n)
+    p = np.ascontiguousarray(rx, dtype=np.float32).reshape(-1, 3)
+    cap = 1 << 16
+    while True:
+        oi = np.empty((cap, 3), np.int32)
+        od = np.empty((cap, 3), np.float64)
+        k = lib().orc_receive(_p(ry, _f32p), _p(ht, _f32p), n, _p(p, _f32p), p.shape[0],
+                              float(delta), float(range0), float(tol), _p(oi, _i32p),
+                              _p(od, _f64p), cap)
+        if k <= cap:
+            return oi[:k].copy(), od[:k].copy()
+        cap = int(k)

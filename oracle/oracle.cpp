@@ -24,6 +24,8 @@
 //  5. tree cost      Eq. 2 applied recursively to score any binary tree.
 //  6. reflection     specular bounce of Sec. III.B.
 //  7. launch dirs    icosahedral subdivision of Sec. III.A; Fibonacci sphere.
+//  8. reception      receiving sphere of Sec. III.C (Eq. 4), every path
+//                    segment against every receiver.
 //
 // Readings of points the paper leaves open (all documented with the design):
 //  * hit rule: edges inclusive (u >= 0, v >= 0, u + v <= 1); |det| <=
@@ -34,6 +36,12 @@
 //    centre of AABB X to the source point; optional normalisation
 //    (dist_norm = 1) d^2 / diag(C)^2 * k_C * t_i.
 //  * Eq. 3 boxes are closed (min <= x <= max).
+//  * Eq. 4 reception: a segment t in [tmin, tend) of ray (o, d) (tend = the
+//    nearer of its hit and tmax) receives at point p when the foot of the
+//    perpendicular from p, t* = (p - o).d / (d.d), lies in [tmin, tend) and
+//    |p - (o + t* d)| <= l delta / sqrt(3) with l = (range0 - tmax) + t*:
+//    the path length from the source, since every bounce leaves the
+//    remaining range in tmax (directions have unit length).
 #include <algorithm>
 #include <array>
 #include <atomic>
@@ -754,6 +762,56 @@ int64_t orc_icosphere(int level, double* out3) {
         emit({a.x * w0 + b.x * wi + c.x * wj, a.y * w0 + b.y * wi + c.y * wj,
               a.z * w0 + b.z * wi + c.z * wj});
       }
+  return w;
+}
+
+// 8. Reception (Sec. III.C, Eq. 4), every ray segment against every
+// receiver.  rays: float32 [n][8] (o, tmin, d, tmax); hit_t: float32 [n]
+// (+inf: no hit); rx: float32 [m][3].  A pair is reported when it is
+// received (class 1: inside by more than tol in distance to the sphere and
+// in t* to both segment ends) or within tol of the boundary (class 2); pairs
+// farther outside are not reported.  out_i: [cap][3] (ray, rx, class);
+// out_d: [cap][3] (l, distance, radius).  Returns the number of pairs found
+// (only the first cap are written).
+int64_t orc_receive(const float* rays, const float* hit_t, int64_t n, const float* rx, int64_t m,
+                    double delta, double range0, double tol, int32_t* out_i, double* out_d,
+                    int64_t cap) {
+  const double k = delta / std::sqrt(3.0);
+  int64_t w = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    const float* r = rays + 8 * i;
+    const V3 o = {(double)r[0], (double)r[1], (double)r[2]};
+    const V3 d = {(double)r[4], (double)r[5], (double)r[6]};
+    const double tmin = (double)r[3], tmax = (double)r[7];
+    const double th = (double)hit_t[i];
+    const double tend = th < tmax ? th : tmax;
+    const double dd = dot(d, d);
+    if (!(dd > 0.0) || !(tend > tmin)) continue;
+    const double lprev = range0 - tmax;
+    for (int64_t j = 0; j < m; ++j) {
+      const V3 p = {(double)rx[3 * j], (double)rx[3 * j + 1], (double)rx[3 * j + 2]};
+      const V3 q = sub(p, o);
+      const double ts = dot(q, d) / dd;
+      const V3 f = {o.x + ts * d.x, o.y + ts * d.y, o.z + ts * d.z};
+      const V3 e = sub(p, f);
+      const double dist = std::sqrt(dot(e, e));
+      const double l = lprev + ts;
+      const double rad = l * k;
+      // signed margins: positive inside
+      const double mr = rad - dist, m0 = ts - tmin, m1 = tend - ts;
+      const double lo = std::min(mr, std::min(m0, m1));
+      if (lo < -tol) continue;
+      if (w < cap) {
+        out_i[3 * w] = (int32_t)i;
+        out_i[3 * w + 1] = (int32_t)j;
+        out_i[3 * w + 2] = lo > tol ? 1 : 2;
+        out_d[3 * w] = l;
+        out_d[3 * w + 1] = dist;
+        out_d[3 * w + 2] = rad;
+      }
+      ++w;
+    }
+  }
   return w;
 }
 

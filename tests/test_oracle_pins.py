@@ -509,3 +509,97 @@ def test_metro_generator_counts_prisms_and_determinism():
     poly = t[0:2 * n:2, 0, :2]
     ref = np.asarray(scenes._prism(poly, h[0]), np.float64).astype(np.float32)
     assert np.array_equal(a.tris[:len(ref)], ref)
+
+
+# --------------------------------------------------------------- reception (Sec. III.C, Eq. 4)
+def _unit(v):
+    v = np.asarray(v, np.float64)
+    return v / np.linalg.norm(v)
+
+
+def test_receive_sphere_radius_closed_form(orc):
+    # Eq. 4: r = l delta / sqrt(3).  A ray from the origin along a skew unit
+    # direction; receivers at path length L, offset sideways by 0.99 r / 1.01 r
+    d = _unit((3.0, -2.0, 1.5))
+    side = _unit(np.cross(d, (0.0, 0.0, 1.0)))
+    delta, L = 0.004, 200.0
+    r = L * delta / math.sqrt(3.0)
+    assert abs(r - 0.46188) < 1e-5  # 200 * 0.004 / 1.7320508
+    rays = np.array([[0, 0, 0, 0, *d, 500.0]], np.float32)
+    rx = np.array([L * d + 0.99 * r * side, L * d + 1.01 * r * side, L * d - 0.5 * r * side, L * d],
+                  np.float32)
+    pairs, vals = orc.receive(rays, np.array([np.inf], np.float32), rx, delta, 500.0)
+    got = {int(j): (int(c), v) for (_, j, c), v in zip(pairs, vals)}
+    assert set(got) == {0, 2, 3}
+    for j in (0, 2, 3):
+        assert got[j][0] == 1
+        assert abs(got[j][1][0] - L) < 1e-4 and abs(got[j][1][2] - r) < 1e-6
+    assert abs(got[3][1][1]) < 1e-4 and abs(got[0][1][1] - 0.99 * r) < 1e-4
+
+
+def test_receive_segment_ends_and_hit_cut(orc):
+    d = _unit((1.0, 1.0, 0.0))
+    rays = np.array([[10, 20, 5, 30.0, *d, 400.0]], np.float32)  # segment starts at t = 30
+    o = np.array([10.0, 20.0, 5.0])
+    rx = np.array([o + 20 * d, o + 80 * d, o + 160 * d, o + 450 * d], np.float32)
+    # no hit: [30, 400) -> 80 and 160 received, 20 (before tmin) and 450 (past tmax) not
+    pairs, _ = orc.receive(rays, np.array([np.inf], np.float32), rx, 0.01, 400.0)
+    assert sorted(int(j) for _, j, c in pairs if c == 1) == [1, 2]
+    # a hit at t = 120 cuts the segment: only 80 remains
+    pairs, _ = orc.receive(rays, np.array([120.0], np.float32), rx, 0.01, 400.0)
+    assert sorted(int(j) for _, j, c in pairs if c == 1) == [1]
+
+
+def test_receive_path_length_after_ground_bounce_is_image_distance(orc):
+    # Tx at height h; a ray hits the ground plane z = 0 and reflects.  Along the
+    # reflected ray the unfolded path length equals the distance from the
+    # receiver to the mirror image of the Tx (image method), so Eq. 4 uses it.
+    h, R0 = 30.0, 500.0
+    tx = np.array([100.0, 50.0, h])
+    g = np.array([160.0, 90.0, 0.0])
+    d0 = _unit(g - tx)
+    ground = np.array([[[-1e4, -1e4, 0], [3e4, -1e4, 0], [-1e4, 3e4, 0]]], np.float32)
+    r0 = np.array([[*tx, 0.0, *d0, R0]], np.float32)
+    hit = orc.closest_brute(ground, r0)
+    assert hit.id[0] == 0
+    refl = orc.reflect(ground, r0, hit.id, hit.t)
+    r1 = refl.astype(np.float32)
+    assert abs(refl[0, 7] - (R0 - np.linalg.norm(g - tx))) < 1e-4  # float32 direction
+    image = tx * np.array([1, 1, -1])
+    p = refl[0, :3] + 75.0 * refl[0, 4:7]  # a receiver on the reflected ray
+    pairs, vals = orc.receive(r1, np.array([np.inf], np.float32), p[None].astype(np.float32), 0.01, R0)
+    assert len(pairs) == 1 and pairs[0, 2] == 1
+    assert abs(vals[0, 0] - np.linalg.norm(p - image)) < 1e-3
+
+
+def test_receive_matches_cross_product_formula(orc):
+    # the same rule written another way (numpy, float64): distance to the line
+    # by |q x d| / |d|, foot by q.d / d.d; decisions agree outside the
+    # tolerance band, whose pairs the checker marks as class 2
+    rng = np.random.default_rng(7)
+    n, m = 300, 200
+    o = rng.uniform(-50, 50, (n, 3))
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    tmin = rng.uniform(0, 5, n)
+    tmax = rng.uniform(50, 120, n)
+    rays = np.concatenate([o, tmin[:, None], d, tmax[:, None]], 1).astype(np.float32)
+    ht = np.where(rng.random(n) < 0.5, rng.uniform(10, 150, n), np.inf).astype(np.float32)
+    rx = rng.uniform(-60, 60, (m, 3)).astype(np.float32)
+    delta, R0, tol = 0.05, 150.0, 1e-6
+    pairs, _ = orc.receive(rays, ht, rx, delta, R0, tol=tol)
+    sure = {(int(i), int(j)) for i, j, c in pairs if c == 1}
+    near = {(int(i), int(j)) for i, j, c in pairs}
+    R = rays.astype(np.float64)
+    P = rx.astype(np.float64)
+    want = set()
+    for i in range(n):
+        oo, dd = R[i, :3], R[i, 4:7]
+        q = P - oo
+        ts = q @ dd / (dd @ dd)
+        dist = np.linalg.norm(np.cross(q, dd), axis=1) / np.linalg.norm(dd)
+        tend = min(float(ht[i]), R[i, 7])
+        ok = (ts >= R[i, 3]) & (ts < tend) & (dist <= (R0 - R[i, 7] + ts) * delta / math.sqrt(3))
+        want |= {(i, int(j)) for j in np.nonzero(ok)[0]}
+    assert len(want) > 20
+    assert sure <= want <= near
