@@ -281,6 +281,56 @@ int rt_reflect(rt_scene scene, const rt_ray* rays_dev, const rt_hit* hits_dev, i
                rt_ray* out_rays_dev, int32_t* out_skip_dev, int32_t* out_src_dev,
                int32_t* out_count_dev, void* stream);
 
+/* ---- reception (Sec. III.C, Eq. 4) ---------------------------------- */
+typedef struct rt_rxset_s* rt_rxset;
+
+/* One received path segment: the ray's index in the rays passed, the
+ * receiver's index, the path length l from the source to the foot of the
+ * perpendicular from the receiver (Eq. 4's l) and the receiver's distance
+ * to the ray there. */
+typedef struct {
+  int32_t ray;
+  int32_t rx;
+  float l;
+  float dist;
+} rt_rx_record; /* 16 B */
+
+typedef struct {
+  float delta;         /* angle between adjacent rays at the source, radians (Eq. 4) */
+  float range0;        /* the paths' initial ray action range; l = (range0 - tmax) + t* */
+  int32_t max_records; /* capacity of out_dev, in records */
+  int32_t reserved;    /* 0 */
+} rt_receive_params;
+
+/* Receivers: rx_host = m * 3 floats (x, y, z), copied to the device into a
+ * uniform grid in which every receiver is entered into each cell its largest
+ * receiving sphere (radius r_max) overlaps.  Synchronous.  Errors:
+ * RT_EINVAL (NULL, m < 1, r_max not positive and finite, non-finite
+ * position), RT_ENOMEM, RT_ECUDA. */
+int rt_rxset_create(const float* rx_host, int32_t m, float r_max, rt_rxset* out);
+
+/* Free a receiver set (synchronous). */
+int rt_rxset_destroy(rt_rxset rs);
+
+/* Receiving-sphere test of Sec. III.C (Eq. 4) for the path segments of n
+ * rays: ray i covers t in [tmin, tend), tend = min(hits[i].t, tmax) (a
+ * miss: tmax), and receives at receiver p when the foot of the
+ * perpendicular from p, t* = (p - o).d / (d.d), lies in [tmin, tend) and
+ * |p - (o + t* d)| <= l delta / sqrt(3) with l = (range0 - tmax) + t*
+ * (every bounce leaves the remaining range in tmax; directions have unit
+ * length, as rt_gen_rays and rt_reflect make them).  Each (ray, receiver)
+ * pair is reported once, in no particular order, as an rt_rx_record in
+ * out_dev; *count_dev (device int, zeroed by the call) receives the number
+ * of pairs found, which may exceed max_records (the records past it are
+ * dropped).  n_dev (nullable, device int): the number of valid rays when it
+ * is smaller than n (a compacted order of rt_batch_order).  Rays with a
+ * non-finite component or tmax <= tmin receive nothing.  Asynchronous on
+ * `stream`.  Errors: RT_EINVAL (NULL buffers, n out of range, delta or
+ * range0 not positive and finite, range0 * delta / sqrt(3) > the set's
+ * r_max, max_records < 0), RT_ECUDA. */
+int rt_receive(rt_rxset rs, const rt_ray* rays_dev, const rt_hit* hits_dev, int64_t n, const int32_t* n_dev,
+               const rt_receive_params* params, rt_rx_record* out_dev, int32_t* count_dev, void* stream);
+
 /* ---- batched multi-bounce tracing ------------------------------------ */
 typedef struct rt_batch_s* rt_batch;
 

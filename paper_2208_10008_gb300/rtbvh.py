@@ -39,7 +39,8 @@ EXPORTS = ["rt_version", "rt_launch_count", "rt_last_error", "rt_scene_upload", 
            "rt_reflect", "rt_batch_create", "rt_batch_run", "rt_batch_stats_get", "rt_batch_order",
            "rt_batch_visibility", "rt_batch_destroy", "rt_session_create", "rt_session_add_scene",
            "rt_session_submit", "rt_session_poll", "rt_session_wait", "rt_session_stats_get",
-           "rt_session_destroy", "rt_scene_set_split_events", "rt_autotune", "rt_debug_inject"]
+           "rt_session_destroy", "rt_scene_set_split_events", "rt_autotune", "rt_debug_inject",
+           "rt_rxset_create", "rt_rxset_destroy", "rt_receive"]
 
 # test hooks (rt_debug_inject)
 RT_DEBUG_SPIN_LIMIT, RT_DEBUG_PHANTOM_TASK, RT_DEBUG_PHANTOM_ITEM, RT_DEBUG_FAIL_ALLOC = 1, 2, 3, 4
@@ -60,6 +61,11 @@ class BuildParams(ctypes.Structure):
 class TraceParams(ctypes.Structure):
     _fields_ = [("flags", ctypes.c_uint32), ("skip_tri_dev", ctypes.c_void_p),
                 ("stats_dev", ctypes.c_void_p), ("n_flagged_dev", ctypes.c_void_p), ("block", ctypes.c_int32)]
+
+
+class ReceiveParams(ctypes.Structure):
+    _fields_ = [("delta", ctypes.c_float), ("range0", ctypes.c_float), ("max_records", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class TuneResult(ctypes.Structure):
@@ -155,6 +161,9 @@ def lib(build: bool = True):
             L.rt_session_wait.argtypes = [vp, ctypes.c_uint64, i64]
             L.rt_session_stats_get.argtypes = [vp, ctypes.POINTER(SessionStats)]
             L.rt_session_destroy.argtypes = [vp]
+            L.rt_rxset_create.argtypes = [vp, i32, ctypes.c_float, ctypes.POINTER(vp)]
+            L.rt_rxset_destroy.argtypes = [vp]
+            L.rt_receive.argtypes = [vp, vp, vp, i64, vp, ctypes.POINTER(ReceiveParams), vp, vp, vp]
             _lib = L
     return _lib
 
@@ -587,3 +596,61 @@ class Session:
             self.destroy()
         except Exception:
             pass
+
+
+# ---- reception (Sec. III.C, Eq. 4) -----------------------------------------
+class RxSet:
+    """Owns one rt_rxset (receivers in a device grid)."""
+
+    def __init__(self, handle, m, r_max):
+        self._h = handle
+        self.m = m
+        self.r_max = r_max
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise RuntimeError("receiver set destroyed")
+        return self._h
+
+    def destroy(self):
+        if self._h:
+            _check(lib().rt_rxset_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def rt_rxset_create(rx, r_max):
+    """Receivers rx (host [m, 3]) for receiving spheres up to radius r_max."""
+    a = np.ascontiguousarray(rx, dtype=np.float32).reshape(-1, 3)
+    h = ctypes.c_void_p()
+    _check(lib().rt_rxset_create(a.ctypes.data_as(ctypes.c_void_p), a.shape[0], float(r_max), ctypes.byref(h)))
+    return RxSet(h.value, a.shape[0], float(r_max))
+
+
+def rt_receive(rs: RxSet, rays, hits, delta, range0, out=None, count=None, n_dev=None, max_records=None,
+               stream=None):
+    """Receiving-sphere test (Eq. 4) of every ray's segment against the receivers.
+
+    Returns (records int32 [max_records, 4] = (ray, rx, l bits, dist bits), count int32 [1]),
+    both on the device; records[:count] are valid (view columns 2-3 as float32 for l, dist)."""
+    import torch
+    rp = _dev_ptr(rays, torch.float32, 8, "rays")
+    hp = _dev_ptr(hits, torch.float32, 4, "hits")
+    n = rays.shape[0]
+    if out is None:
+        out = torch.empty((max_records if max_records is not None else max(1024, n // 4), 4), dtype=torch.int32,
+                          device=rays.device)
+    op = _dev_ptr(out, torch.int32, 4, "out")
+    if count is None:
+        count = torch.zeros(1, dtype=torch.int32, device=rays.device)
+    cp = _dev_ptr(count, torch.int32, None, "count")
+    nd = None if n_dev is None else _dev_ptr(n_dev, torch.int32, None, "n_dev")
+    p = ReceiveParams(float(delta), float(range0), int(out.shape[0]), 0)
+    _check(lib().rt_receive(rs.handle, rp, hp, n, nd, ctypes.byref(p), op, cp, _stream(stream)))
+    return out, count

@@ -348,6 +348,14 @@ def random_rays(scene: Scene, n: int, seed: int, zmin=1.0, zmax=60.0, tmax=np.in
 # --------------------------------------------------------------------------
 
 
+def receiver_grid(size: float, k: int, z: float, x0: float = 0.0, y0: float = 0.0) -> np.ndarray:
+    """k x k receivers at height z over the square [x0, x0 + size] x [y0, y0 + size],
+    cell-centred, float32 [k * k, 3] (row-major in y, then x)."""
+    c = (np.arange(k, dtype=np.float64) + 0.5) * (size / k)
+    xx, yy = np.meshgrid(x0 + c, y0 + c)
+    return np.stack([xx.ravel(), yy.ravel(), np.full(k * k, float(z))], 1).astype(np.float32)
+
+
 def workload_tiny():
     """64-box city, 4096 Fibonacci rays from (100, 100, 30), t_max 1000 m, alpha 1."""
     sc = tiny_city(seed=1)

@@ -65,3 +65,21 @@ def test_debug_hooks_validate_without_gpu():
     for hook in (rtbvh.RT_DEBUG_SPIN_LIMIT, rtbvh.RT_DEBUG_PHANTOM_TASK, rtbvh.RT_DEBUG_PHANTOM_ITEM,
                  rtbvh.RT_DEBUG_FAIL_ALLOC):
         assert lib.rt_debug_inject(hook, 0) == 0
+
+
+def test_reception_entry_points_validate_without_gpu():
+    import ctypes
+    lib = rtbvh.lib()
+    rx = (ctypes.c_float * 6)(0, 0, 0, 1, 1, 1)
+    h = ctypes.c_void_p()
+    assert lib.rt_rxset_create(None, 2, 1.0, ctypes.byref(h)) == -1
+    assert lib.rt_rxset_create(rx, 0, 1.0, ctypes.byref(h)) == -1
+    assert lib.rt_rxset_create(rx, 2, 0.0, ctypes.byref(h)) == -1
+    assert lib.rt_rxset_create(rx, 2, float("inf"), ctypes.byref(h)) == -1
+    bad = (ctypes.c_float * 3)(0, float("nan"), 0)
+    assert lib.rt_rxset_create(bad, 1, 1.0, ctypes.byref(h)) == -1
+    assert b"non-finite" in lib.rt_last_error()
+    assert lib.rt_rxset_destroy(None) == -1
+    p = rtbvh.ReceiveParams(0.01, 500.0, 16, 0)
+    assert lib.rt_receive(None, None, None, 0, None, ctypes.byref(p), None, None, None) == -1
+    assert b"NULL" in lib.rt_last_error()
