@@ -21,6 +21,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -257,6 +258,48 @@ def run_batched(rtbvh, torch, runs):
             "speedup": ms_p / ms_b, "autotuned": tune,
             "batched": "one CUDA graph replay per run (device-side counts)",
             "plain": "per-transmitter rt_gen_rays / rt_trace_closest / rt_reflect calls, counts read by the host"}
+
+
+def run_reception(rtbvh, torch, scenes, rays, hits, hbm, reps=20):
+    """Receiving spheres (Eq. 4) of the step's direct rays against a 64 x 64 receiver grid at
+    1.5 m over the medium city: delta = the icosphere-8 spacing, range 500 m."""
+    R = rays.shape[0]
+    rx = scenes.receiver_grid(1000.0, 64, 1.5)
+    delta = math.atan(2.0) / 2 ** 8
+    rs = rtbvh.rt_rxset_create(rx, 500.0 * delta / math.sqrt(3.0))
+    out = torch.empty((1 << 18, 4), dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+    st = torch.cuda.Stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    with torch.cuda.stream(st):
+        for _ in range(3):
+            rtbvh.rt_receive(rs, rays, hits, delta, 500.0, out=out, count=cnt, stream=st)
+    st.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    with torch.cuda.stream(st):
+        for a, b in ev:
+            flush.zero_()
+            a.record(st)
+            rtbvh.rt_receive(rs, rays, hits, delta, 500.0, out=out, count=cnt, stream=st)
+            b.record(st)
+    st.synchronize()
+    ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    stats = torch.zeros(2, dtype=torch.int64, device="cuda")
+    with torch.cuda.stream(st):
+        rtbvh.rt_receive(rs, rays, hits, delta, 500.0, out=out, count=cnt, stats=stats, stream=st)
+    st.synchronize()
+    pairs = int(cnt.item())
+    cells, entries = (int(v) for v in stats.cpu().tolist())
+    # algorithmic bytes: ray + hit in, two cell bounds per cell visited, an index and a
+    # 16-byte position per receiver entry tested, 16 bytes per record out
+    per_ray = 32 + 16 + 8 * cells / R + 20 * entries / R + 16 * pairs / R
+    gbs = per_ray * R / (ms * 1e-3) / 1e9
+    rs.destroy()
+    return {"workload": "medium_city_icosphere_L8_direct_rays_64x64_receivers_1.5m", "rays": R,
+            "receivers": int(rx.shape[0]), "delta_rad": delta, "pairs": pairs, "ms": ms,
+            "mrays_s": R / (ms * 1e-3) / 1e6, "cells_per_ray": cells / R, "entries_per_ray": entries / R,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                         "bytes_per_ray": per_ray, "kernel": "k_receive"}}
 
 
 def run_alpha_sweep(rtbvh, torch, sc, rays, source, reps=10):
@@ -531,6 +574,10 @@ def run_ours(args):
     extra = {}
     if not args.no_extra:
         extra["alpha_sweep"] = run_alpha_sweep(rtbvh, torch, sc, rays, p["source"])
+        with torch.cuda.stream(stream):
+            run_trace()
+        stream.synchronize()
+        extra["reception"] = run_reception(rtbvh, torch, scenes, rays, hits, hbm)
         extra["batched"] = run_batched(rtbvh, torch, args.batched_runs)
         extra["served"] = run_served(rtbvh, torch, args.serve_seconds)
     mean_trace_ms = statistics.mean(trace_ms)

@@ -300,6 +300,8 @@ typedef struct {
   float range0;        /* the paths' initial ray action range; l = (range0 - tmax) + t* */
   int32_t max_records; /* capacity of out_dev, in records */
   int32_t reserved;    /* 0 */
+  unsigned long long* stats_dev; /* nullable, device [2]: grid cells visited and receiver
+                                    entries tested, summed over the rays (added to, not zeroed) */
 } rt_receive_params;
 
 /* Receivers: rx_host = m * 3 floats (x, y, z), copied to the device into a

@@ -59,12 +59,14 @@ struct RecvArgs {
   int max_records;
   int4* out;
   int* count;
+  unsigned long long* stats;  // nullable: cells visited, entries tested
 };
 
 __device__ __forceinline__ bool finite3(float a, float b, float c) {
   return isfinite(a) && isfinite(b) && isfinite(c);
 }
 
+template <bool kStats>
 __global__ void __launch_bounds__(kRecvBlock) k_receive(RecvArgs A) {
   const int i = blockIdx.x * kRecvBlock + threadIdx.x;
   const int n = A.n_dev ? min(A.n, __ldg(A.n_dev)) : A.n;
@@ -132,10 +134,15 @@ __global__ void __launch_bounds__(kRecvBlock) k_receive(RecvArgs A) {
   }
   int seen[kRecvSeen];
   int ns = 0;
+  unsigned n_cells = 0, n_entries = 0;
   const int max_steps = A.nx + A.ny + A.nz + 3;
   for (int it = 0; it < max_steps; ++it) {
     const int cell = (c[2] * A.ny + c[1]) * A.nx + c[0];
     const int e0 = __ldg(A.cell_start + cell), e1 = __ldg(A.cell_start + cell + 1);
+    if (kStats) {
+      ++n_cells;
+      n_entries += (unsigned)(e1 - e0);
+    }
     for (int e = e0; e < e1; ++e) {
       const int j = __ldg(A.items + e);
       const float4 p = __ldg(A.pos + j);
@@ -159,6 +166,10 @@ __global__ void __launch_bounds__(kRecvBlock) k_receive(RecvArgs A) {
     c[a] += step[a];
     if (c[a] < 0 || c[a] >= dim[a]) break;
     tn[a] += dt[a];
+  }
+  if (kStats) {
+    atomicAdd(A.stats, (unsigned long long)n_cells);
+    atomicAdd(A.stats + 1, (unsigned long long)n_entries);
   }
 }
 
@@ -255,6 +266,7 @@ extern "C" int rt_receive(rt_rxset s, const rt_ray* rays, const rt_hit* hits, in
   if (!(p->delta > 0.f) || !std::isfinite(p->delta) || !(p->range0 > 0.f) || !std::isfinite(p->range0))
     return rt::set_error(RT_EINVAL, "delta and range0 must be positive and finite");
   if (p->max_records < 0 || (p->max_records > 0 && !out)) return rt::set_error(RT_EINVAL, "bad record buffer");
+  if ((uintptr_t)p->stats_dev & 7) return rt::set_error(RT_EINVAL, "stats_dev must be 8-byte aligned");
   const float k = (float)(p->delta / std::sqrt(3.0));
   if ((double)p->range0 * k > (double)s->r_max * 1.0001)
     return rt::set_error(RT_EINVAL, "range0 * delta / sqrt(3) exceeds the receiver set's r_max");
@@ -281,8 +293,12 @@ extern "C" int rt_receive(rt_rxset s, const rt_ray* rays, const rt_hit* hits, in
   A.max_records = p->max_records;
   A.out = reinterpret_cast<int4*>(out);
   A.count = count;
+  A.stats = p->stats_dev;
   const int grid = (int)((n + kRecvBlock - 1) / kRecvBlock);
-  k_receive<<<grid, kRecvBlock, 0, st>>>(A);
+  if (A.stats)
+    k_receive<true><<<grid, kRecvBlock, 0, st>>>(A);
+  else
+    k_receive<false><<<grid, kRecvBlock, 0, st>>>(A);
   rt::count_launches(1);
   e = cudaGetLastError();
   if (e != cudaSuccess) return rt::set_error(RT_ECUDA, cudaGetErrorString(e));

@@ -65,7 +65,7 @@ class TraceParams(ctypes.Structure):
 
 class ReceiveParams(ctypes.Structure):
     _fields_ = [("delta", ctypes.c_float), ("range0", ctypes.c_float), ("max_records", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("reserved", ctypes.c_int32), ("stats_dev", ctypes.c_void_p)]
 
 
 class TuneResult(ctypes.Structure):
@@ -634,11 +634,13 @@ def rt_rxset_create(rx, r_max):
 
 
 def rt_receive(rs: RxSet, rays, hits, delta, range0, out=None, count=None, n_dev=None, max_records=None,
-               stream=None):
+               stats=None, stream=None):
     """Receiving-sphere test (Eq. 4) of every ray's segment against the receivers.
 
     Returns (records int32 [max_records, 4] = (ray, rx, l bits, dist bits), count int32 [1]),
-    both on the device; records[:count] are valid (view columns 2-3 as float32 for l, dist)."""
+    both on the device; records[:count] are valid (view columns 2-3 as float32 for l, dist).
+    stats (optional int64 [2] device tensor): cells visited and receiver entries tested are
+    added to it."""
     import torch
     rp = _dev_ptr(rays, torch.float32, 8, "rays")
     hp = _dev_ptr(hits, torch.float32, 4, "hits")
@@ -651,6 +653,7 @@ def rt_receive(rs: RxSet, rays, hits, delta, range0, out=None, count=None, n_dev
         count = torch.zeros(1, dtype=torch.int32, device=rays.device)
     cp = _dev_ptr(count, torch.int32, None, "count")
     nd = None if n_dev is None else _dev_ptr(n_dev, torch.int32, None, "n_dev")
-    p = ReceiveParams(float(delta), float(range0), int(out.shape[0]), 0)
+    sp = None if stats is None else _dev_ptr(stats, torch.int64, None, "stats").value
+    p = ReceiveParams(float(delta), float(range0), int(out.shape[0]), 0, sp)
     _check(lib().rt_receive(rs.handle, rp, hp, n, nd, ctypes.byref(p), op, cp, _stream(stream)))
     return out, count

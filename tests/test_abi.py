@@ -80,6 +80,6 @@ def test_reception_entry_points_validate_without_gpu():
     assert lib.rt_rxset_create(bad, 1, 1.0, ctypes.byref(h)) == -1
     assert b"non-finite" in lib.rt_last_error()
     assert lib.rt_rxset_destroy(None) == -1
-    p = rtbvh.ReceiveParams(0.01, 500.0, 16, 0)
+    p = rtbvh.ReceiveParams(0.01, 500.0, 16, 0, None)
     assert lib.rt_receive(None, None, None, 0, None, ctypes.byref(p), None, None, None) == -1
     assert b"NULL" in lib.rt_last_error()

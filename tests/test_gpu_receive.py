@@ -136,10 +136,13 @@ def test_receive_full_size_sampled(rb, orc):
     rx = scenes.receiver_grid(1000.0, 64, 1.5)
     delta = math.atan(2.0) / 2 ** 8
     rs = rb.rt_rxset_create(rx, R0 * delta / math.sqrt(3.0))
-    rec, cnt = rb.rt_receive(rs, rays, hits, delta, R0, max_records=1 << 18)
+    stats = torch.zeros(2, dtype=torch.int64, device="cuda")
+    rec, cnt = rb.rt_receive(rs, rays, hits, delta, R0, max_records=1 << 18, stats=stats)
     torch.cuda.synchronize()
     c = int(cnt.item())
     assert c > 0
+    cells, entries = stats.cpu().tolist()
+    assert cells > 0 and entries >= c  # every reported pair was an entry tested
     # every ray that received something, plus a random sample of the others
     rng = np.random.default_rng(5)
     hit_rays = np.unique(rec[:c, 0].cpu().numpy())
