@@ -302,6 +302,9 @@ typedef struct {
   int32_t reserved;    /* 0 */
   unsigned long long* stats_dev; /* nullable, device [2]: grid cells visited and receiver
                                     entries tested, summed over the rays (added to, not zeroed) */
+  const float* delta_ray_dev;    /* nullable, device [n]: each ray's own delta (rays of
+                                    transmitters launched with different counts); a value
+                                    beyond the set's r_max * sqrt(3) / range0 is taken as that */
 } rt_receive_params;
 
 /* Receivers: rx_host = m * 3 floats (x, y, z), copied to the device into a
@@ -333,6 +336,14 @@ int rt_rxset_destroy(rt_rxset rs);
 int rt_receive(rt_rxset rs, const rt_ray* rays_dev, const rt_hit* hits_dev, int64_t n, const int32_t* n_dev,
                const rt_receive_params* params, rt_rx_record* out_dev, int32_t* count_dev, void* stream);
 
+/* ---- binding check ----------------------------------------------------- */
+/* sizeof of every public struct, for bindings to check their mirrors
+ * against, in this order: rt_ray, rt_hit, rt_build_params, rt_trace_params,
+ * rt_bvh_info_t, rt_tune_result, rt_rx_record, rt_receive_params,
+ * rt_batch_desc, rt_batch_stats, rt_request, rt_session_stats.  Writes
+ * min(n, 12) values to sizes (host) and returns 12.  Needs no GPU. */
+int rt_abi_struct_sizes(int64_t* sizes, int32_t n);
+
 /* ---- batched multi-bounce tracing ------------------------------------ */
 typedef struct rt_batch_s* rt_batch;
 
@@ -354,6 +365,11 @@ typedef struct {
   int32_t use_graph;       /* 1: capture the pipeline in a CUDA graph on the second run, replay after */
   int32_t ray_tile;        /* rt_trace_params.block of every walk of the batch (0 = default),
                               e.g. rt_autotune's choice */
+  int32_t receive;         /* 1: receiving spheres (Sec. III.C, Eq. 4) of every order's
+                              segments against the receivers (n_rx > 0) */
+  int32_t max_rx_records;  /* records kept per order when receive = 1 */
+  const float* rx_delta;   /* host, n_tx (nullable): delta of each transmitter's launch; NULL:
+                              icosphere atan(2) / 2^level, Fibonacci sqrt(4 pi / N) */
 } rt_batch_desc;
 
 typedef struct {
@@ -363,6 +379,7 @@ typedef struct {
   int64_t total_rays;                   /* all orders + segments */
   int64_t visible;                      /* segments with no hit */
   int32_t flagged;                      /* float64 re-tests of the last trace (diagnostic) */
+  int64_t received[RT_BATCH_MAX_ORDER + 1]; /* received pairs of each order (receive = 1) */
 } rt_batch_stats;
 
 /* Allocate everything the pipeline needs for these transmitters on `scene`
@@ -392,6 +409,12 @@ int rt_batch_order(rt_batch batch, int order, const rt_ray** rays_dev, const rt_
 
 /* Device array [n_tx * n_rx] (transmitter-major): 1 = segment blocked. */
 int rt_batch_visibility(rt_batch batch, const uint8_t** occluded_dev);
+
+/* Device pointers of order k's reception records (rt_receive's layout; ray
+ * indices into order k's rays) and of its device count (may exceed
+ * max_rx_records; the records past it are dropped).  Errors: RT_EINVAL
+ * (bad order, or the batch was created without receive). */
+int rt_batch_received(rt_batch batch, int order, const rt_rx_record** records_dev, const int32_t** count_dev);
 
 /* Free the batch (synchronous). */
 int rt_batch_destroy(rt_batch batch);

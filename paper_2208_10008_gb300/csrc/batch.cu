@@ -7,10 +7,13 @@
 // on the host: the count of each reflection order stays on the device and
 // the next trace reads it there.  The first run executes directly; the
 // second captures the whole pipeline into a CUDA graph, which every later
-// run replays with a single launch.
+// run replays with a single launch.  With reception on, every order's
+// segments are also tested against the receivers' spheres (Sec. III.C,
+// Eq. 4), each ray with the angular spacing of its own transmitter's launch.
 #include <cuda_runtime.h>
 
 #include <climits>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -41,6 +44,14 @@ struct rt_batch_s {
   cudaGraphExec_t exec = nullptr;
   int runs = 0;
   long long graph_kernels = 0;  // kernels in the captured graph
+  // reception (Eq. 4)
+  bool receive = false;
+  int max_rx = 0;
+  float dmax = 0.f;                             // largest transmitter delta
+  rt_rxset rxset = nullptr;
+  float* delta[RT_BATCH_MAX_ORDER + 1] = {};    // per ray: its transmitter's delta
+  rt_rx_record* rec[RT_BATCH_MAX_ORDER + 1] = {};
+  int* rx_count = nullptr;                      // device: pairs of order k at rx_count[k]
 };
 
 namespace rt {
@@ -49,7 +60,38 @@ int set_error(int code, const char* msg);
 
 namespace {
 
+// Order-0 rays of transmitter t occupy [off[t], off[t + 1]): each gets
+// that transmitter's delta.
+__global__ void k_delta_fill(const long long* __restrict__ off, const float* __restrict__ dtx, int n_tx, int n,
+                             float* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int lo = 0, hi = n_tx - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= i)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  out[i] = dtx[lo];
+}
+
+// A reflected ray inherits its parent's delta (src: parent index).
+__global__ void k_delta_gather(const float* __restrict__ prev, const int* __restrict__ src, const int* __restrict__ n_dev,
+                               int n, float* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= min(n, __ldg(n_dev))) return;
+  out[i] = __ldg(prev + __ldg(src + i));
+}
+
 void free_batch(rt_batch_s* b) {
+  if (b->rxset) rt_rxset_destroy(b->rxset);
+  for (int k = 0; k <= RT_BATCH_MAX_ORDER; ++k) {
+    if (b->delta[k]) cudaFree(b->delta[k]);
+    if (b->rec[k]) cudaFree(b->rec[k]);
+  }
+  if (b->rx_count) cudaFree(b->rx_count);
   for (int k = 0; k <= RT_BATCH_MAX_ORDER; ++k) {
     if (b->rays[k]) cudaFree(b->rays[k]);
     if (b->hits[k]) cudaFree(b->hits[k]);
@@ -66,6 +108,19 @@ void free_batch(rt_batch_s* b) {
   if (b->st) cudaStreamDestroy(b->st);
 }
 
+// Receiving spheres of order k (device count for k >= 1).
+cudaError_t enqueue_receive(rt_batch_s* b, int k) {
+  rt_receive_params p{};
+  p.delta = b->dmax;
+  p.range0 = b->tmax;
+  p.max_records = b->max_rx;
+  p.delta_ray_dev = b->delta[k];
+  if (rt_receive(b->rxset, b->rays[k], b->hits[k], b->n0, k ? b->counts + k : nullptr, &p, b->rec[k],
+                 b->rx_count + k, b->st) != RT_OK)
+    return cudaErrorInvalidValue;
+  return cudaSuccess;
+}
+
 cudaError_t enqueue(rt_batch_s* b) {
   cudaError_t e;
   cudaStream_t st = b->st;
@@ -78,6 +133,7 @@ cudaError_t enqueue(rt_batch_s* b) {
   tp.block = b->ray_tile;
   if ((e = rt::launch_trace_dev(b->scene, b->rays[0], b->n0, nullptr, b->hits[0], nullptr, &tp, b->scr, st)))
     return e;
+  if (b->receive && (e = enqueue_receive(b, 0))) return e;
   for (int k = 1; k <= b->max_order; ++k) {
     const int* prev = k == 1 ? nullptr : b->counts + (k - 1);
     if ((e = rt::launch_reflect(b->scene, b->rays[k - 1], b->hits[k - 1], b->n0, prev, b->rays[k], b->skip[k],
@@ -89,6 +145,13 @@ cudaError_t enqueue(rt_batch_s* b) {
     if ((e = rt::launch_trace_dev(b->scene, b->rays[k], b->n0, b->counts + k, b->hits[k], nullptr, &tk, b->scr,
                                   st)))
       return e;
+    if (b->receive) {
+      const int n = (int)b->n0;
+      k_delta_gather<<<(n + 255) / 256, 256, 0, st>>>(b->delta[k - 1], b->src[k], b->counts + k, n, b->delta[k]);
+      rt::count_launches(1);
+      if ((e = cudaGetLastError())) return e;
+      if ((e = enqueue_receive(b, k))) return e;
+    }
   }
   if (b->n_seg > 0) {
     rt_trace_params tv{};
@@ -117,6 +180,8 @@ int rt_batch_create(rt_scene scene, const rt_batch_desc* d, rt_batch* out) {
   if (d->max_order < 0 || d->max_order > RT_BATCH_MAX_ORDER) return rt::set_error(RT_EINVAL, "max_order out of range");
   if (!(d->tmax > 0.f)) return rt::set_error(RT_EINVAL, "tmax must be > 0");
   if (d->n_rx < 0 || (d->n_rx > 0 && !d->rx_pos)) return rt::set_error(RT_EINVAL, "bad receivers");
+  if (d->receive && (d->n_rx < 1 || d->max_rx_records < 1))
+    return rt::set_error(RT_EINVAL, "reception needs receivers and max_rx_records >= 1");
   rt_batch_s* b = new (std::nothrow) rt_batch_s();
   if (!b) return rt::set_error(RT_ENOMEM, "host allocation failed");
   b->scene = scene;
@@ -180,6 +245,51 @@ int rt_batch_create(rt_scene scene, const rt_batch_desc* d, rt_batch* out) {
     }
   }
   if (e == cudaSuccess) e = cudaMemset(b->counts, 0, (RT_BATCH_MAX_ORDER + 1) * sizeof(int));
+  if (e == cudaSuccess && d->receive) {
+    // each transmitter's delta: the caller's, or the spacing of its launch
+    std::vector<float> dtx(b->n_tx);
+    for (int t = 0; t < b->n_tx; ++t) {
+      double v = d->rx_delta ? (double)d->rx_delta[t]
+                             : (b->kind == RT_RAYS_ICOSPHERE ? std::atan(2.0) / std::ldexp(1.0, (int)b->param[t])
+                                                              : std::sqrt(4.0 * M_PI / (double)b->count[t]));
+      if (!(v > 0.0) || !std::isfinite(v)) {
+        free_batch(b);
+        delete b;
+        return rt::set_error(RT_EINVAL, "bad delta for a transmitter");
+      }
+      dtx[t] = (float)v;
+      b->dmax = std::max(b->dmax, dtx[t]);
+    }
+    b->receive = true;
+    b->max_rx = d->max_rx_records;
+    const int rc = rt_rxset_create(d->rx_pos, d->n_rx, (float)(b->tmax * (double)b->dmax / std::sqrt(3.0)) * 1.0001f,
+                                   &b->rxset);
+    if (rc != RT_OK) {
+      free_batch(b);
+      delete b;
+      return rc;  // the set's own message stays in rt_last_error
+    }
+    for (int k = 0; k <= b->max_order && e == cudaSuccess; ++k) {
+      e = alloc(&b->delta[k], total);
+      if (e == cudaSuccess) e = alloc(&b->rec[k], b->max_rx);
+    }
+    if (e == cudaSuccess) e = alloc(&b->rx_count, RT_BATCH_MAX_ORDER + 1);
+    if (e == cudaSuccess) e = cudaMemset(b->rx_count, 0, (RT_BATCH_MAX_ORDER + 1) * sizeof(int));
+    long long* off = nullptr;
+    float* dd = nullptr;
+    if (e == cudaSuccess) e = alloc(&off, b->n_tx);
+    if (e == cudaSuccess) e = alloc(&dd, b->n_tx);
+    if (e == cudaSuccess) e = cudaMemcpy(off, b->offset.data(), b->n_tx * sizeof(long long), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dd, dtx.data(), b->n_tx * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+      k_delta_fill<<<(int)((total + 255) / 256), 256>>>(off, dd, b->n_tx, (int)total, b->delta[0]);
+      rt::count_launches(1);
+      e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    }
+    if (off) cudaFree(off);
+    if (dd) cudaFree(dd);
+  }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
@@ -251,6 +361,12 @@ int rt_batch_stats_get(rt_batch b, void* stream, rt_batch_stats* s) {
       return rt::set_error(RT_ECUDA, "read visibility");
     for (uint8_t v : o) s->visible += v == 0;
   }
+  if (b->receive) {
+    int rc[RT_BATCH_MAX_ORDER + 1];
+    if (cudaMemcpy(rc, b->rx_count, sizeof(rc), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return rt::set_error(RT_ECUDA, "read reception counts");
+    for (int k = 0; k <= b->max_order; ++k) s->received[k] = rc[k];
+  }
   int fl = 0;
   cudaMemcpy(&fl, b->scr.counter, sizeof(int), cudaMemcpyDeviceToHost);
   s->flagged = fl;
@@ -265,6 +381,14 @@ int rt_batch_order(rt_batch b, int order, const rt_ray** rays, const rt_hit** hi
   if (hits) *hits = b->hits[order];
   if (src) *src = order ? b->src[order] : nullptr;
   if (count) *count = order ? b->counts + order : nullptr;
+  return RT_OK;
+}
+
+int rt_batch_received(rt_batch b, int order, const rt_rx_record** records, const int32_t** count) {
+  if (!b || order < 0 || order > b->max_order) return rt::set_error(RT_EINVAL, "bad batch or order");
+  if (!b->receive) return rt::set_error(RT_EINVAL, "the batch was created without reception");
+  if (records) *records = b->rec[order];
+  if (count) *count = b->rx_count + order;
   return RT_OK;
 }
 

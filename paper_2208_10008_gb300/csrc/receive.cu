@@ -55,6 +55,8 @@ struct RecvArgs {
   const int* items;
   const float4* pos;
   float k;  // delta / sqrt(3)
+  const float* delta_ray;  // nullable: per-ray delta
+  float k_cap;             // largest k the set supports
   float range0;
   int max_records;
   int4* out;
@@ -83,6 +85,7 @@ __global__ void __launch_bounds__(kRecvBlock) k_receive(RecvArgs A) {
   if (!(dd > 0.f)) return;
   const float inv_dd = 1.f / dd;
   const float lprev = A.range0 - tmax;
+  const float kr = A.delta_ray ? fminf(__ldg(A.delta_ray + i) * 0.57735026918962576f, A.k_cap) : A.k;
   // clip [tmin, tend] to the grid box
   const float hx = A.lo.x + A.nx * A.h, hy = A.lo.y + A.ny * A.h, hz = A.lo.z + A.nz * A.h;
   float ta = tmin, tb = tend;
@@ -152,7 +155,7 @@ __global__ void __launch_bounds__(kRecvBlock) k_receive(RecvArgs A) {
       const float ex = qx - ts * dx, ey = qy - ts * dy, ez = qz - ts * dz;
       const float dist = sqrtf(ex * ex + ey * ey + ez * ez);
       const float l = lprev + ts;
-      if (!(dist <= l * A.k)) continue;
+      if (!(dist <= l * kr)) continue;
       bool dup = false;
       for (int q = 0; q < ns; ++q) dup = dup || seen[q] == j;
       if (dup) continue;
@@ -289,6 +292,8 @@ extern "C" int rt_receive(rt_rxset s, const rt_ray* rays, const rt_hit* hits, in
   A.items = s->items;
   A.pos = s->pos;
   A.k = k;
+  A.delta_ray = p->delta_ray_dev;
+  A.k_cap = (float)((double)s->r_max * 1.0001 / (double)p->range0);
   A.range0 = p->range0;
   A.max_records = p->max_records;
   A.out = reinterpret_cast<int4*>(out);
@@ -303,4 +308,13 @@ extern "C" int rt_receive(rt_rxset s, const rt_ray* rays, const rt_hit* hits, in
   e = cudaGetLastError();
   if (e != cudaSuccess) return rt::set_error(RT_ECUDA, cudaGetErrorString(e));
   return RT_OK;
+}
+
+extern "C" int rt_abi_struct_sizes(int64_t* sizes, int32_t n) {
+  const int64_t v[12] = {sizeof(rt_ray),         sizeof(rt_hit),           sizeof(rt_build_params),
+                         sizeof(rt_trace_params), sizeof(rt_bvh_info_t),    sizeof(rt_tune_result),
+                         sizeof(rt_rx_record),    sizeof(rt_receive_params), sizeof(rt_batch_desc),
+                         sizeof(rt_batch_stats),  sizeof(rt_request),       sizeof(rt_session_stats)};
+  for (int32_t i = 0; sizes && i < n && i < 12; ++i) sizes[i] = v[i];
+  return 12;
 }

@@ -40,7 +40,7 @@ EXPORTS = ["rt_version", "rt_launch_count", "rt_last_error", "rt_scene_upload", 
            "rt_batch_visibility", "rt_batch_destroy", "rt_session_create", "rt_session_add_scene",
            "rt_session_submit", "rt_session_poll", "rt_session_wait", "rt_session_stats_get",
            "rt_session_destroy", "rt_scene_set_split_events", "rt_autotune", "rt_debug_inject",
-           "rt_rxset_create", "rt_rxset_destroy", "rt_receive"]
+           "rt_rxset_create", "rt_rxset_destroy", "rt_receive", "rt_batch_received", "rt_abi_struct_sizes"]
 
 # test hooks (rt_debug_inject)
 RT_DEBUG_SPIN_LIMIT, RT_DEBUG_PHANTOM_TASK, RT_DEBUG_PHANTOM_ITEM, RT_DEBUG_FAIL_ALLOC = 1, 2, 3, 4
@@ -65,7 +65,7 @@ class TraceParams(ctypes.Structure):
 
 class ReceiveParams(ctypes.Structure):
     _fields_ = [("delta", ctypes.c_float), ("range0", ctypes.c_float), ("max_records", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("stats_dev", ctypes.c_void_p)]
+                ("reserved", ctypes.c_int32), ("stats_dev", ctypes.c_void_p), ("delta_ray_dev", ctypes.c_void_p)]
 
 
 class TuneResult(ctypes.Structure):
@@ -88,13 +88,14 @@ class BatchDesc(ctypes.Structure):
     _fields_ = [("n_tx", ctypes.c_int32), ("tx_pos", ctypes.c_void_p), ("tx_param", ctypes.c_void_p),
                 ("dir_kind", ctypes.c_int32), ("max_order", ctypes.c_int32), ("tmax", ctypes.c_float),
                 ("n_rx", ctypes.c_int32), ("rx_pos", ctypes.c_void_p), ("use_graph", ctypes.c_int32),
-                ("ray_tile", ctypes.c_int32)]
+                ("ray_tile", ctypes.c_int32), ("receive", ctypes.c_int32), ("max_rx_records", ctypes.c_int32),
+                ("rx_delta", ctypes.c_void_p)]
 
 
 class BatchStats(ctypes.Structure):
     _fields_ = [("n_orders", ctypes.c_int32), ("rays", ctypes.c_int64 * (RT_BATCH_MAX_ORDER + 1)),
                 ("segments", ctypes.c_int64), ("total_rays", ctypes.c_int64), ("visible", ctypes.c_int64),
-                ("flagged", ctypes.c_int32)]
+                ("flagged", ctypes.c_int32), ("received", ctypes.c_int64 * (RT_BATCH_MAX_ORDER + 1))]
 
 
 class Request(ctypes.Structure):
@@ -153,6 +154,8 @@ def lib(build: bool = True):
             L.rt_batch_order.argtypes = [vp, i32, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                          ctypes.POINTER(vp)]
             L.rt_batch_visibility.argtypes = [vp, ctypes.POINTER(vp)]
+            L.rt_batch_received.argtypes = [vp, i32, ctypes.POINTER(vp), ctypes.POINTER(vp)]
+            L.rt_abi_struct_sizes.argtypes = [ctypes.POINTER(ctypes.c_int64), i32]
             L.rt_batch_destroy.argtypes = [vp]
             L.rt_session_create.argtypes = [ctypes.c_size_t, i32, ctypes.POINTER(vp)]
             L.rt_session_add_scene.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int32)]
@@ -475,7 +478,7 @@ class Batch:
     """Owns one rt_batch handle (multi-transmitter, multi-bounce pipeline)."""
 
     def __init__(self, scene, tx_pos, tx_param, kind=RT_RAYS_FIBONACCI, max_order=3, tmax=1000.0, rx_pos=None,
-                 use_graph=True, ray_tile=0):
+                 use_graph=True, ray_tile=0, receive=False, max_rx_records=1 << 16, rx_delta=None):
         self.scene = scene          # keeps the scene alive
         self.tx = np.ascontiguousarray(tx_pos, dtype=np.float32).reshape(-1, 3)
         self.param = np.ascontiguousarray(tx_param, dtype=np.int64).reshape(-1)
@@ -489,6 +492,11 @@ class Batch:
         d.rx_pos = None if self.rx is None else self.rx.ctypes.data
         d.use_graph = 1 if use_graph else 0
         d.ray_tile = int(ray_tile)
+        d.receive = 1 if receive else 0
+        d.max_rx_records = int(max_rx_records)
+        self.rx_delta = None if rx_delta is None else np.ascontiguousarray(rx_delta, dtype=np.float32).reshape(-1)
+        d.rx_delta = None if self.rx_delta is None else self.rx_delta.ctypes.data
+        self.max_rx_records = int(max_rx_records)
         h = ctypes.c_void_p()
         _check(lib().rt_batch_create(scene.handle, ctypes.byref(d), ctypes.byref(h)))
         self._h = h.value
@@ -503,7 +511,14 @@ class Batch:
         st = BatchStats()
         _check(lib().rt_batch_stats_get(self._h, _stream(stream), ctypes.byref(st)))
         return dict(rays=list(st.rays)[: st.n_orders], segments=st.segments, total_rays=st.total_rays,
-                    visible=st.visible, flagged=st.flagged)
+                    visible=st.visible, flagged=st.flagged, received=list(st.received)[: st.n_orders])
+
+    def received(self, k):
+        """(records int32 [count, 4] view (ray in order k, rx, l bits, dist bits), count) of order k."""
+        r, c = ctypes.c_void_p(), ctypes.c_void_p()
+        _check(lib().rt_batch_received(self._h, int(k), ctypes.byref(r), ctypes.byref(c)))
+        n = int(_view(c.value, (1,), "<i4").item())
+        return _view(r.value, (min(n, self.max_rx_records), 4), "<i4"), n
 
     def order(self, k):
         """(rays [n,8], hits [n,4], src [n] or None, count) for order k (views; count is a python int)."""
@@ -654,6 +669,6 @@ def rt_receive(rs: RxSet, rays, hits, delta, range0, out=None, count=None, n_dev
     cp = _dev_ptr(count, torch.int32, None, "count")
     nd = None if n_dev is None else _dev_ptr(n_dev, torch.int32, None, "n_dev")
     sp = None if stats is None else _dev_ptr(stats, torch.int64, None, "stats").value
-    p = ReceiveParams(float(delta), float(range0), int(out.shape[0]), 0, sp)
+    p = ReceiveParams(float(delta), float(range0), int(out.shape[0]), 0, sp, None)
     _check(lib().rt_receive(rs.handle, rp, hp, n, nd, ctypes.byref(p), op, cp, _stream(stream)))
     return out, count

@@ -83,3 +83,17 @@ def test_reception_entry_points_validate_without_gpu():
     p = rtbvh.ReceiveParams(0.01, 500.0, 16, 0, None)
     assert lib.rt_receive(None, None, None, 0, None, ctypes.byref(p), None, None, None) == -1
     assert b"NULL" in lib.rt_last_error()
+
+
+def test_ctypes_mirrors_match_the_header_structs():
+    # a binding struct that is shorter or longer than the library's makes the
+    # library read or write past it: every mirror must have the C size
+    import ctypes
+    lib = rtbvh.lib()
+    sizes = (ctypes.c_int64 * 12)()
+    assert lib.rt_abi_struct_sizes(sizes, 12) == 12
+    mirrors = [32, 16, rtbvh.BuildParams, rtbvh.TraceParams, rtbvh.BvhInfo, rtbvh.TuneResult, 16,
+               rtbvh.ReceiveParams, rtbvh.BatchDesc, rtbvh.BatchStats, rtbvh.Request, rtbvh.SessionStats]
+    for i, m in enumerate(mirrors):
+        want = m if isinstance(m, int) else ctypes.sizeof(m)
+        assert sizes[i] == want, (i, m, sizes[i], want)

@@ -148,3 +148,55 @@ def test_receive_full_size_sampled(rb, orc):
     hit_rays = np.unique(rec[:c, 0].cpu().numpy())
     sample = np.union1d(hit_rays[:2000], rng.choice(len(rays_np), 6000, replace=False))
     _check(orc, rec, cnt, rays_np, hits.cpu().numpy()[:, 0], rx, delta, 1 << 18, ray_subset=sample)
+
+
+def _oracle_by_delta(orc, rays_np, hit_t, rx, delta_ray):
+    # the checker takes one delta per call: group the rays by their delta
+    out_p, out_v = [], []
+    for d in np.unique(delta_ray):
+        idx = np.nonzero(delta_ray == d)[0]
+        p, v = orc.receive(rays_np[idx], hit_t[idx], rx, float(d), R0, tol=TOL)
+        p = p.copy()
+        p[:, 0] = idx[p[:, 0]]
+        out_p.append(p)
+        out_v.append(v)
+    return np.concatenate(out_p), np.concatenate(out_v)
+
+
+def test_batch_reception_every_order_matches_checker(rb, orc):
+    # four transmitters with different Fibonacci counts (so different delta:
+    # sqrt(4 pi / N)) and two reflection orders; each ray keeps its
+    # transmitter's delta through the bounces
+    sc = scenes.medium_city(seed=2)
+    s = rb.rt_scene_upload(sc.tris)
+    rb.rt_bvh_build(s, source=(500.0, 500.0, 20.0), max_leaf=4)
+    tx = np.array([[500, 500, 30], [300, 620, 12], [700, 380, 25], [450, 260, 18]], np.float32)
+    counts = np.array([20000, 8000, 30000, 12000], np.int64)
+    rx = scenes.receiver_grid(1000.0, 24, 1.5)
+    b = rb.Batch(s, tx, counts, kind=rb.RT_RAYS_FIBONACCI, max_order=2, tmax=R0, rx_pos=rx, receive=True,
+                 max_rx_records=1 << 16)
+    for _ in range(3):  # direct run, graph capture, graph replay
+        b.run()
+    torch.cuda.synchronize()
+    st = b.stats()
+    dtx = np.sqrt(4 * np.pi / counts.astype(np.float64)).astype(np.float32)
+    d_prev = np.repeat(dtx, counts)
+    total = 0
+    for k in range(3):
+        rays, hits, src, n = b.order(k)
+        rays_np = rays.cpu().numpy()
+        hit_t = hits.cpu().numpy()[:, 0]
+        d_ray = d_prev if k == 0 else d_prev[src.cpu().numpy()]
+        rec, c = b.received(k)
+        assert c == st["received"][k] and c <= 1 << 16
+        r = rec.cpu().numpy()
+        got = {(int(a), int(bb)) for a, bb in r[:, :2]}
+        assert len(got) == c
+        pairs, vals = _oracle_by_delta(orc, rays_np, hit_t, rx, d_ray)
+        sure = {(int(i), int(j)) for i, j, cl in pairs if cl == 1}
+        near = {(int(i), int(j)) for i, j, _ in pairs}
+        assert sure <= got, "order %d: missed %d" % (k, len(sure - got))
+        assert got <= near, "order %d: %d extra" % (k, len(got - near))
+        total += c
+        d_prev = d_ray
+    assert total > 50
