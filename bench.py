@@ -222,6 +222,22 @@ def run_batched(rtbvh, torch, runs):
     torch.cuda.synchronize()
     ms_b = e0.elapsed_time(e1) / runs
     st = b.stats()
+    b.destroy()
+    # the same batch with the receiving spheres (Eq. 4) of every order against the 64 x 64
+    # receivers, each transmitter with the spacing of its own launch, sqrt(4 pi / N)
+    br = rtbvh.Batch(scene, tx, counts, rtbvh.RT_RAYS_FIBONACCI, max_order=orders, tmax=tmax, rx_pos=rx,
+                     ray_tile=tile, receive=True, max_rx_records=1 << 20)
+    for _ in range(3):
+        br.run()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(runs):
+        br.run()
+    e1.record()
+    torch.cuda.synchronize()
+    ms_r = e0.elapsed_time(e1) / runs
+    st_r = br.stats()
+    br.destroy()
     # plain: the same work, one library call at a time, counts read back by the host
     seg = torch.from_numpy(scenes.segment_rays(np.repeat(tx, len(rx), 0), np.tile(rx, (len(tx), 1)))).cuda()
 
@@ -249,13 +265,15 @@ def run_batched(rtbvh, torch, runs):
         tot = plain()
     torch.cuda.synchronize()
     ms_p = 1e3 * (time.perf_counter() - t0) / max(1, runs // 2)
-    b.destroy()
     scene.destroy()
     return {"workload": "batched_city_10000_buildings_16tx_orders0-3_4096rx", "n_tri": sc.n_tri,
             "rays_per_run": st["total_rays"], "rays_per_order": st["rays"], "visible_pairs": st["visible"],
             "batched_mrays_s": st["total_rays"] / (ms_b * 1e-3) / 1e6, "batched_ms": ms_b,
             "plain_mrays_s": tot / (ms_p * 1e-3) / 1e6, "plain_ms": ms_p,
             "speedup": ms_p / ms_b, "autotuned": tune,
+            "with_reception": {"ms": ms_r, "mrays_s": st_r["total_rays"] / (ms_r * 1e-3) / 1e6,
+                               "received_per_order": st_r["received"],
+                               "overhead": ms_r / ms_b - 1.0},
             "batched": "one CUDA graph replay per run (device-side counts)",
             "plain": "per-transmitter rt_gen_rays / rt_trace_closest / rt_reflect calls, counts read by the host"}
 
