@@ -278,6 +278,89 @@ def run_batched(rtbvh, torch, runs):
             "plain": "per-transmitter rt_gen_rays / rt_trace_closest / rt_reflect calls, counts read by the host"}
 
 
+def run_large(rtbvh, torch, hbm, runs=3):
+    """The large metro (13.2M triangles, HBM-resident tree): build, the whole batch (32 x 2^21
+    direct rays + 1M visibility segments, graph-replayed) at alpha 0.7, and a trace-only
+    measurement of 4 transmitters' rays (8.4M) with counted node and triangle visits on the
+    alpha 0.7 and alpha 1 trees."""
+    from paper_2208_10008_gb300 import scenes
+    sc, tx, counts, rx = scenes.workload_large()
+    scene = rtbvh.rt_scene_upload(sc.tris)
+    src = (10_000.0, 10_000.0, 30.0)
+    tmax = 3000.0
+    st = torch.cuda.Stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rays = torch.cat([rtbvh.rt_gen_rays(rtbvh.RT_RAYS_FIBONACCI, tx[t], int(counts[t]), 0.0, tmax)
+                      for t in range(4)])
+    R = rays.shape[0]
+    hits = torch.empty((R, 4), dtype=torch.float32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    n_s = 1 << 20
+    out = {"workload": "metro_300k_prisms_13.2M_tris_32tx_x_2M_fibonacci_1M_segments", "n_tri": sc.n_tri,
+           "trace_rays": R}
+    for alpha in (1.0, 0.7):  # 0.7 last: the batch below runs on its tree
+        bp = dict(alpha=alpha, dist_norm=1, source=src, max_leaf=4, bins=16)
+        with torch.cuda.stream(st):
+            rtbvh.rt_bvh_build(scene, stream=st, **bp)
+            e0.record(st)
+            rtbvh.rt_bvh_build(scene, stream=st, **bp)
+            e1.record(st)
+        st.synchronize()
+        build_ms = e0.elapsed_time(e1)
+        info = rtbvh.rt_bvh_info(scene)
+        with torch.cuda.stream(st):
+            for _ in range(2):
+                rtbvh.rt_trace_closest(scene, rays, hits, stream=st)
+        st.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(runs)]
+        with torch.cuda.stream(st):
+            for a, c in ev:
+                flush.zero_()
+                a.record(st)
+                rtbvh.rt_trace_closest(scene, rays, hits, stream=st)
+                c.record(st)
+        st.synchronize()
+        ms_trace = statistics.mean(a.elapsed_time(c) for a, c in ev)
+        stats = torch.zeros((n_s, 2), dtype=torch.int32, device="cuda")
+        rtbvh.rt_trace_closest(scene, rays[:n_s], torch.empty((n_s, 4), dtype=torch.float32, device="cuda"),
+                               stats=stats)
+        torch.cuda.synchronize()
+        sm = stats.double().mean(0).cpu().numpy()
+        per_ray = 32 + 16 + 128 * float(sm[0]) + 48 * float(sm[1])
+        gbs = per_ray * R / (ms_trace * 1e-3) / 1e9
+        traffic, ncu_ms = NCU_TRAFFIC_LARGE[alpha]
+        out["alpha_%g" % alpha] = {
+            "build_ms": build_ms, "bvh": {k: info[k] for k in ("n_wide", "depth2", "depth_wide")},
+            "trace_ms": ms_trace, "trace_mrays_s": R / (ms_trace * 1e-3) / 1e6,
+            "hit_fraction": float((hits[:, 1].view(torch.int32) >= 0).double().mean().item()),
+            "nodes_per_ray": float(sm[0]), "tris_per_ray": float(sm[1]),
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                         "bytes_per_ray": per_ray, "kernel": "k_trace + k_retest64",
+                         "traffic": traffic, "traffic_unit": "bytes per launch",
+                         "dram_gbs_from_traffic": traffic / (ms_trace * 1e-3) / 1e9,
+                         "traffic_source": "ncu capture of k_trace<0,0,128> on these rays (%.1f ms cold)" % ncu_ms,
+                         "note": "algorithmic bytes count every node and triangle fetch; the upper tree stays "
+                                 "in L1/L2, so DRAM sees a small part of them: the walk is latency- and "
+                                 "issue-bound, not HBM-bound"}}
+    del rays, hits, flush
+    b = rtbvh.Batch(scene, tx, counts, rtbvh.RT_RAYS_FIBONACCI, max_order=0, tmax=tmax, rx_pos=rx)
+    for _ in range(3):
+        b.run()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(runs):
+        b.run()
+    e1.record()
+    torch.cuda.synchronize()
+    ms_batch = e0.elapsed_time(e1) / runs
+    stb = b.stats()
+    b.destroy()
+    scene.destroy()
+    out.update({"batch_alpha": 0.7, "batch_rays": stb["total_rays"], "batch_ms": ms_batch,
+                "batch_mrays_s": stb["total_rays"] / (ms_batch * 1e-3) / 1e6, "visible_pairs": stb["visible"]})
+    return out
+
+
 def run_reception(rtbvh, torch, scenes, rays, hits, hbm, reps=20):
     """Receiving spheres (Eq. 4) of the step's direct rays against a 64 x 64 receiver grid at
     1.5 m over the medium city: delta = the icosphere-8 spacing, range 500 m."""
@@ -404,6 +487,8 @@ def run_served(rtbvh, torch, seconds):
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # two kernels on this workload, from one ncu capture each of the current
 # kernels (max_leaf 4, 16 bins, 128-ray tile, alpha 0.7).
+NCU_TRAFFIC_LARGE = {  # k_trace<0,0,128> on 4 x 2^21 metro rays (1 ncu pass per launch)
+    0.7: (362.593280e6 + 340.041984e6, 10.5368), 1.0: (296.002816e6 + 145.577728e6, 4.6164)}
 NCU_TRAFFIC = {
     "k_split": (1.703424e6 + 1.024e3, "ncu capture of k_split, medium city (profiles/k_split_medium_city.md)"),
     "k_trace": (21.520384e6 + 0.122112e6,
@@ -596,6 +681,7 @@ def run_ours(args):
             run_trace()
         stream.synchronize()
         extra["reception"] = run_reception(rtbvh, torch, scenes, rays, hits, hbm)
+        extra["large"] = run_large(rtbvh, torch, hbm)
         extra["batched"] = run_batched(rtbvh, torch, args.batched_runs)
         extra["served"] = run_served(rtbvh, torch, args.serve_seconds)
     mean_trace_ms = statistics.mean(trace_ms)

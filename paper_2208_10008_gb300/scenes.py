@@ -384,6 +384,25 @@ def workload_batched(seed: int = 3):
     return sc, tx, counts, rx
 
 
+def workload_large(seed: int = 5):
+    """The large metro (about 13.2M triangles) with 32 transmitters, 2^21 Fibonacci rays
+    each (67M rays, range 3 km), and 1M transmitter-receiver segments (32 x 32,768
+    receivers).  Transmitters stand 10-40 m above the foot of 32 random building walls
+    (so they follow the clustered buildings); receivers are uniform over the area at
+    1.5-10 m."""
+    sc = metro_city(seed=seed)
+    rng = _rng(seed + 2000)
+    walls = rng.integers(0, sc.n_tri - 2, 32)  # the last two triangles are the ground
+    foot = sc.tris[walls].mean(axis=1)
+    tx = np.stack([foot[:, 0], foot[:, 1], rng.uniform(10.0, 40.0, 32)], 1).astype(np.float32)
+    counts = np.full(32, 1 << 21, np.int64)
+    x0, y0, x1, y1 = sc.area
+    n_rx = 32768
+    rx = np.stack([rng.uniform(x0, x1, n_rx), rng.uniform(y0, y1, n_rx), rng.uniform(1.5, 10.0, n_rx)],
+                  1).astype(np.float32)
+    return sc, tx, counts, rx
+
+
 def serving_scenes(n: int = 8, seed0: int = 101):
     """Resident scenes of 1000 .. 50000 buildings (log-spaced), generated as the
     1000-building city with other seeds; area grows with the building count."""
