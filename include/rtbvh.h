@@ -75,6 +75,11 @@ typedef struct {
   int32_t bins;     /* candidate planes per axis + 1: 4 .. 32 */
   int32_t width;    /* children per traversal node: 4 */
   int32_t dist_norm;/* 0 or 1 */
+  float range;      /* ray action range around `source` (Sec. II.B): > 0 builds over only the
+                       triangles whose box lies within range of the source (no point of a path of
+                       total length <= range is farther away, at any reflection order); 0 (or
+                       +inf): all triangles.  Rays traced against such a tree must keep their
+                       whole path within range of the source. */
 } rt_build_params;
 
 /* Trace flags */
@@ -103,6 +108,7 @@ typedef struct {
   int32_t max_leaf_size;  /* largest leaf */
   int32_t status;         /* device status word, 0 = ok */
   double build_ms;        /* device time of the last build (events) */
+  int64_t n_built;        /* triangles in the tree (n_tri unless the build had a range) */
 } rt_bvh_info_t;
 
 /* Library version (major*10000 + minor*100 + patch). */

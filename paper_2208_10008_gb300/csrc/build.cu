@@ -159,9 +159,6 @@ __device__ __forceinline__ BinU binu_record(float4 lo, float4 hi) {
         F(kFull, (x).a1, arg), F(kFull, (x).a2, arg), F(kFull, (x).b0, arg), F(kFull, (x).b1, arg),           \
         F(kFull, (x).b2, arg)                                                                                 \
   }
-__device__ __forceinline__ BinU binu_up(const BinU& x, int o) { return RT_BINU_SHFL(__shfl_up_sync, x, o); }
-__device__ __forceinline__ BinU binu_down(const BinU& x, int o) { return RT_BINU_SHFL(__shfl_down_sync, x, o); }
-__device__ __forceinline__ BinU binu_idx(const BinU& x, int l) { return RT_BINU_SHFL(__shfl_sync, x, l); }
 __device__ __forceinline__ BinU binu_xor(const BinU& x, int o) { return RT_BINU_SHFL(__shfl_xor_sync, x, o); }
 #undef RT_BINU_SHFL
 
@@ -342,17 +339,8 @@ __device__ __forceinline__ void eval_seg(const unsigned* bins0, int K, int n, in
 }
 #undef RT_BINB_SHFL
 
-// One axis (`abins`: its K bins).
-__device__ __forceinline__ void eval_axis_at(const unsigned* abins, int K, int n, int a, const CostP& cp,
-                                             Split& best) {
-  eval_seg<kBinVals, true>(abins, K, n, a, 1, cp, best);
-}
 __device__ __forceinline__ void eval_axis(const unsigned* bins, int K, int n, int a, const CostP& cp, Split& best) {
   eval_seg<kBinVals, true>(bins + a * K * kBinVals, K, n, a, 1, cp, best);
-}
-__device__ __forceinline__ void eval_axes_at(const unsigned* bins0, int K, int n, int a0, int na, const CostP& cp,
-                                             Split& best) {
-  eval_seg<kBinVals, true>(bins0, K, n, a0, na, cp, best);
 }
 __device__ __forceinline__ void eval_axes(const unsigned* bins, int K, int n, int a0, int na, const CostP& cp,
                                           Split& best) {
@@ -362,6 +350,7 @@ __device__ __forceinline__ void eval_axes(const unsigned* bins, int K, int n, in
 // ------------------------------------------------------------------ arguments
 struct BuildArgs {
   const float4* tri;  // input-order triangles
+  const int* sel;     // nullable: input ids of the triangles in this build (a range build)
   float4* rec[2];     // [2T] records (lo.xyz, id) (hi.xyz, morton); a node's range lives
                       // in one buffer, its children go to the other
   Node2* node2;
@@ -380,7 +369,8 @@ struct BuildArgs {
   float4* tri_leaf;
   int32_t* order;
   int* epoch_dev;
-  int n, K, max_leaf;
+  int n, K, max_leaf;  // n: records in this build
+  int n_all;           // triangles in the scene (input ids are below it)
   int big, chunk, rpt, cap_t, cap_c, qa_cap, top_ctas;
   int spin_limit;                    // polls without progress before a wait gives up
   int phantom_tasks, phantom_items;  // test hooks: pending work that never comes
@@ -493,6 +483,64 @@ __device__ __forceinline__ void write_node(const BuildArgs& A, int id, int paren
   A.link2[id] = make_int2(parent, epoch);
 }
 
+// ------------------------------------------------------------------ range selection
+// A build with a ray action range keeps the triangles whose box lies within
+// the range of the source (Sec. II.B): no point of a path of total length
+// <= range is farther from the source, at any reflection order.  The
+// selection keeps input order (block counts, one scan, ordered writes), so
+// the build is the same every time.  The range is widened by 1e-5 of itself
+// so that rounding never drops a reachable triangle.
+__device__ __forceinline__ bool tri_in_range(const float4* __restrict__ tri, int i, float3 s, float r2) {
+  const float4 a = __ldg(tri + 3 * (size_t)i), b = __ldg(tri + 3 * (size_t)i + 1), c = __ldg(tri + 3 * (size_t)i + 2);
+  const float dx = fmaxf(fmaxf(fminf(a.x, fminf(b.x, c.x)) - s.x, s.x - fmaxf(a.x, fmaxf(b.x, c.x))), 0.f);
+  const float dy = fmaxf(fmaxf(fminf(a.y, fminf(b.y, c.y)) - s.y, s.y - fmaxf(a.y, fmaxf(b.y, c.y))), 0.f);
+  const float dz = fmaxf(fmaxf(fminf(a.z, fminf(b.z, c.z)) - s.z, s.z - fmaxf(a.z, fmaxf(b.z, c.z))), 0.f);
+  return dx * dx + dy * dy + dz * dz <= r2;
+}
+
+__global__ void __launch_bounds__(kBlock) k_sel_count(const float4* __restrict__ tri, int n, float3 s, float r2,
+                                                      int* __restrict__ cnt) {
+  const int i = blockIdx.x * kBlock + threadIdx.x;
+  const int c = __syncthreads_count(i < n && tri_in_range(tri, i, s, r2));
+  if (threadIdx.x == 0) cnt[blockIdx.x] = c;
+}
+
+// Exclusive scan of cnt[0 .. nb) in place by one CTA; the total goes to cnt[nb].
+__global__ void __launch_bounds__(1024) k_sel_scan(int* __restrict__ cnt, int nb) {
+  __shared__ int part[1024];
+  const int t = threadIdx.x, per = (nb + 1023) / 1024, b0 = min(t * per, nb), b1 = min(b0 + per, nb);
+  int sum = 0;
+  for (int b = b0; b < b1; ++b) sum += cnt[b];
+  part[t] = sum;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    const int v = t >= o ? part[t - o] : 0;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  int run = part[t] - sum;
+  for (int b = b0; b < b1; ++b) {
+    const int v = cnt[b];
+    cnt[b] = run;
+    run += v;
+  }
+  if (t == 1023) cnt[nb] = part[1023];
+}
+
+__global__ void __launch_bounds__(kBlock) k_sel_write(const float4* __restrict__ tri, int n, float3 s, float r2,
+                                                      const int* __restrict__ off, int* __restrict__ sel) {
+  __shared__ int wc[kWarps];
+  const int i = blockIdx.x * kBlock + threadIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool f = i < n && tri_in_range(tri, i, s, r2);
+  const unsigned bal = __ballot_sync(kFull, f);
+  if (lane == 0) wc[warp] = __popc(bal);
+  __syncthreads();
+  int base = off[blockIdx.x];
+  for (int w = 0; w < warp; ++w) base += wc[w];
+  if (f) sel[base + __popc(bal & ((1u << lane) - 1u))] = i;
+}
+
 // ------------------------------------------------------------------ prep
 __global__ void __launch_bounds__(kBlock) k_prep(BuildArgs A) {
   pdl_wait();
@@ -519,10 +567,11 @@ __global__ void __launch_bounds__(kBlock) k_prep(BuildArgs A) {
     v[9 + k] = -FLT_MAX;  // centre hi
   }
   for (int i = gt; i < n; i += gs) {
-    const float4 a = A.tri[3 * (size_t)i], b = A.tri[3 * (size_t)i + 1], c = A.tri[3 * (size_t)i + 2];
+    const int t = A.sel ? __ldg(A.sel + i) : i;
+    const float4 a = A.tri[3 * (size_t)t], b = A.tri[3 * (size_t)t + 1], c = A.tri[3 * (size_t)t + 2];
     const float lx = fminf(a.x, fminf(b.x, c.x)), ly = fminf(a.y, fminf(b.y, c.y)), lz = fminf(a.z, fminf(b.z, c.z));
     const float hx = fmaxf(a.x, fmaxf(b.x, c.x)), hy = fmaxf(a.y, fmaxf(b.y, c.y)), hz = fmaxf(a.z, fmaxf(b.z, c.z));
-    A.rec[0][2 * (size_t)i] = make_float4(lx, ly, lz, __int_as_float(i));
+    A.rec[0][2 * (size_t)i] = make_float4(lx, ly, lz, __int_as_float(t));
     A.rec[0][2 * (size_t)i + 1] = make_float4(hx, hy, hz, 0.f);
     const float cx = centre(lx, hx), cy = centre(ly, hy), cz = centre(lz, hz);
     v[0] = fminf(v[0], lx);
@@ -2079,7 +2128,7 @@ __global__ void __launch_bounds__(kBlock) k_post(BuildArgs A) {
   }
   for (int i = gt; i < n; i += gs) {
     const int p = __float_as_int(__ldcg(A.rec[0] + 2 * (size_t)i).w);
-    if (p < 0 || p >= n) {
+    if (p < 0 || p >= A.n_all) {
       set_status(A.ctl, kStBadSplit, 20);
       continue;
     }
@@ -2146,12 +2195,34 @@ BuildGeom build_geometry(int64_t n, int nsm) {
 }
 
 cudaError_t launch_build(rt_scene_s* s, const rt_build_params& p, cudaStream_t st) {
-  const int n = (int)s->n_tri;
+  int n = (int)s->n_tri;
+  const int* sel = nullptr;
+  cudaError_t e;
+  if (p.range > 0.f && p.range < 3.0e38f) {
+    // the triangles within the ray action range, in input order; the build
+    // is sized for their count, which the host reads back (one small copy)
+    const int nb = (n + kBlock - 1) / kBlock;
+    if (n > 0) {
+      const float3 src = make_float3(p.source[0], p.source[1], p.source[2]);
+      const float rr = p.range * 1.00001f;
+      k_sel_count<<<nb, kBlock, 0, st>>>(s->tri_in, n, src, rr * rr, s->sel_cnt);
+      k_sel_scan<<<1, 1024, 0, st>>>(s->sel_cnt, nb);
+      k_sel_write<<<nb, kBlock, 0, st>>>(s->tri_in, n, src, rr * rr, s->sel_cnt, s->sel);
+      count_launches(3);
+      if ((e = cudaGetLastError())) return e;
+      if ((e = cudaMemcpyAsync(s->sel_host, s->sel_cnt + nb, sizeof(int), cudaMemcpyDeviceToHost, st))) return e;
+      if ((e = cudaStreamSynchronize(st))) return e;
+      n = *s->sel_host;
+    }
+    sel = s->sel;
+  }
+  s->n_built = n;
   const int nsm = sm_count();
   const BuildGeom g = build_geometry(n, nsm);
   if (g.cap_t > s->geom.cap_t || g.cap_c > s->geom.cap_c || g.qa_cap > s->geom.qa_cap) return cudaErrorInvalidValue;
   BuildArgs A;
   A.tri = s->tri_in;
+  A.sel = sel;
   A.rec[0] = s->rec[0];
   A.rec[1] = s->rec[1];
   A.node2 = s->node2;
@@ -2171,6 +2242,7 @@ cudaError_t launch_build(rt_scene_s* s, const rt_build_params& p, cudaStream_t s
   A.order = s->idx[0];
   A.epoch_dev = s->epoch;
   A.n = n;
+  A.n_all = (int)s->n_tri;
   A.K = p.bins;
   A.max_leaf = p.max_leaf;
   A.big = g.big;
@@ -2186,7 +2258,6 @@ cudaError_t launch_build(rt_scene_s* s, const rt_build_params& p, cudaStream_t s
   A.phantom_items = dh.phantom_items;
   if (A.phantom_items && !A.top_ctas) A.top_ctas = nsm;  // someone must wait for the phantom items
   A.cp = CostP{p.alpha, p.t_i, p.t_trav, p.source[0], p.source[1], p.source[2], p.dist_norm};
-  cudaError_t e;
   if ((e = cudaMemsetAsync(s->ctl, 0, sizeof(BuildCtl), st))) return e;
   const int nch = (n + g.chunk - 1) / g.chunk;
   int gp = (n + kBlock - 1) / kBlock;

@@ -211,4 +211,10 @@ struct rt_scene_s {
   cudaEvent_t split_ev[2] = {nullptr, nullptr};  // caller's events around the split kernel
   bool built = false;
   rt_build_params params{};
+  // range-limited builds: the selected triangles' ids, per-block counts, the
+  // count read back by the host
+  int* sel = nullptr;
+  int* sel_cnt = nullptr;
+  int* sel_host = nullptr;  // pinned
+  int64_t n_built = 0;      // triangles in the current tree
 };

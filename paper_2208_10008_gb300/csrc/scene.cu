@@ -82,9 +82,10 @@ void free_scene_buffers(rt_scene_s* s) {
                   s->top_scnt, s->top_item, s->top_ready, s->ctl, s->scratch.counter, s->scratch.queue, s->scratch.cand,
                   s->host_scr[0].counter, s->host_scr[0].queue, s->host_scr[0].cand,
                   s->host_scr[1].counter, s->host_scr[1].queue, s->host_scr[1].cand, s->reflect_blocks,
-                  s->stage_rays[0], s->stage_rays[1], s->stage_hits[0], s->stage_hits[1]};
+                  s->stage_rays[0], s->stage_rays[1], s->stage_hits[0], s->stage_hits[1], s->sel, s->sel_cnt};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  if (s->sel_host) cudaFreeHost(s->sel_host);
 }
 
 int sm_count_dev() {
@@ -105,7 +106,7 @@ int ensure_capacity(rt_scene_s* s, int64_t n) {
   if (r) {
     void* per_tri[] = {s->tri_in, s->idx[0], s->rec[0], s->rec[1], s->node2, s->link2, s->wide, s->tri_leaf,
                        s->qa, s->qa_ready, s->top_task, s->top_done, s->top_bins, s->top_ccnt, s->top_scnt,
-                       s->top_item, s->top_ready};
+                       s->top_item, s->top_ready, s->sel, s->sel_cnt};
     for (void* p : per_tri)
       if (p) cudaFree(p);
     s->tri_in = s->tri_leaf = nullptr;
@@ -121,6 +122,7 @@ int ensure_capacity(rt_scene_s* s, int64_t n) {
     s->top_bins = s->top_ccnt = s->top_scnt = nullptr;
     s->top_item = nullptr;
     s->top_ready = nullptr;
+    s->sel = s->sel_cnt = nullptr;
     s->cap_tri = 0;
     s->n_tri = 0;
     s->built = false;
@@ -152,6 +154,9 @@ int alloc_capacity(rt_scene_s* s, int64_t m) {
   RT_CUDA(dev_alloc(&s->top_item, (size_t)g.cap_c), "alloc top items");
   RT_CUDA(dev_alloc(&s->top_ready, (size_t)g.cap_c), "alloc top items");
   RT_CUDA(cudaMemset(s->top_ready, 0, sizeof(int) * g.cap_c), "clear top items");
+  RT_CUDA(dev_alloc(&s->sel, m), "alloc range selection");
+  RT_CUDA(dev_alloc(&s->sel_cnt, m / 256 + 2), "alloc range selection");
+  if (!s->sel_host) RT_CUDA(cudaMallocHost((void**)&s->sel_host, sizeof(int)), "alloc pinned count");
   if (!s->epoch) {
     RT_CUDA(cudaMalloc((void**)&s->epoch, sizeof(int)), "alloc epoch");
     RT_CUDA(cudaMemset(s->epoch, 0, sizeof(int)), "clear epoch");
@@ -213,6 +218,7 @@ int check_params(const rt_build_params* p) {
   if (p->bins < 4 || p->bins > rt::kMaxBins) return fail(RT_EINVAL, "bins must be 4..32");
   if (p->width != rt::kWidth) return fail(RT_EINVAL, "width must be 4");
   if (p->dist_norm != 0 && p->dist_norm != 1) return fail(RT_EINVAL, "dist_norm must be 0 or 1");
+  if (!(p->range >= 0.f)) return fail(RT_EINVAL, "range must be >= 0");
   return RT_OK;
 }
 
@@ -287,6 +293,9 @@ int rt_bvh_build(rt_scene s, const rt_build_params* p, void* stream) {
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(st, &cs);
   const bool capturing = cs != cudaStreamCaptureStatusNone;
+  const bool ranged = p->range > 0.f && p->range < 3.0e38f;
+  if (capturing && ranged)
+    return fail(RT_EINVAL, "a build with a range reads its triangle count back and cannot be captured");
   if (!capturing) RT_CUDA(cudaEventRecord(s->ev_build0, st), "record event");
   RT_CUDA(rt::launch_build(s, *p, st), "launch build");
   if (!capturing) RT_CUDA(cudaEventRecord(s->ev_build1, st), "record event");
@@ -333,6 +342,7 @@ int rt_bvh_info(rt_scene s, void* stream, rt_bvh_info_t* info) {
   rt::BuildCtl c;
   RT_CUDA(cudaMemcpy(&c, s->ctl, sizeof(c), cudaMemcpyDeviceToHost), "read control block");
   info->n_tri = s->n_tri;
+  info->n_built = s->n_built;
   info->n_bvh2_internal = c.n_internal;
   info->n_leaves = c.n_leaves;
   info->depth2 = c.depth2;
@@ -377,7 +387,8 @@ int rt_bvh_export(rt_scene s, void* stream, int32_t* child, int64_t* leaf_first,
   RT_CUDA(cudaStreamSynchronize((cudaStream_t)stream), "synchronize");
   rt::BuildCtl c;
   RT_CUDA(cudaMemcpy(&c, s->ctl, sizeof(c), cudaMemcpyDeviceToHost), "read control block");
-  const int64_t n = s->n_tri;
+  const int64_t n = s->n_built;
+  for (int64_t k = n; k < s->n_tri; ++k) prims[k] = -1;  // triangles outside a range build's tree
   std::vector<rt::Node2> nodes((size_t)(n > 0 ? n : 1));
   std::vector<int32_t> idx((size_t)(n > 0 ? n : 1));
   if (n > 0) {

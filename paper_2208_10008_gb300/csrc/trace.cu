@@ -649,7 +649,7 @@ cudaError_t launch_trace_dev(rt_scene_s* s, const rt_ray* rays, int64_t n, const
     A.node2 = s->node2;
     A.link2 = s->link2;
     A.root_ref = &s->ctl->root_ref;
-    A.n_tri = (int)s->n_tri;
+    A.n_tri = (int)s->n_built;
     A.tris = s->tri_leaf;
     A.rays = rays;
     A.n = (int)n;

@@ -55,7 +55,8 @@ class RtError(RuntimeError):
 class BuildParams(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_float), ("t_i", ctypes.c_float), ("t_trav", ctypes.c_float),
                 ("source", ctypes.c_float * 3), ("max_leaf", ctypes.c_int32),
-                ("bins", ctypes.c_int32), ("width", ctypes.c_int32), ("dist_norm", ctypes.c_int32)]
+                ("bins", ctypes.c_int32), ("width", ctypes.c_int32), ("dist_norm", ctypes.c_int32),
+                ("range", ctypes.c_float)]
 
 
 class TraceParams(ctypes.Structure):
@@ -78,7 +79,7 @@ class BvhInfo(ctypes.Structure):
     _fields_ = [("n_tri", ctypes.c_int64), ("n_bvh2_internal", ctypes.c_int64),
                 ("n_leaves", ctypes.c_int64), ("n_wide", ctypes.c_int64), ("depth2", ctypes.c_int32),
                 ("depth_wide", ctypes.c_int32), ("max_leaf_size", ctypes.c_int32),
-                ("status", ctypes.c_int32), ("build_ms", ctypes.c_double)]
+                ("status", ctypes.c_int32), ("build_ms", ctypes.c_double), ("n_built", ctypes.c_int64)]
 
 
 RT_BATCH_MAX_ORDER = 8
@@ -258,12 +259,12 @@ def rt_scene_update(scene: Scene, tris, stream=None):
 
 
 def build_params(alpha=1.0, source=(0.0, 0.0, 0.0), max_leaf=4, bins=16, width=4, dist_norm=0,
-                 t_i=1.0, t_trav=1.0) -> BuildParams:
+                 t_i=1.0, t_trav=1.0, range=0.0) -> BuildParams:
     p = BuildParams()
     p.alpha, p.t_i, p.t_trav = alpha, t_i, t_trav
-    for k in range(3):
-        p.source[k] = float(source[k])
+    p.source[0], p.source[1], p.source[2] = float(source[0]), float(source[1]), float(source[2])
     p.max_leaf, p.bins, p.width, p.dist_norm = int(max_leaf), int(bins), int(width), int(dist_norm)
+    p.range = float(range)
     return p
 
 

@@ -97,3 +97,10 @@ def test_ctypes_mirrors_match_the_header_structs():
     for i, m in enumerate(mirrors):
         want = m if isinstance(m, int) else ctypes.sizeof(m)
         assert sizes[i] == want, (i, m, sizes[i], want)
+
+
+def test_build_params_marshalling_without_gpu():
+    p = rtbvh.build_params(alpha=0.7, source=(1.0, 2.0, 3.0), max_leaf=6, bins=8, dist_norm=1, range=250.0)
+    assert abs(p.alpha - 0.7) < 1e-7 and list(p.source) == [1.0, 2.0, 3.0]
+    assert (p.max_leaf, p.bins, p.width, p.dist_norm) == (6, 8, 4, 1) and p.range == 250.0
+    assert rtbvh.build_params().range == 0.0

@@ -603,3 +603,36 @@ def test_receive_matches_cross_product_formula(orc):
         want |= {(i, int(j)) for j in np.nonzero(ok)[0]}
     assert len(want) > 20
     assert sure <= want <= near
+
+
+# --------------------------------------------------------------- ray action range (Sec. II.B)
+def _box_dist(tris, s):
+    lo = tris.min(axis=1).astype(np.float64)
+    hi = tris.max(axis=1).astype(np.float64)
+    d = np.maximum(np.maximum(lo - s, s - hi), 0.0)
+    return np.sqrt((d * d).sum(1))
+
+
+def test_range_pruning_keeps_every_triangle_a_bounce_chain_hits(orc):
+    # a path of total length <= R never reaches a point farther than R from
+    # its source (triangle inequality), so pruning the triangles whose box is
+    # farther than R drops no hit at any order: check on bounce chains
+    sc = scenes.medium_city(seed=2)
+    src = np.array(sc.tx[0], np.float64)
+    R = 180.0
+    rays = scenes.make_rays(src, scenes.fibonacci_directions(3000), 0.0, R)
+    skip = None
+    dist = _box_dist(sc.tris, src)
+    hit_any = 0
+    for order in range(3):
+        h = orc.closest_brute(sc.tris, rays, skip=skip)
+        ok = h.id >= 0
+        hit_any += ok.sum()
+        assert (dist[h.id[ok]] <= R * (1 + 1e-9)).all()
+        nxt = orc.reflect(sc.tris, rays, h.id, h.t)
+        keep = ok & (nxt[:, 7] > 0)
+        rays = nxt[keep].astype(np.float32)
+        skip = h.id[keep]
+        if len(rays) == 0:
+            break
+    assert hit_any > 1000
