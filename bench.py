@@ -342,7 +342,50 @@ def run_large(rtbvh, torch, hbm, runs=3):
                          "note": "algorithmic bytes count every node and triangle fetch; the upper tree stays "
                                  "in L1/L2, so DRAM sees a small part of them: the walk is latency- and "
                                  "issue-bound, not HBM-bound"}}
+    # a tree per transmitter (NEXT-2): source = the transmitter, pruned to its ray action
+    # range; the paper's one-transmitter comparison of the traditional and improved trees
+    per_tx = {}
+    n_tx = 4
+    for alpha in (1.0, 0.7, 0.4):
+        bms, tms, nb, vis = [], [], [], [0.0, 0.0]
+        for t in range(n_tx):
+            lo, hi = int(counts[:t].sum()), int(counts[: t + 1].sum())
+            rt_, ht_ = rays[lo:hi], hits[lo:hi]
+            bp = dict(alpha=alpha, dist_norm=1, source=tuple(float(v) for v in tx[t]), max_leaf=4, bins=16,
+                      range=tmax)
+            rtbvh.rt_bvh_build(scene, stream=st, **bp)
+            st.synchronize()
+            t0 = time.perf_counter()
+            rtbvh.rt_bvh_build(scene, stream=st, **bp)
+            st.synchronize()
+            bms.append(1e3 * (time.perf_counter() - t0))  # host clock: the build reads its count back
+            nb.append(rtbvh.rt_bvh_info(scene)["n_built"])
+            with torch.cuda.stream(st):
+                rtbvh.rt_trace_closest(scene, rt_, ht_, stream=st)
+                flush.zero_()
+                e0.record(st)
+                rtbvh.rt_trace_closest(scene, rt_, ht_, stream=st)
+                e1.record(st)
+            st.synchronize()
+            tms.append(e0.elapsed_time(e1))
+            sts = torch.zeros((n_s // 4, 2), dtype=torch.int32, device="cuda")
+            rtbvh.rt_trace_closest(scene, rt_[: n_s // 4],
+                                   torch.empty((n_s // 4, 4), dtype=torch.float32, device="cuda"), stats=sts)
+            torch.cuda.synchronize()
+            m = sts.double().mean(0).cpu().numpy()
+            vis[0] += float(m[0]) / n_tx
+            vis[1] += float(m[1]) / n_tx
+        per_tx["alpha_%g" % alpha] = {"build_ms": statistics.mean(bms), "triangles_in_tree": statistics.mean(nb),
+                                      "trace_ms_per_tx": statistics.mean(tms),
+                                      "trace_mrays_s": float(counts[:n_tx].sum()) / (sum(tms) * 1e-3) / 1e6,
+                                      "nodes_per_ray": vis[0], "tris_per_ray": vis[1]}
+    t1 = per_tx["alpha_1"]["trace_ms_per_tx"]
+    for k, v in per_tx.items():
+        v["trace_speedup_vs_alpha1"] = t1 / v["trace_ms_per_tx"]
+    out["tree_per_transmitter"] = dict(per_tx, transmitters=n_tx, range_m=tmax,
+                                       note="build timed on the host clock (it reads its triangle count back)")
     del rays, hits, flush
+    rtbvh.rt_bvh_build(scene, alpha=0.7, dist_norm=1, source=src, max_leaf=4, bins=16)
     b = rtbvh.Batch(scene, tx, counts, rtbvh.RT_RAYS_FIBONACCI, max_order=0, tmax=tmax, rx_pos=rx)
     for _ in range(3):
         b.run()

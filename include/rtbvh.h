@@ -179,13 +179,15 @@ typedef struct {
  * for max_leaf in {2, 4, 6, 8} x bins in {8, 16, 32} x ray tile in {64,
  * 128, 256}, build the scene's BVH from `base` (alpha, t_i, t_trav, source,
  * dist_norm kept) and time the closest-hit walk of the n_rays sample rays
- * (device pointer), each timing the best of 3 with CUDA events; pick the
+ * (device pointer), each timing the median of 5 CUDA-event timings, each
+ * after an untimed 256 MB write that evicts the L2 (cold-cache ranking); pick the
  * lowest build_weight * build_ms + trace_ms (build_weight = builds per
  * traced sample: 1 when the scene is rebuilt for every batch, 0 when it is
  * built once and traced many times).  Every configuration gives the same
  * hits (the hit rule does not depend on the tree).  On return the scene
  * holds the BVH built with the choice.  Synchronous.  Allocates and frees
- * one n_rays hit buffer.  Errors: RT_EINVAL (NULL arguments, n_rays < 1,
+ * one n_rays hit buffer and the 256 MB eviction buffer (without it, when it
+ * cannot be had, the timings are warm-cache).  Errors: RT_EINVAL (NULL arguments, n_rays < 1,
  * build_weight < 0, bad base params), RT_ENOMEM, RT_ECUDA. */
 int rt_autotune(rt_scene scene, const rt_build_params* base, const rt_ray* rays_dev, int64_t n_rays,
                 float build_weight, rt_tune_result* out, void* stream);

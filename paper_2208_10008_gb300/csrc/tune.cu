@@ -3,10 +3,12 @@
 // The knobs are the ones that trade build time against walk time without
 // changing any hit: the leaf size, the number of bins per axis and the ray
 // tile (rays per CTA) of the float32 walk.  Every configuration is built
-// and timed with CUDA events on the caller's stream (best of 3), and the
-// scene is left built with the winner.
+// and timed with CUDA events on the caller's stream (median of 5, L2 flushed
+// before each timing by a 256 MB write, so that the ranking is the one of
+// cold-cache steps), and the scene is left built with the winner.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cfloat>
 #include <climits>
 
@@ -26,20 +28,25 @@ struct Events {
   }
 };
 
-// Device time of `fn` (enqueueing on st), best of `reps`; negative on failure.
+constexpr int kTuneReps = 5;
+constexpr size_t kFlushBytes = size_t(256) << 20;  // twice the L2
+
+// Device time of `fn` (enqueueing on st), median of kTuneReps, each after
+// an untimed write of `flush` (nullable) that evicts the L2; negative on
+// failure.
 template <class F>
-float best_ms(cudaStream_t st, const Events& ev, int reps, F fn, int* err) {
-  float best = FLT_MAX;
-  for (int r = 0; r < reps; ++r) {
+float median_ms(cudaStream_t st, const Events& ev, void* flush, F fn, int* err) {
+  float t[kTuneReps];
+  for (int r = 0; r < kTuneReps; ++r) {
+    if (flush && cudaMemsetAsync(flush, r, kFlushBytes, st) != cudaSuccess) return -1.f;
     if (cudaEventRecord(ev.e[0], st) != cudaSuccess) return -1.f;
     *err = fn();
     if (*err) return -1.f;
     if (cudaEventRecord(ev.e[1], st) != cudaSuccess || cudaEventSynchronize(ev.e[1]) != cudaSuccess) return -1.f;
-    float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, ev.e[0], ev.e[1]) != cudaSuccess) return -1.f;
-    best = ms < best ? ms : best;
+    if (cudaEventElapsedTime(&t[r], ev.e[0], ev.e[1]) != cudaSuccess) return -1.f;
   }
-  return best;
+  std::sort(t, t + kTuneReps);
+  return t[kTuneReps / 2];
 }
 
 }  // namespace
@@ -59,6 +66,11 @@ extern "C" int rt_autotune(rt_scene s, const rt_build_params* base, const rt_ray
     cudaGetLastError();
     return rt::set_error(RT_ENOMEM, "hit buffer");
   }
+  void* flush = nullptr;  // without it (no memory) the timings are warm-cache
+  if (cudaMalloc(&flush, kFlushBytes) != cudaSuccess) {
+    cudaGetLastError();
+    flush = nullptr;
+  }
   const int leaves[] = {2, 4, 6, 8}, binsv[] = {8, 16, 32}, tiles[] = {64, 128, 256};
   rt_tune_result best{};
   best.score_ms = FLT_MAX;
@@ -71,14 +83,15 @@ extern "C" int rt_autotune(rt_scene s, const rt_build_params* base, const rt_ray
       p.bins = bn;
       err = rt_bvh_build(s, &p, stream);  // warm: the first build sizes the scene's buffers
       if (err) goto done;
-      const float tb = best_ms(st, ev, 3, [&] { return rt_bvh_build(s, &p, stream); }, &err);
+      const float tb = median_ms(st, ev, flush, [&] { return rt_bvh_build(s, &p, stream); }, &err);
       if (tb < 0.f) goto fail_cuda;
       for (int tile : tiles) {
         rt_trace_params tp{};
         tp.block = tile;
         err = rt_trace_closest(s, rays, n, hits, &tp, stream);
         if (err) goto done;
-        const float tt = best_ms(st, ev, 3, [&] { return rt_trace_closest(s, rays, n, hits, &tp, stream); }, &err);
+        const float tt =
+            median_ms(st, ev, flush, [&] { return rt_trace_closest(s, rays, n, hits, &tp, stream); }, &err);
         if (tt < 0.f) goto fail_cuda;
         const float score = build_weight * tb + tt;
         ++tried;
@@ -106,9 +119,11 @@ extern "C" int rt_autotune(rt_scene s, const rt_build_params* base, const rt_ray
   *out = best;
 done:
   cudaFree(hits);
+  if (flush) cudaFree(flush);
   return err;
 fail_cuda:
   cudaFree(hits);
+  if (flush) cudaFree(flush);
   if (err) return err;
   return rt::set_error(RT_ECUDA, "timing failed");
 }
