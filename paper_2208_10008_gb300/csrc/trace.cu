@@ -46,6 +46,7 @@ constexpr int kCand = kTraceCand;      // float64 candidates remembered per ray
 struct RayPre {
   float ox, oy, oz, tmin, tmax;
   float ix, iy, iz;  // 1/d
+  int sx, sy, sz;    // 1 when the axis runs negative: the near plane is the box's hi
   float Sx, Sy, Sz;  // shear constants of the watertight test
   int kx, ky, kz;
   bool valid;
@@ -69,6 +70,9 @@ __device__ __forceinline__ RayPre setup_ray(float4 a, float4 b) {
   r.ix = __frcp_rn(dx);
   r.iy = __frcp_rn(dy);
   r.iz = __frcp_rn(dz);
+  r.sx = r.ix >= 0.f ? 0 : 1;
+  r.sy = r.iy >= 0.f ? 0 : 1;
+  r.sz = r.iz >= 0.f ? 0 : 1;
   float ax = fabsf(dx), ay = fabsf(dy), az = fabsf(dz);
   int kz = (ax >= ay && ax >= az) ? 0 : (ay >= az ? 1 : 2);
   int kx = kz == 2 ? 0 : kz + 1;
@@ -207,14 +211,14 @@ __device__ float refine_t(const RayPre& r, float dx, float dy, float dz, float4 
 // whose widened interval meets [tmin, bound], near distances in tn[].
 __device__ __forceinline__ unsigned slab4(const WNode* __restrict__ node, const RayPre& r, float bound,
                                           float tn[4], int4* child) {
+  // planes lo x, hi x, lo y, hi y, lo z, hi z: the ray's near and far ones
+  // are loaded directly (per-ray offsets), no selects
   const float4* p = reinterpret_cast<const float4*>(node);
-  float4 lox = __ldg(p + 0), hix = __ldg(p + 1), loy = __ldg(p + 2), hiy = __ldg(p + 3);
-  float4 loz = __ldg(p + 4), hiz = __ldg(p + 5);
+  const float4 nx = __ldg(p + r.sx), fx = __ldg(p + 1 - r.sx);
+  const float4 ny = __ldg(p + 2 + r.sy), fy = __ldg(p + 3 - r.sy);
+  const float4 nz = __ldg(p + 4 + r.sz), fz = __ldg(p + 5 - r.sz);
   int4 ch = __ldg(reinterpret_cast<const int4*>(p + 6));
   *child = ch;
-  float4 nx = r.ix >= 0.f ? lox : hix, fx = r.ix >= 0.f ? hix : lox;
-  float4 ny = r.iy >= 0.f ? loy : hiy, fy = r.iy >= 0.f ? hiy : loy;
-  float4 nz = r.iz >= 0.f ? loz : hiz, fz = r.iz >= 0.f ? hiz : loz;
   float nxa[4] = {nx.x, nx.y, nx.z, nx.w}, fxa[4] = {fx.x, fx.y, fx.z, fx.w};
   float nya[4] = {ny.x, ny.y, ny.z, ny.w}, fya[4] = {fy.x, fy.y, fy.z, fy.w};
   float nza[4] = {nz.x, nz.y, nz.z, nz.w}, fza[4] = {fz.x, fz.y, fz.z, fz.w};
