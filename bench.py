@@ -533,8 +533,8 @@ def run_served(rtbvh, torch, seconds):
 NCU_TRAFFIC_LARGE = {  # k_trace<0,0,128> on 4 x 2^21 metro rays (1 ncu pass per launch)
     0.7: (362.593280e6 + 340.041984e6, 10.5368), 1.0: (296.002816e6 + 145.577728e6, 4.6164)}
 NCU_TRAFFIC = {
-    "k_split": (1.703424e6 + 1.024e3, "ncu capture of k_split, medium city (profiles/k_split_medium_city.md)"),
-    "k_trace": (21.520384e6 + 0.122112e6,
+    "k_split": (1.694720e6 + 256.0, "ncu capture of k_split, medium city (profiles/k_split_medium_city.md)"),
+    "k_trace": (21.492224e6 + 0.0576e6,
                 "ncu capture of k_trace<0,0,128> (k_retest64 not included), medium city "
                 "(profiles/k_trace_medium_city.md)"),
 }

@@ -857,23 +857,31 @@ __device__ void top_chunk(const BuildArgs& A, TopSmem& S, const TopTask& T, int 
     scl[a] = bin_scale(T.clo[a], T.chi[a], K);
   }
   __syncthreads();
-  // Eq. 2 at every plane: every warp evaluates axis warp mod 3 (no branch on
-  // the warp index around the shuffles: inside one, they run an order of
-  // magnitude slower); warps 0..2 publish.  An axis without extent has all
-  // records in bin 0 and yields no candidate.
-  {
-    Split sp;
-    split_none(sp);
-    eval_axis(S.pbins, K, n, warp % 3, A.cp, sp);
-    if (lane == 0 && warp < 3) S.ax[warp] = sp;
-  }
-  __syncthreads();
-  Split best = S.ax[0];
+  // Eq. 2 at every plane.  Up to 10 bins every warp evaluates all three axes
+  // in one pass and reaches the same split; otherwise every warp evaluates
+  // axis warp mod 3 (no branch on the warp index around the shuffles:
+  // inside one, they run an order of magnitude slower) and warps 0..2
+  // publish.  An axis without extent has all records in bin 0 and yields
+  // no candidate.
+  Split best;
+  split_none(best);
+  if (3 * K <= 32) {
+    eval_axes(S.pbins, K, n, 0, 3, A.cp, best);
+  } else {
+    {
+      Split sp;
+      split_none(sp);
+      eval_axis(S.pbins, K, n, warp % 3, A.cp, sp);
+      if (lane == 0 && warp < 3) S.ax[warp] = sp;
+    }
+    __syncthreads();
+    best = S.ax[0];
 #pragma unroll
-  for (int a = 1; a < 3; ++a) {
-    const float ca = S.ax[a].cost;
-    const int ka = S.ax[a].cand;
-    if (ka != INT_MAX && (ca < best.cost || (ca == best.cost && ka < best.cand))) best = S.ax[a];
+    for (int a = 1; a < 3; ++a) {
+      const float ca = S.ax[a].cost;
+      const int ka = S.ax[a].cand;
+      if (ka != INT_MAX && (ca < best.cost || (ca == best.cost && ka < best.cand))) best = S.ax[a];
+    }
   }
   int axis, plane, nl;
   BinU cu0, cu1;
