@@ -299,7 +299,7 @@ def run_large(rtbvh, torch, hbm, runs=3):
     out = {"workload": "metro_300k_prisms_13.2M_tris_32tx_x_2M_fibonacci_1M_segments", "n_tri": sc.n_tri,
            "trace_rays": R}
     for alpha in (1.0, 0.7):  # 0.7 last: the batch below runs on its tree
-        bp = dict(alpha=alpha, dist_norm=1, source=src, max_leaf=4, bins=16)
+        bp = dict(alpha=alpha, dist_norm=1, source=src, max_leaf=4, bins=16, quantize=1)
         with torch.cuda.stream(st):
             rtbvh.rt_bvh_build(scene, stream=st, **bp)
             e0.record(st)
@@ -321,6 +321,15 @@ def run_large(rtbvh, torch, hbm, runs=3):
                 c.record(st)
         st.synchronize()
         ms_trace = statistics.mean(a.elapsed_time(c) for a, c in ev)
+        evq = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(runs)]
+        with torch.cuda.stream(st):
+            for a, c in evq:
+                flush.zero_()
+                a.record(st)
+                rtbvh.rt_trace_closest(scene, rays, hits, flags=rtbvh.RT_QUANTIZED_NODES, stream=st)
+                c.record(st)
+        st.synchronize()
+        ms_quant = statistics.mean(a.elapsed_time(c) for a, c in evq)
         stats = torch.zeros((n_s, 2), dtype=torch.int32, device="cuda")
         rtbvh.rt_trace_closest(scene, rays[:n_s], torch.empty((n_s, 4), dtype=torch.float32, device="cuda"),
                                stats=stats)
@@ -332,6 +341,7 @@ def run_large(rtbvh, torch, hbm, runs=3):
         out["alpha_%g" % alpha] = {
             "build_ms": build_ms, "bvh": {k: info[k] for k in ("n_wide", "depth2", "depth_wide")},
             "trace_ms": ms_trace, "trace_mrays_s": R / (ms_trace * 1e-3) / 1e6,
+            "trace_ms_quantised_nodes": ms_quant,
             "hit_fraction": float((hits[:, 1].view(torch.int32) >= 0).double().mean().item()),
             "nodes_per_ray": float(sm[0]), "tris_per_ray": float(sm[1]),
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
@@ -444,6 +454,30 @@ def run_reception(rtbvh, torch, scenes, rays, hits, hbm, reps=20):
             "mrays_s": R / (ms * 1e-3) / 1e6, "cells_per_ray": cells / R, "entries_per_ray": entries / R,
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
                          "bytes_per_ray": per_ray, "kernel": "k_receive"}}
+
+
+def run_quantised(rtbvh, torch, scene, rays, bp, tile, reps=10):
+    """The step's walk on the 64-byte quantised nodes against the 128-byte float nodes (same
+    tree, same rays; the hits are identical)."""
+    rtbvh.rt_bvh_build(scene, **bp)
+    hits = torch.empty((rays.shape[0], 4), dtype=torch.float32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    out = {}
+    for name, kw in (("float_nodes_128B", dict(block=tile)), ("quantised_nodes_64B",
+                                                              dict(flags=rtbvh.RT_QUANTIZED_NODES))):
+        for _ in range(3):
+            rtbvh.rt_trace_closest(scene, rays, hits, **kw)
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            rtbvh.rt_trace_closest(scene, rays, hits, **kw)
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        out[name + "_ms"] = statistics.median(ts)
+    return out
 
 
 def run_alpha_sweep(rtbvh, torch, sc, rays, source, reps=10):
@@ -720,6 +754,7 @@ def run_ours(args):
     extra = {}
     if not args.no_extra:
         extra["alpha_sweep"] = run_alpha_sweep(rtbvh, torch, sc, rays, p["source"])
+        extra["quantised_nodes"] = run_quantised(rtbvh, torch, scene, rays, dict(bp, quantize=1), tile)
         with torch.cuda.stream(stream):
             run_trace()
         stream.synchronize()

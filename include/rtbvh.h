@@ -80,11 +80,16 @@ typedef struct {
                        total length <= range is farther away, at any reflection order); 0 (or
                        +inf): all triangles.  Rays traced against such a tree must keep their
                        whole path within range of the source. */
+  int32_t quantize; /* 1: also write the 64-byte traversal nodes (children's planes as bytes
+                       on a per-axis power-of-two grid, rounded outward) that
+                       RT_QUANTIZED_NODES walks; 0: only the 128-byte float nodes */
 } rt_build_params;
 
 /* Trace flags */
 #define RT_NO_FP64_RETEST 1u /* skip the float64 re-test of flagged rays (diagnostics) */
 #define RT_COUNT_STATS 2u    /* count nodes visited / triangles tested per ray */
+#define RT_QUANTIZED_NODES 4u /* walk the 64-byte quantised nodes (the scene's last build had
+                                 quantize = 1); the same hits, half the node bytes */
 
 typedef struct {
   uint32_t flags;

@@ -366,6 +366,7 @@ struct BuildArgs {
   int2* titem;  // chunk items of big nodes
   int* tready;
   WNode* wide;
+  QNode* qwide;  // nullable: also write the 64-byte nodes
   float4* tri_leaf;
   int32_t* order;
   int* epoch_dev;
@@ -2041,6 +2042,84 @@ __device__ __forceinline__ bool ref_ok(const BuildArgs& A, int ref, int epoch) {
 // The 4-wide node rooted at binary node x: open the internal child of
 // largest surface area until there are 4 children (the first of equal areas
 // wins; the opened node's children take its slot and the next free one).
+// The 64-byte form of wide node w: per axis the grid origin is the union
+// box's lower corner and the step 2^e the smallest with 255 steps covering
+// its extent; each lower plane takes the largest byte whose decoded value is
+// not above it, each upper plane the smallest not below it (checked with
+// qplane itself, so the decoded box contains the exact one); when 255 steps
+// fall short after rounding, e grows.
+__device__ QNode quantize_node(const WNode& w) {
+  const float lo[3][4] = {{w.lox.x, w.lox.y, w.lox.z, w.lox.w}, {w.loy.x, w.loy.y, w.loy.z, w.loy.w},
+                          {w.loz.x, w.loz.y, w.loz.z, w.loz.w}};
+  const float hi[3][4] = {{w.hix.x, w.hix.y, w.hix.z, w.hix.w}, {w.hiy.x, w.hiy.y, w.hiy.z, w.hiy.w},
+                          {w.hiz.x, w.hiz.y, w.hiz.z, w.hiz.w}};
+  const int ch[4] = {w.child.x, w.child.y, w.child.z, w.child.w};
+  QNode q;
+  float org[3];
+  unsigned wlo[3], whi[3];
+  int exps = 0;
+  for (int a = 0; a < 3; ++a) {
+    float ulo = INFINITY, uhi = -INFINITY;
+    for (int i = 0; i < 4; ++i)
+      if (ch[i] != INT_MIN) {
+        ulo = fminf(ulo, lo[a][i]);
+        uhi = fmaxf(uhi, hi[a][i]);
+      }
+    if (!(ulo <= uhi)) {  // no child
+      ulo = 0.f;
+      uhi = 0.f;
+    }
+    int e = -126;
+    const float ext = uhi - ulo;
+    if (ext > 0.f) {
+      int k;
+      frexpf(ext * (1.f / 255.f), &k);  // ext / 255 < 2^k
+      e = max(-126, min(127, k));
+    }
+    unsigned bl = 0, bh = 0;
+    for (int attempt = 0; attempt < 8; ++attempt) {
+      const float s = qscale(e);
+      bool ok = true;
+      bl = bh = 0;
+      for (int i = 0; i < 4; ++i) {
+        unsigned ql = 255, qh = 0;  // empty slot: an empty decoded box
+        if (ch[i] != INT_MIN) {
+          int l = (int)floorf((lo[a][i] - ulo) / s), h = (int)ceilf((hi[a][i] - ulo) / s);
+          l = max(0, min(255, l));
+          h = max(0, min(255, h));
+          while (l > 0 && qplane((unsigned)l, s, ulo) > lo[a][i]) --l;
+          while (h < 255 && qplane((unsigned)h, s, ulo) < hi[a][i]) ++h;
+          ok = ok && qplane((unsigned)l, s, ulo) <= lo[a][i] && qplane((unsigned)h, s, ulo) >= hi[a][i];
+          ql = (unsigned)l;
+          qh = (unsigned)h;
+        }
+        bl |= ql << (8 * i);
+        bh |= qh << (8 * i);
+      }
+      if (ok || e >= 127) break;
+      ++e;
+    }
+    org[a] = ulo;
+    wlo[a] = bl;
+    whi[a] = bh;
+    exps |= (e + 128) << (8 * a);
+  }
+  q.ox = org[0];
+  q.oy = org[1];
+  q.oz = org[2];
+  q.exps = exps;
+  q.lox = wlo[0];
+  q.hix = whi[0];
+  q.loy = wlo[1];
+  q.hiy = whi[1];
+  q.loz = wlo[2];
+  q.hiz = whi[2];
+  q.parent = w.meta.x;
+  q.pad = 0;
+  q.child = w.child;
+  return q;
+}
+
 __device__ void make_wide(const BuildArgs& A, int x, int epoch) {
   int ref[kWidth];
   float3 lo[kWidth], hi[kWidth];
@@ -2102,6 +2181,7 @@ __device__ void make_wide(const BuildArgs& A, int x, int epoch) {
   w.child = make_int4(ch[0], ch[1], ch[2], ch[3]);
   w.meta = make_int4(__ldcg(&A.link2[x]).x, 0, 0, 0);
   A.wide[x] = w;
+  if (A.qwide) A.qwide[x] = quantize_node(w);
 }
 
 __global__ void __launch_bounds__(kBlock) k_post(BuildArgs A) {
@@ -2131,6 +2211,7 @@ __global__ void __launch_bounds__(kBlock) k_post(BuildArgs A) {
       }
       w.meta = make_int4(-1, 0, 0, 0);
       A.wide[0] = w;
+      if (A.qwide) A.qwide[0] = quantize_node(w);
       A.ctl->wide_root = 0;
     }
   }
@@ -2246,6 +2327,7 @@ cudaError_t launch_build(rt_scene_s* s, const rt_build_params& p, cudaStream_t s
   A.titem = s->top_item;
   A.tready = s->top_ready;
   A.wide = s->wide;
+  A.qwide = p.quantize ? s->qwide : nullptr;
   A.tri_leaf = s->tri_leaf;
   A.order = s->idx[0];
   A.epoch_dev = s->epoch;

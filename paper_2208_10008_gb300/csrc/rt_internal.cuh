@@ -62,6 +62,30 @@ struct __align__(16) WNode {
 };
 static_assert(sizeof(WNode) == 128, "wide node must be one 128-byte line");
 
+// The same 4-wide node in 64 bytes: the children's planes as bytes on a
+// per-axis grid of step 2^e from the union box's lower corner (origin).
+// A plane decodes as qplane(q, e, origin); a child's decoded box contains its
+// exact box (lower planes rounded down, upper ones up, checked with the
+// decoding itself when the node is written), so a slab test on the decoded
+// planes is conservative.  Empty slots have child ref INT_MIN.
+struct __align__(16) QNode {
+  float ox, oy, oz;
+  int exps;              // (e_x + 128) | (e_y + 128) << 8 | (e_z + 128) << 16
+  unsigned lox, hix, loy, hiy;  // byte i: child i's plane
+  unsigned loz, hiz;
+  int parent, pad;
+  int4 child;
+};
+static_assert(sizeof(QNode) == 64, "quantised node must be 64 bytes");
+
+// 2^e for e in [-126, 127] (a normal float, exact).
+__device__ __forceinline__ float qscale(int e) { return __int_as_float((e + 127) << 23); }
+// The value of byte q of a plane on the grid (origin, 2^e); q * 2^e is
+// exact, so the one rounding is the fused add.
+__device__ __forceinline__ float qplane(unsigned q, float scale, float origin) {
+  return __fmaf_rn(__int_as_float(0x4B000000u | q) - 8388608.f, scale, origin);
+}
+
 struct __align__(16) Task {
   int32_t begin, count, parent, side;  // parent: node2 id (-1 root); side 0/1
   float clo[3];                        // centroid bounds of the task's triangles
@@ -185,6 +209,9 @@ struct rt_scene_s {
   float4* rec[2] = {nullptr, nullptr};   // primitive records (2 float4 each), ping-pong
   rt::Node2* node2 = nullptr;
   rt::WNode* wide = nullptr;
+  rt::QNode* qwide = nullptr;   // 64-byte nodes (builds with quantize = 1)
+  int64_t qwide_cap = 0;
+  bool q_built = false;         // the current tree has its 64-byte nodes
   int2* link2 = nullptr;        // (parent, epoch) per binary node
   int* epoch = nullptr;         // build counter on the device
   float4* tri_leaf = nullptr;

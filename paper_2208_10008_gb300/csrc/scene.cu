@@ -82,7 +82,8 @@ void free_scene_buffers(rt_scene_s* s) {
                   s->top_scnt, s->top_item, s->top_ready, s->ctl, s->scratch.counter, s->scratch.queue, s->scratch.cand,
                   s->host_scr[0].counter, s->host_scr[0].queue, s->host_scr[0].cand,
                   s->host_scr[1].counter, s->host_scr[1].queue, s->host_scr[1].cand, s->reflect_blocks,
-                  s->stage_rays[0], s->stage_rays[1], s->stage_hits[0], s->stage_hits[1], s->sel, s->sel_cnt};
+                  s->stage_rays[0], s->stage_rays[1], s->stage_hits[0], s->stage_hits[1], s->sel, s->sel_cnt,
+                  s->qwide};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (s->sel_host) cudaFreeHost(s->sel_host);
@@ -219,6 +220,7 @@ int check_params(const rt_build_params* p) {
   if (p->width != rt::kWidth) return fail(RT_EINVAL, "width must be 4");
   if (p->dist_norm != 0 && p->dist_norm != 1) return fail(RT_EINVAL, "dist_norm must be 0 or 1");
   if (!(p->range >= 0.f)) return fail(RT_EINVAL, "range must be >= 0");
+  if (p->quantize != 0 && p->quantize != 1) return fail(RT_EINVAL, "quantize must be 0 or 1");
   return RT_OK;
 }
 
@@ -296,8 +298,18 @@ int rt_bvh_build(rt_scene s, const rt_build_params* p, void* stream) {
   const bool ranged = p->range > 0.f && p->range < 3.0e38f;
   if (capturing && ranged)
     return fail(RT_EINVAL, "a build with a range reads its triangle count back and cannot be captured");
+  if (p->quantize && s->qwide_cap < s->cap_tri + 1) {  // the 64-byte nodes, on first use
+    if (capturing) return fail(RT_EINVAL, "the first build with quantize = 1 allocates and cannot be captured");
+    if (s->qwide) cudaFree(s->qwide);
+    s->qwide = nullptr;
+    s->qwide_cap = 0;
+    RT_CUDA(dev_alloc(&s->qwide, s->cap_tri + 1), "alloc quantised nodes");
+    s->qwide_cap = s->cap_tri + 1;
+  }
+  s->q_built = false;
   if (!capturing) RT_CUDA(cudaEventRecord(s->ev_build0, st), "record event");
   RT_CUDA(rt::launch_build(s, *p, st), "launch build");
+  s->q_built = p->quantize != 0;
   if (!capturing) RT_CUDA(cudaEventRecord(s->ev_build1, st), "record event");
   s->params = *p;
   s->built = true;
@@ -448,6 +460,8 @@ static int trace_common(rt_scene s, const rt_ray* rays, int64_t n, rt_hit* hits,
   if (((uintptr_t)rays & 15) || ((uintptr_t)hits & 15)) return fail(RT_EINVAL, "rays/hits must be 16-byte aligned");
   if (params && params->block != 0 && params->block != 64 && params->block != 128 && params->block != 256)
     return fail(RT_EINVAL, "block must be 0, 64, 128 or 256");
+  if (params && (params->flags & RT_QUANTIZED_NODES) && !s->q_built)
+    return fail(RT_EINVAL, "RT_QUANTIZED_NODES needs a build with quantize = 1");
   if (!s->built) return fail(RT_ENOTBUILT, "BVH not built");
   int r = ensure_scratch(s->scratch, n);
   if (r) return r;

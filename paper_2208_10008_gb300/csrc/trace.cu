@@ -237,6 +237,45 @@ __device__ __forceinline__ unsigned slab4(const WNode* __restrict__ node, const 
   return mask;
 }
 
+// slab4 on a 64-byte node: decode the near and far planes of the four
+// children (bytes on the node's per-axis grid) and run the same widened
+// test; empty slots are masked by their child ref.
+__device__ __forceinline__ unsigned slab4q(const QNode* __restrict__ node, const RayPre& r, float bound,
+                                           float tn[4], int4* child) {
+  const float4* p = reinterpret_cast<const float4*>(node);
+  const float4 w0 = __ldg(p);
+  const uint4 w1 = __ldg(reinterpret_cast<const uint4*>(p + 1));
+  const uint4 w2 = __ldg(reinterpret_cast<const uint4*>(p + 2));
+  const int4 ch = __ldg(reinterpret_cast<const int4*>(p + 3));
+  *child = ch;
+  const int ex = __float_as_int(w0.w);
+  const float sx = qscale((ex & 255) - 128), sy = qscale(((ex >> 8) & 255) - 128), sz = qscale(((ex >> 16) & 255) - 128);
+  const unsigned nxw = r.sx ? w1.y : w1.x, fxw = r.sx ? w1.x : w1.y;
+  const unsigned nyw = r.sy ? w1.w : w1.z, fyw = r.sy ? w1.z : w1.w;
+  const unsigned nzw = r.sz ? w2.y : w2.x, fzw = r.sz ? w2.x : w2.y;
+  const int cha[4] = {ch.x, ch.y, ch.z, ch.w};
+  unsigned mask = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const unsigned sel = 0x7540u + i;  // byte i of the word below 0x4B0000 (see qplane)
+    const float nx = __fmaf_rn(__int_as_float(__byte_perm(nxw, 0x4B000000u, sel)) - 8388608.f, sx, w0.x);
+    const float fx = __fmaf_rn(__int_as_float(__byte_perm(fxw, 0x4B000000u, sel)) - 8388608.f, sx, w0.x);
+    const float ny = __fmaf_rn(__int_as_float(__byte_perm(nyw, 0x4B000000u, sel)) - 8388608.f, sy, w0.y);
+    const float fy = __fmaf_rn(__int_as_float(__byte_perm(fyw, 0x4B000000u, sel)) - 8388608.f, sy, w0.y);
+    const float nz = __fmaf_rn(__int_as_float(__byte_perm(nzw, 0x4B000000u, sel)) - 8388608.f, sz, w0.z);
+    const float fz = __fmaf_rn(__int_as_float(__byte_perm(fzw, 0x4B000000u, sel)) - 8388608.f, sz, w0.z);
+    float t0 = fmaxf(fmaxf(__fmul_rn(__fsub_rn(nx, r.ox), r.ix), __fmul_rn(__fsub_rn(ny, r.oy), r.iy)),
+                     __fmul_rn(__fsub_rn(nz, r.oz), r.iz));
+    float t1 = fminf(fminf(__fmul_rn(__fsub_rn(fx, r.ox), r.ix), __fmul_rn(__fsub_rn(fy, r.oy), r.iy)),
+                     __fmul_rn(__fsub_rn(fz, r.oz), r.iz));
+    t0 = t0 - fabsf(t0) * kWiden;
+    t1 = t1 + fabsf(t1) * kWiden;
+    tn[i] = t0;
+    if (cha[i] != INT_MIN && t0 <= t1 && t0 <= bound && t1 >= r.tmin) mask |= 1u << i;
+  }
+  return mask;
+}
+
 // The same conservative slab test for one box (lo, hi) of a binary node.
 __device__ __forceinline__ bool slab1(float4 lo, float4 hi, const RayPre& r, float bound) {
   const float nx = r.ix >= 0.f ? lo.x : hi.x, fx = r.ix >= 0.f ? hi.x : lo.x;
@@ -281,6 +320,7 @@ struct TraceArgs {
   const WNode* wide;
   const int* wide_root;  // device word: index of the root traversal node
   const Node2* node2;
+  const QNode* qwide;    // 64-byte nodes (walk with kQuant)
   const int2* link2;     // (parent, epoch) of every binary node
   const int* root_ref;   // device word: binary root (leaf ref if the root is a leaf)
   int n_tri;             // binary node ids are < n_tri - 1
@@ -298,7 +338,7 @@ struct TraceArgs {
   int qcap;
 };
 
-template <bool kAny, bool kStats, int kTile>
+template <bool kAny, bool kStats, int kTile, bool kQuant = false>
 __global__ void __launch_bounds__(kTile) k_trace(TraceArgs A) {
   const int i = blockIdx.x * kTile + threadIdx.x;
   if (i >= A.n || (A.n_dev && i >= *A.n_dev)) return;
@@ -356,7 +396,7 @@ __global__ void __launch_bounds__(kTile) k_trace(TraceArgs A) {
       if (kStats) ++n_nodes;
       float tn[4];
       int4 ch;
-      unsigned m = slab4(A.wide + ref, r, bound, tn, &ch);
+      unsigned m = kQuant ? slab4q(A.qwide + ref, r, bound, tn, &ch) : slab4(A.wide + ref, r, bound, tn, &ch);
       float ta = (m & 1u) ? tn[0] : INFINITY, tb = (m & 2u) ? tn[1] : INFINITY;
       float tc = (m & 4u) ? tn[2] : INFINITY, td = (m & 8u) ? tn[3] : INFINITY;
       int ra = ch.x, rb = ch.y, rc = ch.z, rd = ch.w;
@@ -645,10 +685,13 @@ cudaError_t launch_trace_dev(rt_scene_s* s, const rt_ray* rays, int64_t n, const
                              uint8_t* occl, const rt_trace_params* tp, TraceScratch& scr, cudaStream_t st) {
   cudaError_t e;
   int n_launched = 0;
+  const bool quant = tp && (tp->flags & RT_QUANTIZED_NODES);
+  if (quant && !s->q_built) return cudaErrorInvalidValue;  // no 64-byte nodes for this tree
   if ((e = cudaMemsetAsync(scr.counter, 0, 2 * sizeof(int), st))) return e;
   if (n > 0) {
     TraceArgs A;
     A.wide = s->wide;
+    A.qwide = s->qwide;
     A.wide_root = &s->ctl->wide_root;
     A.node2 = s->node2;
     A.link2 = s->link2;
@@ -671,7 +714,15 @@ cudaError_t launch_trace_dev(rt_scene_s* s, const rt_ray* rays, int64_t n, const
     const int req = (tp && !stats) ? tp->block : 0;
     const int tile = (req == 64 || req == 256) ? req : kTraceBlock;
     const int grid = (int)((n + tile - 1) / tile);
-    if (stats) {
+    if (quant) {  // the 64-byte node walk: the default tile only
+      const int gq = (int)((n + kTraceBlock - 1) / kTraceBlock);
+      if (occl)
+        stats ? k_trace<true, true, kTraceBlock, true><<<gq, kTraceBlock, 0, st>>>(A)
+              : k_trace<true, false, kTraceBlock, true><<<gq, kTraceBlock, 0, st>>>(A);
+      else
+        stats ? k_trace<false, true, kTraceBlock, true><<<gq, kTraceBlock, 0, st>>>(A)
+              : k_trace<false, false, kTraceBlock, true><<<gq, kTraceBlock, 0, st>>>(A);
+    } else if (stats) {
       if (occl)
         k_trace<true, true, kTraceBlock><<<grid, kTraceBlock, 0, st>>>(A);
       else

@@ -23,6 +23,7 @@ from . import build_ext
 
 RT_NO_FP64_RETEST = 1
 RT_COUNT_STATS = 2
+RT_QUANTIZED_NODES = 4
 RT_RAYS_FIBONACCI = 0
 RT_RAYS_ICOSPHERE = 1
 
@@ -56,7 +57,7 @@ class BuildParams(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_float), ("t_i", ctypes.c_float), ("t_trav", ctypes.c_float),
                 ("source", ctypes.c_float * 3), ("max_leaf", ctypes.c_int32),
                 ("bins", ctypes.c_int32), ("width", ctypes.c_int32), ("dist_norm", ctypes.c_int32),
-                ("range", ctypes.c_float)]
+                ("range", ctypes.c_float), ("quantize", ctypes.c_int32)]
 
 
 class TraceParams(ctypes.Structure):
@@ -259,12 +260,13 @@ def rt_scene_update(scene: Scene, tris, stream=None):
 
 
 def build_params(alpha=1.0, source=(0.0, 0.0, 0.0), max_leaf=4, bins=16, width=4, dist_norm=0,
-                 t_i=1.0, t_trav=1.0, range=0.0) -> BuildParams:
+                 t_i=1.0, t_trav=1.0, range=0.0, quantize=0) -> BuildParams:
     p = BuildParams()
     p.alpha, p.t_i, p.t_trav = alpha, t_i, t_trav
     p.source[0], p.source[1], p.source[2] = float(source[0]), float(source[1]), float(source[2])
     p.max_leaf, p.bins, p.width, p.dist_norm = int(max_leaf), int(bins), int(width), int(dist_norm)
     p.range = float(range)
+    p.quantize = int(quantize)
     return p
 
 
