@@ -565,7 +565,7 @@ def run_served(rtbvh, torch, seconds):
 # two kernels on this workload, from one ncu capture each of the current
 # kernels (max_leaf 4, 16 bins, 128-ray tile, alpha 0.7).
 NCU_TRAFFIC_LARGE = {  # k_trace<0,0,128> on 4 x 2^21 metro rays (1 ncu pass per launch)
-    0.7: (362.593280e6 + 340.041984e6, 10.5368), 1.0: (296.002816e6 + 145.577728e6, 4.6164)}
+    0.7: (362.787072e6 + 325.806592e6, 9.5426), 1.0: (294.681088e6 + 144.702976e6, 4.3015)}
 NCU_TRAFFIC = {
     "k_split": (1.694720e6 + 256.0, "ncu capture of k_split, medium city (profiles/k_split_medium_city.md)"),
     "k_trace": (21.492224e6 + 0.0576e6,

@@ -21,7 +21,8 @@ def compare_closest(gpu_hits, ref, tris=None, rays=None, label=""):
     t, ids, u, v = split_hits(gpu_hits)
     n = len(ids)
     rt, rid = ref.t, ref.id
-    tie = np.isfinite(ref.t2) & (ref.t2 - rt <= TIE_REL * np.abs(rt))
+    with np.errstate(invalid="ignore"):  # inf - inf on rays without a second hit
+        tie = np.isfinite(ref.t2) & (ref.t2 - rt <= TIE_REL * np.abs(rt))
     bad_id = (ids != rid) & ~tie
     if bad_id.any():
         k = np.nonzero(bad_id)[0][:10]
