@@ -202,7 +202,7 @@ int rt_autotune(rt_scene scene, const rt_build_params* base, const rt_ray* rays_
  * Process-wide; value 0 turns a hook off.
  *   RT_DEBUG_SPIN_LIMIT    polls a build's work-queue wait may make without
  *                          progress before it gives up (default 2^24)
- *   RT_DEBUG_PHANTOM_TASK  every later build counts this many mid-level tasks
+ *   RT_DEBUG_PHANTOM_TASK  every later build counts this many subtree tasks
  *                          that are never published: its warps wait for them
  *                          until the spin limit, the build ends with the
  *                          timeout status (rt_bvh_info: RT_ETIMEOUT)

@@ -16,11 +16,13 @@
 //                 bins, stable partition of the chunk into the other record
 //                 buffer, and on the way the children's bins and per-chunk
 //                 counts; the CTA finishing a node's last chunk writes the node
-//                 and publishes its children's items.  The other warps take
-//                 the remaining nodes of more than 32 triangles from a device
-//                 queue (warp per node, the larger child stays with the warp)
-//                 and finish nodes of at most 32 triangles in registers over
-//                 the Morton order of their records.  No CTA waits for another
+//                 and publishes its children's items.  Every CTA takes the
+//                 subtrees (nodes of at most `big` triangles) from a second
+//                 device queue, CTA per subtree, and builds each in shared
+//                 memory: nodes of more than 32 triangles split by the whole
+//                 CTA (the smaller child goes back to the queue), nodes of at
+//                 most 32 finished by single warps in registers over the
+//                 Morton order of their records.  No CTA waits for another
 //                 except for work to appear (bounded waits).
 //   k_post        4-wide traversal nodes (greedy by surface area), stored at the
 //                 id of their binary root; triangles in leaf order
@@ -53,7 +55,7 @@ constexpr int kBinWords = 3 * kMaxBins * kBinVals;
 constexpr int kCntStride = 3 * kMaxBins;
 constexpr int kMaxRpt = 4;     // records per thread of a big node's chunk
 constexpr int kBigMin = 1024;  // big nodes have more triangles than this
-constexpr int kStageW = 256;   // records a mid-level warp keeps in shared memory
+constexpr int kStageW = 256;   // records the global-memory warp split (oversized tasks) stages
 constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
@@ -356,7 +358,7 @@ struct BuildArgs {
   Node2* node2;
   int2* link2;
   BuildCtl* ctl;
-  Task* qa;  // mid-level queue
+  Task* qa;  // subtree queue
   int* qa_ready;
   TopTask* ttask;  // big nodes
   int* tdone;
@@ -407,7 +409,7 @@ __device__ __forceinline__ TopTask load_top_cg(const TopTask* p) {
   return t;
 }
 
-// Hand a task to the mid-level queue (one thread).  The slot's ready word
+// Hand a task to the subtree queue (one thread).  The slot's ready word
 // takes this build's epoch, so stale slots from older builds never match.
 __device__ void push_task(const BuildArgs& A, const Task& t, int epoch) {
   const int s = atomicAdd(&A.ctl->qa_tail, 1);
@@ -420,7 +422,7 @@ __device__ void push_task(const BuildArgs& A, const Task& t, int epoch) {
   st_release(&A.qa_ready[s], epoch);
 }
 
-// Hand up to 3 tasks to the mid-level queue at once (one thread): one slot
+// Hand up to 3 tasks to the subtree queue at once (one thread): one slot
 // reservation, one fence.
 __device__ void push_tasks(const BuildArgs& A, const Task* t, int k, int epoch) {
   if (k <= 0) return;
@@ -620,7 +622,7 @@ __device__ __forceinline__ uint32_t spread10(uint32_t v) {
 }
 
 // ------------------------------------------------------------------ root
-// Morton keys of all records; the root task (a top task, a mid-level task, a
+// Morton keys of all records; the root task (a top task, a subtree task, a
 // leaf or nothing); the root's bins and per-chunk counts when it is a top task.
 __global__ void __launch_bounds__(kBlock) k_bin_root(BuildArgs A) {
   pdl_wait();
@@ -821,7 +823,7 @@ __device__ void top_emit(const BuildArgs& A, TopSmem& S, const TopTask& T, int e
 // partition of the chunk into the other record buffer, and on the way the
 // bins and per-chunk counts of the children that are big nodes too.  The CTA
 // that finishes the node's last chunk writes the node and creates its
-// children: big ones get their chunk items, the others go to the mid-level
+// children: big ones get their chunk items, the others go to the subtree
 // queue.  No CTA ever waits for another.
 __device__ void top_chunk(const BuildArgs& A, TopSmem& S, const TopTask& T, int slot, int j, int epoch) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1153,7 +1155,7 @@ __device__ void top_loop(const BuildArgs& A, TopSmem& S, int epoch) {
     if (it.x < 0) return;
     top_item(A, S, it.x, it.y, epoch);
     __syncthreads();
-    // release: the mid-level tasks this item pushed are counted before the
+    // release: the subtree tasks this item pushed are counted before the
     // item stops counting (the warps' exit test reads ti_pending first)
     if (threadIdx.x == 0) red_release_add(&A.ctl->ti_pending, -1);
   }
@@ -1346,7 +1348,11 @@ __device__ void micro_task(const BuildArgs& A, int begin, int n, int parity, int
   micro_sort_build(A, lo, hi, begin, n, parent, side, depth, epoch, ws);
 }
 
-// ------------------------------------------------------------------ mid levels
+// ------------------------------------------------------------------ subtree queue
+// Claiming subtree tasks, and the split of tasks too large for a CTA's
+// shared memory (more than kSubMax records: a big node whose pools were
+// full, or any task when big = T / 4096 > 1024), done in global memory by
+// one warp until the part it keeps fits.
 struct MidWarp {
   unsigned bins[kBinWords];
   float4 stage[2 * kStageW];
@@ -1378,7 +1384,7 @@ __device__ bool claim_task(const BuildArgs& A, int epoch, Task& t) {
       return true;
     }
     if ((it & 3) == 0) {
-      // done when no big node is left and then no mid-level task either
+      // done when no big node is left and then no subtree task either
       if (ld_acquire(&A.ctl->ti_pending) == 0 && ld_volatile(&A.ctl->qa_pending) == 0) return false;
       if (ld_volatile(&A.ctl->status) != 0) return false;
       const int prog = ld_volatile(&A.ctl->qa_tail) + ld_volatile(&A.ctl->ti_head);
@@ -1933,7 +1939,7 @@ __device__ void sub_tree(const BuildArgs& A, SubSmem& S, const Task& t, int epoc
   __syncthreads();
 }
 
-// The mid-level role of every CTA: take a task from the queue, build its
+// The subtree role of every CTA: take a task from the queue, build its
 // subtree (tasks of more than kSubMax records are first split in global
 // memory by one warp, down to a part that fits), repeat until the queue is
 // drained.
@@ -1993,7 +1999,7 @@ __device__ void sub_loop(const BuildArgs& A, SubSmem& S, int epoch) {
 }
 
 // The split phase: the first top_ctas CTAs work the chunk items of big nodes
-// (CTA per item) and then join the others, which take the mid-level queue
+// (CTA per item) and then join the others, which take the subtree queue
 // (CTA per subtree).  Both run at once, so subtrees proceed while the big
 // nodes of other branches are still being split.
 union SplitSmem {

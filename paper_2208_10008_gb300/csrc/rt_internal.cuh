@@ -116,7 +116,7 @@ struct BuildCtl {
   int ti_head, ti_tail, ti_pending, pad0;
   // pools of one build: top task slots, count slots
   int t_slot_next, t_cnt_next, pad1, pad2;
-  // mid-level task queue (warp per task)
+  // subtree task queue (CTA per task)
   int qa_head, qa_tail, qa_pending, pad3;
   // tree facts
   int n_internal, n_leaves, depth2, max_leaf_size;
@@ -133,7 +133,7 @@ struct BuildGeom {
   int rpt;        // records per thread in a chunk (chunk / 256)
   int cap_t;      // top task slots
   int cap_c;      // count slots and chunk items
-  int qa_cap;     // mid-level queue slots
+  int qa_cap;     // subtree queue slots
 };
 BuildGeom build_geometry(int64_t n_tri, int nsm);
 
@@ -174,7 +174,7 @@ void count_launches(int k);
 // Test hooks of rt_debug_inject (process-wide).
 struct DebugHooks {
   int spin_limit;     // 0: kSpinLimit
-  int phantom_tasks;  // mid-level tasks counted but never published
+  int phantom_tasks;  // subtree tasks counted but never published
   int phantom_items;  // big-node chunk items counted but never published
 };
 DebugHooks debug_hooks();
@@ -215,7 +215,7 @@ struct rt_scene_s {
   int2* link2 = nullptr;        // (parent, epoch) per binary node
   int* epoch = nullptr;         // build counter on the device
   float4* tri_leaf = nullptr;
-  rt::Task* qa = nullptr;       // mid-level task queue
+  rt::Task* qa = nullptr;       // subtree task queue
   int* qa_ready = nullptr;      // epoch stamp of each filled queue slot
   rt::TopTask* top_task = nullptr;  // [cap_t] big nodes
   int* top_done = nullptr;          // [cap_t] finished chunks of each
