@@ -89,3 +89,21 @@ def test_quantised_flag_needs_a_quantised_build(rb):
     with pytest.raises(rb.RtError):
         rb.rt_trace_closest(s, rays, flags=rb.RT_QUANTIZED_NODES)
     torch.cuda.synchronize()
+
+
+def test_quantised_nodes_of_a_range_tree(rb):
+    # both options together: a tree pruned to the range of its source, with
+    # its 64-byte nodes; direct rays within the range hit exactly as on the
+    # whole-scene float tree
+    sc = scenes.medium_city(seed=2)
+    src = tuple(float(v) for v in sc.tx[0])
+    full = rb.rt_scene_upload(sc.tris)
+    rb.rt_bvh_build(full, alpha=0.7, dist_norm=1, source=src, max_leaf=4)
+    part = rb.rt_scene_upload(sc.tris)
+    rb.rt_bvh_build(part, alpha=0.7, dist_norm=1, source=src, max_leaf=4, range=300.0, quantize=1)
+    assert 0 < rb.rt_bvh_info(part)["n_built"] < sc.n_tri
+    rays = torch.from_numpy(scenes.make_rays(src, scenes.icosphere_directions(6), 0.0, 300.0)).cuda()
+    hf = rb.rt_trace_closest(full, rays)
+    hq = rb.rt_trace_closest(part, rays, flags=rb.RT_QUANTIZED_NODES)
+    torch.cuda.synchronize()
+    assert _same(hf, hq)
