@@ -107,3 +107,25 @@ def test_split_events_time_the_split_kernel(rb):
     assert 0 < split <= whole
     # one event without the other is refused
     assert rb.lib().rt_scene_set_split_events(s.handle, ctypes.c_void_p(s0.cuda_event), None) == -1
+
+
+def test_full_size_in_the_benchmarked_launch_configuration(rb, orc):
+    # what the benchmark times: the medium city's 655,362 icosphere rays, the
+    # tree and ray tile the autotuner picks (build weight 1), the build and
+    # the walk launched as in a step; sampled rays against brute force
+    sc, rays_np, _ = scenes.workload_medium()
+    src = tuple(float(v) for v in sc.tx[0])
+    s = rb.rt_scene_upload(sc.tris)
+    rays = dev(rays_np)
+    tune = rb.rt_autotune(s, rays, build_weight=1.0, alpha=0.7, source=src, dist_norm=1)
+    rb.rt_bvh_build(s, alpha=0.7, source=src, dist_norm=1, max_leaf=tune["max_leaf"], bins=tune["bins"])
+    hits = torch.empty((len(rays_np), 4), dtype=torch.float32, device="cuda")
+    nflag = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rb.rt_trace_closest(s, rays, hits, n_flagged=nflag, block=tune["block"])
+    torch.cuda.synchronize()
+    h = hits.cpu().numpy()
+    rng = np.random.default_rng(12)
+    sample = np.union1d(rng.choice(len(rays_np), 6000, replace=False), np.arange(0, len(rays_np), 1111))
+    ref = orc.closest_brute(sc.tris, rays_np[sample])
+    compare_closest(h[sample], ref, sc.tris, rays_np[sample], "benchmarked configuration")
+    assert int(nflag.item()) < len(rays_np) // 1000  # the float64 pass stays rare
