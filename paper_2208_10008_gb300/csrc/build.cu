@@ -1849,7 +1849,7 @@ __device__ void cta_split(const BuildArgs& A, SubSmem& S, const SubNode& X, int 
   if (ex >= 0) {
     const int eb = ex ? nl : 0, en = ex ? nr : nl;
     for (int k = tid; k < 2 * en; k += kBlock) __stcg(A.rec[1] + 2 * ((size_t)gbegin + X.b + eb) + k, dst[2 * eb + k]);
-    __syncthreads();  // thread 0 publishes them below (fence, then a release store)
+    __syncthreads();  // thread 0 publishes them below (a release store)
   }
   if (tid == 0) {
     if (total != nl) set_status(A.ctl, kStBadSplit, 6);
@@ -1863,7 +1863,8 @@ __device__ void cta_split(const BuildArgs& A, SubSmem& S, const SubNode& X, int 
       const int cn = s ? nr : nl, b = X.b + (s ? nl : 0);
       if (cn <= A.max_leaf) continue;
       if (s == ex) {
-        __threadfence();
+        // the records written by every thread above are ordered before this
+        // thread by the barrier; push_task's release store publishes them
         push_task(A, make_task(gbegin + b, cn, id, s, X.depth + 1, s ? R : L, 1), epoch);
       } else if (cn <= kMicro) {
         if (S.nm < kMicroList)
