@@ -1115,9 +1115,10 @@ __device__ void top_emit(const BuildArgs& A, TopSmem& S, const TopTask& T, int e
   }
   if (tid == 0 && (S.created[0] || S.created[1]))
     atomicAdd(&A.ctl->ti_pending, (S.created[0] ? nch0 : 0) + (S.created[1] ? nch1 : 0));
-  __threadfence();
   __syncthreads();
-  // publish the children's chunk items
+  // publish the children's chunk items: each release store also publishes
+  // what every thread wrote before the barrier (the zeroed bins and counts,
+  // the tasks, the pending count)
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
     if (!S.created[s]) continue;
