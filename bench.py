@@ -567,8 +567,8 @@ def run_served(rtbvh, torch, seconds):
 NCU_TRAFFIC_LARGE = {  # k_trace<0,0,128> on 4 x 2^21 metro rays (1 ncu pass per launch)
     0.7: (362.787072e6 + 325.806592e6, 9.5426), 1.0: (294.681088e6 + 144.702976e6, 4.3015)}
 NCU_TRAFFIC = {
-    "k_split": (1.694720e6 + 256.0, "ncu capture of k_split, medium city (profiles/k_split_medium_city.md)"),
-    "k_trace": (21.492224e6 + 0.0576e6,
+    "k_split": (1.703680e6 + 512.0, "ncu capture of k_split, medium city (profiles/k_split_medium_city.md)"),
+    "k_trace": (21.493760e6 + 0.058624e6,
                 "ncu capture of k_trace<0,0,128> (k_retest64 not included), medium city "
                 "(profiles/k_trace_medium_city.md)"),
 }
