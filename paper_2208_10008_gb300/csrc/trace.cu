@@ -38,6 +38,7 @@ namespace {
 constexpr int kTraceBlock = 128;
 constexpr int kStack = 64;
 constexpr int kRetestBlock = 128;
+constexpr unsigned kFullMask = 0xffffffffu;
 constexpr float kU = 5.9604645e-08f;   // unit roundoff of float32, 2^-24
 constexpr float kWiden = 1e-6f;        // relative widening of box intervals
 constexpr float kTieRel = 1e-5f;       // relative window of the best-hit checks
@@ -542,10 +543,16 @@ __device__ bool mt64(D3 o, D3 d, D3 v0, D3 v1, D3 v2, double* t, double* u, doub
   return true;
 }
 
+// One warp per flagged ray: lane q tests candidate q with the float64 rule
+// and a warp reduction keeps the nearest (lowest id on ties); a ray without
+// a complete candidate list walks the tree on lane 0.
 template <bool kAny>
 __global__ void __launch_bounds__(kRetestBlock) k_retest64(TraceArgs A) {
+  static_assert(kCand <= 32, "one candidate per lane");
   const int nflag = min(*(volatile int*)A.counter, A.qcap);
-  for (int j = blockIdx.x * kRetestBlock + threadIdx.x; j < nflag; j += gridDim.x * kRetestBlock) {
+  const int lane = threadIdx.x & 31;
+  const int w0 = (blockIdx.x * kRetestBlock + threadIdx.x) >> 5, nw = (gridDim.x * kRetestBlock) >> 5;
+  for (int j = w0; j < nflag; j += nw) {
     const int i = A.queue[j];
     const float4* r4 = reinterpret_cast<const float4*>(A.rays) + 2 * (size_t)i;
     const float4 ra = r4[0], rb = r4[1];
@@ -554,28 +561,41 @@ __global__ void __launch_bounds__(kRetestBlock) k_retest64(TraceArgs A) {
     const double tmin = ra.w, tmax = rb.w;
     const int skip = A.skip ? A.skip[i] : -1;
     double bt = INFINITY, bu = 0.0, bv = 0.0;
-    int bid = -1, bpos = -1;
-    bool any = false;
+    int bid = INT_MAX, bpos = -1;
     const int* cl = A.cand + (size_t)j * (kCand + 1);
     const int ncand = cl[0];
-    for (int q = 0; q < ncand; ++q) {
-      const float4* tp = A.tris + 3 * (size_t)cl[1 + q];
+    if (lane < ncand) {
+      const int pos = cl[1 + lane];
+      const float4* tp = A.tris + 3 * (size_t)pos;
       const float4 va = tp[0], vb = tp[1], vc = tp[2];
       const int id = __float_as_int(va.w);
-      if (id == skip) continue;
       double t, u, v;
-      if (mt64(o, d, D3{va.x, va.y, va.z}, D3{vb.x, vb.y, vb.z}, D3{vc.x, vc.y, vc.z}, &t, &u, &v) &&
+      if (id != skip && mt64(o, d, D3{va.x, va.y, va.z}, D3{vb.x, vb.y, vb.z}, D3{vc.x, vc.y, vc.z}, &t, &u, &v) &&
           t > tmin && t < tmax) {
-        any = true;
-        if (t < bt || (t == bt && id < bid)) {
-          bt = t;
-          bid = id;
-          bpos = cl[1 + q];
-          bu = u;
-          bv = v;
-        }
+        bt = t;
+        bid = id;
+        bpos = pos;
+        bu = u;
+        bv = v;
       }
     }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const double ot = __shfl_xor_sync(kFullMask, bt, off);
+      const int oid = __shfl_xor_sync(kFullMask, bid, off);
+      const int opos = __shfl_xor_sync(kFullMask, bpos, off);
+      const double ou = __shfl_xor_sync(kFullMask, bu, off), ov = __shfl_xor_sync(kFullMask, bv, off);
+      if (ot < bt || (ot == bt && oid < bid)) {
+        bt = ot;
+        bid = oid;
+        bpos = opos;
+        bu = ou;
+        bv = ov;
+      }
+    }
+    bool any = bid != INT_MAX;
+    if (lane != 0) continue;
+    if (bid == INT_MAX) bid = -1;
     // Without a complete candidate list: a stackless walk of the binary tree
     // (parent links), so that any depth works.  Boxes use the same widened
     // float32 slab test as k_trace, culled at the float64 best distance
@@ -593,7 +613,7 @@ __global__ void __launch_bounds__(kRetestBlock) k_retest64(TraceArgs A) {
         if (mt64(o, d, D3{va.x, va.y, va.z}, D3{vb.x, vb.y, vb.z}, D3{vc.x, vc.y, vc.z}, &t, &u, &v) && t > tmin &&
             t < tmax) {
           any = true;
-          if (t < bt || (t == bt && id < bid)) {
+          if (t < bt || (t == bt && (bid < 0 || id < bid))) {
             bt = t;
             bid = id;
             bpos = first + k;
