@@ -15,14 +15,16 @@
 //     functions.  Signs settled beyond E give a certain hit or miss; anything
 //     else, a second hit within the error window of the best one, a hit near
 //     tmin / tmax, or a stack overflow marks the ray for k_retest64.
-// k_retest64 (float64, one flagged ray per thread)
-//   * the float64 rule on the ray's candidate triangles, or, when the list
-//     overflowed, a stackless walk of the binary tree (parent links) with the
-//     same conservative float32 box test culled at the float64 best
-//     distance, and for every
-//     triangle the float32 bound does not prove missed, the reference hit
-//     rule: Moller-Trumbore with inclusive edges, |det| <= 1e-14 |e1||e2||d|
-//     is parallel, tmin < t < tmax, lowest id on equal t, with the operation
+// k_retest64 (float64, flagged rays only)
+//   * rays with a candidate list: a group of lanes per ray (a warp when few
+//     rays are flagged, one lane when many are) applies the float64 rule to
+//     the candidates and a group reduction keeps the nearest; when the
+//     list overflowed, one thread per ray does a stackless walk of the
+//     binary tree (parent links) with the same conservative float32 box test
+//     culled at the float64 best distance, and for every triangle the
+//     float32 bound does not prove missed, the reference hit rule:
+//     Moller-Trumbore with inclusive edges, |det| <= 1e-14 |e1||e2||d| is
+//     parallel, tmin < t < tmax, lowest id on equal t, with the operation
 //     order fixed and no contraction, so its answer is the float64
 //     definition's answer bit for bit.
 #include <cuda_runtime.h>
@@ -543,35 +545,49 @@ __device__ bool mt64(D3 o, D3 d, D3 v0, D3 v1, D3 v2, double* t, double* u, doub
   return true;
 }
 
-// One warp per flagged ray: lane q tests candidate q with the float64 rule
-// and a warp reduction keeps the nearest (lowest id on ties); a ray without
-// a complete candidate list walks the tree on lane 0.
+// Flagged rays with a candidate list: a group of G lanes each (G a power of
+// two, the widest up to 32 that still gives every flagged ray its own group
+// in this grid, so a handful of rays gets a warp each and a flood gets a
+// thread each); lane q of a group tests candidates q, q + G, ... with the
+// float64 rule and a reduction over the group keeps the nearest (lowest id on
+// ties, the same minimum whatever G is).  Rays without a complete list: one
+// thread each walks the tree.
 template <bool kAny>
 __global__ void __launch_bounds__(kRetestBlock) k_retest64(TraceArgs A) {
-  static_assert(kCand <= 32, "one candidate per lane");
   const int nflag = min(*(volatile int*)A.counter, A.qcap);
-  const int lane = threadIdx.x & 31;
-  const int w0 = (blockIdx.x * kRetestBlock + threadIdx.x) >> 5, nw = (gridDim.x * kRetestBlock) >> 5;
-  for (int j = w0; j < nflag; j += nw) {
-    const int i = A.queue[j];
+  if (nflag <= 0) return;
+  const int nthreads = gridDim.x * kRetestBlock;
+  int lg = 5;
+  while (lg > 0 && ((long long)nflag << lg) > nthreads) --lg;
+  const int tid = blockIdx.x * kRetestBlock + threadIdx.x;
+  const int lane = threadIdx.x & 31, sub = lane & ((1 << lg) - 1);
+  const int ngroups = nthreads >> lg;
+  // jw: the first ray of this warp's groups; the loop is uniform over the warp
+  for (int jw = (tid & ~31) >> lg; jw < nflag; jw += ngroups) {
+    const int j = jw + (lane >> lg);
+    const bool live = j < nflag;
+    const int* cl = A.cand + (size_t)(live ? j : 0) * (kCand + 1);
+    const int ncand = live ? cl[0] : -1;
+    const int i = live ? A.queue[j] : 0;
     const float4* r4 = reinterpret_cast<const float4*>(A.rays) + 2 * (size_t)i;
-    const float4 ra = r4[0], rb = r4[1];
-    const RayPre r = setup_ray(ra, rb);
+    float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rb = ra;
+    if (ncand > 0) {
+      ra = r4[0];
+      rb = r4[1];
+    }
     const D3 o{ra.x, ra.y, ra.z}, d{rb.x, rb.y, rb.z};
     const double tmin = ra.w, tmax = rb.w;
-    const int skip = A.skip ? A.skip[i] : -1;
+    const int skip = (ncand > 0 && A.skip) ? A.skip[i] : -1;
     double bt = INFINITY, bu = 0.0, bv = 0.0;
     int bid = INT_MAX, bpos = -1;
-    const int* cl = A.cand + (size_t)j * (kCand + 1);
-    const int ncand = cl[0];
-    if (lane < ncand) {
-      const int pos = cl[1 + lane];
+    for (int q = sub; q < ncand; q += 1 << lg) {
+      const int pos = cl[1 + q];
       const float4* tp = A.tris + 3 * (size_t)pos;
       const float4 va = tp[0], vb = tp[1], vc = tp[2];
       const int id = __float_as_int(va.w);
       double t, u, v;
       if (id != skip && mt64(o, d, D3{va.x, va.y, va.z}, D3{vb.x, vb.y, vb.z}, D3{vc.x, vc.y, vc.z}, &t, &u, &v) &&
-          t > tmin && t < tmax) {
+          t > tmin && t < tmax && (t < bt || (t == bt && id < bid))) {
         bt = t;
         bid = id;
         bpos = pos;
@@ -579,8 +595,7 @@ __global__ void __launch_bounds__(kRetestBlock) k_retest64(TraceArgs A) {
         bv = v;
       }
     }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
+    for (int off = (1 << lg) >> 1; off > 0; off >>= 1) {
       const double ot = __shfl_xor_sync(kFullMask, bt, off);
       const int oid = __shfl_xor_sync(kFullMask, bid, off);
       const int opos = __shfl_xor_sync(kFullMask, bpos, off);
@@ -593,9 +608,49 @@ __global__ void __launch_bounds__(kRetestBlock) k_retest64(TraceArgs A) {
         bv = ov;
       }
     }
-    bool any = bid != INT_MAX;
-    if (lane != 0) continue;
-    if (bid == INT_MAX) bid = -1;
+    if (ncand < 0 || sub != 0) continue;  // a whole-tree walk is done below
+    if (ncand == 0) {
+      ra = r4[0];
+      rb = r4[1];
+    }
+    const RayPre r = setup_ray(ra, rb);
+    if (kAny) {
+      A.occl[i] = bid != INT_MAX ? 1 : 0;
+    } else {
+      float4 out = make_float4(INFINITY, __int_as_float(-1), 0.f, 0.f);
+      if (bid != INT_MAX) {
+        out = make_float4((float)bt, __int_as_float(bid), (float)bu, (float)bv);
+        // The record is a function of the ray and the winning triangle only:
+        // where the float32 test certifies the winner, report exactly what
+        // the float32 walk reports for it (so the result never depends on
+        // whether this tree's walk flagged the ray).
+        const float4* tp = A.tris + 3 * (size_t)bpos;
+        const float4 va = tp[0], vb = tp[1], vc = tp[2];
+        const TriRes h = tri_test(r, va, vb, vc);
+        if (h.cls == 1 && h.t > r.tmin && h.t < r.tmax) {
+          float t = h.t;
+          if (h.err > 0.25f * (kTieRel * h.t + 1e-6f)) t = refine_t(r, rb.x, rb.y, rb.z, va, vb, vc);
+          out = make_float4(t, __int_as_float(bid), h.u, h.v);
+        }
+      }
+      reinterpret_cast<float4*>(A.hits)[i] = out;
+    }
+  }
+  // rays without a complete candidate list: one thread each walks the tree
+  for (int j = blockIdx.x * kRetestBlock + threadIdx.x; j < nflag; j += gridDim.x * kRetestBlock) {
+    const int i = A.queue[j];
+    const float4* r4 = reinterpret_cast<const float4*>(A.rays) + 2 * (size_t)i;
+    const float4 ra = r4[0], rb = r4[1];
+    const RayPre r = setup_ray(ra, rb);
+    const D3 o{ra.x, ra.y, ra.z}, d{rb.x, rb.y, rb.z};
+    const double tmin = ra.w, tmax = rb.w;
+    const int skip = A.skip ? A.skip[i] : -1;
+    double bt = INFINITY, bu = 0.0, bv = 0.0;
+    int bid = -1, bpos = -1;
+    bool any = false;
+    const int* cl = A.cand + (size_t)j * (kCand + 1);
+    const int ncand = cl[0];
+    if (ncand >= 0) continue;  // done by a warp above
     // Without a complete candidate list: a stackless walk of the binary tree
     // (parent links), so that any depth works.  Boxes use the same widened
     // float32 slab test as k_trace, culled at the float64 best distance
@@ -623,7 +678,7 @@ __global__ void __launch_bounds__(kRetestBlock) k_retest64(TraceArgs A) {
         }
       }
     };
-    if (r.valid && ncand < 0) {
+    if (r.valid) {
       const int root = *A.root_ref;
       if (root >= A.n_tri - 1) {
         // no usable tree: nothing to walk
