@@ -558,7 +558,10 @@ int rt_trace_closest_host(rt_scene s, const rt_ray* rays_host, int64_t n, rt_hit
   for (int k = 0; k < 2; ++k) cudaStreamWaitEvent(s->host_streams[k], ev, 0);
   cudaEventDestroy(ev);
   rt_trace_params tp{};
-  if (params) tp.flags = params->flags;
+  if (params) {  // the device-pointer fields are per-ray arrays of the device paths: not used here
+    tp.flags = params->flags;
+    tp.block = params->block;
+  }
   int rc = RT_OK;
   for (int64_t off = 0, c = 0; off < n; off += chunk, ++c) {
     const int k = (int)(c & 1);

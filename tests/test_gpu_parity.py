@@ -277,6 +277,9 @@ def test_host_buffer_path_matches_device(rb):
     pinned = torch.from_numpy(rays).pin_memory()
     hh = rb.rt_trace_closest_host(s, pinned)
     assert np.array_equal(hh.numpy().view(np.uint32), hd.view(np.uint32))
+    for tile in (64, 256):  # the requested ray tile reaches the chunked walk
+        hh = rb.rt_trace_closest_host(s, pinned, block=tile)
+        assert np.array_equal(hh.numpy().view(np.uint32), hd.view(np.uint32))
 
 
 def test_stats_and_no_retest_flag(rb, orc):
