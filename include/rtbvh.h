@@ -451,7 +451,8 @@ typedef struct {
   int64_t submitted, completed, failed, queued, running, peak_running;
   int64_t rays;              /* rays traced by completed requests (all orders) */
   int64_t pool_bytes, peak_pool_bytes;
-  double p50_ms, p99_ms, mean_ms; /* submit-to-completion latency of completed requests */
+  double p50_ms, p99_ms, mean_ms; /* submit-to-completion latency of the last
+                                     2^20 completed requests */
   double span_s;             /* first submit to last completion */
 } rt_session_stats;
 
@@ -483,7 +484,14 @@ int rt_session_poll(rt_session session, uint64_t ticket, int* done);
  * Errors: RT_EINVAL, RT_ETIMEOUT, RT_ECUDA. */
 int rt_session_wait(rt_session session, uint64_t ticket, int64_t timeout_ns);
 
-/* Counters and latency percentiles so far. */
+/* Forget a finished request: its record is freed and the ticket is unknown
+ * from then on.  Its results stay in the caller's host buffers.  A session
+ * keeps every request until it is released (or the session destroyed), so
+ * a long-running server releases each ticket once it has read the results.
+ * Errors: RT_EINVAL (unknown ticket), RT_EBUSY (still queued or running). */
+int rt_session_release(rt_session session, uint64_t ticket);
+
+/* Counters (totals since creation) and latency percentiles. */
 int rt_session_stats_get(rt_session session, rt_session_stats* stats);
 
 /* Finish queued and running requests, stop the worker, free the pool. */

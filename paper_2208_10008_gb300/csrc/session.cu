@@ -120,6 +120,9 @@ size_t request_bytes(long long n, int orders) {
 
 }  // namespace
 
+// Latency percentiles cover this many of the most recent completed requests.
+constexpr size_t kLatencyWindow = size_t(1) << 20;
+
 struct rt_session_s {
   int device = 0;
   unsigned char* pool_mem = nullptr;
@@ -134,7 +137,8 @@ struct rt_session_s {
   bool stop = false;
   std::thread worker;
   // statistics
-  std::vector<double> lat_ms;
+  std::vector<double> lat_ms;  // ring of the last kLatencyWindow latencies
+  size_t lat_next = 0;
   long long submitted = 0, completed = 0, failed = 0, rays = 0;
   int running = 0, peak_running = 0;
   Clock::time_point t_first, t_last;
@@ -220,7 +224,13 @@ void finish(rt_session_s* S, Slot& sl, bool ok) {
   if (ok) {
     ++S->completed;
     S->rays += rays;
-    S->lat_ms.push_back(std::chrono::duration<double, std::milli>(q->t_done - q->t_submit).count());
+    const double ms = std::chrono::duration<double, std::milli>(q->t_done - q->t_submit).count();
+    if (S->lat_ms.size() < kLatencyWindow) {
+      S->lat_ms.push_back(ms);
+    } else {
+      S->lat_ms[S->lat_next] = ms;
+      S->lat_next = (S->lat_next + 1) % kLatencyWindow;
+    }
     S->t_last = q->t_done;
   } else {
     ++S->failed;
@@ -259,6 +269,9 @@ void worker_loop(rt_session_s* S) {
         lk.unlock();
         const bool ok = start(S, q, sl) == cudaSuccess;
         if (!ok) {
+          // work queued before the failing call may still use the request's
+          // pool memory: let the stream drain before the memory is reused
+          cudaStreamSynchronize(sl.st);
           cudaGetLastError();
           finish(S, sl, false);
         }
@@ -385,6 +398,17 @@ int rt_session_wait(rt_session S, uint64_t ticket, int64_t timeout_ns) {
     return rt::set_error(RT_ETIMEOUT, "request not finished within the timeout");
   }
   return q->state == 3 ? rt::set_error(RT_ECUDA, "request failed") : RT_OK;
+}
+
+int rt_session_release(rt_session S, uint64_t ticket) {
+  if (!S) return rt::set_error(RT_EINVAL, "session is NULL");
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->reqs.find(ticket);
+  if (it == S->reqs.end()) return rt::set_error(RT_EINVAL, "unknown ticket");
+  if (it->second->state < 2) return rt::set_error(RT_EBUSY, "request still queued or running");
+  delete it->second;
+  S->reqs.erase(it);
+  return RT_OK;
 }
 
 int rt_session_stats_get(rt_session S, rt_session_stats* st) {

@@ -39,7 +39,7 @@ EXPORTS = ["rt_version", "rt_launch_count", "rt_last_error", "rt_scene_upload", 
            "rt_trace_closest_host", "rt_trace_closest_noalloc", "rt_ray_count", "rt_gen_rays",
            "rt_reflect", "rt_batch_create", "rt_batch_run", "rt_batch_stats_get", "rt_batch_order",
            "rt_batch_visibility", "rt_batch_destroy", "rt_session_create", "rt_session_add_scene",
-           "rt_session_submit", "rt_session_poll", "rt_session_wait", "rt_session_stats_get",
+           "rt_session_submit", "rt_session_poll", "rt_session_wait", "rt_session_release", "rt_session_stats_get",
            "rt_session_destroy", "rt_scene_set_split_events", "rt_autotune", "rt_debug_inject",
            "rt_rxset_create", "rt_rxset_destroy", "rt_receive", "rt_batch_received", "rt_abi_struct_sizes"]
 
@@ -164,6 +164,7 @@ def lib(build: bool = True):
             L.rt_session_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
             L.rt_session_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)]
             L.rt_session_wait.argtypes = [vp, ctypes.c_uint64, i64]
+            L.rt_session_release.argtypes = [vp, ctypes.c_uint64]
             L.rt_session_stats_get.argtypes = [vp, ctypes.POINTER(SessionStats)]
             L.rt_session_destroy.argtypes = [vp]
             L.rt_rxset_create.argtypes = [vp, i32, ctypes.c_float, ctypes.POINTER(vp)]
@@ -597,6 +598,12 @@ class Session:
 
     def result(self, ticket):
         hits, counts, mo = self._keep[ticket]
+        return hits, counts[: mo + 1]
+
+    def release(self, ticket):
+        """Forget a finished request (rt_session_release); returns its results."""
+        _check(lib().rt_session_release(self._h, ticket))
+        hits, counts, mo = self._keep.pop(ticket)
         return hits, counts[: mo + 1]
 
     def stats(self) -> dict:

@@ -56,6 +56,8 @@ def test_new_entry_points_reject_null_without_gpu():
     assert lib.rt_scene_set_split_events(None, None, None) == -1
     assert lib.rt_autotune(None, None, None, 0, 1.0, None, None) == -1
     assert b"NULL" in lib.rt_last_error()
+    assert lib.rt_session_release(None, 1) == -1
+    assert b"NULL" in lib.rt_last_error()
 
 
 def test_debug_hooks_validate_without_gpu():

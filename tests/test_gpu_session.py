@@ -96,3 +96,26 @@ def test_session_admission_is_bounded_by_memory(rb, world):
         sess.wait(987654, timeout_s=1)
     assert e.value.code == -1
     sess.destroy()
+
+
+def test_session_release_forgets_finished_requests(rb, world):
+    sess = rb.Session(pool_bytes=1 << 30, max_slots=2)   # the 2M-ray request needs about 0.4 GB
+    sid = sess.add_scene(world[3][1])
+    small = sess.submit(sid, (250.0, 250.0, 30.0), rb.RT_RAYS_FIBONACCI, 5000, 1, 500.0)
+    sess.wait(small, timeout_s=60)
+    h0, c0 = sess.result(small)
+    h, c = sess.release(small)            # results stay with the caller
+    assert h is h0 and np.array_equal(c, c0) and c[0] == 5000
+    for call in (lambda: sess.poll(small), lambda: sess.wait(small, timeout_s=1), lambda: sess.release(small)):
+        with pytest.raises(rb.RtError) as e:
+            call()
+        assert e.value.code == -1             # the ticket is unknown once released
+    big = sess.submit(sid, (250.0, 250.0, 30.0), rb.RT_RAYS_FIBONACCI, 1 << 21, 2, 500.0, want_hits=False)
+    with pytest.raises(rb.RtError) as e:     # 2M rays and two bounces cannot be done already
+        sess.release(big)
+    assert e.value.code == -6
+    sess.wait(big, timeout_s=120)
+    sess.release(big)
+    st = sess.stats()
+    assert st["completed"] == 2 and st["failed"] == 0 and st["p99_ms"] >= st["p50_ms"] > 0
+    sess.destroy()
