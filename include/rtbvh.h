@@ -409,7 +409,11 @@ int rt_batch_create(rt_scene scene, const rt_batch_desc* desc, rt_batch* out);
  * (rt_reflect) and trace the survivors (counts never leave the device),
  * then the visibility segments (rt_trace_any).  Work runs on the batch's
  * own stream; `stream` waits for it.  Results stay valid until the next run
- * starts.  Errors: RT_EINVAL, RT_ENOTBUILT, RT_ECUDA. */
+ * starts.  With use_graph the second run captures the pipeline and later
+ * runs replay it; the scene may be updated and rebuilt between runs (not
+ * during one), and a run after a change that moved the scene's arrays or
+ * changed its tree size captures the pipeline again.
+ * Errors: RT_EINVAL, RT_ENOTBUILT, RT_ECUDA. */
 int rt_batch_run(rt_batch batch, void* stream);
 
 /* Synchronous: wait for `stream` and the batch, report counts. */

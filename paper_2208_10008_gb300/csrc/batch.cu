@@ -12,8 +12,10 @@
 // Eq. 4), each ray with the angular spacing of its own transmitter's launch.
 #include <cuda_runtime.h>
 
+#include <array>
 #include <climits>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -42,6 +44,7 @@ struct rt_batch_s {
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  std::array<uintptr_t, 8> graph_scene{};  // scene state the graph was captured with
   int runs = 0;
   long long graph_kernels = 0;  // kernels in the captured graph
   // reception (Eq. 4)
@@ -85,6 +88,22 @@ __global__ void k_delta_gather(const float* __restrict__ prev, const int* __rest
   out[i] = __ldg(prev + __ldg(src + i));
 }
 
+// What a captured pipeline takes from the scene as launch arguments: the
+// arrays the walk and the bounce read and the size of the current tree.  A
+// re-upload that grows the scene, the first quantised build or a rebuild
+// over another range changes it; the graph is then captured again.
+std::array<uintptr_t, 8> scene_key(const rt_scene_s* s) {
+  return {(uintptr_t)s->tri_in, (uintptr_t)s->node2,  (uintptr_t)s->wide, (uintptr_t)s->qwide,
+          (uintptr_t)s->link2,  (uintptr_t)s->tri_leaf, (uintptr_t)s->ctl, (uintptr_t)s->n_built};
+}
+
+void drop_graph(rt_batch_s* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+}
+
 void free_batch(rt_batch_s* b) {
   if (b->rxset) rt_rxset_destroy(b->rxset);
   for (int k = 0; k <= RT_BATCH_MAX_ORDER; ++k) {
@@ -101,8 +120,7 @@ void free_batch(rt_batch_s* b) {
   void* p[] = {b->counts, b->blocks, b->seg, b->occl, b->scr.counter, b->scr.queue, b->scr.cand};
   for (void* q : p)
     if (q) cudaFree(q);
-  if (b->exec) cudaGraphExecDestroy(b->exec);
-  if (b->graph) cudaGraphDestroy(b->graph);
+  drop_graph(b);
   if (b->ev_in) cudaEventDestroy(b->ev_in);
   if (b->ev_out) cudaEventDestroy(b->ev_out);
   if (b->st) cudaStreamDestroy(b->st);
@@ -312,7 +330,11 @@ int rt_batch_run(rt_batch b, void* stream) {
     if (!b->use_graph || b->runs == 0) {
       e = enqueue(b);  // the first run also initialises lazily loaded tables
     } else {
-      if (!b->exec) {
+      if (b->exec && b->graph_scene != scene_key(b->scene)) {
+        e = cudaStreamSynchronize(b->st);  // the last replay may still run
+        drop_graph(b);
+      }
+      if (e == cudaSuccess && !b->exec) {
         e = cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
           const unsigned long long c0 = rt_launch_count();
@@ -323,6 +345,11 @@ int rt_batch_run(rt_batch b, void* stream) {
           if (e2 != cudaSuccess) e = e2;
         }
         if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+        if (e == cudaSuccess) {
+          b->graph_scene = scene_key(b->scene);
+        } else {
+          drop_graph(b);
+        }
       }
       if (e == cudaSuccess) {
         e = cudaGraphLaunch(b->exec, b->st);

@@ -94,3 +94,29 @@ def test_batch_equals_per_call_path_and_is_repeatable(rb):
             m = int(c.item())
             cur, skip = nr[:m].contiguous(), ns[:m].contiguous()
     b.destroy()
+
+
+def test_batch_graph_follows_a_grown_scene(rb):
+    sc, s, tx, counts, rx = _setup(rb, seed=5)
+    b = rb.Batch(s, tx, counts, rb.RT_RAYS_FIBONACCI, max_order=2, tmax=800.0, rx_pos=rx)
+    for _ in range(3):                  # eager run, capture run, replay
+        b.run()
+    torch.cuda.synchronize()
+    # about 3000 triangles instead of 770: every per-triangle array of the scene moves
+    big = scenes.medium_city(seed=7, n_buildings=150, size=200.0)
+    assert len(big.tris) > 2 * len(sc.tris)
+    rb.rt_scene_update(s, big.tris)
+    rb.rt_bvh_build(s, alpha=0.7, source=tuple(tx.mean(0)), max_leaf=4, dist_norm=1)
+    for _ in range(2):                  # captured again, then replayed
+        b.run()
+    torch.cuda.synchronize()
+    got = [b.order(k)[1].clone() for k in range(3)]
+    vis = b.visibility().clone()
+    fresh = rb.Batch(s, tx, counts, rb.RT_RAYS_FIBONACCI, max_order=2, tmax=800.0, rx_pos=rx, use_graph=False)
+    fresh.run()
+    torch.cuda.synchronize()
+    for k in range(3):
+        assert torch.equal(got[k].view(torch.int32), fresh.order(k)[1].view(torch.int32))
+    assert torch.equal(vis, fresh.visibility())
+    b.destroy()
+    fresh.destroy()
