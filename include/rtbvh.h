@@ -258,8 +258,9 @@ int rt_trace_any(rt_scene scene, const rt_ray* rays_dev, int64_t n, uint8_t* occ
  * rays in chunks to device staging buffers, traces them and copies hits
  * back, overlapping the copies of one chunk with the tracing of another.
  * Synchronous with respect to the host buffers: on return, hits_host is
- * filled.  Of params (nullable) only flags and block are read; the
- * device-pointer fields are ignored.  Errors as rt_trace_closest. */
+ * filled.  Of params (nullable) flags and block are used; skip_tri_dev and
+ * stats_dev must be NULL and n_flagged_dev is not written.
+ * Errors as rt_trace_closest. */
 int rt_trace_closest_host(rt_scene scene, const rt_ray* rays_host, int64_t n, rt_hit* hits_host,
                           const rt_trace_params* params, void* stream);
 

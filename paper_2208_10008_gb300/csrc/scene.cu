@@ -537,6 +537,10 @@ int rt_trace_closest_host(rt_scene s, const rt_ray* rays_host, int64_t n, rt_hit
   if (!s->built) return fail(RT_ENOTBUILT, "BVH not built");
   if (params && (params->skip_tri_dev || params->stats_dev))
     return fail(RT_EINVAL, "per-ray device arrays are not supported with host buffers");
+  if (params && params->block != 0 && params->block != 64 && params->block != 128 && params->block != 256)
+    return fail(RT_EINVAL, "block must be 0, 64, 128 or 256");
+  if (params && (params->flags & RT_QUANTIZED_NODES) && !s->q_built)
+    return fail(RT_EINVAL, "RT_QUANTIZED_NODES needs a build with quantize = 1");
   if (n == 0) return RT_OK;
   const int64_t chunk = n < (int64_t(1) << 18) ? n : (int64_t(1) << 18);
   if (s->stage_cap < chunk) {
@@ -558,7 +562,7 @@ int rt_trace_closest_host(rt_scene s, const rt_ray* rays_host, int64_t n, rt_hit
   for (int k = 0; k < 2; ++k) cudaStreamWaitEvent(s->host_streams[k], ev, 0);
   cudaEventDestroy(ev);
   rt_trace_params tp{};
-  if (params) {  // the device-pointer fields are per-ray arrays of the device paths: not used here
+  if (params) {  // n_flagged_dev counts one call of the device path: not written here
     tp.flags = params->flags;
     tp.block = params->block;
   }

@@ -393,19 +393,28 @@ def rt_trace_closest_host(scene: Scene, rays_host, hits_host=None, flags=0, stre
     """Closest hit with host buffers (pinned torch tensors or numpy arrays)."""
     import torch
     if isinstance(rays_host, torch.Tensor):
-        if rays_host.is_cuda or rays_host.dtype != torch.float32 or not rays_host.is_contiguous():
-            raise TypeError("rays_host must be a contiguous host float32 tensor")
+        if rays_host.is_cuda or rays_host.dtype != torch.float32 or not rays_host.is_contiguous() \
+                or rays_host.dim() != 2 or rays_host.shape[1] != 8:
+            raise TypeError("rays_host must be a contiguous host float32 tensor [n, 8]")
         n = rays_host.shape[0]
         rp = ctypes.c_void_p(rays_host.data_ptr())
         if hits_host is None:
             hits_host = torch.empty((n, 4), dtype=torch.float32, pin_memory=True)
+        if not isinstance(hits_host, torch.Tensor) or hits_host.is_cuda or hits_host.dtype != torch.float32 \
+                or not hits_host.is_contiguous() or hits_host.numel() < 4 * n:
+            raise TypeError("hits_host must be a contiguous host float32 tensor of at least [n, 4]")
         hp = ctypes.c_void_p(hits_host.data_ptr())
     else:
         a = np.ascontiguousarray(rays_host, dtype=np.float32)
+        if a.ndim != 2 or a.shape[1] != 8:
+            raise TypeError("rays_host must be [n, 8] (o.xyz, tmin, d.xyz, tmax)")
         n = a.shape[0]
         rp = a.ctypes.data_as(ctypes.c_void_p)
         if hits_host is None:
             hits_host = np.empty((n, 4), np.float32)
+        if not isinstance(hits_host, np.ndarray) or hits_host.dtype != np.float32 \
+                or not hits_host.flags.c_contiguous or hits_host.size < 4 * n:
+            raise TypeError("hits_host must be a C-contiguous float32 array of at least [n, 4]")
         hp = hits_host.ctypes.data_as(ctypes.c_void_p)
     tp = TraceParams()
     tp.flags = int(flags)

@@ -106,3 +106,26 @@ def test_build_params_marshalling_without_gpu():
     assert abs(p.alpha - 0.7) < 1e-7 and list(p.source) == [1.0, 2.0, 3.0]
     assert (p.max_leaf, p.bins, p.width, p.dist_norm) == (6, 8, 4, 1) and p.range == 250.0
     assert rtbvh.build_params().range == 0.0
+
+
+def test_host_trace_binding_rejects_malformed_buffers_without_gpu():
+    """The host-buffer binding checks shapes and types before any library call
+    (a short hit buffer would otherwise be overrun on the host)."""
+    import numpy as np
+    import pytest
+    import torch
+    bad = [
+        (np.zeros((4, 9), np.float32), None),                     # not [n, 8]
+        (np.zeros(32, np.float32), None),                         # flat
+        (np.zeros((4, 8), np.float32), np.zeros((3, 4), np.float32)),   # hits too short
+        (np.zeros((4, 8), np.float32), np.zeros((4, 4), np.float64)),   # wrong dtype
+        (np.zeros((4, 8), np.float32), np.zeros((4, 8), np.float32)[:, ::2]),  # strided
+        (torch.zeros(4, 9), None),
+        (torch.zeros(4, 8, dtype=torch.float64), None),
+        (torch.zeros(4, 8), torch.zeros(3, 4)),
+        (torch.zeros(4, 8), torch.zeros(4, 4, dtype=torch.int32)),
+        (torch.zeros(4, 8), np.zeros((4, 4), np.float32)),        # mixed kinds
+    ]
+    for rays, hits in bad:
+        with pytest.raises(TypeError):
+            rtbvh.rt_trace_closest_host(None, rays, hits)
