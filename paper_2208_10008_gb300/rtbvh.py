@@ -186,7 +186,9 @@ def _stream(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def _dev_ptr(t, dtype, cols=None, name="tensor"):
+def _dev_ptr(t, dtype, cols=None, name="tensor", rows=0):
+    """Raw pointer of a contiguous CUDA tensor: [>= rows, cols] when cols is
+    given, else at least `rows` elements (the library writes that many)."""
     import torch
     if not (isinstance(t, torch.Tensor) and t.is_cuda):
         raise TypeError("%s must be a CUDA tensor" % name)
@@ -194,6 +196,8 @@ def _dev_ptr(t, dtype, cols=None, name="tensor"):
         raise TypeError("%s must be contiguous %s" % (name, dtype))
     if cols is not None and (t.dim() != 2 or t.shape[1] != cols):
         raise TypeError("%s must have shape [n, %d]" % (name, cols))
+    if (t.shape[0] if cols is not None else t.numel()) < rows:
+        raise TypeError("%s holds fewer than %d %s" % (name, rows, "rows" if cols is not None else "elements"))
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -342,7 +346,7 @@ def _trace_params(flags, skip, stats, n_flagged, n, block=0):
         tp.stats_dev = _dev_ptr(stats, torch.int32, 2, "stats").value
         tp.flags |= RT_COUNT_STATS
     if n_flagged is not None:
-        tp.n_flagged_dev = _dev_ptr(n_flagged, torch.int32, None, "n_flagged").value
+        tp.n_flagged_dev = _dev_ptr(n_flagged, torch.int32, None, "n_flagged", 1).value
     return tp
 
 
@@ -354,7 +358,7 @@ def rt_trace_closest(scene: Scene, rays, hits=None, skip=None, flags=0, stats=No
     n = rays.shape[0]
     if hits is None:
         hits = torch.empty((n, 4), dtype=torch.float32, device=rays.device)
-    hp = _dev_ptr(hits, torch.float32, 4, "hits")
+    hp = _dev_ptr(hits, torch.float32, 4, "hits", n)
     tp = _trace_params(flags, skip, stats, n_flagged, n, block)
     _check(lib().rt_trace_closest(scene.handle, rp, n, hp, ctypes.byref(tp), _stream(stream)))
     return hits
@@ -364,7 +368,7 @@ def rt_trace_closest_noalloc(scene: Scene, rays, hits, flags=0, stream=None):
     """Closest hit without device allocation (n <= RT_NOALLOC_MAX_RAYS); hits is caller-provided."""
     import torch
     rp = _dev_ptr(rays, torch.float32, 8, "rays")
-    hp = _dev_ptr(hits, torch.float32, 4, "hits")
+    hp = _dev_ptr(hits, torch.float32, 4, "hits", rays.shape[0])
     tp = TraceParams()
     tp.flags = int(flags)
     _check(lib().rt_trace_closest_noalloc(scene.handle, rp, rays.shape[0], hp, ctypes.byref(tp),
@@ -383,7 +387,7 @@ def rt_trace_any(scene: Scene, rays, occluded=None, skip=None, flags=0, stats=No
     n = rays.shape[0]
     if occluded is None:
         occluded = torch.empty((n,), dtype=torch.uint8, device=rays.device)
-    op = _dev_ptr(occluded, torch.uint8, None, "occluded")
+    op = _dev_ptr(occluded, torch.uint8, None, "occluded", n)
     tp = _trace_params(flags, skip, stats, n_flagged, n, block)
     _check(lib().rt_trace_any(scene.handle, rp, n, op, ctypes.byref(tp), _stream(stream)))
     return occluded
@@ -466,11 +470,11 @@ def rt_reflect(scene: Scene, rays, hits, out_rays=None, out_skip=None, out_src=N
     if out_count is None:
         out_count = torch.zeros((1,), dtype=torch.int32, device=dev)
     _check(lib().rt_reflect(scene.handle, _dev_ptr(rays, torch.float32, 8, "rays"),
-                            _dev_ptr(hits, torch.float32, 4, "hits"), n,
-                            _dev_ptr(out_rays, torch.float32, 8, "out_rays"),
-                            _dev_ptr(out_skip, torch.int32, None, "out_skip"),
-                            _dev_ptr(out_src, torch.int32, None, "out_src"),
-                            _dev_ptr(out_count, torch.int32, None, "out_count"), _stream(stream)))
+                            _dev_ptr(hits, torch.float32, 4, "hits", n), n,
+                            _dev_ptr(out_rays, torch.float32, 8, "out_rays", n),
+                            _dev_ptr(out_skip, torch.int32, None, "out_skip", n),
+                            _dev_ptr(out_src, torch.int32, None, "out_src", n),
+                            _dev_ptr(out_count, torch.int32, None, "out_count", 1), _stream(stream)))
     return out_rays, out_skip, out_src, out_count
 
 
@@ -677,17 +681,17 @@ def rt_receive(rs: RxSet, rays, hits, delta, range0, out=None, count=None, n_dev
     added to it."""
     import torch
     rp = _dev_ptr(rays, torch.float32, 8, "rays")
-    hp = _dev_ptr(hits, torch.float32, 4, "hits")
     n = rays.shape[0]
+    hp = _dev_ptr(hits, torch.float32, 4, "hits", n)
     if out is None:
         out = torch.empty((max_records if max_records is not None else max(1024, n // 4), 4), dtype=torch.int32,
                           device=rays.device)
     op = _dev_ptr(out, torch.int32, 4, "out")
     if count is None:
         count = torch.zeros(1, dtype=torch.int32, device=rays.device)
-    cp = _dev_ptr(count, torch.int32, None, "count")
-    nd = None if n_dev is None else _dev_ptr(n_dev, torch.int32, None, "n_dev")
-    sp = None if stats is None else _dev_ptr(stats, torch.int64, None, "stats").value
+    cp = _dev_ptr(count, torch.int32, None, "count", 1)
+    nd = None if n_dev is None else _dev_ptr(n_dev, torch.int32, None, "n_dev", 1)
+    sp = None if stats is None else _dev_ptr(stats, torch.int64, None, "stats", 2).value
     p = ReceiveParams(float(delta), float(range0), int(out.shape[0]), 0, sp, None)
     _check(lib().rt_receive(rs.handle, rp, hp, n, nd, ctypes.byref(p), op, cp, _stream(stream)))
     return out, count

@@ -306,3 +306,30 @@ def test_errors(rb):
         rb.rt_bvh_build(s, max_leaf=16)
     with pytest.raises(rb.RtError):
         rb.rt_bvh_build(s, bins=2)
+
+
+def test_binding_rejects_short_output_buffers(rb):
+    """A caller's output buffer smaller than the call writes is refused before
+    the library is called (the kernels would write past its end)."""
+    sc, rays, p = scenes.workload_tiny()
+    s, _ = build(rb, sc.tris, alpha=1.0)
+    r = dev(rays)
+    n = r.shape[0]
+    f32, i32 = dict(dtype=torch.float32, device="cuda"), dict(dtype=torch.int32, device="cuda")
+    short = [
+        lambda: rb.rt_trace_closest(s, r, torch.empty((n - 1, 4), **f32)),
+        lambda: rb.rt_trace_closest(s, r, n_flagged=torch.empty(0, **i32)),
+        lambda: rb.rt_trace_any(s, r, torch.empty(n - 1, dtype=torch.uint8, device="cuda")),
+        lambda: rb.rt_trace_closest_noalloc(s, r[:16], torch.empty((15, 4), **f32)),
+        lambda: rb.rt_reflect(s, r, torch.empty((n - 1, 4), **f32)),
+        lambda: rb.rt_reflect(s, r, torch.empty((n, 4), **f32), out_rays=torch.empty((n - 1, 8), **f32)),
+        lambda: rb.rt_reflect(s, r, torch.empty((n, 4), **f32), out_count=torch.empty(0, **i32)),
+    ]
+    for call in short:
+        with pytest.raises(TypeError):
+            call()
+    rs = rb.rt_rxset_create(np.array([[100.0, 100.0, 2.0]]), 1.0)
+    with pytest.raises(TypeError):
+        rb.rt_receive(rs, r, torch.empty((n - 1, 4), **f32), 0.01, 100.0)
+    rs.destroy()
+    s.destroy()
