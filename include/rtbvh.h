@@ -325,8 +325,8 @@ typedef struct {
 /* Receivers: rx_host = m * 3 floats (x, y, z), copied to the device into a
  * uniform grid in which every receiver is entered into each cell its largest
  * receiving sphere (radius r_max) overlaps.  Synchronous.  Errors:
- * RT_EINVAL (NULL, m < 1, r_max not positive and finite, non-finite
- * position), RT_ENOMEM, RT_ECUDA. */
+ * RT_EINVAL (NULL, m outside 1..2^26, r_max not positive and finite,
+ * non-finite position), RT_ENOMEM, RT_ECUDA. */
 int rt_rxset_create(const float* rx_host, int32_t m, float r_max, rt_rxset* out);
 
 /* Free a receiver set (synchronous). */

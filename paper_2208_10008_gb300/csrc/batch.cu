@@ -189,7 +189,7 @@ cudaError_t alloc(T** p, long long n) {
 
 extern "C" {
 
-int rt_batch_create(rt_scene scene, const rt_batch_desc* d, rt_batch* out) {
+static int rt_batch_create_body(rt_scene scene, const rt_batch_desc* d, rt_batch* out) {
   if (!out || !scene || !d) return rt::set_error(RT_EINVAL, "NULL argument");
   *out = nullptr;
   if (d->n_tx < 1 || !d->tx_pos || !d->tx_param) return rt::set_error(RT_EINVAL, "need at least one transmitter");
@@ -202,6 +202,15 @@ int rt_batch_create(rt_scene scene, const rt_batch_desc* d, rt_batch* out) {
     return rt::set_error(RT_EINVAL, "reception needs receivers and max_rx_records >= 1");
   rt_batch_s* b = new (std::nothrow) rt_batch_s();
   if (!b) return rt::set_error(RT_ENOMEM, "host allocation failed");
+  struct Undo {  // frees the half-made batch on every early return or exception
+    rt_batch_s* b;
+    ~Undo() {
+      if (b) {
+        free_batch(b);
+        delete b;
+      }
+    }
+  } undo{b};
   b->scene = scene;
   b->n_tx = d->n_tx;
   b->kind = d->dir_kind;
@@ -209,28 +218,20 @@ int rt_batch_create(rt_scene scene, const rt_batch_desc* d, rt_batch* out) {
   b->n_rx = d->n_rx;
   b->tmax = d->tmax;
   b->use_graph = d->use_graph != 0;
-  if (d->ray_tile != 0 && d->ray_tile != 64 && d->ray_tile != 128 && d->ray_tile != 256) {
-    delete b;
+  if (d->ray_tile != 0 && d->ray_tile != 64 && d->ray_tile != 128 && d->ray_tile != 256)
     return rt::set_error(RT_EINVAL, "ray_tile must be 0, 64, 128 or 256");
-  }
   b->ray_tile = d->ray_tile;
   b->tx.assign(d->tx_pos, d->tx_pos + 3 * d->n_tx);
   long long total = 0;
   for (int t = 0; t < d->n_tx; ++t) {
     const long long c = rt_ray_count(d->dir_kind, d->tx_param[t]);
-    if (c < 0) {
-      delete b;
-      return rt::set_error(RT_EINVAL, "bad ray count for a transmitter");
-    }
+    if (c < 0) return rt::set_error(RT_EINVAL, "bad ray count for a transmitter");
     b->param.push_back(d->tx_param[t]);
     b->count.push_back(c);
     b->offset.push_back(total);
     total += c;
   }
-  if (total < 1 || total > INT_MAX) {
-    delete b;
-    return rt::set_error(RT_EINVAL, "total ray count out of range");
-  }
+  if (total < 1 || total > INT_MAX) return rt::set_error(RT_EINVAL, "total ray count out of range");
   b->n0 = total;
   b->n_seg = (long long)d->n_tx * d->n_rx;
   cudaError_t e = cudaSuccess;
@@ -270,11 +271,7 @@ int rt_batch_create(rt_scene scene, const rt_batch_desc* d, rt_batch* out) {
       double v = d->rx_delta ? (double)d->rx_delta[t]
                              : (b->kind == RT_RAYS_ICOSPHERE ? std::atan(2.0) / std::ldexp(1.0, (int)b->param[t])
                                                               : std::sqrt(4.0 * M_PI / (double)b->count[t]));
-      if (!(v > 0.0) || !std::isfinite(v)) {
-        free_batch(b);
-        delete b;
-        return rt::set_error(RT_EINVAL, "bad delta for a transmitter");
-      }
+      if (!(v > 0.0) || !std::isfinite(v)) return rt::set_error(RT_EINVAL, "bad delta for a transmitter");
       dtx[t] = (float)v;
       b->dmax = std::max(b->dmax, dtx[t]);
     }
@@ -282,11 +279,7 @@ int rt_batch_create(rt_scene scene, const rt_batch_desc* d, rt_batch* out) {
     b->max_rx = d->max_rx_records;
     const int rc = rt_rxset_create(d->rx_pos, d->n_rx, (float)(b->tmax * (double)b->dmax / std::sqrt(3.0)) * 1.0001f,
                                    &b->rxset);
-    if (rc != RT_OK) {
-      free_batch(b);
-      delete b;
-      return rc;  // the set's own message stays in rt_last_error
-    }
+    if (rc != RT_OK) return rc;  // the set's own message stays in rt_last_error
     for (int k = 0; k <= b->max_order && e == cudaSuccess; ++k) {
       e = alloc(&b->delta[k], total);
       if (e == cudaSuccess) e = alloc(&b->rec[k], b->max_rx);
@@ -312,13 +305,16 @@ int rt_batch_create(rt_scene scene, const rt_batch_desc* d, rt_batch* out) {
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
   if (e != cudaSuccess) {
-    free_batch(b);
-    delete b;
     cudaGetLastError();
     return rt::set_error(e == cudaErrorMemoryAllocation ? RT_ENOMEM : RT_ECUDA, cudaGetErrorString(e));
   }
+  undo.b = nullptr;
   *out = b;
   return RT_OK;
+}
+
+int rt_batch_create(rt_scene scene, const rt_batch_desc* d, rt_batch* out) {
+  return rt::abi_guard([&] { return rt_batch_create_body(scene, d, out); });
 }
 
 int rt_batch_run(rt_batch b, void* stream) {
@@ -367,7 +363,7 @@ int rt_batch_run(rt_batch b, void* stream) {
   return RT_OK;
 }
 
-int rt_batch_stats_get(rt_batch b, void* stream, rt_batch_stats* s) {
+static int rt_batch_stats_get_body(rt_batch b, void* stream, rt_batch_stats* s) {
   if (!b || !s) return rt::set_error(RT_EINVAL, "NULL argument");
   if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess || cudaStreamSynchronize(b->st) != cudaSuccess)
     return rt::set_error(RT_ECUDA, "synchronize");
@@ -399,6 +395,10 @@ int rt_batch_stats_get(rt_batch b, void* stream, rt_batch_stats* s) {
   s->flagged = fl;
   s->segments = b->n_seg;
   return RT_OK;
+}
+
+int rt_batch_stats_get(rt_batch b, void* stream, rt_batch_stats* s) {
+  return rt::abi_guard([&] { return rt_batch_stats_get_body(b, stream, s); });
 }
 
 int rt_batch_order(rt_batch b, int order, const rt_ray** rays, const rt_hit** hits, const int32_t** src,

@@ -178,10 +178,11 @@ __global__ void __launch_bounds__(kRecvBlock) k_receive(RecvArgs A) {
 
 }  // namespace
 
-extern "C" int rt_rxset_create(const float* rx, int32_t m, float r_max, rt_rxset* out) {
+static int rt_rxset_create_body(const float* rx, int32_t m, float r_max, rt_rxset* out) {
   if (!rx || !out) return rt::set_error(RT_EINVAL, "NULL argument");
   *out = nullptr;
-  if (m < 1) return rt::set_error(RT_EINVAL, "m must be >= 1");
+  // each receiver lands in at most 8 cells: 2^26 keeps the int cell offsets exact
+  if (m < 1 || m > (1 << 26)) return rt::set_error(RT_EINVAL, "m must be 1..2^26");
   if (!(r_max > 0.f) || !std::isfinite(r_max)) return rt::set_error(RT_EINVAL, "r_max must be positive and finite");
   double lo[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
   for (int32_t j = 0; j < m; ++j)
@@ -208,6 +209,12 @@ extern "C" int rt_rxset_create(const float* rx, int32_t m, float r_max, rt_rxset
   }
   const double R = R0 + 1e-3 * h;  // insertion radius: the sphere plus a rounding margin
   rt_rxset_s* s = new rt_rxset_s();
+  struct Undo {  // frees the half-made set on an error return or exception
+    rt_rxset_s* s;
+    ~Undo() {
+      if (s) rt_rxset_destroy(s);
+    }
+  } undo{s};
   s->h = (float)h;
   s->m = m;
   s->r_max = r_max;
@@ -242,12 +249,15 @@ extern "C" int rt_rxset_create(const float* rx, int32_t m, float r_max, rt_rxset
   if (e == cudaSuccess) e = cudaMemcpy(s->cell_start, start.data(), (ncell + 1) * sizeof(int), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(s->items, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(s->pos, pos.data(), m * sizeof(float4), cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) {
-    rt_rxset_destroy(s);
+  if (e != cudaSuccess)
     return rt::set_error(e == cudaErrorMemoryAllocation ? RT_ENOMEM : RT_ECUDA, cudaGetErrorString(e));
-  }
+  undo.s = nullptr;
   *out = s;
   return RT_OK;
+}
+
+extern "C" int rt_rxset_create(const float* rx, int32_t m, float r_max, rt_rxset* out) {
+  return rt::abi_guard([&] { return rt_rxset_create_body(rx, m, r_max, out); });
 }
 
 extern "C" int rt_rxset_destroy(rt_rxset s) {

@@ -18,9 +18,31 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <exception>
+#include <new>
+
 #include "rtbvh.h"
 
 namespace rt {
+
+// Sets the calling thread's rt_last_error message; returns code.
+int set_error(int code, const char* msg);
+
+// Runs the body of a C-ABI entry point that allocates host memory: a C++
+// exception (a failed allocation) becomes an error code instead of crossing
+// the C ABI, where it would terminate the caller.
+template <class F>
+int abi_guard(F&& body) {
+  try {
+    return body();
+  } catch (const std::bad_alloc&) {
+    return set_error(RT_ENOMEM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return set_error(RT_EINTERNAL, e.what());
+  } catch (...) {
+    return set_error(RT_EINTERNAL, "unexpected host exception");
+  }
+}
 
 constexpr int kMaxLeaf = 15;   // leaf refs pack the count in 4 bits
 constexpr int kMaxBins = 32;

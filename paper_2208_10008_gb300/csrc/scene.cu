@@ -346,7 +346,7 @@ int rt_scene_set_split_events(rt_scene s, void* ev_begin, void* ev_end) {
   return RT_OK;
 }
 
-int rt_bvh_info(rt_scene s, void* stream, rt_bvh_info_t* info) {
+static int rt_bvh_info_body(rt_scene s, void* stream, rt_bvh_info_t* info) {
   g_err[0] = 0;
   if (!s || !info) return fail(RT_EINVAL, "NULL argument");
   if (!s->built) return fail(RT_ENOTBUILT, "BVH not built");
@@ -391,7 +391,11 @@ int rt_bvh_info(rt_scene s, void* stream, rt_bvh_info_t* info) {
   return RT_OK;
 }
 
-int rt_bvh_export(rt_scene s, void* stream, int32_t* child, int64_t* leaf_first, int64_t* leaf_count,
+int rt_bvh_info(rt_scene s, void* stream, rt_bvh_info_t* info) {
+  return rt::abi_guard([&] { return rt_bvh_info_body(s, stream, info); });
+}
+
+static int rt_bvh_export_body(rt_scene s, void* stream, int32_t* child, int64_t* leaf_first, int64_t* leaf_count,
                   int32_t* prims, float* boxes) {
   g_err[0] = 0;
   if (!s || !child || !leaf_first || !leaf_count || !prims) return fail(RT_EINVAL, "NULL argument");
@@ -450,6 +454,11 @@ int rt_bvh_export(rt_scene s, void* stream, int32_t* child, int64_t* leaf_first,
     }
   }
   return RT_OK;
+}
+
+int rt_bvh_export(rt_scene s, void* stream, int32_t* child, int64_t* leaf_first, int64_t* leaf_count,
+                  int32_t* prims, float* boxes) {
+  return rt::abi_guard([&] { return rt_bvh_export_body(s, stream, child, leaf_first, leaf_count, prims, boxes); });
 }
 
 static int trace_common(rt_scene s, const rt_ray* rays, int64_t n, rt_hit* hits, uint8_t* occl,

@@ -305,7 +305,7 @@ void worker_loop(rt_session_s* S) {
 
 extern "C" {
 
-int rt_session_create(size_t pool_bytes, int max_slots, rt_session* out) {
+static int rt_session_create_body(size_t pool_bytes, int max_slots, rt_session* out) {
   if (!out) return rt::set_error(RT_EINVAL, "out is NULL");
   *out = nullptr;
   if (max_slots < 1 || max_slots > 64) return rt::set_error(RT_EINVAL, "max_slots must be 1..64");
@@ -319,24 +319,33 @@ int rt_session_create(size_t pool_bytes, int max_slots, rt_session* out) {
     return rt::set_error(e == cudaErrorMemoryAllocation ? RT_ENOMEM : RT_ECUDA, "pool allocation failed");
   }
   cudaGetDevice(&S->device);
-  S->pool.reset(pool_bytes);
-  S->slots.resize(max_slots);
-  for (Slot& sl : S->slots) {
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&sl.pinned_counts, (RT_BATCH_MAX_ORDER + 1) * sizeof(int));
-  }
-  if (e != cudaSuccess) {
-    cudaGetLastError();
+  try {
+    S->pool.reset(pool_bytes);
+    S->slots.resize(max_slots);
+    for (Slot& sl : S->slots) {
+      if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaMallocHost((void**)&sl.pinned_counts, (RT_BATCH_MAX_ORDER + 1) * sizeof(int));
+    }
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      rt_session_destroy(S);
+      return rt::set_error(RT_ECUDA, "session streams");
+    }
+    S->worker = std::thread(worker_loop, S);
+  } catch (...) {  // no worker is running: free what was made
     rt_session_destroy(S);
-    return rt::set_error(RT_ECUDA, "session streams");
+    throw;
   }
-  S->worker = std::thread(worker_loop, S);
   *out = S;
   return RT_OK;
 }
 
-int rt_session_add_scene(rt_session S, rt_scene scene, int32_t* scene_id) {
+int rt_session_create(size_t pool_bytes, int max_slots, rt_session* out) {
+  return rt::abi_guard([&] { return rt_session_create_body(pool_bytes, max_slots, out); });
+}
+
+static int rt_session_add_scene_body(rt_session S, rt_scene scene, int32_t* scene_id) {
   if (!S || !scene || !scene_id) return rt::set_error(RT_EINVAL, "NULL argument");
   if (!scene->built) return rt::set_error(RT_ENOTBUILT, "build the scene's BVH before adding it");
   std::lock_guard<std::mutex> lk(S->mu);
@@ -345,7 +354,11 @@ int rt_session_add_scene(rt_session S, rt_scene scene, int32_t* scene_id) {
   return RT_OK;
 }
 
-int rt_session_submit(rt_session S, const rt_request* r, uint64_t* ticket) {
+int rt_session_add_scene(rt_session S, rt_scene scene, int32_t* scene_id) {
+  return rt::abi_guard([&] { return rt_session_add_scene_body(S, scene, scene_id); });
+}
+
+static int rt_session_submit_body(rt_session S, const rt_request* r, uint64_t* ticket) {
   if (!S || !r || !ticket) return rt::set_error(RT_EINVAL, "NULL argument");
   const long long n = rt_ray_count(r->dir_kind, r->param);
   if (n < 1 || n > (1 << 30)) return rt::set_error(RT_EINVAL, "bad launch");
@@ -365,15 +378,26 @@ int rt_session_submit(rt_session S, const rt_request* r, uint64_t* ticket) {
     delete q;
     return rt::set_error(RT_ENOMEM, "request larger than the session pool");
   }
-  q->ticket = S->next_ticket++;
+  q->ticket = S->next_ticket;
   q->t_submit = Clock::now();
+  try {
+    S->reqs[q->ticket] = q;
+    S->queue.push_back(q);
+  } catch (...) {  // neither queued nor known: as if never submitted
+    S->reqs.erase(q->ticket);
+    delete q;
+    throw;
+  }
+  ++S->next_ticket;
   if (!S->submitted) S->t_first = q->t_submit;
   ++S->submitted;
-  S->reqs[q->ticket] = q;
-  S->queue.push_back(q);
   *ticket = q->ticket;
   S->cv_work.notify_one();
   return RT_OK;
+}
+
+int rt_session_submit(rt_session S, const rt_request* r, uint64_t* ticket) {
+  return rt::abi_guard([&] { return rt_session_submit_body(S, r, ticket); });
 }
 
 int rt_session_poll(rt_session S, uint64_t ticket, int* done) {
@@ -411,7 +435,7 @@ int rt_session_release(rt_session S, uint64_t ticket) {
   return RT_OK;
 }
 
-int rt_session_stats_get(rt_session S, rt_session_stats* st) {
+static int rt_session_stats_get_body(rt_session S, rt_session_stats* st) {
   if (!S || !st) return rt::set_error(RT_EINVAL, "NULL argument");
   std::lock_guard<std::mutex> lk(S->mu);
   memset(st, 0, sizeof(*st));
@@ -441,6 +465,10 @@ int rt_session_stats_get(rt_session S, rt_session_stats* st) {
     st->span_s = std::chrono::duration<double>(S->t_last - S->t_first).count();
   }
   return RT_OK;
+}
+
+int rt_session_stats_get(rt_session S, rt_session_stats* st) {
+  return rt::abi_guard([&] { return rt_session_stats_get_body(S, st); });
 }
 
 int rt_session_destroy(rt_session S) {

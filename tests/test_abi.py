@@ -76,6 +76,8 @@ def test_reception_entry_points_validate_without_gpu():
     h = ctypes.c_void_p()
     assert lib.rt_rxset_create(None, 2, 1.0, ctypes.byref(h)) == -1
     assert lib.rt_rxset_create(rx, 0, 1.0, ctypes.byref(h)) == -1
+    assert lib.rt_rxset_create(rx, (1 << 26) + 1, 1.0, ctypes.byref(h)) == -1   # checked before rx is read
+    assert b"2^26" in lib.rt_last_error()
     assert lib.rt_rxset_create(rx, 2, 0.0, ctypes.byref(h)) == -1
     assert lib.rt_rxset_create(rx, 2, float("inf"), ctypes.byref(h)) == -1
     bad = (ctypes.c_float * 3)(0, float("nan"), 0)
