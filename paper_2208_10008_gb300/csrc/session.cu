@@ -321,6 +321,7 @@ static int rt_session_create_body(size_t pool_bytes, int max_slots, rt_session* 
   cudaGetDevice(&S->device);
   try {
     S->pool.reset(pool_bytes);
+    S->lat_ms.reserve(kLatencyWindow);  // the worker thread never reallocates it
     S->slots.resize(max_slots);
     for (Slot& sl : S->slots) {
       if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking);
