@@ -273,6 +273,40 @@ def test_eq2_worked_example_tree(orc):
         assert orc.Bvh(tris, alpha=float(alpha_s), source=(0, 0, 0), max_leaf=1).info()["depth"] == depth
 
 
+def _root_left_size(e):
+    def size(c):
+        if c < 0:
+            return int(e["leaf_count"][-1 - c])
+        return size(e["child"][c][0]) + size(e["child"][c][1])
+    return size(e["child"][0][0])
+
+
+def test_eq2_worked_example_scale_free_costs(orc):
+    """Eq. 2 with the scale-free distance term (reading c2): the hand-derived
+    d^2 * k_C / diag(C)^2 of each candidate."""
+    g = json.load(open(os.path.join(GOLDEN, "eq2_worked_example.json")))
+    n1 = g["dist_norm_1"]
+    for c in g["candidates"]:
+        term = n1["term"][str(c["i"])]
+        assert abs(c["d2"] * n1["k_C"] / n1["diag2_C"] - term) < 1e-12
+        for alpha in (1.0, 0.5, 0.4, 0.0):
+            got = orc.eq2_cost(c["box_A"], c["k_A"], c["box_B"], c["k_B"], g["box_C"], alpha, (0, 0, 0), dist_norm=1)
+            want = alpha * c["sah"] + (1 - alpha) * term + 1.0
+            assert abs(got - want) < 1e-12
+
+
+def test_eq2_worked_example_scale_free_split(orc):
+    """The split the scale-free term picks flips between alpha = 0.4 and 0.5,
+    where the raw m^2 term still splits off the nearest triangle."""
+    g = json.load(open(os.path.join(GOLDEN, "eq2_worked_example.json")))
+    tris = np.asarray(g["tris"], np.float32)
+    for alpha_s, i_best in g["dist_norm_1"]["best_split"].items():
+        b = orc.Bvh(tris, alpha=float(alpha_s), source=(0, 0, 0), max_leaf=1, dist_norm=1)
+        assert _root_left_size(b.export()) == i_best, alpha_s
+    raw = orc.Bvh(tris, alpha=0.5, source=(0, 0, 0), max_leaf=1, dist_norm=0)
+    assert _root_left_size(raw.export()) == g["best_split"]["0.5"] == 1
+
+
 def _check_structure(orc, tris, b, max_leaf):
     e = b.export()
     assert sorted(e["prims"].tolist()) == list(range(len(tris)))
