@@ -84,6 +84,20 @@ def job_rate(units_per_rank, world_size, steps, total_ms):
     return world_size * units_per_rank * steps / (total_ms * 1e-3) / 1e6
 
 
+def alu_roofline(nodes_per_ray, tris_per_ray, rays, ms, n_sm, sm_mhz):
+    """Secondary roofline of the walk: FP32 operations at about 20 per child
+    box test (4 children per node) and 40 per triangle test, against one FP32
+    operation per lane per cycle (4 x 32 lanes per SM) at the SM clock."""
+    ops_per_ray = 20.0 * 4.0 * nodes_per_ray + 40.0 * tris_per_ray
+    achieved = ops_per_ray * rays / (ms * 1e-3) / 1e12
+    peak = n_sm * 128 * sm_mhz * 1e6 / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+            "ops_per_ray": ops_per_ray, "kernel": "k_trace + k_retest64 (one rt_trace_closest)",
+            "peak_source": "%d SMs x 128 FP32 lanes x %.0f MHz (median SM clock under load)" % (n_sm, sm_mhz),
+            "note": "estimated operation counts; the walk issues integer, load and stack instructions besides "
+                    "these, so the issue rate (profiled) is higher than this fraction"}
+
+
 # ---------------------------------------------------------------- clocks
 class Clocks:
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -785,6 +799,9 @@ def run_ours(args):
                           "latency of dependent splits, not by bandwidth (events recorded by the library around "
                           "the kernel in every timed step)"}
     dominant_split = mean_split_ms >= mean_trace_ms
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    roof_alu = alu_roofline(nodes_per_ray, tris_per_ray, R, mean_trace_ms, n_sm,
+                            (clk or {}).get("sm_mhz") or 2070.0)
     value = job_rate(R, ws, args.steps, total_ms)
     cpu_v, cores, reps, el = cpu_checker_rate(sc, rays_np, p, args, args.cpu_seconds)
     line = {
@@ -806,6 +823,7 @@ def run_ours(args):
                       "bvh": {k: info[k] for k in ("n_wide", "n_leaves", "depth2", "depth_wide")}},
         "roofline": roof_split if dominant_split else roof_trace,
         "roofline_other": roof_trace if dominant_split else roof_split,
+        "roofline_alu": roof_alu,
         "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": "%d repetitions of the full workload (exact-sweep Eq. 2 build + float64 walk of %d rays) in %.1f s" % (reps, R, el)},
         "e2e": {"value": R / (e2e_step * 1e-3) / 1e6, "unit": UNIT,
