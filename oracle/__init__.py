@@ -11,9 +11,10 @@ paper each function follows.
 
 Pinning status: every function here is pinned by ``tests/test_oracle_pins.py``
 against closed forms, brute force written another way, invariants and
-special cases -- except the alpha < 1 build's tree *shape*, which the paper
-gives no worked example for (parity unpinned: only its invariants and the
-alpha = 1 special case are checked).
+special cases.  The alpha < 1 split choice is pinned on a hand-derived Eq. 2
+example (raw and scale-free distance term); the *shape* of full-size
+alpha < 1 trees is not, as the paper prints no tree (parity unpinned: only
+their invariants and the alpha = 1 special case are checked).
 """
 from __future__ import annotations
 
