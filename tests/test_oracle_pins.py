@@ -307,6 +307,43 @@ def test_eq2_worked_example_scale_free_split(orc):
     assert _root_left_size(raw.export()) == g["best_split"]["0.5"] == 1
 
 
+def _unit_tri(x, y):
+    return [[x, y, 0.0], [x + 1.0, y, 0.0], [x, y + 1.0, 0.0]]
+
+
+def _leaf_prims(e, c):
+    assert c < 0
+    k = -1 - c
+    f, n = int(e["leaf_first"][k]), int(e["leaf_count"][k])
+    return sorted(e["prims"][f:f + n].tolist())
+
+
+def test_split_ties_go_to_the_lowest_axis(orc):
+    """Four flat unit triangles on a 2 x 2 grid (ids 0..3 at (0,0), (2,0),
+    (0,2), (2,2)), alpha = 1.  Cutting the grid along x or along y gives
+    children of area 2*1*3 = 6 with 2 triangles each, SAH = 24/18 for both,
+    from the same operands: an exact tie, which the reading breaks towards
+    the lowest axis.  The x cut keeps {0, 2} together; the y cut would give
+    {0, 1}."""
+    tris = np.asarray([_unit_tri(0, 0), _unit_tri(2, 0), _unit_tri(0, 2), _unit_tri(2, 2)], np.float32)
+    e = orc.Bvh(tris, alpha=1.0, source=(0, 0, 0), max_leaf=2).export()
+    assert len(e["child"]) == 1
+    assert _leaf_prims(e, e["child"][0][0]) == [0, 2] and _leaf_prims(e, e["child"][0][1]) == [1, 3]
+
+
+def test_split_ties_go_to_the_lowest_split_index(orc):
+    """Three flat unit triangles at x = 0, 2, 4 and the source at the centre
+    of symmetry (2.5, 0.5, 0).  Splits after one and after two triangles are
+    mirror images: SAH 2*1 + 6*2 against 6*2 + 2*1 (over 10), distance terms
+    4 + 1 against 1 + 4, equal at every alpha; the reading takes the lower
+    split index, so the left child holds triangle 0 alone."""
+    tris = np.asarray([_unit_tri(0, 0), _unit_tri(2, 0), _unit_tri(4, 0)], np.float32)
+    for alpha in (1.0, 0.5, 0.0):
+        for dn in (0, 1):
+            e = orc.Bvh(tris, alpha=alpha, source=(2.5, 0.5, 0.0), max_leaf=1, dist_norm=dn).export()
+            assert _leaf_prims(e, e["child"][0][0]) == [0], (alpha, dn)
+
+
 def _check_structure(orc, tris, b, max_leaf):
     e = b.export()
     assert sorted(e["prims"].tolist()) == list(range(len(tris)))
