@@ -79,6 +79,21 @@ def test_tri_parallel_and_degenerate_miss(orc):
     assert not orc.tri_hit(TRI, ray((1, 1, 0), (0, 0, 0)))[0]       # zero direction
 
 
+def test_tri_parallel_threshold_scale(orc):
+    """The parallel rule |det| <= 1e-14 |e1||e2||d| on both sides of the
+    threshold.  For a triangle in z = 0 with e1 = (4,0,0), e2 = (0,4,0) and
+    a ray (1, 0, -eps) from height h, det = 16 eps, so the ratio is eps:
+    eps = 1e-8 is a real (grazing) hit at t = h / eps with u = v = 0.25;
+    eps = 1e-15 counts as parallel."""
+    tri0 = np.array([[0, 0, 0], [4, 0, 0], [0, 4, 0]], dtype=np.float32)
+    r = ray((-1.0, 1.0, 2e-8), (1.0, 0.0, -1e-8))
+    hit, t, u, v = orc.tri_hit(tri0, r)
+    t_ref = float(r[2]) / -float(r[6])          # plane z = 0 from the float32 ray
+    assert hit and abs(t - t_ref) <= 1e-9 * t_ref
+    assert abs(u - (-1.0 + t_ref) / 4) < 1e-9 and abs(v - 0.25) < 1e-9
+    assert not orc.tri_hit(tri0, ray((-1.0, 1.0, 2e-15), (1.0, 0.0, -1e-15)))[0]
+
+
 # --------------------------------------------------------------- brute force
 def _solve_brute(tris, rays):
     """Closest hit by solving o + t d = v0 + u e1 + v e2 with numpy.linalg.solve."""
@@ -305,6 +320,34 @@ def test_eq2_worked_example_scale_free_split(orc):
         assert _root_left_size(b.export()) == i_best, alpha_s
     raw = orc.Bvh(tris, alpha=0.5, source=(0, 0, 0), max_leaf=1, dist_norm=0)
     assert _root_left_size(raw.export()) == g["best_split"]["0.5"] == 1
+
+
+def test_eq2_costs_scale_with_t_i_and_t_trav(orc):
+    """Eq. 2 with t_i = 2.5 and t_trav = 0.75 on the worked example: the SAH
+    term scales with t_i, so does the scale-free distance term (it carries
+    k_C t_i), the raw m^2 term does not, and t_trav is added once."""
+    g = json.load(open(os.path.join(GOLDEN, "eq2_worked_example.json")))
+    n1 = g["dist_norm_1"]
+    for c in g["candidates"]:
+        for alpha in (1.0, 0.5, 0.0):
+            for dn, term in ((0, c["d2"]), (1, n1["term"][str(c["i"])] * 2.5)):
+                got = orc.eq2_cost(c["box_A"], c["k_A"], c["box_B"], c["k_B"], g["box_C"], alpha, (0, 0, 0),
+                                   t_i=2.5, t_trav=0.75, dist_norm=dn)
+                want = alpha * 2.5 * c["sah"] + (1 - alpha) * term + 0.75
+                assert abs(got - want) < 1e-12, (c["i"], alpha, dn)
+
+
+def test_t_i_weights_the_raw_split_and_t_trav_does_not(orc):
+    """With the raw m^2 term at alpha = 0.5, t_i = 20 makes the SAH term win:
+    costs 10 SAH + d^2/2 + t_trav = 29.11 / 26.39 / 36.11 for i = 1 / 2 / 3,
+    so the balanced split i = 2 replaces i = 1 (t_i = 1).  t_trav is added to
+    every candidate and never moves the split (reading c3)."""
+    g = json.load(open(os.path.join(GOLDEN, "eq2_worked_example.json")))
+    tris = np.asarray(g["tris"], np.float32)
+    def left(**kw):
+        return _root_left_size(orc.Bvh(tris, alpha=0.5, source=(0, 0, 0), max_leaf=1, **kw).export())
+    assert left(t_i=1.0) == 1 and left(t_i=20.0) == 2
+    assert left(t_i=1.0, t_trav=7.0) == 1 and left(t_i=20.0, t_trav=0.0) == 2
 
 
 def _unit_tri(x, y):
