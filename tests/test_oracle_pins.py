@@ -387,6 +387,25 @@ def test_split_ties_go_to_the_lowest_split_index(orc):
             assert _leaf_prims(e, e["child"][0][0]) == [0], (alpha, dn)
 
 
+def test_split_candidates_follow_the_centroid_order_ties_by_id(orc):
+    """Candidates are the prefixes of the triangles sorted by centroid on
+    each axis, equal centroids in id order.  Triangles in planes x = const:
+    t0 at (0,0,0), t1 at (0,5,5) (same x as t0), t2 at (10,10,10); raw
+    distance term, alpha = 0, source at t1's box centre (0, 5.5, 5.5).
+    Every axis then offers {t0}|{t1,t2} (d^2 = (50 + 37.5)/2, cost 44.75)
+    and {t0,t1}|{t2} ((12.5 + 150)/2, cost 82.25), so t0 is split off.  The
+    cheaper {t1}|{t0,t2} ((0 + 25)/2, cost 13.5) would be a candidate only
+    if t1 came before t0 on x."""
+    def tri(x, y, z):
+        return [[x, y, z], [x, y + 1.0, z], [x, y, z + 1.0]]
+    tris = np.asarray([tri(0, 0, 0), tri(0, 5, 5), tri(10, 10, 10)], np.float32)
+    src = (0.0, 5.5, 5.5)
+    c = orc.eq2_cost([0, 0, 0, 0, 1, 1], 1, [0, 5, 5, 10, 11, 11], 2, [0, 0, 0, 10, 11, 11], 0.0, src)
+    assert c == 44.75
+    e = orc.Bvh(tris, alpha=0.0, source=src, max_leaf=1).export()
+    assert _leaf_prims(e, e["child"][0][0]) == [0]
+
+
 def _check_structure(orc, tris, b, max_leaf):
     e = b.export()
     assert sorted(e["prims"].tolist()) == list(range(len(tris)))
