@@ -131,3 +131,35 @@ def test_host_trace_binding_rejects_malformed_buffers_without_gpu():
     for rays, hits in bad:
         with pytest.raises(TypeError):
             rtbvh.rt_trace_closest_host(None, rays, hits)
+
+
+def test_header_is_plain_c_and_a_c_program_links_without_gpu(tmp_path):
+    """The boundary is a C ABI: the header compiles as pedantic C99 and a C
+    program links against the library and calls it (no GPU calls)."""
+    import shutil
+    import subprocess
+    import pytest
+    gcc = shutil.which("gcc")
+    if not gcc:
+        pytest.skip("gcc not found")
+    inc = os.path.join(ROOT, "include")
+    hdr = os.path.join(inc, "rtbvh.h")
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only", "-x", "c", hdr],
+                   check=True)
+    lib_path = build_ext.build()
+    src = tmp_path / "main.c"
+    src.write_text(
+        '#include "rtbvh.h"\n'
+        "int main(void) {\n"
+        "  rt_ray r = {0};\n"
+        "  (void)r;\n"
+        "  if (rt_version() < 100) return 1;\n"
+        "  if (rt_ray_count(RT_RAYS_ICOSPHERE, 8) != 655362) return 2;\n"
+        "  if (rt_scene_destroy(0) != RT_EINVAL || rt_last_error()[0] == 0) return 3;\n"
+        "  return 0;\n"
+        "}\n")
+    exe = tmp_path / "main"
+    libdir = os.path.dirname(lib_path)
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Werror", "-I", inc, str(src), "-L", libdir, "-lrtbvh",
+                    "-Wl,-rpath," + libdir, "-o", str(exe)], check=True)
+    assert subprocess.run([str(exe)]).returncode == 0
