@@ -522,7 +522,11 @@ int rt_session_destroy(rt_session session);
  *  - Every call shares the one array: calls whose work overlaps on the GPU
  *    (other streams, other host threads) race with each other.  Issue them
  *    on one stream or order them with events.
- *  - The scene's BVH must already be built (building allocates).
+ *  - The scene's BVH must already be built (building allocates), and the
+ *    device the scene was uploaded on must be current (RT_EINVAL otherwise).
+ *  - The array's address is looked up once per device and kept: after a
+ *    device reset (cudaDeviceReset), which invalidates every scene, this
+ *    call must not be used again in the same process.
  * Errors: RT_EINVAL, RT_ENOTBUILT, RT_ECUDA. */
 int rt_trace_closest_noalloc(rt_scene scene, const rt_ray* rays_dev, int64_t n, rt_hit* hits_dev,
                              const rt_trace_params* params, void* stream);

@@ -12,9 +12,9 @@ paper each function follows.
 Pinning status: every function here is pinned by ``tests/test_oracle_pins.py``
 against closed forms, brute force written another way, invariants and
 special cases.  The alpha < 1 split choice is pinned on a hand-derived Eq. 2
-example (raw and scale-free distance term); the *shape* of full-size
-alpha < 1 trees is not, as the paper prints no tree (parity unpinned: only
-their invariants and the alpha = 1 special case are checked).
+example (raw and scale-free distance term), and the recursive tree cost at
+alpha = 0.5 on the same example; the paper prints no tree, so no full-size
+alpha < 1 tree is compared with a published one.
 """
 from __future__ import annotations
 

@@ -142,8 +142,7 @@ def test_bvh_structure_and_quality(rb, orc, alpha, dist_norm, max_leaf):
     c_ref = ob.cost()
     print("quality a=%g dn=%d leaf=%d: gpu %.6g exact-sweep %.6g ratio %.4f depth %d/%d" % (
         alpha, dist_norm, max_leaf, c_gpu, c_ref, c_gpu / c_ref, info["depth2"], ob.info()["depth"]))
-    if alpha == 1.0:
-        assert c_gpu <= 1.10 * c_ref
+    assert c_gpu <= 1.10 * c_ref  # reading c6, at every alpha
 
 
 def test_build_deterministic(rb):

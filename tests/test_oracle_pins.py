@@ -322,6 +322,31 @@ def test_eq2_worked_example_scale_free_split(orc):
     assert _root_left_size(raw.export()) == g["best_split"]["0.5"] == 1
 
 
+def test_tree_cost_alpha_half_worked_example(orc):
+    """The recursive Eq. 2 tree cost at alpha = 0.5 (the recursion the quality
+    bound of reading c6 uses) on the worked example, raw and scale-free: the
+    hand-derived value for the hand-given tree, and the exact sweep builds
+    exactly that tree."""
+    g = json.load(open(os.path.join(GOLDEN, "eq2_worked_example.json")))
+    tris = np.asarray(g["tris"], np.float32)
+    tc = g["tree_cost_alpha_0.5"]
+    for key, dn in (("raw", 0), ("scale_free", 1)):
+        t = tc[key]
+        child = np.asarray(t["child"], np.int32)
+        lf = np.arange(4, dtype=np.int64)
+        lc = np.ones(4, np.int64)
+        prims = np.asarray([l[0] for l in t["leaves"]], np.int32)
+        got = orc.tree_cost(tris, child, lf, lc, prims, 0.5, (0, 0, 0), dist_norm=dn)
+        assert abs(got - t["cost"]) < 1e-12 * t["cost"], key
+        b = orc.Bvh(tris, alpha=0.5, source=(0, 0, 0), max_leaf=1, dist_norm=dn)
+        assert abs(b.cost() - t["cost"]) < 1e-12 * t["cost"], key
+    # a slip in the recursion shows: the children's costs left out (k t_i used
+    # instead) or the area ratio against the wrong box change the value
+    t = tc["raw"]
+    flat = 0.5 * ((2 / 14) * 1 + (10 / 14) * 3) + 0.5 * 10.5 + 1
+    assert abs(flat - t["cost"]) > 1.0
+
+
 def test_eq2_costs_scale_with_t_i_and_t_trav(orc):
     """Eq. 2 with t_i = 2.5 and t_trav = 0.75 on the worked example: the SAH
     term scales with t_i, so does the scale-free distance term (it carries
