@@ -366,6 +366,8 @@ struct BuildArgs {
   unsigned* tccnt;
   unsigned* tscnt;
   int2* titem;  // chunk items of big nodes
+  int4* tplan;  // [cap_t][2]: what a big node reserved for each big child (task slots, count slots,
+                // chunk items, count slots to clear), written by its chunk 0
   int* tready;
   WNode* wide;
   QNode* qwide;  // nullable: also write the 64-byte nodes
@@ -454,17 +456,11 @@ __device__ __forceinline__ Task make_task(int begin, int count, int parent, int 
   return t;
 }
 
-// Reserve `amt` consecutive items of a counter bounded by `cap` (-1 if they
-// do not fit; the counter is then left unchanged).
-__device__ int reserve(int* ctr, int amt, int cap) {
-  int old = ld_volatile(ctr);
-  for (int it = 0; it < (1 << 20); ++it) {
-    if (old + amt > cap) return -1;
-    const int prev = atomicCAS(ctr, old, old + amt);
-    if (prev == old) return old;
-    old = prev;
-  }
-  return -1;
+// Reserve `amt` consecutive items of a counter bounded by `cap`: one atomic
+// add; -1 if they do not fit (the items past cap are then never used).
+__device__ __forceinline__ int reserve(int* ctr, int amt, int cap) {
+  const int old = atomicAdd(ctr, amt);
+  return old + amt <= cap ? old : -1;
 }
 
 // Write binary node `id` (both children's boxes, refs, counts) and link it
@@ -759,6 +755,20 @@ __global__ void __launch_bounds__(kBlock) k_bin_root(BuildArgs A) {
   }
 }
 
+// Tree facts gathered by a warp, added to the control block when it exits.
+struct WarpStats {
+  int n_int, n_leaf, big, deep;
+};
+
+// Account a written binary node (one thread per node).
+__device__ __forceinline__ void note_node(WarpStats& ws, int nl, int nr, bool leafl, bool leafr, int depth) {
+  ++ws.n_int;
+  ws.n_leaf += (int)leafl + (int)leafr;
+  if (leafl) ws.big = max(ws.big, nl);
+  if (leafr) ws.big = max(ws.big, nr);
+  ws.deep = max(ws.deep, (leafl || leafr) ? depth + 1 : depth);
+}
+
 // ------------------------------------------------------------------ big nodes
 struct TopSmem {
   unsigned pbins[kBinWords];
@@ -769,7 +779,8 @@ struct TopSmem {
   int red[kWarps];
   int2 item;
   int last;
-  int created[2], zslot[2], zchunk[2], zn[2], ibase[2];
+  int created[2], ibase[2];
+  int4 plan[2];
 };
 
 __device__ __forceinline__ int block_sum(int v, int* red) {
@@ -814,9 +825,54 @@ __device__ int2 claim_item(const BuildArgs& A, int epoch) {
   return make_int2(-1, 0);
 }
 
-__device__ void top_emit(const BuildArgs& A, TopSmem& S, const TopTask& T, int epoch, int nl, int nr,
+__device__ void top_emit(const BuildArgs& A, TopSmem& S, const TopTask& T, int slot, int epoch, int nl, int nr,
                          const BinU& cu0, const BinU& cu1, bool top0, bool top1, int nch0, int nch1, int cfirst0,
-                         int cfirst1);
+                         int cfirst1, WarpStats& ts);
+
+// Chunk 0 of a big node, as soon as its split is known: reserve what the
+// node's big children will need (two task slots and the count slots for
+// their own children, their chunk items) and clear what their chunks will
+// fill, so that the CTA finishing the node's last chunk only writes and
+// publishes.  The clearing is ordered before that CTA's emit by chunk 0's
+// release of its done count.
+__device__ void top_plan(const BuildArgs& A, TopSmem& S, int slot, bool top0, bool top1, int nch0, int nch1) {
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    int cs[2] = {-1, -1}, cr[2] = {-1, -1}, ib[2] = {-1, -1};
+    // every reservation is issued before any result is used: one round trip
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      if (!(s ? top1 : top0)) continue;
+      const int ncs = s ? nch1 : nch0;
+      cs[s] = reserve(&A.ctl->t_slot_next, 2, A.cap_t);
+      cr[s] = reserve(&A.ctl->t_cnt_next, ncs + 2, A.cap_c);
+      ib[s] = reserve(&A.ctl->ti_tail, ncs, A.cap_c);
+    }
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const int ncs = s ? nch1 : nch0;
+      const int4 pl = (cs[s] >= 0 && cr[s] >= 0 && ib[s] >= 0) ? make_int4(cs[s], cr[s], ib[s], ncs + 2)
+                                                             : make_int4(-1, -1, -1, 0);
+      S.plan[s] = pl;
+      A.tplan[2 * slot + s] = pl;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const int4 pl = S.plan[s];
+    if (pl.x < 0) continue;
+    unsigned* zb = tbins_at(A, pl.x);
+    for (int w = tid; w < 2 * kBinWords; w += kBlock) zb[w] = 0u;
+    if (tid < 2) A.tdone[pl.x + tid] = 0;
+    unsigned* zc = tccnt_at(A, pl.y);
+    unsigned* zs = tscnt_at(A, pl.y);
+    for (int w = tid; w < pl.w * kCntStride; w += kBlock) {
+      zc[w] = 0u;
+      zs[w] = 0u;
+    }
+  }
+}
 
 // Chunk j of big node T (one CTA): Eq. 2 at every bin plane from the node's
 // merged bins (every chunk of the node picks the same plane), stable
@@ -825,7 +881,8 @@ __device__ void top_emit(const BuildArgs& A, TopSmem& S, const TopTask& T, int e
 // that finishes the node's last chunk writes the node and creates its
 // children: big ones get their chunk items, the others go to the subtree
 // queue.  No CTA ever waits for another.
-__device__ void top_chunk(const BuildArgs& A, TopSmem& S, const TopTask& T, int slot, int j, int epoch) {
+__device__ void top_chunk(const BuildArgs& A, TopSmem& S, const TopTask& T, int slot, int j, int epoch,
+                          WarpStats& ts) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int K = A.K, K3 = 3 * K, CH = A.chunk;
   const unsigned lt_mask = (1u << lane) - 1u;
@@ -848,8 +905,6 @@ __device__ void top_chunk(const BuildArgs& A, TopSmem& S, const TopTask& T, int 
     }
   }
   {
-    const unsigned* gb = tbins_at(A, slot);
-    for (int w = tid; w < K3 * kBinVals; w += kBlock) S.pbins[w] = __ldcg(gb + w);
     for (int w = tid; w < 2 * kBinWords; w += kBlock) (&S.cbins[0][0])[w] = 0u;
     for (int w = tid; w < 4 * kCntStride; w += kBlock) (&S.ccnt[0][0][0])[w] = 0u;
   }
@@ -915,6 +970,7 @@ __device__ void top_chunk(const BuildArgs& A, TopSmem& S, const TopTask& T, int 
   const bool top0 = nl > A.big, top1 = nr > A.big;
   const int nch0 = (nl + CH - 1) / CH, nch1 = (nr + CH - 1) / CH;
   const int cfirst0 = T.chunk_res, cfirst1 = T.chunk_res + nch0;
+  if (j == 0) top_plan(A, S, slot, top0, top1, nch0, nch1);
   const float cmin0[3] = {cu0.a0, cu0.a1, cu0.a2}, cmin1[3] = {cu1.a0, cu1.a1, cu1.a2};
   const float scl0[3] = {bin_scale(cu0.a0, cu0.b0, K), bin_scale(cu0.a1, cu0.b1, K), bin_scale(cu0.a2, cu0.b2, K)};
   const float scl1[3] = {bin_scale(cu1.a0, cu1.b0, K), bin_scale(cu1.a1, cu1.b1, K), bin_scale(cu1.a2, cu1.b2, K)};
@@ -1031,14 +1087,15 @@ __device__ void top_chunk(const BuildArgs& A, TopSmem& S, const TopTask& T, int 
     S.last = atomicAdd(&A.tdone[slot], 1) == T.nchunk - 1;
   }
   __syncthreads();
-  if (S.last) top_emit(A, S, T, epoch, nl, nr, cu0, cu1, top0, top1, nch0, nch1, cfirst0, cfirst1);
+  if (S.last) top_emit(A, S, T, slot, epoch, nl, nr, cu0, cu1, top0, top1, nch0, nch1, cfirst0, cfirst1, ts);
 }
 
 // Write the node split by the chunks just finished and create its children
-// (the CTA that finished the node's last chunk).
-__device__ void top_emit(const BuildArgs& A, TopSmem& S, const TopTask& T, int epoch, int nl, int nr,
+// (the CTA that finished the node's last chunk), with what chunk 0 reserved
+// for them; tree facts go to the CTA's own tally (thread 0).
+__device__ void top_emit(const BuildArgs& A, TopSmem& S, const TopTask& T, int slot, int epoch, int nl, int nr,
                          const BinU& cu0, const BinU& cu1, bool top0, bool top1, int nch0, int nch1, int cfirst0,
-                         int cfirst1) {
+                         int cfirst1, WarpStats& ts) {
   const int tid = threadIdx.x;
   const int par = T.parity & 1;
   __threadfence();
@@ -1047,13 +1104,7 @@ __device__ void top_emit(const BuildArgs& A, TopSmem& S, const TopTask& T, int e
     const int refl = nl <= A.max_leaf ? leaf_ref(T.begin, nl) : INT_MAX;
     const int refr = nr <= A.max_leaf ? leaf_ref(T.begin + nl, nr) : INT_MAX;
     write_node(A, id, T.parent, T.side, cu0, refl, nl, cu1, refr, nr, epoch);
-    const int leaves = (refl != INT_MAX) + (refr != INT_MAX);
-    atomicAdd(&A.ctl->n_internal, 1);
-    if (leaves) {
-      atomicAdd(&A.ctl->n_leaves, leaves);
-      atomicMax(&A.ctl->max_leaf_size, max(refl != INT_MAX ? nl : 0, refr != INT_MAX ? nr : 0));
-    }
-    atomicMax(&A.ctl->depth2, leaves ? T.depth + 1 : T.depth);
+    note_node(ts, nl, nr, refl != INT_MAX, refr != INT_MAX, T.depth);
     for (int s = 0; s < 2; ++s) {
       const int cn = s ? nr : nl, cb = T.begin + (s ? nl : 0);
       const BinU& cu = s ? cu1 : cu0;
@@ -1063,11 +1114,8 @@ __device__ void top_emit(const BuildArgs& A, TopSmem& S, const TopTask& T, int e
         continue;
       }
       if (s ? top1 : top0) {
-        const int ncs = s ? nch1 : nch0;
-        const int cs = reserve(&A.ctl->t_slot_next, 2, A.cap_t);
-        const int cr = cs >= 0 ? reserve(&A.ctl->t_cnt_next, ncs + 2, A.cap_c) : -1;
-        const int ib = cr >= 0 ? reserve(&A.ctl->ti_tail, ncs, A.cap_c) : -1;
-        if (ib >= 0) {
+        const int4 pl = __ldcg(A.tplan + 2 * slot + s);
+        if (pl.x >= 0) {
           TopTask X;
           X.begin = cb;
           X.count = cn;
@@ -1080,45 +1128,25 @@ __device__ void top_emit(const BuildArgs& A, TopSmem& S, const TopTask& T, int e
           X.chi[1] = cu.b1;
           X.chi[2] = cu.b2;
           X.depth = T.depth + 1;
-          X.nchunk = ncs;
+          X.nchunk = s ? nch1 : nch0;
           X.chunk_first = s ? cfirst1 : cfirst0;
-          X.child_slot = cs;
-          X.chunk_res = cr;
+          X.child_slot = pl.x;
+          X.chunk_res = pl.y;
           X.parity = par ^ 1;
           A.ttask[T.child_slot + s] = X;
           S.created[s] = 1;
-          S.zslot[s] = cs;
-          S.zchunk[s] = cr;
-          S.zn[s] = ncs + 2;
-          S.ibase[s] = ib;
+          S.ibase[s] = pl.z;
           continue;
         }
       }
       push_task(A, make_task(cb, cn, id, s, T.depth + 1, cu, par ^ 1), epoch);  // pools full: a warp takes it
     }
+    if (S.created[0] || S.created[1])
+      atomicAdd(&A.ctl->ti_pending, (S.created[0] ? nch0 : 0) + (S.created[1] ? nch1 : 0));
   }
-  __syncthreads();
-  // what a created child's chunks will fill: its children's bins, done
-  // counters and chunk counts start empty
-#pragma unroll
-  for (int s = 0; s < 2; ++s) {
-    if (!S.created[s]) continue;
-    unsigned* zb = tbins_at(A, S.zslot[s]);
-    for (int w = tid; w < 2 * kBinWords; w += kBlock) zb[w] = 0u;
-    if (tid < 2) A.tdone[S.zslot[s] + tid] = 0;
-    unsigned* zc = tccnt_at(A, S.zchunk[s]);
-    unsigned* zs = tscnt_at(A, S.zchunk[s]);
-    for (int w = tid; w < S.zn[s] * kCntStride; w += kBlock) {
-      zc[w] = 0u;
-      zs[w] = 0u;
-    }
-  }
-  if (tid == 0 && (S.created[0] || S.created[1]))
-    atomicAdd(&A.ctl->ti_pending, (S.created[0] ? nch0 : 0) + (S.created[1] ? nch1 : 0));
   __syncthreads();
   // publish the children's chunk items: each release store also publishes
-  // what every thread wrote before the barrier (the zeroed bins and counts,
-  // the tasks, the pending count)
+  // what every thread wrote before the barrier (the tasks, the pending count)
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
     if (!S.created[s]) continue;
@@ -1131,11 +1159,24 @@ __device__ void top_emit(const BuildArgs& A, TopSmem& S, const TopTask& T, int e
 }
 
 // Chunk j of big node `slot`, after checking the node's fields.
-__device__ void top_item(const BuildArgs& A, TopSmem& S, int slot, int j, int epoch) {
+__device__ void top_item(const BuildArgs& A, TopSmem& S, int slot, int j, int epoch, WarpStats& ts) {
   const int tid = threadIdx.x;
   TopTask T;
   bool ok = slot >= 0 && slot < A.cap_t;
-  if (ok) T = load_top_cg(A.ttask + slot);
+  // the node's merged bins depend on the slot only: their loads go out with
+  // the task's, into shared memory once both have arrived
+  constexpr int kPer = (kBinWords + kBlock - 1) / kBlock;
+  const int nw = 3 * A.K * kBinVals;
+  unsigned bv[kPer];
+  if (ok) {
+    const unsigned* gb = tbins_at(A, slot);
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) bv[q] = tid + q * kBlock < nw ? __ldcg(gb + tid + q * kBlock) : 0u;
+    T = load_top_cg(A.ttask + slot);
+#pragma unroll
+    for (int q = 0; q < kPer; ++q)
+      if (tid + q * kBlock < nw) S.pbins[tid + q * kBlock] = bv[q];
+  }
   const int n = ok ? T.count : 0;
   ok = ok && T.begin >= 0 && n > A.big && T.begin <= A.n - n && j >= 0 && j < T.nchunk && T.chunk_first >= 0 &&
        T.chunk_first + T.nchunk <= A.cap_c && T.child_slot >= 0 && T.child_slot + 2 <= A.cap_t &&
@@ -1143,22 +1184,29 @@ __device__ void top_item(const BuildArgs& A, TopSmem& S, int slot, int j, int ep
   if (!ok) {
     if (tid == 0) set_status(A.ctl, kStBadSplit, 4);
   } else {
-    top_chunk(A, S, T, slot, j, epoch);
+    top_chunk(A, S, T, slot, j, epoch, ts);
   }
 }
 
 __device__ void top_loop(const BuildArgs& A, TopSmem& S, int epoch) {
+  WarpStats ts{0, 0, 0, 0};  // thread 0's tally of the nodes this CTA wrote
   for (;;) {
     if (threadIdx.x == 0) S.item = claim_item(A, epoch);
     __syncthreads();
     const int2 it = S.item;
     __syncthreads();
-    if (it.x < 0) return;
-    top_item(A, S, it.x, it.y, epoch);
+    if (it.x < 0) break;
+    top_item(A, S, it.x, it.y, epoch, ts);
     __syncthreads();
     // release: the subtree tasks this item pushed are counted before the
     // item stops counting (the warps' exit test reads ti_pending first)
     if (threadIdx.x == 0) red_release_add(&A.ctl->ti_pending, -1);
+  }
+  if (threadIdx.x == 0) {
+    if (ts.n_int) atomicAdd(&A.ctl->n_internal, ts.n_int);
+    if (ts.n_leaf) atomicAdd(&A.ctl->n_leaves, ts.n_leaf);
+    if (ts.big) atomicMax(&A.ctl->max_leaf_size, ts.big);
+    if (ts.deep) atomicMax(&A.ctl->depth2, ts.deep);
   }
 }
 
@@ -1190,10 +1238,6 @@ __device__ __forceinline__ Box6 box_shfl(const Box6& a, int src) {
           __shfl_sync(kFull, a.h0, src), __shfl_sync(kFull, a.h1, src), __shfl_sync(kFull, a.h2, src)};
 }
 
-// Tree facts gathered by a warp, added to the control block when it exits.
-struct WarpStats {
-  int n_int, n_leaf, big, deep;
-};
 
 __device__ void micro_build(const BuildArgs& A, float4 rlo, float4 rhi, int n, int gbase, int parent, int side,
                             int depth, int epoch, WarpStats& ws) {
@@ -1709,14 +1753,6 @@ __device__ __forceinline__ void leaf_out(const BuildArgs& A, const float4* src, 
   for (int k = t0; k < 2 * n; k += nt) A.rec[0][2 * (size_t)gpos + k] = src[k];
 }
 
-// Account a written binary node (one thread per node).
-__device__ __forceinline__ void note_node(WarpStats& ws, int nl, int nr, bool leafl, bool leafr, int depth) {
-  ++ws.n_int;
-  ws.n_leaf += (int)leafl + (int)leafr;
-  if (leafl) ws.big = max(ws.big, nl);
-  if (leafr) ws.big = max(ws.big, nr);
-  ws.deep = max(ws.deep, (leafl || leafr) ? depth + 1 : depth);
-}
 
 // Split node X of the subtree with the whole CTA: bins (count and box) in
 // one shared array, each thread binning a run of records (thread (w, l)
@@ -2333,6 +2369,7 @@ cudaError_t launch_build(rt_scene_s* s, const rt_build_params& p, cudaStream_t s
   A.tccnt = s->top_ccnt;
   A.tscnt = s->top_scnt;
   A.titem = s->top_item;
+  A.tplan = s->top_plan;
   A.tready = s->top_ready;
   A.wide = s->wide;
   A.qwide = p.quantize ? s->qwide : nullptr;

@@ -132,14 +132,18 @@ struct __align__(16) TopTask {
 };
 
 // Device control block of one scene (zeroed at the start of every build).
+// The words every waiting CTA polls share one 128-byte line; the pool
+// counters and the tree facts, updated by atomics, sit on lines of their own.
 struct BuildCtl {
   int status, status_where, epoch, wide_root;
   // chunk items of top tasks (CTA per item)
   int ti_head, ti_tail, ti_pending, pad0;
-  // pools of one build: top task slots, count slots
-  int t_slot_next, t_cnt_next, pad1, pad2;
   // subtree task queue (CTA per task)
   int qa_head, qa_tail, qa_pending, pad3;
+  int pad_a[20];
+  // pools of one build: top task slots, count slots
+  int t_slot_next, t_cnt_next, pad1, pad2;
+  int pad_b[28];
   // tree facts
   int n_internal, n_leaves, depth2, max_leaf_size;
   int root_ref, pad4, pad5, pad6;
@@ -245,6 +249,7 @@ struct rt_scene_s {
   unsigned* top_ccnt = nullptr;     // [cap_c][3 * kMaxBins] per-chunk bin counts
   unsigned* top_scnt = nullptr;     // [cap_c][3 * kMaxBins] per 32-chunk group counts
   int2* top_item = nullptr;         // [cap_c] chunk items (task slot, chunk index)
+  int4* top_plan = nullptr;         // [cap_t][2] what each big node reserved for its big children
   int* top_ready = nullptr;         // [cap_c] epoch stamp of each published item
   rt::BuildGeom geom{};             // geometry the buffers were sized for
   rt::BuildCtl* ctl = nullptr;

@@ -79,7 +79,7 @@ __global__ void k_pack(const float* __restrict__ raw, int n, float4* __restrict_
 void free_scene_buffers(rt_scene_s* s) {
   void* ptrs[] = {s->tri_in, s->idx[0], s->idx[1], s->rec[0], s->rec[1], s->node2, s->wide, s->link2, s->epoch,
                   s->tri_leaf, s->qa, s->qa_ready, s->top_task, s->top_done, s->top_bins, s->top_ccnt,
-                  s->top_scnt, s->top_item, s->top_ready, s->ctl, s->scratch.counter, s->scratch.queue, s->scratch.cand,
+                  s->top_scnt, s->top_item, s->top_plan, s->top_ready, s->ctl, s->scratch.counter, s->scratch.queue, s->scratch.cand,
                   s->host_scr[0].counter, s->host_scr[0].queue, s->host_scr[0].cand,
                   s->host_scr[1].counter, s->host_scr[1].queue, s->host_scr[1].cand, s->reflect_blocks,
                   s->stage_rays[0], s->stage_rays[1], s->stage_hits[0], s->stage_hits[1], s->sel, s->sel_cnt,
@@ -107,7 +107,7 @@ int ensure_capacity(rt_scene_s* s, int64_t n) {
   if (r) {
     void* per_tri[] = {s->tri_in, s->idx[0], s->rec[0], s->rec[1], s->node2, s->link2, s->wide, s->tri_leaf,
                        s->qa, s->qa_ready, s->top_task, s->top_done, s->top_bins, s->top_ccnt, s->top_scnt,
-                       s->top_item, s->top_ready, s->sel, s->sel_cnt};
+                       s->top_item, s->top_plan, s->top_ready, s->sel, s->sel_cnt};
     for (void* p : per_tri)
       if (p) cudaFree(p);
     s->tri_in = s->tri_leaf = nullptr;
@@ -122,6 +122,7 @@ int ensure_capacity(rt_scene_s* s, int64_t n) {
     s->top_done = nullptr;
     s->top_bins = s->top_ccnt = s->top_scnt = nullptr;
     s->top_item = nullptr;
+    s->top_plan = nullptr;
     s->top_ready = nullptr;
     s->sel = s->sel_cnt = nullptr;
     s->cap_tri = 0;
@@ -153,6 +154,7 @@ int alloc_capacity(rt_scene_s* s, int64_t m) {
   RT_CUDA(dev_alloc(&s->top_ccnt, (size_t)g.cap_c * 3 * rt::kMaxBins), "alloc top counts");
   RT_CUDA(dev_alloc(&s->top_scnt, (size_t)g.cap_c * 3 * rt::kMaxBins), "alloc top counts");
   RT_CUDA(dev_alloc(&s->top_item, (size_t)g.cap_c), "alloc top items");
+  RT_CUDA(dev_alloc(&s->top_plan, 2 * (size_t)g.cap_t), "alloc top plans");
   RT_CUDA(dev_alloc(&s->top_ready, (size_t)g.cap_c), "alloc top items");
   RT_CUDA(cudaMemset(s->top_ready, 0, sizeof(int) * g.cap_c), "clear top items");
   RT_CUDA(dev_alloc(&s->sel, m), "alloc range selection");
