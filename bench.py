@@ -84,11 +84,11 @@ def job_rate(units_per_rank, world_size, steps, total_ms):
     return world_size * units_per_rank * steps / (total_ms * 1e-3) / 1e6
 
 
-def alu_roofline(nodes_per_ray, tris_per_ray, rays, ms, n_sm, sm_mhz):
+def alu_roofline(nodes_per_ray, tris_per_ray, rays, ms, n_sm, sm_mhz, width=4):
     """Secondary roofline of the walk: FP32 operations at about 20 per child
-    box test (4 children per node) and 40 per triangle test, against one FP32
-    operation per lane per cycle (4 x 32 lanes per SM) at the SM clock."""
-    ops_per_ray = 20.0 * 4.0 * nodes_per_ray + 40.0 * tris_per_ray
+    box test (width children per node) and 40 per triangle test, against one
+    FP32 operation per lane per cycle (4 x 32 lanes per SM) at the SM clock."""
+    ops_per_ray = 20.0 * width * nodes_per_ray + 40.0 * tris_per_ray
     achieved = ops_per_ray * rays / (ms * 1e-3) / 1e12
     peak = n_sm * 128 * sm_mhz * 1e6 / 1e12
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
@@ -640,19 +640,22 @@ def run_ours(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.Stream()
 
-    # autotuner (outside the timed region): leaf size, bins and ray tile for
-    # this scene and ray set, one build per trace as in every step
-    tune, tile = None, 0
+    # autotuner (outside the timed region): node width, leaf size, bins, ray
+    # tile and stack depth for this scene and ray set, one build per trace as
+    # in every step
+    tune, tile, stack = None, 0, 0
+    bp["width"] = 4
     if not args.no_tune:
         with torch.cuda.stream(stream):
             tune = rtbvh.rt_autotune(scene, rays, build_weight=1.0, stream=stream, **bp)
-        bp["max_leaf"], bp["bins"], tile = tune["max_leaf"], tune["bins"], tune["block"]
+        bp["max_leaf"], bp["bins"], bp["width"] = tune["max_leaf"], tune["bins"], tune["width"]
+        tile, stack = tune["block"], tune["stack"]
 
     def build():
         rtbvh.rt_bvh_build(scene, stream=stream, **bp)
 
     def trace():
-        rtbvh.rt_trace_closest(scene, rays, hits, n_flagged=nflag, stream=stream, block=tile)
+        rtbvh.rt_trace_closest(scene, rays, hits, n_flagged=nflag, stream=stream, block=tile, stack=stack)
 
     with torch.cuda.stream(stream):
         for _ in range(max(args.warmup, 1)):
@@ -667,7 +670,8 @@ def run_ours(args):
     stream.synchronize()
     st = stats.double().mean(0).cpu().numpy()
     nodes_per_ray, tris_per_ray = float(st[0]), float(st[1])
-    bytes_per_ray = 32 + 16 + 128 * nodes_per_ray + 48 * tris_per_ray
+    node_bytes = 32 * bp["width"]
+    bytes_per_ray = 32 + 16 + node_bytes * nodes_per_ray + 48 * tris_per_ray
     flagged = int(nflag.item())
 
     split_bytes = split_kernel_bytes(rtbvh.rt_bvh_export(scene, stream=stream))
@@ -736,7 +740,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         rtbvh.rt_scene_update(scene, tris_host, stream=stream)
         rtbvh.rt_bvh_build(scene, stream=stream, **bp)
-        rtbvh.rt_trace_closest_host(scene, rays_pin, hits_pin, stream=stream, block=tile)
+        rtbvh.rt_trace_closest_host(scene, rays_pin, hits_pin, stream=stream, block=tile, stack=stack)
         torch.cuda.synchronize()
         if k >= args.warmup:
             e2e_ms.append(1e3 * (time.perf_counter() - t0))
@@ -768,7 +772,7 @@ def run_ours(args):
     extra = {}
     if not args.no_extra:
         extra["alpha_sweep"] = run_alpha_sweep(rtbvh, torch, sc, rays, p["source"])
-        extra["quantised_nodes"] = run_quantised(rtbvh, torch, scene, rays, dict(bp, quantize=1), tile)
+        extra["quantised_nodes"] = run_quantised(rtbvh, torch, scene, rays, dict(bp, quantize=1, width=4), tile)
         with torch.cuda.stream(stream):
             run_trace()
         stream.synchronize()
@@ -786,7 +790,8 @@ def run_ours(args):
                   "kernel": "k_trace + k_retest64 (one rt_trace_closest)", "peak_source": peak_src,
                   "ms": mean_trace_ms, "bytes_per_ray": bytes_per_ray, "algorithmic_bytes": bytes_per_ray * R,
                   "l2_probe_gbs": l2_gbs, "frac_of_l2_probe": trace_gbs / l2_gbs,
-                  "note": "algorithmic bytes = 32 ray + 16 hit + 128 B x nodes + 48 B x triangles per ray; "
+                  "note": "algorithmic bytes = 32 ray + 16 hit + node bytes (32 B per child slot) x nodes + "
+                          "48 B x triangles per ray; "
                           "nodes and triangles stay in L2 for this scene"}
     roof_split = {"bound": "hbm", "achieved": split_gbs, "peak": hbm, "unit": "GB/s", "frac": split_gbs / hbm,
                   "traffic": NCU_TRAFFIC["k_split"][0], "traffic_unit": "bytes per launch",
@@ -801,7 +806,7 @@ def run_ours(args):
     dominant_split = mean_split_ms >= mean_trace_ms
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     roof_alu = alu_roofline(nodes_per_ray, tris_per_ray, R, mean_trace_ms, n_sm,
-                            (clk or {}).get("sm_mhz") or 2070.0)
+                            (clk or {}).get("sm_mhz") or 2070.0, bp["width"])
     value = job_rate(R, ws, args.steps, total_ms)
     cpu_v, cores, reps, el = cpu_checker_rate(sc, rays_np, p, args, args.cpu_seconds)
     line = {
@@ -810,7 +815,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_tri": T, "rays_per_step": R, "t_max_m": 500.0,
                    "alpha": args.alpha, "dist_norm": args.dist_norm, "max_leaf": bp["max_leaf"],
-                   "bins": bp["bins"], "ray_tile": tile or 128, "width": 4,
+                   "bins": bp["bins"], "ray_tile": tile or 128, "width": bp["width"], "stack": stack or 64,
                    "autotuned": tune, "step": "bvh_build + trace_closest (fp64 re-test incl.)",
                    "cuda_graph": "trace replayed from a graph; build launched directly (per-step split-kernel events)"
                    if use_graph else False, "l2": "flushed between steps (256 MB write)",

@@ -100,6 +100,9 @@ typedef struct {
                                   flagged for the float64 re-test */
   int32_t block;               /* rays per CTA of the float32 walk (ray tile): 64, 128 or
                                   256; 0 = 128.  Results do not depend on it. */
+  int32_t stack;               /* depth of the walk's per-ray stack: 16, 32 or 64; 0 = 64.
+                                  A ray whose stack would overflow is finished by the
+                                  float64 pass, so results do not depend on it. */
 } rt_trace_params;
 
 /* Build report (rt_bvh_info). */
@@ -177,22 +180,27 @@ typedef struct {
   float build_ms;     /* device time of one build with the choice */
   float trace_ms;     /* device time of one trace of the sample with the choice */
   float score_ms;     /* build_weight * build_ms + trace_ms */
-  float default_score_ms; /* the same for max_leaf 4, bins 16, block 128 */
+  float default_score_ms; /* the same for width 4, max_leaf 4, bins 16, block 128, stack 64 */
+  int32_t width;      /* chosen traversal node width (rt_build_params.width) */
+  int32_t stack;      /* chosen stack depth of the walk (rt_trace_params.stack) */
 } rt_tune_result;
 
-/* Autotuner of the build and walk parameters (no counterpart in the paper):
- * for max_leaf in {2, 4, 6, 8} x bins in {8, 16, 32} x ray tile in {64,
- * 128, 256}, build the scene's BVH from `base` (alpha, t_i, t_trav, source,
- * dist_norm kept) and time the closest-hit walk of the n_rays sample rays
- * (device pointer), each timing the median of 5 CUDA-event timings, each
- * after an untimed 256 MB write that evicts the L2 (cold-cache ranking); pick the
- * lowest build_weight * build_ms + trace_ms (build_weight = builds per
- * traced sample: 1 when the scene is rebuilt for every batch, 0 when it is
- * built once and traced many times).  Every configuration gives the same
- * hits (the hit rule does not depend on the tree).  On return the scene
- * holds the BVH built with the choice.  Synchronous.  Allocates and frees
- * one n_rays hit buffer and the 256 MB eviction buffer (without it, when it
- * cannot be had, the timings are warm-cache).  Errors: RT_EINVAL (NULL arguments, n_rays < 1,
+/* Autotuner of the build and walk parameters (no counterpart in the paper),
+ * in two stages: first the tree, width in {4, 8} x max_leaf in {2, 4, 6, 8}
+ * x bins in {8, 16, 32} (alpha, t_i, t_trav, source, dist_norm, range kept
+ * from `base`), each build timed and the closest-hit walk of the n_rays
+ * sample rays (device pointer) timed with the default tile and stack; then,
+ * on the chosen tree, the walk's ray tile in {64, 128, 256} x stack depth in
+ * {16, 32, 64}.  Every timing is the median of 5 CUDA-event timings, each
+ * after an untimed 256 MB write that evicts the L2 (cold-cache ranking); the
+ * choice minimises build_weight * build_ms + trace_ms (build_weight = builds
+ * per traced sample: 1 when the scene is rebuilt for every batch, 0 when it
+ * is built once and traced many times).  Every configuration gives the same
+ * hits (the hit rule does not depend on the tree or the walk).  On return
+ * the scene holds the BVH built with the choice (never quantised).
+ * Synchronous.  Allocates and frees one n_rays hit buffer and the 256 MB
+ * eviction buffer (without it, when it cannot be had, the timings are
+ * warm-cache).  Errors: RT_EINVAL (NULL arguments, n_rays < 1,
  * build_weight < 0, bad base params), RT_ENOMEM, RT_ECUDA. */
 int rt_autotune(rt_scene scene, const rt_build_params* base, const rt_ray* rays_dev, int64_t n_rays,
                 float build_weight, rt_tune_result* out, void* stream);

@@ -371,6 +371,7 @@ struct BuildArgs {
   int* tready;
   WNode* wide;
   QNode* qwide;  // nullable: also write the 64-byte nodes
+  WNode8* wide8; // nullable: write 8-wide traversal nodes (instead of the 4-wide ones)
   float4* tri_leaf;
   int32_t* order;
   int* epoch_dev;
@@ -2164,9 +2165,12 @@ __device__ QNode quantize_node(const WNode& w) {
   return q;
 }
 
-__device__ void make_wide(const BuildArgs& A, int x, int epoch) {
-  int ref[kWidth];
-  float3 lo[kWidth], hi[kWidth];
+// The W-wide node rooted at binary node x: open the internal child of
+// largest surface area until there are W children (the first of equal areas
+// wins; the opened node's children take its slot and the next free one).
+// Slots past m are empty.
+template <int W>
+__device__ int collapse(const BuildArgs& A, int x, int epoch, int* ref, float3* lo, float3* hi) {
   const Node2 nd = load_node_cg(A.node2 + x);
   child_of(nd, 0, &ref[0], &lo[0], &hi[0]);
   child_of(nd, 1, &ref[1], &lo[1], &hi[1]);
@@ -2176,7 +2180,7 @@ __device__ void make_wide(const BuildArgs& A, int x, int epoch) {
       set_status(A.ctl, kStBadLink, 1);
       ref[q] = INT_MIN;
     }
-  while (m < kWidth) {
+  while (m < W) {
     int pick = -1;
     float best = -1.f;
     for (int q = 0; q < m; ++q)
@@ -2198,34 +2202,51 @@ __device__ void make_wide(const BuildArgs& A, int x, int epoch) {
       }
     ++m;
   }
-  float lx[4], ly[4], lz[4], hx[4], hy[4], hz[4];
-  int ch[4];
-  for (int q = 0; q < kWidth; ++q) {
-    if (q < m && ref[q] != INT_MIN) {
-      lx[q] = lo[q].x;
-      ly[q] = lo[q].y;
-      lz[q] = lo[q].z;
-      hx[q] = hi[q].x;
-      hy[q] = hi[q].y;
-      hz[q] = hi[q].z;
-      ch[q] = ref[q];
-    } else {
-      lx[q] = ly[q] = lz[q] = INFINITY;
-      hx[q] = hy[q] = hz[q] = -INFINITY;
-      ch[q] = INT_MIN;
+  for (int q = m; q < W; ++q) ref[q] = INT_MIN;
+  for (int q = 0; q < W; ++q)
+    if (ref[q] == INT_MIN) {
+      lo[q] = make_float3(INFINITY, INFINITY, INFINITY);
+      hi[q] = make_float3(-INFINITY, -INFINITY, -INFINITY);
     }
-  }
+  return m;
+}
+
+__device__ void make_wide(const BuildArgs& A, int x, int epoch) {
+  int ref[4];
+  float3 lo[4], hi[4];
+  collapse<4>(A, x, epoch, ref, lo, hi);
   WNode w;
-  w.lox = make_float4(lx[0], lx[1], lx[2], lx[3]);
-  w.hix = make_float4(hx[0], hx[1], hx[2], hx[3]);
-  w.loy = make_float4(ly[0], ly[1], ly[2], ly[3]);
-  w.hiy = make_float4(hy[0], hy[1], hy[2], hy[3]);
-  w.loz = make_float4(lz[0], lz[1], lz[2], lz[3]);
-  w.hiz = make_float4(hz[0], hz[1], hz[2], hz[3]);
-  w.child = make_int4(ch[0], ch[1], ch[2], ch[3]);
+  w.lox = make_float4(lo[0].x, lo[1].x, lo[2].x, lo[3].x);
+  w.hix = make_float4(hi[0].x, hi[1].x, hi[2].x, hi[3].x);
+  w.loy = make_float4(lo[0].y, lo[1].y, lo[2].y, lo[3].y);
+  w.hiy = make_float4(hi[0].y, hi[1].y, hi[2].y, hi[3].y);
+  w.loz = make_float4(lo[0].z, lo[1].z, lo[2].z, lo[3].z);
+  w.hiz = make_float4(hi[0].z, hi[1].z, hi[2].z, hi[3].z);
+  w.child = make_int4(ref[0], ref[1], ref[2], ref[3]);
   w.meta = make_int4(__ldcg(&A.link2[x]).x, 0, 0, 0);
   A.wide[x] = w;
   if (A.qwide) A.qwide[x] = quantize_node(w);
+}
+
+__device__ void make_wide8(const BuildArgs& A, int x, int epoch) {
+  int ref[8];
+  float3 lo[8], hi[8];
+  collapse<8>(A, x, epoch, ref, lo, hi);
+  WNode8 w;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int b = 4 * h;
+    w.lox[h] = make_float4(lo[b].x, lo[b + 1].x, lo[b + 2].x, lo[b + 3].x);
+    w.hix[h] = make_float4(hi[b].x, hi[b + 1].x, hi[b + 2].x, hi[b + 3].x);
+    w.loy[h] = make_float4(lo[b].y, lo[b + 1].y, lo[b + 2].y, lo[b + 3].y);
+    w.hiy[h] = make_float4(hi[b].y, hi[b + 1].y, hi[b + 2].y, hi[b + 3].y);
+    w.loz[h] = make_float4(lo[b].z, lo[b + 1].z, lo[b + 2].z, lo[b + 3].z);
+    w.hiz[h] = make_float4(hi[b].z, hi[b + 1].z, hi[b + 2].z, hi[b + 3].z);
+    w.child[h] = make_int4(ref[b], ref[b + 1], ref[b + 2], ref[b + 3]);
+  }
+  w.meta[0] = make_int4(__ldcg(&A.link2[x]).x, 0, 0, 0);
+  w.meta[1] = make_int4(0, 0, 0, 0);
+  A.wide8[x] = w;
 }
 
 __global__ void __launch_bounds__(kBlock) k_post(BuildArgs A) {
@@ -2254,8 +2275,25 @@ __global__ void __launch_bounds__(kBlock) k_post(BuildArgs A) {
         w.child.x = r;
       }
       w.meta = make_int4(-1, 0, 0, 0);
-      A.wide[0] = w;
-      if (A.qwide) A.qwide[0] = quantize_node(w);
+      if (A.wide8) {
+        WNode8 w8;
+        w8.lox[0] = w.lox;
+        w8.hix[0] = w.hix;
+        w8.loy[0] = w.loy;
+        w8.hiy[0] = w.hiy;
+        w8.loz[0] = w.loz;
+        w8.hiz[0] = w.hiz;
+        w8.lox[1] = w8.loy[1] = w8.loz[1] = make_float4(inf, inf, inf, inf);
+        w8.hix[1] = w8.hiy[1] = w8.hiz[1] = make_float4(-inf, -inf, -inf, -inf);
+        w8.child[0] = w.child;
+        w8.child[1] = make_int4(INT_MIN, INT_MIN, INT_MIN, INT_MIN);
+        w8.meta[0] = w.meta;
+        w8.meta[1] = make_int4(0, 0, 0, 0);
+        A.wide8[0] = w8;
+      } else {
+        A.wide[0] = w;
+        if (A.qwide) A.qwide[0] = quantize_node(w);
+      }
       A.ctl->wide_root = 0;
     }
   }
@@ -2269,7 +2307,12 @@ __global__ void __launch_bounds__(kBlock) k_post(BuildArgs A) {
     A.tri_leaf[3 * (size_t)i] = A.tri[3 * (size_t)p];
     A.tri_leaf[3 * (size_t)i + 1] = A.tri[3 * (size_t)p + 1];
     A.tri_leaf[3 * (size_t)i + 2] = A.tri[3 * (size_t)p + 2];
-    if (i < n - 1 && __ldcg(&A.link2[i]).y == epoch) make_wide(A, i, epoch);
+    if (i < n - 1 && __ldcg(&A.link2[i]).y == epoch) {
+      if (A.wide8)
+        make_wide8(A, i, epoch);
+      else
+        make_wide(A, i, epoch);
+    }
   }
 }
 
@@ -2373,6 +2416,7 @@ cudaError_t launch_build(rt_scene_s* s, const rt_build_params& p, cudaStream_t s
   A.tready = s->top_ready;
   A.wide = s->wide;
   A.qwide = p.quantize ? s->qwide : nullptr;
+  A.wide8 = p.width == 8 ? s->wide8 : nullptr;
   A.tri_leaf = s->tri_leaf;
   A.order = s->idx[0];
   A.epoch_dev = s->epoch;

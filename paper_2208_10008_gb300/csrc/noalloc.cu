@@ -50,6 +50,8 @@ extern "C" int rt_trace_closest_noalloc(rt_scene scene, const rt_ray* rays_dev, 
       return rt::set_error(RT_EINVAL, "rays/hits must be 16-byte aligned");
     if (params && params->block != 0 && params->block != 64 && params->block != 128 && params->block != 256)
       return rt::set_error(RT_EINVAL, "block must be 0, 64, 128 or 256");
+    if (params && ((params->stack != 0 && params->stack != 16 && params->stack != 32 && params->stack != 64)))
+      return rt::set_error(RT_EINVAL, "stack must be 0, 16, 32 or 64");
     if (params && (params->flags & RT_QUANTIZED_NODES) && !scene->q_built)
       return rt::set_error(RT_EINVAL, "RT_QUANTIZED_NODES needs a build with quantize = 1");
     if (!scene->built) return rt::set_error(RT_ENOTBUILT, "BVH not built");

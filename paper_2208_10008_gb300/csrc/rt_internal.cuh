@@ -46,7 +46,7 @@ int abi_guard(F&& body) {
 
 constexpr int kMaxLeaf = 15;   // leaf refs pack the count in 4 bits
 constexpr int kMaxBins = 32;
-constexpr int kWidth = 4;
+constexpr int kWidth = 4;           // default children per traversal node (8 on request)
 constexpr int kMicro = 32;          // nodes up to this size are finished by one warp
 constexpr int kSpinLimit = 1 << 24; // bounded device waits (iterations of ~200 ns)
 
@@ -83,6 +83,16 @@ struct __align__(16) WNode {
   int4 meta;
 };
 static_assert(sizeof(WNode) == 128, "wide node must be one 128-byte line");
+
+// 8-wide traversal node, 256 bytes (two lines): child i's box in component
+// i % 4 of plane[.][i / 4]; child refs as in WNode (INT_MIN: empty slot,
+// box lo = +inf, hi = -inf); meta[0].x = binary parent of the node's root.
+struct __align__(16) WNode8 {
+  float4 lox[2], hix[2], loy[2], hiy[2], loz[2], hiz[2];
+  int4 child[2];
+  int4 meta[2];
+};
+static_assert(sizeof(WNode8) == 256, "8-wide node must be 256 bytes");
 
 // The same 4-wide node in 64 bytes: the children's planes as bytes on a
 // per-axis grid of step 2^e from the union box's lower corner (origin).
@@ -236,6 +246,8 @@ struct rt_scene_s {
   rt::Node2* node2 = nullptr;
   rt::WNode* wide = nullptr;
   rt::QNode* qwide = nullptr;   // 64-byte nodes (builds with quantize = 1)
+  rt::WNode8* wide8 = nullptr;  // 8-wide nodes (builds with width = 8)
+  int64_t wide8_cap = 0;
   int64_t qwide_cap = 0;
   bool q_built = false;         // the current tree has its 64-byte nodes
   int2* link2 = nullptr;        // (parent, epoch) per binary node

@@ -83,7 +83,7 @@ void free_scene_buffers(rt_scene_s* s) {
                   s->host_scr[0].counter, s->host_scr[0].queue, s->host_scr[0].cand,
                   s->host_scr[1].counter, s->host_scr[1].queue, s->host_scr[1].cand, s->reflect_blocks,
                   s->stage_rays[0], s->stage_rays[1], s->stage_hits[0], s->stage_hits[1], s->sel, s->sel_cnt,
-                  s->qwide};
+                  s->qwide, s->wide8};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (s->sel_host) cudaFreeHost(s->sel_host);
@@ -219,10 +219,11 @@ int check_params(const rt_build_params* p) {
       return fail(RT_EINVAL, "source must be finite");
   if (p->max_leaf < 1 || p->max_leaf > rt::kMaxLeaf) return fail(RT_EINVAL, "max_leaf must be 1..15");
   if (p->bins < 4 || p->bins > rt::kMaxBins) return fail(RT_EINVAL, "bins must be 4..32");
-  if (p->width != rt::kWidth) return fail(RT_EINVAL, "width must be 4");
+  if (p->width != 4 && p->width != 8) return fail(RT_EINVAL, "width must be 4 or 8");
   if (p->dist_norm != 0 && p->dist_norm != 1) return fail(RT_EINVAL, "dist_norm must be 0 or 1");
   if (!(p->range >= 0.f)) return fail(RT_EINVAL, "range must be >= 0");
   if (p->quantize != 0 && p->quantize != 1) return fail(RT_EINVAL, "quantize must be 0 or 1");
+  if (p->quantize && p->width != 4) return fail(RT_EINVAL, "quantised nodes are 4-wide: quantize needs width 4");
   return RT_OK;
 }
 
@@ -308,6 +309,14 @@ int rt_bvh_build(rt_scene s, const rt_build_params* p, void* stream) {
     RT_CUDA(dev_alloc(&s->qwide, s->cap_tri + 1), "alloc quantised nodes");
     s->qwide_cap = s->cap_tri + 1;
   }
+  if (p->width == 8 && s->wide8_cap < s->cap_tri + 1) {  // the 8-wide nodes, on first use
+    if (capturing) return fail(RT_EINVAL, "the first build with width = 8 allocates and cannot be captured");
+    if (s->wide8) cudaFree(s->wide8);
+    s->wide8 = nullptr;
+    s->wide8_cap = 0;
+    RT_CUDA(dev_alloc(&s->wide8, s->cap_tri + 1), "alloc 8-wide nodes");
+    s->wide8_cap = s->cap_tri + 1;
+  }
   s->q_built = false;
   if (!capturing) RT_CUDA(cudaEventRecord(s->ev_build0, st), "record event");
   RT_CUDA(rt::launch_build(s, *p, st), "launch build");
@@ -373,8 +382,28 @@ static int rt_bvh_info_body(rt_scene s, void* stream, rt_bvh_info_t* info) {
   if (c.status != 0) return fail(RT_EINTERNAL, "device status %d at %d", c.status, c.status_where);
   // traversal nodes reachable from the root, and their depth
   const int64_t slots = s->n_tri > 1 ? s->n_tri : 1;
-  std::vector<rt::WNode> w((size_t)slots);
-  RT_CUDA(cudaMemcpy(w.data(), s->wide, sizeof(rt::WNode) * slots, cudaMemcpyDeviceToHost), "read wide nodes");
+  const int width = s->params.width == 8 ? 8 : 4;
+  std::vector<int32_t> ch((size_t)slots * width);
+  if (width == 8) {
+    std::vector<rt::WNode8> w((size_t)slots);
+    RT_CUDA(cudaMemcpy(w.data(), s->wide8, sizeof(rt::WNode8) * slots, cudaMemcpyDeviceToHost), "read wide nodes");
+    for (int64_t k = 0; k < slots; ++k)
+      for (int q = 0; q < 2; ++q) {
+        ch[8 * k + 4 * q] = w[k].child[q].x;
+        ch[8 * k + 4 * q + 1] = w[k].child[q].y;
+        ch[8 * k + 4 * q + 2] = w[k].child[q].z;
+        ch[8 * k + 4 * q + 3] = w[k].child[q].w;
+      }
+  } else {
+    std::vector<rt::WNode> w((size_t)slots);
+    RT_CUDA(cudaMemcpy(w.data(), s->wide, sizeof(rt::WNode) * slots, cudaMemcpyDeviceToHost), "read wide nodes");
+    for (int64_t k = 0; k < slots; ++k) {
+      ch[4 * k] = w[k].child.x;
+      ch[4 * k + 1] = w[k].child.y;
+      ch[4 * k + 2] = w[k].child.z;
+      ch[4 * k + 3] = w[k].child.w;
+    }
+  }
   std::vector<std::pair<int32_t, int32_t>> st{{c.wide_root, 1}};
   int64_t nw = 0;
   int32_t dw = 0;
@@ -384,9 +413,10 @@ static int rt_bvh_info_body(rt_scene s, void* stream, rt_bvh_info_t* info) {
     if (it.first < 0 || it.first >= slots || nw > slots) return fail(RT_EINTERNAL, "bad wide node %d", it.first);
     ++nw;
     if (it.second > dw) dw = it.second;
-    const int32_t ch[4] = {w[it.first].child.x, w[it.first].child.y, w[it.first].child.z, w[it.first].child.w};
-    for (int k = 0; k < 4; ++k)
-      if (ch[k] >= 0) st.push_back({ch[k], it.second + 1});
+    for (int k = 0; k < width; ++k) {
+      const int32_t c2 = ch[(size_t)it.first * width + k];
+      if (c2 >= 0) st.push_back({c2, it.second + 1});
+    }
   }
   info->n_wide = nw;
   info->depth_wide = dw;
@@ -471,6 +501,8 @@ static int trace_common(rt_scene s, const rt_ray* rays, int64_t n, rt_hit* hits,
   if (((uintptr_t)rays & 15) || ((uintptr_t)hits & 15)) return fail(RT_EINVAL, "rays/hits must be 16-byte aligned");
   if (params && params->block != 0 && params->block != 64 && params->block != 128 && params->block != 256)
     return fail(RT_EINVAL, "block must be 0, 64, 128 or 256");
+  if (params && ((params->stack != 0 && params->stack != 16 && params->stack != 32 && params->stack != 64)))
+    return fail(RT_EINVAL, "stack must be 0, 16, 32 or 64");
   if (params && (params->flags & RT_QUANTIZED_NODES) && !s->q_built)
     return fail(RT_EINVAL, "RT_QUANTIZED_NODES needs a build with quantize = 1");
   if (!s->built) return fail(RT_ENOTBUILT, "BVH not built");
@@ -550,6 +582,8 @@ int rt_trace_closest_host(rt_scene s, const rt_ray* rays_host, int64_t n, rt_hit
     return fail(RT_EINVAL, "per-ray device arrays are not supported with host buffers");
   if (params && params->block != 0 && params->block != 64 && params->block != 128 && params->block != 256)
     return fail(RT_EINVAL, "block must be 0, 64, 128 or 256");
+  if (params && ((params->stack != 0 && params->stack != 16 && params->stack != 32 && params->stack != 64)))
+    return fail(RT_EINVAL, "stack must be 0, 16, 32 or 64");
   if (params && (params->flags & RT_QUANTIZED_NODES) && !s->q_built)
     return fail(RT_EINVAL, "RT_QUANTIZED_NODES needs a build with quantize = 1");
   if (n == 0) return RT_OK;
@@ -576,6 +610,7 @@ int rt_trace_closest_host(rt_scene s, const rt_ray* rays_host, int64_t n, rt_hit
   if (params) {  // n_flagged_dev counts one call of the device path: not written here
     tp.flags = params->flags;
     tp.block = params->block;
+    tp.stack = params->stack;
   }
   int rc = RT_OK;
   for (int64_t off = 0, c = 0; off < n; off += chunk, ++c) {

@@ -29,6 +29,7 @@
 //     definition's answer bit for bit.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cfloat>
 #include <climits>
 
@@ -38,7 +39,7 @@ namespace rt {
 namespace {
 
 constexpr int kTraceBlock = 128;
-constexpr int kStack = 64;
+constexpr int kStack = 64;  // default depth of the walk's stack
 constexpr int kRetestBlock = 128;
 constexpr unsigned kFullMask = 0xffffffffu;
 constexpr float kU = 5.9604645e-08f;   // unit roundoff of float32, 2^-24
@@ -279,6 +280,40 @@ __device__ __forceinline__ unsigned slab4q(const QNode* __restrict__ node, const
   return mask;
 }
 
+// slab4 on an 8-wide node: the same widened test for its 8 children (two
+// halves of four); empty slots have an empty box and never pass.
+__device__ __forceinline__ unsigned slab8(const WNode8* __restrict__ node, const RayPre& r, float bound,
+                                          float tn[8], int ch[8]) {
+  const float4* p = reinterpret_cast<const float4*>(node);
+  unsigned mask = 0;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const float4 nx = __ldg(p + 2 * r.sx + h), fx = __ldg(p + 2 - 2 * r.sx + h);
+    const float4 ny = __ldg(p + 4 + 2 * r.sy + h), fy = __ldg(p + 6 - 2 * r.sy + h);
+    const float4 nz = __ldg(p + 8 + 2 * r.sz + h), fz = __ldg(p + 10 - 2 * r.sz + h);
+    const int4 c = __ldg(reinterpret_cast<const int4*>(p + 12 + h));
+    ch[4 * h] = c.x;
+    ch[4 * h + 1] = c.y;
+    ch[4 * h + 2] = c.z;
+    ch[4 * h + 3] = c.w;
+    const float nxa[4] = {nx.x, nx.y, nx.z, nx.w}, fxa[4] = {fx.x, fx.y, fx.z, fx.w};
+    const float nya[4] = {ny.x, ny.y, ny.z, ny.w}, fya[4] = {fy.x, fy.y, fy.z, fy.w};
+    const float nza[4] = {nz.x, nz.y, nz.z, nz.w}, fza[4] = {fz.x, fz.y, fz.z, fz.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      float t0 = fmaxf(fmaxf(__fmul_rn(__fsub_rn(nxa[i], r.ox), r.ix), __fmul_rn(__fsub_rn(nya[i], r.oy), r.iy)),
+                       __fmul_rn(__fsub_rn(nza[i], r.oz), r.iz));
+      float t1 = fminf(fminf(__fmul_rn(__fsub_rn(fxa[i], r.ox), r.ix), __fmul_rn(__fsub_rn(fya[i], r.oy), r.iy)),
+                       __fmul_rn(__fsub_rn(fza[i], r.oz), r.iz));
+      t0 = t0 - fabsf(t0) * kWiden;
+      t1 = t1 + fabsf(t1) * kWiden;
+      tn[4 * h + i] = t0;
+      if (t0 <= t1 && t0 <= bound && t1 >= r.tmin) mask |= 1u << (4 * h + i);
+    }
+  }
+  return mask;
+}
+
 // The same conservative slab test for one box (lo, hi) of a binary node.
 __device__ __forceinline__ bool slab1(float4 lo, float4 hi, const RayPre& r, float bound) {
   const float nx = r.ix >= 0.f ? lo.x : hi.x, fx = r.ix >= 0.f ? hi.x : lo.x;
@@ -321,6 +356,7 @@ __device__ __forceinline__ int enqueue_flag(int* counter, int* queue, int qcap, 
 
 struct TraceArgs {
   const WNode* wide;
+  const WNode8* wide8;   // 8-wide nodes (walk with kW = 8)
   const int* wide_root;  // device word: index of the root traversal node
   const Node2* node2;
   const QNode* qwide;    // 64-byte nodes (walk with kQuant)
@@ -341,7 +377,7 @@ struct TraceArgs {
   int qcap;
 };
 
-template <bool kAny, bool kStats, int kTile, bool kQuant = false>
+template <bool kAny, bool kStats, int kTile, int kSD, bool kQuant, int kW = 4>
 __global__ void __launch_bounds__(kTile) k_trace(TraceArgs A) {
   const int i = blockIdx.x * kTile + threadIdx.x;
   if (i >= A.n || (A.n_dev && i >= *A.n_dev)) return;
@@ -353,7 +389,7 @@ __global__ void __launch_bounds__(kTile) k_trace(TraceArgs A) {
   bool flag = false, done = false;
   uint32_t n_nodes = 0, n_tris = 0;
   float bound = r.tmax;
-  int2 st[kStack];  // (ref, entry distance bits) of the boxes still to visit
+  int2 st[kSD];  // (ref, entry distance bits) of the boxes still to visit
   int sp = 0;
   // Triangles whose float64 answer could beat the float32 one: uncertain
   // ones and every certain hit near the interval, with a lower bound on t.
@@ -397,6 +433,48 @@ __global__ void __launch_bounds__(kTile) k_trace(TraceArgs A) {
     if (cur_t > bound) continue;
     if (ref >= 0) {
       if (kStats) ++n_nodes;
+      if (kW == 8) {
+        float tn[8];
+        int ch[8];
+        const unsigned m = slab8(A.wide8 + ref, r, bound, tn, ch);
+        const int cnt = __popc(m);
+        if (cnt == 0) continue;
+        if (sp + cnt - 1 > kSD) {  // cannot hold the children: leave it to the float64 pass
+          flag = true;
+          walk_all = true;
+          break;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (!((m >> q) & 1u)) tn[q] = INFINITY;
+        // sort the 8 (t, ref) pairs ascending (19 compare-exchanges)
+        cswap(tn[0], ch[0], tn[2], ch[2]);
+        cswap(tn[1], ch[1], tn[3], ch[3]);
+        cswap(tn[4], ch[4], tn[6], ch[6]);
+        cswap(tn[5], ch[5], tn[7], ch[7]);
+        cswap(tn[0], ch[0], tn[4], ch[4]);
+        cswap(tn[1], ch[1], tn[5], ch[5]);
+        cswap(tn[2], ch[2], tn[6], ch[6]);
+        cswap(tn[3], ch[3], tn[7], ch[7]);
+        cswap(tn[0], ch[0], tn[1], ch[1]);
+        cswap(tn[2], ch[2], tn[3], ch[3]);
+        cswap(tn[4], ch[4], tn[5], ch[5]);
+        cswap(tn[6], ch[6], tn[7], ch[7]);
+        cswap(tn[2], ch[2], tn[4], ch[4]);
+        cswap(tn[3], ch[3], tn[5], ch[5]);
+        cswap(tn[1], ch[1], tn[4], ch[4]);
+        cswap(tn[3], ch[3], tn[6], ch[6]);
+        cswap(tn[1], ch[1], tn[2], ch[2]);
+        cswap(tn[3], ch[3], tn[4], ch[4]);
+        cswap(tn[5], ch[5], tn[6], ch[6]);
+        // push farthest first so the nearest stacked one is popped next
+#pragma unroll
+        for (int q = 7; q >= 1; --q)
+          if (q < cnt) st[sp++] = make_int2(ch[q], __float_as_int(tn[q]));
+        cur = ch[0];
+        cur_t = tn[0];
+        continue;
+      }
       float tn[4];
       int4 ch;
       unsigned m = kQuant ? slab4q(A.qwide + ref, r, bound, tn, &ch) : slab4(A.wide + ref, r, bound, tn, &ch);
@@ -411,7 +489,7 @@ __global__ void __launch_bounds__(kTile) k_trace(TraceArgs A) {
       cswap(tb, rb, tc, rc);
       int cnt = __popc(m);
       if (cnt == 0) continue;
-      if (sp + cnt - 1 > kStack) {  // cannot hold the children: leave it to the float64 pass
+      if (sp + cnt - 1 > kSD) {  // cannot hold the children: leave it to the float64 pass
         flag = true;
         walk_all = true;
         break;
@@ -756,16 +834,55 @@ cudaError_t launch_trace(rt_scene_s* s, const rt_ray* rays, int64_t n, rt_hit* h
   return launch_trace_dev(s, rays, n, nullptr, hits, occl, tp, scr, st);
 }
 
+namespace {
+
+template <bool kAny, bool kStats, int kTile, int kSD, bool kQuant, int kW = 4>
+void walk(const TraceArgs& A, int64_t n, cudaStream_t st) {
+  k_trace<kAny, kStats, kTile, kSD, kQuant, kW><<<(int)((n + kTile - 1) / kTile), kTile, 0, st>>>(A);
+}
+
+// The tuned walks: node width 4 / 8 x ray tile 64 / 128 / 256 x stack depth
+// 16 / 32 / 64.
+template <bool kAny, int kTile, int kW>
+void walk_stack(const TraceArgs& A, int64_t n, int stack, cudaStream_t st) {
+  if (stack == 16)
+    walk<kAny, false, kTile, 16, false, kW>(A, n, st);
+  else if (stack == 32)
+    walk<kAny, false, kTile, 32, false, kW>(A, n, st);
+  else
+    walk<kAny, false, kTile, 64, false, kW>(A, n, st);
+}
+template <bool kAny, int kW>
+void walk_tile(const TraceArgs& A, int64_t n, int tile, int stack, cudaStream_t st) {
+  if (tile == 64)
+    walk_stack<kAny, 64, kW>(A, n, stack, st);
+  else if (tile == 256)
+    walk_stack<kAny, 256, kW>(A, n, stack, st);
+  else
+    walk_stack<kAny, 128, kW>(A, n, stack, st);
+}
+template <bool kAny>
+void walk_tuned(const TraceArgs& A, int64_t n, int width, int tile, int stack, cudaStream_t st) {
+  if (width == 8)
+    walk_tile<kAny, 8>(A, n, tile, stack, st);
+  else
+    walk_tile<kAny, 4>(A, n, tile, stack, st);
+}
+
+}  // namespace
+
 cudaError_t launch_trace_dev(rt_scene_s* s, const rt_ray* rays, int64_t n, const int* n_dev, rt_hit* hits,
                              uint8_t* occl, const rt_trace_params* tp, TraceScratch& scr, cudaStream_t st) {
   cudaError_t e;
   int n_launched = 0;
   const bool quant = tp && (tp->flags & RT_QUANTIZED_NODES);
   if (quant && !s->q_built) return cudaErrorInvalidValue;  // no 64-byte nodes for this tree
+  const int width = s->params.width == 8 ? 8 : 4;          // the traversal nodes the last build wrote
   if ((e = cudaMemsetAsync(scr.counter, 0, 2 * sizeof(int), st))) return e;
   if (n > 0) {
     TraceArgs A;
     A.wide = s->wide;
+    A.wide8 = s->wide8;
     A.qwide = s->qwide;
     A.wide_root = &s->ctl->wide_root;
     A.node2 = s->node2;
@@ -785,38 +902,26 @@ cudaError_t launch_trace_dev(rt_scene_s* s, const rt_ray* rays, int64_t n, const
     A.queue = scr.queue;
     A.cand = scr.cand;
     A.qcap = (int)scr.cap;
-    // ray tile (rays per CTA); the counting walk always uses the default
-    const int req = (tp && !stats) ? tp->block : 0;
-    const int tile = (req == 64 || req == 256) ? req : kTraceBlock;
-    const int grid = (int)((n + tile - 1) / tile);
-    if (quant) {  // the 64-byte node walk: the default tile only
-      const int gq = (int)((n + kTraceBlock - 1) / kTraceBlock);
+    // ray tile (rays per CTA) and stack depth; the counting walk and the
+    // 64-byte node walk use the defaults
+    const int tile = (tp && !stats && !quant && (tp->block == 64 || tp->block == 256)) ? tp->block : kTraceBlock;
+    const int stack = (tp && !stats && !quant && (tp->stack == 16 || tp->stack == 32)) ? tp->stack : kStack;
+    if (quant) {
       if (occl)
-        stats ? k_trace<true, true, kTraceBlock, true><<<gq, kTraceBlock, 0, st>>>(A)
-              : k_trace<true, false, kTraceBlock, true><<<gq, kTraceBlock, 0, st>>>(A);
+        stats ? walk<true, true, kTraceBlock, kStack, true>(A, n, st)
+              : walk<true, false, kTraceBlock, kStack, true>(A, n, st);
       else
-        stats ? k_trace<false, true, kTraceBlock, true><<<gq, kTraceBlock, 0, st>>>(A)
-              : k_trace<false, false, kTraceBlock, true><<<gq, kTraceBlock, 0, st>>>(A);
+        stats ? walk<false, true, kTraceBlock, kStack, true>(A, n, st)
+              : walk<false, false, kTraceBlock, kStack, true>(A, n, st);
     } else if (stats) {
-      if (occl)
-        k_trace<true, true, kTraceBlock><<<grid, kTraceBlock, 0, st>>>(A);
+      if (width == 8)
+        occl ? walk<true, true, kTraceBlock, kStack, false, 8>(A, n, st)
+             : walk<false, true, kTraceBlock, kStack, false, 8>(A, n, st);
       else
-        k_trace<false, true, kTraceBlock><<<grid, kTraceBlock, 0, st>>>(A);
-    } else if (tile == 64) {
-      if (occl)
-        k_trace<true, false, 64><<<grid, 64, 0, st>>>(A);
-      else
-        k_trace<false, false, 64><<<grid, 64, 0, st>>>(A);
-    } else if (tile == 256) {
-      if (occl)
-        k_trace<true, false, 256><<<grid, 256, 0, st>>>(A);
-      else
-        k_trace<false, false, 256><<<grid, 256, 0, st>>>(A);
+        occl ? walk<true, true, kTraceBlock, kStack, false>(A, n, st)
+             : walk<false, true, kTraceBlock, kStack, false>(A, n, st);
     } else {
-      if (occl)
-        k_trace<true, false, kTraceBlock><<<grid, kTraceBlock, 0, st>>>(A);
-      else
-        k_trace<false, false, kTraceBlock><<<grid, kTraceBlock, 0, st>>>(A);
+      occl ? walk_tuned<true>(A, n, width, tile, stack, st) : walk_tuned<false>(A, n, width, tile, stack, st);
     }
     ++n_launched;
     if (!(tp && (tp->flags & RT_NO_FP64_RETEST))) {

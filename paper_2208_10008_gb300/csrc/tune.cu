@@ -1,8 +1,9 @@
 // Autotuner of the build and walk parameters (rt_autotune in rtbvh.h).
 //
 // The knobs are the ones that trade build time against walk time without
-// changing any hit: the leaf size, the number of bins per axis and the ray
-// tile (rays per CTA) of the float32 walk.  Every configuration is built
+// changing any hit: the traversal node width, the leaf size, the number of
+// bins per axis, and the ray tile (rays per CTA) and stack depth of the
+// float32 walk.  Every configuration is built
 // and timed with CUDA events on the caller's stream (median of 5, L2 flushed
 // before each timing by a 256 MB write, so that the ranking is the one of
 // cold-cache steps), and the scene is left built with the winner.
@@ -71,23 +72,30 @@ extern "C" int rt_autotune(rt_scene s, const rt_build_params* base, const rt_ray
     cudaGetLastError();
     flush = nullptr;
   }
-  const int leaves[] = {2, 4, 6, 8}, binsv[] = {8, 16, 32}, tiles[] = {64, 128, 256};
+  // Two stages.  The tree (node width x leaf size x bins), each build timed
+  // and its walk timed with the default tile and stack; then the walk of the
+  // chosen tree (ray tile x stack depth).
+  const int widths[] = {4, 8}, leaves[] = {2, 4, 6, 8}, binsv[] = {8, 16, 32};
+  const int tiles[] = {64, 128, 256}, stacks[] = {16, 32, 64};
   rt_tune_result best{};
   best.score_ms = FLT_MAX;
   best.default_score_ms = -1.f;
+  best.block = 128;
+  best.stack = 64;
   int err = 0, tried = 0;
-  for (int ml : leaves) {
-    for (int bn : binsv) {
-      rt_build_params p = *base;
-      p.max_leaf = ml;
-      p.bins = bn;
-      err = rt_bvh_build(s, &p, stream);  // warm: the first build sizes the scene's buffers
-      if (err) goto done;
-      const float tb = median_ms(st, ev, flush, [&] { return rt_bvh_build(s, &p, stream); }, &err);
-      if (tb < 0.f) goto fail_cuda;
-      for (int tile : tiles) {
+  for (int wd : widths) {
+    for (int ml : leaves) {
+      for (int bn : binsv) {
+        rt_build_params p = *base;
+        p.width = wd;
+        p.max_leaf = ml;
+        p.bins = bn;
+        p.quantize = 0;
+        err = rt_bvh_build(s, &p, stream);  // warm: the first build sizes the scene's buffers
+        if (err) goto done;
+        const float tb = median_ms(st, ev, flush, [&] { return rt_bvh_build(s, &p, stream); }, &err);
+        if (tb < 0.f) goto fail_cuda;
         rt_trace_params tp{};
-        tp.block = tile;
         err = rt_trace_closest(s, rays, n, hits, &tp, stream);
         if (err) goto done;
         const float tt =
@@ -95,11 +103,11 @@ extern "C" int rt_autotune(rt_scene s, const rt_build_params* base, const rt_ray
         if (tt < 0.f) goto fail_cuda;
         const float score = build_weight * tb + tt;
         ++tried;
-        if (ml == 4 && bn == 16 && tile == 128) best.default_score_ms = score;
+        if (wd == 4 && ml == 4 && bn == 16) best.default_score_ms = score;
         if (score < best.score_ms) {
+          best.width = wd;
           best.max_leaf = ml;
           best.bins = bn;
-          best.block = tile;
           best.build_ms = tb;
           best.trace_ms = tt;
           best.score_ms = score;
@@ -109,10 +117,33 @@ extern "C" int rt_autotune(rt_scene s, const rt_build_params* base, const rt_ray
   }
   {
     rt_build_params p = *base;
+    p.width = best.width;
     p.max_leaf = best.max_leaf;
     p.bins = best.bins;
+    p.quantize = 0;
     err = rt_bvh_build(s, &p, stream);
     if (err) goto done;
+    for (int tile : tiles) {
+      for (int sd : stacks) {
+        if (tile == 128 && sd == 64) continue;  // timed in the first stage
+        rt_trace_params tp{};
+        tp.block = tile;
+        tp.stack = sd;
+        err = rt_trace_closest(s, rays, n, hits, &tp, stream);
+        if (err) goto done;
+        const float tt =
+            median_ms(st, ev, flush, [&] { return rt_trace_closest(s, rays, n, hits, &tp, stream); }, &err);
+        if (tt < 0.f) goto fail_cuda;
+        ++tried;
+        const float score = build_weight * best.build_ms + tt;
+        if (score < best.score_ms) {
+          best.block = tile;
+          best.stack = sd;
+          best.trace_ms = tt;
+          best.score_ms = score;
+        }
+      }
+    }
     if (cudaStreamSynchronize(st) != cudaSuccess) goto fail_cuda;
   }
   best.n_tried = tried;

@@ -62,7 +62,8 @@ class BuildParams(ctypes.Structure):
 
 class TraceParams(ctypes.Structure):
     _fields_ = [("flags", ctypes.c_uint32), ("skip_tri_dev", ctypes.c_void_p),
-                ("stats_dev", ctypes.c_void_p), ("n_flagged_dev", ctypes.c_void_p), ("block", ctypes.c_int32)]
+                ("stats_dev", ctypes.c_void_p), ("n_flagged_dev", ctypes.c_void_p), ("block", ctypes.c_int32),
+                ("stack", ctypes.c_int32)]
 
 
 class ReceiveParams(ctypes.Structure):
@@ -73,7 +74,8 @@ class ReceiveParams(ctypes.Structure):
 class TuneResult(ctypes.Structure):
     _fields_ = [("max_leaf", ctypes.c_int32), ("bins", ctypes.c_int32), ("block", ctypes.c_int32),
                 ("n_tried", ctypes.c_int32), ("build_ms", ctypes.c_float), ("trace_ms", ctypes.c_float),
-                ("score_ms", ctypes.c_float), ("default_score_ms", ctypes.c_float)]
+                ("score_ms", ctypes.c_float), ("default_score_ms", ctypes.c_float), ("width", ctypes.c_int32),
+                ("stack", ctypes.c_int32)]
 
 
 class BvhInfo(ctypes.Structure):
@@ -331,11 +333,13 @@ def rt_bvh_export(scene: Scene, stream=None) -> dict:
                 prims=prims[:n], boxes=boxes[: 12 * ni].reshape(-1, 12), info=info)
 
 
-def _trace_params(flags, skip, stats, n_flagged, n, block=0):
+def _trace_params(flags, skip, stats, n_flagged, n, block=0, stack=0):
     import torch
     tp = TraceParams()
     tp.flags = int(flags)
     tp.block = int(block)
+    tp.stack = int(stack)
+    tp.stack = int(stack)
     if skip is not None:
         if skip.shape != (n,):
             raise TypeError("skip must have shape [n]")
@@ -351,7 +355,7 @@ def _trace_params(flags, skip, stats, n_flagged, n, block=0):
 
 
 def rt_trace_closest(scene: Scene, rays, hits=None, skip=None, flags=0, stats=None, n_flagged=None,
-                     stream=None, block=0):
+                     stream=None, block=0, stack=0):
     """Closest hit of every ray; returns hits float32 [n, 4] (see module doc)."""
     import torch
     rp = _dev_ptr(rays, torch.float32, 8, "rays")
@@ -359,7 +363,7 @@ def rt_trace_closest(scene: Scene, rays, hits=None, skip=None, flags=0, stats=No
     if hits is None:
         hits = torch.empty((n, 4), dtype=torch.float32, device=rays.device)
     hp = _dev_ptr(hits, torch.float32, 4, "hits", n)
-    tp = _trace_params(flags, skip, stats, n_flagged, n, block)
+    tp = _trace_params(flags, skip, stats, n_flagged, n, block, stack)
     _check(lib().rt_trace_closest(scene.handle, rp, n, hp, ctypes.byref(tp), _stream(stream)))
     return hits
 
@@ -380,7 +384,7 @@ RT_NOALLOC_MAX_RAYS = 262144
 
 
 def rt_trace_any(scene: Scene, rays, occluded=None, skip=None, flags=0, stats=None, n_flagged=None,
-                 stream=None, block=0):
+                 stream=None, block=0, stack=0):
     """Any hit of every ray; returns uint8 [n] (1 = some triangle within (tmin, tmax))."""
     import torch
     rp = _dev_ptr(rays, torch.float32, 8, "rays")
@@ -388,12 +392,12 @@ def rt_trace_any(scene: Scene, rays, occluded=None, skip=None, flags=0, stats=No
     if occluded is None:
         occluded = torch.empty((n,), dtype=torch.uint8, device=rays.device)
     op = _dev_ptr(occluded, torch.uint8, None, "occluded", n)
-    tp = _trace_params(flags, skip, stats, n_flagged, n, block)
+    tp = _trace_params(flags, skip, stats, n_flagged, n, block, stack)
     _check(lib().rt_trace_any(scene.handle, rp, n, op, ctypes.byref(tp), _stream(stream)))
     return occluded
 
 
-def rt_trace_closest_host(scene: Scene, rays_host, hits_host=None, flags=0, stream=None, block=0):
+def rt_trace_closest_host(scene: Scene, rays_host, hits_host=None, flags=0, stream=None, block=0, stack=0):
     """Closest hit with host buffers (pinned torch tensors or numpy arrays)."""
     import torch
     if isinstance(rays_host, torch.Tensor):

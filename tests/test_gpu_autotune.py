@@ -33,19 +33,23 @@ def test_every_tuning_gives_the_same_hits(rb):
     r = dev(np.concatenate([rays, rnd]))
     s = rb.rt_scene_upload(sc.tris)
     ref = None
-    for ml in (2, 4, 6, 8):
-        for bins in (8, 16, 32):
-            rb.rt_bvh_build(s, alpha=0.7, source=p["source"], max_leaf=ml, bins=bins, dist_norm=1)
-            for tile in (64, 128, 256):
-                h = rb.rt_trace_closest(s, r, block=tile)
-                o = rb.rt_trace_any(s, r, block=tile)
-                torch.cuda.synchronize()
-                got = (h.view(torch.int32).cpu().numpy(), o.cpu().numpy())
-                if ref is None:
-                    ref = got
-                else:
-                    assert np.array_equal(got[0], ref[0]), (ml, bins, tile)
-                    assert np.array_equal(got[1], ref[1]), (ml, bins, tile)
+    for width in (4, 8):
+        for ml in (2, 4, 6, 8):
+            for bins in (8, 16, 32):
+                rb.rt_bvh_build(s, alpha=0.7, source=p["source"], max_leaf=ml, bins=bins, dist_norm=1, width=width)
+                for tile in (64, 128, 256):
+                    for stack in (16, 32, 64):
+                        if (ml, bins) != (4, 16) and stack != 64:
+                            continue  # every stack depth on one tree per width
+                        h = rb.rt_trace_closest(s, r, block=tile, stack=stack)
+                        o = rb.rt_trace_any(s, r, block=tile, stack=stack)
+                        torch.cuda.synchronize()
+                        got = (h.view(torch.int32).cpu().numpy(), o.cpu().numpy())
+                        if ref is None:
+                            ref = got
+                        else:
+                            assert np.array_equal(got[0], ref[0]), (width, ml, bins, tile, stack)
+                            assert np.array_equal(got[1], ref[1]), (width, ml, bins, tile, stack)
 
 
 def test_autotune_result_and_hits(rb, orc):
@@ -53,14 +57,15 @@ def test_autotune_result_and_hits(rb, orc):
     s = rb.rt_scene_upload(sc.tris)
     r = dev(rays)
     res = rb.rt_autotune(s, r, build_weight=1.0, alpha=0.7, source=p["source"], dist_norm=1)
-    assert res["n_tried"] == 36
+    assert res["n_tried"] == 2 * 4 * 3 + 3 * 3 - 1
     assert res["max_leaf"] in (2, 4, 6, 8) and res["bins"] in (8, 16, 32) and res["block"] in (64, 128, 256)
+    assert res["width"] in (4, 8) and res["stack"] in (16, 32, 64)
     assert 0 < res["score_ms"] <= res["default_score_ms"]
     assert res["score_ms"] == pytest.approx(res["build_ms"] + res["trace_ms"], rel=1e-5)
     # the scene is left built with the choice: its tree and hits are valid
     info = rb.rt_bvh_info(s)
     assert info["status"] == 0 and info["max_leaf_size"] <= res["max_leaf"]
-    h = rb.rt_trace_closest(s, r, block=res["block"])
+    h = rb.rt_trace_closest(s, r, block=res["block"], stack=res["stack"])
     torch.cuda.synchronize()
     compare_closest(h.cpu().numpy(), orc.closest_brute(sc.tris, rays), sc.tris, rays, "autotuned")
 
@@ -118,10 +123,11 @@ def test_full_size_in_the_benchmarked_launch_configuration(rb, orc):
     s = rb.rt_scene_upload(sc.tris)
     rays = dev(rays_np)
     tune = rb.rt_autotune(s, rays, build_weight=1.0, alpha=0.7, source=src, dist_norm=1)
-    rb.rt_bvh_build(s, alpha=0.7, source=src, dist_norm=1, max_leaf=tune["max_leaf"], bins=tune["bins"])
+    rb.rt_bvh_build(s, alpha=0.7, source=src, dist_norm=1, max_leaf=tune["max_leaf"], bins=tune["bins"],
+                    width=tune["width"])
     hits = torch.empty((len(rays_np), 4), dtype=torch.float32, device="cuda")
     nflag = torch.zeros(1, dtype=torch.int32, device="cuda")
-    rb.rt_trace_closest(s, rays, hits, n_flagged=nflag, block=tune["block"])
+    rb.rt_trace_closest(s, rays, hits, n_flagged=nflag, block=tune["block"], stack=tune["stack"])
     torch.cuda.synchronize()
     h = hits.cpu().numpy()
     rng = np.random.default_rng(12)
@@ -129,3 +135,39 @@ def test_full_size_in_the_benchmarked_launch_configuration(rb, orc):
     ref = orc.closest_brute(sc.tris, rays_np[sample])
     compare_closest(h[sample], ref, sc.tris, rays_np[sample], "benchmarked configuration")
     assert int(nflag.item()) < len(rays_np) // 1000  # the float64 pass stays rare
+
+
+def test_stack_overflow_goes_to_the_float64_pass(rb, orc):
+    # a 16-deep stack on the deep alpha = 0 tree overflows for some rays: they
+    # are finished by the float64 whole-tree walk and the hits do not change
+    sc, rays, p = scenes.workload_medium(level=4)
+    s = rb.rt_scene_upload(sc.tris)
+    rb.rt_bvh_build(s, alpha=0.0, source=p["source"], max_leaf=1, bins=16, dist_norm=0)
+    r = dev(rays)
+    nf = torch.zeros(1, dtype=torch.int32, device="cuda")
+    deep = rb.rt_trace_closest(s, r, stack=64)
+    short = rb.rt_trace_closest(s, r, stack=16, n_flagged=nf)
+    torch.cuda.synchronize()
+    assert torch.equal(deep.view(torch.int32), short.view(torch.int32))
+    compare_closest(short.cpu().numpy(), orc.closest_brute(sc.tris, rays), sc.tris, rays, "stack 16")
+    print("stack 16 on the alpha = 0 tree: %d rays flagged, depth %d" % (int(nf.item()), rb.rt_bvh_info(s)["depth2"]))
+
+
+@pytest.mark.parametrize("alpha,dist_norm", [(1.0, 0), (0.7, 1), (0.4, 0)])
+def test_width_8_full_icosphere(rb, orc, alpha, dist_norm):
+    # the 8-wide nodes against the checker on all 655,362 medium-city rays
+    sc, rays, p = scenes.workload_medium()
+    s = rb.rt_scene_upload(sc.tris)
+    rb.rt_bvh_build(s, alpha=alpha, source=p["source"], max_leaf=2, bins=16, dist_norm=dist_norm, width=8)
+    info = rb.rt_bvh_info(s)
+    assert info["status"] == 0
+    ref = orc.Bvh(sc.tris, alpha=1.0, max_leaf=4).closest(rays)
+    h = rb.rt_trace_closest(s, dev(rays))
+    torch.cuda.synchronize()
+    compare_closest(h.cpu().numpy(), ref, sc.tris, rays, "width 8 a=%g" % alpha)
+    rb.rt_bvh_build(s, alpha=alpha, source=p["source"], max_leaf=2, bins=16, dist_norm=dist_norm, width=4)
+    info4 = rb.rt_bvh_info(s)
+    # the same binary tree, about half as many levels of traversal nodes
+    assert info4["n_bvh2_internal"] == info["n_bvh2_internal"] and info["depth_wide"] < info4["depth_wide"]
+    print("width 8 a=%g: %d traversal nodes, depth %d (width 4: %d, depth %d)" % (
+        alpha, info["n_wide"], info["depth_wide"], info4["n_wide"], info4["depth_wide"]))
