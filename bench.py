@@ -43,7 +43,7 @@ WORKLOAD = "medium_city_1000_buildings_icosphere_L8"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--alpha", type=float, default=0.7)
@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--batched-runs", type=int, default=5)
     ap.add_argument("--serve-seconds", type=float, default=6.0)
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and served comparisons")
+    ap.add_argument("--extras", default="alpha_sweep,quantised_nodes,reception,large,batched,served",
+                    help="comma-separated extras to run")
     return ap.parse_args()
 
 
@@ -327,6 +329,7 @@ def run_large(rtbvh, torch, hbm, runs=3):
                 rtbvh.rt_trace_closest(scene, rays, hits, stream=st)
         st.synchronize()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(runs)]
+        torch.cuda.nvtx.range_push("metro_trace_alpha_%g" % alpha)
         with torch.cuda.stream(st):
             for a, c in ev:
                 flush.zero_()
@@ -334,6 +337,7 @@ def run_large(rtbvh, torch, hbm, runs=3):
                 rtbvh.rt_trace_closest(scene, rays, hits, stream=st)
                 c.record(st)
         st.synchronize()
+        torch.cuda.nvtx.range_pop()
         ms_trace = statistics.mean(a.elapsed_time(c) for a, c in ev)
         evq = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(runs)]
         with torch.cuda.stream(st):
@@ -351,21 +355,24 @@ def run_large(rtbvh, torch, hbm, runs=3):
         sm = stats.double().mean(0).cpu().numpy()
         per_ray = 32 + 16 + 128 * float(sm[0]) + 48 * float(sm[1])
         gbs = per_ray * R / (ms_trace * 1e-3) / 1e9
-        traffic, ncu_ms = NCU_TRAFFIC_LARGE[alpha]
+        traffic, ncu_src = NCU_TRAFFIC_LARGE[alpha]
         out["alpha_%g" % alpha] = {
             "build_ms": build_ms, "bvh": {k: info[k] for k in ("n_wide", "depth2", "depth_wide")},
             "trace_ms": ms_trace, "trace_mrays_s": R / (ms_trace * 1e-3) / 1e6,
             "trace_ms_quantised_nodes": ms_quant,
             "hit_fraction": float((hits[:, 1].view(torch.int32) >= 0).double().mean().item()),
             "nodes_per_ray": float(sm[0]), "tris_per_ray": float(sm[1]),
-            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-                         "bytes_per_ray": per_ray, "kernel": "k_trace + k_retest64",
+            "roofline": {"bound": "hbm",
+                         "achieved": traffic / (ms_trace * 1e-3) / 1e9 if traffic else None,
+                         "peak": hbm, "unit": "GB/s",
+                         "frac": traffic / (ms_trace * 1e-3) / 1e9 / hbm if traffic else None,
                          "traffic": traffic, "traffic_unit": "bytes per launch",
-                         "dram_gbs_from_traffic": traffic / (ms_trace * 1e-3) / 1e9,
-                         "traffic_source": "ncu capture of k_trace<0,0,128> on these rays (%.1f ms cold)" % ncu_ms,
-                         "note": "algorithmic bytes count every node and triangle fetch; the upper tree stays "
-                                 "in L1/L2, so DRAM sees a small part of them: the walk is latency- and "
-                                 "issue-bound, not HBM-bound"}}
+                         "traffic_source": ncu_src, "kernel": "k_trace + k_retest64",
+                         "algorithmic_bytes_per_ray": per_ray, "algorithmic_gbs": gbs,
+                         "note": "achieved = DRAM bytes of the launch (ncu) over its event time: the fraction of "
+                                 "HBM the walk really uses.  The algorithmic bytes count every node and triangle "
+                                 "fetch; most hit in L1/L2 (the upper tree stays cached), so they exceed DRAM "
+                                 "traffic many times: the walk is latency- and issue-bound"}}
     # a tree per transmitter (NEXT-2): source = the transmitter, pruned to its ray action
     # range; the paper's one-transmitter comparison of the traditional and improved trees
     per_tx = {}
@@ -578,14 +585,35 @@ def run_served(rtbvh, torch, seconds):
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # two kernels on this workload, from one ncu capture each of the current
 # kernels (max_leaf 4, 16 bins, 128-ray tile, alpha 0.7).
-NCU_TRAFFIC_LARGE = {  # k_trace<0,0,128> on 4 x 2^21 metro rays (1 ncu pass per launch)
-    0.7: (362.787072e6 + 325.806592e6, 9.5426), 1.0: (294.681088e6 + 144.702976e6, 4.3015)}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
+# one ncu capture of the current kernels (profiles/); None until captured.
+NCU_TRAFFIC_LARGE = {0.7: (None, "not captured for the current kernel"),
+                     1.0: (None, "not captured for the current kernel")}
 NCU_TRAFFIC = {
-    "k_split": (1.703680e6 + 512.0, "ncu capture of k_split, medium city (profiles/k_split_medium_city.md)"),
-    "k_trace": (21.493760e6 + 0.058624e6,
-                "ncu capture of k_trace<0,0,128> (k_retest64 not included), medium city "
-                "(profiles/k_trace_medium_city.md)"),
+    "k_split": (1.272064e6 + 768.0, "ncu capture of k_split in the timed steps, medium city, autotuned tree "
+                                    "(profiles/k_split_medium_city.md)"),
+    "k_trace": (21.495808e6 + 47872.0, "ncu capture of k_trace<0,0,128,64,0,4> in the timed steps, medium "
+                                       "city (k_retest64 not included; profiles/k_trace_medium_city.md)"),
 }
+
+
+def l2_read_gbs(rtbvh, torch, mb=24, reps=200):
+    """L2 read bandwidth: one launch of rt_probe_l2_read over a buffer that
+    stays in L2, CUDA-event timed on its stream (best of 5 launches)."""
+    buf = torch.ones(mb << 18, dtype=torch.float32, device="cuda")
+    st = torch.cuda.Stream()
+    best = None
+    with torch.cuda.stream(st):
+        rtbvh.rt_probe_l2_read(buf, 2, stream=st)
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            rtbvh.rt_probe_l2_read(buf, reps, stream=st)
+            e1.record(st)
+            st.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+    return (mb << 20) * reps / (best * 1e-3) / 1e9
 
 
 def split_kernel_bytes(ex):
@@ -708,6 +736,7 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     lc0 = rtbvh.rt_launch_count()
+    torch.cuda.nvtx.range_push("timed_steps")
     with torch.cuda.stream(stream):
         for k in range(args.steps):
             flush.zero_()
@@ -718,6 +747,7 @@ def run_ours(args):
             run_trace()
             evs[k][2].record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     lc1 = rtbvh.rt_launch_count()
     rtbvh.rt_scene_set_split_events(scene)
     if dist:
@@ -731,14 +761,14 @@ def run_ours(args):
     gpu_launches = (lc1 - lc0) + (trace_launches * args.steps if use_graph else 0)
 
     # e2e: host buffers through the C ABI (scene + rays in, hits out, every step)
-    tris_host = np.ascontiguousarray(sc.tris)
+    tris_pin = torch.from_numpy(np.ascontiguousarray(sc.tris)).pin_memory()
     rays_pin = torch.from_numpy(rays_np).pin_memory()
     hits_pin = torch.empty((R, 4), dtype=torch.float32).pin_memory()
     e2e_ms = []
     for k in range(args.warmup + args.e2e_steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        rtbvh.rt_scene_update(scene, tris_host, stream=stream)
+        rtbvh.rt_scene_update(scene, tris_pin, stream=stream)
         rtbvh.rt_bvh_build(scene, stream=stream, **bp)
         rtbvh.rt_trace_closest_host(scene, rays_pin, hits_pin, stream=stream, block=tile, stack=stack)
         torch.cuda.synchronize()
@@ -756,49 +786,51 @@ def run_ours(args):
     hbm = peaks.get("hbm_gbs")
     peak_src = "measured" if hbm else "fallback"
     hbm = hbm or 6800.0
-    # L2-resident copy probe (the BVH and triangles of this scene fit in L2)
-    a = torch.empty(24 << 20, dtype=torch.uint8, device="cuda")
-    b = torch.empty_like(a)
-    for _ in range(5):
-        b.copy_(a)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(50):
-        b.copy_(a)
-    e1.record()
-    torch.cuda.synchronize()
-    l2_gbs = 50 * 2 * a.numel() / (e0.elapsed_time(e1) * 1e-3) / 1e9
+    # L2 read probe (the BVH and triangles of this scene fit in L2): one
+    # launch of the library's probe kernel reading 24 MB 200 times
+    l2_gbs = l2_read_gbs(rtbvh, torch)
 
     extra = {}
-    if not args.no_extra:
+    want = set() if args.no_extra else set(x.strip() for x in args.extras.split(",") if x.strip())
+    if "alpha_sweep" in want:
         extra["alpha_sweep"] = run_alpha_sweep(rtbvh, torch, sc, rays, p["source"])
+    if "quantised_nodes" in want:
         extra["quantised_nodes"] = run_quantised(rtbvh, torch, scene, rays, dict(bp, quantize=1, width=4), tile)
+    if "reception" in want:
+        rtbvh.rt_bvh_build(scene, stream=stream, **bp)
         with torch.cuda.stream(stream):
             run_trace()
         stream.synchronize()
         extra["reception"] = run_reception(rtbvh, torch, scenes, rays, hits, hbm)
+    if "large" in want:
         extra["large"] = run_large(rtbvh, torch, hbm)
+    if "batched" in want:
         extra["batched"] = run_batched(rtbvh, torch, args.batched_runs)
+    if "served" in want:
         extra["served"] = run_served(rtbvh, torch, args.serve_seconds)
     mean_trace_ms = statistics.mean(trace_ms)
     mean_split_ms = statistics.mean(split_ms)
     trace_gbs = bytes_per_ray * R / (mean_trace_ms * 1e-3) / 1e9
     split_gbs = split_bytes / (mean_split_ms * 1e-3) / 1e9
-    roof_trace = {"bound": "hbm", "achieved": trace_gbs, "peak": hbm, "unit": "GB/s", "frac": trace_gbs / hbm,
+    roof_trace = {"bound": "l2", "achieved": trace_gbs, "peak": l2_gbs, "unit": "GB/s",
+                  "frac": trace_gbs / l2_gbs,
+                  "peak_source": "measured in this run: rt_probe_l2_read, one launch reading 24 MB 200 times "
+                                 "with L2-only loads",
                   "traffic": NCU_TRAFFIC["k_trace"][0], "traffic_unit": "bytes per launch",
                   "traffic_source": NCU_TRAFFIC["k_trace"][1],
-                  "kernel": "k_trace + k_retest64 (one rt_trace_closest)", "peak_source": peak_src,
+                  "kernel": "k_trace + k_retest64 (one rt_trace_closest)",
                   "ms": mean_trace_ms, "bytes_per_ray": bytes_per_ray, "algorithmic_bytes": bytes_per_ray * R,
-                  "l2_probe_gbs": l2_gbs, "frac_of_l2_probe": trace_gbs / l2_gbs,
+                  "hbm_peak": hbm, "hbm_peak_source": peak_src, "frac_of_hbm": trace_gbs / hbm,
                   "note": "algorithmic bytes = 32 ray + 16 hit + node bytes (32 B per child slot) x nodes + "
-                          "48 B x triangles per ray; "
-                          "nodes and triangles stay in L2 for this scene"}
+                          "48 B x triangles per ray; the nodes and triangles of this scene stay in L2 (DRAM "
+                          "sees only the rays and hits), so the L2 read rate bounds the walk; node fetches "
+                          "that hit in L1 can carry the algorithmic rate past it"}
     roof_split = {"bound": "hbm", "achieved": split_gbs, "peak": hbm, "unit": "GB/s", "frac": split_gbs / hbm,
                   "traffic": NCU_TRAFFIC["k_split"][0], "traffic_unit": "bytes per launch",
                   "traffic_source": NCU_TRAFFIC["k_split"][1],
                   "kernel": "k_split (one launch per build)", "peak_source": peak_src,
-                  "ms": mean_split_ms, "algorithmic_bytes": split_bytes, "l2_probe_gbs": l2_gbs,
-                  "frac_of_l2_probe": split_gbs / l2_gbs,
+                  "ms": mean_split_ms, "algorithmic_bytes": split_bytes, "l2_peak_gbs": l2_gbs,
+                  "frac_of_l2": split_gbs / l2_gbs,
                   "note": "algorithmic bytes = 64 B per record per binary level above the 32-triangle subtrees "
                           "+ 64 B per record for its subtree + 72 B per binary node; the kernel is bound by the "
                           "latency of dependent splits, not by bandwidth (events recorded by the library around "
@@ -834,7 +866,8 @@ def run_ours(args):
         "e2e": {"value": R / (e2e_step * 1e-3) / 1e6, "unit": UNIT,
                 "h2d_bytes_per_step": int(T * 36 + R * 32), "d2h_bytes_per_step": int(R * 16),
                 "ms_per_step": e2e_step,
-                "path": "rt_scene_update(host) + rt_bvh_build + rt_trace_closest_host(pinned)"},
+                "path": "rt_scene_update(pinned host triangles) + rt_bvh_build + rt_trace_closest_host(pinned "
+                        "rays and hits; ray copies under the build)"},
         "gpu_launches": int(gpu_launches),
         "clocks": clk,
     }

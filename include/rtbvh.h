@@ -205,6 +205,16 @@ typedef struct {
 int rt_autotune(rt_scene scene, const rt_build_params* base, const rt_ray* rays_dev, int64_t n_rays,
                 float build_weight, rt_tune_result* out, void* stream);
 
+/* Instrumentation (no counterpart in the paper): enqueue one launch that
+ * reads the device buffer buf_dev (`bytes`, a multiple of 16, 16-byte
+ * aligned; small enough to stay in the L2, e.g. 24 MB) `reps` times with
+ * 16-byte loads cached in the L2 only.  Timing it with events on `stream`
+ * gives the L2 read bandwidth, bytes * reps / time, the ceiling of a walk
+ * whose nodes and triangles stay in the L2.  sink_dev (nullable, one word
+ * per block: 4 x the SM count) is written only to keep the loads; the buffer's
+ * contents do not matter.  Errors: RT_EINVAL, RT_ECUDA. */
+int rt_probe_l2_read(const void* buf_dev, int64_t bytes, int32_t reps, uint32_t* sink_dev, void* stream);
+
 /* Test hooks (no counterpart in the paper): make failures happen on purpose,
  * without faulting the device, so that the error paths can be tested.
  * Process-wide; value 0 turns a hook off.

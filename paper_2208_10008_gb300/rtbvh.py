@@ -41,7 +41,7 @@ EXPORTS = ["rt_version", "rt_launch_count", "rt_last_error", "rt_scene_upload", 
            "rt_batch_visibility", "rt_batch_destroy", "rt_session_create", "rt_session_add_scene",
            "rt_session_submit", "rt_session_poll", "rt_session_wait", "rt_session_release", "rt_session_stats_get",
            "rt_session_destroy", "rt_scene_set_split_events", "rt_autotune", "rt_debug_inject",
-           "rt_rxset_create", "rt_rxset_destroy", "rt_receive", "rt_batch_received", "rt_abi_struct_sizes"]
+           "rt_rxset_create", "rt_rxset_destroy", "rt_receive", "rt_batch_received", "rt_abi_struct_sizes", "rt_probe_l2_read"]
 
 # test hooks (rt_debug_inject)
 RT_DEBUG_SPIN_LIMIT, RT_DEBUG_PHANTOM_TASK, RT_DEBUG_PHANTOM_ITEM, RT_DEBUG_FAIL_ALLOC = 1, 2, 3, 4
@@ -160,6 +160,7 @@ def lib(build: bool = True):
             L.rt_batch_visibility.argtypes = [vp, ctypes.POINTER(vp)]
             L.rt_batch_received.argtypes = [vp, i32, ctypes.POINTER(vp), ctypes.POINTER(vp)]
             L.rt_abi_struct_sizes.argtypes = [ctypes.POINTER(ctypes.c_int64), i32]
+            L.rt_probe_l2_read.argtypes = [vp, i64, i32, vp, vp]
             L.rt_batch_destroy.argtypes = [vp]
             L.rt_session_create.argtypes = [ctypes.c_size_t, i32, ctypes.POINTER(vp)]
             L.rt_session_add_scene.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int32)]
@@ -253,12 +254,21 @@ def rt_scene_upload(tris, stream=None) -> Scene:
 
 
 def rt_scene_update(scene: Scene, tris, stream=None):
+    """Replace the scene's triangles: a CUDA tensor, a host tensor (pinned: the
+    copy is asynchronous on `stream`; keep the tensor until the stream has
+    reached the call) or any array-like (copied, then waited for)."""
     import torch
     if isinstance(tris, torch.Tensor) and tris.is_cuda:
         t = tris.reshape(-1, 9)
         _dev_ptr(t, torch.float32, 9, "tris")
         _check(lib().rt_scene_update(scene.handle, ctypes.c_void_p(t.data_ptr()), t.shape[0], 1, _stream(stream)))
         scene.n_tri = t.shape[0]
+    elif isinstance(tris, torch.Tensor):
+        if tris.dtype != torch.float32 or not tris.is_contiguous() or tris.numel() % 9:
+            raise TypeError("host tris must be a contiguous float32 tensor of [n, 3, 3] or [n, 9]")
+        n = tris.numel() // 9
+        _check(lib().rt_scene_update(scene.handle, ctypes.c_void_p(tris.data_ptr()), n, 0, _stream(stream)))
+        scene.n_tri = n
     else:
         a = np.ascontiguousarray(np.asarray(tris, dtype=np.float32).reshape(-1, 9))
         _check(lib().rt_scene_update(scene.handle, a.ctypes.data_as(ctypes.c_void_p), a.shape[0], 0, _stream(stream)))
@@ -699,3 +709,12 @@ def rt_receive(rs: RxSet, rays, hits, delta, range0, out=None, count=None, n_dev
     p = ReceiveParams(float(delta), float(range0), int(out.shape[0]), 0, sp, None)
     _check(lib().rt_receive(rs.handle, rp, hp, n, nd, ctypes.byref(p), op, cp, _stream(stream)))
     return out, count
+
+
+def rt_probe_l2_read(buf, reps, stream=None):
+    """One launch reading the device tensor `buf` (fits in L2) `reps` times; time it with events."""
+    import torch
+    if not (isinstance(buf, torch.Tensor) and buf.is_cuda and buf.is_contiguous()):
+        raise TypeError("buf must be a contiguous CUDA tensor")
+    nbytes = buf.numel() * buf.element_size()
+    _check(lib().rt_probe_l2_read(ctypes.c_void_p(buf.data_ptr()), nbytes, int(reps), None, _stream(stream)))
