@@ -55,7 +55,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--batched-runs", type=int, default=5)
-    ap.add_argument("--serve-seconds", type=float, default=6.0)
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--serve-repeats", type=int, default=3)
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and served comparisons")
     ap.add_argument("--extras", default="alpha_sweep,quantised_nodes,reception,large,batched,served",
                     help="comma-separated extras to run")
@@ -537,8 +538,13 @@ def run_alpha_sweep(rtbvh, torch, sc, rays, source, reps=10):
     return out
 
 
-def run_served(rtbvh, torch, seconds):
-    """8 resident scenes, Poisson 200 req/s, 64k-4M rays, <= 2 reflections; admission by a pool budget."""
+def run_served(rtbvh, torch, seconds, repeats=3, pool_gib=1.0):
+    """8 resident scenes, Poisson 200 req/s for `seconds`, 64k-4M rays, <= 2
+    reflections.  The same request set is served `repeats` times with 8 slots
+    (continuous batching), once one at a time (1 slot), and once all at
+    once (saturation); the pool budget (1 GiB: about one 4M-ray request)
+    makes memory admission bind.  Latency = submit to completion, split into
+    queue wait (submit to admission) and run time (admission to completion)."""
     from paper_2208_10008_gb300 import scenes
     scs = scenes.serving_scenes()
     built = []
@@ -550,45 +556,66 @@ def run_served(rtbvh, torch, seconds):
         built.append(s)
     torch.cuda.synchronize()
     arrivals = scenes.serving_arrivals(scs, seconds)
+    pool = int(pool_gib * (1 << 30))
 
-    def serve(slots, items):
-        sess = rtbvh.Session(pool_bytes=8 << 30, max_slots=slots)
+    def serve(slots, items, paced=True):
+        sess = rtbvh.Session(pool_bytes=pool, max_slots=slots)
         ids = [sess.add_scene(s) for s in built]
         t0 = time.perf_counter()
-        tickets = []
+        live = []
         for (ta, k, tx, n, mo) in items:
             now = time.perf_counter() - t0
-            if ta > now:
+            if paced and ta > now:
                 time.sleep(ta - now)
-            tickets.append(sess.submit(ids[k], tx, rtbvh.RT_RAYS_FIBONACCI, n, mo, 1000.0, want_hits=False))
-        for t in tickets:
+            live.append(sess.submit(ids[k], tx, rtbvh.RT_RAYS_FIBONACCI, n, mo, 1000.0, want_hits=False))
+            if len(live) > 64:  # forget finished requests as we go
+                keep = []
+                for t in live:
+                    if sess.poll(t):
+                        sess.release(t)
+                    else:
+                        keep.append(t)
+                live = keep
+        for t in live:
             sess.wait(t, timeout_s=600)
         st = sess.stats()
         sess.destroy()
-        return st
+        return {"requests": st["completed"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+                "mean_ms": st["mean_ms"], "wait_p50_ms": st["wait_p50_ms"], "wait_p99_ms": st["wait_p99_ms"],
+                "run_p50_ms": st["run_p50_ms"], "run_p99_ms": st["run_p99_ms"],
+                "mrays_s": st["rays"] / max(st["span_s"], 1e-9) / 1e6, "peak_running": st["peak_running"],
+                "peak_pool_gb": st["peak_pool_bytes"] / 2 ** 30}
 
-    st = serve(8, arrivals)
-    n_seq = min(len(arrivals), 200)
-    sq = serve(1, arrivals[:n_seq])
+    mixed = [serve(8, arrivals) for _ in range(repeats)]
+    alone = serve(1, arrivals)
+    sat = serve(8, arrivals, paced=False)
     for s in built:
         s.destroy()
+
+    def spread(key):
+        v = sorted(m[key] for m in mixed)
+        return {"median": v[len(v) // 2], "min": v[0], "max": v[-1]}
+
     return {"workload": "8_resident_scenes_poisson_200hz_64k-4M_rays_orders0-2", "n_tri": [sc.n_tri for sc in scs],
-            "requests": st["completed"], "seconds_of_arrivals": seconds,
-            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
-            "mrays_s": st["rays"] / max(st["span_s"], 1e-9) / 1e6, "peak_running": st["peak_running"],
-            "peak_pool_gb": st["peak_pool_bytes"] / 2 ** 30, "pool_gb": st["pool_bytes"] / 2 ** 30,
-            "one_at_a_time": {"requests": sq["completed"], "p50_ms": sq["p50_ms"], "p99_ms": sq["p99_ms"],
-                              "mrays_s": sq["rays"] / max(sq["span_s"], 1e-9) / 1e6}}
+            "requests": len(arrivals), "seconds_of_arrivals": seconds, "pool_gb": pool / 2 ** 30, "slots": 8,
+            "repeats": repeats,
+            "p50_ms": spread("p50_ms")["median"], "p99_ms": spread("p99_ms")["median"],
+            "mrays_s": spread("mrays_s")["median"],
+            "spread": {k: spread(k) for k in ("p50_ms", "p99_ms", "wait_p99_ms", "run_p99_ms", "mrays_s")},
+            "runs": mixed, "one_at_a_time": alone, "saturation": sat,
+            "note": "the same arrival set in every run; mixed = 8 slots with memory admission, one_at_a_time = "
+                    "1 slot, saturation = every request submitted at once (throughput bound); hits stay on the "
+                    "device (want_hits off), per-order counts are copied back"}
 
 
 # ---------------------------------------------------------------- GPU
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# two kernels on this workload, from one ncu capture each of the current
-# kernels (max_leaf 4, 16 bins, 128-ray tile, alpha 0.7).
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
 # one ncu capture of the current kernels (profiles/); None until captured.
-NCU_TRAFFIC_LARGE = {0.7: (None, "not captured for the current kernel"),
-                     1.0: (None, "not captured for the current kernel")}
+NCU_TRAFFIC_LARGE = {
+    0.7: (362.228224e6 + 322.753024e6, "ncu capture of k_trace<0,0,128,64,0,4> on the 4 x 2^21 metro rays, "
+                                       "alpha 0.7 tree (profiles/k_trace_metro.md)"),
+    1.0: (294.764544e6 + 144.213248e6, "ncu capture of k_trace<0,0,128,64,0,4> on the 4 x 2^21 metro rays, "
+                                       "alpha 1 tree (profiles/k_trace_metro.md)")}
 NCU_TRAFFIC = {
     "k_split": (1.272064e6 + 768.0, "ncu capture of k_split in the timed steps, medium city, autotuned tree "
                                     "(profiles/k_split_medium_city.md)"),
@@ -807,7 +834,7 @@ def run_ours(args):
     if "batched" in want:
         extra["batched"] = run_batched(rtbvh, torch, args.batched_runs)
     if "served" in want:
-        extra["served"] = run_served(rtbvh, torch, args.serve_seconds)
+        extra["served"] = run_served(rtbvh, torch, args.serve_seconds, args.serve_repeats)
     mean_trace_ms = statistics.mean(trace_ms)
     mean_split_ms = statistics.mean(split_ms)
     trace_gbs = bytes_per_ray * R / (mean_trace_ms * 1e-3) / 1e9

@@ -468,6 +468,14 @@ typedef struct {
   float tmax;                /* ray action range */
   rt_hit* hits_host;         /* nullable: receives the closest hits of the launched rays */
   int64_t* order_counts_host;/* nullable: receives rays traced per order [max_order + 1] */
+  rt_hit* const* order_hits_host; /* nullable: host array of max_order + 1 pointers; entry k
+                                     (k >= 1, nullable) receives the closest hits of the
+                                     order-k reflected rays, in the order of their parents
+                                     (order_counts_host[k] of them; room for the launch's
+                                     ray count); entry 0 is not used (see hits_host) */
+  int32_t* const* order_src_host; /* nullable: like order_hits_host; entry k (k >= 1) receives
+                                     the index of each order-k ray's parent among the
+                                     order-(k-1) rays */
 } rt_request;
 
 typedef struct {
@@ -477,13 +485,15 @@ typedef struct {
   double p50_ms, p99_ms, mean_ms; /* submit-to-completion latency of the last
                                      2^20 completed requests */
   double span_s;             /* first submit to last completion */
+  double wait_p50_ms, wait_p99_ms; /* of the same requests: submit to admission (queue wait) */
+  double run_p50_ms, run_p99_ms;   /* and admission to completion (on the device, results copied) */
 } rt_session_stats;
 
 /* Create a serving session: one device pool of pool_bytes (allocated now)
  * and max_slots concurrent requests (1..64), each on its own stream.  A
  * worker thread admits queued requests in arrival order whenever a slot is
- * free and the pool holds all of the request's buffers (rays, hits and skip
- * arrays per order, re-test scratch: about n * (52 (max_order + 1) + 44)
+ * free and the pool holds all of the request's buffers (rays, hits, skip and
+ * parent arrays per order, re-test scratch: about n * (56 (max_order + 1) + 44)
  * bytes for n rays), so requests of uneven sizes run side by side on the
  * device.  The calling thread's current device is used.
  * Errors: RT_EINVAL, RT_ENOMEM, RT_ECUDA. */

@@ -55,6 +55,8 @@ struct rt_batch_s {
   float* delta[RT_BATCH_MAX_ORDER + 1] = {};    // per ray: its transmitter's delta
   rt_rx_record* rec[RT_BATCH_MAX_ORDER + 1] = {};
   int* rx_count = nullptr;                      // device: pairs of order k at rx_count[k]
+  long long* tx_off = nullptr;                  // device: first order-0 ray of each transmitter
+  float* tx_delta = nullptr;                    // device: each transmitter's delta
 };
 
 namespace rt {
@@ -111,6 +113,8 @@ void free_batch(rt_batch_s* b) {
     if (b->rec[k]) cudaFree(b->rec[k]);
   }
   if (b->rx_count) cudaFree(b->rx_count);
+  if (b->tx_off) cudaFree(b->tx_off);
+  if (b->tx_delta) cudaFree(b->tx_delta);
   for (int k = 0; k <= RT_BATCH_MAX_ORDER; ++k) {
     if (b->rays[k]) cudaFree(b->rays[k]);
     if (b->hits[k]) cudaFree(b->hits[k]);
@@ -234,9 +238,13 @@ static int rt_batch_create_body(rt_scene scene, const rt_batch_desc* d, rt_batch
   if (total < 1 || total > INT_MAX) return rt::set_error(RT_EINVAL, "total ray count out of range");
   b->n0 = total;
   b->n_seg = (long long)d->n_tx * d->n_rx;
-  cudaError_t e = cudaSuccess;
+  // every upload and initialisation below is ordered on the batch's own
+  // stream: creating a batch never waits for other streams' work
+  cudaError_t e = cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
   for (int k = 0; k <= b->max_order && e == cudaSuccess; ++k) {
-    e = alloc(&b->rays[k], total);
+    if (e == cudaSuccess) e = alloc(&b->rays[k], total);
     if (e == cudaSuccess) e = alloc(&b->hits[k], total);
     if (e == cudaSuccess && k > 0) e = alloc(&b->skip[k], total);
     if (e == cudaSuccess && k > 0) e = alloc(&b->src[k], total);
@@ -260,10 +268,11 @@ static int rt_batch_create_body(rt_scene scene, const rt_batch_desc* d, rt_batch
           const float* c = d->rx_pos + 3 * r;
           s = rt_ray{a[0], a[1], a[2], 0.f, c[0] - a[0], c[1] - a[1], c[2] - a[2], 1.f};
         }
-      e = cudaMemcpy(b->seg, h.data(), h.size() * sizeof(rt_ray), cudaMemcpyHostToDevice);
+      e = cudaMemcpyAsync(b->seg, h.data(), h.size() * sizeof(rt_ray), cudaMemcpyHostToDevice, b->st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);  // h is a host temporary
     }
   }
-  if (e == cudaSuccess) e = cudaMemset(b->counts, 0, (RT_BATCH_MAX_ORDER + 1) * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->counts, 0, (RT_BATCH_MAX_ORDER + 1) * sizeof(int), b->st);
   if (e == cudaSuccess && d->receive) {
     // each transmitter's delta: the caller's, or the spacing of its launch
     std::vector<float> dtx(b->n_tx);
@@ -285,25 +294,21 @@ static int rt_batch_create_body(rt_scene scene, const rt_batch_desc* d, rt_batch
       if (e == cudaSuccess) e = alloc(&b->rec[k], b->max_rx);
     }
     if (e == cudaSuccess) e = alloc(&b->rx_count, RT_BATCH_MAX_ORDER + 1);
-    if (e == cudaSuccess) e = cudaMemset(b->rx_count, 0, (RT_BATCH_MAX_ORDER + 1) * sizeof(int));
-    long long* off = nullptr;
-    float* dd = nullptr;
-    if (e == cudaSuccess) e = alloc(&off, b->n_tx);
-    if (e == cudaSuccess) e = alloc(&dd, b->n_tx);
-    if (e == cudaSuccess) e = cudaMemcpy(off, b->offset.data(), b->n_tx * sizeof(long long), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(dd, dtx.data(), b->n_tx * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->rx_count, 0, (RT_BATCH_MAX_ORDER + 1) * sizeof(int), b->st);
+    if (e == cudaSuccess) e = alloc(&b->tx_off, b->n_tx);
+    if (e == cudaSuccess) e = alloc(&b->tx_delta, b->n_tx);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(b->tx_off, b->offset.data(), b->n_tx * sizeof(long long), cudaMemcpyHostToDevice, b->st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(b->tx_delta, dtx.data(), b->n_tx * sizeof(float), cudaMemcpyHostToDevice, b->st);
     if (e == cudaSuccess) {
-      k_delta_fill<<<(int)((total + 255) / 256), 256>>>(off, dd, b->n_tx, (int)total, b->delta[0]);
+      k_delta_fill<<<(int)((total + 255) / 256), 256, 0, b->st>>>(b->tx_off, b->tx_delta, b->n_tx, (int)total,
+                                                                  b->delta[0]);
       rt::count_launches(1);
       e = cudaGetLastError();
-      if (e == cudaSuccess) e = cudaDeviceSynchronize();
     }
-    if (off) cudaFree(off);
-    if (dd) cudaFree(dd);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);  // dtx is a host temporary
   }
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return rt::set_error(e == cudaErrorMemoryAllocation ? RT_ENOMEM : RT_ECUDA, cudaGetErrorString(e));

@@ -587,7 +587,10 @@ int rt_trace_closest_host(rt_scene s, const rt_ray* rays_host, int64_t n, rt_hit
   if (params && (params->flags & RT_QUANTIZED_NODES) && !s->q_built)
     return fail(RT_EINVAL, "RT_QUANTIZED_NODES needs a build with quantize = 1");
   if (n == 0) return RT_OK;
-  const int64_t chunk = n < (int64_t(1) << 18) ? n : (int64_t(1) << 18);
+  // two chunks when they fit in 2 x 2^20 rays (both ray copies can then go
+  // under whatever the caller's stream is still doing), else chunks of 2^20
+  int64_t chunk = (n + 1) / 2;
+  if (chunk > (int64_t(1) << 20)) chunk = int64_t(1) << 20;
   if (s->stage_cap < chunk) {
     for (int k = 0; k < 2; ++k) {
       RT_CUDA(dev_alloc(&s->stage_rays[k], chunk), "alloc staging");
@@ -600,12 +603,12 @@ int rt_trace_closest_host(rt_scene s, const rt_ray* rays_host, int64_t n, rt_hit
     int r = ensure_scratch(s->host_scr[k], chunk);
     if (r) return r;
   }
-  // the pipeline starts after everything already queued on the caller's stream
+  // the ray copies start at once (they read only the caller's host buffer);
+  // the traces wait for everything already queued on the caller's stream
+  // (typically the build)
   cudaEvent_t ev;
   RT_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "create event");
-  cudaEventRecord(ev, (cudaStream_t)stream);
-  for (int k = 0; k < 2; ++k) cudaStreamWaitEvent(s->host_streams[k], ev, 0);
-  cudaEventDestroy(ev);
+  RT_CUDA(cudaEventRecord(ev, (cudaStream_t)stream), "record event");
   rt_trace_params tp{};
   if (params) {  // n_flagged_dev counts one call of the device path: not written here
     tp.flags = params->flags;
@@ -619,6 +622,7 @@ int rt_trace_closest_host(rt_scene s, const rt_ray* rays_host, int64_t n, rt_hit
     cudaStream_t st = s->host_streams[k];
     cudaError_t e = cudaMemcpyAsync(s->stage_rays[k], rays_host + off, cnt * sizeof(rt_ray),
                                     cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && c < 2) e = cudaStreamWaitEvent(st, ev, 0);
     if (e == cudaSuccess) e = rt::launch_trace(s, s->stage_rays[k], cnt, s->stage_hits[k], nullptr, &tp, s->host_scr[k], st);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(hits_host + off, s->stage_hits[k], cnt * sizeof(rt_hit), cudaMemcpyDeviceToHost, st);
@@ -631,6 +635,7 @@ int rt_trace_closest_host(rt_scene s, const rt_ray* rays_host, int64_t n, rt_hit
     cudaError_t e = cudaStreamSynchronize(s->host_streams[k]);
     if (e != cudaSuccess && rc == RT_OK) rc = cuda_fail(e, "synchronize pipeline");
   }
+  cudaEventDestroy(ev);
   return rc;
 }
 

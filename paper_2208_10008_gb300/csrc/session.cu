@@ -95,6 +95,7 @@ struct Req {
   rt_ray* rays[RT_BATCH_MAX_ORDER + 1] = {};
   rt_hit* hits[RT_BATCH_MAX_ORDER + 1] = {};
   int* skip[RT_BATCH_MAX_ORDER + 1] = {};
+  int* src[RT_BATCH_MAX_ORDER + 1] = {};
   int* counts = nullptr;
   int* blocks = nullptr;
   rt::TraceScratch scr;
@@ -110,12 +111,12 @@ struct Slot {
 };
 
 size_t request_bytes(long long n, int orders) {
-  const size_t per_order = (size_t)n * (sizeof(rt_ray) + sizeof(rt_hit) + sizeof(int));
+  const size_t per_order = (size_t)n * (sizeof(rt_ray) + sizeof(rt_hit) + 2 * sizeof(int));
   size_t b = per_order * (size_t)(orders + 1);
   b += 64 + (size_t)(RT_BATCH_MAX_ORDER + 1) * sizeof(int);      // counts
   b += ((size_t)n / 256 + 2) * sizeof(int);                       // reflect blocks
   b += 64 + (size_t)n * sizeof(int) * (1 + rt::kTraceCand + 1);    // trace counter, queue, candidates
-  return b + 64 * 256;                                            // alignment slack (<= 40 arrays)
+  return b + 64 * 256;                                            // alignment slack (<= 48 arrays)
 }
 
 }  // namespace
@@ -136,8 +137,9 @@ struct rt_session_s {
   uint64_t next_ticket = 1;
   bool stop = false;
   std::thread worker;
-  // statistics
-  std::vector<double> lat_ms;  // ring of the last kLatencyWindow latencies
+  // statistics: rings of the last kLatencyWindow latencies (submit to done),
+  // queue waits (submit to admission) and run times (admission to done)
+  std::vector<double> lat_ms, wait_ms, run_ms;
   size_t lat_next = 0;
   long long submitted = 0, completed = 0, failed = 0, rays = 0;
   int running = 0, peak_running = 0;
@@ -164,6 +166,7 @@ cudaError_t start(rt_session_s* S, Req* q, Slot& sl) {
     q->rays[k] = carve<rt_ray>(base, &at, q->n);
     q->hits[k] = carve<rt_hit>(base, &at, q->n);
     q->skip[k] = carve<int>(base, &at, q->n);
+    q->src[k] = carve<int>(base, &at, q->n);
   }
   q->counts = carve<int>(base, &at, RT_BATCH_MAX_ORDER + 1);
   q->blocks = carve<int>(base, &at, q->n / 256 + 2);
@@ -180,7 +183,7 @@ cudaError_t start(rt_session_s* S, Req* q, Slot& sl) {
   if ((e = rt::launch_trace_dev(scene, q->rays[0], q->n, nullptr, q->hits[0], nullptr, &tp, q->scr, st))) return e;
   for (int k = 1; k <= orders; ++k) {
     const int* prev = k == 1 ? nullptr : q->counts + (k - 1);
-    if ((e = rt::launch_reflect(scene, q->rays[k - 1], q->hits[k - 1], q->n, prev, q->rays[k], q->skip[k], nullptr,
+    if ((e = rt::launch_reflect(scene, q->rays[k - 1], q->hits[k - 1], q->n, prev, q->rays[k], q->skip[k], q->src[k],
                                 q->counts + k, q->blocks, q->n, st)))
       return e;
     rt_trace_params tk{};
@@ -204,9 +207,31 @@ cudaError_t start(rt_session_s* S, Req* q, Slot& sl) {
   return cudaEventRecord(sl.done, st);
 }
 
+// The hits (and parent indices) of every reflection order the request asked
+// for: exactly the order's count, known once its work is done, copied from
+// the request's pool memory before that memory is released.
+cudaError_t copy_orders(Req* q, Slot& sl) {
+  cudaError_t e = cudaSuccess;
+  for (int k = 1; k <= q->r.max_order && e == cudaSuccess; ++k) {
+    const long long c = sl.pinned_counts[k];
+    if (c <= 0 || c > q->n) continue;
+    if (q->r.order_hits_host && q->r.order_hits_host[k])
+      e = cudaMemcpyAsync(q->r.order_hits_host[k], q->hits[k], (size_t)c * sizeof(rt_hit), cudaMemcpyDeviceToHost,
+                          sl.st);
+    if (e == cudaSuccess && q->r.order_src_host && q->r.order_src_host[k])
+      e = cudaMemcpyAsync(q->r.order_src_host[k], q->src[k], (size_t)c * sizeof(int), cudaMemcpyDeviceToHost, sl.st);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(sl.st);
+  return e;
+}
+
 void finish(rt_session_s* S, Slot& sl, bool ok) {
   Req* q = sl.req;
   if (ok && q->r.hits_host) memcpy(q->r.hits_host, sl.pinned_hits, (size_t)q->n * sizeof(rt_hit));
+  if (ok && (q->r.order_hits_host || q->r.order_src_host) && copy_orders(q, sl) != cudaSuccess) {
+    cudaGetLastError();
+    ok = false;
+  }
   long long rays = q->n;
   if (ok) {
     for (int k = 1; k <= q->r.max_order; ++k) rays += sl.pinned_counts[k];
@@ -225,10 +250,15 @@ void finish(rt_session_s* S, Slot& sl, bool ok) {
     ++S->completed;
     S->rays += rays;
     const double ms = std::chrono::duration<double, std::milli>(q->t_done - q->t_submit).count();
+    const double wait = std::chrono::duration<double, std::milli>(q->t_start - q->t_submit).count();
     if (S->lat_ms.size() < kLatencyWindow) {
       S->lat_ms.push_back(ms);
+      S->wait_ms.push_back(wait);
+      S->run_ms.push_back(ms - wait);
     } else {
       S->lat_ms[S->lat_next] = ms;
+      S->wait_ms[S->lat_next] = wait;
+      S->run_ms[S->lat_next] = ms - wait;
       S->lat_next = (S->lat_next + 1) % kLatencyWindow;
     }
     S->t_last = q->t_done;
@@ -321,7 +351,9 @@ static int rt_session_create_body(size_t pool_bytes, int max_slots, rt_session* 
   cudaGetDevice(&S->device);
   try {
     S->pool.reset(pool_bytes);
-    S->lat_ms.reserve(kLatencyWindow);  // the worker thread never reallocates it
+    S->lat_ms.reserve(kLatencyWindow);  // the worker thread never reallocates them
+    S->wait_ms.reserve(kLatencyWindow);
+    S->run_ms.reserve(kLatencyWindow);
     S->slots.resize(max_slots);
     for (Slot& sl : S->slots) {
       if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking);
@@ -450,19 +482,23 @@ static int rt_session_stats_get_body(rt_session S, rt_session_stats* st) {
   st->pool_bytes = (int64_t)S->pool.cap();
   st->peak_pool_bytes = (int64_t)S->pool.peak();
   if (!S->lat_ms.empty()) {
-    std::vector<double> v = S->lat_ms;
-    std::sort(v.begin(), v.end());
-    auto pct = [&](double p) {
+    // percentiles (linear interpolation) of one sorted copy
+    auto pct = [](std::vector<double> v, double p) {
+      std::sort(v.begin(), v.end());
       const double x = p * (double)(v.size() - 1);
       const size_t i = (size_t)x;
       const double f = x - (double)i;
       return i + 1 < v.size() ? v[i] * (1.0 - f) + v[i + 1] * f : v[i];
     };
-    st->p50_ms = pct(0.50);
-    st->p99_ms = pct(0.99);
+    st->p50_ms = pct(S->lat_ms, 0.50);
+    st->p99_ms = pct(S->lat_ms, 0.99);
+    st->wait_p50_ms = pct(S->wait_ms, 0.50);
+    st->wait_p99_ms = pct(S->wait_ms, 0.99);
+    st->run_p50_ms = pct(S->run_ms, 0.50);
+    st->run_p99_ms = pct(S->run_ms, 0.99);
     double s = 0;
-    for (double x : v) s += x;
-    st->mean_ms = s / (double)v.size();
+    for (double x : S->lat_ms) s += x;
+    st->mean_ms = s / (double)S->lat_ms.size();
     st->span_s = std::chrono::duration<double>(S->t_last - S->t_first).count();
   }
   return RT_OK;

@@ -105,7 +105,8 @@ class BatchStats(ctypes.Structure):
 class Request(ctypes.Structure):
     _fields_ = [("scene_id", ctypes.c_int32), ("tx", ctypes.c_float * 3), ("dir_kind", ctypes.c_int32),
                 ("param", ctypes.c_int64), ("max_order", ctypes.c_int32), ("tmax", ctypes.c_float),
-                ("hits_host", ctypes.c_void_p), ("order_counts_host", ctypes.c_void_p)]
+                ("hits_host", ctypes.c_void_p), ("order_counts_host", ctypes.c_void_p),
+                ("order_hits_host", ctypes.c_void_p), ("order_src_host", ctypes.c_void_p)]
 
 
 class SessionStats(ctypes.Structure):
@@ -113,7 +114,8 @@ class SessionStats(ctypes.Structure):
                 ("queued", ctypes.c_int64), ("running", ctypes.c_int64), ("peak_running", ctypes.c_int64),
                 ("rays", ctypes.c_int64), ("pool_bytes", ctypes.c_int64), ("peak_pool_bytes", ctypes.c_int64),
                 ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
-                ("span_s", ctypes.c_double)]
+                ("span_s", ctypes.c_double), ("wait_p50_ms", ctypes.c_double), ("wait_p99_ms", ctypes.c_double),
+                ("run_p50_ms", ctypes.c_double), ("run_p99_ms", ctypes.c_double)]
 
 
 def lib_path() -> str:
@@ -597,8 +599,9 @@ class Session:
         self._scenes.append(scene)
         return sid.value
 
-    def submit(self, scene_id, tx, kind, param, max_order=0, tmax=1000.0, want_hits=True):
-        """Returns a ticket; results via result(ticket) after wait()."""
+    def submit(self, scene_id, tx, kind, param, max_order=0, tmax=1000.0, want_hits=True, want_orders=False):
+        """Returns a ticket; results via result(ticket) after wait().  want_orders:
+        also the hits and parent indices of every reflection order (orders(ticket))."""
         n = rt_ray_count(kind, param)
         hits = np.empty((n, 4), np.float32) if want_hits else None
         counts = np.zeros(RT_BATCH_MAX_ORDER + 1, np.int64)
@@ -609,9 +612,18 @@ class Session:
             r.tx[k] = float(tx[k])
         r.hits_host = hits.ctypes.data if hits is not None else None
         r.order_counts_host = counts.ctypes.data
+        orders = None
+        if want_orders and max_order > 0:
+            oh = [None] + [np.empty((n, 4), np.float32) for _ in range(max_order)]
+            osrc = [None] + [np.empty(n, np.int32) for _ in range(max_order)]
+            ph = (ctypes.c_void_p * (max_order + 1))(*([None] + [a.ctypes.data for a in oh[1:]]))
+            ps = (ctypes.c_void_p * (max_order + 1))(*([None] + [a.ctypes.data for a in osrc[1:]]))
+            r.order_hits_host = ctypes.cast(ph, ctypes.c_void_p)
+            r.order_src_host = ctypes.cast(ps, ctypes.c_void_p)
+            orders = (oh, osrc, ph, ps)
         t = ctypes.c_uint64()
         _check(lib().rt_session_submit(self._h, ctypes.byref(r), ctypes.byref(t)))
-        self._keep[t.value] = (hits, counts, int(max_order))
+        self._keep[t.value] = (hits, counts, int(max_order), orders)
         return t.value
 
     def poll(self, ticket) -> bool:
@@ -624,13 +636,22 @@ class Session:
         _check(lib().rt_session_wait(self._h, ticket, ns))
 
     def result(self, ticket):
-        hits, counts, mo = self._keep[ticket]
+        hits, counts, mo, _ = self._keep[ticket]
         return hits, counts[: mo + 1]
+
+    def orders(self, ticket):
+        """[(hits [c_k, 4], parent index [c_k]) for k = 1 .. max_order] of a request
+        submitted with want_orders."""
+        _, counts, mo, orders = self._keep[ticket]
+        if orders is None:
+            return []
+        oh, osrc = orders[0], orders[1]
+        return [(oh[k][: counts[k]], osrc[k][: counts[k]]) for k in range(1, mo + 1)]
 
     def release(self, ticket):
         """Forget a finished request (rt_session_release); returns its results."""
         _check(lib().rt_session_release(self._h, ticket))
-        hits, counts, mo = self._keep.pop(ticket)
+        hits, counts, mo, _ = self._keep.pop(ticket)
         return hits, counts[: mo + 1]
 
     def stats(self) -> dict:

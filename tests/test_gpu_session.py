@@ -53,29 +53,46 @@ def test_session_same_alone_and_in_the_mix(rb, world):
     reqs = _requests(world, 14, seed=11)
     alone = []
     for q in reqs:
-        t = sess.submit(ids[q["scene"]], q["tx"], rb.RT_RAYS_FIBONACCI, q["count"], q["order"], q["tmax"])
+        t = sess.submit(ids[q["scene"]], q["tx"], rb.RT_RAYS_FIBONACCI, q["count"], q["order"], q["tmax"],
+                        want_orders=True)
         sess.wait(t, timeout_s=60)
         h, c = sess.result(t)
-        alone.append((h.copy(), c.copy()))
-    tickets = [sess.submit(ids[q["scene"]], q["tx"], rb.RT_RAYS_FIBONACCI, q["count"], q["order"], q["tmax"])
-               for q in reqs]
+        alone.append((h.copy(), c.copy(), [(oh.copy(), os_.copy()) for oh, os_ in sess.orders(t)]))
+    tickets = [sess.submit(ids[q["scene"]], q["tx"], rb.RT_RAYS_FIBONACCI, q["count"], q["order"], q["tmax"],
+                           want_orders=True) for q in reqs]
     for t in tickets:
         sess.wait(t, timeout_s=120)
-    for (h0, c0), t in zip(alone, tickets):
+    n_orders = 0
+    for (h0, c0, o0), t in zip(alone, tickets):
         h, c = sess.result(t)
         assert np.array_equal(h.view(np.uint32), h0.view(np.uint32))
         assert np.array_equal(c, c0)
+        o = sess.orders(t)
+        assert len(o) == len(o0) == len(c) - 1
+        for (oh, os_), (oh0, os0) in zip(o, o0):   # every reflection order, alone and in the mix
+            assert np.array_equal(oh.view(np.uint32), oh0.view(np.uint32)) and np.array_equal(os_, os0)
+            n_orders += 1
+    assert n_orders >= 5
     st = sess.stats()
     assert st["completed"] == 2 * len(reqs) and st["failed"] == 0
     assert 1 <= st["peak_running"] <= 3 and st["p99_ms"] >= st["p50_ms"] > 0
     assert st["peak_pool_bytes"] <= st["pool_bytes"]
-    # the same as the per-call path on the same launched rays
-    for q, (h0, _) in list(zip(reqs, alone))[:5]:
+    # the same as the per-call path on the same launched rays, every order
+    for q, (h0, c0, o0) in list(zip(reqs, alone))[:6]:
         s = world[q["scene"]][1]
         rays = rb.rt_gen_rays(rb.RT_RAYS_FIBONACCI, q["tx"], q["count"], 0.0, q["tmax"])
         hits = rb.rt_trace_closest(s, rays)
         torch.cuda.synchronize()
         assert np.array_equal(hits.cpu().numpy().view(np.uint32), h0.view(np.uint32))
+        for k in range(1, q["order"] + 1):
+            nr, ns, src, cnt = rb.rt_reflect(s, rays, hits)
+            m = int(cnt.item())
+            rays, hits = nr[:m], rb.rt_trace_closest(s, nr[:m], skip=ns[:m])
+            torch.cuda.synchronize()
+            oh0, os0 = o0[k - 1]
+            assert m == c0[k] == len(oh0)
+            assert np.array_equal(hits.cpu().numpy().view(np.uint32), oh0.view(np.uint32))
+            assert np.array_equal(src[:m].cpu().numpy(), os0)
     sess.destroy()
 
 
