@@ -232,11 +232,13 @@ def run_batched(rtbvh, torch, runs):
         b.run()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0 = rtbvh.rt_launch_count()
     e0.record()
     for _ in range(runs):
         b.run()
     e1.record()
     torch.cuda.synchronize()
+    kernels_per_run = (rtbvh.rt_launch_count() - c0) / runs
     ms_b = e0.elapsed_time(e1) / runs
     st = b.stats()
     b.destroy()
@@ -287,11 +289,13 @@ def run_batched(rtbvh, torch, runs):
             "rays_per_run": st["total_rays"], "rays_per_order": st["rays"], "visible_pairs": st["visible"],
             "batched_mrays_s": st["total_rays"] / (ms_b * 1e-3) / 1e6, "batched_ms": ms_b,
             "plain_mrays_s": tot / (ms_p * 1e-3) / 1e6, "plain_ms": ms_p,
-            "speedup": ms_p / ms_b, "autotuned": tune,
+            "speedup": ms_p / ms_b, "autotuned": tune, "kernels_per_run": kernels_per_run,
             "with_reception": {"ms": ms_r, "mrays_s": st_r["total_rays"] / (ms_r * 1e-3) / 1e6,
                                "received_per_order": st_r["received"],
                                "overhead": ms_r / ms_b - 1.0},
-            "batched": "one CUDA graph replay per run (device-side counts)",
+            "batched": "one CUDA graph replay per run: one kernel writes every transmitter's launch, one "
+                       "cooperative persistent kernel traces every order (walk, float64 pass, stable "
+                       "compaction) and the visibility segments; device-side counts",
             "plain": "per-transmitter rt_gen_rays / rt_trace_closest / rt_reflect calls, counts read by the host"}
 
 

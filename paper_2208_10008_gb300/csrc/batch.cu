@@ -4,12 +4,15 @@
 //
 // One rt_batch owns every buffer the pipeline needs (sized at creation from
 // the transmitters' ray counts), so a run allocates nothing and never waits
-// on the host: the count of each reflection order stays on the device and
-// the next trace reads it there.  The first run executes directly; the
-// second captures the whole pipeline into a CUDA graph, which every later
-// run replays with a single launch.  With reception on, every order's
-// segments are also tested against the receivers' spheres (Sec. III.C,
-// Eq. 4), each ray with the angular spacing of its own transmitter's launch.
+// on the host.  A run is two launches: one kernel writes every
+// transmitter's launch, and one cooperative, persistent kernel traces every
+// reflection order and the visibility segments, its CTAs stepping through
+// the orders together (walk, float64 pass, stable compaction into the next
+// order) with the counts on the device.  The first run executes directly;
+// the second captures the run into a CUDA graph, which every later run
+// replays.  With reception on, every order's segments are then tested
+// against the receivers' spheres (Sec. III.C, Eq. 4), each ray with the
+// angular spacing of its own transmitter's launch.
 #include <cuda_runtime.h>
 
 #include <array>
@@ -44,7 +47,7 @@ struct rt_batch_s {
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  std::array<uintptr_t, 8> graph_scene{};  // scene state the graph was captured with
+  std::array<uintptr_t, 10> graph_scene{};  // scene state the graph was captured with
   int runs = 0;
   long long graph_kernels = 0;  // kernels in the captured graph
   // reception (Eq. 4)
@@ -55,8 +58,16 @@ struct rt_batch_s {
   float* delta[RT_BATCH_MAX_ORDER + 1] = {};    // per ray: its transmitter's delta
   rt_rx_record* rec[RT_BATCH_MAX_ORDER + 1] = {};
   int* rx_count = nullptr;                      // device: pairs of order k at rx_count[k]
-  long long* tx_off = nullptr;                  // device: first order-0 ray of each transmitter
+  long long* tx_off = nullptr;                  // device: first order-0 ray of each transmitter (n_tx + 1)
   float* tx_delta = nullptr;                    // device: each transmitter's delta
+  // the one-launch pipeline
+  float* tx_dev = nullptr;                      // device: transmitter positions
+  long long* param_dev = nullptr;               // device: launch parameters
+  int* chunk = nullptr;                         // per 32-ray chunk of order-k rays
+  int* cta_total = nullptr;
+  int cta_cap = 0;
+  unsigned* bar = nullptr;                      // grid barrier words + status
+  int* take = nullptr;                          // rays handed out per walk phase
 };
 
 namespace rt {
@@ -82,21 +93,14 @@ __global__ void k_delta_fill(const long long* __restrict__ off, const float* __r
   out[i] = dtx[lo];
 }
 
-// A reflected ray inherits its parent's delta (src: parent index).
-__global__ void k_delta_gather(const float* __restrict__ prev, const int* __restrict__ src, const int* __restrict__ n_dev,
-                               int n, float* __restrict__ out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= min(n, __ldg(n_dev))) return;
-  out[i] = __ldg(prev + __ldg(src + i));
-}
-
 // What a captured pipeline takes from the scene as launch arguments: the
 // arrays the walk and the bounce read and the size of the current tree.  A
 // re-upload that grows the scene, the first quantised build or a rebuild
 // over another range changes it; the graph is then captured again.
-std::array<uintptr_t, 8> scene_key(const rt_scene_s* s) {
+std::array<uintptr_t, 10> scene_key(const rt_scene_s* s) {
   return {(uintptr_t)s->tri_in, (uintptr_t)s->node2,  (uintptr_t)s->wide, (uintptr_t)s->qwide,
-          (uintptr_t)s->link2,  (uintptr_t)s->tri_leaf, (uintptr_t)s->ctl, (uintptr_t)s->n_built};
+          (uintptr_t)s->link2,  (uintptr_t)s->tri_leaf, (uintptr_t)s->ctl, (uintptr_t)s->n_built,
+          (uintptr_t)s->wide8,  (uintptr_t)s->params.width};
 }
 
 void drop_graph(rt_batch_s* b) {
@@ -115,6 +119,12 @@ void free_batch(rt_batch_s* b) {
   if (b->rx_count) cudaFree(b->rx_count);
   if (b->tx_off) cudaFree(b->tx_off);
   if (b->tx_delta) cudaFree(b->tx_delta);
+  if (b->tx_dev) cudaFree(b->tx_dev);
+  if (b->param_dev) cudaFree(b->param_dev);
+  if (b->chunk) cudaFree(b->chunk);
+  if (b->cta_total) cudaFree(b->cta_total);
+  if (b->bar) cudaFree(b->bar);
+  if (b->take) cudaFree(b->take);
   for (int k = 0; k <= RT_BATCH_MAX_ORDER; ++k) {
     if (b->rays[k]) cudaFree(b->rays[k]);
     if (b->hits[k]) cudaFree(b->hits[k]);
@@ -130,57 +140,51 @@ void free_batch(rt_batch_s* b) {
   if (b->st) cudaStreamDestroy(b->st);
 }
 
-// Receiving spheres of order k (device count for k >= 1).
-cudaError_t enqueue_receive(rt_batch_s* b, int k) {
-  rt_receive_params p{};
-  p.delta = b->dmax;
-  p.range0 = b->tmax;
-  p.max_records = b->max_rx;
-  p.delta_ray_dev = b->delta[k];
-  if (rt_receive(b->rxset, b->rays[k], b->hits[k], b->n0, k ? b->counts + k : nullptr, &p, b->rec[k],
-                 b->rx_count + k, b->st) != RT_OK)
-    return cudaErrorInvalidValue;
-  return cudaSuccess;
-}
+constexpr long long kBarrierTimeoutNs = 10ll * 1000 * 1000 * 1000;  // 10 s per barrier
 
 cudaError_t enqueue(rt_batch_s* b) {
   cudaError_t e;
   cudaStream_t st = b->st;
-  for (int t = 0; t < b->n_tx; ++t) {
-    if ((e = rt::launch_gen_rays(b->kind, &b->tx[3 * t], b->param[t], 0.f, b->tmax, b->rays[0] + b->offset[t],
-                                 b->count[t], st)))
-      return e;
-  }
-  rt_trace_params tp{};
-  tp.block = b->ray_tile;
-  if ((e = rt::launch_trace_dev(b->scene, b->rays[0], b->n0, nullptr, b->hits[0], nullptr, &tp, b->scr, st)))
+  if ((e = rt::launch_gen_batch(b->kind, b->tx_dev, b->tx_off, b->param_dev, b->n_tx, b->n0, 0.f, b->tmax,
+                                b->rays[0], st)))
     return e;
-  if (b->receive && (e = enqueue_receive(b, 0))) return e;
-  for (int k = 1; k <= b->max_order; ++k) {
-    const int* prev = k == 1 ? nullptr : b->counts + (k - 1);
-    if ((e = rt::launch_reflect(b->scene, b->rays[k - 1], b->hits[k - 1], b->n0, prev, b->rays[k], b->skip[k],
-                                b->src[k], b->counts + k, b->blocks, b->n0, st)))
-      return e;
-    rt_trace_params tk{};
-    tk.skip_tri_dev = b->skip[k];
-    tk.block = b->ray_tile;
-    if ((e = rt::launch_trace_dev(b->scene, b->rays[k], b->n0, b->counts + k, b->hits[k], nullptr, &tk, b->scr,
-                                  st)))
-      return e;
-    if (b->receive) {
-      const int n = (int)b->n0;
-      k_delta_gather<<<(n + 255) / 256, 256, 0, st>>>(b->delta[k - 1], b->src[k], b->counts + k, n, b->delta[k]);
-      rt::count_launches(1);
-      if ((e = cudaGetLastError())) return e;
-      if ((e = enqueue_receive(b, k))) return e;
+  rt::BatchLaunch L;
+  L.max_order = b->max_order;
+  L.n0 = b->n0;
+  L.n_seg = b->n_seg;
+  for (int k = 0; k <= RT_BATCH_MAX_ORDER; ++k) {
+    L.rays[k] = b->rays[k];
+    L.hits[k] = b->hits[k];
+    L.skip[k] = b->skip[k];
+    L.src[k] = b->src[k];
+  }
+  L.counts = b->counts;
+  L.chunk = b->chunk;
+  L.cta_total = b->cta_total;
+  L.cta_cap = b->cta_cap;
+  L.seg = b->seg;
+  L.occl = b->occl;
+  L.bar = b->bar;
+  L.status = reinterpret_cast<int*>(b->bar + 2);
+  L.take = b->take;
+  L.timeout_ns = kBarrierTimeoutNs;
+  L.scr = &b->scr;
+  L.receive = b->receive ? 1 : 0;
+  for (int k = 0; k <= RT_BATCH_MAX_ORDER; ++k) L.delta[k] = b->delta[k];
+  if ((e = rt::launch_batch_persistent(b->scene, L, st))) return e;
+  // the receiving spheres of every order (Sec. III.C, Eq. 4), each ray with
+  // its own transmitter's delta; one launch per order
+  if (b->receive)
+    for (int k = 0; k <= b->max_order; ++k) {
+      rt_receive_params p{};
+      p.delta = b->dmax;
+      p.range0 = b->tmax;
+      p.max_records = b->max_rx;
+      p.delta_ray_dev = b->delta[k];
+      if (rt_receive(b->rxset, b->rays[k], b->hits[k], b->n0, k ? b->counts + k : nullptr, &p, b->rec[k],
+                     b->rx_count + k, st) != RT_OK)
+        return cudaErrorInvalidValue;
     }
-  }
-  if (b->n_seg > 0) {
-    rt_trace_params tv{};
-    tv.block = b->ray_tile;
-    if ((e = rt::launch_trace_dev(b->scene, b->seg, b->n_seg, nullptr, nullptr, b->occl, &tv, b->scr, st)))
-      return e;
-  }
   return cudaSuccess;
 }
 
@@ -250,6 +254,25 @@ static int rt_batch_create_body(rt_scene scene, const rt_batch_desc* d, rt_batch
     if (e == cudaSuccess && k > 0) e = alloc(&b->src[k], total);
   }
   if (e == cudaSuccess) e = alloc(&b->counts, RT_BATCH_MAX_ORDER + 1);
+  if (e == cudaSuccess) e = alloc(&b->chunk, total / 32 + 2);
+  b->cta_cap = rt::persistent_batch_ctas();
+  if (e == cudaSuccess) e = alloc(&b->cta_total, b->cta_cap);
+  if (e == cudaSuccess) e = alloc(&b->bar, 4);
+  if (e == cudaSuccess) e = alloc(&b->take, RT_BATCH_MAX_ORDER + 2);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->bar, 0, 4 * sizeof(unsigned), b->st);
+  if (e == cudaSuccess) e = alloc(&b->tx_dev, 3 * b->n_tx);
+  if (e == cudaSuccess) e = alloc(&b->param_dev, b->n_tx);
+  if (e == cudaSuccess) e = alloc(&b->tx_off, b->n_tx + 1);
+  if (e == cudaSuccess) {
+    std::vector<long long> off(b->offset);
+    off.push_back(total);
+    e = cudaMemcpyAsync(b->tx_off, off.data(), off.size() * sizeof(long long), cudaMemcpyHostToDevice, b->st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(b->tx_dev, b->tx.data(), 3 * b->n_tx * sizeof(float), cudaMemcpyHostToDevice, b->st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(b->param_dev, b->param.data(), b->n_tx * sizeof(long long), cudaMemcpyHostToDevice, b->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);  // off is a host temporary
+  }
   if (e == cudaSuccess) e = alloc(&b->blocks, total / 256 + 2);
   const long long qcap = total > b->n_seg ? total : b->n_seg;
   if (e == cudaSuccess) e = alloc(&b->scr.counter, 4);
@@ -289,16 +312,14 @@ static int rt_batch_create_body(rt_scene scene, const rt_batch_desc* d, rt_batch
     const int rc = rt_rxset_create(d->rx_pos, d->n_rx, (float)(b->tmax * (double)b->dmax / std::sqrt(3.0)) * 1.0001f,
                                    &b->rxset);
     if (rc != RT_OK) return rc;  // the set's own message stays in rt_last_error
+
     for (int k = 0; k <= b->max_order && e == cudaSuccess; ++k) {
       e = alloc(&b->delta[k], total);
       if (e == cudaSuccess) e = alloc(&b->rec[k], b->max_rx);
     }
     if (e == cudaSuccess) e = alloc(&b->rx_count, RT_BATCH_MAX_ORDER + 1);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->rx_count, 0, (RT_BATCH_MAX_ORDER + 1) * sizeof(int), b->st);
-    if (e == cudaSuccess) e = alloc(&b->tx_off, b->n_tx);
     if (e == cudaSuccess) e = alloc(&b->tx_delta, b->n_tx);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(b->tx_off, b->offset.data(), b->n_tx * sizeof(long long), cudaMemcpyHostToDevice, b->st);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(b->tx_delta, dtx.data(), b->n_tx * sizeof(float), cudaMemcpyHostToDevice, b->st);
     if (e == cudaSuccess) {
@@ -349,10 +370,16 @@ int rt_batch_run(rt_batch b, void* stream) {
         if (e == cudaSuccess) {
           b->graph_scene = scene_key(b->scene);
         } else {
+          // no graph of this pipeline on this device (a cooperative launch
+          // that cannot be captured): run it directly from now on; a run is
+          // two launches either way
           drop_graph(b);
+          cudaGetLastError();
+          b->use_graph = false;
+          e = enqueue(b);
         }
       }
-      if (e == cudaSuccess) {
+      if (e == cudaSuccess && b->exec) {
         e = cudaGraphLaunch(b->exec, b->st);
         rt::count_launches((int)b->graph_kernels);
       }
@@ -399,6 +426,10 @@ static int rt_batch_stats_get_body(rt_batch b, void* stream, rt_batch_stats* s) 
   cudaMemcpy(&fl, b->scr.counter, sizeof(int), cudaMemcpyDeviceToHost);
   s->flagged = fl;
   s->segments = b->n_seg;
+  unsigned w[4] = {0, 0, 0, 0};
+  if (cudaMemcpy(w, b->bar, sizeof(w), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return rt::set_error(RT_ECUDA, "read batch status");
+  if (w[2] != 0) return rt::set_error(RT_ETIMEOUT, "a grid barrier of the batch kernel ran out of time");
   return RT_OK;
 }
 

@@ -28,24 +28,30 @@ constexpr int kRayBlock = 256;
 // arithmetic for every i.
 constexpr unsigned long long kGoldenFrac = 0x61C8864680B583EAull;
 
+// Direction i of an n-point Fibonacci launch.
+__device__ __forceinline__ float3 fib_dir(long long i, long long n) {
+  // z = 1 - (2i + 1)/n = (n - 2i - 1)/n and rho = sqrt(1 - z^2) =
+  // sqrt((2i + 1)(2n - 2i - 1)) / n, each from exact integers (no
+  // cancellation near the poles)
+  const double dn = (double)n;
+  const float z = (float)((double)(n - 2 * i - 1) / dn);
+  const float rho = (float)(sqrt((double)(2 * i + 1) * (double)(2 * n - 2 * i - 1)) / dn);
+  // azimuth in turns, i (3 - sqrt 5)/2 mod 1, reduced to [-1/2, 1/2) in
+  // exact integer arithmetic before the one rounding to float
+  const unsigned long long turns = (unsigned long long)i * kGoldenFrac;  // mod 2^64
+  const float a = (float)(int)(unsigned)(turns >> 32) * 2.3283064365386963e-10f;  // 2^-32
+  float s, c;
+  sincospif(2.f * a, &s, &c);
+  return make_float3(__fmul_rn(rho, c), __fmul_rn(rho, s), z);
+}
+
 __global__ void k_gen_fibonacci(float ox, float oy, float oz, long long n, float tmin, float tmax,
                                 float4* __restrict__ rays) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    // z = 1 - (2i + 1)/n = (n - 2i - 1)/n and rho = sqrt(1 - z^2) =
-    // sqrt((2i + 1)(2n - 2i - 1)) / n, each from exact integers (no
-    // cancellation near the poles)
-    const double dn = (double)n;
-    const float z = (float)((double)(n - 2 * i - 1) / dn);
-    const float rho = (float)(sqrt((double)(2 * i + 1) * (double)(2 * n - 2 * i - 1)) / dn);
-    // azimuth in turns, i (3 - sqrt 5)/2 mod 1, reduced to [-1/2, 1/2) in
-    // exact integer arithmetic before the one rounding to float
-    const unsigned long long turns = (unsigned long long)i * kGoldenFrac;  // mod 2^64
-    const float a = (float)(int)(unsigned)(turns >> 32) * 2.3283064365386963e-10f;  // 2^-32
-    float s, c;
-    sincospif(2.f * a, &s, &c);
+    const float3 d = fib_dir(i, n);
     rays[2 * i] = make_float4(ox, oy, oz, tmin);
-    rays[2 * i + 1] = make_float4(rho * c, rho * s, z, tmax);
+    rays[2 * i + 1] = make_float4(d.x, d.y, d.z, tmax);
   }
 }
 
@@ -57,52 +63,83 @@ struct Ico {
 };
 __constant__ Ico c_ico;
 
-__global__ void k_gen_icosphere(float ox, float oy, float oz, int fseg, long long n, float tmin, float tmax,
-                                float4* __restrict__ rays) {
-  const long long f = fseg;
+// Direction k of the launch towards the vertices of the icosahedron with
+// every edge cut into f segments, normalised; every operation rounded
+// explicitly (the same bits in every kernel that generates it).
+__device__ __forceinline__ float3 ico_dir(long long k, long long f) {
   const long long n_edge_pts = 30 * (f - 1);
   const long long per_face = (f - 1) * (f - 2) / 2;
-  const float inv_f = 1.f / (float)f;
+  const float inv_f = __frcp_rn((float)f);
+  float p0, p1, p2;
+  if (k < 12) {
+    p0 = c_ico.v[k][0];
+    p1 = c_ico.v[k][1];
+    p2 = c_ico.v[k][2];
+  } else if (k < 12 + n_edge_pts) {
+    const long long r = k - 12;
+    const int e = (int)(r / (f - 1));
+    const long long s = r - (long long)e * (f - 1) + 1;  // 1 .. f-1
+    const float t = __fmul_rn((float)s, inv_f), u = __fsub_rn(1.f, t);
+    const float* a = c_ico.v[c_ico.e[e][0]];
+    const float* b = c_ico.v[c_ico.e[e][1]];
+    p0 = __fadd_rn(__fmul_rn(a[0], u), __fmul_rn(b[0], t));
+    p1 = __fadd_rn(__fmul_rn(a[1], u), __fmul_rn(b[1], t));
+    p2 = __fadd_rn(__fmul_rn(a[2], u), __fmul_rn(b[2], t));
+  } else {
+    const long long r = k - 12 - n_edge_pts;
+    const int fc = (int)(r / per_face);
+    long long q = r - (long long)fc * per_face;
+    // row i (1 .. f-2) holds f-1-i points; rows start at (i-1)(f-1) - (i-1)i/2
+    const double ff = (double)(f - 1);
+    long long i = 1 + (long long)floor(ff - 0.5 - sqrt(fmax(0.0, (ff - 0.5) * (ff - 0.5) - 2.0 * (double)q)));
+    if (i < 1) i = 1;
+    auto row_start = [&](long long ii) { return (ii - 1) * (f - 1) - (ii - 1) * ii / 2; };
+    while (i > 1 && row_start(i) > q) --i;
+    while (row_start(i + 1) <= q) ++i;
+    const long long j = q - row_start(i) + 1;
+    const float wi = __fmul_rn((float)i, inv_f), wj = __fmul_rn((float)j, inv_f);
+    const float w0 = __fsub_rn(__fsub_rn(1.f, wi), wj);
+    const float* a = c_ico.v[c_ico.f[fc][0]];
+    const float* b = c_ico.v[c_ico.f[fc][1]];
+    const float* c = c_ico.v[c_ico.f[fc][2]];
+    p0 = __fadd_rn(__fadd_rn(__fmul_rn(a[0], w0), __fmul_rn(b[0], wi)), __fmul_rn(c[0], wj));
+    p1 = __fadd_rn(__fadd_rn(__fmul_rn(a[1], w0), __fmul_rn(b[1], wi)), __fmul_rn(c[1], wj));
+    p2 = __fadd_rn(__fadd_rn(__fmul_rn(a[2], w0), __fmul_rn(b[2], wi)), __fmul_rn(c[2], wj));
+  }
+  const float il = rsqrtf(__fadd_rn(__fadd_rn(__fmul_rn(p0, p0), __fmul_rn(p1, p1)), __fmul_rn(p2, p2)));
+  return make_float3(__fmul_rn(p0, il), __fmul_rn(p1, il), __fmul_rn(p2, il));
+}
+
+__global__ void k_gen_icosphere(float ox, float oy, float oz, int fseg, long long n, float tmin, float tmax,
+                                float4* __restrict__ rays) {
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
        k += (long long)gridDim.x * blockDim.x) {
-    float p0, p1, p2;
-    if (k < 12) {
-      p0 = c_ico.v[k][0];
-      p1 = c_ico.v[k][1];
-      p2 = c_ico.v[k][2];
-    } else if (k < 12 + n_edge_pts) {
-      const long long r = k - 12;
-      const int e = (int)(r / (f - 1));
-      const long long s = r - (long long)e * (f - 1) + 1;  // 1 .. f-1
-      const float t = (float)s * inv_f;
-      const float* a = c_ico.v[c_ico.e[e][0]];
-      const float* b = c_ico.v[c_ico.e[e][1]];
-      p0 = a[0] * (1.f - t) + b[0] * t;
-      p1 = a[1] * (1.f - t) + b[1] * t;
-      p2 = a[2] * (1.f - t) + b[2] * t;
-    } else {
-      const long long r = k - 12 - n_edge_pts;
-      const int fc = (int)(r / per_face);
-      long long q = r - (long long)fc * per_face;
-      // row i (1 .. f-2) holds f-1-i points; rows start at (i-1)(f-1) - (i-1)i/2
-      const double ff = (double)(f - 1);
-      long long i = 1 + (long long)floor(ff - 0.5 - sqrt(fmax(0.0, (ff - 0.5) * (ff - 0.5) - 2.0 * (double)q)));
-      if (i < 1) i = 1;
-      auto row_start = [&](long long ii) { return (ii - 1) * (f - 1) - (ii - 1) * ii / 2; };
-      while (i > 1 && row_start(i) > q) --i;
-      while (row_start(i + 1) <= q) ++i;
-      const long long j = q - row_start(i) + 1;
-      const float wi = (float)i * inv_f, wj = (float)j * inv_f, w0 = 1.f - wi - wj;
-      const float* a = c_ico.v[c_ico.f[fc][0]];
-      const float* b = c_ico.v[c_ico.f[fc][1]];
-      const float* c = c_ico.v[c_ico.f[fc][2]];
-      p0 = a[0] * w0 + b[0] * wi + c[0] * wj;
-      p1 = a[1] * w0 + b[1] * wi + c[1] * wj;
-      p2 = a[2] * w0 + b[2] * wi + c[2] * wj;
-    }
-    const float il = rsqrtf(p0 * p0 + p1 * p1 + p2 * p2);
+    const float3 d = ico_dir(k, fseg);
     rays[2 * k] = make_float4(ox, oy, oz, tmin);
-    rays[2 * k + 1] = make_float4(p0 * il, p1 * il, p2 * il, tmax);
+    rays[2 * k + 1] = make_float4(d.x, d.y, d.z, tmax);
+  }
+}
+
+// The launches of many transmitters in one kernel: transmitter t's rays
+// occupy [off[t], off[t + 1]) (each the same rays its own launch writes).
+__global__ void k_gen_batch(int kind, const float* __restrict__ tx, const long long* __restrict__ off,
+                            const long long* __restrict__ param, int n_tx, float tmin, float tmax,
+                            float4* __restrict__ rays) {
+  const long long total = off[n_tx];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    int lo = 0, hi = n_tx - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (off[mid] <= i)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    const long long j = i - off[lo];
+    const float3 d = kind == RT_RAYS_FIBONACCI ? fib_dir(j, off[lo + 1] - off[lo]) : ico_dir(j, 1ll << param[lo]);
+    rays[2 * i] = make_float4(tx[3 * lo], tx[3 * lo + 1], tx[3 * lo + 2], tmin);
+    rays[2 * i + 1] = make_float4(d.x, d.y, d.z, tmax);
   }
 }
 
@@ -196,19 +233,11 @@ __global__ void __launch_bounds__(kRayBlock) k_reflect_scatter(ReflectArgs A) {
   if (pos >= A.cap) return;
   const float4 ra = A.rays[2 * i], rb = A.rays[2 * i + 1];
   const int id = __float_as_int(h.y);
-  const float t = h.x;
-  const float4 a = A.tri_in[3 * (size_t)id], b = A.tri_in[3 * (size_t)id + 1], c = A.tri_in[3 * (size_t)id + 2];
-  const float e1x = b.x - a.x, e1y = b.y - a.y, e1z = b.z - a.z;
-  const float e2x = c.x - a.x, e2y = c.y - a.y, e2z = c.z - a.z;
-  float nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
-  const float inv = rsqrtf(nx * nx + ny * ny + nz * nz);
-  nx *= inv;
-  ny *= inv;
-  nz *= inv;
-  const float dn = rb.x * nx + rb.y * ny + rb.z * nz;
-  A.out_rays[2 * (size_t)pos] = make_float4(fmaf(t, rb.x, ra.x), fmaf(t, rb.y, ra.y), fmaf(t, rb.z, ra.z), 0.f);
-  A.out_rays[2 * (size_t)pos + 1] =
-      make_float4(rb.x - 2.f * dn * nx, rb.y - 2.f * dn * ny, rb.z - 2.f * dn * nz, rb.w - t);
+  float4 o0, o1;
+  reflect_ray(ra, rb, h.x, A.tri_in[3 * (size_t)id], A.tri_in[3 * (size_t)id + 1], A.tri_in[3 * (size_t)id + 2], &o0,
+              &o1);
+  A.out_rays[2 * (size_t)pos] = o0;
+  A.out_rays[2 * (size_t)pos + 1] = o1;
   A.out_skip[pos] = id;
   if (A.out_src) A.out_src[pos] = (int)i;
 }
@@ -294,6 +323,19 @@ cudaError_t launch_gen_rays(int kind, const float* o, long long param, float tmi
     k_gen_icosphere<<<grid_for(count, sms()), kRayBlock, 0, st>>>(o[0], o[1], o[2], 1 << param, count, tmin,
                                                                    tmax, reinterpret_cast<float4*>(rays));
   }
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gen_batch(int kind, const float* tx_dev, const long long* off_dev, const long long* param_dev,
+                             int n_tx, long long total, float tmin, float tmax, rt_ray* rays, cudaStream_t st) {
+  if (total <= 0) return cudaSuccess;
+  if (kind == RT_RAYS_ICOSPHERE) {
+    std::call_once(g_ico_once, init_ico);
+    if (!g_ico_ok) return cudaErrorInitializationError;
+  }
+  k_gen_batch<<<grid_for(total, sms()), kRayBlock, 0, st>>>(kind, tx_dev, off_dev, param_dev, n_tx, tmin, tmax,
+                                                             reinterpret_cast<float4*>(rays));
   count_launches(1);
   return cudaGetLastError();
 }

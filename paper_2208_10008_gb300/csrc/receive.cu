@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "rt_internal.cuh"
+#include "receive_ray.cuh"
 
 namespace rt {
 int set_error(int code, const char* msg);  // records the message for rt_last_error
@@ -40,140 +41,17 @@ struct rt_rxset_s {
 
 namespace {
 
+using rt::RecvArgs;
+using rt::receive_one;
+
 constexpr int kRecvBlock = 256;
-constexpr int kRecvSeen = 16;  // receivers a ray remembers to report each once
-
-struct RecvArgs {
-  const float4* rays;
-  const float4* hits;
-  int n;
-  const int* n_dev;
-  float3 lo;
-  float h, inv_h;
-  int nx, ny, nz;
-  const int* cell_start;
-  const int* items;
-  const float4* pos;
-  float k;  // delta / sqrt(3)
-  const float* delta_ray;  // nullable: per-ray delta
-  float k_cap;             // largest k the set supports
-  float range0;
-  int max_records;
-  int4* out;
-  int* count;
-  unsigned long long* stats;  // nullable: cells visited, entries tested
-};
-
-__device__ __forceinline__ bool finite3(float a, float b, float c) {
-  return isfinite(a) && isfinite(b) && isfinite(c);
-}
 
 template <bool kStats>
 __global__ void __launch_bounds__(kRecvBlock) k_receive(RecvArgs A) {
   const int i = blockIdx.x * kRecvBlock + threadIdx.x;
   const int n = A.n_dev ? min(A.n, __ldg(A.n_dev)) : A.n;
   if (i >= n) return;
-  const float4 ra = __ldg(A.rays + 2 * i), rb = __ldg(A.rays + 2 * i + 1);
-  const float ht = __ldg(&A.hits[i].x);
-  const float tmin = ra.w, tmax = rb.w;
-  const float tend = ht < tmax ? ht : tmax;
-  if (!finite3(ra.x, ra.y, ra.z) || !finite3(rb.x, rb.y, rb.z) || !isfinite(tmin) || !isfinite(tmax) ||
-      !(tend > tmin))
-    return;
-  const float ox = ra.x, oy = ra.y, oz = ra.z, dx = rb.x, dy = rb.y, dz = rb.z;
-  const float dd = dx * dx + dy * dy + dz * dz;
-  if (!(dd > 0.f)) return;
-  const float inv_dd = 1.f / dd;
-  const float lprev = A.range0 - tmax;
-  const float kr = A.delta_ray ? fminf(__ldg(A.delta_ray + i) * 0.57735026918962576f, A.k_cap) : A.k;
-  // clip [tmin, tend] to the grid box
-  const float hx = A.lo.x + A.nx * A.h, hy = A.lo.y + A.ny * A.h, hz = A.lo.z + A.nz * A.h;
-  float ta = tmin, tb = tend;
-  {
-    const float o3[3] = {ox, oy, oz}, d3[3] = {dx, dy, dz};
-    const float l3[3] = {A.lo.x, A.lo.y, A.lo.z}, h3[3] = {hx, hy, hz};
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      if (d3[a] == 0.f) {
-        if (o3[a] < l3[a] || o3[a] > h3[a]) return;
-      } else {
-        const float inv = 1.f / d3[a];
-        float t0 = (l3[a] - o3[a]) * inv, t1 = (h3[a] - o3[a]) * inv;
-        if (t0 > t1) {
-          const float w = t0;
-          t0 = t1;
-          t1 = w;
-        }
-        ta = fmaxf(ta, t0);
-        tb = fminf(tb, t1);
-      }
-    }
-  }
-  if (!(ta <= tb)) return;
-  // entry cell and stepping state per axis
-  int c[3], step[3], dim[3] = {A.nx, A.ny, A.nz};
-  float tn[3], dt[3];
-  {
-    const float o3[3] = {ox, oy, oz}, d3[3] = {dx, dy, dz};
-    const float l3[3] = {A.lo.x, A.lo.y, A.lo.z};
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const float pe = o3[a] + ta * d3[a];
-      c[a] = min(max((int)floorf((pe - l3[a]) * A.inv_h), 0), dim[a] - 1);
-      if (d3[a] > 0.f) {
-        step[a] = 1;
-        tn[a] = (l3[a] + (c[a] + 1) * A.h - o3[a]) / d3[a];
-        dt[a] = A.h / d3[a];
-      } else if (d3[a] < 0.f) {
-        step[a] = -1;
-        tn[a] = (l3[a] + c[a] * A.h - o3[a]) / d3[a];
-        dt[a] = -A.h / d3[a];
-      } else {
-        step[a] = 0;
-        tn[a] = INFINITY;
-        dt[a] = INFINITY;
-      }
-    }
-  }
-  int seen[kRecvSeen];
-  int ns = 0;
-  unsigned n_cells = 0, n_entries = 0;
-  const int max_steps = A.nx + A.ny + A.nz + 3;
-  for (int it = 0; it < max_steps; ++it) {
-    const int cell = (c[2] * A.ny + c[1]) * A.nx + c[0];
-    const int e0 = __ldg(A.cell_start + cell), e1 = __ldg(A.cell_start + cell + 1);
-    if (kStats) {
-      ++n_cells;
-      n_entries += (unsigned)(e1 - e0);
-    }
-    for (int e = e0; e < e1; ++e) {
-      const int j = __ldg(A.items + e);
-      const float4 p = __ldg(A.pos + j);
-      const float qx = p.x - ox, qy = p.y - oy, qz = p.z - oz;
-      const float ts = (qx * dx + qy * dy + qz * dz) * inv_dd;
-      if (!(ts >= tmin && ts < tend)) continue;
-      const float ex = qx - ts * dx, ey = qy - ts * dy, ez = qz - ts * dz;
-      const float dist = sqrtf(ex * ex + ey * ey + ez * ez);
-      const float l = lprev + ts;
-      if (!(dist <= l * kr)) continue;
-      bool dup = false;
-      for (int q = 0; q < ns; ++q) dup = dup || seen[q] == j;
-      if (dup) continue;
-      if (ns < kRecvSeen) seen[ns++] = j;
-      const int slot = atomicAdd(A.count, 1);
-      if (slot < A.max_records) A.out[slot] = make_int4(i, j, __float_as_int(l), __float_as_int(dist));
-    }
-    // next cell: the axis whose boundary comes first
-    const int a = tn[0] <= tn[1] ? (tn[0] <= tn[2] ? 0 : 2) : (tn[1] <= tn[2] ? 1 : 2);
-    if (tn[a] > tb) break;
-    c[a] += step[a];
-    if (c[a] < 0 || c[a] >= dim[a]) break;
-    tn[a] += dt[a];
-  }
-  if (kStats) {
-    atomicAdd(A.stats, (unsigned long long)n_cells);
-    atomicAdd(A.stats + 1, (unsigned long long)n_entries);
-  }
+  receive_one<kStats>(A, i, A.rays, A.hits, A.delta_ray, A.out, A.count);
 }
 
 }  // namespace
@@ -269,6 +147,41 @@ extern "C" int rt_rxset_destroy(rt_rxset s) {
   return RT_OK;
 }
 
+namespace rt {
+int receive_args(const rt_rxset_s* s, const rt_receive_params* p, RecvArgs* A) {
+  if (!s || !p) return rt::set_error(RT_EINVAL, "NULL argument");
+  if (!(p->delta > 0.f) || !std::isfinite(p->delta) || !(p->range0 > 0.f) || !std::isfinite(p->range0))
+    return rt::set_error(RT_EINVAL, "delta and range0 must be positive and finite");
+  if (p->max_records < 0) return rt::set_error(RT_EINVAL, "bad record buffer");
+  if ((uintptr_t)p->stats_dev & 7) return rt::set_error(RT_EINVAL, "stats_dev must be 8-byte aligned");
+  const float k = (float)(p->delta / std::sqrt(3.0));
+  if ((double)p->range0 * k > (double)s->r_max * 1.0001)
+    return rt::set_error(RT_EINVAL, "range0 * delta / sqrt(3) exceeds the receiver set's r_max");
+  A->rays = nullptr;
+  A->hits = nullptr;
+  A->n = 0;
+  A->n_dev = nullptr;
+  A->lo = make_float3(s->lo[0], s->lo[1], s->lo[2]);
+  A->h = s->h;
+  A->inv_h = 1.f / s->h;
+  A->nx = s->dims[0];
+  A->ny = s->dims[1];
+  A->nz = s->dims[2];
+  A->cell_start = s->cell_start;
+  A->items = s->items;
+  A->pos = s->pos;
+  A->k = k;
+  A->delta_ray = p->delta_ray_dev;
+  A->k_cap = (float)((double)s->r_max * 1.0001 / (double)p->range0);
+  A->range0 = p->range0;
+  A->max_records = p->max_records;
+  A->out = nullptr;
+  A->count = nullptr;
+  A->stats = p->stats_dev;
+  return RT_OK;
+}
+}  // namespace rt
+
 extern "C" int rt_receive(rt_rxset s, const rt_ray* rays, const rt_hit* hits, int64_t n, const int32_t* n_dev,
                           const rt_receive_params* p, rt_rx_record* out, int32_t* count, void* stream) {
   if (!s || !p || !count) return rt::set_error(RT_EINVAL, "NULL argument");
@@ -276,39 +189,20 @@ extern "C" int rt_receive(rt_rxset s, const rt_ray* rays, const rt_hit* hits, in
   if (n > 0 && (!rays || !hits)) return rt::set_error(RT_EINVAL, "NULL rays or hits");
   if (((uintptr_t)rays & 15) || ((uintptr_t)hits & 15) || ((uintptr_t)out & 15))
     return rt::set_error(RT_EINVAL, "rays, hits and records must be 16-byte aligned");
-  if (!(p->delta > 0.f) || !std::isfinite(p->delta) || !(p->range0 > 0.f) || !std::isfinite(p->range0))
-    return rt::set_error(RT_EINVAL, "delta and range0 must be positive and finite");
-  if (p->max_records < 0 || (p->max_records > 0 && !out)) return rt::set_error(RT_EINVAL, "bad record buffer");
-  if ((uintptr_t)p->stats_dev & 7) return rt::set_error(RT_EINVAL, "stats_dev must be 8-byte aligned");
-  const float k = (float)(p->delta / std::sqrt(3.0));
-  if ((double)p->range0 * k > (double)s->r_max * 1.0001)
-    return rt::set_error(RT_EINVAL, "range0 * delta / sqrt(3) exceeds the receiver set's r_max");
+  if (p->max_records > 0 && !out) return rt::set_error(RT_EINVAL, "bad record buffer");
+  RecvArgs A;
+  const int rc = rt::receive_args(s, p, &A);
+  if (rc != RT_OK) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int32_t), st);
   if (e != cudaSuccess) return rt::set_error(RT_ECUDA, cudaGetErrorString(e));
   if (n == 0) return RT_OK;
-  RecvArgs A;
   A.rays = reinterpret_cast<const float4*>(rays);
   A.hits = reinterpret_cast<const float4*>(hits);
   A.n = (int)n;
   A.n_dev = n_dev;
-  A.lo = make_float3(s->lo[0], s->lo[1], s->lo[2]);
-  A.h = s->h;
-  A.inv_h = 1.f / s->h;
-  A.nx = s->dims[0];
-  A.ny = s->dims[1];
-  A.nz = s->dims[2];
-  A.cell_start = s->cell_start;
-  A.items = s->items;
-  A.pos = s->pos;
-  A.k = k;
-  A.delta_ray = p->delta_ray_dev;
-  A.k_cap = (float)((double)s->r_max * 1.0001 / (double)p->range0);
-  A.range0 = p->range0;
-  A.max_records = p->max_records;
   A.out = reinterpret_cast<int4*>(out);
   A.count = count;
-  A.stats = p->stats_dev;
   const int grid = (int)((n + kRecvBlock - 1) / kRecvBlock);
   if (A.stats)
     k_receive<true><<<grid, kRecvBlock, 0, st>>>(A);

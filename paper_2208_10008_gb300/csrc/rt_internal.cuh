@@ -118,6 +118,28 @@ __device__ __forceinline__ float qplane(unsigned q, float scale, float origin) {
   return __fmaf_rn(__int_as_float(0x4B000000u | q) - 8388608.f, scale, origin);
 }
 
+// Specular bounce (Sec. III.B) of the ray (ra = origin, tmin; rb = direction,
+// tmax) at its hit t on triangle (a, b, c): origin o + t d, direction
+// d - 2 (d.n) n about the unit geometric normal n of (b - a) x (c - a), the
+// range left tmax - t.  Every operation is rounded explicitly, so every
+// kernel that bounces a ray writes the same bits.
+__device__ __forceinline__ void reflect_ray(float4 ra, float4 rb, float t, float4 a, float4 b, float4 c,
+                                            float4* o0, float4* o1) {
+  const float e1x = __fsub_rn(b.x, a.x), e1y = __fsub_rn(b.y, a.y), e1z = __fsub_rn(b.z, a.z);
+  const float e2x = __fsub_rn(c.x, a.x), e2y = __fsub_rn(c.y, a.y), e2z = __fsub_rn(c.z, a.z);
+  float nx = __fsub_rn(__fmul_rn(e1y, e2z), __fmul_rn(e1z, e2y));
+  float ny = __fsub_rn(__fmul_rn(e1z, e2x), __fmul_rn(e1x, e2z));
+  float nz = __fsub_rn(__fmul_rn(e1x, e2y), __fmul_rn(e1y, e2x));
+  const float inv = rsqrtf(__fadd_rn(__fadd_rn(__fmul_rn(nx, nx), __fmul_rn(ny, ny)), __fmul_rn(nz, nz)));
+  nx = __fmul_rn(nx, inv);
+  ny = __fmul_rn(ny, inv);
+  nz = __fmul_rn(nz, inv);
+  const float k = __fmul_rn(2.f, __fadd_rn(__fadd_rn(__fmul_rn(rb.x, nx), __fmul_rn(rb.y, ny)), __fmul_rn(rb.z, nz)));
+  *o0 = make_float4(__fmaf_rn(t, rb.x, ra.x), __fmaf_rn(t, rb.y, ra.y), __fmaf_rn(t, rb.z, ra.z), 0.f);
+  *o1 = make_float4(__fsub_rn(rb.x, __fmul_rn(k, nx)), __fsub_rn(rb.y, __fmul_rn(k, ny)),
+                    __fsub_rn(rb.z, __fmul_rn(k, nz)), __fsub_rn(rb.w, t));
+}
+
 struct __align__(16) Task {
   int32_t begin, count, parent, side;  // parent: node2 id (-1 root); side 0/1
   float clo[3];                        // centroid bounds of the task's triangles
@@ -228,6 +250,39 @@ cudaError_t launch_trace_dev(struct ::rt_scene_s* s, const rt_ray* rays, int64_t
                              cudaStream_t st);
 cudaError_t launch_gen_rays(int kind, const float* origin, long long param, float tmin, float tmax,
                             rt_ray* rays, long long count, cudaStream_t st);
+// Device buffers of a batch for the one-launch pipeline (launch_batch_persistent).
+struct BatchLaunch {
+  int max_order;
+  long long n0, n_seg;
+  rt_ray* rays[RT_BATCH_MAX_ORDER + 1];
+  rt_hit* hits[RT_BATCH_MAX_ORDER + 1];
+  int* skip[RT_BATCH_MAX_ORDER + 1];
+  int* src[RT_BATCH_MAX_ORDER + 1];
+  int* counts;      // [RT_BATCH_MAX_ORDER + 1]
+  int* chunk;       // [n0 / 32 + 1]
+  int* cta_total;   // [cta_cap]
+  int cta_cap;
+  const rt_ray* seg;
+  uint8_t* occl;
+  unsigned* bar;    // [4]
+  int* status;
+  int* take;        // [RT_BATCH_MAX_ORDER + 2]
+  long long timeout_ns;
+  TraceScratch* scr;
+  // reception (Eq. 4) afterwards: every bounced ray takes its parent's delta
+  int receive;
+  float* delta[RT_BATCH_MAX_ORDER + 1];         // per ray: its transmitter's delta (order 0 given)
+};
+// Every order of a batch and its visibility segments in one cooperative
+// launch (trace.cu); the order-0 rays must already be in rays[0].
+cudaError_t launch_batch_persistent(struct ::rt_scene_s* s, const BatchLaunch& b, cudaStream_t st);
+// The most CTAs the one-launch pipeline may use on this device.
+int persistent_batch_ctas();
+
+// Launches of n_tx transmitters in one kernel (device arrays: tx 3 floats
+// each, off n_tx + 1 ray offsets, param the launch parameters).
+cudaError_t launch_gen_batch(int kind, const float* tx_dev, const long long* off_dev, const long long* param_dev,
+                             int n_tx, long long total, float tmin, float tmax, rt_ray* rays, cudaStream_t st);
 cudaError_t launch_reflect(const struct ::rt_scene_s* s, const rt_ray* rays, const rt_hit* hits,
                            long long n, const int* n_dev, rt_ray* out_rays, int* out_skip,
                            int* out_src, int* out_count, int* block_counts, long long cap,

@@ -377,13 +377,15 @@ struct TraceArgs {
   int qcap;
 };
 
-template <bool kAny, bool kStats, int kTile, int kSD, bool kQuant, int kW = 4>
-__global__ void __launch_bounds__(kTile) k_trace(TraceArgs A) {
-  const int i = blockIdx.x * kTile + threadIdx.x;
-  if (i >= A.n || (A.n_dev && i >= *A.n_dev)) return;
-  const float4* r4 = reinterpret_cast<const float4*>(A.rays) + 2 * (size_t)i;
+// The float32 walk of ray i (the whole of Fig. 4 for one ray): results,
+// statistics and the flag for the float64 pass.
+template <bool kAny, bool kStats, int kSD, bool kQuant, int kW>
+__device__ __forceinline__ void walk_one(const TraceArgs& A, const int i, const rt_ray* __restrict__ rays,
+                                         rt_hit* __restrict__ hits, uint8_t* __restrict__ occl,
+                                         const int32_t* __restrict__ skip_ids) {
+  const float4* r4 = reinterpret_cast<const float4*>(rays) + 2 * (size_t)i;
   const RayPre r = setup_ray(__ldg(r4), __ldg(r4 + 1));
-  const int skip = A.skip ? __ldg(A.skip + i) : -1;
+  const int skip = skip_ids ? __ldg(skip_ids + i) : -1;
   float t1 = INFINITY, t2 = INFINITY, e1 = 0.f, e2 = 0.f, bu = 0.f, bv = 0.f;
   int id1 = -1, pos1 = -1;
   bool flag = false, done = false;
@@ -551,7 +553,7 @@ __global__ void __launch_bounds__(kTile) k_trace(TraceArgs A) {
     }
   }
   if (kAny) {
-    A.occl[i] = done ? 1 : 0;
+    occl[i] = done ? 1 : 0;
     if (done) flag = false;
   } else {
     if (t2 < INFINITY && t2 <= t1 + kTieRel * t1 + e1 + e2) flag = true;
@@ -563,7 +565,7 @@ __global__ void __launch_bounds__(kTile) k_trace(TraceArgs A) {
     }
     float4 out = id1 >= 0 ? make_float4(t1, __int_as_float(id1), bu, bv)
                           : make_float4(INFINITY, __int_as_float(-1), 0.f, 0.f);
-    reinterpret_cast<float4*>(A.hits)[i] = out;
+    reinterpret_cast<float4*>(hits)[i] = out;
   }
   if (kStats && A.stats) {
     A.stats[2 * (size_t)i] = n_nodes;
@@ -580,6 +582,13 @@ __global__ void __launch_bounds__(kTile) k_trace(TraceArgs A) {
       c[0] = walk_all ? -1 : w;
     }
   }
+}
+
+template <bool kAny, bool kStats, int kTile, int kSD, bool kQuant, int kW = 4>
+__global__ void __launch_bounds__(kTile) k_trace(TraceArgs A) {
+  const int i = blockIdx.x * kTile + threadIdx.x;
+  if (i >= A.n || (A.n_dev && i >= *A.n_dev)) return;
+  walk_one<kAny, kStats, kSD, kQuant, kW>(A, i, A.rays, A.hits, A.occl, A.skip);
 }
 
 // ---------------------------------------------------------------- float64
@@ -630,14 +639,16 @@ __device__ bool mt64(D3 o, D3 d, D3 v0, D3 v1, D3 v2, double* t, double* u, doub
 // float64 rule and a reduction over the group keeps the nearest (lowest id on
 // ties, the same minimum whatever G is).  Rays without a complete list: one
 // thread each walks the tree.
+// The float64 pass over every flagged ray, by threads tid of nthreads
+// (nthreads a multiple of 32, whole warps).
 template <bool kAny>
-__global__ void __launch_bounds__(kRetestBlock) k_retest64(TraceArgs A) {
+__device__ void retest_all(const TraceArgs& A, const int tid, const int nthreads, const rt_ray* __restrict__ rays,
+                           rt_hit* __restrict__ hits, uint8_t* __restrict__ occl,
+                           const int32_t* __restrict__ skip_ids) {
   const int nflag = min(*(volatile int*)A.counter, A.qcap);
   if (nflag <= 0) return;
-  const int nthreads = gridDim.x * kRetestBlock;
   int lg = 5;
   while (lg > 0 && ((long long)nflag << lg) > nthreads) --lg;
-  const int tid = blockIdx.x * kRetestBlock + threadIdx.x;
   const int lane = threadIdx.x & 31, sub = lane & ((1 << lg) - 1);
   const int ngroups = nthreads >> lg;
   // jw: the first ray of this warp's groups; the loop is uniform over the warp
@@ -647,7 +658,7 @@ __global__ void __launch_bounds__(kRetestBlock) k_retest64(TraceArgs A) {
     const int* cl = A.cand + (size_t)(live ? j : 0) * (kCand + 1);
     const int ncand = live ? cl[0] : -1;
     const int i = live ? A.queue[j] : 0;
-    const float4* r4 = reinterpret_cast<const float4*>(A.rays) + 2 * (size_t)i;
+    const float4* r4 = reinterpret_cast<const float4*>(rays) + 2 * (size_t)i;
     float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rb = ra;
     if (ncand > 0) {
       ra = r4[0];
@@ -655,7 +666,7 @@ __global__ void __launch_bounds__(kRetestBlock) k_retest64(TraceArgs A) {
     }
     const D3 o{ra.x, ra.y, ra.z}, d{rb.x, rb.y, rb.z};
     const double tmin = ra.w, tmax = rb.w;
-    const int skip = (ncand > 0 && A.skip) ? A.skip[i] : -1;
+    const int skip = (ncand > 0 && skip_ids) ? skip_ids[i] : -1;
     double bt = INFINITY, bu = 0.0, bv = 0.0;
     int bid = INT_MAX, bpos = -1;
     for (int q = sub; q < ncand; q += 1 << lg) {
@@ -693,7 +704,7 @@ __global__ void __launch_bounds__(kRetestBlock) k_retest64(TraceArgs A) {
     }
     const RayPre r = setup_ray(ra, rb);
     if (kAny) {
-      A.occl[i] = bid != INT_MAX ? 1 : 0;
+      occl[i] = bid != INT_MAX ? 1 : 0;
     } else {
       float4 out = make_float4(INFINITY, __int_as_float(-1), 0.f, 0.f);
       if (bid != INT_MAX) {
@@ -711,18 +722,18 @@ __global__ void __launch_bounds__(kRetestBlock) k_retest64(TraceArgs A) {
           out = make_float4(t, __int_as_float(bid), h.u, h.v);
         }
       }
-      reinterpret_cast<float4*>(A.hits)[i] = out;
+      reinterpret_cast<float4*>(hits)[i] = out;
     }
   }
   // rays without a complete candidate list: one thread each walks the tree
-  for (int j = blockIdx.x * kRetestBlock + threadIdx.x; j < nflag; j += gridDim.x * kRetestBlock) {
+  for (int j = tid; j < nflag; j += nthreads) {
     const int i = A.queue[j];
-    const float4* r4 = reinterpret_cast<const float4*>(A.rays) + 2 * (size_t)i;
+    const float4* r4 = reinterpret_cast<const float4*>(rays) + 2 * (size_t)i;
     const float4 ra = r4[0], rb = r4[1];
     const RayPre r = setup_ray(ra, rb);
     const D3 o{ra.x, ra.y, ra.z}, d{rb.x, rb.y, rb.z};
     const double tmin = ra.w, tmax = rb.w;
-    const int skip = A.skip ? A.skip[i] : -1;
+    const int skip = skip_ids ? skip_ids[i] : -1;
     double bt = INFINITY, bu = 0.0, bv = 0.0;
     int bid = -1, bpos = -1;
     bool any = false;
@@ -793,7 +804,7 @@ __global__ void __launch_bounds__(kRetestBlock) k_retest64(TraceArgs A) {
       }
     }
     if (kAny) {
-      A.occl[i] = any ? 1 : 0;
+      occl[i] = any ? 1 : 0;
     } else {
       float4 out = make_float4(INFINITY, __int_as_float(-1), 0.f, 0.f);
       if (bid >= 0) {
@@ -811,8 +822,227 @@ __global__ void __launch_bounds__(kRetestBlock) k_retest64(TraceArgs A) {
           out = make_float4(t, __int_as_float(bid), h.u, h.v);
         }
       }
-      reinterpret_cast<float4*>(A.hits)[i] = out;
+      reinterpret_cast<float4*>(hits)[i] = out;
     }
+  }
+}
+
+template <bool kAny>
+__global__ void __launch_bounds__(kRetestBlock) k_retest64(TraceArgs A) {
+  retest_all<kAny>(A, blockIdx.x * kRetestBlock + threadIdx.x, gridDim.x * kRetestBlock, A.rays, A.hits, A.occl,
+                   A.skip);
+}
+
+// ---------------------------------------------------------------- one launch for a whole batch
+// Every reflection order of a batch (Sec. III.B: trace, bounce, trace the
+// bounced rays, until the order limit) and the visibility segments in one
+// cooperative launch: the CTAs stay resident and step through the phases
+// together, separated by grid barriers:
+//   for each order k: walk (float32) -> barrier -> float64 pass of the flagged
+//   rays -> barrier -> survivors per 32-ray chunk -> barrier -> offsets
+//   (stable, in ray order) -> barrier -> bounce into order k + 1 -> barrier;
+//   then the segments: walk (any hit) -> barrier -> float64 pass.
+// The walk, the float64 pass and the bounce are the same device code as the
+// separate kernels (rt_trace_closest, rt_reflect), so every order's rays,
+// hits and parent indices are the same bits.  A barrier waits at most
+// timeout_ns (global timer); when it runs out the status word is set and
+// every CTA leaves.
+struct PersistArgs {
+  TraceArgs T;           // scene arrays and the float64 pass's scratch
+  const float4* tri_in;  // input-order triangles (bounces)
+  int max_order;
+  int n0;
+  rt_ray* rays[RT_BATCH_MAX_ORDER + 1];
+  rt_hit* hits[RT_BATCH_MAX_ORDER + 1];
+  int* skip[RT_BATCH_MAX_ORDER + 1];
+  int* src[RT_BATCH_MAX_ORDER + 1];
+  int* counts;       // counts[k]: rays of order k >= 1 (written here)
+  int* chunk;        // per 32-ray chunk: survivors, then the chunk's first output position
+  int* cta_total;    // per CTA: survivors of its chunks
+  const rt_ray* seg;
+  int n_seg;
+  uint8_t* occl;
+  unsigned* bar;     // [0] arrivals, [1] generation (zero before the launch)
+  int* status;       // 0, or 1 when a barrier ran out of time
+  int* take;         // [RT_BATCH_MAX_ORDER + 2]: rays handed out so far by each walk phase (orders,
+                     // then the segments; zero before)
+  long long timeout_ns;
+  int receive;       // 1: carry each ray's delta (reception, Eq. 4) through the bounces
+  float* delta[RT_BATCH_MAX_ORDER + 1];
+};
+
+constexpr int kPersistBlock = 128;
+constexpr int kPersistMinBlocks = 8;  // 64 registers: the walk's own budget
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid barrier (all CTAs resident: cooperative launch).  Returns false when
+// the batch failed (a barrier ran out of time); the caller then leaves.
+__device__ bool grid_sync(const PersistArgs& P) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned* arrive = P.bar;
+    volatile unsigned* gen = P.bar + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    int good = 1;
+    if (atomicAdd(arrive, 1u) == gridDim.x - 1) {
+      atomicExch(arrive, 0u);
+      __threadfence();
+      atomicAdd(P.bar + 1, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (*gen == g) {
+        if (*(volatile int*)P.status != 0) {
+          good = 0;
+          break;
+        }
+        if (global_ns() - t0 > (unsigned long long)P.timeout_ns) {
+          atomicCAS(P.status, 0, 1);
+          good = 0;
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+    ok = good && *(volatile int*)P.status == 0;
+  }
+  __syncthreads();
+  return ok;
+}
+
+// A walk phase: every warp takes batches of 64 rays from the phase's device
+// counter until none is left (each lane walks two rays of a batch), so the
+// CTAs that drew cheap rays take more and the phase ends with the last rays.
+template <bool kAny, int kW>
+__device__ __forceinline__ void walk_phase(const TraceArgs& A, int* take, int n, const rt_ray* rays, rt_hit* hits,
+                                           uint8_t* occl, const int* skip) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    int b = 0;
+    if (lane == 0) b = atomicAdd(take, 64);
+    b = __shfl_sync(kFullMask, b, 0);
+    if (b >= n) break;
+    if (b + lane < n) walk_one<kAny, false, kStack, false, kW>(A, b + lane, rays, hits, occl, skip);
+    if (b + 32 + lane < n) walk_one<kAny, false, kStack, false, kW>(A, b + 32 + lane, rays, hits, occl, skip);
+  }
+}
+
+__device__ __forceinline__ bool bounces(const rt_hit* hits, const rt_ray* rays, int i) {
+  const float4 h = reinterpret_cast<const float4*>(hits)[i];
+  const float tmax = reinterpret_cast<const float4*>(rays)[2 * (size_t)i + 1].w;
+  return __float_as_int(h.y) >= 0 && tmax - h.x > 0.f;
+}
+
+template <int kW>
+__global__ void __launch_bounds__(kPersistBlock, kPersistMinBlocks) k_batch(const __grid_constant__ PersistArgs P) {
+  __shared__ int red[kPersistBlock / 32];
+  __shared__ int carry;
+  const int nth = gridDim.x * kPersistBlock;
+  const int tid = blockIdx.x * kPersistBlock + threadIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int kWarps = kPersistBlock / 32;
+  const TraceArgs& A = P.T;  // scene arrays (stats, occl, n_dev unused here)
+  for (int k = 0;; ++k) {
+    const int n = k == 0 ? P.n0 : *(volatile int*)(P.counts + k);
+    const rt_ray* rays = P.rays[k];
+    rt_hit* hits = P.hits[k];
+    const int* skip = k ? P.skip[k] : nullptr;
+    walk_phase<false, kW>(A, P.take + k, n, rays, hits, nullptr, skip);
+    if (!grid_sync(P)) return;
+    retest_all<false>(A, tid, nth, rays, hits, nullptr, skip);
+    if (!grid_sync(P)) return;
+    if (k == P.max_order) break;
+    // survivors of the bounce per 32-ray chunk; CTA b owns a contiguous run of chunks
+    if (tid == 0) *A.counter = 0;  // the next order's flags (this order's float64 pass is done)
+    const int nch = (n + 31) / 32, per = (nch + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int c0 = min(nch, (int)blockIdx.x * per), c1 = min(nch, c0 + per);
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int c = c0 + warp; c < c1; c += kWarps) {
+      const int i = c * 32 + lane;
+      const unsigned m = __ballot_sync(kFullMask, i < n && bounces(hits, rays, i));
+      if (lane == 0) {
+        P.chunk[c] = __popc(m);
+        atomicAdd(&carry, __popc(m));
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) P.cta_total[blockIdx.x] = carry;
+    if (!grid_sync(P)) return;
+    // first output position of every chunk: the survivors of the CTAs before
+    // this one, then a scan over this CTA's chunks in order
+    {
+      int part = 0;
+      for (int b = threadIdx.x; b < (int)blockIdx.x; b += kPersistBlock) part += P.cta_total[b];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(kFullMask, part, o);
+      if (lane == 0) red[warp] = part;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < kWarps; ++w) t += red[w];
+        carry = t;
+      }
+      __syncthreads();
+      for (int t0 = c0; t0 < c1; t0 += kPersistBlock) {
+        const int c = t0 + threadIdx.x;
+        const int v = c < c1 ? P.chunk[c] : 0;
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(kFullMask, x, o);
+          if (lane >= o) x += y;
+        }
+        if (lane == 31) red[warp] = x;
+        __syncthreads();
+        int off = carry, tot = 0;
+        for (int w = 0; w < kWarps; ++w) {
+          if (w < warp) off += red[w];
+          tot += red[w];
+        }
+        if (c < c1) P.chunk[c] = off + x - v;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += tot;
+        __syncthreads();
+      }
+      if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) P.counts[k + 1] = carry;
+    }
+    if (!grid_sync(P)) return;
+    // the bounce: every surviving ray of the chunk at its place in order k + 1
+    for (int c = c0 + warp; c < c1; c += kWarps) {
+      const int i = c * 32 + lane;
+      const bool keep = i < n && bounces(hits, rays, i);
+      const unsigned m = __ballot_sync(kFullMask, keep);
+      if (!keep) continue;
+      const int pos = P.chunk[c] + __popc(m & ((1u << lane) - 1u));
+      const float4* r4 = reinterpret_cast<const float4*>(rays) + 2 * (size_t)i;
+      const float4 h = reinterpret_cast<const float4*>(hits)[i];
+      const int id = __float_as_int(h.y);
+      float4 o0, o1;
+      reflect_ray(r4[0], r4[1], h.x, P.tri_in[3 * (size_t)id], P.tri_in[3 * (size_t)id + 1],
+                  P.tri_in[3 * (size_t)id + 2], &o0, &o1);
+      float4* out = reinterpret_cast<float4*>(P.rays[k + 1]) + 2 * (size_t)pos;
+      out[0] = o0;
+      out[1] = o1;
+      P.skip[k + 1][pos] = id;
+      P.src[k + 1][pos] = i;
+      if (P.receive) P.delta[k + 1][pos] = P.delta[k][i];
+    }
+    if (!grid_sync(P)) return;
+  }
+  if (P.n_seg > 0) {
+    if (tid == 0) *A.counter = 0;
+    if (!grid_sync(P)) return;
+    walk_phase<true, kW>(A, P.take + RT_BATCH_MAX_ORDER + 1, P.n_seg, P.seg, nullptr, P.occl, nullptr);
+    if (!grid_sync(P)) return;
+    retest_all<true>(A, tid, nth, P.seg, nullptr, P.occl, nullptr);
   }
 }
 
@@ -941,6 +1171,84 @@ cudaError_t launch_trace_dev(rt_scene_s* s, const rt_ray* rays, int64_t n, const
   }
   count_launches(n_launched);
   return cudaGetLastError();
+}
+
+cudaError_t launch_batch_persistent(rt_scene_s* s, const BatchLaunch& b, cudaStream_t st) {
+  PersistArgs P;
+  TraceArgs& A = P.T;
+  A.wide = s->wide;
+  A.wide8 = s->wide8;
+  A.qwide = s->qwide;
+  A.wide_root = &s->ctl->wide_root;
+  A.node2 = s->node2;
+  A.link2 = s->link2;
+  A.root_ref = &s->ctl->root_ref;
+  A.n_tri = (int)s->n_built;
+  A.tris = s->tri_leaf;
+  A.counter = b.scr->counter;
+  A.queue = b.scr->queue;
+  A.cand = b.scr->cand;
+  A.qcap = (int)b.scr->cap;
+  A.n_dev = nullptr;
+  A.stats = nullptr;
+  P.tri_in = s->tri_in;
+  P.max_order = b.max_order;
+  P.n0 = (int)b.n0;
+  for (int k = 0; k <= RT_BATCH_MAX_ORDER; ++k) {
+    P.rays[k] = b.rays[k];
+    P.hits[k] = b.hits[k];
+    P.skip[k] = b.skip[k];
+    P.src[k] = b.src[k];
+  }
+  P.counts = b.counts;
+  P.chunk = b.chunk;
+  P.cta_total = b.cta_total;
+  P.seg = b.seg;
+  P.n_seg = (int)b.n_seg;
+  P.occl = b.occl;
+  P.bar = b.bar;
+  P.status = b.status;
+  P.take = b.take;
+  P.receive = b.receive;
+  for (int k = 0; k <= RT_BATCH_MAX_ORDER; ++k) P.delta[k] = b.delta[k];
+  P.timeout_ns = b.timeout_ns;
+  cudaError_t e;
+  // arrivals, generation, status and the phases' ray counters start from
+  // zero; the flag counter too
+  if ((e = cudaMemsetAsync(b.bar, 0, 4 * sizeof(unsigned), st))) return e;
+  if ((e = cudaMemsetAsync(b.take, 0, (RT_BATCH_MAX_ORDER + 2) * sizeof(int), st))) return e;
+  if ((e = cudaMemsetAsync(b.scr->counter, 0, 2 * sizeof(int), st))) return e;
+  const bool w8 = s->params.width == 8;
+  void (*k)(PersistArgs) = w8 ? k_batch<8> : k_batch<4>;
+  static int per_sm[2] = {0, 0};
+  int& ps = per_sm[w8 ? 1 : 0];
+  if (!ps) {
+    int nb = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kPersistBlock, 0))) return e;
+    ps = nb;
+  }
+  if (ps < 1) return cudaErrorCooperativeLaunchTooLarge;
+  const int grid = std::min(ps * sm_count_t(), b.cta_cap);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kPersistBlock);
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if ((e = cudaLaunchKernelEx(&cfg, k, P))) return e;
+  count_launches(1);
+  return cudaSuccess;
+}
+
+int persistent_batch_ctas() {
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<4>, kPersistBlock, 0);
+  int nb8 = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb8, k_batch<8>, kPersistBlock, 0);
+  return std::max(std::max(nb, nb8), 1) * sm_count_t();
 }
 
 }  // namespace rt
