@@ -822,7 +822,8 @@ def run_ours(args):
     l2_gbs = l2_read_gbs(rtbvh, torch)
 
     extra = {}
-    want = set() if args.no_extra else set(x.strip() for x in args.extras.split(",") if x.strip())
+    # the extra measurements are single-GPU comparisons: a multi-GPU run (replicas) skips them
+    want = set() if (args.no_extra or ws > 1) else set(x.strip() for x in args.extras.split(",") if x.strip())
     if "alpha_sweep" in want:
         extra["alpha_sweep"] = run_alpha_sweep(rtbvh, torch, sc, rays, p["source"])
     if "quantised_nodes" in want:
