@@ -916,24 +916,24 @@ __device__ void top_chunk(const BuildArgs& A, TopSmem& S, const TopTask& T, int 
     scl[a] = bin_scale(T.clo[a], T.chi[a], K);
   }
   __syncthreads();
-  // Eq. 2 at every plane.  Up to 10 bins every warp evaluates all three axes
-  // in one pass and reaches the same split; otherwise every warp evaluates
-  // axis warp mod 3 (no branch on the warp index around the shuffles:
-  // inside one, they run an order of magnitude slower) and warps 0..2
-  // publish.  An axis without extent has all records in bin 0 and yields
-  // no candidate.
+  // Eq. 2 at every plane.  Up to 10 bins warp 0 evaluates all three axes in
+  // one pass; otherwise warp a evaluates axis a (a < 3).  The others wait at
+  // the barrier and read the choice from shared memory.  An axis without
+  // extent has all records in bin 0 and yields no candidate.
   Split best;
-  split_none(best);
+  if (warp < (3 * K <= 32 ? 1 : 3)) {
+    Split sp;
+    split_none(sp);
+    if (3 * K <= 32)
+      eval_axes(S.pbins, K, n, 0, 3, A.cp, sp);
+    else
+      eval_axis(S.pbins, K, n, warp, A.cp, sp);
+    if (lane == 0) S.ax[warp] = sp;
+  }
+  __syncthreads();
   if (3 * K <= 32) {
-    eval_axes(S.pbins, K, n, 0, 3, A.cp, best);
+    best = S.ax[0];
   } else {
-    {
-      Split sp;
-      split_none(sp);
-      eval_axis(S.pbins, K, n, warp % 3, A.cp, sp);
-      if (lane == 0 && warp < 3) S.ax[warp] = sp;
-    }
-    __syncthreads();
     best = S.ax[0];
 #pragma unroll
     for (int a = 1; a < 3; ++a) {
@@ -1659,6 +1659,7 @@ struct SubSmem {
   SubNode cur;          // the next node the CTA splits
   Task task;
   int red[kWarps];
+  int2 pick;  // the split Eq. 2 chose: candidate, records on the left
   int nm, mnext, got;
 };
 static_assert(sizeof(MidWarp) <= sizeof(float4) * 2 * 2 * kSubMax, "a warp's global-memory split state fits");
@@ -1758,8 +1759,9 @@ __device__ __forceinline__ void leaf_out(const BuildArgs& A, const float4* src, 
 // Split node X of the subtree with the whole CTA: bins (count and box) in
 // one shared array, each thread binning a run of records (thread (w, l)
 // takes run l * 8 + w, so the lanes of a warp work far apart); Eq. 2
-// evaluated by every warp (all reach the same split); stable partition by a
-// block scan, which also gathers both children's unions.  Thread 0 writes
+// evaluated by warp 0, its choice read by all from shared memory (one
+// warp's shuffles instead of eight); stable partition by a block scan,
+// which also gathers both children's unions.  Thread 0 writes
 // the node and routes the children: the larger one of more than 32 records
 // becomes S.cur (S.got), the smaller one of more than 32 goes to the device
 // queue, those of at most 32 to the small-node list.
@@ -1788,14 +1790,19 @@ __device__ void cta_split(const BuildArgs& A, SubSmem& S, const SubNode& X, int 
     bin_run(cb, src, k0, k1, K, cmin, scl);
   }
   __syncthreads();
-  Split best;
-  split_none(best);
-  eval_box(cb, K, n, scl, A.cp, best);
+  if (warp == 0) {  // one warp evaluates Eq. 2 (the others wait at the barrier)
+    Split best;
+    split_none(best);
+    eval_box(cb, K, n, scl, A.cp, best);
+    if (lane == 0) S.pick = make_int2(best.cand, best.L.n);
+  }
+  __syncthreads();
+  const int2 pick = S.pick;
   int axis, plane, nl;
-  if (best.cand != INT_MAX) {
-    axis = best.cand / (K - 1);
-    plane = 1 + best.cand % (K - 1);
-    nl = best.L.n;
+  if (pick.x != INT_MAX) {
+    axis = pick.x / (K - 1);
+    plane = 1 + pick.x % (K - 1);
+    nl = pick.y;
   } else {
     axis = -1;
     plane = 0;
@@ -1841,6 +1848,14 @@ __device__ void cta_split(const BuildArgs& A, SubSmem& S, const SubNode& X, int 
     total += v;
   }
   int lb = before + inc - cnt, rb = k0 - lb;
+  // the larger child of more than 32 records stays; the other one of more
+  // than 32 goes to the device queue, where an idle CTA takes it, so the
+  // subtree spreads over the SMs as it branches: its records go straight to
+  // buffer 1 here instead of to shared memory
+  const int nr = n - nl;
+  const int keep = nl >= nr ? 0 : 1;
+  const int ex = (keep == 0 ? nr : nl) > kMicro ? 1 - keep : -1;
+  float4* gx = A.rec[1] + 2 * ((size_t)gbegin + X.b);
   unsigned ua[kBinVals], ub[kBinVals];
 #pragma unroll
   for (int q = 0; q < kBinVals; ++q) ua[q] = ub[q] = 0u;
@@ -1851,8 +1866,13 @@ __device__ void cta_split(const BuildArgs& A, SubSmem& S, const SubNode& X, int 
       const bool left = (fl >> i) & 1u;
       const int d = left ? lb++ : nl + rb++;
       if (d < n) {
-        dst[2 * d] = rl[i];
-        dst[2 * d + 1] = rh[i];
+        if ((left ? 0 : 1) == ex) {
+          __stcg(gx + 2 * d, rl[i]);
+          __stcg(gx + 2 * d + 1, rh[i]);
+        } else {
+          dst[2 * d] = rl[i];
+          dst[2 * d + 1] = rh[i];
+        }
       }
       const RecCodes rc =
           rec_codes(rl[i], rh[i], centre(rl[i].x, rh[i].x), centre(rl[i].y, rh[i].y), centre(rl[i].z, rh[i].z));
@@ -1875,20 +1895,9 @@ __device__ void cta_split(const BuildArgs& A, SubSmem& S, const SubNode& X, int 
   }
   __syncthreads();
   const BinU L = binu_load(cu), R = binu_load(cu + kBinVals);
-  const int nr = n - nl;
   const bool leafl = nl <= A.max_leaf, leafr = nr <= A.max_leaf;
   if (leafl) leaf_out(A, dst, gbegin + X.b, nl, tid, kBlock);
   if (leafr) leaf_out(A, dst + 2 * nl, gbegin + X.b + nl, nr, tid, kBlock);
-  // the larger child of more than 32 records stays; the other one of more
-  // than 32 goes to the device queue (records to buffer 1), where an idle
-  // CTA takes it, so the subtree spreads over the SMs as it branches
-  const int keep = nl >= nr ? 0 : 1;
-  const int ex = (keep == 0 ? nr : nl) > kMicro ? 1 - keep : -1;
-  if (ex >= 0) {
-    const int eb = ex ? nl : 0, en = ex ? nr : nl;
-    for (int k = tid; k < 2 * en; k += kBlock) __stcg(A.rec[1] + 2 * ((size_t)gbegin + X.b + eb) + k, dst[2 * eb + k]);
-    __syncthreads();  // thread 0 publishes them below (a release store)
-  }
   if (tid == 0) {
     if (total != nl) set_status(A.ctl, kStBadSplit, 6);
     const int id = gbegin + X.b + nl - 1;
@@ -1901,8 +1910,8 @@ __device__ void cta_split(const BuildArgs& A, SubSmem& S, const SubNode& X, int 
       const int cn = s ? nr : nl, b = X.b + (s ? nl : 0);
       if (cn <= A.max_leaf) continue;
       if (s == ex) {
-        // the records written by every thread above are ordered before this
-        // thread by the barrier; push_task's release store publishes them
+        // the records written to buffer 1 by every thread are ordered before
+        // this thread by the barrier; push_task's release store publishes them
         push_task(A, make_task(gbegin + b, cn, id, s, X.depth + 1, s ? R : L, 1), epoch);
       } else if (cn <= kMicro) {
         if (S.nm < kMicroList)
@@ -2442,9 +2451,13 @@ cudaError_t launch_build(rt_scene_s* s, const rt_build_params& p, cudaStream_t s
   int gp = (n + kBlock - 1) / kBlock;
   gp = std::max(1, std::min(gp, nsm * 8));
   static bool attr = false;
+  static int split_per_sm = 2;  // resident split CTAs per SM (at most 2)
   if (!attr) {
     if ((e = cudaFuncSetAttribute(k_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SplitSmem))))
       return e;
+    int occ = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_split, kBlock, sizeof(SplitSmem)))) return e;
+    split_per_sm = std::max(1, std::min(2, occ));
     attr = true;
   }
   if ((e = launch(k_prep, gp, 0, st, false, A))) return e;
@@ -2453,7 +2466,7 @@ cudaError_t launch_build(rt_scene_s* s, const rt_build_params& p, cudaStream_t s
   if (s->split_ev[0] && (e = cudaStreamIsCapturing(st, &cs))) return e;
   const unsigned evflags = cs == cudaStreamCaptureStatusNone ? cudaEventRecordDefault : cudaEventRecordExternal;
   if (s->split_ev[0] && (e = cudaEventRecordWithFlags(s->split_ev[0], st, evflags))) return e;
-  if ((e = launch(k_split, 2 * nsm, sizeof(SplitSmem), st, true, A))) return e;
+  if ((e = launch(k_split, split_per_sm * nsm, sizeof(SplitSmem), st, true, A))) return e;
   if (s->split_ev[1] && (e = cudaEventRecordWithFlags(s->split_ev[1], st, evflags))) return e;
   if ((e = launch(k_post, gp, 0, st, true, A))) return e;
   count_launches(4);
