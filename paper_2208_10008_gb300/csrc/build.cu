@@ -193,31 +193,44 @@ __device__ __forceinline__ RecCodes rec_codes(float4 lo, float4 hi, float cx, fl
   return r;
 }
 
-// Add the record of every lane whose key is >= 0 to its bin entry `e`
-// (lanes with equal keys name the same entry; `cnt`, may be null, also gets
-// the number of records).  One pass per distinct key in the warp: the lanes
-// holding it are combined with full-warp reductions and the first of them
-// issues the shared-memory atomics.  All 32 lanes of the warp must call.
-__device__ __forceinline__ void bin_add_warp(int key, unsigned* e, unsigned* cnt, const RecCodes& c) {
+// Add the record of every lane with cell >= 0 to its bin on each axis: entry
+// e[a] (count at bins + e[a] * kBinVals, then the 12 code maxima) and, if
+// cnt is not null, cnt[e[a]].  The cell names the entries (equal cells,
+// equal entries).  Lanes whose cells are equal and adjacent form a run: a
+// segmented warp scan gives the run's last lane the run's count and code
+// maxima, and that lane alone issues the shared-memory atomics, for all
+// three axes.  Records in Morton or input order come in runs of one cell,
+// so a warp costs one scan of 12 words instead of reductions per distinct
+// bin and axis.  All 32 lanes of the warp must call.
+__device__ __forceinline__ void bin_add_runs(int cell, const int* e, unsigned* bins, unsigned* cnt,
+                                             const RecCodes& c) {
   const int lane = threadIdx.x & 31;
-  __syncwarp();  // lanes that left a divergent loop must run together from here
-  unsigned act = __ballot_sync(kFull, key >= 0);
-  while (act) {
-    const int leader = __ffs(act) - 1;
-    const int k = __shfl_sync(kFull, key, leader);
-    const unsigned peers = __ballot_sync(kFull, key == k);
-    const bool mine = (peers >> lane) & 1u;
-    unsigned r[12];
+  __syncwarp();
+  const int prev = __shfl_up_sync(kFull, cell, 1), next = __shfl_down_sync(kFull, cell, 1);
+  const bool head = lane == 0 || prev != cell, tail = lane == 31 || next != cell;
+  const unsigned heads = __ballot_sync(kFull, head);
+  const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));  // first lane of the run
+  unsigned v[12];
 #pragma unroll
-    for (int q = 0; q < 12; ++q) r[q] = __reduce_max_sync(kFull, mine ? c.v[q] : 0u);
-    if (lane == leader) {
-      const unsigned m = (unsigned)__popc(peers);
-      atomicAdd(e, m);
+  for (int q = 0; q < 12; ++q) v[q] = c.v[q];
 #pragma unroll
-      for (int q = 0; q < 12; ++q) atomicMax(e + 1 + q, r[q]);
-      if (cnt) atomicAdd(cnt, m);
+  for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+    for (int q = 0; q < 12; ++q) {
+      const unsigned u = __shfl_up_sync(kFull, v[q], o);
+      if (lane - o >= start) v[q] = max(v[q], u);
     }
-    act &= ~peers;
+  }
+  if (tail && cell >= 0) {
+    const unsigned m = (unsigned)(lane - start + 1);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      unsigned* b = bins + e[a] * kBinVals;
+      atomicAdd(b, m);
+#pragma unroll
+      for (int q = 0; q < 12; ++q) atomicMax(b + 1 + q, v[q]);
+      if (cnt) atomicAdd(cnt + e[a], m);
+    }
   }
 }
 
@@ -725,11 +738,14 @@ __global__ void __launch_bounds__(kBlock) k_bin_root(BuildArgs A) {
       if (top) {
         const float cc[3] = {cx, cy, cz};
         const RecCodes rc = rec_codes(lo, hi, cx, cy, cz);
+        int e[3], cell = 0;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-          const int e = a * K + bin_of(cc[a], cl[a], scl[a], K);
-          bin_add_warp(valid ? e : -1, sbins + e * kBinVals, scnt + e, rc);
+          const int b = bin_of(cc[a], cl[a], scl[a], K);
+          e[a] = a * K + b;
+          cell = cell * kMaxBins + b;
         }
+        bin_add_runs(valid ? cell : -1, e, sbins, scnt, rc);
       }
     }
     if (top) {
@@ -1044,13 +1060,14 @@ __device__ void top_chunk(const BuildArgs& A, TopSmem& S, const TopTask& T, int 
       const float cx = centre(lo[r].x, hi[r].x), cy = centre(lo[r].y, hi[r].y), cz = centre(lo[r].z, hi[r].z);
       const float cc[3] = {cx, cy, cz};
       const RecCodes rc = rec_codes(lo[r], hi[r], cx, cy, cz);
+      int e[3], cell = s * 2 + (jj & 1);
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const int b = s ? bin_of(cc[a], cmin1[a], scl1[a], K) : bin_of(cc[a], cmin0[a], scl0[a], K);
-        const int e = a * K + b;
-        const int key = act ? ((s * 2 + (jj & 1)) * 3 + a) * kMaxBins + b : -1;
-        bin_add_warp(key, &S.cbins[s][e * kBinVals], &S.ccnt[s][jj & 1][e], rc);
+        e[a] = a * K + b;
+        cell = cell * kMaxBins + b;
       }
+      bin_add_runs(act ? cell : -1, e, &S.cbins[s][0], &S.ccnt[s][jj & 1][0], rc);
     }
     lrun += rtot;
     rrun += min(kBlock, rn - r * kBlock) - rtot;
