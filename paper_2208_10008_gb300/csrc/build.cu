@@ -310,27 +310,19 @@ __device__ __forceinline__ void eval_seg(const unsigned* bins0, int K, int n, in
   }
   const BinB L = RT_BINB_SHFL(__shfl_up_sync, pre, 1);  // lane sl: bins 0 .. sl-1 of its axis
   const BinB C = RT_BINB_SHFL(__shfl_sync, pre, min(g * K + K - 1, 31));
-  float cost = INFINITY;
-  int cand = INT_MAX;
-  if (in && sl >= 1 && L.n > 0 && L.n < n) {
-    const float c = eq2_cost(make_float3(L.l0, L.l1, L.l2), make_float3(L.h0, L.h1, L.h2), L.n,
-                             make_float3(suf.l0, suf.l1, suf.l2), make_float3(suf.h0, suf.h1, suf.h2), n - L.n,
-                             make_float3(C.l0, C.l1, C.l2), make_float3(C.h0, C.h1, C.h2), cp);
-    if (c < INFINITY) {
-      cost = c;
-      cand = a * (K - 1) + sl - 1;
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const float oc = __shfl_xor_sync(kFull, cost, o);
-    const int ok = __shfl_xor_sync(kFull, cand, o);
-    if (oc < cost || (oc == cost && ok < cand)) {
-      cost = oc;
-      cand = ok;
-    }
-  }
-  if (__any_sync(kFull, cand != INT_MAX && (cost < best.cost || (cost == best.cost && cand < best.cand)))) {
+  // Eq. 2 in every lane (a plane without records on both sides costs
+  // infinity), then the lowest cost by two warp reductions: costs are >= +0
+  // (alpha in [0, 1], t_i > 0, t_trav >= 0), so their bit patterns order as
+  // their values, and the lowest candidate among equal costs wins
+  const float c = eq2_cost(make_float3(L.l0, L.l1, L.l2), make_float3(L.h0, L.h1, L.h2), L.n,
+                           make_float3(suf.l0, suf.l1, suf.l2), make_float3(suf.h0, suf.h1, suf.h2), n - L.n,
+                           make_float3(C.l0, C.l1, C.l2), make_float3(C.h0, C.h1, C.h2), cp);
+  const bool ok = in && sl >= 1 && L.n > 0 && L.n < n && c < INFINITY;
+  const unsigned key = ok ? __float_as_uint(c + 0.f) : __float_as_uint(INFINITY);
+  const unsigned kmin = __reduce_min_sync(kFull, key);
+  const int cand = (int)__reduce_min_sync(kFull, ok && key == kmin ? (unsigned)(a * (K - 1) + sl - 1) : 0xffffffffu);
+  const float cost = __uint_as_float(kmin);
+  if (cand >= 0 && (cost < best.cost || (cost == best.cost && cand < best.cand))) {
     const int ax = cand / (K - 1), gw = ax - a0, pl = cand - ax * (K - 1) + 1;  // plane pl of axis ax
     const int w = gw * K + pl;
     const BinB Lb = RT_BINB_SHFL(__shfl_sync, L, w), Rb = RT_BINB_SHFL(__shfl_sync, suf, w);
