@@ -508,13 +508,15 @@ def run_quantised(rtbvh, torch, scene, rays, bp, tile, reps=10):
 
 def run_alpha_sweep(rtbvh, torch, sc, rays, source, reps=10):
     """The paper's comparison on this workload: the traditional SAH tree
-    (alpha = 1, Eq. 1) against the improved trees (alpha < 1, Eq. 2), same
-    rays, same walk: build and trace device times, nodes and triangles per ray."""
+    (alpha = 1, Eq. 1) against the improved trees (alpha < 1, Eq. 2; the
+    scale-free distance term, and at alpha 0.7 also the raw and the
+    count-weighted forms), same rays, same walk: build and trace device
+    times, nodes and triangles per ray."""
     out = []
     scene = rtbvh.rt_scene_upload(sc.tris)
     hits = torch.empty((rays.shape[0], 4), dtype=torch.float32, device="cuda")
     stats = torch.zeros((rays.shape[0], 2), dtype=torch.int32, device="cuda")
-    for alpha, dn in ((1.0, 0), (0.7, 1), (0.4, 1)):
+    for alpha, dn in ((1.0, 0), (0.7, 1), (0.4, 1), (0.7, 0), (0.7, 2)):
         kw = dict(alpha=alpha, dist_norm=dn, source=source, max_leaf=4, bins=16)
         rtbvh.rt_bvh_build(scene, **kw)
         rtbvh.rt_trace_closest(scene, rays, hits)

@@ -64,7 +64,10 @@ typedef struct {
  * (Eq. 2; Eq. 1 when alpha = 1) with S the AABB surface area (Eq. 3 boxes),
  * k the triangle counts and d^2 = (d_A^2 + d_B^2)/2, d_X the distance from
  * the centre of X's AABB to `source`.  dist_norm = 1 replaces d^2 by
- * d^2 / diag(C)^2 * k_C t_i (scale-free); 0 keeps the paper's raw m^2.
+ * d^2 / diag(C)^2 * k_C t_i (scale-free); dist_norm = 2 by
+ * (k_A d_A^2 + k_B d_B^2) / diag(C)^2 * t_i (scale-free, each child's
+ * distance weighted by its triangles, as the SAH term weights its area);
+ * 0 keeps the paper's raw m^2.
  * A node becomes a leaf when it holds at most max_leaf triangles. */
 typedef struct {
   float alpha;      /* [0, 1] */
@@ -74,7 +77,7 @@ typedef struct {
   int32_t max_leaf; /* 1 .. 15 */
   int32_t bins;     /* candidate planes per axis + 1: 4 .. 32 */
   int32_t width;    /* children per traversal node: 4 */
-  int32_t dist_norm;/* 0 or 1 */
+  int32_t dist_norm;/* 0, 1 or 2 */
   float range;      /* ray action range around `source` (Sec. II.B): > 0 builds over only the
                        triangles whose box lies within range of the source (no point of a path of
                        total length <= range is farther away, at any reflection order); 0 (or

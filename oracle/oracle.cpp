@@ -34,7 +34,10 @@
 //    tmax <= tmin miss.
 //  * Eq. 2 distance: d^2 = (d_A^2 + d_B^2) / 2 with d_X the distance from the
 //    centre of AABB X to the source point; optional normalisation
-//    (dist_norm = 1) d^2 / diag(C)^2 * k_C * t_i.
+//    (dist_norm = 1) d^2 / diag(C)^2 * k_C * t_i, or the count-weighted
+//    scale-free form (dist_norm = 2) (k_A d_A^2 + k_B d_B^2) / diag(C)^2 * t_i,
+//    which weights each child's distance by its triangles as the SAH term
+//    weights its area.
 //  * Eq. 3 boxes are closed (min <= x <= max).
 //  * Eq. 4 reception: a segment t in [tmin, tend) of ray (o, d) (tend = the
 //    nearer of its hit and tmax) receives at point p when the foot of the
@@ -215,7 +218,10 @@ double eq2(const Box& A, double kA, const Box& B, double kB, const Box& C, const
     diag2 += dc * dc;
   }
   double d2 = 0.5 * (dA2 + dB2);
-  if (p.dist_norm) d2 = (diag2 > 0.0 ? d2 / diag2 : 0.0) * (kA + kB) * p.t_i;
+  if (p.dist_norm == 2)
+    d2 = (diag2 > 0.0 ? (kA * dA2 + kB * dB2) / diag2 : 0.0) * p.t_i;
+  else if (p.dist_norm)
+    d2 = (diag2 > 0.0 ? d2 / diag2 : 0.0) * (kA + kB) * p.t_i;
   return p.alpha * sah + (1.0 - p.alpha) * d2 + p.t_trav;
 }
 
@@ -652,7 +658,10 @@ double orc_tree_cost(const float* tris, int64_t n_tri, int64_t n_internal, const
       diag2 += dc * dc;
     }
     double d2 = 0.5 * (dA2 + dB2);
-    if (p.dist_norm) d2 = (diag2 > 0.0 ? d2 / diag2 : 0.0) * (kk[0] + kk[1]) * p.t_i;
+    if (p.dist_norm == 2)
+      d2 = (diag2 > 0.0 ? (kk[0] * dA2 + kk[1] * dB2) / diag2 : 0.0) * p.t_i;
+    else if (p.dist_norm)
+      d2 = (diag2 > 0.0 ? d2 / diag2 : 0.0) * (kk[0] + kk[1]) * p.t_i;
     cost[i] = p.alpha * sah + (1.0 - p.alpha) * d2 + p.t_trav;
     count[i] = kk[0] + kk[1];
     box[i] = C;

@@ -118,11 +118,15 @@ __device__ __forceinline__ float eq2_cost(float3 llo, float3 lhi, int nl, float3
                              : (float)(nl + nr) * p.t_i;
   const float ax = 0.5f * (llo.x + lhi.x) - p.sx, ay = 0.5f * (llo.y + lhi.y) - p.sy, az = 0.5f * (llo.z + lhi.z) - p.sz;
   const float bx = 0.5f * (rlo.x + rhi.x) - p.sx, by = 0.5f * (rlo.y + rhi.y) - p.sy, bz = 0.5f * (rlo.z + rhi.z) - p.sz;
-  float d2 = 0.5f * ((ax * ax + ay * ay + az * az) + (bx * bx + by * by + bz * bz));
+  const float da2 = ax * ax + ay * ay + az * az, db2 = bx * bx + by * by + bz * bz;
+  float d2 = 0.5f * (da2 + db2);
   if (p.dist_norm) {
     const float dx = chi.x - clo.x, dy = chi.y - clo.y, dz = chi.z - clo.z;
     const float diag2 = dx * dx + dy * dy + dz * dz;
-    d2 = (diag2 > 0.f ? d2 * __fdividef(1.f, diag2) : 0.f) * (float)(nl + nr) * p.t_i;
+    if (p.dist_norm == 2)  // each child's distance weighted by its triangles
+      d2 = (diag2 > 0.f ? ((float)nl * da2 + (float)nr * db2) * __fdividef(1.f, diag2) : 0.f) * p.t_i;
+    else
+      d2 = (diag2 > 0.f ? d2 * __fdividef(1.f, diag2) : 0.f) * (float)(nl + nr) * p.t_i;
   }
   return p.alpha * sah + (1.f - p.alpha) * d2 + p.t_trav;
 }

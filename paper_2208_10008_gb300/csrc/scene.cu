@@ -220,7 +220,7 @@ int check_params(const rt_build_params* p) {
   if (p->max_leaf < 1 || p->max_leaf > rt::kMaxLeaf) return fail(RT_EINVAL, "max_leaf must be 1..15");
   if (p->bins < 4 || p->bins > rt::kMaxBins) return fail(RT_EINVAL, "bins must be 4..32");
   if (p->width != 4 && p->width != 8) return fail(RT_EINVAL, "width must be 4 or 8");
-  if (p->dist_norm != 0 && p->dist_norm != 1) return fail(RT_EINVAL, "dist_norm must be 0 or 1");
+  if (p->dist_norm < 0 || p->dist_norm > 2) return fail(RT_EINVAL, "dist_norm must be 0, 1 or 2");
   if (!(p->range >= 0.f)) return fail(RT_EINVAL, "range must be >= 0");
   if (p->quantize != 0 && p->quantize != 1) return fail(RT_EINVAL, "quantize must be 0 or 1");
   if (p->quantize && p->width != 4) return fail(RT_EINVAL, "quantised nodes are 4-wide: quantize needs width 4");

@@ -143,10 +143,17 @@ class Checker:
         dA = float(np.linalg.norm(0.5 * (la.astype(np.float64) + ha) - self.src))
         dB = float(np.linalg.norm(0.5 * (lb.astype(np.float64) + hb) - self.src))
         w = 1.0
+        term = 0.5 * (dA * dA + dB * dB)
         if self.dist_norm:
             diag2 = float(((hc - lc).astype(np.float64) ** 2).sum())
-            w = (ka + kb) * self.t_i / diag2 if diag2 > 0 else 0.0
-        term = 0.5 * (dA * dA + dB * dB) * w
+            if self.dist_norm == 2:
+                # (ka dA^2 + kb dB^2) t_i / diag2: a centre error moves it by at most
+                # 2 max(ka, kb) t_i / diag2 (dA + dB) times the error
+                term = (ka * dA * dA + kb * dB * dB) * self.t_i / diag2 if diag2 > 0 else 0.0
+                w = 2.0 * max(ka, kb) * self.t_i / diag2 if diag2 > 0 else 0.0
+            else:
+                w = (ka + kb) * self.t_i / diag2 if diag2 > 0 else 0.0
+                term *= w
         M = max(float(np.abs(np.concatenate([lc, hc])).max()), float(np.abs(self.src).max()))
         return c, cost_tol(abs(sah), abs(term), dA, dB, M, self.alpha, w, self.t_trav)
 

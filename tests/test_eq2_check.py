@@ -59,7 +59,7 @@ def city():
     return sc.tris, (150.0, 150.0, 30.0)
 
 
-@pytest.mark.parametrize("alpha,dist_norm,bins", [(0.7, 1, 16), (0.4, 0, 8), (0.0, 0, 16), (1.0, 0, 32)])
+@pytest.mark.parametrize("alpha,dist_norm,bins", [(0.7, 1, 16), (0.4, 0, 8), (0.0, 0, 16), (1.0, 0, 32), (0.4, 2, 16)])
 def test_rule_tree_passes(orc, city, alpha, dist_norm, bins):
     tris, src = city
     ex = _build(orc, tris, alpha, src, dist_norm, bins, max_leaf=2)

@@ -34,9 +34,9 @@ def medium():
 
 # (alpha, dist_norm, bins, max_leaf): the benchmarked tree first (alpha 0.7,
 # scale-free term, 8 bins, leaf 2), then both distance forms at alpha 0.7 /
-# 0.4 / 0, and the SAH tree
+# 0.4 / 0, the count-weighted form, and the SAH tree
 CASES = [(0.7, 1, 8, 2), (0.7, 0, 16, 4), (0.4, 1, 16, 4), (0.4, 0, 32, 4), (0.0, 1, 16, 1), (0.0, 0, 16, 4),
-         (1.0, 0, 16, 4)]
+         (0.7, 2, 16, 2), (0.0, 2, 8, 4), (1.0, 0, 16, 4)]
 
 
 @pytest.mark.parametrize("alpha,dist_norm,bins,max_leaf", CASES)
@@ -67,7 +67,8 @@ def test_every_split_is_the_eq2_minimum_batched_city(rb, orc):
     assert st["over_1024"] >= 100
 
 
-@pytest.mark.parametrize("alpha,dist_norm", [(1.0, 0), (0.7, 1), (0.7, 0), (0.4, 1), (0.4, 0), (0.0, 0)])
+@pytest.mark.parametrize("alpha,dist_norm", [(1.0, 0), (0.7, 1), (0.7, 0), (0.4, 1), (0.4, 0), (0.0, 0), (0.7, 2),
+                                              (0.0, 2)])
 def test_tree_cost_against_exact_sweep(rb, orc, medium, alpha, dist_norm):
     tris, src = medium
     s = rb.rt_scene_upload(tris)

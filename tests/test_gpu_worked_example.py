@@ -37,6 +37,7 @@ def test_device_root_split_is_the_hand_derived_one(rb):
     tris = np.asarray(g["tris"], np.float32)
     cases = [(0, a, i) for a, i in g["best_split"].items()]
     cases += [(1, a, i) for a, i in g["dist_norm_1"]["best_split"].items()]
+    cases += [(2, a, i) for a, i in g["dist_norm_2"]["best_split"].items()]
     for dist_norm, alpha_s, i_best in cases:
         s = rb.rt_scene_upload(tris)
         rb.rt_bvh_build(s, alpha=float(alpha_s), source=(0.0, 0.0, 0.0), max_leaf=1, dist_norm=dist_norm)

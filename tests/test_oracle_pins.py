@@ -322,6 +322,38 @@ def test_eq2_worked_example_scale_free_split(orc):
     assert _root_left_size(raw.export()) == g["best_split"]["0.5"] == 1
 
 
+def test_eq2_worked_example_count_weighted_costs(orc):
+    """Eq. 2 with the count-weighted scale-free distance term (dist_norm = 2):
+    the hand-derived (k_A d_A^2 + k_B d_B^2) / diag(C)^2 of each candidate, and
+    with equal counts the same value as the scale-free term."""
+    g = json.load(open(os.path.join(GOLDEN, "eq2_worked_example.json")))
+    n2, n1 = g["dist_norm_2"], g["dist_norm_1"]
+    for c in g["candidates"]:
+        i = str(c["i"])
+        assert abs(0.5 * (n2["dA2"][i] + n2["dB2"][i]) - c["d2"]) < 1e-12
+        term = n2["term"][i]
+        assert abs((c["k_A"] * n2["dA2"][i] + c["k_B"] * n2["dB2"][i]) / n1["diag2_C"] - term) < 1e-12
+        for alpha in (1.0, 0.5, 0.2, 0.1, 0.0):
+            got = orc.eq2_cost(c["box_A"], c["k_A"], c["box_B"], c["k_B"], g["box_C"], alpha, (0, 0, 0), dist_norm=2)
+            want = alpha * c["sah"] + (1 - alpha) * term + 1.0
+            assert abs(got - want) < 1e-12
+            if c["k_A"] == c["k_B"]:
+                same = orc.eq2_cost(c["box_A"], c["k_A"], c["box_B"], c["k_B"], g["box_C"], alpha, (0, 0, 0),
+                                    dist_norm=1)
+                assert abs(got - same) < 1e-12
+
+
+def test_eq2_worked_example_count_weighted_split(orc):
+    """The exact sweep with the count-weighted term picks the hand-derived
+    root split on each side of its crossover (alpha = 0.1228...), and the
+    lower of two equal-cost splits (i = 1 against i = 3) at alpha = 0."""
+    g = json.load(open(os.path.join(GOLDEN, "eq2_worked_example.json")))
+    tris = np.asarray(g["tris"], np.float32)
+    for alpha_s, i_best in g["dist_norm_2"]["best_split"].items():
+        b = orc.Bvh(tris, alpha=float(alpha_s), source=(0, 0, 0), max_leaf=1, dist_norm=2)
+        assert _root_left_size(b.export()) == i_best, alpha_s
+
+
 def test_tree_cost_alpha_half_worked_example(orc):
     """The recursive Eq. 2 tree cost at alpha = 0.5 (the recursion the quality
     bound of reading c6 uses) on the worked example, raw and scale-free: the
@@ -451,7 +483,7 @@ def test_bvh_equals_brute_tiny_city(orc, alpha, max_leaf):
     sc, rays, _ = scenes.workload_tiny()
     ref = orc.closest_brute(sc.tris, rays)
     ref_any = orc.any_brute(sc.tris, rays)
-    for dn in (0, 1):
+    for dn in (0, 1, 2):
         b = orc.Bvh(sc.tris, alpha=alpha, source=sc.tx[0], max_leaf=max_leaf, dist_norm=dn)
         _check_structure(orc, sc.tris, b, max_leaf)
         h = b.closest(rays)
