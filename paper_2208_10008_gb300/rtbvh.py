@@ -439,6 +439,7 @@ def rt_trace_closest_host(scene: Scene, rays_host, hits_host=None, flags=0, stre
     tp = TraceParams()
     tp.flags = int(flags)
     tp.block = int(block)
+    tp.stack = int(stack)
     _check(lib().rt_trace_closest_host(scene.handle, rp, n, hp, ctypes.byref(tp), _stream(stream)))
     return hits_host
 

@@ -281,6 +281,21 @@ def test_host_buffer_path_matches_device(rb):
         assert np.array_equal(hh.numpy().view(np.uint32), hd.view(np.uint32))
 
 
+def test_host_buffer_path_many_chunks(rb):
+    # more rays than the pipeline's two staging buffers hold at once (2 x 2^20):
+    # chunks of 2^20 take the buffers in turn; every hit equals the device
+    # path's, bit for bit
+    sc, _, p = scenes.workload_medium(level=1)
+    s, _ = build(rb, sc.tris, alpha=0.7, source=p["source"], dist_norm=1)
+    rays = scenes.random_rays(sc, 4 * (1 << 20) + 12345, seed=91, tmax=300.0)
+    hd = trace(rb, s, rays)
+    pinned = torch.from_numpy(rays).pin_memory()
+    hh = rb.rt_trace_closest_host(s, pinned, stack=32)
+    assert np.array_equal(hh.numpy().view(np.uint32), hd.view(np.uint32))
+    hn = rb.rt_trace_closest_host(s, rays[:777])  # pageable numpy buffers, a short batch
+    assert np.array_equal(hn.view(np.uint32), hd[:777].view(np.uint32))
+
+
 def test_stats_and_no_retest_flag(rb, orc):
     sc, rays, p = scenes.workload_tiny()
     s, _ = build(rb, sc.tris, alpha=1.0)
