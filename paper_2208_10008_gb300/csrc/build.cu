@@ -1654,7 +1654,7 @@ __device__ void mid_split(const BuildArgs& A, MidWarp& W, const Task& t, int epo
 constexpr int kSubMax = 1024;            // records of a subtree built in shared memory
 constexpr int kMicroList = kSubMax / 2;  // nodes of at most 32 records (>= 2 each, disjoint)
 constexpr int kBoxVals = 7;              // a subtree bin: count, box lo (complemented codes), box hi
-constexpr int kCtaBinWords = 3 * kMaxBins * kBoxVals + 2 * kBinVals;  // bins, then the children's unions
+constexpr int kCtaBinWords = 3 * kMaxBins * kBoxVals + 4 * kBinVals;  // bins, then two sets of children's unions
 static_assert(kSubMax <= kBlock * 4, "a CTA partition keeps at most 4 records per thread");
 static_assert(kSubMax <= 1024 && kMicro < 64, "packed small-node fields");
 
@@ -1669,7 +1669,6 @@ struct SubSmem {
   float4 rec[2][2 * kSubMax];
   unsigned bins[kCtaBinWords];
   int2 ml[kMicroList];  // nodes of at most 32: (parent, b | n << 10 | side << 16 | par << 17 | depth << 18)
-  SubNode cur;          // the next node the CTA splits
   Task task;
   int red[kWarps];
   int2 pick;  // the split Eq. 2 chose: candidate, records on the left
@@ -1769,22 +1768,25 @@ __device__ __forceinline__ void leaf_out(const BuildArgs& A, const float4* src, 
 }
 
 
-// Split node X of the subtree with the whole CTA: bins (count and box) in
-// one shared array, each thread binning a run of records (thread (w, l)
-// takes run l * 8 + w, so the lanes of a warp work far apart); Eq. 2
-// evaluated by warp 0, its choice read by all from shared memory (one
-// warp's shuffles instead of eight); stable partition by a block scan,
-// which also gathers both children's unions.  Thread 0 writes
-// the node and routes the children: the larger one of more than 32 records
-// becomes S.cur (S.got), the smaller one of more than 32 goes to the device
-// queue, those of at most 32 to the small-node list.
-__device__ void cta_split(const BuildArgs& A, SubSmem& S, const SubNode& X, int gbegin, int tdepth, int epoch,
+// Split node X of the subtree with the whole CTA (split `it` of the task's
+// chain): bins (count and box) in one shared array, each thread binning a
+// run of records (thread (w, l) takes run l * 8 + w, so the lanes of a warp
+// work far apart); Eq. 2 evaluated by warp 0, its choice read by all from
+// shared memory (one warp's shuffles instead of eight); stable partition by
+// a block scan, which also gathers both children's unions (into one of two
+// sets, alternating with `it`) and clears the bins and the other set for
+// the next split.  Thread 0 writes the node and routes the other children:
+// the smaller one of more than 32 records goes to the device queue, those
+// of at most 32 to the small-node list.  If the larger child has more than
+// 32 records, every thread makes it X (true) and goes on without a barrier.
+__device__ bool cta_split(const BuildArgs& A, SubSmem& S, SubNode& X, int it, int gbegin, int tdepth, int epoch,
                           WarpStats& ws) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int K = A.K, n = X.n, p = X.par;
   const int nbw = 3 * K * kBoxVals;
-  unsigned* cb = S.bins;
-  unsigned* cu = cb + nbw;  // the children's unions, 2 x 13 words
+  unsigned* cb = S.bins;  // zero on entry
+  unsigned* cu = cb + nbw + (it & 1) * 2 * kBinVals;  // the children's unions, 2 x 13 words (zero on entry)
+  unsigned* cu_next = cb + nbw + ((it + 1) & 1) * 2 * kBinVals;
   const float4* src = S.rec[p] + 2 * X.b;
   float4* dst = S.rec[p ^ 1] + 2 * X.b;
   float cmin[3], scl[3];
@@ -1793,11 +1795,9 @@ __device__ void cta_split(const BuildArgs& A, SubSmem& S, const SubNode& X, int 
     cmin[a] = X.clo[a];
     scl[a] = bin_scale(X.clo[a], X.chi[a], K);
   }
-  for (int w = tid; w < nbw + 2 * kBinVals; w += kBlock) cb[w] = 0u;
   // thread t owns records [t c, t c + c), c <= 4, for the partition; runs
   // for the bins use the spread order
   const int c = (n + kBlock - 1) / kBlock;
-  __syncthreads();
   {
     const int r = lane * kWarps + warp, k0 = min(r * c, n), k1 = min(k0 + c, n);
     bin_run(cb, src, k0, k1, K, cmin, scl);
@@ -1861,6 +1861,10 @@ __device__ void cta_split(const BuildArgs& A, SubSmem& S, const SubNode& X, int 
     total += v;
   }
   int lb = before + inc - cnt, rb = k0 - lb;
+  // the bins are done with (Eq. 2 read them before the barriers above):
+  // clear them, and the other unions, for the next split
+  for (int w = tid; w < nbw; w += kBlock) cb[w] = 0u;
+  if (tid < 2 * kBinVals) cu_next[tid] = 0u;
   // the larger child of more than 32 records stays; the other one of more
   // than 32 goes to the device queue, where an idle CTA takes it, so the
   // subtree spreads over the SMs as it branches: its records go straight to
@@ -1911,13 +1915,12 @@ __device__ void cta_split(const BuildArgs& A, SubSmem& S, const SubNode& X, int 
   const bool leafl = nl <= A.max_leaf, leafr = nr <= A.max_leaf;
   if (leafl) leaf_out(A, dst, gbegin + X.b, nl, tid, kBlock);
   if (leafr) leaf_out(A, dst + 2 * nl, gbegin + X.b + nl, nr, tid, kBlock);
+  const int id = gbegin + X.b + nl - 1;
   if (tid == 0) {
     if (total != nl) set_status(A.ctl, kStBadSplit, 6);
-    const int id = gbegin + X.b + nl - 1;
     write_node(A, id, X.parent, X.side, L, leafl ? leaf_ref(gbegin + X.b, nl) : INT_MAX, nl, R,
                leafr ? leaf_ref(gbegin + X.b + nl, nr) : INT_MAX, nr, epoch);
     note_node(ws, nl, nr, leafl, leafr, X.depth);
-    S.got = 0;
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
       const int cn = s ? nr : nl, b = X.b + (s ? nl : 0);
@@ -1931,13 +1934,15 @@ __device__ void cta_split(const BuildArgs& A, SubSmem& S, const SubNode& X, int 
           S.ml[S.nm++] = micro_pack(b, cn, id, s, X.depth + 1 - tdepth, p ^ 1);
         else
           set_status(A.ctl, kStQueueOverflow, 4);
-      } else {
-        S.cur = sub_node(b, cn, id, s, X.depth + 1, p ^ 1, s ? R : L);
-        S.got = 1;
       }
     }
   }
-  __syncthreads();
+  // every thread takes the kept child from the unions it read (no barrier:
+  // thread 0's node write and release fence overlap the next split's
+  // binning, which reads only the kept child's records)
+  if ((keep ? nr : nl) <= kMicro) return false;
+  X = sub_node(X.b + (keep ? nl : 0), keep ? nr : nl, id, keep, X.depth + 1, p ^ 1, keep ? R : L);
+  return true;
 }
 
 // The warps finish the collected nodes of at most 32 records, one node per
@@ -1969,32 +1974,30 @@ __device__ void sub_tree(const BuildArgs& A, SubSmem& S, const Task& t, int epoc
   const int n = t.count;
   const float4* g = A.rec[t.pad & 1] + 2 * (size_t)t.begin;
   for (int k = tid; k < 2 * n; k += kBlock) S.rec[0][k] = __ldcg(g + k);
+  // the first split's bins and unions start at zero
+  for (int w = tid; w < kCtaBinWords; w += kBlock) S.bins[w] = 0u;
   if (tid == 0) {
     S.nm = 0;
     S.mnext = 0;
-    S.got = 0;
-    if (n <= kMicro) {
-      S.ml[S.nm++] = micro_pack(0, n, t.parent, t.side, 0, 0);
-    } else {
-      SubNode& r = S.cur;
-      r.b = 0;
-      r.n = n;
-      r.parent = t.parent;
-      r.side = t.side;
-      r.depth = t.depth;
-      r.par = 0;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        r.clo[a] = t.clo[a];
-        r.chi[a] = t.chi[a];
-      }
-      S.got = 1;
-    }
+    if (n <= kMicro) S.ml[S.nm++] = micro_pack(0, n, t.parent, t.side, 0, 0);
   }
   __syncthreads();
-  while (S.got) {  // the chain of larger children, split by the whole CTA
-    const SubNode X = S.cur;
-    cta_split(A, S, X, t.begin, t.depth, epoch, ws);
+  if (n > kMicro) {  // the chain of larger children, split by the whole CTA
+    SubNode X;
+    X.b = 0;
+    X.n = n;
+    X.parent = t.parent;
+    X.side = t.side;
+    X.depth = t.depth;
+    X.par = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      X.clo[a] = t.clo[a];
+      X.chi[a] = t.chi[a];
+    }
+    for (int it = 0; cta_split(A, S, X, it, t.begin, t.depth, epoch, ws); ++it) {
+    }
+    __syncthreads();  // thread 0's last additions to the small-node list
   }
   micro_phase(A, S, t.begin, t.depth, epoch, ws);
   __syncthreads();
