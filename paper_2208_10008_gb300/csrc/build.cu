@@ -1672,6 +1672,7 @@ struct SubSmem {
   Task task;
   int red[kWarps];
   int2 pick;  // the split Eq. 2 chose: candidate, records on the left
+  float4 pbox[3];  // and the boxes of its children (left lo, hi; right lo, hi)
   int nm, mnext, got;
 };
 static_assert(sizeof(MidWarp) <= sizeof(float4) * 2 * 2 * kSubMax, "a warp's global-memory split state fits");
@@ -1807,7 +1808,13 @@ __device__ bool cta_split(const BuildArgs& A, SubSmem& S, SubNode& X, int it, in
     Split best;
     split_none(best);
     eval_box(cb, K, n, scl, A.cp, best);
-    if (lane == 0) S.pick = make_int2(best.cand, best.L.n);
+    if (lane == 0) {
+      S.pick = make_int2(best.cand, best.L.n);
+      // both children's boxes: the unions of the bins' boxes on each side
+      S.pbox[0] = make_float4(best.L.l0, best.L.l1, best.L.l2, best.L.h0);
+      S.pbox[1] = make_float4(best.L.h1, best.L.h2, best.R.l0, best.R.l1);
+      S.pbox[2] = make_float4(best.R.l2, best.R.h0, best.R.h1, best.R.h2);
+    }
   }
   __syncthreads();
   const int2 pick = S.pick;
@@ -1899,19 +1906,47 @@ __device__ bool cta_split(const BuildArgs& A, SubSmem& S, SubNode& X, int it, in
         acc13_add(ub, rc);
     }
   }
-  acc13_warp(ua);
-  acc13_warp(ub);
-  if (lane == 0) {
-    atomicAdd(cu, ua[0]);
-    atomicAdd(cu + kBinVals, ub[0]);
+  // the children's unions: with a plane, count and box are known (Eq. 2's
+  // scans) and only the centre bounds (words 7..12) are gathered; without
+  // one, all 13 words
+  if (axis >= 0) {
 #pragma unroll
-    for (int q = 1; q < kBinVals; ++q) {
-      atomicMax(cu + q, ua[q]);
-      atomicMax(cu + kBinVals + q, ub[q]);
+    for (int q = 7; q < kBinVals; ++q) {
+      ua[q] = __reduce_max_sync(kFull, ua[q]);
+      ub[q] = __reduce_max_sync(kFull, ub[q]);
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int q = 7; q < kBinVals; ++q) {
+        atomicMax(cu + q, ua[q]);
+        atomicMax(cu + kBinVals + q, ub[q]);
+      }
+    }
+  } else {
+    acc13_warp(ua);
+    acc13_warp(ub);
+    if (lane == 0) {
+      atomicAdd(cu, ua[0]);
+      atomicAdd(cu + kBinVals, ub[0]);
+#pragma unroll
+      for (int q = 1; q < kBinVals; ++q) {
+        atomicMax(cu + q, ua[q]);
+        atomicMax(cu + kBinVals + q, ub[q]);
+      }
     }
   }
   __syncthreads();
-  const BinU L = binu_load(cu), R = binu_load(cu + kBinVals);
+  BinU L, R;
+  if (axis >= 0) {
+    const float4 b0 = S.pbox[0], b1 = S.pbox[1], b2 = S.pbox[2];
+    L = {nl, b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, uval(~cu[7]), uval(~cu[8]), uval(~cu[9]), uval(cu[10]),
+         uval(cu[11]), uval(cu[12])};
+    R = {n - nl, b1.z, b1.w, b2.x, b2.y, b2.z, b2.w, uval(~cu[kBinVals + 7]), uval(~cu[kBinVals + 8]),
+         uval(~cu[kBinVals + 9]), uval(cu[kBinVals + 10]), uval(cu[kBinVals + 11]), uval(cu[kBinVals + 12])};
+  } else {
+    L = binu_load(cu);
+    R = binu_load(cu + kBinVals);
+  }
   const bool leafl = nl <= A.max_leaf, leafr = nr <= A.max_leaf;
   if (leafl) leaf_out(A, dst, gbegin + X.b, nl, tid, kBlock);
   if (leafr) leaf_out(A, dst + 2 * nl, gbegin + X.b + nl, nr, tid, kBlock);
