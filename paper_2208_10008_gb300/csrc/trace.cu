@@ -827,8 +827,12 @@ __device__ void retest_all(const TraceArgs& A, const int tid, const int nthreads
   }
 }
 
+// Launched as a programmatic dependent of the walk: its CTAs are placed as
+// the walk's last CTAs retire and wait here until the walk's results are
+// visible.
 template <bool kAny>
 __global__ void __launch_bounds__(kRetestBlock) k_retest64(TraceArgs A) {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   retest_all<kAny>(A, blockIdx.x * kRetestBlock + threadIdx.x, gridDim.x * kRetestBlock, A.rays, A.hits, A.occl,
                    A.skip);
 }
@@ -1158,10 +1162,17 @@ cudaError_t launch_trace_dev(rt_scene_s* s, const rt_ray* rays, int64_t n, const
       int g = (int)((n + kRetestBlock - 1) / kRetestBlock);
       int gmax = sm_count_t() * 4;
       g = g < gmax ? g : gmax;
-      if (occl)
-        k_retest64<true><<<g, kRetestBlock, 0, st>>>(A);
-      else
-        k_retest64<false><<<g, kRetestBlock, 0, st>>>(A);
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)g);
+      cfg.blockDim = dim3(kRetestBlock);
+      cfg.stream = st;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      at[0].val.programmaticStreamSerializationAllowed = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      if ((e = occl ? cudaLaunchKernelEx(&cfg, k_retest64<true>, A) : cudaLaunchKernelEx(&cfg, k_retest64<false>, A)))
+        return e;
       ++n_launched;
     }
   }
