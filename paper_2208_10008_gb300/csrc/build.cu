@@ -77,6 +77,11 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
 __device__ __forceinline__ void st_release(int* p, int v) {
   asm volatile("st.release.gpu.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+__device__ __forceinline__ int atom_add_acq_rel(int* p, int v) {
+  int old;
+  asm volatile("atom.acq_rel.gpu.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
 __device__ __forceinline__ void red_release_add(int* p, int v) {
   asm volatile("red.release.gpu.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -1094,12 +1099,12 @@ __device__ void top_chunk(const BuildArgs& A, TopSmem& S, const TopTask& T, int 
       }
     }
   }
-  // the last chunk of the node to finish writes it and creates its children
+  // the last chunk of the node to finish writes it and creates its children:
+  // the count is an acquire-release add (this CTA's writes, ordered before
+  // thread 0 by the barrier, are released with it; the last chunk's thread 0
+  // acquires every other chunk's, among them chunk 0's plan)
   __syncthreads();
-  if (tid == 0) {
-    __threadfence();
-    S.last = atomicAdd(&A.tdone[slot], 1) == T.nchunk - 1;
-  }
+  if (tid == 0) S.last = atom_add_acq_rel(&A.tdone[slot], 1) == T.nchunk - 1;
   __syncthreads();
   if (S.last) top_emit(A, S, T, slot, epoch, nl, nr, cu0, cu1, top0, top1, nch0, nch1, cfirst0, cfirst1, ts);
 }
@@ -1112,7 +1117,6 @@ __device__ void top_emit(const BuildArgs& A, TopSmem& S, const TopTask& T, int s
                          int cfirst1, WarpStats& ts) {
   const int tid = threadIdx.x;
   const int par = T.parity & 1;
-  __threadfence();
   if (tid == 0) {
     const int id = T.begin + nl - 1;
     const int refl = nl <= A.max_leaf ? leaf_ref(T.begin, nl) : INT_MAX;
