@@ -799,6 +799,8 @@ struct TopSmem {
   int last;
   int created[2], ibase[2];
   int4 plan[2];
+  Task ptask[2];  // subtree-sized children the emit hands to the subtree queue
+  int np;
 };
 
 __device__ __forceinline__ int block_sum(int v, int* red) {
@@ -1118,6 +1120,7 @@ __device__ void top_emit(const BuildArgs& A, TopSmem& S, const TopTask& T, int s
   const int tid = threadIdx.x;
   const int par = T.parity & 1;
   if (tid == 0) {
+    S.np = 0;
     const int id = T.begin + nl - 1;
     const int refl = nl <= A.max_leaf ? leaf_ref(T.begin, nl) : INT_MAX;
     const int refr = nr <= A.max_leaf ? leaf_ref(T.begin + nl, nr) : INT_MAX;
@@ -1128,7 +1131,7 @@ __device__ void top_emit(const BuildArgs& A, TopSmem& S, const TopTask& T, int s
       const BinU& cu = s ? cu1 : cu0;
       S.created[s] = 0;
       if (cn <= A.max_leaf) {
-        if (par == 0) push_task(A, make_task(cb, cn, id, s, T.depth + 1, cu, 1), epoch);  // copy to buffer 0
+        if (par == 0) S.ptask[S.np++] = make_task(cb, cn, id, s, T.depth + 1, cu, 1);  // copy to buffer 0
         continue;
       }
       if (s ? top1 : top0) {
@@ -1157,14 +1160,18 @@ __device__ void top_emit(const BuildArgs& A, TopSmem& S, const TopTask& T, int s
           continue;
         }
       }
-      push_task(A, make_task(cb, cn, id, s, T.depth + 1, cu, par ^ 1), epoch);  // pools full: a warp takes it
+      S.ptask[S.np++] = make_task(cb, cn, id, s, T.depth + 1, cu, par ^ 1);  // pools full: a warp takes it
     }
     if (S.created[0] || S.created[1])
       atomicAdd(&A.ctl->ti_pending, (S.created[0] ? nch0 : 0) + (S.created[1] ? nch1 : 0));
   }
   __syncthreads();
   // publish the children's chunk items: each release store also publishes
-  // what every thread wrote before the barrier (the tasks, the pending count)
+  // what every thread wrote before the barrier (the tasks, the pending
+  // count); meanwhile a thread of warp 1 hands the subtree-sized children to
+  // the subtree queue (one reservation, release stores), so that neither
+  // publication waits for the other's fence
+  if (tid == 32 && S.np > 0) push_tasks(A, S.ptask, S.np, epoch);
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
     if (!S.created[s]) continue;
