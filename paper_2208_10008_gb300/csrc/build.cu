@@ -2501,17 +2501,6 @@ cudaError_t launch_build(rt_scene_s* s, const rt_build_params& p, cudaStream_t s
   A.cap_t = s->geom.cap_t;
   A.cap_c = s->geom.cap_c;
   A.qa_cap = s->geom.qa_cap;
-  A.top_ctas = n > g.big ? nsm : 0;
-  const DebugHooks dh = debug_hooks();
-  A.spin_limit = dh.spin_limit > 0 ? dh.spin_limit : kSpinLimit;
-  A.phantom_tasks = dh.phantom_tasks;
-  A.phantom_items = dh.phantom_items;
-  if (A.phantom_items && !A.top_ctas) A.top_ctas = nsm;  // someone must wait for the phantom items
-  A.cp = CostP{p.alpha, p.t_i, p.t_trav, p.source[0], p.source[1], p.source[2], p.dist_norm};
-  if ((e = cudaMemsetAsync(s->ctl, 0, sizeof(BuildCtl), st))) return e;
-  const int nch = (n + g.chunk - 1) / g.chunk;
-  int gp = (n + kBlock - 1) / kBlock;
-  gp = std::max(1, std::min(gp, nsm * 8));
   static bool attr = false;
   static int split_per_sm = 2;  // resident split CTAs per SM (at most 2)
   if (!attr) {
@@ -2522,6 +2511,22 @@ cudaError_t launch_build(rt_scene_s* s, const rt_build_params& p, cudaStream_t s
     split_per_sm = std::max(1, std::min(2, occ));
     attr = true;
   }
+  // the big-node chunks go to the first nsm CTAs, which then join the rest on
+  // the subtree queue, so that subtrees proceed while other branches' big
+  // nodes are split; when a depth has many more chunks than SMs (large
+  // scenes) every CTA takes chunks first
+  const int64_t nchunks = (n + g.chunk - 1) / g.chunk;
+  A.top_ctas = n > g.big ? (nchunks > 8 * (int64_t)nsm ? split_per_sm * nsm : nsm) : 0;
+  const DebugHooks dh = debug_hooks();
+  A.spin_limit = dh.spin_limit > 0 ? dh.spin_limit : kSpinLimit;
+  A.phantom_tasks = dh.phantom_tasks;
+  A.phantom_items = dh.phantom_items;
+  if (A.phantom_items && !A.top_ctas) A.top_ctas = nsm;  // someone must wait for the phantom items
+  A.cp = CostP{p.alpha, p.t_i, p.t_trav, p.source[0], p.source[1], p.source[2], p.dist_norm};
+  if ((e = cudaMemsetAsync(s->ctl, 0, sizeof(BuildCtl), st))) return e;
+  const int nch = (n + g.chunk - 1) / g.chunk;
+  int gp = (n + kBlock - 1) / kBlock;
+  gp = std::max(1, std::min(gp, nsm * 8));
   if ((e = launch(k_prep, gp, 0, st, false, A))) return e;
   if ((e = launch(k_bin_root, std::max(1, std::min(nch, nsm * 4)), 0, st, true, A))) return e;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
