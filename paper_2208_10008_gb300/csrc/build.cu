@@ -55,6 +55,7 @@ constexpr int kBinWords = 3 * kMaxBins * kBinVals;
 constexpr int kCntStride = 3 * kMaxBins;
 constexpr int kMaxRpt = 4;     // records per thread of a big node's chunk
 constexpr int kBigMin = 1024;  // big nodes have more triangles than this
+constexpr int kStageW = 256;   // records the global-memory warp split (oversized tasks) stages
 constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
@@ -158,6 +159,19 @@ __device__ __forceinline__ BinU binu_join(const BinU& x, const BinU& y) {
           fminf(x.a0, y.a0), fminf(x.a1, y.a1), fminf(x.a2, y.a2),
           fmaxf(x.b0, y.b0), fmaxf(x.b1, y.b1), fmaxf(x.b2, y.b2)};
 }
+__device__ __forceinline__ BinU binu_record(float4 lo, float4 hi) {
+  const float cx = centre(lo.x, hi.x), cy = centre(lo.y, hi.y), cz = centre(lo.z, hi.z);
+  return {1, lo.x, lo.y, lo.z, hi.x, hi.y, hi.z, cx, cy, cz, cx, cy, cz};
+}
+#define RT_BINU_SHFL(F, x, arg)                                                                               \
+  BinU {                                                                                                      \
+    F(kFull, (x).n, arg), F(kFull, (x).l0, arg), F(kFull, (x).l1, arg), F(kFull, (x).l2, arg),                \
+        F(kFull, (x).h0, arg), F(kFull, (x).h1, arg), F(kFull, (x).h2, arg), F(kFull, (x).a0, arg),           \
+        F(kFull, (x).a1, arg), F(kFull, (x).a2, arg), F(kFull, (x).b0, arg), F(kFull, (x).b1, arg),           \
+        F(kFull, (x).b2, arg)                                                                                 \
+  }
+__device__ __forceinline__ BinU binu_xor(const BinU& x, int o) { return RT_BINU_SHFL(__shfl_xor_sync, x, o); }
+#undef RT_BINU_SHFL
 
 // Decode a 13-word bin entry.
 __device__ __forceinline__ BinU binu_load(const unsigned* e) {
@@ -229,6 +243,13 @@ __device__ __forceinline__ void bin_add_runs(int cell, const int* e, unsigned* b
   }
 }
 
+// Add one record to bin entry `e` with plain shared-memory atomics (callers
+// spread the lanes over distant records, so lanes rarely share an entry).
+__device__ __forceinline__ void bin_add_plain(unsigned* e, const RecCodes& c) {
+  atomicAdd(e, 1u);
+#pragma unroll
+  for (int q = 0; q < 12; ++q) atomicMax(e + 1 + q, c.v[q]);
+}
 
 // ------------------------------------------------------------------ Eq. 2 evaluation
 struct Split {
@@ -1384,7 +1405,28 @@ __device__ void micro_sort_build(const BuildArgs& A, float4 lo, float4 hi, int g
   if (__any_sync(kFull, n > A.max_leaf)) micro_build(A, slo, shi, n, gbegin, parent, side, depth, epoch, ws);
 }
 
+// micro_sort_build of a node whose records sit in global buffer `parity`.
+__device__ void micro_task(const BuildArgs& A, int begin, int n, int parity, int parent, int side, int depth,
+                           int epoch, WarpStats& ws) {
+  const int lane = threadIdx.x & 31;
+  float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
+  if (lane < n) {
+    const float4* p = A.rec[parity] + 2 * ((size_t)begin + lane);
+    lo = __ldcg(p);
+    hi = __ldcg(p + 1);
+  }
+  micro_sort_build(A, lo, hi, begin, n, parent, side, depth, epoch, ws);
+}
+
 // ------------------------------------------------------------------ subtree queue
+// Claiming subtree tasks, and the split of tasks too large for a CTA's
+// shared memory (more than kSubMax records: a big node whose pools were
+// full, or any task when big = T / 4096 > 1024), done in global memory by
+// one warp until the part it keeps fits.
+struct MidWarp {
+  unsigned bins[kBinWords];
+  float4 stage[2 * kStageW];
+};
 // One thread takes the next queue slot and waits for it to be filled (the
 // other threads of the CTA wait at a barrier; nothing warp-synchronous runs
 // in this loop).  Returns false when the queue is drained (no big node and
@@ -1429,6 +1471,188 @@ __device__ bool claim_task(const BuildArgs& A, int epoch, Task& t) {
   }
 }
 
+// Split one node of more than 32 triangles with one warp (bin, Eq. 2, stable
+// partition), write it, and route its children: the larger internal child
+// becomes *cont, the other is queued, small ones are finished here.
+__device__ void mid_split(const BuildArgs& A, MidWarp& W, const Task& t, int epoch, WarpStats& ws, Task& cont,
+                          bool& have_cont) {
+  const int lane = threadIdx.x & 31;
+  const int K = A.K, K3 = 3 * K, n = t.count, par = t.pad & 1;
+  const float4* src = A.rec[par] + 2 * (size_t)t.begin;
+  float4* dst = A.rec[par ^ 1] + 2 * (size_t)t.begin;
+  const bool staged = n <= kStageW;
+  float cmin[3], scl[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    cmin[a] = t.clo[a];
+    scl[a] = bin_scale(t.clo[a], t.chi[a], K);
+  }
+  for (int w = lane; w < K3 * kBinVals; w += 32) W.bins[w] = 0u;
+  if (staged) {  // two records per lane in flight
+    for (int k0 = lane; k0 < n; k0 += 64) {
+      float4 v[4];
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+        if (k0 + 32 * u < n) {
+          v[2 * u] = __ldcg(src + 2 * (k0 + 32 * u));
+          v[2 * u + 1] = __ldcg(src + 2 * (k0 + 32 * u) + 1);
+        }
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+        if (k0 + 32 * u < n) {
+          W.stage[2 * (k0 + 32 * u)] = v[2 * u];
+          W.stage[2 * (k0 + 32 * u) + 1] = v[2 * u + 1];
+        }
+    }
+  }
+  __syncwarp();
+  // lane l bins records l*c .. l*c + c - 1: lanes work on distant records,
+  // which seldom share a bin, so plain atomics rarely collide
+  {
+    const int c = (n + 31) / 32;
+    for (int i = 0; i < c; ++i) {
+      const int k = lane * c + i;
+      if (k < n) {
+        const float4 lo = staged ? W.stage[2 * k] : __ldcg(src + 2 * k);
+        const float4 hi = staged ? W.stage[2 * k + 1] : __ldcg(src + 2 * k + 1);
+        const float cx = centre(lo.x, hi.x), cy = centre(lo.y, hi.y), cz = centre(lo.z, hi.z);
+        const RecCodes rc = rec_codes(lo, hi, cx, cy, cz);
+        bin_add_plain(W.bins + (0 * K + bin_of(cx, cmin[0], scl[0], K)) * kBinVals, rc);
+        bin_add_plain(W.bins + (1 * K + bin_of(cy, cmin[1], scl[1], K)) * kBinVals, rc);
+        bin_add_plain(W.bins + (2 * K + bin_of(cz, cmin[2], scl[2], K)) * kBinVals, rc);
+      }
+    }
+  }
+  __syncwarp();
+  Split best;
+  split_none(best);
+  if (3 * K <= 32) {  // all three axes in one pass
+    eval_axes(W.bins, K, n, 0, 3, A.cp, best);
+  } else if (2 * K <= 32) {  // x and y in one pass, then z
+    eval_axes(W.bins, K, n, 0, 2, A.cp, best);
+    if (__any_sync(kFull, scl[2] > 0.f)) eval_axis(W.bins, K, n, 2, A.cp, best);
+  } else {
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if (__any_sync(kFull, scl[a] > 0.f)) eval_axis(W.bins, K, n, a, A.cp, best);
+  }
+  int axis, plane, nl;
+  if (best.cand != INT_MAX) {
+    axis = best.cand / (K - 1);
+    plane = 1 + best.cand % (K - 1);
+    nl = best.L.n;
+  } else {
+    axis = -1;
+    plane = 0;
+    nl = n / 2;
+  }
+  const float acmin = sel3(cmin[0], cmin[1], cmin[2], axis < 0 ? 0 : axis);
+  const float ascl = sel3(scl[0], scl[1], scl[2], axis < 0 ? 0 : axis);
+  // stable partition into the other buffer (child bounds by reduction when
+  // no plane was usable)
+  int lrun = 0, rrun = 0;
+  BinU accL = binu_empty(), accR = binu_empty();
+  for (int g = 0; __any_sync(kFull, g < n); g += 32) {
+    const int k = g + lane;
+    const bool valid = k < n;
+    float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
+    if (valid) {
+      if (staged) {
+        lo = W.stage[2 * k];
+        hi = W.stage[2 * k + 1];
+      } else {
+        lo = __ldcg(src + 2 * k);
+        hi = __ldcg(src + 2 * k + 1);
+      }
+    }
+    bool left = false;
+    if (valid) {
+      if (axis >= 0) {
+        const float cc = axis == 0 ? centre(lo.x, hi.x) : (axis == 1 ? centre(lo.y, hi.y) : centre(lo.z, hi.z));
+        left = bin_of(cc, acmin, ascl, K) < plane;
+      } else {
+        left = k < nl;
+      }
+    }
+    __syncwarp();
+    const unsigned bal = __ballot_sync(kFull, left);
+    const int rank = __popc(bal & ((1u << lane) - 1u));
+    const int dest = left ? lrun + rank : nl + rrun + (lane - rank);
+    if (valid && dest < n) {
+      dst[2 * dest] = lo;
+      dst[2 * dest + 1] = hi;
+      if (axis < 0) {
+        if (left)
+          accL = binu_join(accL, binu_record(lo, hi));
+        else
+          accR = binu_join(accR, binu_record(lo, hi));
+      }
+    }
+    const int tot = __popc(bal);
+    lrun += tot;
+    rrun += min(32, n - g) - tot;
+  }
+  BinU L = best.L, R = best.R;
+  if (__any_sync(kFull, axis < 0)) {
+    __syncwarp();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      accL = binu_join(accL, binu_xor(accL, o));
+      accR = binu_join(accR, binu_xor(accR, o));
+    }
+    L = accL;
+    R = accR;
+  }
+  if (lane == 0 && lrun != nl) set_status(A.ctl, kStBadSplit, 2);
+  __syncwarp();
+  const int nr = n - nl;
+  // leaves keep their records in buffer 0
+  if (par == 0) {
+    if (nl <= A.max_leaf)
+      for (int k = lane; k < 2 * nl; k += 32) A.rec[0][2 * (size_t)t.begin + k] = __ldcg(dst + k);
+    if (nr <= A.max_leaf)
+      for (int k = lane; k < 2 * nr; k += 32) A.rec[0][2 * ((size_t)t.begin + nl) + k] = __ldcg(dst + 2 * nl + k);
+  }
+  const int id = t.begin + nl - 1;
+  const int refl = nl <= A.max_leaf ? leaf_ref(t.begin, nl) : INT_MAX;
+  const int refr = nr <= A.max_leaf ? leaf_ref(t.begin + nl, nr) : INT_MAX;
+  if (lane == 0) write_node(A, id, t.parent, t.side, L, refl, nl, R, refr, nr, epoch);
+  ++ws.n_int;
+  const int leaves = (refl != INT_MAX) + (refr != INT_MAX);
+  ws.n_leaf += leaves;
+  if (refl != INT_MAX) ws.big = max(ws.big, nl);
+  if (refr != INT_MAX) ws.big = max(ws.big, nr);
+  ws.deep = max(ws.deep, leaves ? t.depth + 1 : t.depth);
+  // children: the larger one of more than 32 stays with this warp
+  L.n = nl;
+  R.n = nr;
+  const bool bigl = nl > kMicro, bigr = nr > kMicro;
+  const int keep = (bigl && bigr) ? (nl >= nr ? 0 : 1) : (bigl ? 0 : (bigr ? 1 : -1));
+  if (keep >= 0) {
+    cont = keep == 0 ? make_task(t.begin, nl, id, 0, t.depth + 1, L, par ^ 1)
+                     : make_task(t.begin + nl, nr, id, 1, t.depth + 1, R, par ^ 1);
+    have_cont = true;
+  }
+  if (lane == 0) {
+    Task out[3];
+    int k = 0;
+    if (bigl && bigr)  // the other big child
+      out[k++] = keep == 0 ? make_task(t.begin + nl, nr, id, 1, t.depth + 1, R, par ^ 1)
+                           : make_task(t.begin, nl, id, 0, t.depth + 1, L, par ^ 1);
+    // small subtrees go to idle warps while this one goes on down the tree
+    if (keep >= 0) {
+      if (nl > A.max_leaf && !bigl) out[k++] = make_task(t.begin, nl, id, 0, t.depth + 1, L, par ^ 1);
+      if (nr > A.max_leaf && !bigr) out[k++] = make_task(t.begin + nl, nr, id, 1, t.depth + 1, R, par ^ 1);
+    }
+    push_tasks(A, out, k, epoch);
+  }
+  __syncwarp();
+  if (keep < 0) {
+    if (nl > A.max_leaf) micro_task(A, t.begin, nl, par ^ 1, id, 0, t.depth + 1, epoch, ws);
+    if (nr > A.max_leaf) micro_task(A, t.begin + nl, nr, par ^ 1, id, 1, t.depth + 1, epoch, ws);
+  }
+}
+
 // ------------------------------------------------------------------ subtrees in shared memory
 // A CTA takes a task of at most kSubMax records, loads its records into
 // shared memory once and builds the subtree there.  Every node of more than
@@ -1462,6 +1686,7 @@ struct SubSmem {
   float4 pbox[3];  // and the boxes of its children (left lo, hi; right lo, hi)
   int nm, mnext, got;
 };
+static_assert(sizeof(MidWarp) <= sizeof(float4) * 2 * 2 * kSubMax, "a warp's global-memory split state fits");
 
 __device__ __forceinline__ SubNode sub_node(int b, int n, int parent, int side, int depth, int par, const BinU& u) {
   SubNode x;
@@ -1495,13 +1720,12 @@ __device__ __forceinline__ void flush_box(unsigned* e, const unsigned* acc) {
 #pragma unroll
   for (int q = 1; q < kBoxVals; ++q) atomicMax(e + q, acc[q]);
 }
-template <bool kGlobal = false>  // records in global memory (L2 loads)
 __device__ __forceinline__ void bin_run(unsigned* bins, const float4* src, int k0, int k1, int K, const float* cmin,
                                         const float* scl) {
   int key[3] = {-1, -1, -1};
   unsigned acc[3][kBoxVals];
   for (int k = k0; k < k1; ++k) {
-    const float4 lo = kGlobal ? __ldcg(src + 2 * k) : src[2 * k], hi = kGlobal ? __ldcg(src + 2 * k + 1) : src[2 * k + 1];
+    const float4 lo = src[2 * k], hi = src[2 * k + 1];
     const unsigned c6[6] = {~ucode(lo.x), ~ucode(lo.y), ~ucode(lo.z), ucode(hi.x), ucode(hi.y), ucode(hi.z)};
     const float cc[3] = {centre(lo.x, hi.x), centre(lo.y, hi.y), centre(lo.z, hi.z)};
 #pragma unroll
@@ -1789,138 +2013,6 @@ __device__ void micro_phase(const BuildArgs& A, SubSmem& S, int gbegin, int tdep
   }
 }
 
-// Split task t of more than kSubMax records (a big node whose pools were
-// full, or any task when big = T / 4096 > kSubMax) in global memory with the
-// whole CTA: bins as in cta_split (each thread a run of records, read from
-// L2), Eq. 2 by warp 0, then a stable partition into the other buffer in
-// rounds of kBlock records (a block scan per round) that gathers both
-// children's unions.  Thread 0 writes the node; leaves go to buffer 0; the
-// smaller child goes to the queue.  The larger child becomes t (true) for
-// another split here, or for sub_tree once it fits shared memory.
-__device__ bool gsplit(const BuildArgs& A, SubSmem& S, Task& t, int epoch, WarpStats& ws) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int K = A.K, n = t.count, par = t.pad & 1;
-  const int nbw = 3 * K * kBoxVals;
-  unsigned* cb = S.bins;
-  unsigned* cu = cb + nbw;  // the children's unions, 2 x 13 words
-  const float4* src = A.rec[par] + 2 * (size_t)t.begin;
-  float4* dst = A.rec[par ^ 1] + 2 * (size_t)t.begin;
-  float cmin[3], scl[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    cmin[a] = t.clo[a];
-    scl[a] = bin_scale(t.clo[a], t.chi[a], K);
-  }
-  for (int w = tid; w < nbw + 2 * kBinVals; w += kBlock) cb[w] = 0u;
-  __syncthreads();
-  {
-    const int c = (n + kBlock - 1) / kBlock;
-    const int r = lane * kWarps + warp, k0 = min(r * c, n), k1 = min(k0 + c, n);
-    bin_run<true>(cb, src, k0, k1, K, cmin, scl);
-  }
-  __syncthreads();
-  if (warp == 0) {
-    Split best;
-    split_none(best);
-    eval_box(cb, K, n, scl, A.cp, best);
-    if (lane == 0) S.pick = make_int2(best.cand, best.L.n);
-  }
-  __syncthreads();
-  const int2 pick = S.pick;
-  int axis, plane, nl;
-  if (pick.x != INT_MAX) {
-    axis = pick.x / (K - 1);
-    plane = 1 + pick.x % (K - 1);
-    nl = pick.y;
-  } else {
-    axis = -1;
-    plane = 0;
-    nl = n / 2;
-  }
-  const float acmin = sel3(cmin[0], cmin[1], cmin[2], axis < 0 ? 0 : axis);
-  const float ascl = sel3(scl[0], scl[1], scl[2], axis < 0 ? 0 : axis);
-  const unsigned lt_mask = (1u << lane) - 1u;
-  unsigned ua[kBinVals], ub[kBinVals];
-#pragma unroll
-  for (int q = 0; q < kBinVals; ++q) ua[q] = ub[q] = 0u;
-  int lrun = 0, rrun = 0;
-  for (int r0 = 0; r0 < n; r0 += kBlock) {
-    const int k = r0 + tid;
-    const bool valid = k < n;
-    float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
-    if (valid) {
-      lo = __ldcg(src + 2 * k);
-      hi = __ldcg(src + 2 * k + 1);
-    }
-    const float cx = centre(lo.x, hi.x), cy = centre(lo.y, hi.y), cz = centre(lo.z, hi.z);
-    bool left = false;
-    if (valid) left = axis >= 0 ? bin_of(axis == 0 ? cx : (axis == 1 ? cy : cz), acmin, ascl, K) < plane : k < nl;
-    const unsigned bal = __ballot_sync(kFull, left);
-    if (lane == 0) S.red[warp] = __popc(bal);
-    __syncthreads();
-    int woff = 0, rtot = 0;
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) {
-      const int v = S.red[w];
-      woff += w < warp ? v : 0;
-      rtot += v;
-    }
-    if (valid) {
-      const int lbefore = woff + __popc(bal & lt_mask);
-      const int d = left ? lrun + lbefore : nl + rrun + (tid - lbefore);
-      if (d < n) {
-        __stcg(dst + 2 * d, lo);
-        __stcg(dst + 2 * d + 1, hi);
-      }
-      const RecCodes rc = rec_codes(lo, hi, cx, cy, cz);
-      if (left)
-        acc13_add(ua, rc);
-      else
-        acc13_add(ub, rc);
-    }
-    lrun += rtot;
-    rrun += min(kBlock, n - r0) - rtot;
-    __syncthreads();  // S.red is written again next round
-  }
-  acc13_warp(ua);
-  acc13_warp(ub);
-  if (lane == 0) {
-    atomicAdd(cu, ua[0]);
-    atomicAdd(cu + kBinVals, ub[0]);
-#pragma unroll
-    for (int q = 1; q < kBinVals; ++q) {
-      atomicMax(cu + q, ua[q]);
-      atomicMax(cu + kBinVals + q, ub[q]);
-    }
-  }
-  __syncthreads();
-  const BinU L = binu_load(cu), R = binu_load(cu + kBinVals);
-  const int nr = n - nl;
-  const bool leafl = nl <= A.max_leaf, leafr = nr <= A.max_leaf;
-  // leaves keep their records in buffer 0
-  if (par == 0) {
-    if (leafl)
-      for (int k = tid; k < 2 * nl; k += kBlock) A.rec[0][2 * (size_t)t.begin + k] = __ldcg(dst + k);
-    if (leafr)
-      for (int k = tid; k < 2 * nr; k += kBlock) A.rec[0][2 * ((size_t)t.begin + nl) + k] = __ldcg(dst + 2 * nl + k);
-  }
-  const int keep = nl >= nr ? 0 : 1;
-  const int id = t.begin + nl - 1;
-  if (tid == 0) {
-    if (lrun != nl) set_status(A.ctl, kStBadSplit, 7);
-    write_node(A, id, t.parent, t.side, L, leafl ? leaf_ref(t.begin, nl) : INT_MAX, nl, R,
-               leafr ? leaf_ref(t.begin + nl, nr) : INT_MAX, nr, epoch);
-    note_node(ws, nl, nr, leafl, leafr, t.depth);
-    const int s = 1 - keep, cn = s ? nr : nl;
-    // the records written by every thread above are ordered before this
-    // thread by the barriers; push_task's release store publishes them
-    if (cn > A.max_leaf) push_task(A, make_task(t.begin + (s ? nl : 0), cn, id, s, t.depth + 1, s ? R : L, par ^ 1), epoch);
-  }
-  t = make_task(t.begin + (keep ? nl : 0), keep ? nr : nl, id, keep, t.depth + 1, keep ? R : L, par ^ 1);
-  __syncthreads();  // the bins and unions are cleared again by the next split
-  return true;
-}
-
 // Build the subtree of task t (max_leaf < t.count <= kSubMax) in shared
 // memory with the whole CTA.
 __device__ void sub_tree(const BuildArgs& A, SubSmem& S, const Task& t, int epoch, WarpStats& ws) {
@@ -1959,10 +2051,10 @@ __device__ void sub_tree(const BuildArgs& A, SubSmem& S, const Task& t, int epoc
 
 // The subtree role of every CTA: take a task from the queue, build its
 // subtree (tasks of more than kSubMax records are first split in global
-// memory by the whole CTA, down to a part that fits), repeat until the queue
-// is drained.
+// memory by one warp, down to a part that fits), repeat until the queue is
+// drained.
 __device__ void sub_loop(const BuildArgs& A, SubSmem& S, int epoch) {
-  const int tid = threadIdx.x, lane = tid & 31;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   WarpStats ws{0, 0, 0, 0};
   for (;;) {
     if (tid == 0) S.got = claim_task(A, epoch, S.task);
@@ -1980,9 +2072,29 @@ __device__ void sub_loop(const BuildArgs& A, SubSmem& S, int epoch) {
         for (int k = tid; k < 2 * t.count; k += kBlock)
           A.rec[0][2 * (size_t)t.begin + k] = __ldcg(A.rec[1] + 2 * (size_t)t.begin + k);
     } else {
-      // split in global memory by the whole CTA until the kept part fits
-      while (t.count > kSubMax) gsplit(A, S, t, epoch, ws);
-      sub_tree(A, S, t, epoch, ws);
+      if (t.count > kSubMax) {
+        if (warp == 0) {
+          MidWarp& W = *reinterpret_cast<MidWarp*>(&S.rec[0][0]);
+          Task cur = t;
+          bool more = true;
+          while (more && cur.count > kSubMax) {
+            Task nx;
+            more = false;
+            mid_split(A, W, cur, epoch, ws, nx, more);
+            if (more) cur = nx;
+          }
+          if (lane == 0) {
+            S.got = more;
+            S.task = cur;
+          }
+        }
+        __syncthreads();
+        t = S.task;
+        const bool more = S.got;
+        __syncthreads();
+        if (!more) t.count = 0;
+      }
+      if (t.count > 0) sub_tree(A, S, t, epoch, ws);
     }
     __syncthreads();
     // the pushes of this task counted first, so this never reads zero early
