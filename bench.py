@@ -623,7 +623,7 @@ NCU_TRAFFIC_LARGE = {
     1.0: (294.764544e6 + 144.213248e6, "ncu capture of k_trace<0,0,128,64,0,4> on the 4 x 2^21 metro rays, "
                                        "alpha 1 tree (profiles/k_trace_metro.md)")}
 NCU_TRAFFIC = {
-    "k_split": (1.739776e6 + 1536.0, "ncu capture of k_split in the timed steps, medium city, autotuned tree "
+    "k_split": (1.738752e6 + 768.0, "ncu capture of k_split in the timed steps, medium city, autotuned tree "
                                     "(profiles/k_split_medium_city.md)"),
     "k_trace": (21.495808e6 + 47872.0, "ncu capture of k_trace<0,0,128,64,0,4> in the timed steps, medium "
                                        "city (k_retest64 not included; profiles/k_trace_medium_city.md)"),
