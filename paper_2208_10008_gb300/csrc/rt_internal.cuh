@@ -328,6 +328,7 @@ struct rt_scene_s {
   rt_hit* stage_hits[2] = {nullptr, nullptr};
   int64_t stage_cap = 0;
   cudaStream_t host_streams[2] = {nullptr, nullptr};
+  cudaEvent_t host_ev = nullptr;  // the host pipeline's wait on the caller's stream
   cudaEvent_t ev_build0 = nullptr, ev_build1 = nullptr;
   cudaEvent_t split_ev[2] = {nullptr, nullptr};  // caller's events around the split kernel
   bool built = false;

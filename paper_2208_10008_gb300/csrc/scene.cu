@@ -282,6 +282,7 @@ int rt_scene_destroy(rt_scene s) {
   free_scene_buffers(s);
   for (int k = 0; k < 2; ++k)
     if (s->host_streams[k]) cudaStreamDestroy(s->host_streams[k]);
+  if (s->host_ev) cudaEventDestroy(s->host_ev);
   if (s->ev_build0) cudaEventDestroy(s->ev_build0);
   if (s->ev_build1) cudaEventDestroy(s->ev_build1);
   delete s;
@@ -606,8 +607,8 @@ int rt_trace_closest_host(rt_scene s, const rt_ray* rays_host, int64_t n, rt_hit
   // the ray copies start at once (they read only the caller's host buffer);
   // the traces wait for everything already queued on the caller's stream
   // (typically the build)
-  cudaEvent_t ev;
-  RT_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "create event");
+  if (!s->host_ev) RT_CUDA(cudaEventCreateWithFlags(&s->host_ev, cudaEventDisableTiming), "create event");
+  cudaEvent_t ev = s->host_ev;
   RT_CUDA(cudaEventRecord(ev, (cudaStream_t)stream), "record event");
   rt_trace_params tp{};
   if (params) {  // n_flagged_dev counts one call of the device path: not written here
@@ -635,7 +636,6 @@ int rt_trace_closest_host(rt_scene s, const rt_ray* rays_host, int64_t n, rt_hit
     cudaError_t e = cudaStreamSynchronize(s->host_streams[k]);
     if (e != cudaSuccess && rc == RT_OK) rc = cuda_fail(e, "synchronize pipeline");
   }
-  cudaEventDestroy(ev);
   return rc;
 }
 
