@@ -1683,6 +1683,7 @@ struct SubSmem {
   Task task;
   int red[kWarps];
   int2 pick;  // the split Eq. 2 chose: candidate, records on the left
+  int mord[32];  // the order in which the warps take the small nodes (largest first)
   float4 pbox[3];  // and the boxes of its children (left lo, hi; right lo, hi)
   int nm, mnext, got;
 };
@@ -1996,12 +1997,31 @@ __device__ bool cta_split(const BuildArgs& A, SubSmem& S, SubNode& X, int it, in
 __device__ void micro_phase(const BuildArgs& A, SubSmem& S, int gbegin, int tdepth, int epoch, WarpStats& ws) {
   const int lane = threadIdx.x & 31;
   const int nm = S.nm;
+  // more nodes than warps (up to 32): warp 0 orders them largest first, so
+  // that the last round of builds holds the quickest ones
+  const bool order = nm > kWarps && nm <= 32;
+  if (order) {
+    if (threadIdx.x < 32) {
+      unsigned key = lane < nm ? ((unsigned)(63 - ((S.ml[lane].y >> 10) & 63)) << 8) | (unsigned)lane : 0xffffffffu;
+#pragma unroll
+      for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int jj = k >> 1; jj > 0; jj >>= 1) {
+          const unsigned ok = __shfl_xor_sync(kFull, key, jj);
+          const bool up = (lane & k) == 0, lower = (lane & jj) == 0;
+          if ((lower == up) ? (ok < key) : (ok > key)) key = ok;
+        }
+      }
+      S.mord[lane] = (int)(key & 255u);
+    }
+    __syncthreads();
+  }
   for (;;) {
     int i = 0;
     if (lane == 0) i = atomicAdd(&S.mnext, 1);
     i = __shfl_sync(kFull, i, 0);
     if (i >= nm) break;
-    const int2 m = S.ml[i];
+    const int2 m = S.ml[order ? S.mord[i] : i];
     const int f = m.y;
     const int b = f & 1023, n = (f >> 10) & 63, side = (f >> 16) & 1, par = (f >> 17) & 1, dep = f >> 18;
     float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
