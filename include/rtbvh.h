@@ -286,7 +286,8 @@ int rt_trace_closest_host(rt_scene scene, const rt_ray* rays_host, int64_t n, rt
                           const rt_trace_params* params, void* stream);
 
 /* Launch direction sets (Sec. III.A). */
-#define RT_RAYS_FIBONACCI 0 /* param = number of rays N: z_i = 1 - (2i+1)/N, azimuth i pi (3 - sqrt 5) */
+#define RT_RAYS_FIBONACCI 0 /* param = number of rays N: z_i = 1 - (2i+1)/N, azimuth i pi (3 - sqrt 5);
+                               launched in band order (rt_launch_index) */
 #define RT_RAYS_ICOSPHERE 1 /* param = level L: vertices of the icosahedron with every edge cut into
                                f = 2^L, 10 f^2 + 2 rays; order: 12 corners, edge points, face points */
 
@@ -298,10 +299,24 @@ int64_t rt_ray_count(int kind, int64_t param);
  * directions (float32, formed with the azimuth reduced exactly in integer
  * arithmetic for RT_RAYS_FIBONACCI; the planar subdivision point normalised
  * for RT_RAYS_ICOSPHERE), tmin / tmax as given.  capacity must be at least
- * rt_ray_count(kind, param).  Icosphere levels 0..12.
+ * rt_ray_count(kind, param).  Icosphere levels 0..12.  Slot s holds
+ * direction rt_launch_index(kind, param, s): Fibonacci rays come in band
+ * order (rt_launch_index) so that neighbouring slots are neighbouring
+ * directions; icosphere rays in the order given with RT_RAYS_ICOSPHERE.
  * Errors: RT_EINVAL, RT_ECUDA. */
 int rt_gen_rays(int kind, const float* origin, int64_t param, float tmin, float tmax, rt_ray* rays_dev,
                 int64_t capacity, void* stream);
+
+/* Index, in the order of the RT_RAYS_* definitions, of the direction that
+ * rt_gen_rays (and every batch or session launch) writes to slot `slot`;
+ * -1 for an invalid kind, param or slot.  RT_RAYS_FIBONACCI with N rays:
+ * w = the largest Fibonacci number (1, 2, 3, 5, 8, ...; w >= 2) with
+ * w^2 <= 80 N, and c = the one of the two Fibonacci numbers before w that
+ * has an even index (F_1 = F_2 = 1); slot b w + t with (b + 1) w <= N holds
+ * direction b w + (t c mod w), which walks the w consecutive spiral points
+ * of band b in order of azimuth; every later slot holds its own direction.
+ * RT_RAYS_ICOSPHERE: slot itself.  Never touches the GPU. */
+int64_t rt_launch_index(int kind, int64_t param, int64_t slot);
 
 /* Specular bounce (Sec. III.B: a ray that meets a facet generates a
  * reflected ray) with compaction.  For every ray i whose hit has tri >= 0

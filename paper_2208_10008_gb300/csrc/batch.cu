@@ -266,12 +266,21 @@ static int rt_batch_create_body(rt_scene scene, const rt_batch_desc* d, rt_batch
   if (e == cudaSuccess) {
     std::vector<long long> off(b->offset);
     off.push_back(total);
+    // the generator's parameters: the level, or a Fibonacci launch's band
+    // width and step packed as w << 32 | c
+    std::vector<long long> gp(b->param);
+    if (b->kind == RT_RAYS_FIBONACCI)
+      for (int t = 0; t < b->n_tx; ++t) {
+        long long w = 1, c = 1;
+        rt::fib_launch_order(b->count[t], &w, &c);
+        gp[t] = (long long)(((unsigned long long)w << 32) | (unsigned long long)c);
+      }
     e = cudaMemcpyAsync(b->tx_off, off.data(), off.size() * sizeof(long long), cudaMemcpyHostToDevice, b->st);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(b->tx_dev, b->tx.data(), 3 * b->n_tx * sizeof(float), cudaMemcpyHostToDevice, b->st);
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(b->param_dev, b->param.data(), b->n_tx * sizeof(long long), cudaMemcpyHostToDevice, b->st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);  // off is a host temporary
+      e = cudaMemcpyAsync(b->param_dev, gp.data(), b->n_tx * sizeof(long long), cudaMemcpyHostToDevice, b->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);  // off and gp are host temporaries
   }
   if (e == cudaSuccess) e = alloc(&b->blocks, total / 256 + 2);
   const long long qcap = total > b->n_seg ? total : b->n_seg;

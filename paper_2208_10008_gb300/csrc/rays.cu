@@ -3,8 +3,10 @@
 // k_gen_fibonacci / k_gen_icosphere write rays from a source point towards
 //   Fibonacci-sphere points or the vertices of a subdivided regular
 //   icosahedron (f = 2^level segments per edge, 10 f^2 + 2 directions), in
-//   float32, in the same order as the host generators: the 12 corners, the
-//   points inside each edge, the points inside each face.
+//   float32.  Icosphere rays come in the order of the host generator (the 12
+//   corners, the points inside each edge, the points inside each face);
+//   Fibonacci rays in band order (fib_launch_order), so that the 32 rays of
+//   a warp are neighbours on the sphere and walk the same nodes.
 // k_reflect_* turn every hit ray into its specular reflection r = d -
 //   2 (d.n) n about the unit geometric normal of the hit triangle, starting at
 //   the hit point with the remaining range tmax - t and the hit triangle to
@@ -45,11 +47,20 @@ __device__ __forceinline__ float3 fib_dir(long long i, long long n) {
   return make_float3(__fmul_rn(rho, c), __fmul_rn(rho, s), z);
 }
 
-__global__ void k_gen_fibonacci(float ox, float oy, float oz, long long n, float tmin, float tmax,
-                                float4* __restrict__ rays) {
+// Spiral point held by slot s of an n-point launch in band order: slot
+// b w + t of a full band b holds point b w + (t c mod w); the slots past the
+// last full band hold their own point.
+__device__ __forceinline__ long long fib_slot(long long s, long long n, long long w, long long c) {
+  const long long b = s / w;
+  if ((b + 1) * w > n) return s;
+  return b * w + (s - b * w) * c % w;
+}
+
+__global__ void k_gen_fibonacci(float ox, float oy, float oz, long long n, long long w, long long c, float tmin,
+                                float tmax, float4* __restrict__ rays) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    const float3 d = fib_dir(i, n);
+    const float3 d = fib_dir(fib_slot(i, n, w, c), n);
     rays[2 * i] = make_float4(ox, oy, oz, tmin);
     rays[2 * i + 1] = make_float4(d.x, d.y, d.z, tmax);
   }
@@ -121,7 +132,9 @@ __global__ void k_gen_icosphere(float ox, float oy, float oz, int fseg, long lon
 }
 
 // The launches of many transmitters in one kernel: transmitter t's rays
-// occupy [off[t], off[t + 1]) (each the same rays its own launch writes).
+// occupy [off[t], off[t + 1]) (each the same rays its own launch writes);
+// param[t] holds the icosphere level, or the band width w and step c of a
+// Fibonacci launch as w << 32 | c.
 __global__ void k_gen_batch(int kind, const float* __restrict__ tx, const long long* __restrict__ off,
                             const long long* __restrict__ param, int n_tx, float tmin, float tmax,
                             float4* __restrict__ rays) {
@@ -137,7 +150,14 @@ __global__ void k_gen_batch(int kind, const float* __restrict__ tx, const long l
         hi = mid - 1;
     }
     const long long j = i - off[lo];
-    const float3 d = kind == RT_RAYS_FIBONACCI ? fib_dir(j, off[lo + 1] - off[lo]) : ico_dir(j, 1ll << param[lo]);
+    float3 d;
+    if (kind == RT_RAYS_FIBONACCI) {
+      const long long n = off[lo + 1] - off[lo];
+      const unsigned long long wc = (unsigned long long)param[lo];
+      d = fib_dir(fib_slot(j, n, (long long)(wc >> 32), (long long)(wc & 0xffffffffull)), n);
+    } else {
+      d = ico_dir(j, 1ll << param[lo]);
+    }
     rays[2 * i] = make_float4(tx[3 * lo], tx[3 * lo + 1], tx[3 * lo + 2], tmin);
     rays[2 * i + 1] = make_float4(d.x, d.y, d.z, tmax);
   }
@@ -311,11 +331,35 @@ int sms() {
 
 }  // namespace
 
+void fib_launch_order(long long n, long long* w, long long* c) {
+  // Fibonacci numbers F_k (F_1 = F_2 = 1); w = F_k, the largest with
+  // F_k^2 <= 80 n (k >= 3), which makes a band about sqrt(80 n) points long
+  // and 2 sqrt(80 / n) high in z: a warp's 32 neighbours in azimuth then
+  // cover a patch about as wide as it is high.  The points j g mod 1
+  // (g = (3 - sqrt 5) / 2), j < F_k, follow one another in the order
+  // j -> j + c mod F_k with c the even-indexed one of F_(k-1) and F_(k-2)
+  // (three-gap theorem; the continued fraction of g has all partial
+  // quotients 1 after the first two).
+  long long f2 = 1, f1 = 1, f = 2;  // F_(k-2), F_(k-1), F_k for k = 3
+  int k = 3;
+  const long long lim = 80 * (n > 0 ? n : 0);
+  while ((f1 + f) <= lim / (f1 + f)) {
+    f2 = f1;
+    f1 = f;
+    f = f1 + f2;
+    ++k;
+  }
+  *w = f;
+  *c = ((k - 1) & 1) == 0 ? f1 : f2;
+}
+
 cudaError_t launch_gen_rays(int kind, const float* o, long long param, float tmin, float tmax, rt_ray* rays,
                             long long count, cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
   if (kind == RT_RAYS_FIBONACCI) {
-    k_gen_fibonacci<<<grid_for(count, sms()), kRayBlock, 0, st>>>(o[0], o[1], o[2], count, tmin, tmax,
+    long long w = 1, c = 1;
+    fib_launch_order(count, &w, &c);
+    k_gen_fibonacci<<<grid_for(count, sms()), kRayBlock, 0, st>>>(o[0], o[1], o[2], count, w, c, tmin, tmax,
                                                                    reinterpret_cast<float4*>(rays));
   } else {
     std::call_once(g_ico_once, init_ico);

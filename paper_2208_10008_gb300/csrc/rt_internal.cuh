@@ -250,6 +250,10 @@ cudaError_t launch_trace_dev(struct ::rt_scene_s* s, const rt_ray* rays, int64_t
                              cudaStream_t st);
 cudaError_t launch_gen_rays(int kind, const float* origin, long long param, float tmin, float tmax,
                             rt_ray* rays, long long count, cudaStream_t st);
+// Band width w and in-band step c of the launch order of an n-ray Fibonacci
+// set: slot b w + t of a full band b holds spiral point b w + (t c mod w), the
+// slots past the last full band their own point (host only).
+void fib_launch_order(long long n, long long* w, long long* c);
 // Device buffers of a batch for the one-launch pipeline (launch_batch_persistent).
 struct BatchLaunch {
   int max_order;
@@ -280,7 +284,8 @@ cudaError_t launch_batch_persistent(struct ::rt_scene_s* s, const BatchLaunch& b
 int persistent_batch_ctas();
 
 // Launches of n_tx transmitters in one kernel (device arrays: tx 3 floats
-// each, off n_tx + 1 ray offsets, param the launch parameters).
+// each, off n_tx + 1 ray offsets, param the icosphere level or, for
+// Fibonacci launches, fib_launch_order's w << 32 | c).
 cudaError_t launch_gen_batch(int kind, const float* tx_dev, const long long* off_dev, const long long* param_dev,
                              int n_tx, long long total, float tmin, float tmax, rt_ray* rays, cudaStream_t st);
 cudaError_t launch_reflect(const struct ::rt_scene_s* s, const rt_ray* rays, const rt_hit* hits,

@@ -537,6 +537,17 @@ int64_t rt_ray_count(int kind, int64_t param) {
   return -1;
 }
 
+int64_t rt_launch_index(int kind, int64_t param, int64_t slot) {
+  const int64_t n = rt_ray_count(kind, param);
+  if (n < 0 || slot < 0 || slot >= n) return -1;
+  if (kind != RT_RAYS_FIBONACCI) return slot;
+  long long w = 1, c = 1;
+  rt::fib_launch_order(n, &w, &c);
+  const int64_t b = slot / w;
+  if ((b + 1) * w > n) return slot;
+  return b * w + (slot - b * w) * c % w;
+}
+
 int rt_gen_rays(int kind, const float* origin, int64_t param, float tmin, float tmax, rt_ray* rays_dev,
                 int64_t capacity, void* stream) {
   g_err[0] = 0;

@@ -36,7 +36,7 @@ ERRORS = {-1: "RT_EINVAL", -2: "RT_ENOMEM", -3: "RT_ENOTBUILT", -4: "RT_ETIMEOUT
 # Every symbol the header declares (checked by the ABI test).
 EXPORTS = ["rt_version", "rt_launch_count", "rt_last_error", "rt_scene_upload", "rt_scene_destroy", "rt_scene_update",
            "rt_bvh_build", "rt_bvh_info", "rt_bvh_export", "rt_trace_closest", "rt_trace_any",
-           "rt_trace_closest_host", "rt_trace_closest_noalloc", "rt_ray_count", "rt_gen_rays",
+           "rt_trace_closest_host", "rt_trace_closest_noalloc", "rt_ray_count", "rt_launch_index", "rt_gen_rays",
            "rt_reflect", "rt_batch_create", "rt_batch_run", "rt_batch_stats_get", "rt_batch_order",
            "rt_batch_visibility", "rt_batch_destroy", "rt_session_create", "rt_session_add_scene",
            "rt_session_submit", "rt_session_poll", "rt_session_wait", "rt_session_release", "rt_session_stats_get",
@@ -151,6 +151,8 @@ def lib(build: bool = True):
             L.rt_trace_closest_noalloc.argtypes = [vp, vp, i64, vp, ctypes.POINTER(TraceParams), vp]
             L.rt_ray_count.restype = i64
             L.rt_ray_count.argtypes = [i32, i64]
+            L.rt_launch_index.restype = i64
+            L.rt_launch_index.argtypes = [i32, i64, i64]
             L.rt_gen_rays.argtypes = [i32, ctypes.POINTER(ctypes.c_float), i64, ctypes.c_float, ctypes.c_float,
                                       vp, i64, vp]
             L.rt_reflect.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp, vp]
@@ -456,9 +458,17 @@ def rt_ray_count(kind: int, param: int) -> int:
     return int(lib().rt_ray_count(int(kind), int(param)))
 
 
+def rt_launch_index(kind: int, param: int, slot: int) -> int:
+    """Direction index (RT_RAYS_* order) that a launch writes to `slot`; -1 if invalid."""
+    return int(lib().rt_launch_index(int(kind), int(param), int(slot)))
+
+
 def rt_gen_rays(kind: int, origin, param: int, tmin: float = 0.0, tmax: float = float("inf"), rays=None,
                 stream=None):
-    """Launch rays of Sec. III.A on the device; returns float32 [n, 8] CUDA tensor."""
+    """Launch rays of Sec. III.A on the device; returns float32 [n, 8] CUDA tensor.
+
+    Slot s holds direction rt_launch_index(kind, param, s) (Fibonacci rays in
+    band order: neighbouring slots are neighbouring directions)."""
     import torch
     n = rt_ray_count(kind, param)
     if n < 0:

@@ -42,3 +42,24 @@ def compare_closest(gpu_hits, ref, tris=None, rays=None, label=""):
             ok, tt, _, _ = oracle.tri_hit(tris[ids[k]], rays[k])
             assert ok and abs(tt - rt[k]) <= T_REL * rt[k] + T_ABS, (label, k)
     return n, int(hit.sum()), int(tie.sum())
+
+
+def fibonacci_launch_perm(n):
+    """Spiral index held by each slot of an n-ray Fibonacci launch in band
+    order, by brute force: the spiral is cut into bands of w consecutive
+    points, w the largest of the Fibonacci numbers 2, 3, 5, 8, ... with
+    w^2 <= 80 n; the slots of each full band take its points in increasing
+    azimuth measured from the band's first point (azimuth of point i:
+    i (3 - sqrt 5) / 2 turns); the slots after the last full band keep their
+    own point."""
+    a, w = 1, 2
+    while (a + w) ** 2 <= 80 * n:
+        a, w = w, a + w
+    g = (3.0 - np.sqrt(5.0)) / 2.0
+    j = np.arange(w, dtype=np.float64)
+    order = np.argsort(np.mod(j * g, 1.0), kind="stable")
+    perm = np.arange(n, dtype=np.int64)
+    for b in range(n // w):
+        perm[b * w:(b + 1) * w] = b * w + order
+    return perm
+

@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 from paper_2208_10008_gb300 import scenes
-from helpers import compare_closest, split_hits
+from helpers import compare_closest, fibonacci_launch_perm, split_hits
 
 pytestmark = pytest.mark.gpu
 
@@ -47,10 +47,10 @@ def test_batch_orders_match_checker(rb, orc, use_graph):
         assert n == st["rays"][k]
         skip = None
         if k == 0:
-            # launched rays: each transmitter's Fibonacci set, in order
+            # launched rays: each transmitter's Fibonacci set, in band order
             off = 0
             for t, c in enumerate(counts):
-                d = orc.fibonacci(int(c))
+                d = orc.fibonacci(int(c))[fibonacci_launch_perm(int(c))]
                 assert np.abs(r[off:off + c, 4:7] - d).max() < 2e-6
                 assert np.allclose(r[off:off + c, 0:3], tx[t].astype(np.float32))
                 off += c

@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 from paper_2208_10008_gb300 import scenes
-from helpers import compare_closest, split_hits
+from helpers import compare_closest, fibonacci_launch_perm, split_hits
 
 pytestmark = pytest.mark.gpu
 
@@ -23,7 +23,7 @@ def rb():
 def test_fibonacci_launch_matches_checker(rb, orc, n):
     o = (12.5, -3.0, 30.0)
     r = rb.rt_gen_rays(rb.RT_RAYS_FIBONACCI, o, n, 0.25, 750.0).cpu().numpy()
-    ref = orc.fibonacci(n)
+    ref = orc.fibonacci(n)[fibonacci_launch_perm(n)]      # band order: slot s holds direction perm[s]
     assert r.shape == (n, 8)
     assert np.abs(r[:, 4:7] - ref).max() < 2e-6
     assert (r[:, 0:3] == np.float32(o)).all() and (r[:, 3] == 0.25).all() and (r[:, 7] == 750.0).all()
