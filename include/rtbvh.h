@@ -289,7 +289,8 @@ int rt_trace_closest_host(rt_scene scene, const rt_ray* rays_host, int64_t n, rt
 #define RT_RAYS_FIBONACCI 0 /* param = number of rays N: z_i = 1 - (2i+1)/N, azimuth i pi (3 - sqrt 5);
                                launched in band order (rt_launch_index) */
 #define RT_RAYS_ICOSPHERE 1 /* param = level L: vertices of the icosahedron with every edge cut into
-                               f = 2^L, 10 f^2 + 2 rays; order: 12 corners, edge points, face points */
+                               f = 2^L, 10 f^2 + 2 rays; order: 12 corners, edge points, face points
+                               row by row; launched in tile order (rt_launch_index) */
 
 /* Number of rays of a launch (RT_RAYS_FIBONACCI: param; RT_RAYS_ICOSPHERE:
  * 10 * 4^param + 2); -1 for an invalid kind or param.  Never touches the GPU. */
@@ -300,9 +301,9 @@ int64_t rt_ray_count(int kind, int64_t param);
  * arithmetic for RT_RAYS_FIBONACCI; the planar subdivision point normalised
  * for RT_RAYS_ICOSPHERE), tmin / tmax as given.  capacity must be at least
  * rt_ray_count(kind, param).  Icosphere levels 0..12.  Slot s holds
- * direction rt_launch_index(kind, param, s): Fibonacci rays come in band
- * order (rt_launch_index) so that neighbouring slots are neighbouring
- * directions; icosphere rays in the order given with RT_RAYS_ICOSPHERE.
+ * direction rt_launch_index(kind, param, s): rays come in band (Fibonacci)
+ * or tile (icosphere) order, so that the 32 rays of a warp are neighbouring
+ * directions.
  * Errors: RT_EINVAL, RT_ECUDA. */
 int rt_gen_rays(int kind, const float* origin, int64_t param, float tmin, float tmax, rt_ray* rays_dev,
                 int64_t capacity, void* stream);
@@ -315,7 +316,13 @@ int rt_gen_rays(int kind, const float* origin, int64_t param, float tmin, float 
  * has an even index (F_1 = F_2 = 1); slot b w + t with (b + 1) w <= N holds
  * direction b w + (t c mod w), which walks the w consecutive spiral points
  * of band b in order of azimuth; every later slot holds its own direction.
- * RT_RAYS_ICOSPHERE: slot itself.  Never touches the GPU. */
+ * RT_RAYS_ICOSPHERE: corners and edge points keep their slots; each face's
+ * interior (rows i = 1 .. f-2 of f-1-i points) is cut into bands of 8 rows,
+ * and a band lists the columns all 8 rows hold as tiles of 8 rows x 4
+ * columns (row by row inside a tile), then the rest of its rows row by row;
+ * odd bands (counted from 0) list the rest first and the tiles from the last
+ * to the first; the rows after the last full band follow row by row.  Never
+ * touches the GPU. */
 int64_t rt_launch_index(int kind, int64_t param, int64_t slot);
 
 /* Specular bounce (Sec. III.B: a ray that meets a facet generates a

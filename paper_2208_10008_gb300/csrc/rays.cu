@@ -3,10 +3,8 @@
 // k_gen_fibonacci / k_gen_icosphere write rays from a source point towards
 //   Fibonacci-sphere points or the vertices of a subdivided regular
 //   icosahedron (f = 2^level segments per edge, 10 f^2 + 2 directions), in
-//   float32.  Icosphere rays come in the order of the host generator (the 12
-//   corners, the points inside each edge, the points inside each face);
-//   Fibonacci rays in band order (fib_launch_order), so that the 32 rays of
-//   a warp are neighbours on the sphere and walk the same nodes.
+//   float32, in launch order (fib_slot, ico_slot_point): the 32 rays of a
+//   warp are neighbours on the sphere and walk the same nodes.
 // k_reflect_* turn every hit ray into its specular reflection r = d -
 //   2 (d.n) n about the unit geometric normal of the hit triangle, starting at
 //   the hit point with the remaining range tmax - t and the hit triangle to
@@ -34,10 +32,13 @@ constexpr unsigned long long kGoldenFrac = 0x61C8864680B583EAull;
 __device__ __forceinline__ float3 fib_dir(long long i, long long n) {
   // z = 1 - (2i + 1)/n = (n - 2i - 1)/n and rho = sqrt(1 - z^2) =
   // sqrt((2i + 1)(2n - 2i - 1)) / n, each from exact integers (no
-  // cancellation near the poles)
-  const double dn = (double)n;
-  const float z = (float)((double)(n - 2 * i - 1) / dn);
-  const float rho = (float)(sqrt((double)(2 * i + 1) * (double)(2 * n - 2 * i - 1)) / dn);
+  // cancellation near the poles), in float32 with every step rounded to
+  // nearest: each integer, the product, the root and the quotient add at
+  // most half an ulp, so z and rho lie within 4 ulp (< 2.5e-7) of their
+  // exact values
+  const float fn = __ll2float_rn(n);
+  const float z = __fdiv_rn(__ll2float_rn(n - 2 * i - 1), fn);
+  const float rho = __fdiv_rn(__fsqrt_rn(__fmul_rn(__ll2float_rn(2 * i + 1), __ll2float_rn(2 * n - 2 * i - 1))), fn);
   // azimuth in turns, i (3 - sqrt 5)/2 mod 1, reduced to [-1/2, 1/2) in
   // exact integer arithmetic before the one rounding to float
   const unsigned long long turns = (unsigned long long)i * kGoldenFrac;  // mod 2^64
@@ -45,15 +46,6 @@ __device__ __forceinline__ float3 fib_dir(long long i, long long n) {
   float s, c;
   sincospif(2.f * a, &s, &c);
   return make_float3(__fmul_rn(rho, c), __fmul_rn(rho, s), z);
-}
-
-// Spiral point held by slot s of an n-point launch in band order: slot
-// b w + t of a full band b holds point b w + (t c mod w); the slots past the
-// last full band hold their own point.
-__device__ __forceinline__ long long fib_slot(long long s, long long n, long long w, long long c) {
-  const long long b = s / w;
-  if ((b + 1) * w > n) return s;
-  return b * w + (s - b * w) * c % w;
 }
 
 __global__ void k_gen_fibonacci(float ox, float oy, float oz, long long n, long long w, long long c, float tmin,
@@ -74,45 +66,29 @@ struct Ico {
 };
 __constant__ Ico c_ico;
 
-// Direction k of the launch towards the vertices of the icosahedron with
-// every edge cut into f segments, normalised; every operation rounded
-// explicitly (the same bits in every kernel that generates it).
-__device__ __forceinline__ float3 ico_dir(long long k, long long f) {
-  const long long n_edge_pts = 30 * (f - 1);
-  const long long per_face = (f - 1) * (f - 2) / 2;
+// Direction towards point p of the icosahedron with every edge cut into f
+// segments, normalised; every operation rounded explicitly (the same bits in
+// every kernel that generates it).
+__device__ __forceinline__ float3 ico_dir(const IcoPt& p, long long f) {
   const float inv_f = __frcp_rn((float)f);
   float p0, p1, p2;
-  if (k < 12) {
-    p0 = c_ico.v[k][0];
-    p1 = c_ico.v[k][1];
-    p2 = c_ico.v[k][2];
-  } else if (k < 12 + n_edge_pts) {
-    const long long r = k - 12;
-    const int e = (int)(r / (f - 1));
-    const long long s = r - (long long)e * (f - 1) + 1;  // 1 .. f-1
-    const float t = __fmul_rn((float)s, inv_f), u = __fsub_rn(1.f, t);
-    const float* a = c_ico.v[c_ico.e[e][0]];
-    const float* b = c_ico.v[c_ico.e[e][1]];
+  if (p.kind == 0) {
+    p0 = c_ico.v[p.a][0];
+    p1 = c_ico.v[p.a][1];
+    p2 = c_ico.v[p.a][2];
+  } else if (p.kind == 1) {
+    const float t = __fmul_rn((float)p.i, inv_f), u = __fsub_rn(1.f, t);
+    const float* a = c_ico.v[c_ico.e[p.a][0]];
+    const float* b = c_ico.v[c_ico.e[p.a][1]];
     p0 = __fadd_rn(__fmul_rn(a[0], u), __fmul_rn(b[0], t));
     p1 = __fadd_rn(__fmul_rn(a[1], u), __fmul_rn(b[1], t));
     p2 = __fadd_rn(__fmul_rn(a[2], u), __fmul_rn(b[2], t));
   } else {
-    const long long r = k - 12 - n_edge_pts;
-    const int fc = (int)(r / per_face);
-    long long q = r - (long long)fc * per_face;
-    // row i (1 .. f-2) holds f-1-i points; rows start at (i-1)(f-1) - (i-1)i/2
-    const double ff = (double)(f - 1);
-    long long i = 1 + (long long)floor(ff - 0.5 - sqrt(fmax(0.0, (ff - 0.5) * (ff - 0.5) - 2.0 * (double)q)));
-    if (i < 1) i = 1;
-    auto row_start = [&](long long ii) { return (ii - 1) * (f - 1) - (ii - 1) * ii / 2; };
-    while (i > 1 && row_start(i) > q) --i;
-    while (row_start(i + 1) <= q) ++i;
-    const long long j = q - row_start(i) + 1;
-    const float wi = __fmul_rn((float)i, inv_f), wj = __fmul_rn((float)j, inv_f);
+    const float wi = __fmul_rn((float)p.i, inv_f), wj = __fmul_rn((float)p.j, inv_f);
     const float w0 = __fsub_rn(__fsub_rn(1.f, wi), wj);
-    const float* a = c_ico.v[c_ico.f[fc][0]];
-    const float* b = c_ico.v[c_ico.f[fc][1]];
-    const float* c = c_ico.v[c_ico.f[fc][2]];
+    const float* a = c_ico.v[c_ico.f[p.a][0]];
+    const float* b = c_ico.v[c_ico.f[p.a][1]];
+    const float* c = c_ico.v[c_ico.f[p.a][2]];
     p0 = __fadd_rn(__fadd_rn(__fmul_rn(a[0], w0), __fmul_rn(b[0], wi)), __fmul_rn(c[0], wj));
     p1 = __fadd_rn(__fadd_rn(__fmul_rn(a[1], w0), __fmul_rn(b[1], wi)), __fmul_rn(c[1], wj));
     p2 = __fadd_rn(__fadd_rn(__fmul_rn(a[2], w0), __fmul_rn(b[2], wi)), __fmul_rn(c[2], wj));
@@ -125,7 +101,7 @@ __global__ void k_gen_icosphere(float ox, float oy, float oz, int fseg, long lon
                                 float4* __restrict__ rays) {
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
        k += (long long)gridDim.x * blockDim.x) {
-    const float3 d = ico_dir(k, fseg);
+    const float3 d = ico_dir(ico_slot_point(k, fseg), fseg);
     rays[2 * k] = make_float4(ox, oy, oz, tmin);
     rays[2 * k + 1] = make_float4(d.x, d.y, d.z, tmax);
   }
@@ -156,7 +132,7 @@ __global__ void k_gen_batch(int kind, const float* __restrict__ tx, const long l
       const unsigned long long wc = (unsigned long long)param[lo];
       d = fib_dir(fib_slot(j, n, (long long)(wc >> 32), (long long)(wc & 0xffffffffull)), n);
     } else {
-      d = ico_dir(j, 1ll << param[lo]);
+      d = ico_dir(ico_slot_point(j, 1ll << param[lo]), 1ll << param[lo]);
     }
     rays[2 * i] = make_float4(tx[3 * lo], tx[3 * lo + 1], tx[3 * lo + 2], tmin);
     rays[2 * i + 1] = make_float4(d.x, d.y, d.z, tmax);

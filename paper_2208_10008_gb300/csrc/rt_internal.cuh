@@ -15,6 +15,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 #include <string.h>
 
@@ -251,9 +252,106 @@ cudaError_t launch_trace_dev(struct ::rt_scene_s* s, const rt_ray* rays, int64_t
 cudaError_t launch_gen_rays(int kind, const float* origin, long long param, float tmin, float tmax,
                             rt_ray* rays, long long count, cudaStream_t st);
 // Band width w and in-band step c of the launch order of an n-ray Fibonacci
-// set: slot b w + t of a full band b holds spiral point b w + (t c mod w), the
-// slots past the last full band their own point (host only).
+// set (host only; fib_slot uses them).
 void fib_launch_order(long long n, long long* w, long long* c);
+
+// Launch orders (slot -> direction), shared by the generators and
+// rt_launch_index.
+
+// Spiral point held by slot s of an n-point Fibonacci launch in band order:
+// slot b w + t of a full band b holds point b w + (t c mod w), which walks the
+// band's points in order of azimuth; the slots past the last full band hold
+// their own point.
+__host__ __device__ inline long long fib_slot(long long s, long long n, long long w, long long c) {
+  const long long b = s / w;
+  if ((b + 1) * w > n) return s;
+  return b * w + (s - b * w) * c % w;
+}
+
+// A point of the icosahedron with every edge cut into f segments: corner a
+// (kind 0); point i (1 .. f-1) inside edge a (kind 1); point (i, j) inside
+// face a, row i (1 .. f-2) of f-1-i points, column j (1 .. f-1-i) (kind 2).
+struct IcoPt {
+  int kind, a;
+  long long i, j;
+};
+
+// First point of face row i among the face's points listed row by row.
+__host__ __device__ inline long long ico_row_start(long long i, long long f) {
+  return (i - 1) * (f - 1) - (i - 1) * i / 2;
+}
+
+// Index of p in the order of RT_RAYS_ICOSPHERE: the 12 corners, the points
+// inside each edge, the points inside each face row by row.
+__host__ __device__ inline long long ico_index(const IcoPt& p, long long f) {
+  if (p.kind == 0) return p.a;
+  if (p.kind == 1) return 12 + p.a * (f - 1) + p.i - 1;
+  return 12 + 30 * (f - 1) + p.a * ((f - 1) * (f - 2) / 2) + ico_row_start(p.i, f) + p.j - 1;
+}
+
+// Point held by slot s (0 <= s < 10 f^2 + 2) of an icosphere launch in tile
+// order.  Corners and edge points keep their order.  A face's rows are cut
+// into bands of 8 (band r: rows 8r+1 .. 8r+8); a band lists the columns all
+// 8 of its rows hold as tiles of 8 rows x 4 columns (row by row inside a
+// tile), the rest of its rows row by row; even bands run tiles then rest,
+// odd bands rest then tiles from the last to the first, so the walk turns
+// at the ends of the bands; the rows after the last full band follow row by
+// row.  32 consecutive slots of a face lie in one or two neighbouring tiles.
+__host__ __device__ inline IcoPt ico_slot_point(long long s, long long f) {
+  if (s < 12) return IcoPt{0, (int)s, 0, 0};
+  const long long ne = 30 * (f - 1);
+  if (s < 12 + ne) {
+    const long long r = s - 12;
+    const long long e = r / (f - 1);
+    return IcoPt{1, (int)e, r - e * (f - 1) + 1, 0};
+  }
+  const long long per_face = (f - 1) * (f - 2) / 2;
+  const long long r0 = s - 12 - ne;
+  const long long fc = r0 / per_face;
+  const long long q = r0 - fc * per_face;
+  const long long nb = (f - 2) / 8;
+  // points before band b: sum over b' < b of 8f - 44 - 64 b'
+  auto before = [f](long long b) { return (8 * f - 12) * b - 32 * b * b; };
+  long long i, j;
+  if (q >= before(nb)) {
+    const long long q2 = ico_row_start(8 * nb + 1, f) + q - before(nb);
+    i = 8 * nb + 1;
+    while (ico_row_start(i + 1, f) <= q2) ++i;
+    j = q2 - ico_row_start(i, f) + 1;
+  } else {
+    // the root of before(b) = q, then exact by stepping
+    const double b0 = 8.0 * (double)f - 12.0;
+    long long r = (long long)((b0 - sqrt(fmax(0.0, b0 * b0 - 128.0 * (double)q))) / 64.0);
+    if (r < 0) r = 0;
+    if (r > nb - 1) r = nb - 1;
+    while (r > 0 && before(r) > q) --r;
+    while (r + 1 < nb && before(r + 1) <= q) ++r;
+    const long long u = q - before(r);
+    const long long l7 = f - 9 - 8 * r;  // points in the band's last row
+    const long long nblk = l7 / 4, tiles = 32 * nblk, rest = 8 * (l7 - 4 * nblk) + 28;
+    const bool odd = (r & 1) != 0;
+    const bool in_tiles = odd ? u >= rest : u < tiles;
+    long long v = odd ? (in_tiles ? u - rest : u) : (in_tiles ? u : u - tiles);
+    if (in_tiles) {
+      long long blk = v / 32;
+      if (odd) blk = nblk - 1 - blk;
+      const long long w = v - (v / 32) * 32;
+      i = 8 * r + 1 + w / 4;
+      j = 4 * blk + (w & 3) + 1;
+    } else {
+      // row k of the rest holds (l7 - 4 nblk) + 7 - k points
+      const long long e = l7 - 4 * nblk;
+      long long k = 0;
+      while (k < 7 && v >= e + 7 - k) {
+        v -= e + 7 - k;
+        ++k;
+      }
+      i = 8 * r + 1 + k;
+      j = 4 * nblk + 1 + v;
+    }
+  }
+  return IcoPt{2, (int)fc, i, j};
+}
 // Device buffers of a batch for the one-launch pipeline (launch_batch_persistent).
 struct BatchLaunch {
   int max_order;

@@ -540,12 +540,13 @@ int64_t rt_ray_count(int kind, int64_t param) {
 int64_t rt_launch_index(int kind, int64_t param, int64_t slot) {
   const int64_t n = rt_ray_count(kind, param);
   if (n < 0 || slot < 0 || slot >= n) return -1;
-  if (kind != RT_RAYS_FIBONACCI) return slot;
+  if (kind == RT_RAYS_ICOSPHERE) {
+    const long long f = 1ll << param;
+    return rt::ico_index(rt::ico_slot_point(slot, f), f);
+  }
   long long w = 1, c = 1;
   rt::fib_launch_order(n, &w, &c);
-  const int64_t b = slot / w;
-  if ((b + 1) * w > n) return slot;
-  return b * w + (slot - b * w) * c % w;
+  return rt::fib_slot(slot, n, w, c);
 }
 
 int rt_gen_rays(int kind, const float* origin, int64_t param, float tmin, float tmax, rt_ray* rays_dev,

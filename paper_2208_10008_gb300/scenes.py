@@ -305,6 +305,46 @@ def icosphere_directions(level: int) -> np.ndarray:
     return p / np.linalg.norm(p, axis=1, keepdims=True)
 
 
+def icosphere_launch_order(level: int) -> np.ndarray:
+    """Index (in icosphere_directions' order) of the direction in each slot of
+    an icosphere launch in tile order, int64 [10 f^2 + 2].
+
+    Corners and edge points keep their order.  Each face's interior (rows
+    i = 1 .. f-2 of f-1-i points j = 1 .. f-1-i) is cut into bands of 8 rows;
+    a band lists the columns all 8 of its rows hold as tiles of 8 rows x 4
+    columns (tile after tile, row by row inside a tile) and the rest of its
+    rows row by row; even bands (counted from 0) run tiles then rest, odd
+    bands rest then the tiles from the last to the first; the rows after the
+    last full band follow row by row.
+    """
+    f = 1 << level
+    n = 10 * f * f + 2
+    head = 12 + 30 * (f - 1)
+    per_face = (f - 1) * (f - 2) // 2
+    def row_start(i):                      # first point of row i in a face
+        return (i - 1) * (f - 1) - (i - 1) * i // 2
+    local = []
+    nb = (f - 2) // 8 if f >= 2 else 0
+    for r in range(nb):
+        rows = [8 * r + 1 + k for k in range(8)]
+        lens = [f - 1 - i for i in rows]
+        nblk = lens[-1] // 4
+        tiles = [[row_start(rows[k]) + 4 * b + c for k in range(8) for c in range(4)] for b in range(nblk)]
+        rest = [row_start(rows[k]) + j - 1 for k in range(8) for j in range(4 * nblk + 1, lens[k] + 1)]
+        if r % 2 == 0:
+            local += [x for t in tiles for x in t] + rest
+        else:
+            local += rest + [x for t in reversed(tiles) for x in t]
+    for i in range(8 * nb + 1, f - 1):
+        local += [row_start(i) + j - 1 for j in range(1, f - i)]
+    local = np.asarray(local, dtype=np.int64)
+    assert local.size == max(per_face, 0)
+    perm = np.arange(n, dtype=np.int64)
+    for fc in range(20):
+        perm[head + fc * per_face:head + (fc + 1) * per_face] = head + fc * per_face + local
+    return perm
+
+
 def make_rays(origin, dirs, tmin: float = 0.0, tmax: float = np.inf) -> np.ndarray:
     """Pack rays from one origin as float32 [R, 8] = (o, tmin, d, tmax)."""
     dirs = np.asarray(dirs, dtype=np.float64)
@@ -364,9 +404,10 @@ def workload_tiny():
 
 
 def workload_medium(level: int = 8):
-    """1000-prism city, icosphere level-8 rays (655,362) from the centre at 30 m, t_max 500 m."""
+    """1000-prism city, icosphere level-8 rays (655,362) from the centre at 30 m, t_max 500 m,
+    in the launch order of the device generator (icosphere_launch_order)."""
     sc = medium_city(seed=2)
-    rays = make_rays(sc.tx[0], icosphere_directions(level), 0.0, 500.0)
+    rays = make_rays(sc.tx[0], icosphere_directions(level)[icosphere_launch_order(level)], 0.0, 500.0)
     return sc, rays, dict(alpha=0.4, source=tuple(sc.tx[0]))
 
 

@@ -1,12 +1,13 @@
-"""Band launch order of Fibonacci rays (no GPU): the library's slot -> direction
-map equals a brute-force sort by azimuth, and the order makes each warp's 32
-rays neighbours on the sphere."""
+"""Launch orders (no GPU): the library's slot -> direction map equals, for
+Fibonacci rays, a brute-force sort of each band by azimuth and, for icosphere
+rays, the host generator's tile order; both make each warp's 32 rays
+neighbours on the sphere."""
 import ctypes
 
 import numpy as np
 import pytest
 
-from paper_2208_10008_gb300 import rtbvh
+from paper_2208_10008_gb300 import rtbvh, scenes
 from helpers import fibonacci_launch_perm
 
 
@@ -74,5 +75,57 @@ def test_launch_index_edges_without_gpu():
     assert lib.rt_launch_index(rtbvh.RT_RAYS_FIBONACCI, 0, 0) == -1
     assert lib.rt_launch_index(7, 100, 3) == -1
     assert lib.rt_launch_index(rtbvh.RT_RAYS_ICOSPHERE, 13, 0) == -1
-    assert [lib.rt_launch_index(rtbvh.RT_RAYS_ICOSPHERE, 2, s) for s in (0, 5, 161)] == [0, 5, 161]
+    assert lib.rt_launch_index(rtbvh.RT_RAYS_ICOSPHERE, 2, 162) == -1
+    # level 2: every face holds 3 points in rows 1 and 2 (no full band): the identity
+    assert [lib.rt_launch_index(rtbvh.RT_RAYS_ICOSPHERE, 2, s) for s in range(162)] == list(range(162))
     assert rtbvh.rt_launch_index(rtbvh.RT_RAYS_FIBONACCI, 1, 0) == 0
+
+
+@pytest.mark.parametrize("level", range(0, 9))
+def test_library_icosphere_order_matches_host_without_gpu(level):
+    lib = rtbvh.lib()
+    perm = scenes.icosphere_launch_order(level)
+    n = len(perm)
+    assert n == 10 * 4 ** level + 2 and np.array_equal(np.sort(perm), np.arange(n))
+    slots = np.arange(n) if n <= 200_000 else np.unique(np.r_[np.arange(0, n, 7), np.arange(n - 5000, n)])
+    got = np.array([lib.rt_launch_index(rtbvh.RT_RAYS_ICOSPHERE, level, int(s)) for s in slots], dtype=np.int64)
+    assert np.array_equal(got, perm[slots])
+
+
+def _face_point(level, k):
+    """(face, row i, column j) of a face point given by its icosphere_directions index."""
+    f = 1 << level
+    q = k - 12 - 30 * (f - 1)
+    per_face = (f - 1) * (f - 2) // 2
+    fc, q = divmod(q, per_face)
+    i = 1
+    while q >= f - 1 - i:
+        q -= f - 1 - i
+        i += 1
+    return fc, i, q + 1
+
+
+def test_icosphere_tiles_are_8_by_4_lattice_blocks():
+    # level 6 (f = 64): the first band of face 0 starts with its tiles, each
+    # 32 slots covering rows 1..8 and 4 adjacent columns; band 1 (rows 9..16)
+    # starts with its rest and ends with its first tile
+    level, f = 6, 64
+    perm = scenes.icosphere_launch_order(level)
+    head = 12 + 30 * (f - 1)
+    for t in range(3):
+        pts = [_face_point(level, int(perm[head + 32 * t + u])) for u in range(32)]
+        assert {p[0] for p in pts} == {0}
+        assert sorted({p[1] for p in pts}) == list(range(1, 9))
+        assert sorted({p[2] for p in pts}) == [4 * t + 1 + c for c in range(4)]
+    band0 = 8 * (f - 2) - 28
+    first_of_band1 = _face_point(level, int(perm[head + band0]))
+    last_of_band1 = _face_point(level, int(perm[head + band0 + 8 * (f - 10) - 28 - 1]))
+    assert first_of_band1[1] == 9 and first_of_band1[2] > 40      # the rest lies at the far end
+    assert last_of_band1[1] == 16 and last_of_band1[2] == 4        # the first tile ends the band
+
+
+def test_icosphere_tile_order_makes_warps_coherent():
+    d = scenes.icosphere_directions(8)
+    spacing = np.sqrt(4 * np.pi / len(d))
+    assert _warp_spread(d) > 10 * spacing                # rows of 32 points along a face, edges
+    assert _warp_spread(d[scenes.icosphere_launch_order(8)]) < 6 * spacing
