@@ -319,9 +319,10 @@ __host__ __device__ inline IcoPt ico_slot_point(long long s, long long f) {
     while (ico_row_start(i + 1, f) <= q2) ++i;
     j = q2 - ico_row_start(i, f) + 1;
   } else {
-    // the root of before(b) = q, then exact by stepping
-    const double b0 = 8.0 * (double)f - 12.0;
-    long long r = (long long)((b0 - sqrt(fmax(0.0, b0 * b0 - 128.0 * (double)q))) / 64.0);
+    // the root of before(b) = q (radicand exact in integers, root in
+    // float32: off by less than one band), then exact by stepping
+    const long long b0 = 8 * f - 12, rad = b0 * b0 - 128 * q;
+    long long r = (long long)(((float)b0 - sqrtf((float)(rad > 0 ? rad : 0))) * (1.f / 64.f));
     if (r < 0) r = 0;
     if (r > nb - 1) r = nb - 1;
     while (r > 0 && before(r) > q) --r;
