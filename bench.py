@@ -618,14 +618,14 @@ def run_served(rtbvh, torch, seconds, repeats=3, pool_gib=1.0):
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
 # one ncu capture of the current kernels (profiles/); None until captured.
 NCU_TRAFFIC_LARGE = {
-    0.7: (362.228224e6 + 322.753024e6, "ncu capture of k_trace<0,0,128,64,0,4> on the 4 x 2^21 metro rays, "
-                                       "alpha 0.7 tree (profiles/k_trace_metro.md)"),
-    1.0: (294.764544e6 + 144.213248e6, "ncu capture of k_trace<0,0,128,64,0,4> on the 4 x 2^21 metro rays, "
-                                       "alpha 1 tree (profiles/k_trace_metro.md)")}
+    0.7: (277.015211e6 + 172.735488e6, "ncu capture of k_trace<0,0,128,64,0,4> on the 4 x 2^21 metro rays, "
+                                        "alpha 0.7 tree, mean of 3 launches (profiles/k_trace_metro.md)"),
+    1.0: (272.821589e6 + 134.244011e6, "ncu capture of k_trace<0,0,128,64,0,4> on the 4 x 2^21 metro rays, "
+                                        "alpha 1 tree, mean of 3 launches (profiles/k_trace_metro.md)")}
 NCU_TRAFFIC = {
-    "k_split": (1.738752e6 + 768.0, "ncu capture of k_split in the timed steps, medium city, autotuned tree "
+    "k_split": (1.747968e6 + 768.0, "ncu capture of k_split in the timed steps, medium city, autotuned tree "
                                     "(profiles/k_split_medium_city.md)"),
-    "k_trace": (21.495808e6 + 47872.0, "ncu capture of k_trace<0,0,128,64,0,4> in the timed steps, medium "
+    "k_trace": (21.461504e6 + 17920.0, "ncu capture of k_trace<0,0,128,64,0,4> in the timed steps, medium "
                                        "city (k_retest64 not included; profiles/k_trace_medium_city.md)"),
 }
 
