@@ -276,8 +276,12 @@ int rt_trace_any(rt_scene scene, const rt_ray* rays_dev, int64_t n, uint8_t* occ
 
 /* Closest hit with HOST buffers: rays_host and hits_host are host memory
  * (pinned for overlap; pageable works but serialises).  The library copies
- * rays in chunks to device staging buffers, traces them and copies hits
- * back, overlapping the copies of one chunk with the tracing of another.
+ * rays in chunks to device staging buffers and traces them, overlapping the
+ * copies of one chunk with the tracing of another.  When hits_host is
+ * 16-byte aligned page-locked memory mapped into the device's address space
+ * (cudaHostAlloc / cudaMallocHost / a mapped registration, as reported by
+ * cudaPointerGetAttributes), the walk writes the hit records straight into
+ * it; otherwise hits go to device staging buffers and are copied back.
  * Synchronous with respect to the host buffers: on return, hits_host is
  * filled.  Of params (nullable) flags and block are used; skip_tri_dev and
  * stats_dev must be NULL and n_flagged_dev is not written.

@@ -628,6 +628,18 @@ int rt_trace_closest_host(rt_scene s, const rt_ray* rays_host, int64_t n, rt_hit
     tp.block = params->block;
     tp.stack = params->stack;
   }
+  // page-locked hits the device can address: the walk and the float64 pass
+  // (which only write hit records) store into them directly, so no copy
+  // back waits for the last chunk's walk
+  rt_hit* hits_mapped = nullptr;
+  if (((uintptr_t)hits_host & 15) == 0) {
+    cudaPointerAttributes pa{};
+    if (cudaPointerGetAttributes(&pa, hits_host) == cudaSuccess) {
+      if (pa.type == cudaMemoryTypeHost && pa.devicePointer) hits_mapped = static_cast<rt_hit*>(pa.devicePointer);
+    } else {
+      cudaGetLastError();  // not a pointer CUDA knows: stage as for pageable memory
+    }
+  }
   int rc = RT_OK;
   for (int64_t off = 0, c = 0; off < n; off += chunk, ++c) {
     const int k = (int)(c & 1);
@@ -636,8 +648,9 @@ int rt_trace_closest_host(rt_scene s, const rt_ray* rays_host, int64_t n, rt_hit
     cudaError_t e = cudaMemcpyAsync(s->stage_rays[k], rays_host + off, cnt * sizeof(rt_ray),
                                     cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && c < 2) e = cudaStreamWaitEvent(st, ev, 0);
-    if (e == cudaSuccess) e = rt::launch_trace(s, s->stage_rays[k], cnt, s->stage_hits[k], nullptr, &tp, s->host_scr[k], st);
-    if (e == cudaSuccess)
+    rt_hit* out = hits_mapped ? hits_mapped + off : s->stage_hits[k];
+    if (e == cudaSuccess) e = rt::launch_trace(s, s->stage_rays[k], cnt, out, nullptr, &tp, s->host_scr[k], st);
+    if (e == cudaSuccess && !hits_mapped)
       e = cudaMemcpyAsync(hits_host + off, s->stage_hits[k], cnt * sizeof(rt_hit), cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) {
       rc = cuda_fail(e, "host pipeline");
