@@ -120,3 +120,27 @@ def test_batch_graph_follows_a_grown_scene(rb):
     assert torch.equal(vis, fresh.visibility())
     b.destroy()
     fresh.destroy()
+
+
+def test_batch_icosphere_launches_in_tile_order(rb, orc):
+    # icosphere transmitters: every transmitter's launch is the checker's
+    # directions in tile order and the same bits as its own rt_gen_rays call;
+    # the direct rays' hits against the float64 brute force
+    sc, s, tx, _, _ = _setup(rb, seed=9)
+    levels = np.array([3, 5, 4])
+    b = rb.Batch(s, tx, levels, rb.RT_RAYS_ICOSPHERE, max_order=1, tmax=600.0)
+    b.run()
+    torch.cuda.synchronize()
+    rays, hits, _, n = b.order(0)
+    r, h = rays.cpu().numpy(), hits.cpu().numpy()
+    counts = [rb.rt_ray_count(rb.RT_RAYS_ICOSPHERE, int(L)) for L in levels]
+    assert n == sum(counts)
+    off = 0
+    for t, (L, c) in enumerate(zip(levels, counts)):
+        ref = orc.icosphere(int(L))[scenes.icosphere_launch_order(int(L))]
+        assert np.abs(r[off:off + c, 4:7] - ref).max() < 2e-6
+        own = rb.rt_gen_rays(rb.RT_RAYS_ICOSPHERE, tx[t], int(L), 0.0, 600.0).cpu().numpy()
+        assert np.array_equal(r[off:off + c].view(np.uint32), own.view(np.uint32))
+        off += c
+    compare_closest(h, orc.closest_brute(sc.tris, r), sc.tris, r, "icosphere batch, direct rays")
+    b.destroy()
