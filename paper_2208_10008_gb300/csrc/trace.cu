@@ -921,20 +921,21 @@ __device__ bool grid_sync(const PersistArgs& P) {
   return ok;
 }
 
-// A walk phase: every warp takes batches of 64 rays from the phase's device
-// counter until none is left (each lane walks two rays of a batch), so the
-// CTAs that drew cheap rays take more and the phase ends with the last rays.
+// A walk phase: every warp takes batches of 32 rays (a ray per lane) from
+// the phase's device counter until none is left, so the CTAs that drew cheap
+// rays take more and the phase ends with the last rays.  (Batches of 64,
+// two walks per lane one after the other, made every warp wait for its
+// slowest lane twice per claim.)
 template <bool kAny, int kW>
 __device__ __forceinline__ void walk_phase(const TraceArgs& A, int* take, int n, const rt_ray* rays, rt_hit* hits,
                                            uint8_t* occl, const int* skip) {
   const int lane = threadIdx.x & 31;
   for (;;) {
     int b = 0;
-    if (lane == 0) b = atomicAdd(take, 64);
+    if (lane == 0) b = atomicAdd(take, 32);
     b = __shfl_sync(kFullMask, b, 0);
     if (b >= n) break;
     if (b + lane < n) walk_one<kAny, false, kStack, false, kW>(A, b + lane, rays, hits, occl, skip);
-    if (b + 32 + lane < n) walk_one<kAny, false, kStack, false, kW>(A, b + 32 + lane, rays, hits, occl, skip);
   }
 }
 
