@@ -129,3 +129,18 @@ def test_icosphere_tile_order_makes_warps_coherent():
     spacing = np.sqrt(4 * np.pi / len(d))
     assert _warp_spread(d) > 10 * spacing                # rows of 32 points along a face, edges
     assert _warp_spread(d[scenes.icosphere_launch_order(8)]) < 6 * spacing
+
+
+@pytest.mark.parametrize("level", [10, 12])
+def test_library_icosphere_order_high_levels_sampled_without_gpu(level):
+    lib = rtbvh.lib()
+    perm = scenes.icosphere_launch_order(level)
+    n = len(perm)
+    rng = np.random.default_rng(level)
+    f = 1 << level
+    head = 12 + 30 * (f - 1)
+    per_face = (f - 1) * (f - 2) // 2
+    slots = np.unique(np.r_[rng.integers(0, n, 20000), np.arange(head, head + 3000),
+                            np.arange(n - per_face - 1000, n - per_face + 1000), np.arange(n - 3000, n)])
+    got = np.array([lib.rt_launch_index(rtbvh.RT_RAYS_ICOSPHERE, level, int(s)) for s in slots], dtype=np.int64)
+    assert np.array_equal(got, perm[slots])
