@@ -279,6 +279,14 @@ def test_host_buffer_path_matches_device(rb):
     for tile in (64, 256):  # the requested ray tile reaches the chunked walk
         hh = rb.rt_trace_closest_host(s, pinned, block=tile)
         assert np.array_equal(hh.numpy().view(np.uint32), hd.view(np.uint32))
+    # page-locked hits 4 bytes off a 16-byte boundary: the walk cannot store
+    # records there, so they go through the staging buffers; same bits
+    n = len(rays)
+    spare = torch.empty(4 * n + 1, dtype=torch.float32).pin_memory()
+    odd = spare[1:].view(n, 4)
+    assert odd.data_ptr() % 16 == 4
+    rb.rt_trace_closest_host(s, pinned, odd)
+    assert np.array_equal(odd.numpy().view(np.uint32), hd.view(np.uint32))
 
 
 def test_host_buffer_path_many_chunks(rb):
