@@ -237,10 +237,13 @@ int rt_probe_l2_read(const void* buf_dev, int64_t bytes, int32_t reps, uint32_t*
 #define RT_DEBUG_FAIL_ALLOC 4
 int rt_debug_inject(int hook, int64_t value);
 
-/* Synchronous: wait for the stream, then report the built tree.  Errors:
- * RT_EINVAL, RT_ENOTBUILT, RT_ECUDA; RT_ETIMEOUT when a work-queue wait of
- * the build ran out (status 1); RT_EINTERNAL when the device status word
- * reports a failed check (info->status says which). */
+/* Synchronous: wait for the stream, then report the built tree.  Counting
+ * the traversal nodes reachable from the root takes a temporary device array
+ * of their child references (16 bytes per node slot, 32 for 8-wide nodes),
+ * read back to the host.  Errors: RT_EINVAL, RT_ENOTBUILT, RT_ENOMEM,
+ * RT_ECUDA; RT_ETIMEOUT when a work-queue wait of the build ran out
+ * (status 1); RT_EINTERNAL when the device status word reports a failed
+ * check (info->status says which). */
 int rt_bvh_info(rt_scene scene, void* stream, rt_bvh_info_t* info);
 
 /* Synchronous: copy the binary tree (Sec. II.C, Fig. 1) to host arrays in

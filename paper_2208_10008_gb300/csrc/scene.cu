@@ -76,6 +76,22 @@ __global__ void k_pack(const float* __restrict__ raw, int n, float4* __restrict_
   }
 }
 
+// The child references of every traversal node slot (width of them per
+// slot, in slot order), for the host's count of the reachable nodes: 16 or
+// 32 bytes per node instead of the whole 128- or 256-byte node.
+__global__ void k_child_refs(const rt::WNode* __restrict__ w4, const rt::WNode8* __restrict__ w8, int64_t slots,
+                             int4* __restrict__ out) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < slots;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    if (w8) {
+      out[2 * k] = w8[k].child[0];
+      out[2 * k + 1] = w8[k].child[1];
+    } else {
+      out[k] = w4[k].child;
+    }
+  }
+}
+
 void free_scene_buffers(rt_scene_s* s) {
   void* ptrs[] = {s->tri_in, s->idx[0], s->idx[1], s->rec[0], s->rec[1], s->node2, s->wide, s->link2, s->epoch,
                   s->tri_leaf, s->qa, s->qa_ready, s->top_task, s->top_done, s->top_bins, s->top_ccnt,
@@ -385,25 +401,20 @@ static int rt_bvh_info_body(rt_scene s, void* stream, rt_bvh_info_t* info) {
   const int64_t slots = s->n_tri > 1 ? s->n_tri : 1;
   const int width = s->params.width == 8 ? 8 : 4;
   std::vector<int32_t> ch((size_t)slots * width);
-  if (width == 8) {
-    std::vector<rt::WNode8> w((size_t)slots);
-    RT_CUDA(cudaMemcpy(w.data(), s->wide8, sizeof(rt::WNode8) * slots, cudaMemcpyDeviceToHost), "read wide nodes");
-    for (int64_t k = 0; k < slots; ++k)
-      for (int q = 0; q < 2; ++q) {
-        ch[8 * k + 4 * q] = w[k].child[q].x;
-        ch[8 * k + 4 * q + 1] = w[k].child[q].y;
-        ch[8 * k + 4 * q + 2] = w[k].child[q].z;
-        ch[8 * k + 4 * q + 3] = w[k].child[q].w;
-      }
-  } else {
-    std::vector<rt::WNode> w((size_t)slots);
-    RT_CUDA(cudaMemcpy(w.data(), s->wide, sizeof(rt::WNode) * slots, cudaMemcpyDeviceToHost), "read wide nodes");
-    for (int64_t k = 0; k < slots; ++k) {
-      ch[4 * k] = w[k].child.x;
-      ch[4 * k + 1] = w[k].child.y;
-      ch[4 * k + 2] = w[k].child.z;
-      ch[4 * k + 3] = w[k].child.w;
-    }
+  {
+    // gathered on the device: only the references cross to the host
+    int4* refs = nullptr;
+    RT_CUDA(dev_alloc(&refs, slots * (width / 4)), "alloc child references");
+    const int64_t blocks = (slots + 255) / 256;
+    const int grid = (int)(blocks < 4 * (int64_t)sm_count_dev() ? blocks : 4 * (int64_t)sm_count_dev());
+    cudaStream_t st = (cudaStream_t)stream;
+    k_child_refs<<<grid, 256, 0, st>>>(width == 8 ? nullptr : s->wide, width == 8 ? s->wide8 : nullptr, slots, refs);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(ch.data(), refs, sizeof(int32_t) * (size_t)slots * width, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(refs);
+    RT_CUDA(e, "read child references");
   }
   std::vector<std::pair<int32_t, int32_t>> st{{c.wide_root, 1}};
   int64_t nw = 0;
