@@ -144,3 +144,18 @@ def test_library_icosphere_order_high_levels_sampled_without_gpu(level):
                             np.arange(n - per_face - 1000, n - per_face + 1000), np.arange(n - 3000, n)])
     got = np.array([lib.rt_launch_index(rtbvh.RT_RAYS_ICOSPHERE, level, int(s)) for s in slots], dtype=np.int64)
     assert np.array_equal(got, perm[slots])
+
+
+def test_library_launch_index_many_counts_without_gpu():
+    # 52 distinct seeded ray counts from 1 to 3M, which meet every band width
+    # from 8 to 10,946 (both parities of the step rule): sampled slots of each
+    # against the brute-force azimuth sort
+    lib = rtbvh.lib()
+    rng = np.random.default_rng(2208)
+    counts = np.unique(np.r_[np.exp(rng.uniform(0, np.log(3e6), 58)).astype(np.int64), 1, 3_000_000])
+    for n in counts:
+        n = int(n)
+        perm = fibonacci_launch_perm(n)
+        k = np.unique(np.r_[rng.integers(0, n, 300), np.arange(max(0, n - 40), n)])
+        got = np.array([lib.rt_launch_index(rtbvh.RT_RAYS_FIBONACCI, n, int(s)) for s in k], dtype=np.int64)
+        assert np.array_equal(got, perm[k]), n
